@@ -169,6 +169,17 @@ def perturbation_2d(p, seed, amplitude):
     return up * scale, vp * scale
 
 
+def _solve_equilibrated(A, b):
+    """Dense LU solve (partial pivoting) of a batch of real systems A x = b
+    with complex b, after scaling every row to unit max-norm.  The tau
+    systems mix rows of very different size (boundary rows ~ n^2, viscous
+    rows ~ nu n^4); equilibration changes only the rounding of the LU, not the
+    discrete system."""
+    sc = 1.0 / np.max(np.abs(A), axis=-1)
+    return np.linalg.solve((A * sc[..., :, None]).astype(complex),
+                           (b * sc)[..., None])[..., 0]
+
+
 # ----------------------------------------------------------------------------
 # The channel
 # ----------------------------------------------------------------------------
@@ -296,7 +307,7 @@ class Channel2D:
             b[m, :N - 2] = R[m, :N - 2]
             b[m, N - 2] = (p.dt / a0) * R[m].sum()
             b[m, N - 1] = (p.dt / a0) * (sgn * R[m]).sum()
-        return np.linalg.solve(A.astype(complex), b[..., None])[..., 0]
+        return _solve_equilibrated(A, b)
 
     def solve_velocity(self, Rq, a0):
         """Velocity tau systems.  nu = beta / Re.
@@ -319,7 +330,7 @@ class Channel2D:
         A[N - 1] = sgn
         b = Rq[0].copy()
         b[N - 2:] = 0.0
-        u[0] = np.linalg.solve(A, b)
+        u[0] = _solve_equilibrated(A[None], b[None])[0]
         # m >= 1: coupled v-phi
         Z = np.zeros((2 * N, 2 * N))
         for m in range(1, K):
@@ -334,7 +345,7 @@ class Channel2D:
             Z[2 * N - 1, :N] = -sgn * n * n
             rhs = np.zeros(2 * N, dtype=complex)
             rhs[:N - 2] = Rq[m, :N - 2]
-            z = np.linalg.solve(Z, rhs)
+            z = _solve_equilibrated(Z[None], rhs[None])[0]
             v[m] = z[:N]
             u[m] = 1j * (self.D @ v[m]) / self.k[m]
         return u, v
@@ -427,8 +438,12 @@ class Channel2D:
         out["n_mid_band3"] = int(np.sum(np.abs(tr_m - 3.0) <= tau))
         out["n_mid_band0"] = int(np.sum(np.abs(tr_m) <= tau))
         out["mid_sums"] = np.array([[np.sum(qq ** k) for k in range(1, 5)] for qq in q])
+        # blow-up (the paper reports finite-time blow-up below a resolution
+        # threshold, Sec. 2; its criterion is not stated): a non-finite state,
+        # max Tr c above a threshold, or an rms velocity sqrt(2E) above one.
         finite = all(np.all(np.isfinite(a)) for a in s.as_list())
-        blow = (not finite) or out["max_trc"] > p.blowup_trc_max or \
-            float(np.max(np.sqrt(u * u + v * v))) > p.blowup_u_max
-        out["blowup"] = bool(blow or not np.isfinite(out["max_trc"]))
+        blow = (not finite) or not np.isfinite(out["max_trc"]) or \
+            out["max_trc"] > p.blowup_trc_max or \
+            math.sqrt(max(2.0 * out["energy"], 0.0)) > p.blowup_u_max
+        out["blowup"] = bool(blow)
         return out

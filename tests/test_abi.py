@@ -1,0 +1,51 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every function that include/ptt.h declares (no compute calls here)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ptt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ptt_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2606_09468_gb300 as P
+    if not os.path.exists(P.LIB_PATH):
+        from paper_2606_09468_gb300.build import build
+        build()
+    return P.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_2606_09468_gb300 as P
+    names = _declared()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in P.EXPORTS, n
+
+
+def test_status_strings_and_param_checks_without_gpu(lib):
+    import paper_2606_09468_gb300 as P
+    assert P.ptt_status_string(0) == "ok"
+    assert "blow" in P.ptt_status_string(1)
+    # host-side validation only (no device call)
+    assert P.ptt_workspace_size([P.make_params(nx=64, ny=65)]) > 0
+    for bad in (dict(nx=63), dict(ny=66), dict(nz=4), dict(nx=14), dict(beta=0.0)):
+        with pytest.raises(P.PttError):
+            P.ptt_workspace_size([P.make_params(**bad)])
+
+
+def test_workspace_grows_with_members(lib):
+    import paper_2606_09468_gb300 as P
+    one = P.ptt_workspace_size([P.make_params(nx=64, ny=65)])
+    two = P.ptt_workspace_size([P.make_params(nx=64, ny=65)] * 2)
+    rag = P.ptt_workspace_size([P.make_params(nx=64, ny=65), P.make_params(nx=128, ny=97)])
+    assert one < two < rag
