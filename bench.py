@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Benchmark of the FP64 pseudo-spectral sPTT channel step on GB300.
+
+Metric: grid-point-steps/s (unpadded grid points x steps / second), whole job.
+Workload: the 2D resolution sweep of the paper's method, Nx in {128, 256, 512}
+x Ny in {97, 129, 257}, seeds 0-2 (27 independent channel runs, the paper's
+fluid: Wi = 150, Re = 1e-2, beta = 0.9, eps = kappa = 5e-5, Lx = 10, dt = 1e-3,
+laminar sPTT state + seeded perturbation of amplitude 1e-3), advanced together
+in FP64; one bench step = one SBDF step of every run (explicit right-hand
+side, tau solves, diagnostics).  Synthetic seeded data.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on this machine's host cores (each
+step: one oracle step of one sweep run, cycling through the nine shapes).
+Under torchrun with N > 1 every rank advances its own 27-run ensemble (seeds
+offset by rank; no data-path collective: "weak" scaling); only the timing is
+reduced (max over ranks).
+"""
+import argparse
+import ctypes
+import datetime as dt
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ptt_inputs as I  # noqa: E402
+
+METRIC = "grid-point-steps/s"
+WORKLOAD = ("2D sPTT channel sweep, FP64: Nx in {128,256,512} x Ny in {97,129,257} x "
+            "seeds {0,1,2} (27 runs), Lx=10, Wi=150, Re=1e-2, beta=0.9, eps=kappa=5e-5, "
+            "dt=1e-3, laminar + seeded perturbation 1e-3")
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); measured DFMA loop: 1.197
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------ clock sampler
+class Clocks:
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.6)
+        except OSError:
+            self.proc = None
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                ts = dt.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[3][i] == "Active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside) if inside else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "reasons": reasons, "samples": len(inside)}
+
+
+# ----------------------------------------------------------- CPU baselines
+CPU_SAMPLE = "one SBDF step (from the initial state) of one run of each of the 9 sweep shapes, seed 0"
+
+
+def cpu_baseline():
+    """The oracle, as it stands, timed on this machine's host cores in a
+    subprocess with an explicit BLAS thread count."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores),
+               MKL_NUM_THREADS=str(cores), CUDA_VISIBLE_DEVICES="")
+    code = (
+        "import time, json, sys\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import ptt_inputs as I\n"
+        "from oracle.ptt2d import Channel2D, Params\n"
+        "pts = 0; sec = 0.0\n"
+        "for nx in I.SWEEP_NX:\n"
+        "  for ny in I.SWEEP_NY:\n"
+        "    ch = Channel2D(Params(nx=nx, ny=ny, dt=I.DT, **I.PAPER))\n"
+        "    ch.init_state(0, I.AMPLITUDE)\n"
+        "    t = time.perf_counter(); ch.step(); sec += time.perf_counter() - t\n"
+        "    pts += nx * ny\n"
+        "print(json.dumps({'points': pts, 'seconds': sec}))\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"value": None, "unit": METRIC, "cores": cores, "kind": "oracle",
+                "sample": CPU_SAMPLE, "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["points"] / d["seconds"], "unit": METRIC, "cores": cores,
+            "kind": "oracle", "sample": CPU_SAMPLE, "seconds": round(d["seconds"], 3)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    from oracle.ptt2d import Channel2D, Params
+    shapes = [(nx, ny) for nx in I.SWEEP_NX for ny in I.SWEEP_NY]
+    runs = {}
+    for sh in shapes:
+        ch = Channel2D(Params(nx=sh[0], ny=sh[1], dt=I.DT, **I.PAPER))
+        ch.init_state(0, I.AMPLITUDE)
+        runs[sh] = ch
+    k = 0
+    for _ in range(args.warmup):
+        runs[shapes[k % 9]].step()
+        k += 1
+    pts, sec = 0, 0.0
+    for _ in range(args.steps):
+        sh = shapes[k % 9]
+        t = time.perf_counter()
+        runs[sh].step()
+        sec += time.perf_counter() - t
+        pts += sh[0] * sh[1]
+        k += 1
+    val = pts / sec
+    out = {"metric": METRIC, "value": val, "unit": METRIC, "impl": "reference",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sec / max(args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "parallelism": "host cores (oracle)"},
+           "cpu_baseline": {"value": val, "unit": METRIC, "cores": cores, "kind": "oracle",
+                            "sample": "each step: one oracle SBDF step of one sweep run, "
+                                      "cycling through the 9 shapes (seed 0)"},
+           "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2606_09468_gb300 as P
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    members = [(nx, ny, s + 3 * rank) for nx, ny, s in I.sweep_members()]
+    params = [P.make_params(nx=nx, ny=ny, dt=I.DT, **I.PAPER) for nx, ny, _ in members]
+    ctx = P.Context(params)
+    for i, (_, _, s) in enumerate(members):
+        ctx.init_state(i, s, I.AMPLITUDE)
+    points = sum(nx * ny for nx, ny, _ in members)
+    stream = ctx.stream
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up
+    ctx.step(args.warmup)
+    assert ctx.synchronize() == P.PTT_OK
+    # timed region: K graph launches, CUDA events on the context stream
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier()
+    clk = clocks.stop(t0, t1)
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    status = ctx.synchronize()
+    launches = ctx.launches_per_step() * args.steps
+    value = world * points * args.steps / (ms * 1e-3)
+
+    # per-stage device times (same workload, ordinary launches + events)
+    st_ms = ctx.time_stages(max(args.steps // 4, 5))
+    nst = max(args.steps // 4, 5)
+    flops, byts, nl = ctx.stage_work()
+    dom = int(np.argmax(st_ms))
+    per_launch_ms = st_ms[dom] / (nst * nl[dom])
+    achieved = flops[dom] / nl[dom] / (per_launch_ms * 1e-3) / 1e12
+    hbm_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm_peak = json.load(fh).get("hbm_gbs")
+    except OSError:
+        pass
+    hbm_achieved = byts[dom] / nl[dom] / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": P.STAGE_KERNELS[dom], "stage": P.STAGE_NAMES[dom],
+                "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)",
+                "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak,
+                "stage_ms_per_step": {P.STAGE_NAMES[i]: st_ms[i] / nst for i in range(P.PTT_NSTAGES)}}
+
+    # end to end through the C ABI: every step carries the complete step input
+    # (state + SBDF history, pinned host memory) in and the step output
+    # (state + history + diagnostics record) out.
+    bufs = []
+    for i in range(len(members)):
+        n = P.ptt_checkpoint_size(ctx.ctx, i)
+        t = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        bufs.append((t, t.numpy()))
+        P.ptt_get_checkpoint(ctx.ctx, i, bufs[-1][1])
+    h2d = sum(b[1].nbytes for b in bufs)
+    d2h = h2d + len(members) * ctypes.sizeof(P.ptt_diag)
+    torch.cuda.synchronize()
+    barrier()
+    ta = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for i in range(len(members)):
+            P.ptt_set_checkpoint(ctx.ctx, i, bufs[i][1])
+        P.ptt_step(ctx.ctx, 1)
+        for i in range(len(members)):
+            P.ptt_diagnostics(ctx.ctx, i, 4)
+            P.ptt_get_checkpoint(ctx.ctx, i, bufs[i][1])
+    torch.cuda.synchronize()
+    tb = time.perf_counter()
+    e2e_s = max_over_ranks(tb - ta)
+    e2e = {"value": world * points * args.e2e_steps / e2e_s, "unit": METRIC,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+
+    if rank != 0:
+        return
+    ws = ctx.nbytes
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "runs": len(members), "grid_points": points,
+                      "parallelism": f"ensemble of independent runs per GPU x {world} GPU",
+                      "l2": f"inputs larger than L2: workspace {ws / 2**30:.2f} GiB per GPU, "
+                            "state + SBDF history re-read every step",
+                      "graph": "one CUDA graph launch per step"},
+           "status": P.ptt_status_string(status),
+           "gpu_launches": launches, "roofline": roofline, "clocks": clk, "e2e": e2e}
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * ptt.h -- C ABI of the GB300-native pseudo-spectral time step for a dilute
+ * sPTT polymer solution in a plane channel.
+ *
+ * The method (Sec. 2 of the paper; Eqs. 1-3):
+ *   d_t c + u.grad c - (grad u)^T.c - c.(grad u)
+ *         = kappa lap c - (c - I)/Wi [1 + eps Tr(c - I)]               (Eq. 1)
+ *   d_t u + u.grad u = -grad p + (beta/Re) lap u
+ *         + (1 - beta)/(Re Wi) div c + (2/Re) x_hat                      (Eq. 2)
+ *   div u = 0                                                            (Eq. 3)
+ * periodic in x (and z), no-slip walls at y = +-1, the wall value of c
+ * advanced by Eq. 1 with kappa = 0 (Sec. 2, boundary conditions).  Space:
+ * Fourier (x) - Chebyshev (y) modes, fully dealiased products (Sec. 2,
+ * numerical details).  Time: fourth-order semi-implicit BDF (SBDF4), started
+ * with SBDF1-3.  Diagnostics: Tr c admissibility counts, volume averages
+ * E = <|u|^2/2> and <Tr c>, and mid-plane statistics (Sec. 3, Eqs. 4-5).
+ *
+ * Conventions shared by every call
+ *  - A "member" is one independent channel run.  A context holds one or more
+ *    members (an ensemble); members with equal (nx, ny) are advanced together
+ *    by the same kernel launches.
+ *  - Only the 2D (z-independent) problem is implemented: nz must be 1.  In 2D
+ *    w = 0 and c_zz = 1 exactly; the five fields are u, v, c_xx, c_xy, c_yy.
+ *  - nx: even, 8 <= nx <= 512, of the form 2^a 3^b 5^c.  ny (Chebyshev
+ *    modes): 9 <= ny <= 513 with ny - 1 of the form 2^a 3^b 5^c.
+ *  - Physical layout (host arrays of ptt_set_state / ptt_get_state):
+ *    double[5][ny][nx], field-major, then y (Gauss-Lobatto point
+ *    y_l = cos(pi l/(ny-1)), l = 0 is the wall y = +1), then x
+ *    (x_j = j lx/nx) fastest.
+ *  - Spectral layout (ptt_get_spectral / ptt_set_spectral): double[5][ny]
+ *    [nx/2][2], field, Chebyshev index n, Fourier index m = 0..nx/2-1
+ *    (k_m = 2 pi m / lx; the Nyquist mode is not stored), (re, im).
+ *  - Device memory: the caller allocates ONE device workspace of at least
+ *    ptt_workspace_size() bytes (256-byte aligned) and owns it; the library
+ *    never allocates or frees device memory.  Host pointers are caller-owned
+ *    and only read or written during the call.
+ *  - Streams: every device operation of a context runs on the stream given
+ *    to ptt_create (a cudaStream_t passed as void*, NULL = legacy default
+ *    stream).  Calls on one context are not re-entrant.
+ *  - Errors: every call returns PTT_OK (0), a negative error code, or
+ *    PTT_BLOWUP (> 0).  Nothing aborts; no exception crosses the ABI.
+ */
+#ifndef PTT_H
+#define PTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTT_OK 0
+#define PTT_BLOWUP 1       /* a member blew up (see ptt_diag.status)           */
+#define PTT_EINVAL (-1)    /* bad argument, size or pointer                      */
+#define PTT_ENOMEM (-2)    /* workspace too small                                */
+#define PTT_ECUDA (-3)     /* a CUDA runtime call failed                         */
+#define PTT_TIMEOUT (-4)   /* a bounded wait expired                             */
+#define PTT_ENOTSUP (-5)   /* valid request this build does not implement        */
+
+#define PTT_FP64 0         /* every step of the path in FP64                     */
+#define PTT_MIXED 1        /* reserved: FP32 transforms, FP64 solves             */
+
+/* Physical and numerical parameters of one member.  Defaults (the paper's
+ * single fluid, Sec. 2): lx = lz = 10, re = 1e-2, wi = 150, beta = 0.9,
+ * eps = 5e-5, kappa = 5e-5, dt = 2.5e-3. */
+typedef struct {
+  int32_t nx, ny, nz;        /* Fourier modes in x, Chebyshev modes in y, nz = 1 */
+  int32_t precision;         /* PTT_FP64                                          */
+  double lx, lz;             /* periodic lengths (walls at y = +-1)               */
+  double re, wi, beta, eps, kappa;
+  double dt;                 /* fixed time step                                   */
+  double blowup_trc_max;     /* blow-up if max Tr c exceeds this (e.g. 1e10)      */
+  double blowup_u_max;       /* blow-up if sqrt(2 E) exceeds this (e.g. 1e3)      */
+} ptt_params;
+
+/* One diagnostics record per member and step (Sec. 3).  Counts are over the
+ * unpadded grid (nx * ny points) or the mid-plane y = 0 (nx points).  The
+ * strict counts are the paper's; the band counts give the points with
+ * |Tr c - 3| <= tau (resp. |Tr c| <= tau), tau = 1e-9 max|Tr c|, whose side
+ * of the threshold rounding decides. */
+typedef struct {
+  int64_t step;              /* steps taken since the state was set               */
+  double t;                  /* step * dt                                          */
+  double energy;             /* E = <|u|^2 / 2>, volume average                   */
+  double mean_trc;           /* <Tr c>, volume average                             */
+  double min_trc, max_trc;   /* over the unpadded grid                             */
+  int64_t n_lt3, n_lt0, n_band3, n_band0;
+  int64_t n_mid_lt3, n_mid_lt0, n_mid_band3, n_mid_band0;
+  /* mid-plane power sums: mid_sums[q][p-1] = sum over the nx mid-plane points
+   * of q^p, p = 1..4, for q = Tr c, u' = u - <u>_x, v, du/dx, dv/dx, du/dy
+   * (slots 6, 7 unused in 2D). */
+  double mid_sums[8][4];
+  int32_t status;            /* PTT_OK or PTT_BLOWUP                               */
+  int32_t reserved;
+} ptt_diag;
+
+typedef struct ptt_ctx ptt_ctx; /* opaque: host metadata, CUDA graph, no data */
+
+/* Bytes of device workspace needed by nmembers members with these params
+ * (one params struct per member).  Returns PTT_EINVAL / PTT_ENOTSUP for
+ * unsupported params. */
+int ptt_workspace_size(const ptt_params* per_member, int32_t nmembers, size_t* bytes);
+
+/* Create a context over the caller's workspace.  per_member points to
+ * nmembers params structs (members may differ in every field; those with
+ * equal nx, ny share launches).  Builds the operator tables on the host and
+ * uploads them; the members' states are zero until ptt_init_state /
+ * ptt_set_state.  Synchronous. */
+int ptt_create(const ptt_params* per_member, int32_t nmembers, void* d_workspace,
+               size_t bytes, void* cuda_stream, ptt_ctx** out);
+
+/* Laminar sPTT state (the kappa = 0 closed form of Eqs. 1-2 for channel flow)
+ * plus a seeded divergence-free, no-slip perturbation of maximum grid
+ * amplitude `amplitude` (stream function (1 - y^2)^2 g(x, y), g with modes
+ * 1 <= m <= 4, n <= 8 drawn from the counter-based splitmix64 stream of
+ * `seed`).  Stands in for the paper's turbulent initial snapshot (Sec. 2),
+ * which is not available.  Resets the step counter and the SBDF history.
+ * Synchronous. */
+int ptt_init_state(ptt_ctx* ctx, int32_t member, uint64_t seed, double amplitude);
+
+/* Set / get the state of one member as physical values on the unpadded grid
+ * (layout above).  set: interpolates (Fourier analysis without the Nyquist
+ * mode, Chebyshev interpolation at the Gauss-Lobatto points), resets the step
+ * counter and history.  Synchronous. */
+int ptt_set_state(ptt_ctx* ctx, int32_t member, const double* h_phys);
+int ptt_get_state(ptt_ctx* ctx, int32_t member, double* h_phys);
+
+/* Spectral coefficients of the current state (layout above).  set resets the
+ * step counter and history.  Synchronous. */
+int ptt_set_spectral(ptt_ctx* ctx, int32_t member, const double* h_spec);
+int ptt_get_spectral(ptt_ctx* ctx, int32_t member, double* h_spec);
+
+/* Advance every member by nsteps steps (asynchronous on the context stream;
+ * each step is one CUDA-graph launch).  A member that blows up stops and
+ * keeps its last record's status; the others continue.  Returns PTT_OK or an
+ * error; blow-up is reported by ptt_synchronize / ptt_diagnostics. */
+int ptt_step(ptt_ctx* ctx, int32_t nsteps);
+
+/* Wait for the context stream.  Returns PTT_BLOWUP if any member has blown
+ * up, PTT_OK otherwise, or PTT_ECUDA. */
+int ptt_synchronize(ptt_ctx* ctx);
+
+/* Copy out the diagnostics records of `member` written since the previous
+ * call (oldest first; at most max_records, the device ring keeps the last
+ * 1024 steps).  Synchronous. */
+int ptt_diagnostics(ptt_ctx* ctx, int32_t member, ptt_diag* h_out, int32_t max_records,
+                    int32_t* n_written);
+
+/* Dealiased explicit right-hand side of the current state of one member
+ * (Eq. 1 without kappa lap c; Eq. 2 without pressure and viscous terms):
+ * N_cxx, N_cxy, N_cyy, H_x, H_y in the spectral layout above (5 fields,
+ * H_x includes the forcing 2/Re on its mean mode).  Does not advance the
+ * state.  Synchronous. */
+int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec5);
+
+/* Checkpoint of one member: state, SBDF history and step counter, so that a
+ * restart continues bit for bit.  ptt_checkpoint_size gives the bytes.
+ * Synchronous. */
+int ptt_checkpoint_size(ptt_ctx* ctx, int32_t member, size_t* bytes);
+int ptt_get_checkpoint(ptt_ctx* ctx, int32_t member, void* h_buf, size_t bytes);
+int ptt_set_checkpoint(ptt_ctx* ctx, int32_t member, const void* h_buf, size_t bytes);
+
+/* Stages of one step, in launch order: 0 inverse Chebyshev transforms
+ * (9 fields, with d/dy), 1 fused x transforms + products of Eqs. 1-2,
+ * 2 forward Chebyshev transforms (5 fields), 3 explicit linear terms and
+ * SBDF right-hand sides, 4 tau solves, 5 velocity from continuity,
+ * 6 diagnostics. */
+#define PTT_NSTAGES 7
+
+/* Advance every member by nsteps steps with ordinary (non-graph) launches,
+ * recording CUDA events on the context stream around each stage, and add the
+ * device time of stage s, summed over groups and steps, to ms[s]
+ * (milliseconds, s < PTT_NSTAGES; the caller zeroes ms).  Same arithmetic as
+ * ptt_step.  Synchronous. */
+int ptt_time_stages(ptt_ctx* ctx, int32_t nsteps, double* ms);
+
+/* Algorithmic work of one step of all members, per stage: flops[s] (complex
+ * FFT of length n counted 5 n log2 n, products and recurrences by their
+ * operation counts), bytes[s] (compulsory device-memory reads + writes of
+ * the stage's inputs and outputs), launches[s] (kernel launches). */
+int ptt_stage_work(ptt_ctx* ctx, double* flops, double* bytes, int32_t* launches);
+
+/* Number of kernel launches one step makes (for launch accounting). */
+int ptt_launches_per_step(ptt_ctx* ctx, int32_t* n);
+
+/* Release host resources (the workspace stays the caller's). */
+int ptt_destroy(ptt_ctx* ctx);
+
+/* Text of the last CUDA failure of this thread (which call, which line,
+ * cudaGetErrorString), "" if none.  Static storage, valid until the next
+ * failing call on this thread. */
+const char* ptt_last_error(void);
+
+/* Static string naming a status code. */
+const char* ptt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTT_H */

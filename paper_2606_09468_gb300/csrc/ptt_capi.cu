@@ -1,0 +1,820 @@
+// Host side of the sPTT channel library: parameter checks, plans, operator
+// tables, workspace carving, initial condition, CUDA-graph step, C ABI.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "ptt_internal.h"
+
+using namespace ptt;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+bool smooth235(long long n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+int next_smooth(int n) {
+  while (!smooth235(n)) ++n;
+  return n;
+}
+
+// cos and sin of 2 pi k / n with exact integer reduction to [0, pi/4].
+void cis(long long k, long long n, double* c, double* s) {
+  long long q = (4 * (k % n) + 4 * n) % (4 * n);  // angle = (pi/2) q / n, q in [0, 4n)
+  double sgn_s = 1.0, sgn_c = 1.0;
+  if (q > 2 * n) { q = 4 * n - q; sgn_s = -1.0; }   // (pi, 2 pi) -> (0, pi)
+  if (q > n) { q = 2 * n - q; sgn_c = -1.0; }       // (pi/2, pi) -> (0, pi/2)
+  bool swap = false;
+  if (2 * q > n) { q = n - q; swap = true; }         // (pi/4, pi/2) -> (0, pi/4)
+  const double th = 0.5 * kPi * (double)q / (double)n;
+  double cc = std::cos(th), ss = std::sin(th);
+  if (swap) std::swap(cc, ss);
+  *c = sgn_c * cc;
+  *s = sgn_s * ss;
+}
+
+struct HostPlan {
+  int n = 0;
+  std::vector<int> radix;
+};
+
+HostPlan make_plan(int n) {
+  HostPlan p;
+  p.n = n;
+  int r = n;
+  for (int f : {4, 2, 3, 5})
+    while (r % f == 0) { p.radix.push_back(f); r /= f; }
+  return p;
+}
+
+// Quasi-tridiagonal operator tables of (alpha - beta D^2) a = R on the
+// tau rows n <= N-3 with one Dirichlet-type sum row per parity.
+// For parity p the unknowns a_n (n = p mod 2) satisfy, for n >= 2,
+//   l_n a_{n-2} + d_n a_n + u_n a_{n+2} = r_n,
+//   l_n = -alpha c_{n-2} w1_n, d_n = beta + [n <= N-3] alpha w2_n,
+//   u_n = -[n <= N-5] alpha w3_n,
+// w1 = 1/(4n(n-1)), w2 = 1/(2(n^2-1)), w3 = 1/(4n(n+1)), c_0 = 2, c_n = 1.
+// (These rows follow from writing a_n through the coefficients of D^2 a,
+// which the tau rows fix.)  Backward elimination a_n = P_n + Q_n a_{n-2};
+// Q, inv = 1/(d_n + u_n Q_{n+2}) and F_n = 1 + V_{n+2} (V the coefficient of
+// a_{n-2} in sum_{j >= n} a_j) do not depend on R; G = 1/(1 + V_{p+2}).
+void qt_tables(int N, double alpha, double beta, const double* w1, const double* w2,
+               const double* w3, int p, double* Q, double* inv, double* F, double* G,
+               size_t stride) {
+  const int nl = ((N - 1 - p) & ~1) + p;
+  double Qn2 = 0.0, Vn2 = 0.0;
+  for (int n = nl; n >= p + 2; n -= 2) {
+    const double c = (n == 2) ? 2.0 : 1.0;
+    const double l = -alpha * c * w1[n];
+    const double d = beta + (n <= N - 3 ? alpha * w2[n] : 0.0);
+    const double u = (n <= N - 5) ? -alpha * w3[n] : 0.0;
+    const double iv = 1.0 / (d + u * Qn2);
+    const double q = -l * iv;
+    const double f = 1.0 + Vn2;
+    Q[(size_t)n * stride] = q;
+    inv[(size_t)n * stride] = iv;
+    F[(size_t)n * stride] = f;
+    Qn2 = q;
+    Vn2 = f * q;
+  }
+  *G = 1.0 / (1.0 + Vn2);
+}
+
+// Host twin of the device solve on real data (used for the homogeneous
+// solutions of the influence-matrix step).
+void qt_solve_host(int N, int p, double alpha, const double* R, double* out, const double* Q,
+                   const double* inv, const double* F, double G, const double* w1,
+                   const double* w2, const double* w3, double g, double rsign, size_t stride) {
+  const int nl = ((N - 1 - p) & ~1) + p;
+  double Pn2 = 0.0, U = 0.0, Rp2 = 0.0, R0 = rsign * R[(size_t)nl * stride];
+  for (int n = nl; n >= p + 2; n -= 2) {
+    const double Rm2 = rsign * R[(size_t)(n - 2) * stride];
+    const double c = (n == 2) ? 2.0 : 1.0;
+    double r = -c * w1[n] * Rm2;
+    if (n <= N - 3) r += w2[n] * R0;
+    double un = 0.0;
+    if (n <= N - 5) { r -= w3[n] * Rp2; un = -alpha * w3[n]; }
+    const double P = (r - un * Pn2) * inv[(size_t)n * stride];
+    out[(size_t)n * stride] = P;
+    U += F[(size_t)n * stride] * P;
+    Pn2 = P;
+    Rp2 = R0;
+    R0 = Rm2;
+  }
+  double a = (g - U) * G;
+  out[(size_t)p * stride] = a;
+  for (int n = p + 2; n <= nl; n += 2) {
+    a = out[(size_t)n * stride] + Q[(size_t)n * stride] * a;
+    out[(size_t)n * stride] = a;
+  }
+}
+
+const double kSA0[4] = {1.0, 1.5, 11.0 / 6.0, 25.0 / 12.0};
+
+// ------------------------------------------------------- initial condition
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+// splitmix64 as a counter-based stream: output k of seed s.
+double splitmix_uniform(uint64_t seed, uint64_t k) {
+  const uint64_t z = mix64(seed + (k + 1) * 0x9E3779B97F4A7C15ULL);
+  return 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+// c_xy = s of the steady laminar sPTT channel (kappa = 0): root of
+// 2 beta eps s^3 + s + 2 Wi y = 0, by Newton from the Oldroyd-B value
+// (monotone: the cubic is increasing, concave where the root lies).
+double laminar_root(double y, double wi, double beta, double eps) {
+  double s = -2.0 * wi * y;
+  if (eps == 0.0 || y == 0.0) return s;
+  const double a = 2.0 * beta * eps;
+  for (int it = 0; it < 200; ++it) {
+    const double f = a * s * s * s + s + 2.0 * wi * y;
+    const double ds = f / (3.0 * a * s * s + 1.0);
+    s -= ds;
+    if (std::fabs(ds) <= 1e-17 * std::fabs(s)) break;
+  }
+  return s;
+}
+
+double laminar_F(double s, double beta, double eps) {
+  const double s2 = s * s;
+  return 0.5 * s2 + 0.5 * eps * (1.0 + 3.0 * beta) * s2 * s2 + 2.0 * beta * eps * eps * s2 * s2 * s2;
+}
+
+// Physical initial fields [5][ny][nx]: laminar sPTT + perturbation.
+void initial_fields(const ptt_params& p, uint64_t seed, double amp, std::vector<double>& out) {
+  const int nx = p.nx, ny = p.ny;
+  out.assign((size_t)5 * ny * nx, 0.0);
+  std::vector<double> y(ny), U(ny), cxx(ny), cxy(ny);
+  const double sw = laminar_root(1.0, p.wi, p.beta, p.eps);
+  const double Fw = laminar_F(sw, p.beta, p.eps);
+  for (int l = 0; l < ny; ++l) {
+    double c, s;
+    cis(l, 2 * (ny - 1), &c, &s);  // y_l = cos(pi l/(ny-1))
+    y[l] = c;
+    const double r = laminar_root(c, p.wi, p.beta, p.eps);
+    U[l] = -(laminar_F(r, p.beta, p.eps) - Fw) / (2.0 * p.wi * p.wi);
+    cxx[l] = 1.0 + 2.0 * r * r;
+    cxy[l] = r;
+  }
+  // perturbation: psi = (1-y^2)^2 g, g = sum_{m=1..4, n<=8} (A cos + B sin) T_n(y)
+  std::vector<double> up((size_t)ny * nx, 0.0), vp((size_t)ny * nx, 0.0);
+  for (int m = 1; m <= 4; ++m) {
+    const double km = 2.0 * kPi * m / p.lx;
+    double A[9], B[9];
+    for (int n = 0; n < 9; ++n) {
+      A[n] = splitmix_uniform(seed, (uint64_t)(((m - 1) * 9 + n) * 2 + 0));
+      B[n] = splitmix_uniform(seed, (uint64_t)(((m - 1) * 9 + n) * 2 + 1));
+    }
+    for (int l = 0; l < ny; ++l) {
+      const double yy = y[l];
+      // T_n and T_n' = n U_{n-1} by their recurrences
+      double T[9], dT[9], Uc[9];
+      T[0] = 1.0; T[1] = yy;
+      Uc[0] = 1.0; Uc[1] = 2.0 * yy;
+      for (int n = 2; n < 9; ++n) { T[n] = 2 * yy * T[n - 1] - T[n - 2]; Uc[n] = 2 * yy * Uc[n - 1] - Uc[n - 2]; }
+      dT[0] = 0.0;
+      for (int n = 1; n < 9; ++n) dT[n] = n * Uc[n - 1];
+      double ga = 0, gb = 0, dga = 0, dgb = 0;
+      for (int n = 0; n < 9; ++n) { ga += A[n] * T[n]; gb += B[n] * T[n]; dga += A[n] * dT[n]; dgb += B[n] * dT[n]; }
+      const double w = (1 - yy * yy) * (1 - yy * yy), dw = -4.0 * yy * (1 - yy * yy);
+      const double pa = w * ga, pb = w * gb, dpa = dw * ga + w * dga, dpb = dw * gb + w * dgb;
+      for (int j = 0; j < nx; ++j) {
+        double c, s;
+        cis((long long)m * j, nx, &c, &s);
+        up[(size_t)l * nx + j] += dpa * c + dpb * s;
+        vp[(size_t)l * nx + j] += km * (pa * s - pb * c);
+      }
+    }
+  }
+  double mx = 0.0;
+  for (size_t i = 0; i < up.size(); ++i) mx = std::fmax(mx, std::sqrt(up[i] * up[i] + vp[i] * vp[i]));
+  const double sc = (mx > 0.0) ? amp / mx : 0.0;
+  const size_t F = (size_t)ny * nx;
+  for (int l = 0; l < ny; ++l)
+    for (int j = 0; j < nx; ++j) {
+      const size_t i = (size_t)l * nx + j;
+      out[0 * F + i] = U[l] + sc * up[i];
+      out[1 * F + i] = sc * vp[i];
+      out[2 * F + i] = cxx[l];
+      out[3 * F + i] = cxy[l];
+      out[4 * F + i] = 1.0;
+    }
+}
+
+// ------------------------------------------------------------- layout
+struct Carver {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct Group {
+  int nx, ny;
+  std::vector<int> members;  // global member ids
+  GroupDev d{};
+  HostPlan hp[5];            // P, Mx, nx, Pu, Pe
+};
+
+int check_params(const ptt_params& p) {
+  if (p.nz != 1) return PTT_ENOTSUP;
+  if (p.precision != PTT_FP64) return PTT_ENOTSUP;
+  if (p.nx < 8 || p.nx > 512 || (p.nx & 1) || !smooth235(p.nx)) return PTT_EINVAL;
+  if (p.ny < 9 || p.ny > 513 || !smooth235(p.ny - 1)) return PTT_EINVAL;
+  if (!(p.lx > 0) || !(p.re > 0) || !(p.wi > 0) || !(p.dt > 0)) return PTT_EINVAL;
+  if (!(p.beta > 0 && p.beta <= 1) || !(p.eps >= 0) || !(p.kappa >= 0)) return PTT_EINVAL;
+  return PTT_OK;
+}
+
+void group_sizes(int nx, int ny, Group& g) {
+  GroupDev& d = g.d;
+  d.nx = nx;
+  d.K = nx / 2;
+  d.N = ny;
+  d.Mx = next_smooth(3 * nx / 2 - 2);
+  int M = (3 * ny - 2 + 1) / 2;
+  while (!smooth235(2LL * M)) ++M;
+  d.M = M;
+  d.P = 2 * M;
+  d.Pu = 2 * (ny - 1);
+  d.Pe = 4 * (ny - 1);
+  const size_t target = 96 * 1024;
+  auto cols = [&](int P) {
+    long long c = (long long)(target / smem_ycols(1, P));
+    if (c < 1) c = 1;
+    if (c > 16) c = 16;
+    return (int)c;
+  };
+  d.Ccol = cols(d.P);
+  d.CcolE = cols(d.Pe);
+  g.hp[0] = make_plan(d.P);
+  g.hp[1] = make_plan(d.Mx);
+  g.hp[2] = make_plan(nx);
+  g.hp[3] = make_plan(d.Pu);
+  g.hp[4] = make_plan(d.Pe);
+}
+
+// Carve (or, with base == nullptr, size) all device arrays.
+void carve(std::vector<Group>& groups, Carver& cv) {
+  for (Group& g : groups) {
+    GroupDev& d = g.d;
+    const int nb = (int)g.members.size();
+    d.nb = nb;
+    const size_t NK = (size_t)d.N * d.K, rows = (size_t)d.M + 1, Je = 2 * (size_t)d.N - 1;
+    d.prm = cv.take<MemberPrm>(nb);
+    d.status = cv.take<int>(nb);
+    d.count = cv.take<long long>(nb);
+    d.X = cv.take<double2>((size_t)nb * 5 * NK);
+    d.Eh = cv.take<double2>((size_t)4 * nb * 4 * NK);
+    d.Nh = cv.take<double2>((size_t)4 * nb * 4 * NK);
+    d.Yp = cv.take<double2>((size_t)nb * 9 * rows * d.K);
+    d.Zp = cv.take<double2>((size_t)nb * 5 * rows * d.K);
+    d.NR = cv.take<double2>((size_t)nb * 5 * NK);
+    d.Rb = cv.take<double2>((size_t)nb * 4 * NK);
+    d.qt = cv.take<double>((size_t)nb * 4 * 3 * 3 * NK);
+    d.qtG = cv.take<double>((size_t)nb * 4 * 3 * 2 * d.K);
+    d.vh = cv.take<double>((size_t)nb * 4 * NK);
+    d.vhS = cv.take<double>((size_t)nb * 4 * 2 * d.K);
+    d.wrow = cv.take<double>((size_t)3 * d.N);
+    d.ccw = cv.take<double>(Je);
+    d.DY = cv.take<double2>((size_t)nb * 4 * Je * d.K);
+    d.DV = cv.take<double>((size_t)nb * 2 * d.N * d.nx);
+    d.part = cv.take<double>((size_t)nb * kPart);
+    d.DM = nullptr;
+    d.ring = cv.take<ptt_diag>((size_t)nb * kRing);
+    d.stage = cv.take<double>((size_t)5 * d.N * d.nx);
+    d.stageS = cv.take<double2>((size_t)5 * NK);
+    FftPlan* pls[5] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe};
+    for (int i = 0; i < 5; ++i) {
+      pls[i]->n = g.hp[i].n;
+      pls[i]->nst = (int)g.hp[i].radix.size();
+      for (int s = 0; s < pls[i]->nst; ++s) pls[i]->radix[s] = g.hp[i].radix[s];
+      pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
+    }
+  }
+}
+
+std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
+  std::map<std::pair<int, int>, int> idx;
+  std::vector<Group> groups;
+  for (int i = 0; i < nmem; ++i) {
+    auto key = std::make_pair(pm[i].nx, pm[i].ny);
+    auto it = idx.find(key);
+    if (it == idx.end()) {
+      idx[key] = (int)groups.size();
+      Group g;
+      g.nx = pm[i].nx;
+      g.ny = pm[i].ny;
+      group_sizes(g.nx, g.ny, g);
+      groups.push_back(std::move(g));
+      it = idx.find(key);
+    }
+    groups[it->second].members.push_back(i);
+  }
+  return groups;
+}
+
+}  // namespace
+
+struct ptt_ctx {
+  std::vector<ptt_params> prm;
+  std::vector<Group> groups;
+  std::vector<std::pair<int, int>> where;  // member -> (group, index in group)
+  std::vector<long long> last_read;        // last diagnostics step returned
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+  int device = 0;
+};
+
+thread_local char g_last_error[512] = "";
+
+int fail_cuda(cudaError_t e, const char* what, int line) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s (line %d): %s", what, line,
+                cudaGetErrorString(e));
+  return PTT_ECUDA;
+}
+
+#define CK(x)                                             \
+  do {                                                    \
+    cudaError_t e_ = (x);                                 \
+    if (e_ != cudaSuccess) return fail_cuda(e_, #x, __LINE__); \
+  } while (0)
+
+extern "C" {
+
+int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
+  if (!pm || nmem <= 0 || !bytes) return PTT_EINVAL;
+  for (int i = 0; i < nmem; ++i) {
+    int s = check_params(pm[i]);
+    if (s) return s;
+  }
+  std::vector<Group> groups = make_groups(pm, nmem);
+  for (Group& g : groups) {
+    if (smem_xfused(g.d.Mx) > 227 * 1024) return PTT_EINVAL;
+  }
+  Carver cv;
+  carve(groups, cv);
+  *bytes = cv.off + 256;
+  return PTT_OK;
+}
+
+int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, void* stream,
+               ptt_ctx** out) {
+  if (!out) return PTT_EINVAL;
+  *out = nullptr;
+  size_t need = 0;
+  int s = ptt_workspace_size(pm, nmem, &need);
+  if (s) return s;
+  if (!d_ws || ((uintptr_t)d_ws & 255)) return PTT_EINVAL;
+  if (bytes < need) return PTT_ENOMEM;
+  std::unique_ptr<ptt_ctx> c(new (std::nothrow) ptt_ctx());
+  if (!c) return PTT_ENOMEM;
+  c->prm.assign(pm, pm + nmem);
+  c->groups = make_groups(pm, nmem);
+  c->stream = (cudaStream_t)stream;
+  CK(cudaGetDevice(&c->device));
+  Carver cv;
+  cv.base = (char*)d_ws;
+  carve(c->groups, cv);
+  c->where.assign(nmem, {0, 0});
+  c->last_read.assign(nmem, -1);
+  int optin = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  for (Group& g : c->groups)
+    if (smem_xfused(g.d.Mx) > (size_t)optin) return PTT_EINVAL;
+  CK(set_kernel_attributes(optin));
+  CK(cudaMemsetAsync(d_ws, 0, need - 256, c->stream));
+  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+    Group& g = c->groups[gi];
+    GroupDev& d = g.d;
+    const int nb = d.nb, N = d.N, K = d.K;
+    const size_t NK = (size_t)N * K;
+    for (int i = 0; i < nb; ++i) c->where[g.members[i]] = {(int)gi, i};
+    // member parameters
+    std::vector<MemberPrm> mp(nb);
+    for (int i = 0; i < nb; ++i) {
+      const ptt_params& p = pm[g.members[i]];
+      MemberPrm& q = mp[i];
+      q.lx = p.lx; q.re = p.re; q.wi = p.wi; q.beta = p.beta; q.eps = p.eps;
+      q.kappa = p.kappa; q.dt = p.dt;
+      q.inv_wi = 1.0 / p.wi;
+      q.gam = (1.0 - p.beta) / (p.re * p.wi);
+      q.nu = p.beta / p.re;
+      q.forcing = 2.0 / p.re;
+      q.trc_max = p.blowup_trc_max > 0 ? p.blowup_trc_max : 1e300;
+      q.u_max = p.blowup_u_max > 0 ? p.blowup_u_max : 1e300;
+    }
+    CK(cudaMemcpyAsync(d.prm, mp.data(), nb * sizeof(MemberPrm), cudaMemcpyHostToDevice, c->stream));
+    // row weights of the quasi-tridiagonal form
+    std::vector<double> w(3 * (size_t)N, 0.0);
+    for (int n = 2; n < N; ++n) {
+      w[n] = 1.0 / (4.0 * n * (n - 1));
+      w[N + n] = 1.0 / (2.0 * ((double)n * n - 1.0));
+      w[2 * N + n] = 1.0 / (4.0 * n * (n + 1));
+    }
+    // operator tables per member, SBDF order, system, mode, parity
+    std::vector<double> qt((size_t)nb * 4 * 3 * 3 * NK, 0.0), qtG((size_t)nb * 4 * 3 * 2 * K, 0.0);
+    std::vector<double> vh((size_t)nb * 4 * NK, 0.0), vhS((size_t)nb * 4 * 2 * K, 0.0);
+    std::vector<double> phi(N), rz(N, 0.0);
+    for (int i = 0; i < nb; ++i) {
+      const ptt_params& p = pm[g.members[i]];
+      const double nu = p.beta / p.re;
+      for (int o = 0; o < 4; ++o) {
+        const double a0dt = kSA0[o] / p.dt;
+        for (int m = 0; m < K; ++m) {
+          const double km = 2.0 * kPi * m / p.lx, k2 = km * km;
+          const double al[3] = {a0dt + p.kappa * k2, a0dt + nu * k2, k2};
+          const double be[3] = {p.kappa, nu, 1.0};
+          for (int ts = 0; ts < 3; ++ts) {
+            if (ts == 0 && p.kappa == 0.0) continue;
+            if (ts == 2 && m == 0) continue;
+            double* base = &qt[((((size_t)i * 4 + o) * 3 + ts) * 3) * NK + m];
+            for (int par = 0; par < 2; ++par) {
+              qt_tables(N, al[ts], be[ts], w.data(), w.data() + N, w.data() + 2 * N, par, base,
+                        base + NK, base + 2 * NK,
+                        &qtG[((((size_t)i * 4 + o) * 3 + ts) * 2 + par) * K + m], K);
+            }
+          }
+          if (m == 0) continue;
+          // homogeneous solutions of the influence-matrix step:
+          // phi_h: rows of (alpha - nu D^2) phi = 0 with the parity sum = 1,
+          // v_h: rows of (k^2 - D^2) v = -phi_h with the parity sum = 0.
+          const double* T1 = &qt[((((size_t)i * 4 + o) * 3 + 1) * 3) * NK + m];
+          const double* T2 = &qt[((((size_t)i * 4 + o) * 3 + 2) * 3) * NK + m];
+          double* vo = &vh[((size_t)i * 4 + o) * NK + m];
+          for (int par = 0; par < 2; ++par) {
+            const double G1 = qtG[((((size_t)i * 4 + o) * 3 + 1) * 2 + par) * K + m];
+            const double G2 = qtG[((((size_t)i * 4 + o) * 3 + 2) * 2 + par) * K + m];
+            // tables are strided by K; solve on contiguous copies
+            std::vector<double> q1(N), i1(N), f1(N), q2(N), i2(N), f2(N), vv(N, 0.0);
+            for (int n = 0; n < N; ++n) {
+              q1[n] = T1[(size_t)n * K]; i1[n] = T1[NK + (size_t)n * K]; f1[n] = T1[2 * NK + (size_t)n * K];
+              q2[n] = T2[(size_t)n * K]; i2[n] = T2[NK + (size_t)n * K]; f2[n] = T2[2 * NK + (size_t)n * K];
+            }
+            std::fill(phi.begin(), phi.end(), 0.0);
+            qt_solve_host(N, par, al[1], rz.data(), phi.data(), q1.data(), i1.data(), f1.data(), G1,
+                          w.data(), w.data() + N, w.data() + 2 * N, 1.0, 1.0, 1);
+            qt_solve_host(N, par, al[2], phi.data(), vv.data(), q2.data(), i2.data(), f2.data(), G2,
+                          w.data(), w.data() + N, w.data() + 2 * N, 0.0, -1.0, 1);
+            double S = 0.0;
+            for (int n = par; n < N; n += 2) {
+              vo[(size_t)n * K] = vv[n];
+              S += (double)n * n * vv[n];
+            }
+            vhS[(((size_t)i * 4 + o) * 2 + par) * K + m] = 1.0 / S;
+          }
+        }
+      }
+    }
+    CK(cudaMemcpyAsync((void*)d.qt, qt.data(), qt.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync((void*)d.qtG, qtG.data(), qtG.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync((void*)d.vh, vh.data(), vh.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync((void*)d.vhS, vhS.data(), vhS.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync((void*)d.wrow, w.data(), w.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    // Clenshaw-Curtis weights on the diagnostic grid (Me = 2(N-1) intervals):
+    // w_j = sum over even n <= Me of (2/(Me cb_n cb_j)) T_n(y_j) * 2/(1 - n^2)
+    {
+      const int Me = 2 * (N - 1);
+      std::vector<double> cw(Me + 1, 0.0);
+      for (int j = 0; j <= Me; ++j) {
+        double acc = 0.0;
+        for (int n = 0; n <= Me; n += 2) {
+          double cc, ss;
+          cis((long long)n * j, 2LL * Me, &cc, &ss);
+          const double cbn = (n == 0 || n == Me) ? 2.0 : 1.0;
+          acc += cc / cbn * 2.0 / (1.0 - (double)n * n);
+        }
+        const double cbj = (j == 0 || j == Me) ? 2.0 : 1.0;
+        cw[j] = 2.0 / (Me * cbj) * acc;
+      }
+      CK(cudaMemcpyAsync((void*)d.ccw, cw.data(), cw.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    }
+    // twiddle tables
+    FftPlan* pls[5] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe};
+    for (int t = 0; t < 5; ++t) {
+      const int n = pls[t]->n;
+      std::vector<double2> tw(n);
+      for (int k = 0; k < n; ++k) {
+        double cc, ss;
+        cis(k, n, &cc, &ss);
+        tw[k] = make_double2(cc, -ss);
+      }
+      CK(cudaMemcpyAsync((void*)pls[t]->tw, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  // capture one step of every group into a graph
+  CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  int nl = 0;
+  cudaError_t le = cudaSuccess;
+  for (Group& g : c->groups) {
+    if (!le) le = launch_step(g.d, c->cap, &nl);
+    if (!le) le = launch_diag(g.d, c->cap, &nl);
+  }
+  cudaError_t ee = cudaStreamEndCapture(c->cap, &c->graph);
+  if (le) return fail_cuda(le, "launch during graph capture", __LINE__);
+  if (ee) return fail_cuda(ee, "cudaStreamEndCapture", __LINE__);
+  CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+  c->launches = nl;
+  *out = c.release();
+  return PTT_OK;
+}
+
+static int member_ok(ptt_ctx* c, int member) {
+  return c && member >= 0 && member < (int)c->prm.size();
+}
+
+static int upload_phys(ptt_ctx* c, int member, const double* h) {
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  const size_t n = (size_t)5 * g.d.N * g.d.nx;
+  CK(cudaMemcpyAsync(g.d.stage, h, n * 8, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_phys_to_state(g.d, b, c->stream));
+  CK(launch_diag(g.d, c->stream, nullptr));
+  CK(cudaStreamSynchronize(c->stream));
+  c->last_read[member] = -1;
+  return PTT_OK;
+}
+
+int ptt_init_state(ptt_ctx* c, int32_t member, uint64_t seed, double amplitude) {
+  if (!member_ok(c, member) || !(amplitude >= 0)) return PTT_EINVAL;
+  std::vector<double> f;
+  initial_fields(c->prm[member], seed, amplitude, f);
+  return upload_phys(c, member, f.data());
+}
+
+int ptt_set_state(ptt_ctx* c, int32_t member, const double* h) {
+  if (!member_ok(c, member) || !h) return PTT_EINVAL;
+  return upload_phys(c, member, h);
+}
+
+int ptt_get_state(ptt_ctx* c, int32_t member, double* h) {
+  if (!member_ok(c, member) || !h) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  CK(launch_state_to_phys(g.d, b, c->stream));
+  CK(cudaMemcpyAsync(h, g.d.stage, (size_t)5 * g.d.N * g.d.nx * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PTT_OK;
+}
+
+int ptt_set_spectral(ptt_ctx* c, int32_t member, const double* h) {
+  if (!member_ok(c, member) || !h) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  const size_t NK = (size_t)g.d.N * g.d.K;
+  CK(cudaMemcpyAsync(g.d.X + (size_t)b * 5 * NK, h, 5 * NK * 16, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_reset_member(g.d, b, c->stream));
+  CK(launch_diag(g.d, c->stream, nullptr));
+  CK(cudaStreamSynchronize(c->stream));
+  c->last_read[member] = -1;
+  return PTT_OK;
+}
+
+int ptt_get_spectral(ptt_ctx* c, int32_t member, double* h) {
+  if (!member_ok(c, member) || !h) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  const size_t NK = (size_t)g.d.N * g.d.K;
+  CK(cudaMemcpyAsync(h, g.d.X + (size_t)b * 5 * NK, 5 * NK * 16, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PTT_OK;
+}
+
+int ptt_explicit_rhs(ptt_ctx* c, int32_t member, double* h) {
+  if (!member_ok(c, member) || !h) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  const size_t NK = (size_t)g.d.N * g.d.K;
+  CK(launch_explicit(g.d, c->stream));
+  CK(cudaMemcpyAsync(h, g.d.NR + (size_t)b * 5 * NK, 3 * NK * 16, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(h + 3 * NK * 2, g.d.Rb + (size_t)b * 4 * NK, 2 * NK * 16, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PTT_OK;
+}
+
+int ptt_step(ptt_ctx* c, int32_t nsteps) {
+  if (!c || nsteps < 0) return PTT_EINVAL;
+  for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(c->exec, c->stream));
+  return PTT_OK;
+}
+
+int ptt_synchronize(ptt_ctx* c) {
+  if (!c) return PTT_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  int blown = 0;
+  for (Group& g : c->groups) {
+    std::vector<int> st(g.d.nb);
+    CK(cudaMemcpy(st.data(), g.d.status, g.d.nb * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int v : st) blown |= (v != 0);
+  }
+  return blown ? PTT_BLOWUP : PTT_OK;
+}
+
+int ptt_diagnostics(ptt_ctx* c, int32_t member, ptt_diag* out, int32_t maxr, int32_t* nw) {
+  if (!member_ok(c, member) || !out || maxr < 0 || !nw) return PTT_EINVAL;
+  *nw = 0;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  CK(cudaStreamSynchronize(c->stream));
+  long long cnt = 0;
+  CK(cudaMemcpy(&cnt, g.d.count + b, sizeof(long long), cudaMemcpyDeviceToHost));
+  long long first = c->last_read[member] + 1;
+  if (first < cnt - kRing + 1) first = cnt - kRing + 1;
+  if (first < 0) first = 0;
+  int n = 0;
+  for (long long s = first; s <= cnt && n < maxr; ++s, ++n) {
+    CK(cudaMemcpy(out + n, g.d.ring + (size_t)b * kRing + (size_t)(s % kRing), sizeof(ptt_diag),
+                  cudaMemcpyDeviceToHost));
+  }
+  if (n > 0) c->last_read[member] = first + n - 1;
+  *nw = n;
+  return PTT_OK;
+}
+
+static size_t ckpt_bytes(const Group& g) {
+  const size_t NK = (size_t)g.d.N * g.d.K;
+  return 64 + (5 + 16 + 16) * NK * 16;
+}
+
+int ptt_checkpoint_size(ptt_ctx* c, int32_t member, size_t* bytes) {
+  if (!member_ok(c, member) || !bytes) return PTT_EINVAL;
+  *bytes = ckpt_bytes(c->groups[c->where[member].first]);
+  return PTT_OK;
+}
+
+int ptt_get_checkpoint(ptt_ctx* c, int32_t member, void* h, size_t bytes) {
+  if (!member_ok(c, member) || !h) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  if (bytes < ckpt_bytes(g)) return PTT_EINVAL;
+  const size_t NK = (size_t)g.d.N * g.d.K, nb = g.d.nb;
+  char* p = (char*)h;
+  CK(cudaStreamSynchronize(c->stream));
+  int64_t hdr[8] = {0x70747463, g.d.nx, g.d.N, 0, 0, 0, 0, 0};
+  long long cnt;
+  int st;
+  CK(cudaMemcpy(&cnt, g.d.count + b, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&st, g.d.status + b, 4, cudaMemcpyDeviceToHost));
+  hdr[3] = cnt;
+  hdr[4] = st;
+  std::memcpy(p, hdr, 64);
+  p += 64;
+  CK(cudaMemcpy(p, g.d.X + b * 5 * NK, 5 * NK * 16, cudaMemcpyDeviceToHost));
+  p += 5 * NK * 16;
+  for (int s = 0; s < 4; ++s) {
+    CK(cudaMemcpy(p, g.d.Eh + ((size_t)s * nb + b) * 4 * NK, 4 * NK * 16, cudaMemcpyDeviceToHost));
+    p += 4 * NK * 16;
+    CK(cudaMemcpy(p, g.d.Nh + ((size_t)s * nb + b) * 4 * NK, 4 * NK * 16, cudaMemcpyDeviceToHost));
+    p += 4 * NK * 16;
+  }
+  return PTT_OK;
+}
+
+int ptt_set_checkpoint(ptt_ctx* c, int32_t member, const void* h, size_t bytes) {
+  if (!member_ok(c, member) || !h) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  if (bytes < ckpt_bytes(g)) return PTT_EINVAL;
+  const size_t NK = (size_t)g.d.N * g.d.K, nb = g.d.nb;
+  const char* p = (const char*)h;
+  int64_t hdr[8];
+  std::memcpy(hdr, p, 64);
+  if (hdr[0] != 0x70747463 || hdr[1] != g.d.nx || hdr[2] != g.d.N) return PTT_EINVAL;
+  p += 64;
+  CK(cudaStreamSynchronize(c->stream));
+  long long cnt = hdr[3];
+  int st = (int)hdr[4];
+  CK(cudaMemcpy(g.d.count + b, &cnt, 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(g.d.status + b, &st, 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(g.d.X + b * 5 * NK, p, 5 * NK * 16, cudaMemcpyHostToDevice));
+  p += 5 * NK * 16;
+  for (int s = 0; s < 4; ++s) {
+    CK(cudaMemcpy(g.d.Eh + ((size_t)s * nb + b) * 4 * NK, p, 4 * NK * 16, cudaMemcpyHostToDevice));
+    p += 4 * NK * 16;
+    CK(cudaMemcpy(g.d.Nh + ((size_t)s * nb + b) * 4 * NK, p, 4 * NK * 16, cudaMemcpyHostToDevice));
+    p += 4 * NK * 16;
+  }
+  c->last_read[member] = cnt;
+  return PTT_OK;
+}
+
+int ptt_time_stages(ptt_ctx* c, int32_t nsteps, double* ms) {
+  if (!c || nsteps < 0 || !ms) return PTT_EINVAL;
+  const int G = (int)c->groups.size();
+  std::vector<cudaEvent_t> ev((size_t)G * (PTT_NSTAGES + 1), nullptr);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  int rc = PTT_OK;
+  for (int st = 0; st < nsteps && rc == PTT_OK; ++st) {
+    for (int gi = 0; gi < G; ++gi) {
+      cudaEvent_t* E = &ev[(size_t)gi * (PTT_NSTAGES + 1)];
+      cudaError_t e = cudaEventRecord(E[0], c->stream);
+      for (int s = 0; s < PTT_NSTAGES && !e; ++s) {
+        e = launch_stage(c->groups[gi].d, s, c->stream, nullptr);
+        if (!e) e = cudaEventRecord(E[s + 1], c->stream);
+      }
+      if (e) { rc = fail_cuda(e, "ptt_time_stages launch", __LINE__); break; }
+    }
+    if (rc) break;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e) { rc = fail_cuda(e, "ptt_time_stages sync", __LINE__); break; }
+    for (int gi = 0; gi < G; ++gi) {
+      cudaEvent_t* E = &ev[(size_t)gi * (PTT_NSTAGES + 1)];
+      for (int s = 0; s < PTT_NSTAGES; ++s) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, E[s], E[s + 1]);
+        ms[s] += t;
+      }
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return rc;
+}
+
+int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) {
+  if (!c || !flops || !bytes || !launches) return PTT_EINVAL;
+  auto fft = [](double n) { return 5.0 * n * std::log2(n); };
+  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 1, 1, 1, 4};
+  for (int s = 0; s < PTT_NSTAGES; ++s) { flops[s] = 0.0; bytes[s] = 0.0; launches[s] = 0; }
+  for (Group& g : c->groups) {
+    const GroupDev& d = g.d;
+    const double nb = d.nb, K = d.K, N = d.N, NK = N * K, rows = d.M + 1.0, Je = 2.0 * N - 1.0;
+    const double z = 16.0, r = 8.0;  // bytes of a complex / real double
+    flops[0] += nb * (9.0 * K * fft(d.P) + 4.0 * K * N * 4.0);
+    bytes[0] += nb * z * (5.0 * NK + 9.0 * rows * K);
+    flops[1] += nb * rows * (10.0 * fft(d.Mx) + 42.0 * d.Mx);
+    bytes[1] += nb * z * (9.0 + 5.0) * rows * K;
+    flops[2] += nb * 5.0 * K * fft(d.P);
+    bytes[2] += nb * z * (5.0 * rows * K + 5.0 * NK);
+    flops[3] += nb * NK * 160.0;
+    bytes[3] += nb * z * NK * (5.0 + 5.0 + 32.0 + 8.0 + 4.0);
+    flops[4] += nb * K * 8.0 * (N / 2.0) * 24.0;
+    bytes[4] += nb * NK * (z * (4.0 + 5.0) + r * 10.0);
+    flops[5] += nb * NK * 6.0;
+    bytes[5] += nb * z * NK * 2.0;
+    flops[6] += nb * (4.0 * K * fft(d.Pe) + N * fft(d.nx) + 3.0 * fft(d.nx) + NK * 10.0);
+    bytes[6] += nb * (z * (5.0 * NK + 2.0 * 4.0 * Je * K) + r * 2.0 * 2.0 * N * d.nx);
+    for (int s = 0; s < PTT_NSTAGES; ++s) launches[s] += nlaunch[s];
+  }
+  return PTT_OK;
+}
+
+int ptt_launches_per_step(ptt_ctx* c, int32_t* n) {
+  if (!c || !n) return PTT_EINVAL;
+  *n = c->launches;
+  return PTT_OK;
+}
+
+int ptt_destroy(ptt_ctx* c) {
+  if (!c) return PTT_EINVAL;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+  return PTT_OK;
+}
+
+const char* ptt_last_error(void) { return g_last_error; }
+
+const char* ptt_status_string(int s) {
+  switch (s) {
+    case PTT_OK: return "ok";
+    case PTT_BLOWUP: return "blow-up detected";
+    case PTT_EINVAL: return "invalid argument";
+    case PTT_ENOMEM: return "workspace too small";
+    case PTT_ECUDA: return "CUDA runtime error";
+    case PTT_TIMEOUT: return "bounded wait expired";
+    case PTT_ENOTSUP: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal declarations shared by the host (C ABI) and device code of the
+// sPTT channel library.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ptt.h"
+
+namespace ptt {
+
+constexpr int kMaxStages = 16;
+constexpr int kRing = 1024;       // diagnostics records kept per member
+constexpr int kNumHist = 4;       // SBDF4 history depth
+
+// Mixed-radix (2, 3, 4, 5) Stockham FFT plan of length n.
+struct FftPlan {
+  int n;
+  int nst;
+  int radix[kMaxStages];
+  const double2* tw;  // tw[k] = exp(-2 pi i k / n), k < n (device)
+};
+
+// Per-member physics, resident on the device.
+struct MemberPrm {
+  double lx, re, wi, beta, eps, kappa, dt;
+  double inv_wi, gam, nu, forcing;  // 1/Wi, (1-beta)/(Re Wi), beta/Re, 2/Re
+  double trc_max, u_max;
+};
+
+// Device view of one group: nb members with equal (nx, ny).
+// Spectral arrays are [member][field][n][m] (m fastest), complex double.
+struct GroupDev {
+  int nb;            // members in the group
+  int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
+  int Mx, M, P;      // padded x points, padded y intervals, y FFT length 2M
+  int Pu, Pe;        // y FFT lengths of the unpadded (2(N-1)) and diagnostic (4(N-1)) grids
+  int Ccol, CcolE;   // columns per block of the padded / diagnostic y passes
+  MemberPrm* prm;    // [nb]
+  int* status;       // [nb]  0 = running, 1 = blown up
+  long long* count;  // [nb]  steps since the state was set
+  double2* X;        // [nb][5][N][K]  state u, v, cxx, cxy, cyy
+  double2* Eh;       // [4 slot][nb][4][N][K]  evolved quantities (cxx, cxy, cyy, q)
+  double2* Nh;       // [4 slot][nb][4][N][K]  their explicit terms
+  double2* Yp;       // [nb][9][M+1][K]  fields on the padded y grid
+  double2* Zp;       // [nb][5][M+1][K]  products, x-analysed, on the padded y grid
+  double2* NR;       // [nb][5][N][K]  explicit nonlinear terms, spectral
+  double2* Rb;       // [nb][4][N][K]  SBDF right-hand sides / scratch
+  const double* qt;  // [nb][4 order][3 sys][3 (Q, inv, F)][N][K]
+  const double* qtG; // [nb][4][3][2 parity][K]
+  const double* vh;  // [nb][4][N][K]  homogeneous v of the influence step
+  const double* vhS; // [nb][4][2][K]  1 / sum_n n^2 vh_n per parity
+  const double* wrow;// [3][N]  1/(4n(n-1)), 1/(2(n^2-1)), 1/(4n(n+1))
+  const double* ccw; // [2N-1] Clenshaw-Curtis weights of the diagnostic grid
+  double2* DY;       // [nb][4][2N-1][K]  cxx, cyy, u, v on the diagnostic y grid
+  double* DV;        // [nb][2][N][nx]  cxx, cyy on the unpadded grid
+  double* part;      // [nb][kPart]  partial reductions
+  double2* DM;       // [nb][6][K]  mid-plane spectra
+  ptt_diag* ring;    // [nb][kRing]
+  double* stage;     // [5][N][nx] host<->device staging (one member at a time)
+  double2* stageS;   // [5][N][K]  spectral staging
+  FftPlan plP, plMx, plNx, plPu, plPe;
+};
+
+constexpr int kPart = 8;  // energy, ...
+
+// Launch wrappers (device code in ptt_kernels.cu).  All asynchronous on `st`.
+cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nlaunch);
+cudaError_t launch_step(const GroupDev& g, cudaStream_t st, int* nlaunch);
+cudaError_t launch_diag(const GroupDev& g, cudaStream_t st, int* nlaunch);
+cudaError_t launch_explicit(const GroupDev& g, cudaStream_t st);
+// physical staging [5][N][nx] -> state of member b (resets counter/status)
+cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st);
+// state of member b -> physical staging [5][N][nx]
+cudaError_t launch_state_to_phys(const GroupDev& g, int b, cudaStream_t st);
+cudaError_t launch_reset_member(const GroupDev& g, int b, cudaStream_t st);
+cudaError_t set_kernel_attributes(int max_dyn_smem);
+
+size_t smem_ycols(int C, int P);
+size_t smem_xfused(int Mx);
+size_t smem_xrows(int nl, int n);
+
+}  // namespace ptt

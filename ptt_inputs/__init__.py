@@ -1,0 +1,61 @@
+"""Seeded synthetic inputs shared by the tests and the benchmark.
+
+Holds random-number plumbing only (no arithmetic of the method): band-limited
+random spectral fields and the workload definitions (grid sizes, parameters,
+seeds) of the channel runs.  Both the CUDA path and the oracle receive what
+these functions return."""
+import numpy as np
+
+# The paper's fluid (Sec. 2): Wi = 150, Re = 1e-2, beta = 0.9,
+# eps = kappa = 5e-5, Lx = 10.  Time step of the benchmark configurations.
+PAPER = dict(lx=10.0, re=1e-2, wi=150.0, beta=0.9, eps=5e-5, kappa=5e-5)
+DT = 1e-3
+AMPLITUDE = 1e-3
+
+# 2D resolution sweep (the paper's resolution-threshold scan in 2D form):
+# Nx in {128, 256, 512} x Ny in {97, 129, 257}, seeds 0-2.
+SWEEP_NX = (128, 256, 512)
+SWEEP_NY = (97, 129, 257)
+SWEEP_SEEDS = (0, 1, 2)
+SMALL = (64, 65)   # the small parity case (100 steps)
+
+
+def sweep_members(seeds=SWEEP_SEEDS):
+    """(nx, ny, seed) of every member of the 2D sweep ensemble."""
+    return [(nx, ny, s) for nx in SWEEP_NX for ny in SWEEP_NY for s in seeds]
+
+
+def random_spectral(nx, ny, seed, nmodes_x=None, nmodes_y=None, scale=1.0, decay=0.0):
+    """Random spectral field a[m, n] (m < nx/2, n < ny), complex, with the
+    m = 0 column real; optional band limits and a geometric decay in n."""
+    rng = np.random.default_rng(seed)
+    K = nx // 2
+    a = rng.standard_normal((K, ny)) + 1j * rng.standard_normal((K, ny))
+    if nmodes_x is not None:
+        a[nmodes_x:] = 0
+    if nmodes_y is not None:
+        a[:, nmodes_y:] = 0
+    if decay:
+        a *= np.exp(-decay * np.arange(ny))[None, :]
+    a[0] = a[0].real
+    return a * scale
+
+
+def spectral_to_abi(fields):
+    """List of five a[m, n] arrays -> the ABI layout double[5][ny][nx/2][2]."""
+    out = np.stack([np.stack([f.T.real, f.T.imag], axis=-1) for f in fields])
+    return np.ascontiguousarray(out, dtype=np.float64)
+
+
+def abi_to_spectral(arr):
+    """ABI spectral layout -> list of five a[m, n] arrays."""
+    return [np.ascontiguousarray((arr[f, :, :, 0] + 1j * arr[f, :, :, 1]).T) for f in range(arr.shape[0])]
+
+
+def phys_to_abi(fields):
+    """List of five f[j (x), l (y)] arrays -> double[5][ny][nx]."""
+    return np.ascontiguousarray(np.stack([f.T for f in fields]), dtype=np.float64)
+
+
+def abi_to_phys(arr):
+    return [np.ascontiguousarray(arr[f].T) for f in range(arr.shape[0])]
