@@ -154,6 +154,33 @@ int ptt_diagnostics(ptt_ctx* ctx, int32_t member, ptt_diag* h_out, int32_t max_r
  * state.  Synchronous. */
 int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec5);
 
+/* Workspace-free explicit right-hand side, for callers that cannot allocate
+ * device memory (an application that owns every device byte and hands this
+ * library none, a plugin with no allocator of its own, a loop in which an
+ * allocation and its implicit synchronisation are not allowed).  The paper
+ * has no counterpart: this is a deployment variant of ptt_explicit_rhs.
+ *
+ * Same output as ptt_explicit_rhs for one run with params *p, but from and
+ * to device memory the caller passes: d_spec holds the spectral state
+ * double[5][ny][nx/2][2] (u, v, c_xx, c_xy, c_yy), d_out receives
+ * double[5][ny][nx/2][2] (N_cxx, N_cxy, N_cyy, H_x, H_y); both 16-byte
+ * aligned, distinct.  The padded-grid intermediates live in a static device
+ * array of 32 MiB that the library image carries (held on every GPU that
+ * loads the library until the process exits); shapes whose intermediates
+ * exceed it (14 (M+1) (nx/2) 16 bytes plus tables, M the padded Chebyshev
+ * grid, e.g. nx = 512, ny = 513) return PTT_ENOMEM with the sizes in
+ * ptt_last_error().  No device memory is allocated or freed.
+ *
+ * The first call on a device, with that device current, looks up the
+ * array's device address and sets the kernels' shared-memory limits; make
+ * that first call before any stream capture.  Every call on a device shares
+ * the one array and rewrites what it needs (the array keeps the last call's
+ * contents), so calls that overlap on the GPU -- from different host threads
+ * or streams -- race and must be serialised by the caller.  Runs on
+ * cuda_stream (a cudaStream_t as void*) and returns after synchronising it. */
+int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spec, double* d_out,
+                             void* cuda_stream);
+
 /* Checkpoint of one member: state, SBDF history and step counter, so that a
  * restart continues bit for bit.  ptt_checkpoint_size gives the bytes.
  * Synchronous. */

@@ -54,6 +54,7 @@ _SIGS = {
     "ptt_synchronize": [_VP],
     "ptt_diagnostics": [_VP, _I32, ctypes.POINTER(ptt_diag), _I32, ctypes.POINTER(_I32)],
     "ptt_explicit_rhs": [_VP, _I32, _DP],
+    "ptt_explicit_rhs_noalloc": [ctypes.POINTER(ptt_params), _VP, _VP, _VP],
     "ptt_checkpoint_size": [_VP, _I32, ctypes.POINTER(_SZ)],
     "ptt_get_checkpoint": [_VP, _I32, _VP, _SZ],
     "ptt_set_checkpoint": [_VP, _I32, _VP, _SZ],
@@ -172,6 +173,13 @@ def ptt_diagnostics(ctx, member, max_records=1024):
 def ptt_explicit_rhs(ctx, member, out):
     _check("ptt_explicit_rhs", load_library().ptt_explicit_rhs(ctx, member, _dptr(out)))
     return out
+
+
+def ptt_explicit_rhs_noalloc(params, d_spec_ptr, d_out_ptr, stream_ptr=0):
+    """Workspace-free explicit right-hand side (device pointers in and out);
+    for callers that cannot allocate device memory.  Returns the status."""
+    return _check("ptt_explicit_rhs_noalloc", load_library().ptt_explicit_rhs_noalloc(
+        ctypes.byref(params), _VP(d_spec_ptr), _VP(d_out_ptr), _VP(stream_ptr)))
 
 
 def ptt_checkpoint_size(ctx, member):

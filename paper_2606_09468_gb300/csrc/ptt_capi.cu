@@ -363,6 +363,51 @@ int fail_cuda(cudaError_t e, const char* what, int line) {
     if (e_ != cudaSuccess) return fail_cuda(e_, #x, __LINE__); \
   } while (0)
 
+// ---------------------------------------------------------------------------
+// Host helpers shared with the workspace-free entry point (ptt_noalloc.cu).
+namespace ptt {
+
+void set_last_error(const char* msg) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+}
+
+int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
+               std::vector<double2>& twMx, MemberPrm& prm) {
+  const int s = check_params(p);
+  if (s) return s;
+  Group g;
+  g.nx = p.nx;
+  g.ny = p.ny;
+  group_sizes(p.nx, p.ny, g);
+  d = g.d;
+  d.nb = 1;
+  FftPlan* pls[2] = {&d.plP, &d.plMx};
+  std::vector<double2>* tws[2] = {&twP, &twMx};
+  for (int i = 0; i < 2; ++i) {
+    const HostPlan& hp = g.hp[i];
+    pls[i]->n = hp.n;
+    pls[i]->nst = (int)hp.radix.size();
+    for (int k = 0; k < pls[i]->nst; ++k) pls[i]->radix[k] = hp.radix[k];
+    tws[i]->resize(hp.n);
+    for (int k = 0; k < hp.n; ++k) {
+      double cc, ss;
+      cis(k, hp.n, &cc, &ss);
+      (*tws[i])[k] = make_double2(cc, -ss);
+    }
+  }
+  prm.lx = p.lx; prm.re = p.re; prm.wi = p.wi; prm.beta = p.beta; prm.eps = p.eps;
+  prm.kappa = p.kappa; prm.dt = p.dt;
+  prm.inv_wi = 1.0 / p.wi;
+  prm.gam = (1.0 - p.beta) / (p.re * p.wi);
+  prm.nu = p.beta / p.re;
+  prm.forcing = 2.0 / p.re;
+  prm.trc_max = p.blowup_trc_max > 0 ? p.blowup_trc_max : 1e300;
+  prm.u_max = p.blowup_u_max > 0 ? p.blowup_u_max : 1e300;
+  return PTT_OK;
+}
+
+}  // namespace ptt
+
 extern "C" {
 
 int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {

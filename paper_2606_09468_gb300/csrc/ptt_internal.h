@@ -2,6 +2,7 @@
 // sPTT channel library.  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "ptt.h"
@@ -74,6 +75,11 @@ cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_state_to_phys(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_reset_member(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t set_kernel_attributes(int max_dyn_smem);
+
+// Host helpers (ptt_capi.cu) used by the workspace-free entry point.
+void set_last_error(const char* msg);
+int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
+               std::vector<double2>& twMx, MemberPrm& prm);
 
 size_t smem_ycols(int C, int P);
 size_t smem_xfused(int Mx);

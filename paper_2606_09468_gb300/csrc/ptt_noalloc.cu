@@ -1,0 +1,130 @@
+// Workspace-free variant of the explicit right-hand side (ptt_explicit_rhs_noalloc).
+//
+// Some callers cannot allocate device memory: code that runs inside a host
+// library with a fixed memory budget handed out by someone else, plugins
+// whose device memory is owned by the embedding application, or real-time
+// loops in which an allocation (and the implicit synchronisation it brings)
+// is not allowed.  For them the padded-grid intermediates of this entry
+// point live in one file-scope device array, g_noalloc_scratch, sized
+// kNoAllocBytes.  The array is part of the library's device image: every GPU
+// on which the library is loaded holds those bytes until the process exits.
+//
+// In host code the name g_noalloc_scratch is a host-side stand-in, not a
+// device address; the device address is obtained once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "ptt_internal.h"
+
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;  // 32 MiB per device
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_mu;
+void* g_dev_ptr[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Device address of the scratch array on the current device; first call per
+// device also raises the kernels' dynamic shared-memory limit.
+int scratch_for_current_device(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) {
+    ptt::set_last_error(cudaGetErrorString(e));
+    return PTT_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return PTT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_dev_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      char msg[256];
+      std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress(g_noalloc_scratch): %s",
+                    cudaGetErrorString(e));
+      ptt::set_last_error(msg);
+      return PTT_ECUDA;
+    }
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!e) e = ptt::set_kernel_attributes(optin);
+    if (e) {
+      ptt::set_last_error(cudaGetErrorString(e));
+      return PTT_ECUDA;
+    }
+    g_dev_ptr[dev] = p;
+  }
+  *out = g_dev_ptr[dev];
+  return PTT_OK;
+}
+
+}  // namespace
+
+extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spec, double* d_out,
+                                        void* cuda_stream) {
+  if (!p || !d_spec || !d_out) return PTT_EINVAL;
+  if (((uintptr_t)d_spec & 15) || ((uintptr_t)d_out & 15) || d_spec == d_out) return PTT_EINVAL;
+  ptt::GroupDev g{};
+  ptt::MemberPrm prm{};
+  std::vector<double2> twP, twMx;
+  int s = ptt::shape_plan(*p, g, twP, twMx, prm);
+  if (s) return s;
+  const size_t rows = (size_t)g.M + 1, K = g.K, NK = (size_t)g.N * K;
+  // layout of the scratch array
+  size_t off = 0;
+  const size_t oYp = off; off = align256(off + 9 * rows * K * sizeof(double2));
+  const size_t oZp = off; off = align256(off + 5 * rows * K * sizeof(double2));
+  const size_t oTP = off; off = align256(off + twP.size() * sizeof(double2));
+  const size_t oTM = off; off = align256(off + twMx.size() * sizeof(double2));
+  const size_t oPr = off; off = align256(off + sizeof(ptt::MemberPrm));
+  const size_t oSt = off; off = align256(off + sizeof(int));
+  const size_t oCn = off; off = align256(off + sizeof(long long));
+  if (off > kNoAllocBytes) {
+    char msg[256];
+    std::snprintf(msg, sizeof(msg),
+                  "ptt_explicit_rhs_noalloc: nx=%d ny=%d needs %zu bytes of scratch, the "
+                  "static array holds %zu",
+                  p->nx, p->ny, off, kNoAllocBytes);
+    ptt::set_last_error(msg);
+    return PTT_ENOMEM;
+  }
+  void* base = nullptr;
+  s = scratch_for_current_device(&base);
+  if (s) return s;
+  char* b = (char*)base;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  g.Yp = (double2*)(b + oYp);
+  g.Zp = (double2*)(b + oZp);
+  g.plP.tw = (const double2*)(b + oTP);
+  g.plMx.tw = (const double2*)(b + oTM);
+  g.prm = (ptt::MemberPrm*)(b + oPr);
+  g.status = (int*)(b + oSt);
+  g.count = (long long*)(b + oCn);
+  g.X = (double2*)d_spec;             // read only: stage 0 and the stress divergence
+  g.NR = (double2*)d_out;             // N_cxx, N_cxy, N_cyy, then N_u, N_v
+  g.Rb = (double2*)d_out + 3 * NK;    // H_x, H_y overwrite N_u, N_v in place
+  cudaError_t e;
+  // status and step counter must read zero; tables and parameters are
+  // rewritten on every call (the array keeps the previous call's contents)
+  if ((e = cudaMemsetAsync(b + oSt, 0, sizeof(int), st)) ||
+      (e = cudaMemsetAsync(b + oCn, 0, sizeof(long long), st)) ||
+      (e = cudaMemcpyAsync(b + oTP, twP.data(), twP.size() * sizeof(double2),
+                           cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(b + oTM, twMx.data(), twMx.size() * sizeof(double2),
+                           cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(b + oPr, &prm, sizeof(prm), cudaMemcpyHostToDevice, st)) ||
+      (e = ptt::launch_explicit(g, st)) ||
+      (e = cudaStreamSynchronize(st))) {
+    char msg[256];
+    std::snprintf(msg, sizeof(msg), "ptt_explicit_rhs_noalloc: %s", cudaGetErrorString(e));
+    ptt::set_last_error(msg);
+    return PTT_ECUDA;
+  }
+  return PTT_OK;
+}
