@@ -164,12 +164,13 @@ int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec5);
  * to device memory the caller passes: d_spec holds the spectral state
  * double[5][ny][nx/2][2] (u, v, c_xx, c_xy, c_yy), d_out receives
  * double[5][ny][nx/2][2] (N_cxx, N_cxy, N_cyy, H_x, H_y); both 16-byte
- * aligned, distinct.  The padded-grid intermediates live in a static device
- * array of 32 MiB that the library image carries (held on every GPU that
- * loads the library until the process exits); shapes whose intermediates
- * exceed it (14 (M+1) (nx/2) 16 bytes plus tables, M the padded Chebyshev
- * grid, e.g. nx = 512, ny = 513) return PTT_ENOMEM with the sizes in
- * ptt_last_error().  No device memory is allocated or freed.
+ * aligned, distinct.  The intermediates live in a static device array of
+ * 48 MiB that the library image carries (held on every GPU that loads the
+ * library until the process exits); shapes whose intermediates exceed it
+ * ((12 ny + 14 (M+1)) (nx/2) 16 bytes plus tables, M the padded Chebyshev
+ * grid: every shape up to nx = 512, ny = 257 fits, nx = 512, ny = 513 does
+ * not) return PTT_ENOMEM with the sizes in ptt_last_error().  No device
+ * memory is allocated or freed.
  *
  * The first call on a device, with that device current, looks up the
  * array's device address and sets the kernels' shared-memory limits; make
@@ -190,10 +191,10 @@ int ptt_set_checkpoint(ptt_ctx* ctx, int32_t member, const void* h_buf, size_t b
 
 /* Stages of one step, in launch order: 0 inverse Chebyshev transforms
  * (9 fields, with d/dy), 1 fused x transforms + products of Eqs. 1-2,
- * 2 forward Chebyshev transforms (5 fields), 3 explicit linear terms and
- * SBDF right-hand sides, 4 tau solves, 5 velocity from continuity,
- * 6 diagnostics. */
-#define PTT_NSTAGES 7
+ * 2 forward Chebyshev transforms (5 fields), 3 per-mode spectral stage
+ * (explicit linear terms, SBDF sums, tau solves, velocity from continuity),
+ * 4 diagnostics. */
+#define PTT_NSTAGES 5
 
 /* Advance every member by nsteps steps with ordinary (non-graph) launches,
  * recording CUDA events on the context stream around each stage, and add the

@@ -199,10 +199,10 @@ def ptt_set_checkpoint(ctx, member, buf):
         ctx, member, buf.ctypes.data_as(_VP), buf.nbytes))
 
 
-PTT_NSTAGES = 7
-STAGE_NAMES = ("cheb_inverse", "x_fused_products", "cheb_forward", "rhs_sbdf", "tau_solve",
-               "velocity", "diagnostics")
-STAGE_KERNELS = ("k_ycols", "k_xfused", "k_ycols", "k_rhs", "k_solve", "k_uvel",
+PTT_NSTAGES = 5
+STAGE_NAMES = ("cheb_inverse", "x_fused_products", "cheb_forward", "spectral_sbdf_solve",
+               "diagnostics")
+STAGE_KERNELS = ("k_ycols", "k_xfused", "k_ycols", "k_spec+k_tick",
                  "k_ycols+k_diag_part+k_xrows+k_diag_final")
 
 

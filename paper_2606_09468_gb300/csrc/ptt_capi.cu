@@ -345,6 +345,8 @@ struct ptt_ctx {
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> gstreams;  // one capture branch per group
+  std::vector<cudaEvent_t> gevents;
   int launches = 0;
   int device = 0;
 };
@@ -449,7 +451,7 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   int optin = 0;
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
   for (Group& g : c->groups)
-    if (smem_xfused(g.d.Mx) > (size_t)optin) return PTT_EINVAL;
+    if (smem_xfused(g.d.Mx) > (size_t)optin || smem_spec(g.d.N) > (size_t)optin) return PTT_EINVAL;
   CK(set_kernel_attributes(optin));
   CK(cudaMemsetAsync(d_ws, 0, need - 256, c->stream));
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
@@ -496,37 +498,32 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
           for (int ts = 0; ts < 3; ++ts) {
             if (ts == 0 && p.kappa == 0.0) continue;
             if (ts == 2 && m == 0) continue;
-            double* base = &qt[((((size_t)i * 4 + o) * 3 + ts) * 3) * NK + m];
+            double* base = &qt[((((size_t)i * 4 + o) * 3 + ts) * 3) * NK + (size_t)m * N];
             for (int par = 0; par < 2; ++par) {
               qt_tables(N, al[ts], be[ts], w.data(), w.data() + N, w.data() + 2 * N, par, base,
                         base + NK, base + 2 * NK,
-                        &qtG[((((size_t)i * 4 + o) * 3 + ts) * 2 + par) * K + m], K);
+                        &qtG[((((size_t)i * 4 + o) * 3 + ts) * 2 + par) * K + m], 1);
             }
           }
           if (m == 0) continue;
           // homogeneous solutions of the influence-matrix step:
           // phi_h: rows of (alpha - nu D^2) phi = 0 with the parity sum = 1,
           // v_h: rows of (k^2 - D^2) v = -phi_h with the parity sum = 0.
-          const double* T1 = &qt[((((size_t)i * 4 + o) * 3 + 1) * 3) * NK + m];
-          const double* T2 = &qt[((((size_t)i * 4 + o) * 3 + 2) * 3) * NK + m];
-          double* vo = &vh[((size_t)i * 4 + o) * NK + m];
+          const double* T1 = &qt[((((size_t)i * 4 + o) * 3 + 1) * 3) * NK + (size_t)m * N];
+          const double* T2 = &qt[((((size_t)i * 4 + o) * 3 + 2) * 3) * NK + (size_t)m * N];
+          double* vo = &vh[((size_t)i * 4 + o) * NK + (size_t)m * N];
           for (int par = 0; par < 2; ++par) {
             const double G1 = qtG[((((size_t)i * 4 + o) * 3 + 1) * 2 + par) * K + m];
             const double G2 = qtG[((((size_t)i * 4 + o) * 3 + 2) * 2 + par) * K + m];
-            // tables are strided by K; solve on contiguous copies
-            std::vector<double> q1(N), i1(N), f1(N), q2(N), i2(N), f2(N), vv(N, 0.0);
-            for (int n = 0; n < N; ++n) {
-              q1[n] = T1[(size_t)n * K]; i1[n] = T1[NK + (size_t)n * K]; f1[n] = T1[2 * NK + (size_t)n * K];
-              q2[n] = T2[(size_t)n * K]; i2[n] = T2[NK + (size_t)n * K]; f2[n] = T2[2 * NK + (size_t)n * K];
-            }
+            std::vector<double> vv(N, 0.0);
             std::fill(phi.begin(), phi.end(), 0.0);
-            qt_solve_host(N, par, al[1], rz.data(), phi.data(), q1.data(), i1.data(), f1.data(), G1,
+            qt_solve_host(N, par, al[1], rz.data(), phi.data(), T1, T1 + NK, T1 + 2 * NK, G1,
                           w.data(), w.data() + N, w.data() + 2 * N, 1.0, 1.0, 1);
-            qt_solve_host(N, par, al[2], phi.data(), vv.data(), q2.data(), i2.data(), f2.data(), G2,
+            qt_solve_host(N, par, al[2], phi.data(), vv.data(), T2, T2 + NK, T2 + 2 * NK, G2,
                           w.data(), w.data() + N, w.data() + 2 * N, 0.0, -1.0, 1);
             double S = 0.0;
             for (int n = par; n < N; n += 2) {
-              vo[(size_t)n * K] = vv[n];
+              vo[n] = vv[n];
               S += (double)n * n * vv[n];
             }
             vhS[(((size_t)i * 4 + o) * 2 + par) * K + m] = 1.0 / S;
@@ -572,14 +569,23 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
     }
     CK(cudaStreamSynchronize(c->stream));
   }
-  // capture one step of every group into a graph
+  // capture one step of every group into a graph: the groups are
+  // independent, so each gets its own branch (fork/join through events)
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  c->gstreams.assign(c->groups.size(), nullptr);
+  c->gevents.assign(c->groups.size() + 1, nullptr);
+  for (auto& s2 : c->gstreams) CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+  for (auto& e2 : c->gevents) CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
   int nl = 0;
-  cudaError_t le = cudaSuccess;
-  for (Group& g : c->groups) {
-    if (!le) le = launch_step(g.d, c->cap, &nl);
-    if (!le) le = launch_diag(g.d, c->cap, &nl);
+  cudaError_t le = cudaEventRecord(c->gevents.back(), c->cap);
+  for (size_t gi = 0; gi < c->groups.size() && !le; ++gi) {
+    cudaStream_t gs = c->gstreams[gi];
+    le = cudaStreamWaitEvent(gs, c->gevents.back(), 0);
+    if (!le) le = launch_step(c->groups[gi].d, gs, &nl);
+    if (!le) le = launch_diag(c->groups[gi].d, gs, &nl);
+    if (!le) le = cudaEventRecord(c->gevents[gi], gs);
+    if (!le) le = cudaStreamWaitEvent(c->cap, c->gevents[gi], 0);
   }
   cudaError_t ee = cudaStreamEndCapture(c->cap, &c->graph);
   if (le) return fail_cuda(le, "launch during graph capture", __LINE__);
@@ -633,7 +639,8 @@ int ptt_set_spectral(ptt_ctx* c, int32_t member, const double* h) {
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
   const size_t NK = (size_t)g.d.N * g.d.K;
-  CK(cudaMemcpyAsync(g.d.X + (size_t)b * 5 * NK, h, 5 * NK * 16, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(g.d.stageS, h, 5 * NK * 16, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_transpose(g.d.stageS, g.d.X + (size_t)b * 5 * NK, 5, g.d.N, g.d.K, c->stream));
   CK(launch_reset_member(g.d, b, c->stream));
   CK(launch_diag(g.d, c->stream, nullptr));
   CK(cudaStreamSynchronize(c->stream));
@@ -646,7 +653,8 @@ int ptt_get_spectral(ptt_ctx* c, int32_t member, double* h) {
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
   const size_t NK = (size_t)g.d.N * g.d.K;
-  CK(cudaMemcpyAsync(h, g.d.X + (size_t)b * 5 * NK, 5 * NK * 16, cudaMemcpyDeviceToHost, c->stream));
+  CK(launch_transpose(g.d.X + (size_t)b * 5 * NK, g.d.stageS, 5, g.d.K, g.d.N, c->stream));
+  CK(cudaMemcpyAsync(h, g.d.stageS, 5 * NK * 16, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return PTT_OK;
 }
@@ -657,9 +665,9 @@ int ptt_explicit_rhs(ptt_ctx* c, int32_t member, double* h) {
   Group& g = c->groups[gi];
   const size_t NK = (size_t)g.d.N * g.d.K;
   CK(launch_explicit(g.d, c->stream));
-  CK(cudaMemcpyAsync(h, g.d.NR + (size_t)b * 5 * NK, 3 * NK * 16, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(h + 3 * NK * 2, g.d.Rb + (size_t)b * 4 * NK, 2 * NK * 16, cudaMemcpyDeviceToHost,
-                     c->stream));
+  CK(launch_transpose(g.d.NR + (size_t)b * 5 * NK, g.d.stageS, 3, g.d.K, g.d.N, c->stream));
+  CK(launch_transpose(g.d.Rb + (size_t)b * 4 * NK, g.d.stageS + 3 * NK, 2, g.d.K, g.d.N, c->stream));
+  CK(cudaMemcpyAsync(h, g.d.stageS, 5 * NK * 16, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return PTT_OK;
 }
@@ -805,26 +813,27 @@ int ptt_time_stages(ptt_ctx* c, int32_t nsteps, double* ms) {
 int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) {
   if (!c || !flops || !bytes || !launches) return PTT_EINVAL;
   auto fft = [](double n) { return 5.0 * n * std::log2(n); };
-  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 1, 1, 1, 4};
+  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 2, 4};
   for (int s = 0; s < PTT_NSTAGES; ++s) { flops[s] = 0.0; bytes[s] = 0.0; launches[s] = 0; }
   for (Group& g : c->groups) {
     const GroupDev& d = g.d;
     const double nb = d.nb, K = d.K, N = d.N, NK = N * K, rows = d.M + 1.0, Je = 2.0 * N - 1.0;
     const double z = 16.0, r = 8.0;  // bytes of a complex / real double
+    // 0: 9 complex DCT-I columns (FFT of the 2M-point even extension) + 4 d/dy
     flops[0] += nb * (9.0 * K * fft(d.P) + 4.0 * K * N * 4.0);
     bytes[0] += nb * z * (5.0 * NK + 9.0 * rows * K);
+    // 1: per padded row 7 inverse + 3 forward complex FFTs of Mx, 42 flops of products per point
     flops[1] += nb * rows * (10.0 * fft(d.Mx) + 42.0 * d.Mx);
     bytes[1] += nb * z * (9.0 + 5.0) * rows * K;
+    // 2: 5 complex DCT-I columns
     flops[2] += nb * 5.0 * K * fft(d.P);
     bytes[2] += nb * z * (5.0 * rows * K + 5.0 * NK);
-    flops[3] += nb * NK * 160.0;
-    bytes[3] += nb * z * NK * (5.0 + 5.0 + 32.0 + 8.0 + 4.0);
-    flops[4] += nb * K * 8.0 * (N / 2.0) * 24.0;
-    bytes[4] += nb * NK * (z * (4.0 + 5.0) + r * 10.0);
-    flops[5] += nb * NK * 6.0;
-    bytes[5] += nb * z * NK * 2.0;
-    flops[6] += nb * (4.0 * K * fft(d.Pe) + N * fft(d.nx) + 3.0 * fft(d.nx) + NK * 10.0);
-    bytes[6] += nb * (z * (5.0 * NK + 2.0 * 4.0 * Je * K) + r * 2.0 * 2.0 * N * d.nx);
+    // 3: 6 recurrences, SBDF sums over 4 levels of 8 fields, 8 tau sweeps
+    flops[3] += nb * NK * (6.0 * 4.0 + 4.0 * 4.0 * 8.0 + 8.0 * 24.0 / 2.0);
+    bytes[3] += nb * (z * NK * (5.0 + 5.0 + 32.0 + 8.0 + 5.0) + r * NK * 10.0);
+    // 4: diagnostics
+    flops[4] += nb * (4.0 * K * fft(d.Pe) + N * fft(d.nx) + 3.0 * fft(d.nx) + NK * 10.0);
+    bytes[4] += nb * (z * (5.0 * NK + 2.0 * 4.0 * Je * K) + r * 2.0 * 2.0 * N * d.nx);
     for (int s = 0; s < PTT_NSTAGES; ++s) launches[s] += nlaunch[s];
   }
   return PTT_OK;
@@ -843,6 +852,8 @@ int ptt_destroy(ptt_ctx* c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (auto s2 : c->gstreams) if (s2) cudaStreamDestroy(s2);
+  for (auto e2 : c->gevents) if (e2) cudaEventDestroy(e2);
   delete c;
   return PTT_OK;
 }

@@ -29,7 +29,8 @@ struct MemberPrm {
 };
 
 // Device view of one group: nb members with equal (nx, ny).
-// Spectral arrays are [member][field][n][m] (m fastest), complex double.
+// Spectral arrays are [member][field][m][n] (n fastest), complex double;
+// arrays of values on a y grid are [member][field][j][m] (m fastest).
 struct GroupDev {
   int nb;            // members in the group
   int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
@@ -39,16 +40,16 @@ struct GroupDev {
   MemberPrm* prm;    // [nb]
   int* status;       // [nb]  0 = running, 1 = blown up
   long long* count;  // [nb]  steps since the state was set
-  double2* X;        // [nb][5][N][K]  state u, v, cxx, cxy, cyy
-  double2* Eh;       // [4 slot][nb][4][N][K]  evolved quantities (cxx, cxy, cyy, q)
-  double2* Nh;       // [4 slot][nb][4][N][K]  their explicit terms
+  double2* X;        // [nb][5][K][N]  state u, v, cxx, cxy, cyy
+  double2* Eh;       // [4 slot][nb][4][K][N]  evolved quantities (cxx, cxy, cyy, q)
+  double2* Nh;       // [4 slot][nb][4][K][N]  their explicit terms
   double2* Yp;       // [nb][9][M+1][K]  fields on the padded y grid
   double2* Zp;       // [nb][5][M+1][K]  products, x-analysed, on the padded y grid
-  double2* NR;       // [nb][5][N][K]  explicit nonlinear terms, spectral
-  double2* Rb;       // [nb][4][N][K]  SBDF right-hand sides / scratch
-  const double* qt;  // [nb][4 order][3 sys][3 (Q, inv, F)][N][K]
+  double2* NR;       // [nb][5][K][N]  explicit nonlinear terms, spectral
+  double2* Rb;       // [nb][4][K][N]  H_x, H_y of ptt_explicit_rhs
+  const double* qt;  // [nb][4 order][3 sys][3 (Q, inv, F)][K][N]
   const double* qtG; // [nb][4][3][2 parity][K]
-  const double* vh;  // [nb][4][N][K]  homogeneous v of the influence step
+  const double* vh;  // [nb][4][K][N]  homogeneous v of the influence step
   const double* vhS; // [nb][4][2][K]  1 / sum_n n^2 vh_n per parity
   const double* wrow;// [3][N]  1/(4n(n-1)), 1/(2(n^2-1)), 1/(4n(n+1))
   const double* ccw; // [2N-1] Clenshaw-Curtis weights of the diagnostic grid
@@ -58,7 +59,7 @@ struct GroupDev {
   double2* DM;       // [nb][6][K]  mid-plane spectra
   ptt_diag* ring;    // [nb][kRing]
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
-  double2* stageS;   // [5][N][K]  spectral staging
+  double2* stageS;   // [5][N][K]  values on the unpadded y grid, x analysed
   FftPlan plP, plMx, plNx, plPu, plPe;
 };
 
@@ -84,5 +85,8 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
 size_t smem_ycols(int C, int P);
 size_t smem_xfused(int Mx);
 size_t smem_xrows(int nl, int n);
+size_t smem_spec(int N);
+cudaError_t launch_transpose(const double2* src, double2* dst, int nf, int rows, int cols,
+                             cudaStream_t st);
 
 }  // namespace ptt

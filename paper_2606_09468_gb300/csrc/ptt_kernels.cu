@@ -7,13 +7,18 @@
 //   k_xfused            per padded y row: inverse x FFTs of 14 fields, the
 //                       sPTT / advection products of Eqs. 1-2, forward x FFTs
 //   k_ycols  (forward)  padded y values -> Chebyshev coefficients (truncated)
-//   k_rhs               linear explicit terms, curl-curl forcing, SBDF sums
-//   k_solve             per (mode, system, parity) quasi-tridiagonal tau solve
-//   k_uvel              u from continuity, step counter
+//   k_spec              per Fourier mode, out of shared memory: linear
+//                       explicit terms, curl-curl forcing, SBDF sums, the
+//                       quasi-tridiagonal tau solves, u from continuity
+//   k_tick              step counters
 // followed by the diagnostics of Sec. 3 (k_ycols, k_diag_part, k_xrows,
 // k_diag_final).  All transforms are mixed-radix (2, 3, 4, 5) Stockham FFTs
 // in shared memory; the Chebyshev transforms are discrete cosine transforms
 // of type I computed as FFTs of the even extension.
+//
+// Layouts: spectral arrays [member][field][m][n] (each mode's Chebyshev
+// column contiguous); values on a y grid [member][field][j][m] (each y row's
+// Fourier modes contiguous).
 #include <cstdio>
 
 #include "ptt_internal.h"
@@ -157,7 +162,9 @@ __constant__ double c_sb[4][4] = {{1.0, 0.0, 0.0, 0.0},
                                   {4.0, -6.0, 4.0, -1.0}};
 
 // ------------------------------------------------------ Chebyshev columns
-// Column transforms along y for a batch of members and fields.
+// Column transforms along y for a batch of members and fields.  Coefficient
+// side: column m, row n at m*cm + n*cn; value side: column m, row j at
+// m*vm + j*vj (within one field of one member).
 struct YJob {
   const double2* src;
   double2* dst;
@@ -166,7 +173,9 @@ struct YJob {
   int src_field[8];
   int dst_field[8];
   int deriv[8];       // inverse only: transform d/dy of the field
-  int K;              // columns (= row length)
+  long long cm, cn;   // coefficient-side strides
+  long long vm, vj;   // value-side strides
+  int K;              // columns
   int N, M;           // Chebyshev modes, grid intervals (P = 2M)
   int inverse;        // 1: coefficients -> values (M+1 rows); 0: values -> coefficients (N rows)
   int C;              // columns per block
@@ -201,13 +210,13 @@ __global__ void __launch_bounds__(256) k_ycols(YJob J) {
   double2* A = sm;
   double2* B = sm + (size_t)C * P;
   double2* a0s = B + (size_t)C * P;  // [C] a_0, [C] a_M
-  const double2* src = J.src + b * J.src_mstride + J.src_field[f] * J.src_fstride + c0;
-  double2* dst = J.dst + b * J.dst_mstride + J.dst_field[f] * J.dst_fstride + c0;
+  const double2* src = J.src + b * J.src_mstride + J.src_field[f] * J.src_fstride;
+  double2* dst = J.dst + b * J.dst_mstride + J.dst_field[f] * J.dst_fstride;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (J.inverse) {
     for (int i = tid; i < N * C; i += nt) {
-      const int n = i / C, c = i - n * C;
-      A[c * P + n] = (c < nc) ? src[(size_t)n * K + c] : czero();
+      const int c = i / N, n = i - c * N;
+      A[c * P + n] = (c < nc) ? src[(c0 + c) * J.cm + n * J.cn] : czero();
     }
     __syncthreads();
     if (J.deriv[f]) {
@@ -232,13 +241,13 @@ __global__ void __launch_bounds__(256) k_ycols(YJob J) {
       if (c < nc) {
         double2 v = cadd(res[c * P + j], a0s[c]);
         v = (j & 1) ? csub(v, a0s[C + c]) : cadd(v, a0s[C + c]);
-        dst[(size_t)j * K + c] = cscl(v, 0.5);
+        dst[j * J.vj + (c0 + c) * J.vm] = cscl(v, 0.5);
       }
     }
   } else {
     for (int i = tid; i < (M + 1) * C; i += nt) {
       const int j = i / C, c = i - j * C;
-      A[c * P + j] = (c < nc) ? src[(size_t)j * K + c] : czero();
+      A[c * P + j] = (c < nc) ? src[j * J.vj + (c0 + c) * J.vm] : czero();
     }
     __syncthreads();
     for (int i = tid; i < C * P; i += nt) {
@@ -249,18 +258,15 @@ __global__ void __launch_bounds__(256) k_ycols(YJob J) {
     double2* res = fft_lines<-1>(A, B, C, P, J.pl);
     const double inv = 1.0 / M;
     for (int i = tid; i < N * C; i += nt) {
-      const int n = i / C, c = i - n * C;
+      const int c = i / N, n = i - c * N;
       if (c < nc) {
         const double s = (n == 0 || n == M) ? 0.5 * inv : inv;
-        dst[(size_t)n * K + c] = cscl(res[c * P + n], s);
+        dst[(c0 + c) * J.cm + n * J.cn] = cscl(res[c * P + n], s);
       }
     }
   }
 }
 
-// ---------------------------------------------------------- Fourier rows
-// Row transforms along x: complex modes m < K <-> real values at n points,
-// two real fields packed in one complex line.
 struct XJob {
   const double2* srcC;  // c2r: complex rows
   const double* srcR;   // r2c: real rows
@@ -416,255 +422,391 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
   }
 }
 
-// ------------------------------------------------ explicit terms and SBDF
-// One thread per (member, Fourier mode m); loops over the Chebyshev index.
-// NR fields: 0 Ncxx, 1 Ncxy, 2 Ncyy, 3 Nu (advection), 4 Nv.
-// mode 0: full step; mode 1: only H_x, H_y into Rb[0], Rb[1] (no history).
-__global__ void k_rhs(GroupDev g, int mode) {
+// ------------------------------------------- warp-cooperative recurrences
+// FP64 runs at a few lanes per clock per SM on this part, so a warp FP64
+// instruction costs the same pipe time whether 1 or 32 lanes are active.
+// The Chebyshev recurrences and the tau sweeps are therefore written as
+// warp scans: each lane takes a contiguous chunk, composes it sequentially,
+// and the chunks are combined with shuffles.
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxChunk = 8;  // tau sweeps: up to 8 rows per lane (ny <= 513)
+
+__device__ __forceinline__ double2 shfl_down2(double2 v, int o) {
+  return make_double2(__shfl_down_sync(kFull, v.x, o), __shfl_down_sync(kFull, v.y, o));
+}
+__device__ __forceinline__ double2 shfl_up2(double2 v, int o) {
+  return make_double2(__shfl_up_sync(kFull, v.x, o), __shfl_up_sync(kFull, v.y, o));
+}
+__device__ __forceinline__ double2 warp_allsum2(double2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(kFull, v.x, o);
+    v.y += __shfl_xor_sync(kFull, v.y, o);
+  }
+  return v;
+}
+
+// Chebyshev derivative by one warp: out_n = (2/c_n) sum_{p > n, p + n odd} p a_p
+// (c_0 = 2), as two same-parity suffix sums T(k) = sum_{p >= k, p = k mod 2} p a_p
+// with out_{k-1} = (2/c_{k-1}) T(k).  `out` must not alias `a`.
+__device__ void warp_cheb_deriv(const double2* a, double2* out, int N) {
+  const int lane = threadIdx.x & 31;
+  for (int par = 0; par < 2; ++par) {
+    const int L = (N - par + 1) / 2;
+    const int c = (L + 31) / 32;
+    const int i0 = min(lane * c, L), i1 = min(i0 + c, L);
+    double2 acc = czero();
+    for (int i = i1 - 1; i >= i0; --i) {
+      const int k = par + 2 * i;
+      acc = cfma((double)k, a[k], acc);
+      if (k >= 1) out[k - 1] = cscl(acc, k == 1 ? 1.0 : 2.0);
+    }
+    double2 inc = acc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const double2 v = shfl_down2(inc, o);
+      if (lane + o < 32) inc = cadd(inc, v);
+    }
+    double2 ex = shfl_down2(inc, 1);
+    if (lane == 31) ex = czero();
+    for (int i = i0; i < i1; ++i) {
+      const int k = par + 2 * i;
+      if (k >= 1) out[k - 1] = cfma(k == 1 ? 1.0 : 2.0, ex, out[k - 1]);
+    }
+  }
+  if (lane == 0) out[N - 1] = czero();
+  __syncwarp();
+}
+
+// Warp-cooperative quasi-tridiagonal tau solve (system stated at k_spec): the backward
+// elimination P_i = alpha_i + beta_i P_{i+1} and the forward substitution
+// a_i = P_i + Q_i a_{i-1} are affine recurrences, evaluated as warp scans of
+// affine maps; the boundary sums are warp reductions.  `out` may alias R.
+__device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, double2* out,
+                              const double* Q, const double* inv, const double* F, double G,
+                              const double* w1, const double* w2, const double* w3,
+                              double bcfac, double rsign) {
+  const int lane = threadIdx.x & 31;
+  const int L = (N - p + 1) / 2;  // unknowns a_{p+2i}, i < L; rows i = 1..L-1
+  const int nr = L - 1;
+  const int c = (nr + 31) / 32;
+  const int i0 = min(1 + lane * c, L), i1 = min(i0 + c, L);
+  double2 al[kMaxChunk];
+  double be[kMaxChunk];
+  double2 rs = czero();
+#pragma unroll
+  for (int t = 0; t < kMaxChunk; ++t) {
+    const int i = i0 + t;
+    if (t < c && i < i1) {
+      const int n = p + 2 * i;
+      const double2 Rm2 = cscl(R[n - 2], rsign);
+      const double2 R0 = cscl(R[n], rsign);
+      const double cc = (n == 2) ? 2.0 : 1.0;
+      double2 r = cscl(Rm2, -cc * w1[n]);
+      if (n <= N - 3) r = cfma(w2[n], R0, r);
+      double un = 0.0;
+      if (n <= N - 5) {
+        r = cfma(-w3[n], cscl(R[n + 2], rsign), r);
+        un = -alpha * w3[n];
+      }
+      al[t] = cscl(r, inv[n]);
+      be[t] = -un * inv[n];
+      rs = cadd(rs, R0);
+    } else {
+      al[t] = czero();
+      be[t] = 1.0;
+    }
+  }
+  if (lane == 0) rs = cadd(rs, cscl(R[p], rsign));
+  __syncwarp();
+  // backward: chunk map P_{i0} = A + B P_{i1}
+  double2 A = czero();
+  double B = 1.0;
+#pragma unroll
+  for (int t = kMaxChunk - 1; t >= 0; --t) {
+    if (t < c && i0 + t < i1) {
+      A = cfma(be[t], A, al[t]);
+      B *= be[t];
+    }
+  }
+  double2 SA = A;
+  double SB = B;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double2 hA = shfl_down2(SA, o);
+    const double hB = __shfl_down_sync(kFull, SB, o);
+    if (lane + o < 32) {
+      SA = cfma(SB, hA, SA);
+      SB *= hB;
+    }
+  }
+  double2 Pin = shfl_down2(SA, 1);
+  if (lane == 31) Pin = czero();
+  double2 U = czero();
+  double2 P = Pin;
+#pragma unroll
+  for (int t = kMaxChunk - 1; t >= 0; --t) {
+    const int i = i0 + t;
+    if (t < c && i < i1) {
+      const int n = p + 2 * i;
+      P = cfma(be[t], P, al[t]);
+      out[n] = P;
+      U = cfma(F[n], P, U);
+    }
+  }
+  U = warp_allsum2(U);
+  rs = warp_allsum2(rs);
+  const double2 a0 = cscl(csub(cscl(rs, bcfac), U), G);
+  // forward: chunk map a_{i1-1} = C + D a_{i0-1}
+  double2 Cc = czero();
+  double Dd = 1.0;
+  double2 Pv[kMaxChunk];
+  double Qv[kMaxChunk];
+#pragma unroll
+  for (int t = 0; t < kMaxChunk; ++t) {
+    const int i = i0 + t;
+    if (t < c && i < i1) {
+      const int n = p + 2 * i;
+      Pv[t] = out[n];
+      Qv[t] = Q[n];
+      Cc = cfma(Qv[t], Cc, Pv[t]);
+      Dd *= Qv[t];
+    }
+  }
+  double2 IC = Cc;
+  double ID = Dd;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double2 hC = shfl_up2(IC, o);
+    const double hD = __shfl_up_sync(kFull, ID, o);
+    if (lane >= o) {
+      IC = cfma(ID, hC, IC);
+      ID *= hD;
+    }
+  }
+  double2 EC = shfl_up2(IC, 1);
+  double ED = __shfl_up_sync(kFull, ID, 1);
+  if (lane == 0) { EC = czero(); ED = 1.0; }
+  double2 av = cfma(ED, a0, EC);
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < kMaxChunk; ++t) {
+    const int i = i0 + t;
+    if (t < c && i < i1) {
+      av = cfma(Qv[t], av, Pv[t]);
+      out[p + 2 * i] = av;
+    }
+  }
+  if (lane == 0) out[p] = a0;
+  __syncwarp();
+}
+
+// ---------------------------------------------- per-mode spectral stage
+// The tau system solved per (mode, system, parity) by warp_qt_solve:
+//   (alpha - beta D^2) a = rsign * R   on tau rows n <= N-3,
+//   sum_{n = p mod 2} a_n = bcfac * sum_{n = p mod 2} rsign * R_n,
+// taken in the three-term form that integrating twice gives (rows n >= 2);
+// beta enters only through the operator tables.
+
+// One block per (member, Fourier mode m).  Every column of the mode lives in
+// shared memory; the recurrences (Chebyshev derivatives, tau sweeps) run as
+// warp scans, the rest in parallel over the Chebyshev index.  256 threads:
+// the eight (system, parity) solves get a warp each.
+//   explicit terms (Eq. 2): H_x = N_u + gam (i k c_xx + D c_xy) (+ 2/Re on the
+//     mean mode), H_y = N_v + gam (i k c_xy + D c_yy); forcing of the evolved
+//     velocity quantity: -D(i k H_x) - k^2 H_y (m >= 1, phi = lap v), H_x (m = 0)
+//   evolved quantities x = (c_xx, c_xy, c_yy, q), q = (D^2 - k^2) v or U
+//   SBDF sums R = sum_j (-a_{j+1}/dt) x^{n-j} + b_j N^{n-j} (Sec. 2: 4th-order
+//     semi-implicit BDF, orders 1-3 on the first steps)
+//   tau solves: c with the wall rows of Eq. 1 at kappa = 0; velocity by
+//     phi-Helmholtz, v-Poisson and the influence correction v'(+-1) = 0
+//   u = i (D v) / k from continuity (Eq. 3)
+// mode 1: only H_x, H_y into Rb[0], Rb[1] (explicit right-hand side).
+__global__ void __launch_bounds__(256) k_spec(GroupDev g, int mode) {
   const int b = blockIdx.y;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= g.K || g.status[b]) return;
+  const int m = blockIdx.x;
+  if (g.status[b]) return;
   const int K = g.K, N = g.N, nb = g.nb;
   const size_t NK = (size_t)N * K;
   const MemberPrm pr = g.prm[b];
   const long long cnt = g.count[b];
   const int slot = (int)(cnt & 3);
-  const double km = 2.0 * 3.14159265358979323846 * m / pr.lx;
-  const double km2 = km * km;
-  const double gam = pr.gam;
-  const double2* X = g.X + (size_t)b * 5 * NK + m;
-  const double2* NR = g.NR + (size_t)b * 5 * NK + m;
-  double2* R = g.Rb + (size_t)b * 4 * NK + m;
-  // pass 1: H_x = Nu + gam (i k cxx + D cxy) (+ 2/Re on the mean mode),
-  //         H_y = Nv + gam (i k cxy + D cyy)                        (Eq. 2)
-  {
-    double2 p1 = czero(), p0 = czero(), q1 = czero(), q0 = czero();
-    double2 axy = X[3 * NK + (size_t)(N - 1) * K], ayy = X[4 * NK + (size_t)(N - 1) * K];
-    for (int n = N - 1; n >= 0; --n) {
-      const double2 dxy = (n == 0) ? cscl(p0, 0.5) : p0;
-      const double2 dyy = (n == 0) ? cscl(q0, 0.5) : q0;
-      const size_t o = (size_t)n * K;
-      const double2 cxx = X[2 * NK + o], cxy = axy, cyy = ayy;
-      double2 hx = cadd(NR[3 * NK + o], cscl(cadd(cscl(mul_i(cxx), km), dxy), gam));
-      double2 hy = cadd(NR[4 * NK + o], cscl(cadd(cscl(mul_i(cxy), km), dyy), gam));
-      if (m == 0 && n == 0) hx.x += pr.forcing;
-      R[0 * NK + o] = hx;
-      R[1 * NK + o] = hy;
-      if (n >= 1) {
-        const double2 nxy = X[3 * NK + o - K], nyy = X[4 * NK + o - K];
-        const double2 pm = cfma(2.0 * n, cxy, p1);
-        const double2 qm = cfma(2.0 * n, cyy, q1);
-        p1 = p0; p0 = pm; q1 = q0; q0 = qm;
-        axy = nxy; ayy = nyy;
-      }
-    }
-  }
-  if (mode == 1) return;
-  double2* E = g.Eh + ((size_t)slot * nb + b) * 4 * NK + m;
-  double2* Nn = g.Nh + ((size_t)slot * nb + b) * 4 * NK + m;
-  // pass 2: forcing of the evolved velocity quantity.  m >= 1: the curl of
-  // Eq. 2 taken twice, -D(i k H_x) - k^2 H_y; m = 0: H_x (mean flow).
-  {
-    double2 p1 = czero(), p0 = czero();
-    double2 ahx = R[(size_t)(N - 1) * K];
-    for (int n = N - 1; n >= 0; --n) {
-      const size_t o = (size_t)n * K;
-      const double2 dhx = (n == 0) ? cscl(p0, 0.5) : p0;
-      const double2 hx = ahx;
-      double2 nq;
-      if (m == 0) nq = hx;
-      else nq = csub(cscl(mul_i(dhx), -km), cscl(R[1 * NK + o], km2));
-      Nn[3 * NK + o] = nq;
-      Nn[0 * NK + o] = NR[0 * NK + o];
-      Nn[1 * NK + o] = NR[1 * NK + o];
-      Nn[2 * NK + o] = NR[2 * NK + o];
-      E[0 * NK + o] = X[2 * NK + o];
-      E[1 * NK + o] = X[3 * NK + o];
-      E[2 * NK + o] = X[4 * NK + o];
-      if (n >= 1) {
-        const double2 nhx = R[o - K];
-        const double2 pm = cfma(2.0 * n, hx, p1);
-        p1 = p0; p0 = pm;
-        ahx = nhx;
-      }
-    }
-  }
-  // pass 3: evolved velocity quantity q = (D^2 - k^2) v (m >= 1), U (m = 0)
-  if (m == 0) {
-    for (int n = 0; n < N; ++n) E[3 * NK + (size_t)n * K] = X[(size_t)n * K];
-  } else {
-    // D v into R[2]
-    double2 p1 = czero(), p0 = czero();
-    double2 av = X[1 * NK + (size_t)(N - 1) * K];
-    for (int n = N - 1; n >= 0; --n) {
-      const size_t o = (size_t)n * K;
-      R[2 * NK + o] = (n == 0) ? cscl(p0, 0.5) : p0;
-      if (n >= 1) {
-        const double2 nv = X[1 * NK + o - K];
-        const double2 pm = cfma(2.0 * n, av, p1);
-        p1 = p0; p0 = pm; av = nv;
-      }
-    }
-    p1 = czero(); p0 = czero();
-    double2 ad = R[2 * NK + (size_t)(N - 1) * K];
-    for (int n = N - 1; n >= 0; --n) {
-      const size_t o = (size_t)n * K;
-      const double2 d2 = (n == 0) ? cscl(p0, 0.5) : p0;
-      E[3 * NK + o] = cfma(-km2, X[1 * NK + o], d2);
-      if (n >= 1) {
-        const double2 nd = R[2 * NK + o - K];
-        const double2 pm = cfma(2.0 * n, ad, p1);
-        p1 = p0; p0 = pm; ad = nd;
-      }
-    }
-  }
-  // pass 4: SBDF right-hand sides R_s = sum_j (-a_{j+1}/dt) x^{n-j}_s + b_j N^{n-j}_s
-  const int o4 = (cnt < 3) ? (int)cnt : 3;
-  const double idt = 1.0 / pr.dt;
-  for (int s = 0; s < 4; ++s) {
-    for (int n = 0; n < N; ++n) {
-      const size_t o = (size_t)s * NK + (size_t)n * K;
-      double2 acc = czero();
-      for (int jj = 0; jj <= o4; ++jj) {
-        const size_t sl = (size_t)((slot - jj) & 3);
-        const double2 ex = g.Eh[(sl * nb + b) * 4 * NK + m + o];
-        const double2 en = g.Nh[(sl * nb + b) * 4 * NK + m + o];
-        acc = cfma(-c_sa[o4][jj + 1] * idt, ex, acc);
-        acc = cfma(c_sb[o4][jj], en, acc);
-      }
-      R[o] = acc;
-    }
-  }
-}
-
-// Quasi-tridiagonal Chebyshev-tau solve of one parity p of
-//   (alpha - beta D^2) a = rsign * R   on tau rows n <= N-3,
-//   sum_{n = p mod 2} a_n = bcfac * sum_{n = p mod 2} rsign * R_n.
-// Rows n >= 2 of the system in the form obtained by integrating twice
-// (three-term in n; the operator tables Q, inv, F and G carry the
-// right-hand-side-independent part of the elimination).  `out` may alias R.
-__device__ void qt_solve(int N, int K, int p, double alpha, const double2* R, double2* out,
-                         const double* Q, const double* inv, const double* F, double G,
-                         const double* w1, const double* w2, const double* w3,
-                         double bcfac, double rsign) {
-  const int nl = ((N - 1 - p) & ~1) + p;
-  double2 Pn2 = czero(), U = czero(), rsum = czero();
-  double2 Rp2 = czero();
-  double2 R0 = cscl(R[(size_t)nl * K], rsign);
-  for (int n = nl; n >= p + 2; n -= 2) {
-    const double2 Rm2 = cscl(R[(size_t)(n - 2) * K], rsign);
-    rsum = cadd(rsum, R0);
-    const double c = (n == 2) ? 2.0 : 1.0;
-    double2 r = cscl(Rm2, -c * w1[n]);
-    if (n <= N - 3) r = cfma(w2[n], R0, r);
-    double un = 0.0;
-    if (n <= N - 5) { r = cfma(-w3[n], Rp2, r); un = -alpha * w3[n]; }
-    const double2 P = cscl(cfma(-un, Pn2, r), inv[(size_t)n * K]);
-    out[(size_t)n * K] = P;
-    U = cfma(F[(size_t)n * K], P, U);
-    Pn2 = P;
-    Rp2 = R0;
-    R0 = Rm2;
-  }
-  rsum = cadd(rsum, R0);
-  double2 a = cscl(csub(cscl(rsum, bcfac), U), G);
-  out[(size_t)p * K] = a;
-  for (int n = p + 2; n <= nl; n += 2) {
-    a = cfma(Q[(size_t)n * K], a, out[(size_t)n * K]);
-    out[(size_t)n * K] = a;
-  }
-}
-
-// One thread per (member, mode m, system, parity).  Systems: 0-2 the c
-// components (Helmholtz with the wall-ODE Dirichlet rows), 3 the velocity
-// (m = 0: mean-flow Helmholtz; m >= 1: v-phi by the influence matrix).
-__global__ void k_solve(GroupDev g) {
-  const int b = blockIdx.z;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= g.K || g.status[b]) return;
-  const int sys = blockIdx.y >> 1, p = blockIdx.y & 1;
-  const int K = g.K, N = g.N;
-  const size_t NK = (size_t)N * K;
-  const MemberPrm pr = g.prm[b];
-  const long long cnt = g.count[b];
   const int o = (cnt < 3) ? (int)cnt : 3;
-  const double a0 = c_sa[o][0];
   const double km = 2.0 * 3.14159265358979323846 * m / pr.lx;
   const double km2 = km * km;
-  double2* X = g.X + (size_t)b * 5 * NK + m;
-  double2* R = g.Rb + (size_t)b * 4 * NK + (size_t)sys * NK + m;
+  extern __shared__ double2 sm[];
+  double2* sc0 = sm;            // c_xx  -> new c_xx
+  double2* sc1 = sm + N;        // c_xy  -> new c_xy
+  double2* sc2 = sm + 2 * N;    // c_yy  -> new c_yy
+  double2* sv = sm + 3 * N;     // v     -> new v
+  double2* shx = sm + 4 * N;    // N_u   -> H_x
+  double2* shy = sm + 5 * N;    // N_v   -> H_y -> new u
+  double2* sq = sm + 6 * N;     // q
+  double2* snq = sm + 7 * N;    // forcing of q
+  double2* sR = sm + 8 * N;     // R[4][N]
+  double* tb = reinterpret_cast<double*>(sm + 12 * N);  // [3 sys][Q, inv, F][N], vh[N]
+  const double2* X = g.X + (size_t)b * 5 * NK + (size_t)m * N;
+  const double2* NR = g.NR + (size_t)b * 5 * NK + (size_t)m * N;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < N; i += nt) {
+    sc0[i] = X[2 * NK + i];
+    sc1[i] = X[3 * NK + i];
+    sc2[i] = X[4 * NK + i];
+    sv[i] = X[NK + i];
+    shx[i] = NR[3 * NK + i];
+    shy[i] = NR[4 * NK + i];
+    if (m == 0) sq[i] = X[i];
+  }
+  if (mode == 0) {
+    const double* qt = g.qt + ((size_t)b * 4 + o) * 3 * 3 * NK + (size_t)m * N;
+    for (int i = tid; i < 9 * N; i += nt) {
+      const int w = i / N, n = i - w * N;
+      tb[i] = qt[(size_t)w * NK + n];
+    }
+    const double* vh = g.vh + ((size_t)b * 4 + o) * NK + (size_t)m * N;
+    for (int i = tid; i < N; i += nt) tb[9 * N + i] = vh[i];
+  }
+  __syncthreads();
+  // derivatives, one warp each: D c_xy -> sR[0], D c_yy -> sR[1], D v -> sR[2] -> D^2 v -> sq
+  {
+    const int warp = tid >> 5;
+    if (warp == 0) warp_cheb_deriv(sc1, sR, N);
+    else if (warp == 1) warp_cheb_deriv(sc2, sR + N, N);
+    else if (warp == 2 && mode == 0 && m != 0) {
+      warp_cheb_deriv(sv, sR + 2 * N, N);
+      warp_cheb_deriv(sR + 2 * N, sq, N);
+    }
+  }
+  __syncthreads();
+  for (int n = tid; n < N; n += nt) {
+    double2 hx = cadd(shx[n], cscl(cadd(cscl(mul_i(sc0[n]), km), sR[n]), pr.gam));
+    const double2 hy = cadd(shy[n], cscl(cadd(cscl(mul_i(sc1[n]), km), sR[N + n]), pr.gam));
+    if (m == 0 && n == 0) hx.x += pr.forcing;
+    shx[n] = hx;
+    shy[n] = hy;
+    if (mode == 0 && m != 0) sq[n] = cfma(-km2, sv[n], sq[n]);
+  }
+  __syncthreads();
+  if (mode == 1) {
+    double2* R = g.Rb + (size_t)b * 4 * NK + (size_t)m * N;
+    for (int i = tid; i < N; i += nt) {
+      R[i] = shx[i];
+      R[NK + i] = shy[i];
+    }
+    return;
+  }
+  // forcing of q: m >= 1: -D(i k H_x) - k^2 H_y; m = 0: H_x
+  if (m != 0 && tid < 32) warp_cheb_deriv(shx, sR, N);
+  __syncthreads();
+  for (int n = tid; n < N; n += nt)
+    snq[n] = (m == 0) ? shx[n] : csub(cscl(mul_i(sR[n]), -km), cscl(shy[n], km2));
+  __syncthreads();
+  // history slot and SBDF sums
+  {
+    double2* E = g.Eh + ((size_t)slot * nb + b) * 4 * NK + (size_t)m * N;
+    double2* Nn = g.Nh + ((size_t)slot * nb + b) * 4 * NK + (size_t)m * N;
+    const double idt = 1.0 / pr.dt;
+    for (int i = tid; i < N; i += nt) {
+      const double2 x[4] = {sc0[i], sc1[i], sc2[i], sq[i]};
+      const double2 nn[4] = {NR[i], NR[NK + i], NR[2 * NK + i], snq[i]};
+      double2 acc[4];
+      for (int s = 0; s < 4; ++s) {
+        E[s * NK + i] = x[s];
+        Nn[s * NK + i] = nn[s];
+        acc[s] = cfma(c_sb[o][0], nn[s], cscl(x[s], -c_sa[o][1] * idt));
+      }
+      for (int jj = 1; jj <= o; ++jj) {
+        const size_t sl = (size_t)((slot - jj) & 3);
+        const double2* Eo = g.Eh + (sl * nb + b) * 4 * NK + (size_t)m * N + i;
+        const double2* No = g.Nh + (sl * nb + b) * 4 * NK + (size_t)m * N + i;
+        const double ca = -c_sa[o][jj + 1] * idt, cb = c_sb[o][jj];
+        for (int s = 0; s < 4; ++s) acc[s] = cfma(cb, No[s * NK], cfma(ca, Eo[s * NK], acc[s]));
+      }
+      for (int s = 0; s < 4; ++s) sR[s * N + i] = acc[s];
+    }
+  }
+  __syncthreads();
   const double* w1 = g.wrow;
   const double* w2 = g.wrow + N;
   const double* w3 = g.wrow + 2 * N;
-  auto tab = [&](int ts, int which) {
-    return g.qt + (((((size_t)b * 4 + o) * 3 + ts) * 3 + which) * NK) + m;
-  };
-  auto tabG = [&](int ts) { return g.qtG[((((size_t)b * 4 + o) * 3 + ts) * 2 + p) * K + m]; };
-  if (sys < 3) {
-    double2* out = X + (size_t)(2 + sys) * NK;
-    const double alpha = a0 / pr.dt + pr.kappa * km2;
-    if (pr.kappa == 0.0) {
-      const double ia = 1.0 / alpha;
-      for (int n = p; n < N; n += 2) out[(size_t)n * K] = cscl(R[(size_t)n * K], ia);
-      return;
+  const double a0 = c_sa[o][0];
+  {  // eight (system, parity) tau solves, one warp each
+    const int t = tid >> 5;
+    const int sys = t >> 1, p = t & 1;
+    auto G = [&](int ts) { return g.qtG[((((size_t)b * 4 + o) * 3 + ts) * 2 + p) * K + m]; };
+    const double* T0 = tb;
+    const double* T1 = tb + 3 * N;
+    const double* T2 = tb + 6 * N;
+    const int lane = tid & 31;
+    if (sys < 3) {
+      double2* out = sm + (size_t)sys * N;  // sc0, sc1, sc2
+      const double2* R = sR + (size_t)sys * N;
+      const double alpha = a0 / pr.dt + pr.kappa * km2;
+      if (pr.kappa == 0.0) {
+        const double ia = 1.0 / alpha;
+        for (int n = p + 2 * lane; n < N; n += 64) out[n] = cscl(R[n], ia);
+      } else {
+        warp_qt_solve(N, p, alpha, R, out, T0, T0 + N, T0 + 2 * N, G(0), w1, w2, w3, pr.dt / a0,
+                      1.0);
+      }
+    } else if (m == 0) {
+      warp_qt_solve(N, p, a0 / pr.dt, sR + 3 * N, shy, T1, T1 + N, T1 + 2 * N, G(1), w1, w2, w3,
+                    0.0, 1.0);
+      for (int n = p + 2 * lane; n < N; n += 64) sv[n] = czero();
+    } else {
+      double2* Rv = sR + 3 * N;
+      warp_qt_solve(N, p, a0 / pr.dt + pr.nu * km2, Rv, Rv, T1, T1 + N, T1 + 2 * N, G(1), w1, w2,
+                    w3, 0.0, 1.0);
+      warp_qt_solve(N, p, km2, Rv, sv, T2, T2 + N, T2 + 2 * N, G(2), w1, w2, w3, 0.0, -1.0);
+      double2 sacc = czero();
+      for (int n = p + 2 * lane; n < N; n += 64) sacc = cfma((double)n * n, sv[n], sacc);
+      sacc = warp_allsum2(sacc);
+      const double* vh = tb + 9 * N;
+      const double2 coef = cscl(sacc, -g.vhS[(((size_t)b * 4 + o) * 2 + p) * K + m]);
+      for (int n = p + 2 * lane; n < N; n += 64)
+        sv[n] = make_double2(fma(coef.x, vh[n], sv[n].x), fma(coef.y, vh[n], sv[n].y));
     }
-    qt_solve(N, K, p, alpha, R, out, tab(0, 0), tab(0, 1), tab(0, 2), tabG(0), w1, w2, w3,
-             pr.dt / a0, 1.0);
-    return;
   }
-  if (m == 0) {
-    qt_solve(N, K, p, a0 / pr.dt, R, X, tab(1, 0), tab(1, 1), tab(1, 2), tabG(1), w1, w2, w3,
-             0.0, 1.0);
-    for (int n = p; n < N; n += 2) X[NK + (size_t)n * K] = czero();
-    return;
+  __syncthreads();
+  // u = i (D v) / k (m >= 1), continuity
+  if (m != 0) {
+    if (tid < 32) warp_cheb_deriv(sv, sR, N);
+    __syncthreads();
+    const double ik = 1.0 / km;
+    for (int n = tid; n < N; n += nt) shy[n] = cscl(mul_i(sR[n]), ik);
+    __syncthreads();
   }
-  // phi_p (in place in R), then v_p, then the influence correction
-  qt_solve(N, K, p, a0 / pr.dt + pr.nu * km2, R, R, tab(1, 0), tab(1, 1), tab(1, 2), tabG(1),
-           w1, w2, w3, 0.0, 1.0);
-  double2* V = X + NK;
-  qt_solve(N, K, p, km2, R, V, tab(2, 0), tab(2, 1), tab(2, 2), tabG(2), w1, w2, w3, 0.0, -1.0);
-  double2 s = czero();
-  for (int n = p; n < N; n += 2) s = cfma((double)n * n, V[(size_t)n * K], s);
-  const double* vh = g.vh + ((size_t)b * 4 + o) * NK + m;
-  const double2 coef = cscl(s, -g.vhS[(((size_t)b * 4 + o) * 2 + p) * K + m]);
-  for (int n = p; n < N; n += 2) {
-    const size_t on = (size_t)n * K;
-    V[on] = make_double2(fma(coef.x, vh[on], V[on].x), fma(coef.y, vh[on], V[on].y));
+  double2* Xw = g.X + (size_t)b * 5 * NK + (size_t)m * N;
+  for (int i = tid; i < N; i += nt) {
+    Xw[i] = shy[i];
+    Xw[NK + i] = sv[i];
+    Xw[2 * NK + i] = sc0[i];
+    Xw[3 * NK + i] = sc1[i];
+    Xw[4 * NK + i] = sc2[i];
   }
 }
 
-// u = i (D v) / k from continuity (Eq. 3), m >= 1.  Advances the counter.
-__global__ void k_uvel(GroupDev g) {
-  const int b = blockIdx.y;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= g.K || g.status[b]) return;
-  const int K = g.K, N = g.N;
-  const size_t NK = (size_t)N * K;
-  const MemberPrm pr = g.prm[b];
-  double2* X = g.X + (size_t)b * 5 * NK + m;
-  if (m == 0) {
-    g.count[b] += 1;
-    return;
+// Advance the step counters (after every block of k_spec has read them).
+__global__ void k_tick(GroupDev g) {
+  const int b = threadIdx.x + blockIdx.x * blockDim.x;
+  if (b < g.nb && !g.status[b]) g.count[b] += 1;
+}
+
+// Complex transpose of nf fields: dst[f][c][r] = src[f][r][c] (rows x cols).
+__global__ void k_transpose(const double2* __restrict__ src, double2* __restrict__ dst, int rows,
+                            int cols) {
+  __shared__ double2 t[32][33];
+  const int f = blockIdx.z;
+  const size_t off = (size_t)f * rows * cols;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = src[off + (size_t)r * cols + c];
   }
-  const double ik = pr.lx / (2.0 * 3.14159265358979323846 * m);
-  double2 p1 = czero(), p0 = czero();
-  double2 av = X[NK + (size_t)(N - 1) * K];
-  for (int n = N - 1; n >= 0; --n) {
-    const size_t o = (size_t)n * K;
-    const double2 d = (n == 0) ? cscl(p0, 0.5) : p0;
-    X[o] = cscl(mul_i(d), ik);
-    if (n >= 1) {
-      const double2 nv = X[NK + o - K];
-      const double2 pm = cfma(2.0 * n, av, p1);
-      p1 = p0; p0 = pm; av = nv;
-    }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) dst[off + (size_t)c * rows + r] = t[threadIdx.x][i];
   }
 }
 
 // ------------------------------------------------------------ diagnostics
-// Partial reductions per member, one block each (deterministic order):
-// part[0] = E by Clenshaw-Curtis in y (exact: 2N-1 points for degree 2N-2)
-// and Parseval in x; part[1] = <Tr c>; part[2] = sum |state| (finiteness).
 __device__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -678,6 +820,18 @@ __device__ double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
+__device__ double2 warp_sum2(double2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// Partial reductions per member, one block each (deterministic order):
+// part[0] = E by Clenshaw-Curtis in y (exact: 2N-1 points for degree 2N-2)
+// and Parseval in x; part[1] = <Tr c> from the mean mode with
+// int T_n = 2/(1-n^2) (n even); part[2] = sum |state| (finiteness).
 __global__ void __launch_bounds__(512) k_diag_part(GroupDev g) {
   const int b = blockIdx.x;
   if (g.status[b]) return;
@@ -696,7 +850,7 @@ __global__ void __launch_bounds__(512) k_diag_part(GroupDev g) {
   const double2* X = g.X + (size_t)b * 5 * NK;
   double mt = 0.0;
   for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    if ((n & 1) == 0) mt += (X[2 * NK + (size_t)n * K].x + X[4 * NK + (size_t)n * K].x) * (2.0 / (1.0 - (double)n * n));
+    if ((n & 1) == 0) mt += (X[2 * NK + n].x + X[4 * NK + n].x) * (2.0 / (1.0 - (double)n * n));
   }
   mt = block_sum(mt, sh);
   double cs = 0.0;
@@ -717,6 +871,7 @@ __global__ void __launch_bounds__(512) k_diag_final(GroupDev g) {
   if (g.status[b]) return;
   __shared__ double sh[32];
   __shared__ double s_tau, s_stats[4];
+  __shared__ double smn[32], smx[32], sma[32];
   extern __shared__ double2 dsm[];
   const int K = g.K, N = g.N, nx = g.nx;
   const size_t NK = (size_t)N * K;
@@ -741,7 +896,6 @@ __global__ void __launch_bounds__(512) k_diag_final(GroupDev g) {
   }
   nanf = __syncthreads_or(nanf);
   {
-    __shared__ double smn[32], smx[32], sma[32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) { smn[w] = mn; smx[w] = mx; sma[w] = ma; }
     __syncthreads();
@@ -768,36 +922,44 @@ __global__ void __launch_bounds__(512) k_diag_final(GroupDev g) {
   double cnt4[4] = {(double)c3, (double)c0, (double)b3, (double)b0};
   double tot4[4];
   for (int q = 0; q < 4; ++q) tot4[q] = block_sum(cnt4[q], sh);
-  // mid-plane spectra at y = 0: T_n(0) = cos(n pi/2), T_n'(0) = n sin(n pi/2)
+  // mid-plane spectra at y = 0: T_n(0) = cos(n pi/2), T_n'(0) = n sin(n pi/2);
+  // one warp per Fourier mode, lanes over the Chebyshev index
   double2* L = dsm;              // 3 lines of nx
   double2* L2 = dsm + 3 * nx;    // ping-pong
   const double2* X = g.X + (size_t)b * 5 * NK;
   const double kfac = 2.0 * 3.14159265358979323846 / pr.lx;
   for (int i = threadIdx.x; i < 3 * nx; i += blockDim.x) L[i] = czero();
   __syncthreads();
-  for (int m = threadIdx.x; m < K; m += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int m = warp; m < K; m += nw) {
     double2 tr = czero(), u = czero(), v = czero(), uy = czero();
-    for (int n = 0; n < N; ++n) {
-      const size_t o = (size_t)n * K + m;
+    const size_t cm = (size_t)m * N;
+    for (int n = lane; n < N; n += 32) {
       const int r4 = n & 3;
       if (r4 == 0 || r4 == 2) {
         const double s = (r4 == 0) ? 1.0 : -1.0;
-        tr = cfma(s, cadd(X[2 * NK + o], X[4 * NK + o]), tr);
-        u = cfma(s, X[o], u);
-        v = cfma(s, X[NK + o], v);
+        tr = cfma(s, cadd(X[2 * NK + cm + n], X[4 * NK + cm + n]), tr);
+        u = cfma(s, X[cm + n], u);
+        v = cfma(s, X[NK + cm + n], v);
       } else {
         const double s = (r4 == 1) ? (double)n : -(double)n;
-        uy = cfma(s, X[o], uy);
+        uy = cfma(s, X[cm + n], uy);
       }
     }
-    const double km = kfac * m;
-    double2 ux = cscl(mul_i(u), km), vx = cscl(mul_i(v), km);
-    if (m == 0) { tr.x += 1.0; u = czero(); tr.y = v.y = uy.y = 0.0; ux = vx = czero(); }
-    // lines: (Tr c, u') (v, ux) (vx, uy); Hermitian fill
-    double2 F[6] = {tr, u, v, ux, vx, uy};
-    for (int l = 0; l < 3; ++l) {
-      L[l * nx + m] = cadd(F[2 * l], mul_i(F[2 * l + 1]));
-      if (m > 0) L[l * nx + nx - m] = cadd(cconj(F[2 * l]), mul_i(cconj(F[2 * l + 1])));
+    tr = warp_sum2(tr);
+    u = warp_sum2(u);
+    v = warp_sum2(v);
+    uy = warp_sum2(uy);
+    if (lane == 0) {
+      const double km = kfac * m;
+      double2 ux = cscl(mul_i(u), km), vx = cscl(mul_i(v), km);
+      if (m == 0) { tr.x += 1.0; u = czero(); tr.y = v.y = uy.y = 0.0; ux = vx = czero(); }
+      // lines: (Tr c, u') (v, ux) (vx, uy); Hermitian fill
+      const double2 F[6] = {tr, u, v, ux, vx, uy};
+      for (int l = 0; l < 3; ++l) {
+        L[l * nx + m] = cadd(F[2 * l], mul_i(F[2 * l + 1]));
+        if (m > 0) L[l * nx + nx - m] = cadd(cconj(F[2 * l]), mul_i(cconj(F[2 * l + 1])));
+      }
     }
   }
   __syncthreads();
@@ -854,6 +1016,8 @@ __global__ void k_reset(GroupDev g, int b) {
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
+// Spectral coefficients (internal layout [member][field][m][n]) <-> values on
+// a y grid stored [member][field][j][m].
 YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl) {
   YJob J{};
   J.K = g.K;
@@ -863,6 +1027,10 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl)
   J.C = C;
   J.pl = pl;
   J.status = g.status;
+  J.cm = g.N;
+  J.cn = 1;
+  J.vm = 1;
+  J.vj = g.K;
   return J;
 }
 
@@ -871,6 +1039,7 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl)
 size_t smem_ycols(int C, int P) { return (size_t)(2 * C * P + 2 * C) * sizeof(double2); }
 size_t smem_xfused(int Mx) { return (size_t)14 * Mx * sizeof(double2); }
 size_t smem_xrows(int nl, int n) { return (size_t)2 * nl * n * sizeof(double2); }
+size_t smem_spec(int N) { return (size_t)12 * N * sizeof(double2) + (size_t)10 * N * sizeof(double); }
 
 template <typename F>
 static cudaError_t optin(F* fn, int optin_bytes) {
@@ -886,6 +1055,7 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
   if ((e = optin(k_ycols, optin_bytes))) return e;
   if ((e = optin(k_xfused, optin_bytes))) return e;
   if ((e = optin(k_xrows, optin_bytes))) return e;
+  if ((e = optin(k_spec, optin_bytes))) return e;
   if ((e = optin(k_diag_final, optin_bytes))) return e;
   return cudaSuccess;
 }
@@ -926,18 +1096,11 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       break;
     }
     case 3:
-      k_rhs<<<dim3(cdiv(g.K, 128), g.nb), 128, 0, st>>>(g, 0);
-      n = 1;
+      k_spec<<<dim3(g.K, g.nb), 256, smem_spec(g.N), st>>>(g, 0);
+      k_tick<<<cdiv(g.nb, 128), 128, 0, st>>>(g);
+      n = 2;
       break;
-    case 4:
-      k_solve<<<dim3(cdiv(g.K, 64), 8, g.nb), 64, 0, st>>>(g);
-      n = 1;
-      break;
-    case 5:
-      k_uvel<<<dim3(cdiv(g.K, 128), g.nb), 128, 0, st>>>(g);
-      n = 1;
-      break;
-    case 6: {  // diagnostics
+    case 4: {  // diagnostics
       const int Je = 2 * g.N - 1;
       YJob J = make_yjob(g, true, 2 * (g.N - 1), g.CcolE, g.plPe);
       J.src = g.X; J.dst = g.DY;
@@ -970,12 +1133,12 @@ cudaError_t launch_explicit(const GroupDev& g, cudaStream_t st) {
     cudaError_t e = launch_stage(g, s, st, nullptr);
     if (e) return e;
   }
-  k_rhs<<<dim3(cdiv(g.K, 128), g.nb), 128, 0, st>>>(g, 1);
+  k_spec<<<dim3(g.K, g.nb), 256, smem_spec(g.N), st>>>(g, 1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step(const GroupDev& g, cudaStream_t st, int* nl) {
-  for (int s = 0; s < 6; ++s) {
+  for (int s = 0; s < 4; ++s) {
     cudaError_t e = launch_stage(g, s, st, nl);
     if (e) return e;
   }
@@ -983,11 +1146,17 @@ cudaError_t launch_step(const GroupDev& g, cudaStream_t st, int* nl) {
 }
 
 cudaError_t launch_diag(const GroupDev& g, cudaStream_t st, int* nl) {
-  return launch_stage(g, 6, st, nl);
+  return launch_stage(g, 4, st, nl);
 }
 
 cudaError_t launch_reset_member(const GroupDev& g, int b, cudaStream_t st) {
   k_reset<<<1, 32, 0, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const double2* src, double2* dst, int nf, int rows, int cols,
+                             cudaStream_t st) {
+  k_transpose<<<dim3(cdiv(cols, 32), cdiv(rows, 32), nf), dim3(32, 8), 0, st>>>(src, dst, rows, cols);
   return cudaGetLastError();
 }
 

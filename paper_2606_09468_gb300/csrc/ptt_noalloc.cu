@@ -20,7 +20,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocBytes = size_t(32) << 20;  // 32 MiB per device
+constexpr size_t kNoAllocBytes = size_t(48) << 20;  // 48 MiB per device
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -78,6 +78,9 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   const size_t rows = (size_t)g.M + 1, K = g.K, NK = (size_t)g.N * K;
   // layout of the scratch array
   size_t off = 0;
+  const size_t oX = off; off = align256(off + 5 * NK * sizeof(double2));
+  const size_t oNR = off; off = align256(off + 5 * NK * sizeof(double2));
+  const size_t oRb = off; off = align256(off + 2 * NK * sizeof(double2));
   const size_t oYp = off; off = align256(off + 9 * rows * K * sizeof(double2));
   const size_t oZp = off; off = align256(off + 5 * rows * K * sizeof(double2));
   const size_t oTP = off; off = align256(off + twP.size() * sizeof(double2));
@@ -99,6 +102,9 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   if (s) return s;
   char* b = (char*)base;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  g.X = (double2*)(b + oX);     // input in the kernels' mode-major layout
+  g.NR = (double2*)(b + oNR);   // N_cxx, N_cxy, N_cyy, N_u, N_v
+  g.Rb = (double2*)(b + oRb);   // H_x, H_y
   g.Yp = (double2*)(b + oYp);
   g.Zp = (double2*)(b + oZp);
   g.plP.tw = (const double2*)(b + oTP);
@@ -106,9 +112,6 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   g.prm = (ptt::MemberPrm*)(b + oPr);
   g.status = (int*)(b + oSt);
   g.count = (long long*)(b + oCn);
-  g.X = (double2*)d_spec;             // read only: stage 0 and the stress divergence
-  g.NR = (double2*)d_out;             // N_cxx, N_cxy, N_cyy, then N_u, N_v
-  g.Rb = (double2*)d_out + 3 * NK;    // H_x, H_y overwrite N_u, N_v in place
   cudaError_t e;
   // status and step counter must read zero; tables and parameters are
   // rewritten on every call (the array keeps the previous call's contents)
@@ -119,7 +122,10 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
       (e = cudaMemcpyAsync(b + oTM, twMx.data(), twMx.size() * sizeof(double2),
                            cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(b + oPr, &prm, sizeof(prm), cudaMemcpyHostToDevice, st)) ||
+      (e = ptt::launch_transpose((const double2*)d_spec, g.X, 5, g.N, g.K, st)) ||
       (e = ptt::launch_explicit(g, st)) ||
+      (e = ptt::launch_transpose(g.NR, (double2*)d_out, 3, g.K, g.N, st)) ||
+      (e = ptt::launch_transpose(g.Rb, (double2*)d_out + 3 * NK, 2, g.K, g.N, st)) ||
       (e = cudaStreamSynchronize(st))) {
     char msg[256];
     std::snprintf(msg, sizeof(msg), "ptt_explicit_rhs_noalloc: %s", cudaGetErrorString(e));
