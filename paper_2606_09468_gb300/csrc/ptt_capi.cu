@@ -297,9 +297,9 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.vhS = cv.take<double>((size_t)nb * 4 * 2 * d.K);
     d.wrow = cv.take<double>((size_t)3 * d.N);
     d.ccw = cv.take<double>(Je);
-    d.DY = cv.take<double2>((size_t)nb * 4 * Je * d.K);
-    d.DV = cv.take<double>((size_t)nb * 2 * d.N * d.nx);
-    d.part = cv.take<double>((size_t)nb * kPart);
+    d.DY = cv.take<double2>((size_t)nb * 3 * Je * d.K);
+    d.DV = cv.take<double>((size_t)nb * d.N * d.nx);
+    d.part = cv.take<double>((size_t)nb * kTiles * kPart);
     d.DM = nullptr;
     d.ring = cv.take<ptt_diag>((size_t)nb * kRing);
     d.stage = cv.take<double>((size_t)5 * d.N * d.nx);
@@ -813,7 +813,7 @@ int ptt_time_stages(ptt_ctx* c, int32_t nsteps, double* ms) {
 int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) {
   if (!c || !flops || !bytes || !launches) return PTT_EINVAL;
   auto fft = [](double n) { return 5.0 * n * std::log2(n); };
-  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 2, 4};
+  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 2, 5};
   for (int s = 0; s < PTT_NSTAGES; ++s) { flops[s] = 0.0; bytes[s] = 0.0; launches[s] = 0; }
   for (Group& g : c->groups) {
     const GroupDev& d = g.d;
@@ -832,8 +832,8 @@ int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) 
     flops[3] += nb * NK * (6.0 * 4.0 + 4.0 * 4.0 * 8.0 + 8.0 * 24.0 / 2.0);
     bytes[3] += nb * (z * NK * (5.0 + 5.0 + 32.0 + 8.0 + 5.0) + r * NK * 10.0);
     // 4: diagnostics
-    flops[4] += nb * (4.0 * K * fft(d.Pe) + N * fft(d.nx) + 3.0 * fft(d.nx) + NK * 10.0);
-    bytes[4] += nb * (z * (5.0 * NK + 2.0 * 4.0 * Je * K) + r * 2.0 * 2.0 * N * d.nx);
+    flops[4] += nb * (3.0 * K * fft(d.Pe) + N * fft(d.nx) + 3.0 * fft(d.nx) + NK * 10.0);
+    bytes[4] += nb * (z * (5.0 * NK + 2.0 * 3.0 * Je * K) + r * 2.0 * N * d.nx);
     for (int s = 0; s < PTT_NSTAGES; ++s) launches[s] += nlaunch[s];
   }
   return PTT_OK;

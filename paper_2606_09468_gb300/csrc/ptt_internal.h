@@ -53,9 +53,9 @@ struct GroupDev {
   const double* vhS; // [nb][4][2][K]  1 / sum_n n^2 vh_n per parity
   const double* wrow;// [3][N]  1/(4n(n-1)), 1/(2(n^2-1)), 1/(4n(n+1))
   const double* ccw; // [2N-1] Clenshaw-Curtis weights of the diagnostic grid
-  double2* DY;       // [nb][4][2N-1][K]  cxx, cyy, u, v on the diagnostic y grid
-  double* DV;        // [nb][2][N][nx]  cxx, cyy on the unpadded grid
-  double* part;      // [nb][kPart]  partial reductions
+  double2* DY;       // [nb][3][2N-1][K]  cxx+cyy, u, v on the diagnostic y grid
+  double* DV;        // [nb][N][nx]  cxx+cyy on the unpadded grid
+  double* part;      // [nb][kTiles][kPart]  partial reductions
   double2* DM;       // [nb][6][K]  mid-plane spectra
   ptt_diag* ring;    // [nb][kRing]
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
@@ -63,7 +63,8 @@ struct GroupDev {
   FftPlan plP, plMx, plNx, plPu, plPe;
 };
 
-constexpr int kPart = 8;  // energy, ...
+constexpr int kPart = 16;  // values per diagnostics tile
+constexpr int kTiles = 16; // diagnostics tiles per member
 
 // Launch wrappers (device code in ptt_kernels.cu).  All asynchronous on `st`.
 cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nlaunch);

@@ -11,8 +11,8 @@
 //                       explicit terms, curl-curl forcing, SBDF sums, the
 //                       quasi-tridiagonal tau solves, u from continuity
 //   k_tick              step counters
-// followed by the diagnostics of Sec. 3 (k_ycols, k_diag_part, k_xrows,
-// k_diag_final).  All transforms are mixed-radix (2, 3, 4, 5) Stockham FFTs
+// followed by the diagnostics of Sec. 3 (k_ycols, k_xrows, k_diag_part,
+// k_diag_count, k_diag_final).  All transforms are mixed-radix (2, 3, 4, 5) Stockham FFTs
 // in shared memory; the Chebyshev transforms are discrete cosine transforms
 // of type I computed as FFTs of the even extension.
 //
@@ -171,6 +171,7 @@ struct YJob {
   long long src_mstride, dst_mstride;  // per member (elements)
   long long src_fstride, dst_fstride;  // per field (elements)
   int src_field[8];
+  int src_field2[8];  // inverse only: >= 0 adds this field to src_field
   int dst_field[8];
   int deriv[8];       // inverse only: transform d/dy of the field
   long long cm, cn;   // coefficient-side strides
@@ -214,9 +215,17 @@ __global__ void __launch_bounds__(256) k_ycols(YJob J) {
   double2* dst = J.dst + b * J.dst_mstride + J.dst_field[f] * J.dst_fstride;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (J.inverse) {
+    const double2* src2 = (J.src_field2[f] >= 0)
+        ? J.src + b * J.src_mstride + J.src_field2[f] * J.src_fstride : nullptr;
     for (int i = tid; i < N * C; i += nt) {
       const int c = i / N, n = i - c * N;
-      A[c * P + n] = (c < nc) ? src[(c0 + c) * J.cm + n * J.cn] : czero();
+      double2 v = czero();
+      if (c < nc) {
+        const long long o = (c0 + c) * J.cm + n * J.cn;
+        v = src[o];
+        if (src2) v = cadd(v, src2[o]);
+      }
+      A[c * P + n] = v;
     }
     __syncthreads();
     if (J.deriv[f]) {
@@ -828,105 +837,162 @@ __device__ double2 warp_sum2(double2 v) {
   return v;
 }
 
-// Partial reductions per member, one block each (deterministic order):
-// part[0] = E by Clenshaw-Curtis in y (exact: 2N-1 points for degree 2N-2)
-// and Parseval in x; part[1] = <Tr c> from the mean mode with
-// int T_n = 2/(1-n^2) (n even); part[2] = sum |state| (finiteness).
-__global__ void __launch_bounds__(512) k_diag_part(GroupDev g) {
-  const int b = blockIdx.x;
-  if (g.status[b]) return;
-  __shared__ double sh[32];
-  const int K = g.K, N = g.N, Je = 2 * N - 1;
-  const size_t NK = (size_t)N * K;
-  const double2* DY = g.DY + (size_t)b * 4 * Je * K;
-  double e = 0.0;
-  for (int i = threadIdx.x; i < Je * K; i += blockDim.x) {
-    const int j = i / K, m = i - j * K;
-    const double2 uu = DY[(size_t)2 * Je * K + i], vv = DY[(size_t)3 * Je * K + i];
-    const double w = (m == 0 ? 1.0 : 2.0) * g.ccw[j];
-    e += w * (uu.x * uu.x + uu.y * uu.y + vv.x * vv.x + vv.y * vv.y);
+// Diagnostics of one step, per member, as tiles (kTiles blocks per member)
+// with partial results in part[member][tile][kPart] reduced in a fixed
+// order (deterministic):
+//   DY: (c_xx + c_yy, u, v) on the diagnostic y grid (2N-1 Gauss-Lobatto
+//       points, Fourier modes); DV: c_xx + c_yy on the unpadded grid.
+//   E = <|u|^2/2> by Clenshaw-Curtis in y (exact for degree 2N-2) and
+//   Parseval in x; extrema of Tr c = c_xx + c_yy + 1; a non-finite test of
+//   the state on the bit patterns; then the counts of Tr c < 3, < 0 and the
+//   tie bands |Tr c - 3|, |Tr c| <= tau = 1e-9 max|Tr c|.
+enum { P_E = 0, P_MIN, P_MAX, P_AMAX, P_BAD, P_C3, P_C0, P_B3, P_B0 };
+
+__device__ __forceinline__ bool nonfinite(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL;
+}
+
+// block-wide (sum, min, max, max, or) reduction, result valid in thread 0
+struct Red5 { double s, mn, mx, ma; int bad; };
+__device__ Red5 block_red5(Red5 r) {
+  __shared__ double ss[32], smn[32], smx[32], sma[32];
+  __shared__ int sbad[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    r.s += __shfl_down_sync(0xffffffffu, r.s, o);
+    r.mn = fmin(r.mn, __shfl_down_sync(0xffffffffu, r.mn, o));
+    r.mx = fmax(r.mx, __shfl_down_sync(0xffffffffu, r.mx, o));
+    r.ma = fmax(r.ma, __shfl_down_sync(0xffffffffu, r.ma, o));
+    r.bad |= __shfl_down_sync(0xffffffffu, r.bad, o);
   }
-  e = block_sum(e, sh);
-  const double2* X = g.X + (size_t)b * 5 * NK;
-  double mt = 0.0;
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    if ((n & 1) == 0) mt += (X[2 * NK + n].x + X[4 * NK + n].x) * (2.0 / (1.0 - (double)n * n));
-  }
-  mt = block_sum(mt, sh);
-  double cs = 0.0;
-  for (size_t i = threadIdx.x; i < 5 * NK; i += blockDim.x) cs += fabs(X[i].x) + fabs(X[i].y);
-  cs = block_sum(cs, sh);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { ss[w] = r.s; smn[w] = r.mn; smx[w] = r.mx; sma[w] = r.ma; sbad[w] = r.bad; }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double* pp = g.part + (size_t)b * kPart;
-    pp[0] = 0.25 * e;
-    pp[1] = 0.5 * mt + 1.0;
-    pp[2] = cs;
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      r.s += ss[i]; r.mn = fmin(r.mn, smn[i]); r.mx = fmax(r.mx, smx[i]);
+      r.ma = fmax(r.ma, sma[i]); r.bad |= sbad[i];
+    }
+  }
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_diag_part(GroupDev g) {
+  const int b = blockIdx.y, tile = blockIdx.x;
+  if (g.status[b]) return;
+  const int K = g.K, N = g.N, nx = g.nx, Je = 2 * N - 1;
+  const size_t NK = (size_t)N * K;
+  const double2* DY = g.DY + (size_t)b * 3 * Je * K;
+  Red5 r{0.0, 1e308, -1e308, 0.0, 0};
+  // energy: DY fields 1 (u) and 2 (v)
+  {
+    const long long tot = (long long)Je * K, per = (tot + kTiles - 1) / kTiles;
+    const long long i0 = tile * per, i1 = min(tot, i0 + per);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const int j = (int)(i / K), m = (int)(i - (long long)j * K);
+      const double2 uu = DY[(size_t)Je * K + i], vv = DY[(size_t)2 * Je * K + i];
+      const double w = (m == 0 ? 1.0 : 2.0) * g.ccw[j];
+      r.s += w * (uu.x * uu.x + uu.y * uu.y + vv.x * vv.x + vv.y * vv.y);
+    }
+  }
+  // extrema of Tr c on the unpadded grid
+  {
+    const double* tr = g.DV + (size_t)b * N * nx;
+    const long long tot = (long long)N * nx, per = (tot + kTiles - 1) / kTiles;
+    const long long i0 = tile * per, i1 = min(tot, i0 + per);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const double t = tr[i] + 1.0;
+      r.bad |= nonfinite(t);
+      r.mn = fmin(r.mn, t);
+      r.mx = fmax(r.mx, t);
+      r.ma = fmax(r.ma, fabs(t));
+    }
+  }
+  // non-finite state values (integer test)
+  {
+    const double* X = reinterpret_cast<const double*>(g.X + (size_t)b * 5 * NK);
+    const long long tot = 10LL * NK, per = (tot + kTiles - 1) / kTiles;
+    const long long i0 = tile * per, i1 = min(tot, i0 + per);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) r.bad |= nonfinite(X[i]);
+  }
+  r = block_red5(r);
+  if (threadIdx.x == 0) {
+    double* pp = g.part + ((size_t)b * kTiles + tile) * kPart;
+    pp[P_E] = r.s;
+    pp[P_MIN] = r.mn;
+    pp[P_MAX] = r.mx;
+    pp[P_AMAX] = r.ma;
+    pp[P_BAD] = r.bad ? 1.0 : 0.0;
   }
 }
 
-// Per member: volume counts over the unpadded grid, mid-plane statistics,
-// blow-up test, record.
-__global__ void __launch_bounds__(512) k_diag_final(GroupDev g) {
-  const int b = blockIdx.x;
+__global__ void __launch_bounds__(256) k_diag_count(GroupDev g) {
+  const int b = blockIdx.y, tile = blockIdx.x;
   if (g.status[b]) return;
-  __shared__ double sh[32];
-  __shared__ double s_tau, s_stats[4];
-  __shared__ double smn[32], smx[32], sma[32];
-  extern __shared__ double2 dsm[];
-  const int K = g.K, N = g.N, nx = g.nx;
-  const size_t NK = (size_t)N * K;
-  const MemberPrm pr = g.prm[b];
-  const double* cxx = g.DV + (size_t)b * 2 * N * nx;
-  const double* cyy = cxx + (size_t)N * nx;
-  const int npts = N * nx;
-  // pass A: min, max, max|.|
-  double mn = 1e308, mx = -1e308, ma = 0.0;
-  bool nanf = false;
-  for (int i = threadIdx.x; i < npts; i += blockDim.x) {
-    const double t = cxx[i] + cyy[i] + 1.0;
-    if (!(t == t)) nanf = true;
-    mn = fmin(mn, t);
-    mx = fmax(mx, t);
-    ma = fmax(ma, fabs(t));
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
-    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    ma = fmax(ma, __shfl_down_sync(0xffffffffu, ma, o));
-  }
-  nanf = __syncthreads_or(nanf);
-  {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { smn[w] = mn; smx[w] = mx; sma[w] = ma; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-        mn = fmin(mn, smn[i]); mx = fmax(mx, smx[i]); ma = fmax(ma, sma[i]);
-      }
-      s_stats[0] = nanf ? __longlong_as_double(0x7ff8000000000000LL) : mn;
-      s_stats[1] = nanf ? __longlong_as_double(0x7ff8000000000000LL) : mx;
-      s_tau = 1e-9 * ma;
-    }
-    __syncthreads();
-  }
-  const double tau = s_tau;
-  // pass B: counts
-  long long c3 = 0, c0 = 0, b3 = 0, b0 = 0;
-  for (int i = threadIdx.x; i < npts; i += blockDim.x) {
-    const double t = cxx[i] + cyy[i] + 1.0;
+  const int N = g.N, nx = g.nx;
+  double ma = 0.0;
+  for (int t = 0; t < kTiles; ++t) ma = fmax(ma, g.part[((size_t)b * kTiles + t) * kPart + P_AMAX]);
+  const double tau = 1e-9 * ma;
+  const double* tr = g.DV + (size_t)b * N * nx;
+  const long long tot = (long long)N * nx, per = (tot + kTiles - 1) / kTiles;
+  const long long i0 = tile * per, i1 = min(tot, i0 + per);
+  int c3 = 0, c0 = 0, b3 = 0, b0 = 0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const double t = tr[i] + 1.0;
     c3 += (t < 3.0);
     c0 += (t < 0.0);
     b3 += (fabs(t - 3.0) <= tau);
     b0 += (fabs(t) <= tau);
   }
-  double cnt4[4] = {(double)c3, (double)c0, (double)b3, (double)b0};
-  double tot4[4];
-  for (int q = 0; q < 4; ++q) tot4[q] = block_sum(cnt4[q], sh);
+  for (int o = 16; o > 0; o >>= 1) {
+    c3 += __shfl_down_sync(0xffffffffu, c3, o);
+    c0 += __shfl_down_sync(0xffffffffu, c0, o);
+    b3 += __shfl_down_sync(0xffffffffu, b3, o);
+    b0 += __shfl_down_sync(0xffffffffu, b0, o);
+  }
+  __shared__ int sc[4][32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sc[0][w] = c3; sc[1][w] = c0; sc[2][w] = b3; sc[3][w] = b0; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t4[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q)
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t4[q] += sc[q][i];
+    double* pp = g.part + ((size_t)b * kTiles + tile) * kPart;
+    pp[P_C3] = (double)t4[0];
+    pp[P_C0] = (double)t4[1];
+    pp[P_B3] = (double)t4[2];
+    pp[P_B0] = (double)t4[3];
+  }
+}
+
+// Per member: reduce the tiles, <Tr c> from the mean mode, mid-plane
+// statistics, blow-up test, record.
+__global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
+  const int b = blockIdx.x;
+  if (g.status[b]) return;
+  __shared__ double sh[32];
+  extern __shared__ double2 dsm[];
+  const int K = g.K, N = g.N, nx = g.nx;
+  const size_t NK = (size_t)N * K;
+  const MemberPrm pr = g.prm[b];
+  const double* pp = g.part + (size_t)b * kTiles * kPart;
+  double tau;
+  {
+    double ma = 0.0;
+    for (int t = 0; t < kTiles; ++t) ma = fmax(ma, pp[t * kPart + P_AMAX]);
+    tau = 1e-9 * ma;
+  }
+  const double2* X = g.X + (size_t)b * 5 * NK;
+  // <Tr c> = 1/2 int (c_xx + c_yy)_0 dy + 1, int T_n = 2/(1-n^2), n even
+  double mt = 0.0;
+  for (int n = threadIdx.x; n < N; n += blockDim.x)
+    if ((n & 1) == 0) mt += (X[2 * NK + n].x + X[4 * NK + n].x) * (2.0 / (1.0 - (double)n * n));
+  mt = block_sum(mt, sh);
   // mid-plane spectra at y = 0: T_n(0) = cos(n pi/2), T_n'(0) = n sin(n pi/2);
   // one warp per Fourier mode, lanes over the Chebyshev index
   double2* L = dsm;              // 3 lines of nx
   double2* L2 = dsm + 3 * nx;    // ping-pong
-  const double2* X = g.X + (size_t)b * 5 * NK;
   const double kfac = 2.0 * 3.14159265358979323846 / pr.lx;
   for (int i = threadIdx.x; i < 3 * nx; i += blockDim.x) L[i] = czero();
   __syncthreads();
@@ -983,23 +1049,33 @@ __global__ void __launch_bounds__(512) k_diag_final(GroupDev g) {
   double mct[4];
   for (int q = 0; q < 4; ++q) mct[q] = block_sum(mc[q], sh);
   if (threadIdx.x == 0) {
-    const double* pp = g.part + (size_t)b * kPart;
+    double e = 0.0, mn = 1e308, mx = -1e308, c4[4] = {0, 0, 0, 0};
+    bool bad = false;
+    for (int t = 0; t < kTiles; ++t) {
+      const double* q = pp + t * kPart;
+      e += q[P_E];
+      mn = fmin(mn, q[P_MIN]);
+      mx = fmax(mx, q[P_MAX]);
+      bad |= (q[P_BAD] != 0.0);
+      for (int k = 0; k < 4; ++k) c4[k] += q[P_C3 + k];
+    }
+    e *= 0.25;
     const long long step = g.count[b];
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
     ptt_diag r;
     r.step = step;
     r.t = step * pr.dt;
-    r.energy = pp[0];
-    r.mean_trc = pp[1];
-    r.min_trc = s_stats[0];
-    r.max_trc = s_stats[1];
-    r.n_lt3 = (long long)tot4[0]; r.n_lt0 = (long long)tot4[1];
-    r.n_band3 = (long long)tot4[2]; r.n_band0 = (long long)tot4[3];
+    r.energy = e;
+    r.mean_trc = 0.5 * mt + 1.0;
+    r.min_trc = bad ? qnan : mn;
+    r.max_trc = bad ? qnan : mx;
+    r.n_lt3 = (long long)c4[0]; r.n_lt0 = (long long)c4[1];
+    r.n_band3 = (long long)c4[2]; r.n_band0 = (long long)c4[3];
     r.n_mid_lt3 = (long long)mct[0]; r.n_mid_lt0 = (long long)mct[1];
     r.n_mid_band3 = (long long)mct[2]; r.n_mid_band0 = (long long)mct[3];
     for (int qq = 0; qq < 8; ++qq)
       for (int k = 0; k < 4; ++k) r.mid_sums[qq][k] = (qq < 6) ? msum[qq][k] : 0.0;
-    const bool fin = isfinite(pp[2]) && isfinite(pp[0]) && isfinite(r.max_trc);
-    const bool blow = !fin || r.max_trc > pr.trc_max || sqrt(2.0 * pp[0]) > pr.u_max;
+    const bool blow = bad || !isfinite(e) || r.max_trc > pr.trc_max || sqrt(2.0 * e) > pr.u_max;
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
     g.ring[(size_t)b * kRing + (size_t)(step % kRing)] = r;
@@ -1031,6 +1107,7 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl)
   J.cn = 1;
   J.vm = 1;
   J.vj = g.K;
+  for (int i = 0; i < 8; ++i) J.src_field2[i] = -1;
   return J;
 }
 
@@ -1104,21 +1181,23 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       const int Je = 2 * g.N - 1;
       YJob J = make_yjob(g, true, 2 * (g.N - 1), g.CcolE, g.plPe);
       J.src = g.X; J.dst = g.DY;
-      J.src_mstride = 5 * NK; J.dst_mstride = 4LL * Je * g.K;
+      J.src_mstride = 5 * NK; J.dst_mstride = 3LL * Je * g.K;
       J.src_fstride = NK; J.dst_fstride = (long long)Je * g.K;
-      const int sf[4] = {2, 4, 0, 1};
-      for (int i = 0; i < 4; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = 0; }
-      k_ycols<<<dim3(cdiv(g.K, g.CcolE), 4, g.nb), 256, smem_ycols(g.CcolE, g.Pe), st>>>(J);
-      k_diag_part<<<g.nb, 512, 0, st>>>(g);
+      const int sf[3] = {2, 0, 1};   // c_xx (+ c_yy), u, v
+      for (int i = 0; i < 3; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = 0; }
+      J.src_field2[0] = 4;
+      k_ycols<<<dim3(cdiv(g.K, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Pe), st>>>(J);
       XJob X{};
       X.srcC = g.DY; X.dstR = g.DV;
-      X.src_mstride = 4LL * Je * g.K; X.dst_mstride = 2LL * g.N * g.nx;
+      X.src_mstride = 3LL * Je * g.K; X.dst_mstride = (long long)g.N * g.nx;
       X.src_fstride = (long long)Je * g.K; X.dst_fstride = (long long)g.N * g.nx;
       X.src_rstep = 2; X.dst_rstep = 1;
-      X.nf = 2; X.K = g.K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
+      X.nf = 1; X.K = g.K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
       k_xrows<<<dim3(g.N, g.nb), 256, smem_xrows(1, g.nx), st>>>(X);
-      k_diag_final<<<g.nb, 512, smem_xrows(3, g.nx), st>>>(g);
-      n = 4;
+      k_diag_part<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
+      k_diag_count<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
+      k_diag_final<<<g.nb, 256, smem_xrows(3, g.nx), st>>>(g);
+      n = 5;
       break;
     }
     default:
