@@ -167,7 +167,7 @@ int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec5);
  * aligned, distinct.  The intermediates live in a static device array of
  * 48 MiB that the library image carries (held on every GPU that loads the
  * library until the process exits); shapes whose intermediates exceed it
- * ((12 ny + 14 (M+1)) (nx/2) 16 bytes plus tables, M the padded Chebyshev
+ * ((12 ny + 14 M) (nx/2) 16 bytes plus tables, M the padded Chebyshev
  * grid: every shape up to nx = 512, ny = 257 fits, nx = 512, ny = 513 does
  * not) return PTT_ENOMEM with the sizes in ptt_last_error().  No device
  * memory is allocated or freed.

@@ -233,7 +233,7 @@ struct Group {
   int nx, ny;
   std::vector<int> members;  // global member ids
   GroupDev d{};
-  HostPlan hp[5];            // P, Mx, nx, Pu, Pe
+  HostPlan hp[5];            // M, Mx, nx, Pu, Me
 };
 
 int check_params(const ptt_params& p) {
@@ -246,6 +246,11 @@ int check_params(const ptt_params& p) {
   return PTT_OK;
 }
 
+// Sizes of one shape.  Padded y grid: M Gauss points, M even, M 5-smooth
+// (one FFT of length M per column), M >= (3 ny - 2)/2 so that quadratic
+// products are alias-free for the retained Chebyshev modes (T_k aliases to
+// -T_{2M-k} on the Gauss points).  Diagnostic grid for the energy: Me >= 2 ny - 1
+// Gauss points (Fejer's first rule is exact to degree Me - 1 >= 2 ny - 2).
 void group_sizes(int nx, int ny, Group& g) {
   GroupDev& d = g.d;
   d.nx = nx;
@@ -253,11 +258,13 @@ void group_sizes(int nx, int ny, Group& g) {
   d.N = ny;
   d.Mx = next_smooth(3 * nx / 2 - 2);
   int M = (3 * ny - 2 + 1) / 2;
-  while (!smooth235(2LL * M)) ++M;
+  while ((M & 1) || !smooth235(M)) ++M;
   d.M = M;
-  d.P = 2 * M;
+  d.P = M;
   d.Pu = 2 * (ny - 1);
-  d.Pe = 4 * (ny - 1);
+  int Me = 2 * ny - 1;
+  while ((Me & 1) || !smooth235(Me)) ++Me;
+  d.Me = Me;
   const size_t target = 96 * 1024;
   auto cols = [&](int P) {
     long long c = (long long)(target / smem_ycols(1, P));
@@ -265,13 +272,14 @@ void group_sizes(int nx, int ny, Group& g) {
     if (c > 16) c = 16;
     return (int)c;
   };
-  d.Ccol = cols(d.P);
-  d.CcolE = cols(d.Pe);
-  g.hp[0] = make_plan(d.P);
+  d.Ccol = cols(d.M);
+  d.CcolE = cols(d.Me);
+  d.CcolU = cols(d.Pu);
+  g.hp[0] = make_plan(d.M);
   g.hp[1] = make_plan(d.Mx);
   g.hp[2] = make_plan(nx);
   g.hp[3] = make_plan(d.Pu);
-  g.hp[4] = make_plan(d.Pe);
+  g.hp[4] = make_plan(d.Me);
 }
 
 // Carve (or, with base == nullptr, size) all device arrays.
@@ -280,7 +288,7 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     GroupDev& d = g.d;
     const int nb = (int)g.members.size();
     d.nb = nb;
-    const size_t NK = (size_t)d.N * d.K, rows = (size_t)d.M + 1, Je = 2 * (size_t)d.N - 1;
+    const size_t NK = (size_t)d.N * d.K, rows = (size_t)d.M, Je = (size_t)d.Me;
     d.prm = cv.take<MemberPrm>(nb);
     d.status = cv.take<int>(nb);
     d.count = cv.take<long long>(nb);
@@ -297,7 +305,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.vhS = cv.take<double>((size_t)nb * 4 * 2 * d.K);
     d.wrow = cv.take<double>((size_t)3 * d.N);
     d.ccw = cv.take<double>(Je);
-    d.DY = cv.take<double2>((size_t)nb * 3 * Je * d.K);
+    d.DY = cv.take<double2>((size_t)nb * 2 * Je * d.K);
+    d.DT = cv.take<double2>((size_t)nb * NK);
     d.DV = cv.take<double>((size_t)nb * d.N * d.nx);
     d.part = cv.take<double>((size_t)nb * kTiles * kPart);
     d.DM = nullptr;
@@ -311,6 +320,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       for (int s = 0; s < pls[i]->nst; ++s) pls[i]->radix[s] = g.hp[i].radix[s];
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
     }
+    d.tw4P = cv.take<double2>((size_t)d.M);
+    d.tw4E = cv.take<double2>((size_t)d.Me);
   }
 }
 
@@ -374,7 +385,7 @@ void set_last_error(const char* msg) {
 }
 
 int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
-               std::vector<double2>& twMx, MemberPrm& prm) {
+               std::vector<double2>& twMx, std::vector<double2>& tw4, MemberPrm& prm) {
   const int s = check_params(p);
   if (s) return s;
   Group g;
@@ -396,6 +407,12 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
       cis(k, hp.n, &cc, &ss);
       (*tws[i])[k] = make_double2(cc, -ss);
     }
+  }
+  tw4.resize(d.M);
+  for (int k = 0; k < d.M; ++k) {
+    double cc, ss;
+    cis(k, 4LL * d.M, &cc, &ss);
+    tw4[k] = make_double2(cc, -ss);
   }
   prm.lx = p.lx; prm.re = p.re; prm.wi = p.wi; prm.beta = p.beta; prm.eps = p.eps;
   prm.kappa = p.kappa; prm.dt = p.dt;
@@ -536,23 +553,38 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
     CK(cudaMemcpyAsync((void*)d.vh, vh.data(), vh.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync((void*)d.vhS, vhS.data(), vhS.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync((void*)d.wrow, w.data(), w.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    // Clenshaw-Curtis weights on the diagnostic grid (Me = 2(N-1) intervals):
-    // w_j = sum over even n <= Me of (2/(Me cb_n cb_j)) T_n(y_j) * 2/(1 - n^2)
+    // Fejer's first rule on the Me Gauss points y_j = cos(theta_j),
+    // theta_j = pi (2j+1)/(2 Me): w_j = int of the interpolant's basis,
+    // w_j = (2/Me) [1 + sum_{n even, 2 <= n < Me} cos(n theta_j) * 2/(1 - n^2)]
     {
-      const int Me = 2 * (N - 1);
-      std::vector<double> cw(Me + 1, 0.0);
-      for (int j = 0; j <= Me; ++j) {
-        double acc = 0.0;
-        for (int n = 0; n <= Me; n += 2) {
+      const int Me = d.Me;
+      std::vector<double> cw(Me, 0.0);
+      for (int j = 0; j < Me; ++j) {
+        double acc = 1.0;
+        for (int n = 2; n < Me; n += 2) {
           double cc, ss;
-          cis((long long)n * j, 2LL * Me, &cc, &ss);
-          const double cbn = (n == 0 || n == Me) ? 2.0 : 1.0;
-          acc += cc / cbn * 2.0 / (1.0 - (double)n * n);
+          cis((long long)n * (2 * j + 1), 4LL * Me, &cc, &ss);
+          acc += cc * 2.0 / (1.0 - (double)n * n);
         }
-        const double cbj = (j == 0 || j == Me) ? 2.0 : 1.0;
-        cw[j] = 2.0 / (Me * cbj) * acc;
+        cw[j] = 2.0 / Me * acc;
       }
       CK(cudaMemcpyAsync((void*)d.ccw, cw.data(), cw.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    }
+    // quarter-period twiddles of the Gauss-grid transforms: exp(-i pi k/(2M))
+    {
+      const int Ms[2] = {d.M, d.Me};
+      const double2* dst[2] = {d.tw4P, d.tw4E};
+      for (int t = 0; t < 2; ++t) {
+        std::vector<double2> tw(Ms[t]);
+        for (int k = 0; k < Ms[t]; ++k) {
+          double cc, ss;
+          cis(k, 4LL * Ms[t], &cc, &ss);
+          tw[k] = make_double2(cc, -ss);
+        }
+        CK(cudaMemcpyAsync((void*)dst[t], tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+      }
     }
     // twiddle tables
     FftPlan* pls[5] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe};
@@ -813,27 +845,29 @@ int ptt_time_stages(ptt_ctx* c, int32_t nsteps, double* ms) {
 int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) {
   if (!c || !flops || !bytes || !launches) return PTT_EINVAL;
   auto fft = [](double n) { return 5.0 * n * std::log2(n); };
-  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 2, 5};
+  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 2, 6};
   for (int s = 0; s < PTT_NSTAGES; ++s) { flops[s] = 0.0; bytes[s] = 0.0; launches[s] = 0; }
   for (Group& g : c->groups) {
     const GroupDev& d = g.d;
-    const double nb = d.nb, K = d.K, N = d.N, NK = N * K, rows = d.M + 1.0, Je = 2.0 * N - 1.0;
+    const double nb = d.nb, K = d.K, N = d.N, NK = N * K, rows = d.M, Je = d.Me;
     const double z = 16.0, r = 8.0;  // bytes of a complex / real double
-    // 0: 9 complex DCT-I columns (FFT of the 2M-point even extension) + 4 d/dy
-    flops[0] += nb * (9.0 * K * fft(d.P) + 4.0 * K * N * 4.0);
+    // 0: 9 complex columns, DCT-III on the M Gauss points (one FFT of M) + 4 d/dy
+    flops[0] += nb * (9.0 * K * (fft(d.M) + 8.0 * d.M) + 4.0 * K * N * 4.0);
     bytes[0] += nb * z * (5.0 * NK + 9.0 * rows * K);
     // 1: per padded row 7 inverse + 3 forward complex FFTs of Mx, 42 flops of products per point
     flops[1] += nb * rows * (10.0 * fft(d.Mx) + 42.0 * d.Mx);
     bytes[1] += nb * z * (9.0 + 5.0) * rows * K;
-    // 2: 5 complex DCT-I columns
-    flops[2] += nb * 5.0 * K * fft(d.P);
+    // 2: 5 complex columns, DCT-II
+    flops[2] += nb * 5.0 * K * (fft(d.M) + 8.0 * d.M);
     bytes[2] += nb * z * (5.0 * rows * K + 5.0 * NK);
     // 3: 6 recurrences, SBDF sums over 4 levels of 8 fields, 8 tau sweeps
     flops[3] += nb * NK * (6.0 * 4.0 + 4.0 * 4.0 * 8.0 + 8.0 * 24.0 / 2.0);
     bytes[3] += nb * (z * NK * (5.0 + 5.0 + 32.0 + 8.0 + 5.0) + r * NK * 10.0);
-    // 4: diagnostics
-    flops[4] += nb * (3.0 * K * fft(d.Pe) + N * fft(d.nx) + 3.0 * fft(d.nx) + NK * 10.0);
-    bytes[4] += nb * (z * (5.0 * NK + 2.0 * 3.0 * Je * K) + r * 2.0 * N * d.nx);
+    // 4: diagnostics: DCT-I of one field (FFT of 2(N-1)), DCT-III of u, v on Me points,
+    //    x transforms of the unpadded rows and the mid-plane, reductions
+    flops[4] += nb * (K * fft(d.Pu) + 2.0 * K * (fft(d.Me) + 8.0 * d.Me) + N * fft(d.nx) +
+                      3.0 * fft(d.nx) + NK * 10.0 + 8.0 * Je * K);
+    bytes[4] += nb * (z * (5.0 * NK + 2.0 * 2.0 * Je * K + 2.0 * NK) + r * 2.0 * N * d.nx);
     for (int s = 0; s < PTT_NSTAGES; ++s) launches[s] += nlaunch[s];
   }
   return PTT_OK;

@@ -34,17 +34,17 @@ struct MemberPrm {
 struct GroupDev {
   int nb;            // members in the group
   int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
-  int Mx, M, P;      // padded x points, padded y intervals, y FFT length 2M
-  int Pu, Pe;        // y FFT lengths of the unpadded (2(N-1)) and diagnostic (4(N-1)) grids
-  int Ccol, CcolE;   // columns per block of the padded / diagnostic y passes
+  int Mx, M, P;      // padded x points, padded y Gauss points (= y FFT length), P = M
+  int Pu, Me;        // y FFT length of the unpadded grid (2(N-1)); diagnostic Gauss points
+  int Ccol, CcolE, CcolU;  // columns per block: padded / diagnostic / unpadded y passes
   MemberPrm* prm;    // [nb]
   int* status;       // [nb]  0 = running, 1 = blown up
   long long* count;  // [nb]  steps since the state was set
   double2* X;        // [nb][5][K][N]  state u, v, cxx, cxy, cyy
   double2* Eh;       // [4 slot][nb][4][K][N]  evolved quantities (cxx, cxy, cyy, q)
   double2* Nh;       // [4 slot][nb][4][K][N]  their explicit terms
-  double2* Yp;       // [nb][9][M+1][K]  fields on the padded y grid
-  double2* Zp;       // [nb][5][M+1][K]  products, x-analysed, on the padded y grid
+  double2* Yp;       // [nb][9][M][K]  fields on the padded y grid (Gauss points)
+  double2* Zp;       // [nb][5][M][K]  products, x-analysed, on the padded y grid
   double2* NR;       // [nb][5][K][N]  explicit nonlinear terms, spectral
   double2* Rb;       // [nb][4][K][N]  H_x, H_y of ptt_explicit_rhs
   const double* qt;  // [nb][4 order][3 sys][3 (Q, inv, F)][K][N]
@@ -52,15 +52,18 @@ struct GroupDev {
   const double* vh;  // [nb][4][K][N]  homogeneous v of the influence step
   const double* vhS; // [nb][4][2][K]  1 / sum_n n^2 vh_n per parity
   const double* wrow;// [3][N]  1/(4n(n-1)), 1/(2(n^2-1)), 1/(4n(n+1))
-  const double* ccw; // [2N-1] Clenshaw-Curtis weights of the diagnostic grid
-  double2* DY;       // [nb][3][2N-1][K]  cxx+cyy, u, v on the diagnostic y grid
+  const double* ccw; // [Me] Fejer weights of the diagnostic Gauss grid
+  double2* DY;       // [nb][2][Me][K]  u, v on the diagnostic y grid
+  double2* DT;       // [nb][N][K]  cxx+cyy on the unpadded y rows, Fourier modes
   double* DV;        // [nb][N][nx]  cxx+cyy on the unpadded grid
   double* part;      // [nb][kTiles][kPart]  partial reductions
   double2* DM;       // [nb][6][K]  mid-plane spectra
   ptt_diag* ring;    // [nb][kRing]
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
   double2* stageS;   // [5][N][K]  values on the unpadded y grid, x analysed
-  FftPlan plP, plMx, plNx, plPu, plPe;
+  const double2* tw4P;  // [M]  exp(-i pi k/(2M)), padded Gauss grid
+  const double2* tw4E;  // [Me] exp(-i pi k/(2Me)), diagnostic Gauss grid
+  FftPlan plP, plMx, plNx, plPu, plPe;   // lengths M, Mx, nx, 2(N-1), Me
 };
 
 constexpr int kPart = 16;  // values per diagnostics tile
@@ -81,7 +84,7 @@ cudaError_t set_kernel_attributes(int max_dyn_smem);
 // Host helpers (ptt_capi.cu) used by the workspace-free entry point.
 void set_last_error(const char* msg);
 int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
-               std::vector<double2>& twMx, MemberPrm& prm);
+               std::vector<double2>& twMx, std::vector<double2>& tw4, MemberPrm& prm);
 
 size_t smem_ycols(int C, int P);
 size_t smem_xfused(int Mx);

@@ -161,276 +161,6 @@ __constant__ double c_sb[4][4] = {{1.0, 0.0, 0.0, 0.0},
                                   {3.0, -3.0, 1.0, 0.0},
                                   {4.0, -6.0, 4.0, -1.0}};
 
-// ------------------------------------------------------ Chebyshev columns
-// Column transforms along y for a batch of members and fields.  Coefficient
-// side: column m, row n at m*cm + n*cn; value side: column m, row j at
-// m*vm + j*vj (within one field of one member).
-struct YJob {
-  const double2* src;
-  double2* dst;
-  long long src_mstride, dst_mstride;  // per member (elements)
-  long long src_fstride, dst_fstride;  // per field (elements)
-  int src_field[8];
-  int src_field2[8];  // inverse only: >= 0 adds this field to src_field
-  int dst_field[8];
-  int deriv[8];       // inverse only: transform d/dy of the field
-  long long cm, cn;   // coefficient-side strides
-  long long vm, vj;   // value-side strides
-  int K;              // columns
-  int N, M;           // Chebyshev modes, grid intervals (P = 2M)
-  int inverse;        // 1: coefficients -> values (M+1 rows); 0: values -> coefficients (N rows)
-  int C;              // columns per block
-  const int* status;  // skip members with status != 0 (may be null)
-  FftPlan pl;
-};
-
-// Chebyshev derivative in place: b_{n-1} = b_{n+1} + 2 n a_n, b_0 halved.
-__device__ void cheb_deriv_inplace(double2* a, int N) {
-  double2 bnp1 = czero(), bn = czero();
-  double2 acur = a[N - 1];
-  a[N - 1] = czero();
-  for (int n = N - 1; n >= 1; --n) {
-    double2 anext = a[n - 1];
-    double2 bnm1 = cfma(2.0 * n, acur, bnp1);
-    a[n - 1] = bnm1;
-    bnp1 = bn;
-    bn = bnm1;
-    acur = anext;
-  }
-  a[0] = cscl(a[0], 0.5);
-}
-
-__global__ void __launch_bounds__(256) k_ycols(YJob J) {
-  const int b = blockIdx.z;
-  if (J.status && J.status[b]) return;
-  const int f = blockIdx.y;
-  const int C = J.C, K = J.K, N = J.N, M = J.M, P = 2 * J.M;
-  const int c0 = blockIdx.x * C;
-  const int nc = min(C, K - c0);
-  extern __shared__ double2 sm[];
-  double2* A = sm;
-  double2* B = sm + (size_t)C * P;
-  double2* a0s = B + (size_t)C * P;  // [C] a_0, [C] a_M
-  const double2* src = J.src + b * J.src_mstride + J.src_field[f] * J.src_fstride;
-  double2* dst = J.dst + b * J.dst_mstride + J.dst_field[f] * J.dst_fstride;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (J.inverse) {
-    const double2* src2 = (J.src_field2[f] >= 0)
-        ? J.src + b * J.src_mstride + J.src_field2[f] * J.src_fstride : nullptr;
-    for (int i = tid; i < N * C; i += nt) {
-      const int c = i / N, n = i - c * N;
-      double2 v = czero();
-      if (c < nc) {
-        const long long o = (c0 + c) * J.cm + n * J.cn;
-        v = src[o];
-        if (src2) v = cadd(v, src2[o]);
-      }
-      A[c * P + n] = v;
-    }
-    __syncthreads();
-    if (J.deriv[f]) {
-      if (tid < C) cheb_deriv_inplace(A + tid * P, N);
-      __syncthreads();
-    }
-    if (tid < C) {
-      a0s[tid] = A[tid * P];
-      a0s[C + tid] = (N > M) ? A[tid * P + M] : czero();
-    }
-    // even extension: A[n] = a_n (n <= M, zero for n >= N), A[P-n] = a_n
-    for (int i = tid; i < C * P; i += nt) {
-      const int c = i / P, n = i - c * P;
-      if (n >= N && n <= M) A[i] = czero();
-      else if (n > M) { const int r = P - n; A[i] = (r < N) ? A[c * P + r] : czero(); }
-    }
-    __syncthreads();
-    double2* res = fft_lines<-1>(A, B, C, P, J.pl);
-    // f_j = (F_j + a_0 + (-1)^j a_M) / 2
-    for (int i = tid; i < (M + 1) * C; i += nt) {
-      const int j = i / C, c = i - j * C;
-      if (c < nc) {
-        double2 v = cadd(res[c * P + j], a0s[c]);
-        v = (j & 1) ? csub(v, a0s[C + c]) : cadd(v, a0s[C + c]);
-        dst[j * J.vj + (c0 + c) * J.vm] = cscl(v, 0.5);
-      }
-    }
-  } else {
-    for (int i = tid; i < (M + 1) * C; i += nt) {
-      const int j = i / C, c = i - j * C;
-      A[c * P + j] = (c < nc) ? src[j * J.vj + (c0 + c) * J.vm] : czero();
-    }
-    __syncthreads();
-    for (int i = tid; i < C * P; i += nt) {
-      const int c = i / P, j = i - c * P;
-      if (j > M) A[i] = A[c * P + (P - j)];
-    }
-    __syncthreads();
-    double2* res = fft_lines<-1>(A, B, C, P, J.pl);
-    const double inv = 1.0 / M;
-    for (int i = tid; i < N * C; i += nt) {
-      const int c = i / N, n = i - c * N;
-      if (c < nc) {
-        const double s = (n == 0 || n == M) ? 0.5 * inv : inv;
-        dst[(c0 + c) * J.cm + n * J.cn] = cscl(res[c * P + n], s);
-      }
-    }
-  }
-}
-
-struct XJob {
-  const double2* srcC;  // c2r: complex rows
-  const double* srcR;   // r2c: real rows
-  double2* dstC;
-  double* dstR;
-  long long src_mstride, dst_mstride, src_fstride, dst_fstride;
-  int src_rstep, dst_rstep;  // row index multipliers (elements per row = K or n)
-  int nf;                    // fields (<= 6)
-  int K, n;
-  int c2r;
-  const int* status;
-  FftPlan pl;
-};
-
-__global__ void __launch_bounds__(256) k_xrows(XJob J) {
-  const int b = blockIdx.y;
-  if (J.status && J.status[b]) return;
-  const int row = blockIdx.x;
-  const int K = J.K, n = J.n, nf = J.nf, nl = (nf + 1) / 2;
-  extern __shared__ double2 sm[];
-  double2* A = sm;
-  double2* Bb = sm + (size_t)nl * n;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (J.c2r) {
-    const double2* src = J.srcC + b * J.src_mstride + (long long)row * J.src_rstep * K;
-    for (int i = tid; i < nl * n; i += nt) {
-      const int l = i / n, k = i - l * n;
-      const int fa = 2 * l, fb = 2 * l + 1;
-      int kk = -1;
-      bool cj = false;
-      if (k < K) kk = k;
-      else if (k > n - K) { kk = n - k; cj = true; }
-      double2 h = czero();
-      if (kk >= 0) {
-        double2 F = src[fa * J.src_fstride + kk];
-        double2 G = (fb < nf) ? src[fb * J.src_fstride + kk] : czero();
-        if (kk == 0) { F.y = 0.0; G.y = 0.0; }
-        if (cj) { F = cconj(F); G = cconj(G); }
-        h = cadd(F, mul_i(G));
-      }
-      A[i] = h;
-    }
-    __syncthreads();
-    double2* res = fft_lines<+1>(A, Bb, nl, n, J.pl);
-    double* dst = J.dstR + b * J.dst_mstride + (long long)row * J.dst_rstep * n;
-    for (int i = tid; i < nl * n; i += nt) {
-      const int l = i / n, x = i - l * n;
-      const double2 h = res[i];
-      dst[(2 * l) * J.dst_fstride + x] = h.x;
-      if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + x] = h.y;
-    }
-  } else {
-    const double* src = J.srcR + b * J.src_mstride + (long long)row * J.src_rstep * n;
-    for (int i = tid; i < nl * n; i += nt) {
-      const int l = i / n, x = i - l * n;
-      const double fa = src[(2 * l) * J.src_fstride + x];
-      const double fb = (2 * l + 1 < nf) ? src[(2 * l + 1) * J.src_fstride + x] : 0.0;
-      A[i] = make_double2(fa, fb);
-    }
-    __syncthreads();
-    double2* res = fft_lines<-1>(A, Bb, nl, n, J.pl);
-    double2* dst = J.dstC + b * J.dst_mstride + (long long)row * J.dst_rstep * K;
-    const double inv = 1.0 / n;
-    for (int i = tid; i < nl * K; i += nt) {
-      const int l = i / K, k = i - l * K;
-      const double2 hk = res[l * n + k];
-      const double2 hm = cconj(res[l * n + (k == 0 ? 0 : n - k)]);
-      // F = (hk + conj(h_{-k}))/2, G = (hk - conj(h_{-k}))/(2i)
-      const double2 F = cscl(cadd(hk, hm), 0.5 * inv);
-      const double2 d = csub(hk, hm);
-      const double2 G = make_double2(0.5 * inv * d.y, -0.5 * inv * d.x);
-      dst[(2 * l) * J.dst_fstride + k] = F;
-      if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + k] = G;
-    }
-  }
-}
-
-// ------------------------------------------------ fused x pass + products
-// Yp fields: 0 u, 1 v, 2 du/dy, 3 cxx, 4 cxy, 5 cyy, 6 dcxx/dy, 7 dcxy/dy, 8 dcyy/dy.
-// Physical lines (pairs re/im): (u, v) (uy, ux) (vx, cxx) (cxy, cyy)
-// (cxx_y, cxy_y) (cyy_y, cxx_x) (cxy_x, cyy_x).
-__constant__ int c_xsrc[14] = {0, 1, 2, 0, 1, 3, 4, 5, 6, 7, 8, 3, 4, 5};
-__constant__ int c_xik[14] = {0, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 1, 1, 1};
-
-__global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
-  const int b = blockIdx.y;
-  if (g.status[b]) return;
-  const int j = blockIdx.x;
-  const int K = g.K, Mx = g.Mx, rows = g.M + 1;
-  const MemberPrm pr = g.prm[b];
-  extern __shared__ double2 sm[];
-  double2* A = sm;
-  double2* B = sm + 7 * Mx;
-  const double2* Y = g.Yp + (size_t)b * 9 * rows * K + (size_t)j * K;
-  const double kfac = 2.0 * 3.14159265358979323846 / pr.lx;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < 7 * Mx; i += nt) {
-    const int l = i / Mx, k = i - l * Mx;
-    int kk = -1;
-    bool cj = false;
-    if (k < K) kk = k;
-    else if (k > Mx - K) { kk = Mx - k; cj = true; }
-    double2 h = czero();
-    if (kk >= 0) {
-      const int fa = 2 * l, fb = 2 * l + 1;
-      double2 F = Y[(size_t)c_xsrc[fa] * rows * K + kk];
-      double2 G = Y[(size_t)c_xsrc[fb] * rows * K + kk];
-      if (kk == 0) { F.y = 0.0; G.y = 0.0; }
-      const double km = kfac * kk;
-      if (c_xik[fa]) F = cscl(mul_i(F), km);
-      if (c_xik[fb]) G = cscl(mul_i(G), km);
-      if (cj) { F = cconj(F); G = cconj(G); }
-      h = cadd(F, mul_i(G));
-    }
-    A[i] = h;
-  }
-  __syncthreads();
-  double2* res = fft_lines<+1>(A, B, 7, Mx, g.plMx);
-  double2* oth = (res == A) ? B : A;
-  const double eps = pr.eps, iwi = pr.inv_wi;
-  for (int x = tid; x < Mx; x += nt) {
-    const double2 h0 = res[x], h1 = res[Mx + x], h2 = res[2 * Mx + x], h3 = res[3 * Mx + x];
-    const double2 h4 = res[4 * Mx + x], h5 = res[5 * Mx + x], h6 = res[6 * Mx + x];
-    const double u = h0.x, v = h0.y, uy = h1.x, ux = h1.y, vx = h2.x, cxx = h2.y;
-    const double cxy = h3.x, cyy = h3.y, cxx_y = h4.x, cxy_y = h4.y, cyy_y = h5.x;
-    const double cxx_x = h5.y, cxy_x = h6.x, cyy_x = h6.y;
-    // Eq. 1: L_ij = du_i/dx_j (L_yy = -ux by continuity); relaxation factor
-    // f = 1 + eps Tr(c - I) with c_zz = 1.
-    const double rw = (1.0 + eps * (cxx + cyy - 2.0)) * iwi;
-    const double ncxx = -(u * cxx_x + v * cxx_y) + 2.0 * (ux * cxx + uy * cxy) - (cxx - 1.0) * rw;
-    const double ncxy = -(u * cxy_x + v * cxy_y) + uy * cyy + vx * cxx - cxy * rw;
-    const double ncyy = -(u * cyy_x + v * cyy_y) + 2.0 * (vx * cxy - ux * cyy) - (cyy - 1.0) * rw;
-    // Eq. 2 advection
-    const double nu_ = -(u * ux + v * uy);
-    const double nv_ = -(u * vx - v * ux);
-    oth[x] = make_double2(ncxx, ncxy);
-    oth[Mx + x] = make_double2(ncyy, nu_);
-    oth[2 * Mx + x] = make_double2(nv_, 0.0);
-  }
-  __syncthreads();
-  double2* r2 = fft_lines<-1>(oth, res, 3, Mx, g.plMx);
-  double2* Z = g.Zp + (size_t)b * 5 * rows * K + (size_t)j * K;
-  const double inv = 1.0 / Mx;
-  for (int i = tid; i < 3 * K; i += nt) {
-    const int l = i / K, k = i - l * K;
-    const double2 hk = r2[l * Mx + k];
-    const double2 hm = cconj(r2[l * Mx + (k == 0 ? 0 : Mx - k)]);
-    const double2 F = cscl(cadd(hk, hm), 0.5 * inv);
-    const double2 d = csub(hk, hm);
-    const double2 G = make_double2(0.5 * inv * d.y, -0.5 * inv * d.x);
-    Z[(size_t)(2 * l) * rows * K + k] = F;
-    if (l < 2) Z[(size_t)(2 * l + 1) * rows * K + k] = G;
-  }
-}
-
 // ------------------------------------------- warp-cooperative recurrences
 // FP64 runs at a few lanes per clock per SM on this part, so a warp FP64
 // instruction costs the same pipe time whether 1 or 32 lanes are active.
@@ -607,6 +337,356 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
 }
 
 // ---------------------------------------------- per-mode spectral stage
+// ------------------------------------------------------ Chebyshev columns
+// Column transforms along y for a batch of members and fields.  Coefficient
+// side: column m, row n at m*cm + n*cn; value side: column m, row j at
+// m*vm + j*vj (within one field of one member).
+struct YJob {
+  const double2* src;
+  double2* dst;
+  long long src_mstride, dst_mstride;  // per member (elements)
+  long long src_fstride, dst_fstride;  // per field (elements)
+  int src_field[8];
+  int src_field2[8];  // inverse only: >= 0 adds this field to src_field
+  int dst_field[8];
+  int deriv[8];       // inverse only: transform d/dy of the field
+  long long cm, cn;   // coefficient-side strides
+  long long vm, vj;   // value-side strides
+  int K;              // columns
+  int N, M;           // Chebyshev modes, grid intervals (P = 2M)
+  int inverse;        // 1: coefficients -> values; 0: values -> coefficients (N rows)
+  int gauss;          // 0: M+1 Gauss-Lobatto points (DCT-I, FFT length 2M);
+                      // 1: M Gauss points (DCT-II/III, FFT length M, M even)
+  const double2* tw4; // gauss: tw4[k] = exp(-i pi k / (2M)), k < M
+  int C;              // columns per block
+  const int* status;  // skip members with status != 0 (may be null)
+  FftPlan pl;
+};
+
+// Values at the M Gauss points y_j = cos(pi (2j+1)/(2M)) from coefficients
+// (DCT-III) and back (DCT-II), each as one complex FFT of length M: the
+// output (input) order is permuted v_n = f_{2n}, v_{M-1-n} = f_{2n+1}, and a
+// quarter-period twiddle exp(-+ i pi k/(2M)) maps between the two (Makhoul's
+// construction; the real and imaginary parts of a column ride in one FFT).
+__device__ void ycols_gauss(const YJob& J, const double2* src, const double2* src2, double2* dst,
+                            double2* A, double2* B, int c0, int nc) {
+  const int C = J.C, N = J.N, Mg = J.M;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int f = blockIdx.y;
+  if (J.inverse) {
+    for (int i = tid; i < Mg * C; i += nt) {
+      const int c = i / Mg, n = i - c * Mg;
+      double2 v = czero();
+      if (c < nc && n < N) {
+        const long long o = (c0 + c) * J.cm + n * J.cn;
+        v = src[o];
+        if (src2) v = cadd(v, src2[o]);
+      }
+      A[i] = v;
+    }
+    __syncthreads();
+    if (J.deriv[f]) {
+      for (int c = tid >> 5; c < C; c += (nt >> 5)) warp_cheb_deriv(A + c * Mg, B + c * Mg, N);
+      __syncthreads();
+      for (int i = tid; i < N * C; i += nt) {
+        const int c = i / N, n = i - c * N;
+        A[c * Mg + n] = B[c * Mg + n];
+      }
+      __syncthreads();
+    }
+    // V_0 = a_0, V_k = (1/2) exp(+i pi k/(2M)) (a_k - i a_{M-k})
+    for (int i = tid; i < Mg * C; i += nt) {
+      const int c = i / Mg, k = i - c * Mg;
+      const double2 ak = A[i];
+      double2 V;
+      if (k == 0) {
+        V = ak;
+      } else {
+        const double2 amk = A[c * Mg + Mg - k];
+        const double2 w = cconj(__ldg(&J.tw4[k]));
+        V = cscl(cmul(w, csub(ak, mul_i(amk))), 0.5);
+      }
+      B[i] = V;
+    }
+    __syncthreads();
+    double2* res = fft_lines<+1>(B, A, C, Mg, J.pl);
+    for (int i = tid; i < Mg * C; i += nt) {
+      const int j = i / C, c = i - j * C;
+      if (c < nc) {
+        const int pos = (j & 1) ? (Mg - 1 - (j >> 1)) : (j >> 1);
+        dst[j * J.vj + (c0 + c) * J.vm] = res[c * Mg + pos];
+      }
+    }
+  } else {
+    for (int i = tid; i < Mg * C; i += nt) {
+      const int j = i / C, c = i - j * C;
+      const int pos = (j & 1) ? (Mg - 1 - (j >> 1)) : (j >> 1);
+      A[c * Mg + pos] = (c < nc) ? src[j * J.vj + (c0 + c) * J.vm] : czero();
+    }
+    __syncthreads();
+    double2* res = fft_lines<-1>(A, B, C, Mg, J.pl);
+    const double s0 = 1.0 / Mg, s1 = 2.0 / Mg;
+    for (int i = tid; i < N * C; i += nt) {
+      const int c = i / N, k = i - c * N;
+      if (c < nc) {
+        const double2 Vk = res[c * Mg + k];
+        const double2 Vm = cconj(res[c * Mg + (k == 0 ? 0 : Mg - k)]);
+        const double2 Vr = cscl(cadd(Vk, Vm), 0.5);
+        const double2 d = csub(Vk, Vm);
+        const double2 Vi = make_double2(0.5 * d.y, -0.5 * d.x);
+        const double2 w = __ldg(&J.tw4[k]);
+        const double xr = w.x * Vr.x - w.y * Vr.y;
+        const double xi = w.x * Vi.x - w.y * Vi.y;
+        const double sc = (k == 0) ? s0 : s1;
+        dst[(c0 + c) * J.cm + k * J.cn] = make_double2(sc * xr, sc * xi);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ycols(YJob J) {
+  const int b = blockIdx.z;
+  if (J.status && J.status[b]) return;
+  const int f = blockIdx.y;
+  // FFT length per column: M on the Gauss grid, 2M (even extension) on the
+  // Gauss-Lobatto grid; shared memory holds 2 C lines of it (+ 2 C scalars)
+  const int C = J.C, K = J.K, N = J.N, M = J.M, P = J.gauss ? J.M : 2 * J.M;
+  const int c0 = blockIdx.x * C;
+  const int nc = min(C, K - c0);
+  extern __shared__ double2 sm[];
+  double2* A = sm;
+  double2* B = sm + (size_t)C * P;
+  double2* a0s = B + (size_t)C * P;  // [C] a_0, [C] a_M (Gauss-Lobatto path)
+  const double2* src = J.src + b * J.src_mstride + J.src_field[f] * J.src_fstride;
+  double2* dst = J.dst + b * J.dst_mstride + J.dst_field[f] * J.dst_fstride;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double2* src2 = (J.inverse && J.src_field2[f] >= 0)
+      ? J.src + b * J.src_mstride + J.src_field2[f] * J.src_fstride : nullptr;
+  if (J.gauss) {
+    ycols_gauss(J, src, src2, dst, A, B, c0, nc);
+    return;
+  }
+  if (J.inverse) {
+    for (int i = tid; i < N * C; i += nt) {
+      const int c = i / N, n = i - c * N;
+      double2 v = czero();
+      if (c < nc) {
+        const long long o = (c0 + c) * J.cm + n * J.cn;
+        v = src[o];
+        if (src2) v = cadd(v, src2[o]);
+      }
+      A[c * P + n] = v;
+    }
+    __syncthreads();
+    if (J.deriv[f]) {
+      // d/dy of each column by one warp (suffix sums), via the ping-pong buffer
+      for (int c = tid >> 5; c < C; c += (nt >> 5)) warp_cheb_deriv(A + c * P, B + c * P, N);
+      __syncthreads();
+      for (int i = tid; i < N * C; i += nt) {
+        const int c = i / N, n = i - c * N;
+        A[c * P + n] = B[c * P + n];
+      }
+      __syncthreads();
+    }
+    if (tid < C) {
+      a0s[tid] = A[tid * P];
+      a0s[C + tid] = (N > M) ? A[tid * P + M] : czero();
+    }
+    // even extension: A[n] = a_n (n <= M, zero for n >= N), A[P-n] = a_n
+    for (int i = tid; i < C * P; i += nt) {
+      const int c = i / P, n = i - c * P;
+      if (n >= N && n <= M) A[i] = czero();
+      else if (n > M) { const int r = P - n; A[i] = (r < N) ? A[c * P + r] : czero(); }
+    }
+    __syncthreads();
+    double2* res = fft_lines<-1>(A, B, C, P, J.pl);
+    // f_j = (F_j + a_0 + (-1)^j a_M) / 2
+    for (int i = tid; i < (M + 1) * C; i += nt) {
+      const int j = i / C, c = i - j * C;
+      if (c < nc) {
+        double2 v = cadd(res[c * P + j], a0s[c]);
+        v = (j & 1) ? csub(v, a0s[C + c]) : cadd(v, a0s[C + c]);
+        dst[j * J.vj + (c0 + c) * J.vm] = cscl(v, 0.5);
+      }
+    }
+  } else {
+    for (int i = tid; i < (M + 1) * C; i += nt) {
+      const int j = i / C, c = i - j * C;
+      A[c * P + j] = (c < nc) ? src[j * J.vj + (c0 + c) * J.vm] : czero();
+    }
+    __syncthreads();
+    for (int i = tid; i < C * P; i += nt) {
+      const int c = i / P, j = i - c * P;
+      if (j > M) A[i] = A[c * P + (P - j)];
+    }
+    __syncthreads();
+    double2* res = fft_lines<-1>(A, B, C, P, J.pl);
+    const double inv = 1.0 / M;
+    for (int i = tid; i < N * C; i += nt) {
+      const int c = i / N, n = i - c * N;
+      if (c < nc) {
+        const double s = (n == 0 || n == M) ? 0.5 * inv : inv;
+        dst[(c0 + c) * J.cm + n * J.cn] = cscl(res[c * P + n], s);
+      }
+    }
+  }
+}
+
+struct XJob {
+  const double2* srcC;  // c2r: complex rows
+  const double* srcR;   // r2c: real rows
+  double2* dstC;
+  double* dstR;
+  long long src_mstride, dst_mstride, src_fstride, dst_fstride;
+  int src_rstep, dst_rstep;  // row index multipliers (elements per row = K or n)
+  int nf;                    // fields (<= 6)
+  int K, n;
+  int c2r;
+  const int* status;
+  FftPlan pl;
+};
+
+__global__ void __launch_bounds__(256) k_xrows(XJob J) {
+  const int b = blockIdx.y;
+  if (J.status && J.status[b]) return;
+  const int row = blockIdx.x;
+  const int K = J.K, n = J.n, nf = J.nf, nl = (nf + 1) / 2;
+  extern __shared__ double2 sm[];
+  double2* A = sm;
+  double2* Bb = sm + (size_t)nl * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (J.c2r) {
+    const double2* src = J.srcC + b * J.src_mstride + (long long)row * J.src_rstep * K;
+    for (int i = tid; i < nl * n; i += nt) {
+      const int l = i / n, k = i - l * n;
+      const int fa = 2 * l, fb = 2 * l + 1;
+      int kk = -1;
+      bool cj = false;
+      if (k < K) kk = k;
+      else if (k > n - K) { kk = n - k; cj = true; }
+      double2 h = czero();
+      if (kk >= 0) {
+        double2 F = src[fa * J.src_fstride + kk];
+        double2 G = (fb < nf) ? src[fb * J.src_fstride + kk] : czero();
+        if (kk == 0) { F.y = 0.0; G.y = 0.0; }
+        if (cj) { F = cconj(F); G = cconj(G); }
+        h = cadd(F, mul_i(G));
+      }
+      A[i] = h;
+    }
+    __syncthreads();
+    double2* res = fft_lines<+1>(A, Bb, nl, n, J.pl);
+    double* dst = J.dstR + b * J.dst_mstride + (long long)row * J.dst_rstep * n;
+    for (int i = tid; i < nl * n; i += nt) {
+      const int l = i / n, x = i - l * n;
+      const double2 h = res[i];
+      dst[(2 * l) * J.dst_fstride + x] = h.x;
+      if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + x] = h.y;
+    }
+  } else {
+    const double* src = J.srcR + b * J.src_mstride + (long long)row * J.src_rstep * n;
+    for (int i = tid; i < nl * n; i += nt) {
+      const int l = i / n, x = i - l * n;
+      const double fa = src[(2 * l) * J.src_fstride + x];
+      const double fb = (2 * l + 1 < nf) ? src[(2 * l + 1) * J.src_fstride + x] : 0.0;
+      A[i] = make_double2(fa, fb);
+    }
+    __syncthreads();
+    double2* res = fft_lines<-1>(A, Bb, nl, n, J.pl);
+    double2* dst = J.dstC + b * J.dst_mstride + (long long)row * J.dst_rstep * K;
+    const double inv = 1.0 / n;
+    for (int i = tid; i < nl * K; i += nt) {
+      const int l = i / K, k = i - l * K;
+      const double2 hk = res[l * n + k];
+      const double2 hm = cconj(res[l * n + (k == 0 ? 0 : n - k)]);
+      // F = (hk + conj(h_{-k}))/2, G = (hk - conj(h_{-k}))/(2i)
+      const double2 F = cscl(cadd(hk, hm), 0.5 * inv);
+      const double2 d = csub(hk, hm);
+      const double2 G = make_double2(0.5 * inv * d.y, -0.5 * inv * d.x);
+      dst[(2 * l) * J.dst_fstride + k] = F;
+      if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + k] = G;
+    }
+  }
+}
+
+// ------------------------------------------------ fused x pass + products
+// Yp fields: 0 u, 1 v, 2 du/dy, 3 cxx, 4 cxy, 5 cyy, 6 dcxx/dy, 7 dcxy/dy, 8 dcyy/dy.
+// Physical lines (pairs re/im): (u, v) (uy, ux) (vx, cxx) (cxy, cyy)
+// (cxx_y, cxy_y) (cyy_y, cxx_x) (cxy_x, cyy_x).
+__constant__ int c_xsrc[14] = {0, 1, 2, 0, 1, 3, 4, 5, 6, 7, 8, 3, 4, 5};
+__constant__ int c_xik[14] = {0, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 1, 1, 1};
+
+__global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
+  const int b = blockIdx.y;
+  if (g.status[b]) return;
+  const int j = blockIdx.x;
+  const int K = g.K, Mx = g.Mx, rows = g.M;
+  const MemberPrm pr = g.prm[b];
+  extern __shared__ double2 sm[];
+  double2* A = sm;
+  double2* B = sm + 7 * Mx;
+  const double2* Y = g.Yp + (size_t)b * 9 * rows * K + (size_t)j * K;
+  const double kfac = 2.0 * 3.14159265358979323846 / pr.lx;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < 7 * Mx; i += nt) {
+    const int l = i / Mx, k = i - l * Mx;
+    int kk = -1;
+    bool cj = false;
+    if (k < K) kk = k;
+    else if (k > Mx - K) { kk = Mx - k; cj = true; }
+    double2 h = czero();
+    if (kk >= 0) {
+      const int fa = 2 * l, fb = 2 * l + 1;
+      double2 F = Y[(size_t)c_xsrc[fa] * rows * K + kk];
+      double2 G = Y[(size_t)c_xsrc[fb] * rows * K + kk];
+      if (kk == 0) { F.y = 0.0; G.y = 0.0; }
+      const double km = kfac * kk;
+      if (c_xik[fa]) F = cscl(mul_i(F), km);
+      if (c_xik[fb]) G = cscl(mul_i(G), km);
+      if (cj) { F = cconj(F); G = cconj(G); }
+      h = cadd(F, mul_i(G));
+    }
+    A[i] = h;
+  }
+  __syncthreads();
+  double2* res = fft_lines<+1>(A, B, 7, Mx, g.plMx);
+  double2* oth = (res == A) ? B : A;
+  const double eps = pr.eps, iwi = pr.inv_wi;
+  for (int x = tid; x < Mx; x += nt) {
+    const double2 h0 = res[x], h1 = res[Mx + x], h2 = res[2 * Mx + x], h3 = res[3 * Mx + x];
+    const double2 h4 = res[4 * Mx + x], h5 = res[5 * Mx + x], h6 = res[6 * Mx + x];
+    const double u = h0.x, v = h0.y, uy = h1.x, ux = h1.y, vx = h2.x, cxx = h2.y;
+    const double cxy = h3.x, cyy = h3.y, cxx_y = h4.x, cxy_y = h4.y, cyy_y = h5.x;
+    const double cxx_x = h5.y, cxy_x = h6.x, cyy_x = h6.y;
+    // Eq. 1: L_ij = du_i/dx_j (L_yy = -ux by continuity); relaxation factor
+    // f = 1 + eps Tr(c - I) with c_zz = 1.
+    const double rw = (1.0 + eps * (cxx + cyy - 2.0)) * iwi;
+    const double ncxx = -(u * cxx_x + v * cxx_y) + 2.0 * (ux * cxx + uy * cxy) - (cxx - 1.0) * rw;
+    const double ncxy = -(u * cxy_x + v * cxy_y) + uy * cyy + vx * cxx - cxy * rw;
+    const double ncyy = -(u * cyy_x + v * cyy_y) + 2.0 * (vx * cxy - ux * cyy) - (cyy - 1.0) * rw;
+    // Eq. 2 advection
+    const double nu_ = -(u * ux + v * uy);
+    const double nv_ = -(u * vx - v * ux);
+    oth[x] = make_double2(ncxx, ncxy);
+    oth[Mx + x] = make_double2(ncyy, nu_);
+    oth[2 * Mx + x] = make_double2(nv_, 0.0);
+  }
+  __syncthreads();
+  double2* r2 = fft_lines<-1>(oth, res, 3, Mx, g.plMx);
+  double2* Z = g.Zp + (size_t)b * 5 * rows * K + (size_t)j * K;
+  const double inv = 1.0 / Mx;
+  for (int i = tid; i < 3 * K; i += nt) {
+    const int l = i / K, k = i - l * K;
+    const double2 hk = r2[l * Mx + k];
+    const double2 hm = cconj(r2[l * Mx + (k == 0 ? 0 : Mx - k)]);
+    const double2 F = cscl(cadd(hk, hm), 0.5 * inv);
+    const double2 d = csub(hk, hm);
+    const double2 G = make_double2(0.5 * inv * d.y, -0.5 * inv * d.x);
+    Z[(size_t)(2 * l) * rows * K + k] = F;
+    if (l < 2) Z[(size_t)(2 * l + 1) * rows * K + k] = G;
+  }
+}
+
 // The tau system solved per (mode, system, parity) by warp_qt_solve:
 //   (alpha - beta D^2) a = rsign * R   on tau rows n <= N-3,
 //   sum_{n = p mod 2} a_n = bcfac * sum_{n = p mod 2} rsign * R_n,
@@ -840,9 +920,9 @@ __device__ double2 warp_sum2(double2 v) {
 // Diagnostics of one step, per member, as tiles (kTiles blocks per member)
 // with partial results in part[member][tile][kPart] reduced in a fixed
 // order (deterministic):
-//   DY: (c_xx + c_yy, u, v) on the diagnostic y grid (2N-1 Gauss-Lobatto
-//       points, Fourier modes); DV: c_xx + c_yy on the unpadded grid.
-//   E = <|u|^2/2> by Clenshaw-Curtis in y (exact for degree 2N-2) and
+//   DY: (u, v) on Me >= 2N-1 Gauss points (Fourier modes); DT, DV:
+//       c_xx + c_yy on the unpadded Gauss-Lobatto rows (modes, then values).
+//   E = <|u|^2/2> by Fejer's first rule in y (exact for degree 2N-2) and
 //   Parseval in x; extrema of Tr c = c_xx + c_yy + 1; a non-finite test of
 //   the state on the bit patterns; then the counts of Tr c < 3, < 0 and the
 //   tie bands |Tr c - 3|, |Tr c| <= tau = 1e-9 max|Tr c|.
@@ -880,17 +960,17 @@ __device__ Red5 block_red5(Red5 r) {
 __global__ void __launch_bounds__(256) k_diag_part(GroupDev g) {
   const int b = blockIdx.y, tile = blockIdx.x;
   if (g.status[b]) return;
-  const int K = g.K, N = g.N, nx = g.nx, Je = 2 * N - 1;
+  const int K = g.K, N = g.N, nx = g.nx, Je = g.Me;
   const size_t NK = (size_t)N * K;
-  const double2* DY = g.DY + (size_t)b * 3 * Je * K;
+  const double2* DY = g.DY + (size_t)b * 2 * Je * K;
   Red5 r{0.0, 1e308, -1e308, 0.0, 0};
-  // energy: DY fields 1 (u) and 2 (v)
+  // energy: DY fields 0 (u) and 1 (v) on the Me Gauss points (Fejer weights)
   {
     const long long tot = (long long)Je * K, per = (tot + kTiles - 1) / kTiles;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const int j = (int)(i / K), m = (int)(i - (long long)j * K);
-      const double2 uu = DY[(size_t)Je * K + i], vv = DY[(size_t)2 * Je * K + i];
+      const double2 uu = DY[i], vv = DY[(size_t)Je * K + i];
       const double w = (m == 0 ? 1.0 : 2.0) * g.ccw[j];
       r.s += w * (uu.x * uu.x + uu.y * uu.y + vv.x * vv.x + vv.y * vv.y);
     }
@@ -1094,8 +1174,11 @@ inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) /
 
 // Spectral coefficients (internal layout [member][field][m][n]) <-> values on
 // a y grid stored [member][field][j][m].
-YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl) {
+YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl,
+               const double2* tw4 = nullptr) {
   YJob J{};
+  J.gauss = tw4 ? 1 : 0;
+  J.tw4 = tw4;
   J.K = g.K;
   J.N = g.N;
   J.M = M;
@@ -1139,22 +1222,22 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
 
 // Stage s of one step for one group (see ptt.h: PTT_NSTAGES).
 cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl) {
-  const int rows = g.M + 1;
+  const int rows = g.M;
   const size_t NK = (size_t)g.N * g.K;
   int n = 0;
   switch (stage) {
-    case 0: {  // inverse y: 9 fields on the padded grid (two launches: 8 + 1)
-      YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP);
+    case 0: {  // inverse y: 9 fields on the padded Gauss grid (two launches: 8 + 1)
+      YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4P);
       J.src = g.X; J.dst = g.Yp;
       J.src_mstride = 5 * NK; J.dst_mstride = 9LL * rows * g.K;
       J.src_fstride = NK; J.dst_fstride = (long long)rows * g.K;
       const int sf[9] = {0, 1, 0, 2, 3, 4, 2, 3, 4};
       const int dv[9] = {0, 0, 1, 0, 0, 0, 1, 1, 1};
       for (int i = 0; i < 8; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = dv[i]; }
-      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 8, g.nb), 256, smem_ycols(g.Ccol, g.P), st>>>(J);
+      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 8, g.nb), 256, smem_ycols(g.Ccol, g.M), st>>>(J);
       YJob J2 = J;
       J2.src_field[0] = sf[8]; J2.dst_field[0] = 8; J2.deriv[0] = dv[8];
-      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 1, g.nb), 256, smem_ycols(g.Ccol, g.P), st>>>(J2);
+      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 1, g.nb), 256, smem_ycols(g.Ccol, g.M), st>>>(J2);
       n = 2;
       break;
     }
@@ -1163,12 +1246,12 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       n = 1;
       break;
     case 2: {  // forward y of the 5 explicit fields
-      YJob F = make_yjob(g, false, g.M, g.Ccol, g.plP);
+      YJob F = make_yjob(g, false, g.M, g.Ccol, g.plP, g.tw4P);
       F.src = g.Zp; F.dst = g.NR;
       F.src_mstride = 5LL * rows * g.K; F.dst_mstride = 5 * NK;
       F.src_fstride = (long long)rows * g.K; F.dst_fstride = NK;
       for (int i = 0; i < 5; ++i) { F.src_field[i] = i; F.dst_field[i] = i; F.deriv[i] = 0; }
-      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, smem_ycols(g.Ccol, g.P), st>>>(F);
+      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, smem_ycols(g.Ccol, g.M), st>>>(F);
       n = 1;
       break;
     }
@@ -1178,26 +1261,31 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       n = 2;
       break;
     case 4: {  // diagnostics
-      const int Je = 2 * g.N - 1;
-      YJob J = make_yjob(g, true, 2 * (g.N - 1), g.CcolE, g.plPe);
+      // c_xx + c_yy on the unpadded Gauss-Lobatto rows (DCT-I), then x
+      YJob T = make_yjob(g, true, g.N - 1, g.CcolU, g.plPu);
+      T.src = g.X; T.dst = g.DT;
+      T.src_mstride = 5 * NK; T.dst_mstride = (long long)NK;
+      T.src_fstride = NK; T.dst_fstride = 0;
+      T.src_field[0] = 2; T.src_field2[0] = 4; T.dst_field[0] = 0; T.deriv[0] = 0;
+      k_ycols<<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu), st>>>(T);
+      // u, v on the Me Gauss points of the energy quadrature
+      YJob J = make_yjob(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
       J.src = g.X; J.dst = g.DY;
-      J.src_mstride = 5 * NK; J.dst_mstride = 3LL * Je * g.K;
-      J.src_fstride = NK; J.dst_fstride = (long long)Je * g.K;
-      const int sf[3] = {2, 0, 1};   // c_xx (+ c_yy), u, v
-      for (int i = 0; i < 3; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = 0; }
-      J.src_field2[0] = 4;
-      k_ycols<<<dim3(cdiv(g.K, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Pe), st>>>(J);
+      J.src_mstride = 5 * NK; J.dst_mstride = 2LL * g.Me * g.K;
+      J.src_fstride = NK; J.dst_fstride = (long long)g.Me * g.K;
+      for (int i = 0; i < 2; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
+      k_ycols<<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me), st>>>(J);
       XJob X{};
-      X.srcC = g.DY; X.dstR = g.DV;
-      X.src_mstride = 3LL * Je * g.K; X.dst_mstride = (long long)g.N * g.nx;
-      X.src_fstride = (long long)Je * g.K; X.dst_fstride = (long long)g.N * g.nx;
-      X.src_rstep = 2; X.dst_rstep = 1;
+      X.srcC = g.DT; X.dstR = g.DV;
+      X.src_mstride = (long long)NK; X.dst_mstride = (long long)g.N * g.nx;
+      X.src_fstride = 0; X.dst_fstride = 0;
+      X.src_rstep = 1; X.dst_rstep = 1;
       X.nf = 1; X.K = g.K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
       k_xrows<<<dim3(g.N, g.nb), 256, smem_xrows(1, g.nx), st>>>(X);
       k_diag_part<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
       k_diag_count<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
       k_diag_final<<<g.nb, 256, smem_xrows(3, g.nx), st>>>(g);
-      n = 5;
+      n = 6;
       break;
     }
     default:
@@ -1249,24 +1337,24 @@ cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st) {
   X.nf = 5; X.K = g.K; X.n = g.nx; X.c2r = 0; X.status = nullptr; X.pl = g.plNx;
   k_xrows<<<dim3(g.N, 1), 256, smem_xrows(3, g.nx), st>>>(X);
   // y analysis (DCT-I on the N Gauss-Lobatto points) -> X of member b
-  YJob J = make_yjob(g, false, g.N - 1, g.CcolE, g.plPu);
+  YJob J = make_yjob(g, false, g.N - 1, g.CcolU, g.plPu);
   J.status = nullptr;
   J.src = g.stageS; J.dst = g.X + (size_t)b * 5 * NK;
   J.src_fstride = NK; J.dst_fstride = NK;
   for (int i = 0; i < 5; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<<<dim3(cdiv(g.K, g.CcolE), 5, 1), 256, smem_ycols(g.CcolE, g.Pu), st>>>(J);
+  k_ycols<<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu), st>>>(J);
   k_reset<<<1, 32, 0, st>>>(g, b);
   return cudaGetLastError();
 }
 
 cudaError_t launch_state_to_phys(const GroupDev& g, int b, cudaStream_t st) {
   const size_t NK = (size_t)g.N * g.K;
-  YJob J = make_yjob(g, true, g.N - 1, g.CcolE, g.plPu);
+  YJob J = make_yjob(g, true, g.N - 1, g.CcolU, g.plPu);
   J.status = nullptr;
   J.src = g.X + (size_t)b * 5 * NK; J.dst = g.stageS;
   J.src_fstride = NK; J.dst_fstride = NK;
   for (int i = 0; i < 5; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<<<dim3(cdiv(g.K, g.CcolE), 5, 1), 256, smem_ycols(g.CcolE, g.Pu), st>>>(J);
+  k_ycols<<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu), st>>>(J);
   XJob X{};
   X.srcC = g.stageS; X.dstR = g.stage;
   X.src_fstride = NK; X.dst_fstride = (long long)g.N * g.nx;

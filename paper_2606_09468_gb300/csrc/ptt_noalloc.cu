@@ -72,10 +72,10 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   if (((uintptr_t)d_spec & 15) || ((uintptr_t)d_out & 15) || d_spec == d_out) return PTT_EINVAL;
   ptt::GroupDev g{};
   ptt::MemberPrm prm{};
-  std::vector<double2> twP, twMx;
-  int s = ptt::shape_plan(*p, g, twP, twMx, prm);
+  std::vector<double2> twP, twMx, tw4;
+  int s = ptt::shape_plan(*p, g, twP, twMx, tw4, prm);
   if (s) return s;
-  const size_t rows = (size_t)g.M + 1, K = g.K, NK = (size_t)g.N * K;
+  const size_t rows = (size_t)g.M, K = g.K, NK = (size_t)g.N * K;
   // layout of the scratch array
   size_t off = 0;
   const size_t oX = off; off = align256(off + 5 * NK * sizeof(double2));
@@ -85,6 +85,7 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   const size_t oZp = off; off = align256(off + 5 * rows * K * sizeof(double2));
   const size_t oTP = off; off = align256(off + twP.size() * sizeof(double2));
   const size_t oTM = off; off = align256(off + twMx.size() * sizeof(double2));
+  const size_t oT4 = off; off = align256(off + tw4.size() * sizeof(double2));
   const size_t oPr = off; off = align256(off + sizeof(ptt::MemberPrm));
   const size_t oSt = off; off = align256(off + sizeof(int));
   const size_t oCn = off; off = align256(off + sizeof(long long));
@@ -109,6 +110,7 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   g.Zp = (double2*)(b + oZp);
   g.plP.tw = (const double2*)(b + oTP);
   g.plMx.tw = (const double2*)(b + oTM);
+  g.tw4P = (const double2*)(b + oT4);
   g.prm = (ptt::MemberPrm*)(b + oPr);
   g.status = (int*)(b + oSt);
   g.count = (long long*)(b + oCn);
@@ -120,6 +122,8 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
       (e = cudaMemcpyAsync(b + oTP, twP.data(), twP.size() * sizeof(double2),
                            cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(b + oTM, twMx.data(), twMx.size() * sizeof(double2),
+                           cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(b + oT4, tw4.data(), tw4.size() * sizeof(double2),
                            cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(b + oPr, &prm, sizeof(prm), cudaMemcpyHostToDevice, st)) ||
       (e = ptt::launch_transpose((const double2*)d_spec, g.X, 5, g.N, g.K, st)) ||
