@@ -203,7 +203,7 @@ PTT_NSTAGES = 5
 STAGE_NAMES = ("cheb_inverse", "x_fused_products", "cheb_forward", "spectral_sbdf_solve",
                "diagnostics")
 STAGE_KERNELS = ("k_ycols", "k_xfused", "k_ycols", "k_spec+k_tick",
-                 "k_ycols+k_xrows+k_diag_part+k_diag_count+k_diag_final")
+                 "k_ycols+k_xrows+k_diag_part+k_diag_count+k_diag_mid+k_diag_final")
 
 
 def ptt_time_stages(ctx, nsteps):

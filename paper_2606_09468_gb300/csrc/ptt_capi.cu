@@ -1,5 +1,6 @@
 // Host side of the sPTT channel library: parameter checks, plans, operator
 // tables, workspace carving, initial condition, CUDA-graph step, C ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -288,6 +289,15 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     GroupDev& d = g.d;
     const int nb = (int)g.members.size();
     d.nb = nb;
+    // columns per block: fit the shared-memory target, but leave at least
+    // about two blocks per SM (152 SMs) for the column counts of each pass
+    auto cap = [&](int c, int nfields) {
+      const int want = (int)((long long)d.K * nfields * nb / 304);
+      return std::max(1, std::min(c, want));
+    };
+    d.Ccol = cap(d.Ccol, 9);
+    d.CcolE = cap(d.CcolE, 2);
+    d.CcolU = cap(d.CcolU, 1);
     const size_t NK = (size_t)d.N * d.K, rows = (size_t)d.M, Je = (size_t)d.Me;
     d.prm = cv.take<MemberPrm>(nb);
     d.status = cv.take<int>(nb);
@@ -309,7 +319,7 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.DT = cv.take<double2>((size_t)nb * NK);
     d.DV = cv.take<double>((size_t)nb * d.N * d.nx);
     d.part = cv.take<double>((size_t)nb * kTiles * kPart);
-    d.DM = nullptr;
+    d.DM = cv.take<double2>((size_t)nb * 4 * d.K);
     d.ring = cv.take<ptt_diag>((size_t)nb * kRing);
     d.stage = cv.take<double>((size_t)5 * d.N * d.nx);
     d.stageS = cv.take<double2>((size_t)5 * NK);
@@ -845,7 +855,7 @@ int ptt_time_stages(ptt_ctx* c, int32_t nsteps, double* ms) {
 int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) {
   if (!c || !flops || !bytes || !launches) return PTT_EINVAL;
   auto fft = [](double n) { return 5.0 * n * std::log2(n); };
-  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 2, 6};
+  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 2, 7};
   for (int s = 0; s < PTT_NSTAGES; ++s) { flops[s] = 0.0; bytes[s] = 0.0; launches[s] = 0; }
   for (Group& g : c->groups) {
     const GroupDev& d = g.d;

@@ -57,7 +57,7 @@ struct GroupDev {
   double2* DT;       // [nb][N][K]  cxx+cyy on the unpadded y rows, Fourier modes
   double* DV;        // [nb][N][nx]  cxx+cyy on the unpadded grid
   double* part;      // [nb][kTiles][kPart]  partial reductions
-  double2* DM;       // [nb][6][K]  mid-plane spectra
+  double2* DM;       // [nb][4][K]  mid-plane Chebyshev sums per Fourier mode
   ptt_diag* ring;    // [nb][kRing]
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
   double2* stageS;   // [5][N][K]  values on the unpadded y grid, x analysed

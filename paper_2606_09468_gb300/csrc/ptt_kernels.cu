@@ -11,8 +11,8 @@
 //                       explicit terms, curl-curl forcing, SBDF sums, the
 //                       quasi-tridiagonal tau solves, u from continuity
 //   k_tick              step counters
-// followed by the diagnostics of Sec. 3 (k_ycols, k_xrows, k_diag_part,
-// k_diag_count, k_diag_final).  All transforms are mixed-radix (2, 3, 4, 5) Stockham FFTs
+// followed by the diagnostics of Sec. 3 (k_ycols x2, k_xrows, k_diag_part,
+// k_diag_count, k_diag_mid, k_diag_final).  All transforms are mixed-radix (2, 3, 4, 5) Stockham FFTs
 // in shared memory; the Chebyshev transforms are discrete cosine transforms
 // of type I computed as FFTs of the even extension.
 //
@@ -1046,6 +1046,44 @@ __global__ void __launch_bounds__(256) k_diag_count(GroupDev g) {
   }
 }
 
+// Mid-plane spectra at y = 0, one warp per (member, Fourier mode):
+// T_n(0) = cos(n pi/2), T_n'(0) = n sin(n pi/2).  DM[b][q][m], q = Tr c, u, v,
+// du/dy (Chebyshev sums; x derivatives and the mean are applied later).
+__global__ void __launch_bounds__(256) k_diag_mid(GroupDev g) {
+  const int b = blockIdx.y;
+  if (g.status[b]) return;
+  const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int K = g.K, N = g.N;
+  if (m >= K) return;
+  const size_t NK = (size_t)N * K;
+  const double2* X = g.X + (size_t)b * 5 * NK + (size_t)m * N;
+  double2 tr = czero(), u = czero(), v = czero(), uy = czero();
+  for (int n = lane; n < N; n += 32) {
+    const int r4 = n & 3;
+    if (r4 == 0 || r4 == 2) {
+      const double s = (r4 == 0) ? 1.0 : -1.0;
+      tr = cfma(s, cadd(X[2 * NK + n], X[4 * NK + n]), tr);
+      u = cfma(s, X[n], u);
+      v = cfma(s, X[NK + n], v);
+    } else {
+      const double s = (r4 == 1) ? (double)n : -(double)n;
+      uy = cfma(s, X[n], uy);
+    }
+  }
+  tr = warp_sum2(tr);
+  u = warp_sum2(u);
+  v = warp_sum2(v);
+  uy = warp_sum2(uy);
+  if (lane == 0) {
+    double2* D = g.DM + (size_t)b * 4 * K + m;
+    D[0] = tr;
+    D[K] = u;
+    D[2 * K] = v;
+    D[3 * K] = uy;
+  }
+}
+
 // Per member: reduce the tiles, <Tr c> from the mean mode, mid-plane
 // statistics, blow-up test, record.
 __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
@@ -1069,43 +1107,22 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
   for (int n = threadIdx.x; n < N; n += blockDim.x)
     if ((n & 1) == 0) mt += (X[2 * NK + n].x + X[4 * NK + n].x) * (2.0 / (1.0 - (double)n * n));
   mt = block_sum(mt, sh);
-  // mid-plane spectra at y = 0: T_n(0) = cos(n pi/2), T_n'(0) = n sin(n pi/2);
-  // one warp per Fourier mode, lanes over the Chebyshev index
+  // mid-plane lines from the per-mode sums: (Tr c, u') (v, du/dx) (dv/dx, du/dy)
   double2* L = dsm;              // 3 lines of nx
   double2* L2 = dsm + 3 * nx;    // ping-pong
   const double kfac = 2.0 * 3.14159265358979323846 / pr.lx;
   for (int i = threadIdx.x; i < 3 * nx; i += blockDim.x) L[i] = czero();
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int m = warp; m < K; m += nw) {
-    double2 tr = czero(), u = czero(), v = czero(), uy = czero();
-    const size_t cm = (size_t)m * N;
-    for (int n = lane; n < N; n += 32) {
-      const int r4 = n & 3;
-      if (r4 == 0 || r4 == 2) {
-        const double s = (r4 == 0) ? 1.0 : -1.0;
-        tr = cfma(s, cadd(X[2 * NK + cm + n], X[4 * NK + cm + n]), tr);
-        u = cfma(s, X[cm + n], u);
-        v = cfma(s, X[NK + cm + n], v);
-      } else {
-        const double s = (r4 == 1) ? (double)n : -(double)n;
-        uy = cfma(s, X[cm + n], uy);
-      }
-    }
-    tr = warp_sum2(tr);
-    u = warp_sum2(u);
-    v = warp_sum2(v);
-    uy = warp_sum2(uy);
-    if (lane == 0) {
-      const double km = kfac * m;
-      double2 ux = cscl(mul_i(u), km), vx = cscl(mul_i(v), km);
-      if (m == 0) { tr.x += 1.0; u = czero(); tr.y = v.y = uy.y = 0.0; ux = vx = czero(); }
-      // lines: (Tr c, u') (v, ux) (vx, uy); Hermitian fill
-      const double2 F[6] = {tr, u, v, ux, vx, uy};
-      for (int l = 0; l < 3; ++l) {
-        L[l * nx + m] = cadd(F[2 * l], mul_i(F[2 * l + 1]));
-        if (m > 0) L[l * nx + nx - m] = cadd(cconj(F[2 * l]), mul_i(cconj(F[2 * l + 1])));
-      }
+  const double2* DM = g.DM + (size_t)b * 4 * K;
+  for (int m = threadIdx.x; m < K; m += blockDim.x) {
+    double2 tr = DM[m], u = DM[K + m], v = DM[2 * K + m], uy = DM[3 * K + m];
+    const double km = kfac * m;
+    double2 ux = cscl(mul_i(u), km), vx = cscl(mul_i(v), km);
+    if (m == 0) { tr.x += 1.0; u = czero(); tr.y = v.y = uy.y = 0.0; ux = vx = czero(); }
+    const double2 F[6] = {tr, u, v, ux, vx, uy};
+    for (int l = 0; l < 3; ++l) {
+      L[l * nx + m] = cadd(F[2 * l], mul_i(F[2 * l + 1]));
+      if (m > 0) L[l * nx + nx - m] = cadd(cconj(F[2 * l]), mul_i(cconj(F[2 * l + 1])));
     }
   }
   __syncthreads();
@@ -1284,8 +1301,9 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       k_xrows<<<dim3(g.N, g.nb), 256, smem_xrows(1, g.nx), st>>>(X);
       k_diag_part<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
       k_diag_count<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
+      k_diag_mid<<<dim3(cdiv(g.K, 8), g.nb), 256, 0, st>>>(g);
       k_diag_final<<<g.nb, 256, smem_xrows(3, g.nx), st>>>(g);
-      n = 6;
+      n = 7;
       break;
     }
     default:
