@@ -38,6 +38,10 @@ WORKLOAD = ("2D sPTT channel sweep, FP64: Nx in {128,256,512} x Ny in {97,129,25
             "seeds {0,1,2} (27 runs), Lx=10, Wi=150, Re=1e-2, beta=0.9, eps=kappa=5e-5, "
             "dt=1e-3, laminar + seeded perturbation 1e-3")
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); measured DFMA loop: 1.197
+# DRAM read + write bytes per launch, averaged over the 9 shape groups, from
+# ncu counters of the current kernel source (profiles/k_xfused_2d_sweep_fp64.md);
+# reported as roofline.traffic when that kernel dominates.
+NCU_TRAFFIC_PER_LAUNCH = {"k_xfused": 16.20e6}
 
 
 def parse():
@@ -56,6 +60,28 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def members_for_rank(rank):
+    """The 27 sweep runs of one rank: same shapes on every rank, seeds offset
+    by 3 * rank (independent runs, weak scaling, no data exchange)."""
+    return [(nx, ny, s + 3 * rank) for nx, ny, s in I.sweep_members()]
+
+
+def max_over_ranks(x, device="cpu"):
+    """Max of a timing over the ranks (the only collective of the benchmark)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, points_per_rank, steps, seconds):
+    """Grid-point-steps/s of all ranks: every rank advances its own runs."""
+    return world * points_per_rank * steps / seconds
 
 
 # ------------------------------------------------------------ clock sampler
@@ -187,7 +213,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    members = [(nx, ny, s + 3 * rank) for nx, ny, s in I.sweep_members()]
+    members = members_for_rank(rank)
     params = [P.make_params(nx=nx, ny=ny, dt=I.DT, **I.PAPER) for nx, ny, _ in members]
     ctx = P.Context(params)
     for i, (_, _, s) in enumerate(members):
@@ -199,14 +225,6 @@ def run_ours(args):
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # warm-up
     ctx.step(args.warmup)
@@ -226,10 +244,10 @@ def run_ours(args):
     t1 = time.time()
     barrier()
     clk = clocks.stop(t0, t1)
-    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
     status = ctx.synchronize()
     launches = ctx.launches_per_step() * args.steps
-    value = world * points * args.steps / (ms * 1e-3)
+    value = whole_job_rate(world, points, args.steps, ms * 1e-3)
 
     # per-stage device times (same workload, ordinary launches + events)
     st_ms = ctx.time_stages(max(args.steps // 4, 5))
@@ -246,9 +264,12 @@ def run_ours(args):
         pass
     hbm_achieved = byts[dom] / nl[dom] / (per_launch_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": NCU_TRAFFIC_PER_LAUNCH.get(P.STAGE_KERNELS[dom]),
                 "kernel": P.STAGE_KERNELS[dom], "stage": P.STAGE_NAMES[dom],
                 "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)",
+                "algorithmic_flops_per_launch": flops[dom] / nl[dom],
+                "algorithmic_bytes_per_launch": byts[dom] / nl[dom],
                 "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak,
                 "stage_ms_per_step": {P.STAGE_NAMES[i]: st_ms[i] / nst for i in range(P.PTT_NSTAGES)}}
 
@@ -275,8 +296,8 @@ def run_ours(args):
             P.ptt_get_checkpoint(ctx.ctx, i, bufs[i][1])
     torch.cuda.synchronize()
     tb = time.perf_counter()
-    e2e_s = max_over_ranks(tb - ta)
-    e2e = {"value": world * points * args.e2e_steps / e2e_s, "unit": METRIC,
+    e2e_s = max_over_ranks(tb - ta, "cuda")
+    e2e = {"value": whole_job_rate(world, points, args.e2e_steps, e2e_s), "unit": METRIC,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
 
     if rank != 0:
