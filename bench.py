@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false",
+                    help="skip the mixed-precision measurement")
     return ap.parse_args()
 
 
@@ -300,6 +302,44 @@ def run_ours(args):
     e2e = {"value": whole_job_rate(world, points, args.e2e_steps, e2e_s), "unit": METRIC,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
 
+    # mixed precision form (FP32 transforms and products, FP64 state and
+    # solves) of the same workload: rate, and its deviation from the FP64 GPU
+    # path after the warm-up steps from the same initial state
+    mixed = None
+    if args.mixed:
+        mparams = [P.make_params(nx=nx, ny=ny, dt=I.DT, precision=P.PTT_MIXED, **I.PAPER)
+                   for nx, ny, _ in members]
+        mctx = P.Context(mparams)
+        fctx = P.Context([params[-1]])
+        for i, (_, _, s) in enumerate(members):
+            mctx.init_state(i, s, I.AMPLITUDE)
+        fctx.init_state(0, members[-1][2], I.AMPLITUDE)
+        mctx.step(args.warmup)
+        fctx.step(args.warmup)
+        assert mctx.synchronize() == P.PTT_OK and fctx.synchronize() == P.PTT_OK
+        a = mctx.get_state(len(members) - 1)
+        r = fctx.get_state(0)
+        dev = [float(np.max(np.abs(a[f] - r[f])) / np.max(np.abs(r[f]))) for f in range(5)]
+        fctx.close()
+        barrier()
+        torch.cuda.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(mctx.stream)
+        mctx.step(args.steps)
+        m1.record(mctx.stream)
+        torch.cuda.synchronize()
+        mms = max_over_ranks(m0.elapsed_time(m1), "cuda")
+        mval = whole_job_rate(world, points, args.steps, mms * 1e-3)
+        mixed = {"value": mval, "unit": METRIC, "ms_per_step": mms / args.steps,
+                 "speedup_vs_fp64": mval / value, "dtype": "f32 transforms / f64 state+solves",
+                 "status": P.ptt_status_string(mctx.synchronize()),
+                 "max_rel_field_dev_vs_fp64_gpu": dict(zip(["u", "v", "cxx", "cxy", "cyy"], dev)),
+                 "dev_after_steps": args.warmup, "dev_member": "512x257",
+                 "stated_error_vs_oracle": "tests/test_gpu_mixed.py: 1 step <= 1e-8; 100 steps "
+                                           "<= 1e-7 (u, c), <= 1e-4 (v, the 1e-3 perturbation)"}
+        mctx.close()
+
     if rank != 0:
         return
     ws = ctx.nbytes
@@ -313,6 +353,8 @@ def run_ours(args):
                       "graph": "one CUDA graph launch per step"},
            "status": P.ptt_status_string(status),
            "gpu_launches": launches, "roofline": roofline, "clocks": clk, "e2e": e2e}
+    if mixed is not None:
+        out["mixed"] = mixed
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))

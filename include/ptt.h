@@ -59,14 +59,15 @@ extern "C" {
 #define PTT_ENOTSUP (-5)   /* valid request this build does not implement        */
 
 #define PTT_FP64 0         /* every step of the path in FP64                     */
-#define PTT_MIXED 1        /* reserved: FP32 transforms, FP64 solves             */
+#define PTT_MIXED 1        /* FP32 transforms and products; FP64 state, SBDF sums,
+                              tau solves and diagnostics                         */
 
 /* Physical and numerical parameters of one member.  Defaults (the paper's
  * single fluid, Sec. 2): lx = lz = 10, re = 1e-2, wi = 150, beta = 0.9,
  * eps = 5e-5, kappa = 5e-5, dt = 2.5e-3. */
 typedef struct {
   int32_t nx, ny, nz;        /* Fourier modes in x, Chebyshev modes in y, nz = 1 */
-  int32_t precision;         /* PTT_FP64                                          */
+  int32_t precision;         /* PTT_FP64 or PTT_MIXED                             */
   double lx, lz;             /* periodic lengths (walls at y = +-1)               */
   double re, wi, beta, eps, kappa;
   double dt;                 /* fixed time step                                   */
@@ -161,7 +162,8 @@ int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec5);
  * has no counterpart: this is a deployment variant of ptt_explicit_rhs.
  *
  * Same output as ptt_explicit_rhs for one run with params *p, but from and
- * to device memory the caller passes: d_spec holds the spectral state
+ * to device memory the caller passes (FP64 only: PTT_ENOTSUP for
+ * PTT_MIXED): d_spec holds the spectral state
  * double[5][ny][nx/2][2] (u, v, c_xx, c_xy, c_yy), d_out receives
  * double[5][ny][nx/2][2] (N_cxx, N_cxy, N_cyy, H_x, H_y); both 16-byte
  * aligned, distinct.  The intermediates live in a static device array of

@@ -7,6 +7,7 @@
 #include <map>
 #include <memory>
 #include <new>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -239,7 +240,7 @@ struct Group {
 
 int check_params(const ptt_params& p) {
   if (p.nz != 1) return PTT_ENOTSUP;
-  if (p.precision != PTT_FP64) return PTT_ENOTSUP;
+  if (p.precision != PTT_FP64 && p.precision != PTT_MIXED) return PTT_ENOTSUP;
   if (p.nx < 8 || p.nx > 512 || (p.nx & 1) || !smooth235(p.nx)) return PTT_EINVAL;
   if (p.ny < 9 || p.ny > 513 || !smooth235(p.ny - 1)) return PTT_EINVAL;
   if (!(p.lx > 0) || !(p.re > 0) || !(p.wi > 0) || !(p.dt > 0)) return PTT_EINVAL;
@@ -268,7 +269,7 @@ void group_sizes(int nx, int ny, Group& g) {
   d.Me = Me;
   const size_t target = 96 * 1024;
   auto cols = [&](int P) {
-    long long c = (long long)(target / smem_ycols(1, P));
+    long long c = (long long)(target / smem_ycols(1, P, 0));
     if (c < 1) c = 1;
     if (c > 16) c = 16;
     return (int)c;
@@ -305,8 +306,17 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.X = cv.take<double2>((size_t)nb * 5 * NK);
     d.Eh = cv.take<double2>((size_t)4 * nb * 4 * NK);
     d.Nh = cv.take<double2>((size_t)4 * nb * 4 * NK);
-    d.Yp = cv.take<double2>((size_t)nb * 9 * rows * d.K);
-    d.Zp = cv.take<double2>((size_t)nb * 5 * rows * d.K);
+    if (d.f32) {
+      d.Yp = nullptr;
+      d.Zp = nullptr;
+      d.Ypf = cv.take<float2>((size_t)nb * 9 * rows * d.K);
+      d.Zpf = cv.take<float2>((size_t)nb * 5 * rows * d.K);
+    } else {
+      d.Yp = cv.take<double2>((size_t)nb * 9 * rows * d.K);
+      d.Zp = cv.take<double2>((size_t)nb * 5 * rows * d.K);
+      d.Ypf = nullptr;
+      d.Zpf = nullptr;
+    }
     d.NR = cv.take<double2>((size_t)nb * 5 * NK);
     d.Rb = cv.take<double2>((size_t)nb * 4 * NK);
     d.qt = cv.take<double>((size_t)nb * 4 * 3 * 3 * NK);
@@ -329,17 +339,19 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       pls[i]->nst = (int)g.hp[i].radix.size();
       for (int s = 0; s < pls[i]->nst; ++s) pls[i]->radix[s] = g.hp[i].radix[s];
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
+      pls[i]->twf = (d.f32 && i < 2) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
     }
     d.tw4P = cv.take<double2>((size_t)d.M);
+    d.tw4Pf = d.f32 ? cv.take<float2>((size_t)d.M) : nullptr;
     d.tw4E = cv.take<double2>((size_t)d.Me);
   }
 }
 
 std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
-  std::map<std::pair<int, int>, int> idx;
+  std::map<std::tuple<int, int, int>, int> idx;
   std::vector<Group> groups;
   for (int i = 0; i < nmem; ++i) {
-    auto key = std::make_pair(pm[i].nx, pm[i].ny);
+    auto key = std::make_tuple(pm[i].nx, pm[i].ny, pm[i].precision);
     auto it = idx.find(key);
     if (it == idx.end()) {
       idx[key] = (int)groups.size();
@@ -347,6 +359,7 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
       g.nx = pm[i].nx;
       g.ny = pm[i].ny;
       group_sizes(g.nx, g.ny, g);
+      g.d.f32 = (pm[i].precision == PTT_MIXED) ? 1 : 0;
       groups.push_back(std::move(g));
       it = idx.find(key);
     }
@@ -398,6 +411,7 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
                std::vector<double2>& twMx, std::vector<double2>& tw4, MemberPrm& prm) {
   const int s = check_params(p);
   if (s) return s;
+  if (p.precision != PTT_FP64) return PTT_ENOTSUP;
   Group g;
   g.nx = p.nx;
   g.ny = p.ny;
@@ -447,7 +461,7 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
   }
   std::vector<Group> groups = make_groups(pm, nmem);
   for (Group& g : groups) {
-    if (smem_xfused(g.d.Mx) > 227 * 1024) return PTT_EINVAL;
+    if (smem_xfused(g.d.Mx, g.d.f32) > 227 * 1024) return PTT_EINVAL;
   }
   Carver cv;
   carve(groups, cv);
@@ -478,7 +492,7 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   int optin = 0;
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
   for (Group& g : c->groups)
-    if (smem_xfused(g.d.Mx) > (size_t)optin || smem_spec(g.d.N) > (size_t)optin) return PTT_EINVAL;
+    if (smem_xfused(g.d.Mx, g.d.f32) > (size_t)optin || smem_spec(g.d.N) > (size_t)optin) return PTT_EINVAL;
   CK(set_kernel_attributes(optin));
   CK(cudaMemsetAsync(d_ws, 0, need - 256, c->stream));
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
@@ -593,6 +607,12 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
         }
         CK(cudaMemcpyAsync((void*)dst[t], tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice,
                            c->stream));
+        if (t == 0 && d.tw4Pf) {
+          std::vector<float2> twf(tw.size());
+          for (size_t k = 0; k < tw.size(); ++k) twf[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+          CK(cudaMemcpyAsync((void*)d.tw4Pf, twf.data(), twf.size() * sizeof(float2),
+                             cudaMemcpyHostToDevice, c->stream));
+        }
         CK(cudaStreamSynchronize(c->stream));
       }
     }
@@ -607,6 +627,12 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
         tw[k] = make_double2(cc, -ss);
       }
       CK(cudaMemcpyAsync((void*)pls[t]->tw, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+      if (pls[t]->twf) {
+        std::vector<float2> twf(n);
+        for (int k = 0; k < n; ++k) twf[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+        CK(cudaMemcpyAsync((void*)pls[t]->twf, twf.data(), n * sizeof(float2), cudaMemcpyHostToDevice,
+                           c->stream));
+      }
       CK(cudaStreamSynchronize(c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));

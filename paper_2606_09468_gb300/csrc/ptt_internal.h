@@ -19,6 +19,7 @@ struct FftPlan {
   int nst;
   int radix[kMaxStages];
   const double2* tw;  // tw[k] = exp(-2 pi i k / n), k < n (device)
+  const float2* twf;  // the same in single precision (mixed groups), or null
 };
 
 // Per-member physics, resident on the device.
@@ -33,6 +34,7 @@ struct MemberPrm {
 // arrays of values on a y grid are [member][field][j][m] (m fastest).
 struct GroupDev {
   int nb;            // members in the group
+  int f32;           // 1: mixed precision (FP32 transforms and products)
   int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
   int Mx, M, P;      // padded x points, padded y Gauss points (= y FFT length), P = M
   int Pu, Me;        // y FFT length of the unpadded grid (2(N-1)); diagnostic Gauss points
@@ -45,6 +47,8 @@ struct GroupDev {
   double2* Nh;       // [4 slot][nb][4][K][N]  their explicit terms
   double2* Yp;       // [nb][9][M][K]  fields on the padded y grid (Gauss points)
   double2* Zp;       // [nb][5][M][K]  products, x-analysed, on the padded y grid
+  float2* Ypf;       // mixed groups: Yp in single precision
+  float2* Zpf;       // mixed groups: Zp in single precision
   double2* NR;       // [nb][5][K][N]  explicit nonlinear terms, spectral
   double2* Rb;       // [nb][4][K][N]  H_x, H_y of ptt_explicit_rhs
   const double* qt;  // [nb][4 order][3 sys][3 (Q, inv, F)][K][N]
@@ -62,6 +66,7 @@ struct GroupDev {
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
   double2* stageS;   // [5][N][K]  values on the unpadded y grid, x analysed
   const double2* tw4P;  // [M]  exp(-i pi k/(2M)), padded Gauss grid
+  const float2* tw4Pf;  // the same in single precision (mixed groups)
   const double2* tw4E;  // [Me] exp(-i pi k/(2Me)), diagnostic Gauss grid
   FftPlan plP, plMx, plNx, plPu, plPe;   // lengths M, Mx, nx, 2(N-1), Me
 };
@@ -86,8 +91,8 @@ void set_last_error(const char* msg);
 int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
                std::vector<double2>& twMx, std::vector<double2>& tw4, MemberPrm& prm);
 
-size_t smem_ycols(int C, int P);
-size_t smem_xfused(int Mx);
+size_t smem_ycols(int C, int P, int f32);
+size_t smem_xfused(int Mx, int f32);
 size_t smem_xrows(int nl, int n);
 size_t smem_spec(int N);
 cudaError_t launch_transpose(const double2* src, double2* dst, int nf, int rows, int cols,

@@ -40,22 +40,50 @@ __device__ __forceinline__ double2 cfma(double s, double2 a, double2 c) {  // s*
 }
 __device__ __forceinline__ double2 czero() { return make_double2(0.0, 0.0); }
 
+// single precision twins (mixed-precision transforms)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscl(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cfma(float s, float2 a, float2 c) {
+  return make_float2(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y));
+}
+
+template <typename C2> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+template <typename C2> __device__ __forceinline__ C2 zero2();
+template <> __device__ __forceinline__ double2 zero2<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 zero2<float2>() { return make_float2(0.f, 0.f); }
+template <typename D> __device__ __forceinline__ D cvt2(double2 v);
+template <typename D> __device__ __forceinline__ D cvt2(float2 v);
+template <> __device__ __forceinline__ double2 cvt2<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 cvt2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <> __device__ __forceinline__ double2 cvt2<double2>(float2 v) { return make_double2(v.x, v.y); }
+template <> __device__ __forceinline__ float2 cvt2<float2>(float2 v) { return v; }
+
 // ------------------------------------------------------------ radix DFTs
 // DIR = -1: exp(-2 pi i jk/R) (forward); DIR = +1: exp(+2 pi i jk/R).
 template <int DIR, int R> struct Bfly;
 
 template <int DIR> struct Bfly<DIR, 2> {
-  static __device__ __forceinline__ void run(double2* v) {
-    double2 t = v[0];
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    C2 t = v[0];
     v[0] = cadd(t, v[1]);
     v[1] = csub(t, v[1]);
   }
 };
 
 template <int DIR> struct Bfly<DIR, 4> {
-  static __device__ __forceinline__ void run(double2* v) {
-    double2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    double2 s13 = cadd(v[1], v[3]), d13 = mul_i(csub(v[1], v[3]));
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    C2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    C2 s13 = cadd(v[1], v[3]), d13 = mul_i(csub(v[1], v[3]));
     v[0] = cadd(s02, s13);
     v[2] = csub(s02, s13);
     if (DIR < 0) { v[1] = csub(d02, d13); v[3] = cadd(d02, d13); }
@@ -64,11 +92,13 @@ template <int DIR> struct Bfly<DIR, 4> {
 };
 
 template <int DIR> struct Bfly<DIR, 3> {
-  static __device__ __forceinline__ void run(double2* v) {
-    const double s = DIR * 0.86602540378443864676;  // sin(2 pi / 3), signed
-    double2 t1 = cadd(v[1], v[2]);
-    double2 it2 = mul_i(csub(v[1], v[2]));
-    double2 m = cfma(-0.5, t1, v[0]);
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    using T = typename RealOf<C2>::T;
+    const T s = (T)(DIR * 0.86602540378443864676);  // sin(2 pi / 3), signed
+    C2 t1 = cadd(v[1], v[2]);
+    C2 it2 = mul_i(csub(v[1], v[2]));
+    C2 m = cfma((T)-0.5, t1, v[0]);
     v[0] = cadd(v[0], t1);
     v[1] = cfma(s, it2, m);
     v[2] = cfma(-s, it2, m);
@@ -76,17 +106,19 @@ template <int DIR> struct Bfly<DIR, 3> {
 };
 
 template <int DIR> struct Bfly<DIR, 5> {
-  static __device__ __forceinline__ void run(double2* v) {
-    const double c1 = 0.30901699437494742410;   // cos(2 pi / 5)
-    const double c2 = -0.80901699437494742410;  // cos(4 pi / 5)
-    const double s1 = DIR * 0.95105651629515357212;  // sin(2 pi / 5), signed
-    const double s2 = DIR * 0.58778525229247312917;  // sin(4 pi / 5), signed
-    double2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
-    double2 t3 = mul_i(csub(v[1], v[4])), t4 = mul_i(csub(v[2], v[3]));
-    double2 b1 = cfma(c1, t1, cfma(c2, t2, v[0]));
-    double2 b2 = cfma(c2, t1, cfma(c1, t2, v[0]));
-    double2 e1 = cfma(s1, t3, cscl(t4, s2));
-    double2 e2 = cfma(s2, t3, cscl(t4, -s1));
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    using T = typename RealOf<C2>::T;
+    const T c1 = (T)0.30901699437494742410;   // cos(2 pi / 5)
+    const T c2 = (T)-0.80901699437494742410;  // cos(4 pi / 5)
+    const T s1 = (T)(DIR * 0.95105651629515357212);  // sin(2 pi / 5), signed
+    const T s2 = (T)(DIR * 0.58778525229247312917);  // sin(4 pi / 5), signed
+    C2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    C2 t3 = mul_i(csub(v[1], v[4])), t4 = mul_i(csub(v[2], v[3]));
+    C2 b1 = cfma(c1, t1, cfma(c2, t2, v[0]));
+    C2 b2 = cfma(c2, t1, cfma(c1, t2, v[0]));
+    C2 e1 = cfma(s1, t3, cscl(t4, s2));
+    C2 e2 = cfma(s2, t3, cscl(t4, -s1));
     v[0] = cadd(v[0], cadd(t1, t2));
     v[1] = cadd(b1, e1);
     v[4] = csub(b1, e1);
@@ -96,26 +128,26 @@ template <int DIR> struct Bfly<DIR, 5> {
 };
 
 // One Stockham pass of radix R over nl lines (line l at offset l*ls).
-template <int DIR, int R>
-__device__ __forceinline__ void fft_pass(const double2* __restrict__ src, double2* __restrict__ dst,
+template <int DIR, int R, typename C2>
+__device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restrict__ dst,
                                          int nl, int ls, int n, int Ns,
-                                         const double2* __restrict__ tw) {
+                                         const C2* __restrict__ tw) {
   const int nb = n / R;
   const int st = n / (Ns * R);
   const int total = nl * nb;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int l = t / nb;
     const int j = t - l * nb;
-    const double2* s = src + l * ls;
-    double2* d = dst + l * ls;
+    const C2* s = src + l * ls;
+    C2* d = dst + l * ls;
     const int jm = j % Ns;
-    double2 v[R];
+    C2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[j + r * nb];
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        double2 w = __ldg(&tw[jm * r * st]);
+        C2 w = __ldg(&tw[jm * r * st]);
         if (DIR > 0) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
@@ -127,25 +159,30 @@ __device__ __forceinline__ void fft_pass(const double2* __restrict__ src, double
   }
 }
 
+template <typename C2> __device__ __forceinline__ const C2* plan_tw(const FftPlan& pl);
+template <> __device__ __forceinline__ const double2* plan_tw<double2>(const FftPlan& pl) { return pl.tw; }
+template <> __device__ __forceinline__ const float2* plan_tw<float2>(const FftPlan& pl) { return pl.twf; }
+
 // Unnormalised DFT of nl lines of length pl.n held in `a`, using `b` as the
 // ping-pong buffer.  Returns the buffer holding the result.  Must be called
 // by the whole block after a __syncthreads(); ends with one.
-template <int DIR>
-__device__ double2* fft_lines(double2* a, double2* b, int nl, int ls, const FftPlan& pl) {
-  double2* src = a;
-  double2* dst = b;
+template <int DIR, typename C2>
+__device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl) {
+  C2* src = a;
+  C2* dst = b;
+  const C2* tw = plan_tw<C2>(pl);
   int Ns = 1;
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.radix[s];
     switch (R) {
-      case 2: fft_pass<DIR, 2>(src, dst, nl, ls, pl.n, Ns, pl.tw); break;
-      case 3: fft_pass<DIR, 3>(src, dst, nl, ls, pl.n, Ns, pl.tw); break;
-      case 4: fft_pass<DIR, 4>(src, dst, nl, ls, pl.n, Ns, pl.tw); break;
-      default: fft_pass<DIR, 5>(src, dst, nl, ls, pl.n, Ns, pl.tw); break;
+      case 2: fft_pass<DIR, 2>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      case 3: fft_pass<DIR, 3>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      case 4: fft_pass<DIR, 4>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      default: fft_pass<DIR, 5>(src, dst, nl, ls, pl.n, Ns, tw); break;
     }
     __syncthreads();
     Ns *= R;
-    double2* t = src; src = dst; dst = t;
+    C2* t = src; src = dst; dst = t;
   }
   return src;
 }
@@ -173,6 +210,9 @@ constexpr int kMaxChunk = 8;  // tau sweeps: up to 8 rows per lane (ny <= 513)
 __device__ __forceinline__ double2 shfl_down2(double2 v, int o) {
   return make_double2(__shfl_down_sync(kFull, v.x, o), __shfl_down_sync(kFull, v.y, o));
 }
+__device__ __forceinline__ float2 shfl_down2(float2 v, int o) {
+  return make_float2(__shfl_down_sync(kFull, v.x, o), __shfl_down_sync(kFull, v.y, o));
+}
 __device__ __forceinline__ double2 shfl_up2(double2 v, int o) {
   return make_double2(__shfl_up_sync(kFull, v.x, o), __shfl_up_sync(kFull, v.y, o));
 }
@@ -187,31 +227,33 @@ __device__ __forceinline__ double2 warp_allsum2(double2 v) {
 // Chebyshev derivative by one warp: out_n = (2/c_n) sum_{p > n, p + n odd} p a_p
 // (c_0 = 2), as two same-parity suffix sums T(k) = sum_{p >= k, p = k mod 2} p a_p
 // with out_{k-1} = (2/c_{k-1}) T(k).  `out` must not alias `a`.
-__device__ void warp_cheb_deriv(const double2* a, double2* out, int N) {
+template <typename C2>
+__device__ void warp_cheb_deriv(const C2* a, C2* out, int N) {
+  using T = typename RealOf<C2>::T;
   const int lane = threadIdx.x & 31;
   for (int par = 0; par < 2; ++par) {
     const int L = (N - par + 1) / 2;
     const int c = (L + 31) / 32;
     const int i0 = min(lane * c, L), i1 = min(i0 + c, L);
-    double2 acc = czero();
+    C2 acc = zero2<C2>();
     for (int i = i1 - 1; i >= i0; --i) {
       const int k = par + 2 * i;
-      acc = cfma((double)k, a[k], acc);
-      if (k >= 1) out[k - 1] = cscl(acc, k == 1 ? 1.0 : 2.0);
+      acc = cfma((T)k, a[k], acc);
+      if (k >= 1) out[k - 1] = cscl(acc, (T)(k == 1 ? 1 : 2));
     }
-    double2 inc = acc;
+    C2 inc = acc;
     for (int o = 1; o < 32; o <<= 1) {
-      const double2 v = shfl_down2(inc, o);
+      const C2 v = shfl_down2(inc, o);
       if (lane + o < 32) inc = cadd(inc, v);
     }
-    double2 ex = shfl_down2(inc, 1);
-    if (lane == 31) ex = czero();
+    C2 ex = shfl_down2(inc, 1);
+    if (lane == 31) ex = zero2<C2>();
     for (int i = i0; i < i1; ++i) {
       const int k = par + 2 * i;
-      if (k >= 1) out[k - 1] = cfma(k == 1 ? 1.0 : 2.0, ex, out[k - 1]);
+      if (k >= 1) out[k - 1] = cfma((T)(k == 1 ? 1 : 2), ex, out[k - 1]);
     }
   }
-  if (lane == 0) out[N - 1] = czero();
+  if (lane == 0) out[N - 1] = zero2<C2>();
   __syncwarp();
 }
 
@@ -340,10 +382,11 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
 // ------------------------------------------------------ Chebyshev columns
 // Column transforms along y for a batch of members and fields.  Coefficient
 // side: column m, row n at m*cm + n*cn; value side: column m, row j at
-// m*vm + j*vj (within one field of one member).
+// m*vm + j*vj (within one field of one member).  Input and output may be in
+// double or single precision independently of the compute type.
 struct YJob {
-  const double2* src;
-  double2* dst;
+  const void* src;
+  void* dst;
   long long src_mstride, dst_mstride;  // per member (elements)
   long long src_fstride, dst_fstride;  // per field (elements)
   int src_field[8];
@@ -353,34 +396,51 @@ struct YJob {
   long long cm, cn;   // coefficient-side strides
   long long vm, vj;   // value-side strides
   int K;              // columns
-  int N, M;           // Chebyshev modes, grid intervals (P = 2M)
+  int N, M;           // Chebyshev modes, grid intervals / points
   int inverse;        // 1: coefficients -> values; 0: values -> coefficients (N rows)
   int gauss;          // 0: M+1 Gauss-Lobatto points (DCT-I, FFT length 2M);
                       // 1: M Gauss points (DCT-II/III, FFT length M, M even)
-  const double2* tw4; // gauss: tw4[k] = exp(-i pi k / (2M)), k < M
+  int src_f32, dst_f32;  // element types of src / dst (0: complex double, 1: complex float)
+  const double2* tw4;    // gauss: tw4[k] = exp(-i pi k / (2M)), k < M
+  const float2* tw4f;    // the same in single precision
   int C;              // columns per block
   const int* status;  // skip members with status != 0 (may be null)
   FftPlan pl;
 };
+
+template <typename CT>
+__device__ __forceinline__ CT ld2(const void* p, long long i, int f32) {
+  return f32 ? cvt2<CT>(static_cast<const float2*>(p)[i]) : cvt2<CT>(static_cast<const double2*>(p)[i]);
+}
+template <typename CT>
+__device__ __forceinline__ void st2(void* p, long long i, int f32, CT v) {
+  if (f32) static_cast<float2*>(p)[i] = cvt2<float2>(v);
+  else static_cast<double2*>(p)[i] = cvt2<double2>(v);
+}
+template <typename CT> __device__ __forceinline__ CT ld_tw4(const YJob& J, int k);
+template <> __device__ __forceinline__ double2 ld_tw4<double2>(const YJob& J, int k) { return __ldg(&J.tw4[k]); }
+template <> __device__ __forceinline__ float2 ld_tw4<float2>(const YJob& J, int k) { return __ldg(&J.tw4f[k]); }
 
 // Values at the M Gauss points y_j = cos(pi (2j+1)/(2M)) from coefficients
 // (DCT-III) and back (DCT-II), each as one complex FFT of length M: the
 // output (input) order is permuted v_n = f_{2n}, v_{M-1-n} = f_{2n+1}, and a
 // quarter-period twiddle exp(-+ i pi k/(2M)) maps between the two (Makhoul's
 // construction; the real and imaginary parts of a column ride in one FFT).
-__device__ void ycols_gauss(const YJob& J, const double2* src, const double2* src2, double2* dst,
-                            double2* A, double2* B, int c0, int nc) {
+template <typename CT>
+__device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, void* dst,
+                            CT* A, CT* B, int c0, int nc) {
+  using T = typename RealOf<CT>::T;
   const int C = J.C, N = J.N, Mg = J.M;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int f = blockIdx.y;
   if (J.inverse) {
     for (int i = tid; i < Mg * C; i += nt) {
       const int c = i / Mg, n = i - c * Mg;
-      double2 v = czero();
+      CT v = zero2<CT>();
       if (c < nc && n < N) {
         const long long o = (c0 + c) * J.cm + n * J.cn;
-        v = src[o];
-        if (src2) v = cadd(v, src2[o]);
+        v = ld2<CT>(src, o, J.src_f32);
+        if (src2) v = cadd(v, ld2<CT>(src2, o, J.src_f32));
       }
       A[i] = v;
     }
@@ -397,75 +457,67 @@ __device__ void ycols_gauss(const YJob& J, const double2* src, const double2* sr
     // V_0 = a_0, V_k = (1/2) exp(+i pi k/(2M)) (a_k - i a_{M-k})
     for (int i = tid; i < Mg * C; i += nt) {
       const int c = i / Mg, k = i - c * Mg;
-      const double2 ak = A[i];
-      double2 V;
+      const CT ak = A[i];
+      CT V;
       if (k == 0) {
         V = ak;
       } else {
-        const double2 amk = A[c * Mg + Mg - k];
-        const double2 w = cconj(__ldg(&J.tw4[k]));
-        V = cscl(cmul(w, csub(ak, mul_i(amk))), 0.5);
+        const CT amk = A[c * Mg + Mg - k];
+        const CT w = cconj(ld_tw4<CT>(J, k));
+        V = cscl(cmul(w, csub(ak, mul_i(amk))), (T)0.5);
       }
       B[i] = V;
     }
     __syncthreads();
-    double2* res = fft_lines<+1>(B, A, C, Mg, J.pl);
+    CT* res = fft_lines<+1>(B, A, C, Mg, J.pl);
     for (int i = tid; i < Mg * C; i += nt) {
       const int j = i / C, c = i - j * C;
       if (c < nc) {
         const int pos = (j & 1) ? (Mg - 1 - (j >> 1)) : (j >> 1);
-        dst[j * J.vj + (c0 + c) * J.vm] = res[c * Mg + pos];
+        st2<CT>(dst, j * J.vj + (c0 + c) * J.vm, J.dst_f32, res[c * Mg + pos]);
       }
     }
   } else {
     for (int i = tid; i < Mg * C; i += nt) {
       const int j = i / C, c = i - j * C;
       const int pos = (j & 1) ? (Mg - 1 - (j >> 1)) : (j >> 1);
-      A[c * Mg + pos] = (c < nc) ? src[j * J.vj + (c0 + c) * J.vm] : czero();
+      A[c * Mg + pos] = (c < nc) ? ld2<CT>(src, j * J.vj + (c0 + c) * J.vm, J.src_f32) : zero2<CT>();
     }
     __syncthreads();
-    double2* res = fft_lines<-1>(A, B, C, Mg, J.pl);
-    const double s0 = 1.0 / Mg, s1 = 2.0 / Mg;
+    CT* res = fft_lines<-1>(A, B, C, Mg, J.pl);
+    const T s0 = (T)(1.0 / Mg), s1 = (T)(2.0 / Mg);
     for (int i = tid; i < N * C; i += nt) {
       const int c = i / N, k = i - c * N;
       if (c < nc) {
-        const double2 Vk = res[c * Mg + k];
-        const double2 Vm = cconj(res[c * Mg + (k == 0 ? 0 : Mg - k)]);
-        const double2 Vr = cscl(cadd(Vk, Vm), 0.5);
-        const double2 d = csub(Vk, Vm);
-        const double2 Vi = make_double2(0.5 * d.y, -0.5 * d.x);
-        const double2 w = __ldg(&J.tw4[k]);
-        const double xr = w.x * Vr.x - w.y * Vr.y;
-        const double xi = w.x * Vi.x - w.y * Vi.y;
-        const double sc = (k == 0) ? s0 : s1;
-        dst[(c0 + c) * J.cm + k * J.cn] = make_double2(sc * xr, sc * xi);
+        const CT Vk = res[c * Mg + k];
+        const CT Vm = cconj(res[c * Mg + (k == 0 ? 0 : Mg - k)]);
+        const CT Vr = cscl(cadd(Vk, Vm), (T)0.5);
+        const CT d = csub(Vk, Vm);
+        CT Vi;
+        Vi.x = (T)0.5 * d.y;
+        Vi.y = (T)-0.5 * d.x;
+        const CT w = ld_tw4<CT>(J, k);
+        const T xr = w.x * Vr.x - w.y * Vr.y;
+        const T xi = w.x * Vi.x - w.y * Vi.y;
+        const T sc = (k == 0) ? s0 : s1;
+        CT o;
+        o.x = sc * xr;
+        o.y = sc * xi;
+        st2<CT>(dst, (c0 + c) * J.cm + k * J.cn, J.dst_f32, o);
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_ycols(YJob J) {
-  const int b = blockIdx.z;
-  if (J.status && J.status[b]) return;
-  const int f = blockIdx.y;
-  // FFT length per column: M on the Gauss grid, 2M (even extension) on the
-  // Gauss-Lobatto grid; shared memory holds 2 C lines of it (+ 2 C scalars)
-  const int C = J.C, K = J.K, N = J.N, M = J.M, P = J.gauss ? J.M : 2 * J.M;
-  const int c0 = blockIdx.x * C;
-  const int nc = min(C, K - c0);
-  extern __shared__ double2 sm[];
-  double2* A = sm;
-  double2* B = sm + (size_t)C * P;
-  double2* a0s = B + (size_t)C * P;  // [C] a_0, [C] a_M (Gauss-Lobatto path)
-  const double2* src = J.src + b * J.src_mstride + J.src_field[f] * J.src_fstride;
-  double2* dst = J.dst + b * J.dst_mstride + J.dst_field[f] * J.dst_fstride;
+// Gauss-Lobatto path (double precision only): DCT-I by the even extension.
+__device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v, void* dstv,
+                              double2* A, double2* B, double2* a0s, int c0, int nc) {
+  const int C = J.C, N = J.N, M = J.M, P = 2 * J.M;
+  const double2* src = static_cast<const double2*>(srcv);
+  const double2* src2 = static_cast<const double2*>(src2v);
+  double2* dst = static_cast<double2*>(dstv);
   const int tid = threadIdx.x, nt = blockDim.x;
-  const double2* src2 = (J.inverse && J.src_field2[f] >= 0)
-      ? J.src + b * J.src_mstride + J.src_field2[f] * J.src_fstride : nullptr;
-  if (J.gauss) {
-    ycols_gauss(J, src, src2, dst, A, B, c0, nc);
-    return;
-  }
+  const int f = blockIdx.y;
   if (J.inverse) {
     for (int i = tid; i < N * C; i += nt) {
       const int c = i / N, n = i - c * N;
@@ -479,7 +531,6 @@ __global__ void __launch_bounds__(256) k_ycols(YJob J) {
     }
     __syncthreads();
     if (J.deriv[f]) {
-      // d/dy of each column by one warp (suffix sums), via the ping-pong buffer
       for (int c = tid >> 5; c < C; c += (nt >> 5)) warp_cheb_deriv(A + c * P, B + c * P, N);
       __syncthreads();
       for (int i = tid; i < N * C; i += nt) {
@@ -532,6 +583,37 @@ __global__ void __launch_bounds__(256) k_ycols(YJob J) {
   }
 }
 
+template <typename CT>
+__global__ void __launch_bounds__(256) k_ycols(YJob J) {
+  const int b = blockIdx.z;
+  if (J.status && J.status[b]) return;
+  const int f = blockIdx.y;
+  // FFT length per column: M on the Gauss grid, 2M (even extension) on the
+  // Gauss-Lobatto grid; shared memory holds 2 C lines of it (+ 2 C scalars)
+  const int C = J.C, K = J.K, P = J.gauss ? J.M : 2 * J.M;
+  const int c0 = blockIdx.x * C;
+  const int nc = min(C, K - c0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  CT* A = reinterpret_cast<CT*>(smraw);
+  CT* B = A + (size_t)C * P;
+  const size_t es = J.src_f32 ? sizeof(float2) : sizeof(double2);
+  const size_t ed = J.dst_f32 ? sizeof(float2) : sizeof(double2);
+  const void* src = static_cast<const char*>(J.src) + (b * J.src_mstride + J.src_field[f] * J.src_fstride) * es;
+  void* dst = static_cast<char*>(J.dst) + (b * J.dst_mstride + J.dst_field[f] * J.dst_fstride) * ed;
+  const void* src2 = (J.inverse && J.src_field2[f] >= 0)
+      ? static_cast<const char*>(J.src) + (b * J.src_mstride + J.src_field2[f] * J.src_fstride) * es
+      : nullptr;
+  if (J.gauss) {
+    ycols_gauss<CT>(J, src, src2, dst, A, B, c0, nc);
+  } else if constexpr (sizeof(CT) == sizeof(double2)) {
+    ycols_lobatto(J, src, src2, dst, reinterpret_cast<double2*>(A), reinterpret_cast<double2*>(B),
+                  reinterpret_cast<double2*>(B) + (size_t)C * P, c0, nc);
+  }
+}
+
+// ---------------------------------------------------------- Fourier rows
+// Row transforms along x: complex modes m < K <-> real values at n points,
+// two real fields packed in one complex line.
 struct XJob {
   const double2* srcC;  // c2r: complex rows
   const double* srcR;   // r2c: real rows
@@ -616,17 +698,28 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
 __constant__ int c_xsrc[14] = {0, 1, 2, 0, 1, 3, 4, 5, 6, 7, 8, 3, 4, 5};
 __constant__ int c_xik[14] = {0, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 1, 1, 1};
 
+template <typename C2> __device__ __forceinline__ const C2* yp_ptr(const GroupDev& g);
+template <> __device__ __forceinline__ const double2* yp_ptr<double2>(const GroupDev& g) { return g.Yp; }
+template <> __device__ __forceinline__ const float2* yp_ptr<float2>(const GroupDev& g) { return g.Ypf; }
+template <typename C2> __device__ __forceinline__ C2* zp_ptr(const GroupDev& g);
+template <> __device__ __forceinline__ double2* zp_ptr<double2>(const GroupDev& g) { return g.Zp; }
+template <> __device__ __forceinline__ float2* zp_ptr<float2>(const GroupDev& g) { return g.Zpf; }
+
+// C2 = double2: the FP64 path; C2 = float2: the mixed path (FP32 transforms
+// and products, FP64 state and solves).
+template <typename C2>
 __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
+  using T = typename RealOf<C2>::T;
   const int b = blockIdx.y;
   if (g.status[b]) return;
   const int j = blockIdx.x;
   const int K = g.K, Mx = g.Mx, rows = g.M;
   const MemberPrm pr = g.prm[b];
-  extern __shared__ double2 sm[];
-  double2* A = sm;
-  double2* B = sm + 7 * Mx;
-  const double2* Y = g.Yp + (size_t)b * 9 * rows * K + (size_t)j * K;
-  const double kfac = 2.0 * 3.14159265358979323846 / pr.lx;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2* A = reinterpret_cast<C2*>(smraw);
+  C2* B = A + 7 * Mx;
+  const C2* Y = yp_ptr<C2>(g) + (size_t)b * 9 * rows * K + (size_t)j * K;
+  const T kfac = (T)(2.0 * 3.14159265358979323846 / pr.lx);
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < 7 * Mx; i += nt) {
     const int l = i / Mx, k = i - l * Mx;
@@ -634,13 +727,13 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
     bool cj = false;
     if (k < K) kk = k;
     else if (k > Mx - K) { kk = Mx - k; cj = true; }
-    double2 h = czero();
+    C2 h = zero2<C2>();
     if (kk >= 0) {
       const int fa = 2 * l, fb = 2 * l + 1;
-      double2 F = Y[(size_t)c_xsrc[fa] * rows * K + kk];
-      double2 G = Y[(size_t)c_xsrc[fb] * rows * K + kk];
-      if (kk == 0) { F.y = 0.0; G.y = 0.0; }
-      const double km = kfac * kk;
+      C2 F = Y[(size_t)c_xsrc[fa] * rows * K + kk];
+      C2 G = Y[(size_t)c_xsrc[fb] * rows * K + kk];
+      if (kk == 0) { F.y = 0; G.y = 0; }
+      const T km = kfac * kk;
       if (c_xik[fa]) F = cscl(mul_i(F), km);
       if (c_xik[fb]) G = cscl(mul_i(G), km);
       if (cj) { F = cconj(F); G = cconj(G); }
@@ -649,39 +742,45 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
     A[i] = h;
   }
   __syncthreads();
-  double2* res = fft_lines<+1>(A, B, 7, Mx, g.plMx);
-  double2* oth = (res == A) ? B : A;
-  const double eps = pr.eps, iwi = pr.inv_wi;
+  C2* res = fft_lines<+1>(A, B, 7, Mx, g.plMx);
+  C2* oth = (res == A) ? B : A;
+  const T eps = (T)pr.eps, iwi = (T)pr.inv_wi;
   for (int x = tid; x < Mx; x += nt) {
-    const double2 h0 = res[x], h1 = res[Mx + x], h2 = res[2 * Mx + x], h3 = res[3 * Mx + x];
-    const double2 h4 = res[4 * Mx + x], h5 = res[5 * Mx + x], h6 = res[6 * Mx + x];
-    const double u = h0.x, v = h0.y, uy = h1.x, ux = h1.y, vx = h2.x, cxx = h2.y;
-    const double cxy = h3.x, cyy = h3.y, cxx_y = h4.x, cxy_y = h4.y, cyy_y = h5.x;
-    const double cxx_x = h5.y, cxy_x = h6.x, cyy_x = h6.y;
+    const C2 h0 = res[x], h1 = res[Mx + x], h2 = res[2 * Mx + x], h3 = res[3 * Mx + x];
+    const C2 h4 = res[4 * Mx + x], h5 = res[5 * Mx + x], h6 = res[6 * Mx + x];
+    const T u = h0.x, v = h0.y, uy = h1.x, ux = h1.y, vx = h2.x, cxx = h2.y;
+    const T cxy = h3.x, cyy = h3.y, cxx_y = h4.x, cxy_y = h4.y, cyy_y = h5.x;
+    const T cxx_x = h5.y, cxy_x = h6.x, cyy_x = h6.y;
     // Eq. 1: L_ij = du_i/dx_j (L_yy = -ux by continuity); relaxation factor
     // f = 1 + eps Tr(c - I) with c_zz = 1.
-    const double rw = (1.0 + eps * (cxx + cyy - 2.0)) * iwi;
-    const double ncxx = -(u * cxx_x + v * cxx_y) + 2.0 * (ux * cxx + uy * cxy) - (cxx - 1.0) * rw;
-    const double ncxy = -(u * cxy_x + v * cxy_y) + uy * cyy + vx * cxx - cxy * rw;
-    const double ncyy = -(u * cyy_x + v * cyy_y) + 2.0 * (vx * cxy - ux * cyy) - (cyy - 1.0) * rw;
+    const T rw = ((T)1 + eps * (cxx + cyy - (T)2)) * iwi;
+    const T ncxx = -(u * cxx_x + v * cxx_y) + (T)2 * (ux * cxx + uy * cxy) - (cxx - (T)1) * rw;
+    const T ncxy = -(u * cxy_x + v * cxy_y) + uy * cyy + vx * cxx - cxy * rw;
+    const T ncyy = -(u * cyy_x + v * cyy_y) + (T)2 * (vx * cxy - ux * cyy) - (cyy - (T)1) * rw;
     // Eq. 2 advection
-    const double nu_ = -(u * ux + v * uy);
-    const double nv_ = -(u * vx - v * ux);
-    oth[x] = make_double2(ncxx, ncxy);
-    oth[Mx + x] = make_double2(ncyy, nu_);
-    oth[2 * Mx + x] = make_double2(nv_, 0.0);
+    const T nu_ = -(u * ux + v * uy);
+    const T nv_ = -(u * vx - v * ux);
+    C2 o0, o1, o2;
+    o0.x = ncxx; o0.y = ncxy;
+    o1.x = ncyy; o1.y = nu_;
+    o2.x = nv_; o2.y = 0;
+    oth[x] = o0;
+    oth[Mx + x] = o1;
+    oth[2 * Mx + x] = o2;
   }
   __syncthreads();
-  double2* r2 = fft_lines<-1>(oth, res, 3, Mx, g.plMx);
-  double2* Z = g.Zp + (size_t)b * 5 * rows * K + (size_t)j * K;
-  const double inv = 1.0 / Mx;
+  C2* r2 = fft_lines<-1>(oth, res, 3, Mx, g.plMx);
+  C2* Z = zp_ptr<C2>(g) + (size_t)b * 5 * rows * K + (size_t)j * K;
+  const T inv = (T)(1.0 / Mx);
   for (int i = tid; i < 3 * K; i += nt) {
     const int l = i / K, k = i - l * K;
-    const double2 hk = r2[l * Mx + k];
-    const double2 hm = cconj(r2[l * Mx + (k == 0 ? 0 : Mx - k)]);
-    const double2 F = cscl(cadd(hk, hm), 0.5 * inv);
-    const double2 d = csub(hk, hm);
-    const double2 G = make_double2(0.5 * inv * d.y, -0.5 * inv * d.x);
+    const C2 hk = r2[l * Mx + k];
+    const C2 hm = cconj(r2[l * Mx + (k == 0 ? 0 : Mx - k)]);
+    const C2 F = cscl(cadd(hk, hm), (T)0.5 * inv);
+    const C2 d = csub(hk, hm);
+    C2 G;
+    G.x = (T)0.5 * inv * d.y;
+    G.y = (T)-0.5 * inv * d.x;
     Z[(size_t)(2 * l) * rows * K + k] = F;
     if (l < 2) Z[(size_t)(2 * l + 1) * rows * K + k] = G;
   }
@@ -1196,6 +1295,7 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl,
   YJob J{};
   J.gauss = tw4 ? 1 : 0;
   J.tw4 = tw4;
+  J.tw4f = g.tw4Pf;
   J.K = g.K;
   J.N = g.N;
   J.M = M;
@@ -1213,8 +1313,10 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl,
 
 }  // namespace
 
-size_t smem_ycols(int C, int P) { return (size_t)(2 * C * P + 2 * C) * sizeof(double2); }
-size_t smem_xfused(int Mx) { return (size_t)14 * Mx * sizeof(double2); }
+size_t smem_ycols(int C, int P, int f32) {
+  return (size_t)(2 * C * P + 2 * C) * (f32 ? sizeof(float2) : sizeof(double2));
+}
+size_t smem_xfused(int Mx, int f32) { return (size_t)14 * Mx * (f32 ? sizeof(float2) : sizeof(double2)); }
 size_t smem_xrows(int nl, int n) { return (size_t)2 * nl * n * sizeof(double2); }
 size_t smem_spec(int N) { return (size_t)12 * N * sizeof(double2) + (size_t)10 * N * sizeof(double); }
 
@@ -1229,8 +1331,10 @@ static cudaError_t optin(F* fn, int optin_bytes) {
 
 cudaError_t set_kernel_attributes(int optin_bytes) {
   cudaError_t e;
-  if ((e = optin(k_ycols, optin_bytes))) return e;
-  if ((e = optin(k_xfused, optin_bytes))) return e;
+  if ((e = optin(k_ycols<double2>, optin_bytes))) return e;
+  if ((e = optin(k_ycols<float2>, optin_bytes))) return e;
+  if ((e = optin(k_xfused<double2>, optin_bytes))) return e;
+  if ((e = optin(k_xfused<float2>, optin_bytes))) return e;
   if ((e = optin(k_xrows, optin_bytes))) return e;
   if ((e = optin(k_spec, optin_bytes))) return e;
   if ((e = optin(k_diag_final, optin_bytes))) return e;
@@ -1245,30 +1349,41 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
   switch (stage) {
     case 0: {  // inverse y: 9 fields on the padded Gauss grid (two launches: 8 + 1)
       YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4P);
-      J.src = g.X; J.dst = g.Yp;
+      J.src = g.X; J.dst = g.f32 ? (void*)g.Ypf : (void*)g.Yp;
+      J.dst_f32 = g.f32;
       J.src_mstride = 5 * NK; J.dst_mstride = 9LL * rows * g.K;
       J.src_fstride = NK; J.dst_fstride = (long long)rows * g.K;
       const int sf[9] = {0, 1, 0, 2, 3, 4, 2, 3, 4};
       const int dv[9] = {0, 0, 1, 0, 0, 0, 1, 1, 1};
       for (int i = 0; i < 8; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = dv[i]; }
-      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 8, g.nb), 256, smem_ycols(g.Ccol, g.M), st>>>(J);
       YJob J2 = J;
       J2.src_field[0] = sf[8]; J2.dst_field[0] = 8; J2.deriv[0] = dv[8];
-      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 1, g.nb), 256, smem_ycols(g.Ccol, g.M), st>>>(J2);
+      const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
+      if (g.f32) {
+        k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 8, g.nb), 256, sm, st>>>(J);
+        k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 1, g.nb), 256, sm, st>>>(J2);
+      } else {
+        k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 8, g.nb), 256, sm, st>>>(J);
+        k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 1, g.nb), 256, sm, st>>>(J2);
+      }
       n = 2;
       break;
     }
     case 1:
-      k_xfused<<<dim3(rows, g.nb), 512, smem_xfused(g.Mx), st>>>(g);
+      if (g.f32) k_xfused<float2><<<dim3(rows, g.nb), 512, smem_xfused(g.Mx, 1), st>>>(g);
+      else k_xfused<double2><<<dim3(rows, g.nb), 512, smem_xfused(g.Mx, 0), st>>>(g);
       n = 1;
       break;
     case 2: {  // forward y of the 5 explicit fields
       YJob F = make_yjob(g, false, g.M, g.Ccol, g.plP, g.tw4P);
-      F.src = g.Zp; F.dst = g.NR;
+      F.src = g.f32 ? (const void*)g.Zpf : (const void*)g.Zp; F.dst = g.NR;
+      F.src_f32 = g.f32;
       F.src_mstride = 5LL * rows * g.K; F.dst_mstride = 5 * NK;
       F.src_fstride = (long long)rows * g.K; F.dst_fstride = NK;
       for (int i = 0; i < 5; ++i) { F.src_field[i] = i; F.dst_field[i] = i; F.deriv[i] = 0; }
-      k_ycols<<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, smem_ycols(g.Ccol, g.M), st>>>(F);
+      const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
+      if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
+      else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
       n = 1;
       break;
     }
@@ -1284,14 +1399,14 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       T.src_mstride = 5 * NK; T.dst_mstride = (long long)NK;
       T.src_fstride = NK; T.dst_fstride = 0;
       T.src_field[0] = 2; T.src_field2[0] = 4; T.dst_field[0] = 0; T.deriv[0] = 0;
-      k_ycols<<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu), st>>>(T);
+      k_ycols<double2><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
       // u, v on the Me Gauss points of the energy quadrature
       YJob J = make_yjob(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
       J.src = g.X; J.dst = g.DY;
       J.src_mstride = 5 * NK; J.dst_mstride = 2LL * g.Me * g.K;
       J.src_fstride = NK; J.dst_fstride = (long long)g.Me * g.K;
       for (int i = 0; i < 2; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-      k_ycols<<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me), st>>>(J);
+      k_ycols<double2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
       XJob X{};
       X.srcC = g.DT; X.dstR = g.DV;
       X.src_mstride = (long long)NK; X.dst_mstride = (long long)g.N * g.nx;
@@ -1360,7 +1475,7 @@ cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st) {
   J.src = g.stageS; J.dst = g.X + (size_t)b * 5 * NK;
   J.src_fstride = NK; J.dst_fstride = NK;
   for (int i = 0; i < 5; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu), st>>>(J);
+  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
   k_reset<<<1, 32, 0, st>>>(g, b);
   return cudaGetLastError();
 }
@@ -1372,7 +1487,7 @@ cudaError_t launch_state_to_phys(const GroupDev& g, int b, cudaStream_t st) {
   J.src = g.X + (size_t)b * 5 * NK; J.dst = g.stageS;
   J.src_fstride = NK; J.dst_fstride = NK;
   for (int i = 0; i < 5; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu), st>>>(J);
+  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
   XJob X{};
   X.srcC = g.stageS; X.dstR = g.stage;
   X.src_fstride = NK; X.dst_fstride = (long long)g.N * g.nx;
