@@ -16,6 +16,8 @@ Modules
   spectral  Fourier-Chebyshev building blocks (Sec. 2, numerical details).
   ptt2d     The 2D (z-independent) channel: Eqs. 1-3, the SBDF4 step, the
             per-mode tau solves and the diagnostics of Sec. 3 (Eqs. 4-5).
+  ptt3d     The 3D channel (Sec. 2 geometry): the same step with the spanwise
+            direction, the v-eta velocity solve and six c components.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
 the chaotic regime beyond ~100 steps, which no closed form reaches (parity
@@ -23,3 +25,4 @@ unpinned there beyond the round-off comparison with the GPU path).
 """
 from .spectral import *  # noqa: F401,F403
 from . import ptt2d  # noqa: F401
+from . import ptt3d  # noqa: F401
