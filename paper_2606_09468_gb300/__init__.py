@@ -261,23 +261,35 @@ class Context:
         return p.nx, p.ny
 
     def phys_buffer(self, member):
-        nx, ny = self.shape(member)
-        return np.empty((5, ny, nx))
+        p = self.params[member]
+        if p.nz > 1:
+            return np.empty((9, p.ny, p.nz, p.nx))
+        return np.empty((5, p.ny, p.nx))
 
     def spec_buffer(self, member):
-        nx, ny = self.shape(member)
-        return np.empty((5, ny, nx // 2, 2))
+        p = self.params[member]
+        if p.nz > 1:
+            return np.empty((9, p.ny, p.nx // 2, p.nz, 2))
+        return np.empty((5, p.ny, p.nx // 2, 2))
 
     def init_state(self, member, seed, amplitude):
         ptt_init_state(self.ctx, member, seed, amplitude)
 
     def set_state(self, member, phys):
+        phys = np.asarray(phys)
+        if phys.shape != self.phys_buffer(member).shape:
+            raise ValueError(f"physical state of member {member}: shape {phys.shape}, "
+                             f"expected {self.phys_buffer(member).shape}")
         ptt_set_state(self.ctx, member, phys)
 
     def get_state(self, member):
         return ptt_get_state(self.ctx, member, self.phys_buffer(member))
 
     def set_spectral(self, member, spec):
+        spec = np.asarray(spec)
+        if spec.shape != self.spec_buffer(member).shape:
+            raise ValueError(f"spectral state of member {member}: shape {spec.shape}, "
+                             f"expected {self.spec_buffer(member).shape}")
         ptt_set_spectral(self.ctx, member, spec)
 
     def get_spectral(self, member):

@@ -1,6 +1,6 @@
 """Build the in-tree CUDA library ``libptt.so`` for sm_103a with nvcc.
 
-Three translation units compiled in parallel, linked with the static CUDA
+Four translation units compiled in parallel, linked with the static CUDA
 runtime.  Usage: ``python -m paper_2606_09468_gb300.build`` or ``build()``."""
 import concurrent.futures as cf
 import os
@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libptt.so")
-SOURCES = ["ptt_kernels.cu", "ptt_capi.cu", "ptt_noalloc.cu"]
+SOURCES = ["ptt_kernels.cu", "ptt_kernels3d.cu", "ptt_capi.cu", "ptt_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -40,7 +40,8 @@ def build(verbose=False, extra=()):
             for s, o in zip(SOURCES, objs)]
     with cf.ThreadPoolExecutor(len(cmds)) as ex:
         logs = list(ex.map(_run, cmds))
-    logs.append(_run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs]))
+    logs.append(_run([nvcc, *ARCH, "-shared", "-cudart", "static", "-Xlinker", "--no-undefined",
+                      "-o", LIB, *objs]))
     if verbose:
         for lg in logs:
             if lg.strip():

@@ -218,6 +218,84 @@ void initial_fields(const ptt_params& p, uint64_t seed, double amp, std::vector<
     }
 }
 
+// Physical initial fields of a 3D run, [9][ny][nz][nx]: laminar sPTT +
+// perturbation u' = d psi1/dy, v' = -d psi1/dx - d psi2/dz, w' = d psi2/dy,
+// psi_c = (1 - y^2)^2 sum_{mx <= 4, mz <= 2, (mx, mz) != 0, n <= 8}
+//         (A cos(kx x + kz z) + B sin(kx x + kz z)) T_n(y),
+// A, B from the splitmix64 stream of `seed`, output
+// ((((c*5 + mx)*3 + mz)*9 + n)*2 + {0, 1}); scaled to max |u'| = amp.
+void initial_fields3(const ptt_params& p, uint64_t seed, double amp, std::vector<double>& out) {
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const size_t F = (size_t)ny * nz * nx;
+  out.assign(9 * F, 0.0);
+  std::vector<double> y(ny), U(ny), cxx(ny), cxy(ny);
+  const double sw = laminar_root(1.0, p.wi, p.beta, p.eps);
+  const double Fw = laminar_F(sw, p.beta, p.eps);
+  for (int l = 0; l < ny; ++l) {
+    double c, s;
+    cis(l, 2 * (ny - 1), &c, &s);
+    y[l] = c;
+    const double r = laminar_root(c, p.wi, p.beta, p.eps);
+    U[l] = -(laminar_F(r, p.beta, p.eps) - Fw) / (2.0 * p.wi * p.wi);
+    cxx[l] = 1.0 + 2.0 * r * r;
+    cxy[l] = r;
+  }
+  std::vector<double> up(F, 0.0), vp(F, 0.0), wp(F, 0.0);
+  for (int cc = 0; cc < 2; ++cc) {
+    for (int mx = 0; mx <= 4; ++mx) {
+      for (int mz = 0; mz <= 2; ++mz) {
+        if (mx == 0 && mz == 0) continue;
+        const double kx = 2.0 * kPi * mx / p.lx, kz = 2.0 * kPi * mz / p.lz;
+        double A[9], B[9];
+        for (int n = 0; n < 9; ++n) {
+          const uint64_t base = (uint64_t)((((cc * 5 + mx) * 3 + mz) * 9 + n) * 2);
+          A[n] = splitmix_uniform(seed, base + 0);
+          B[n] = splitmix_uniform(seed, base + 1);
+        }
+        for (int l = 0; l < ny; ++l) {
+          const double yy = y[l];
+          double T[9], Uc[9], dT[9];
+          T[0] = 1.0; T[1] = yy; Uc[0] = 1.0; Uc[1] = 2.0 * yy;
+          for (int n = 2; n < 9; ++n) { T[n] = 2 * yy * T[n - 1] - T[n - 2]; Uc[n] = 2 * yy * Uc[n - 1] - Uc[n - 2]; }
+          dT[0] = 0.0;
+          for (int n = 1; n < 9; ++n) dT[n] = n * Uc[n - 1];
+          double ga = 0, gb = 0, dga = 0, dgb = 0;
+          for (int n = 0; n < 9; ++n) { ga += A[n] * T[n]; gb += B[n] * T[n]; dga += A[n] * dT[n]; dgb += B[n] * dT[n]; }
+          const double w = (1 - yy * yy) * (1 - yy * yy), dw = -4.0 * yy * (1 - yy * yy);
+          const double pa = w * ga, pb = w * gb, dpa = dw * ga + w * dga, dpb = dw * gb + w * dgb;
+          for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < nx; ++j) {
+              double c, s;
+              cis((long long)mx * j * nz + (long long)mz * k * nx, (long long)nx * nz, &c, &s);
+              const size_t i = ((size_t)l * nz + k) * nx + j;
+              const double dy = dpa * c + dpb * s;        // d psi / dy
+              const double dh = -pa * s + pb * c;         // (d psi/dx)/kx = (d psi/dz)/kz
+              if (cc == 0) { up[i] += dy; vp[i] -= kx * dh; }
+              else { wp[i] += dy; vp[i] -= kz * dh; }
+            }
+        }
+      }
+    }
+  }
+  double mxv = 0.0;
+  for (size_t i = 0; i < F; ++i) mxv = std::fmax(mxv, std::sqrt(up[i] * up[i] + vp[i] * vp[i] + wp[i] * wp[i]));
+  const double sc = (mxv > 0.0) ? amp / mxv : 0.0;
+  for (int l = 0; l < ny; ++l)
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < nx; ++j) {
+        const size_t i = ((size_t)l * nz + k) * nx + j;
+        out[0 * F + i] = U[l] + sc * up[i];
+        out[1 * F + i] = sc * vp[i];
+        out[2 * F + i] = sc * wp[i];
+        out[3 * F + i] = cxx[l];
+        out[4 * F + i] = cxy[l];
+        out[5 * F + i] = 0.0;
+        out[6 * F + i] = 1.0;
+        out[7 * F + i] = 0.0;
+        out[8 * F + i] = 1.0;
+      }
+}
+
 // ------------------------------------------------------------- layout
 struct Carver {
   size_t off = 0;
@@ -232,14 +310,15 @@ struct Carver {
 };
 
 struct Group {
-  int nx, ny;
+  int nx, ny, nz;
   std::vector<int> members;  // global member ids
   GroupDev d{};
-  HostPlan hp[5];            // M, Mx, nx, Pu, Me
+  HostPlan hp[7];            // M, Mx, nx, Pu, Me, Mz, nz
 };
 
 int check_params(const ptt_params& p) {
-  if (p.nz != 1) return PTT_ENOTSUP;
+  if (p.nz != 1 && (p.nz < 4 || p.nz > 512 || (p.nz & 1) || !smooth235(p.nz))) return PTT_EINVAL;
+  if (p.nz > 1 && !(p.lz > 0)) return PTT_EINVAL;
   if (p.precision != PTT_FP64 && p.precision != PTT_MIXED) return PTT_ENOTSUP;
   if (p.nx < 8 || p.nx > 512 || (p.nx & 1) || !smooth235(p.nx)) return PTT_EINVAL;
   if (p.ny < 9 || p.ny > 513 || !smooth235(p.ny - 1)) return PTT_EINVAL;
@@ -253,11 +332,14 @@ int check_params(const ptt_params& p) {
 // products are alias-free for the retained Chebyshev modes (T_k aliases to
 // -T_{2M-k} on the Gauss points).  Diagnostic grid for the energy: Me >= 2 ny - 1
 // Gauss points (Fejer's first rule is exact to degree Me - 1 >= 2 ny - 2).
-void group_sizes(int nx, int ny, Group& g) {
+void group_sizes(int nx, int ny, int nz, Group& g) {
   GroupDev& d = g.d;
   d.nx = nx;
   d.K = nx / 2;
   d.N = ny;
+  d.nz = nz;
+  d.KZ = d.K * nz;
+  d.Mz = (nz > 1) ? next_smooth(3 * nz / 2 - 2) : 1;
   d.Mx = next_smooth(3 * nx / 2 - 2);
   int M = (3 * ny - 2 + 1) / 2;
   while ((M & 1) || !smooth235(M)) ++M;
@@ -282,6 +364,8 @@ void group_sizes(int nx, int ny, Group& g) {
   g.hp[2] = make_plan(nx);
   g.hp[3] = make_plan(d.Pu);
   g.hp[4] = make_plan(d.Me);
+  g.hp[5] = make_plan(d.Mz);
+  g.hp[6] = make_plan(nz);
 }
 
 // Carve (or, with base == nullptr, size) all device arrays.
@@ -293,53 +377,74 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     // columns per block: fit the shared-memory target, but leave at least
     // about two blocks per SM (152 SMs) for the column counts of each pass
     auto cap = [&](int c, int nfields) {
-      const int want = (int)((long long)d.K * nfields * nb / 304);
+      const int want = (int)((long long)d.KZ * nfields * nb / 304);
       return std::max(1, std::min(c, want));
     };
     d.Ccol = cap(d.Ccol, 9);
     d.CcolE = cap(d.CcolE, 2);
     d.CcolU = cap(d.CcolU, 1);
-    const size_t NK = (size_t)d.N * d.K, rows = (size_t)d.M, Je = (size_t)d.Me;
+    const bool d3 = d.nz > 1;
+    const size_t nf = d3 ? 9 : 5, ne = d3 ? 8 : 4;   // state fields, evolved quantities
+    const size_t NK = (size_t)d.N * d.KZ, rows = (size_t)d.M, Je = (size_t)d.Me;
+    const size_t KZ = d.KZ, K = d.K, nzz = d.nz;
     d.prm = cv.take<MemberPrm>(nb);
     d.status = cv.take<int>(nb);
     d.count = cv.take<long long>(nb);
-    d.X = cv.take<double2>((size_t)nb * 5 * NK);
-    d.Eh = cv.take<double2>((size_t)4 * nb * 4 * NK);
-    d.Nh = cv.take<double2>((size_t)4 * nb * 4 * NK);
-    if (d.f32) {
-      d.Yp = nullptr;
-      d.Zp = nullptr;
-      d.Ypf = cv.take<float2>((size_t)nb * 9 * rows * d.K);
-      d.Zpf = cv.take<float2>((size_t)nb * 5 * rows * d.K);
+    d.X = cv.take<double2>((size_t)nb * nf * NK);
+    d.Eh = cv.take<double2>((size_t)4 * nb * ne * NK);
+    d.Nh = cv.take<double2>((size_t)4 * nb * ne * NK);
+    d.Yp = d.Zp = nullptr;
+    d.Ypf = d.Zpf = nullptr;
+    d.Y3 = d.Z3 = d.W3 = d.V3 = nullptr;
+    d.Y3f = d.Z3f = d.W3f = d.V3f = nullptr;
+    if (!d3) {
+      if (d.f32) {
+        d.Ypf = cv.take<float2>((size_t)nb * 9 * rows * K);
+        d.Zpf = cv.take<float2>((size_t)nb * 5 * rows * K);
+      } else {
+        d.Yp = cv.take<double2>((size_t)nb * 9 * rows * K);
+        d.Zp = cv.take<double2>((size_t)nb * 5 * rows * K);
+      }
     } else {
-      d.Yp = cv.take<double2>((size_t)nb * 9 * rows * d.K);
-      d.Zp = cv.take<double2>((size_t)nb * 5 * rows * d.K);
-      d.Ypf = nullptr;
-      d.Zpf = nullptr;
+      const size_t yp = rows * KZ, zp = rows * d.Mz * K;
+      if (d.f32) {
+        d.Y3f = cv.take<float2>((size_t)nb * 17 * yp);
+        d.Z3f = cv.take<float2>((size_t)nb * 26 * zp);
+        d.W3f = cv.take<float2>((size_t)nb * 9 * zp);
+        d.V3f = cv.take<float2>((size_t)nb * 9 * yp);
+      } else {
+        d.Y3 = cv.take<double2>((size_t)nb * 17 * yp);
+        d.Z3 = cv.take<double2>((size_t)nb * 26 * zp);
+        d.W3 = cv.take<double2>((size_t)nb * 9 * zp);
+        d.V3 = cv.take<double2>((size_t)nb * 9 * yp);
+      }
     }
-    d.NR = cv.take<double2>((size_t)nb * 5 * NK);
+    d.NR = cv.take<double2>((size_t)nb * nf * NK);
     d.Rb = cv.take<double2>((size_t)nb * 4 * NK);
     d.qt = cv.take<double>((size_t)nb * 4 * 3 * 3 * NK);
-    d.qtG = cv.take<double>((size_t)nb * 4 * 3 * 2 * d.K);
+    d.qtG = cv.take<double>((size_t)nb * 4 * 3 * 2 * KZ);
     d.vh = cv.take<double>((size_t)nb * 4 * NK);
-    d.vhS = cv.take<double>((size_t)nb * 4 * 2 * d.K);
+    d.vhS = cv.take<double>((size_t)nb * 4 * 2 * KZ);
     d.wrow = cv.take<double>((size_t)3 * d.N);
     d.ccw = cv.take<double>(Je);
-    d.DY = cv.take<double2>((size_t)nb * 2 * Je * d.K);
+    d.DY = cv.take<double2>((size_t)nb * (d3 ? 3 : 2) * Je * KZ);
     d.DT = cv.take<double2>((size_t)nb * NK);
-    d.DV = cv.take<double>((size_t)nb * d.N * d.nx);
+    d.DV = cv.take<double>((size_t)nb * d.N * nzz * d.nx);
     d.part = cv.take<double>((size_t)nb * kTiles * kPart);
-    d.DM = cv.take<double2>((size_t)nb * 4 * d.K);
+    d.DM = cv.take<double2>((size_t)nb * (d3 ? 8 : 4) * KZ);
+    d.DZ = d3 ? cv.take<double2>(std::max((size_t)nb, (size_t)9) * d.N * nzz * K) : nullptr;
+    d.DMZ = d3 ? cv.take<double2>((size_t)nb * 8 * nzz * K) : nullptr;
+    d.MV = d3 ? cv.take<double>((size_t)nb * 8 * nzz * d.nx) : nullptr;
     d.ring = cv.take<ptt_diag>((size_t)nb * kRing);
-    d.stage = cv.take<double>((size_t)5 * d.N * d.nx);
-    d.stageS = cv.take<double2>((size_t)5 * NK);
-    FftPlan* pls[5] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe};
-    for (int i = 0; i < 5; ++i) {
+    d.stage = cv.take<double>((size_t)nf * d.N * nzz * d.nx);
+    d.stageS = cv.take<double2>((size_t)nf * NK);
+    FftPlan* pls[7] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe, &d.plMz, &d.plNz};
+    for (int i = 0; i < 7; ++i) {
       pls[i]->n = g.hp[i].n;
       pls[i]->nst = (int)g.hp[i].radix.size();
       for (int s = 0; s < pls[i]->nst; ++s) pls[i]->radix[s] = g.hp[i].radix[s];
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
-      pls[i]->twf = (d.f32 && i < 2) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
+      pls[i]->twf = (d.f32 && (i < 2 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
     }
     d.tw4P = cv.take<double2>((size_t)d.M);
     d.tw4Pf = d.f32 ? cv.take<float2>((size_t)d.M) : nullptr;
@@ -348,17 +453,18 @@ void carve(std::vector<Group>& groups, Carver& cv) {
 }
 
 std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
-  std::map<std::tuple<int, int, int>, int> idx;
+  std::map<std::tuple<int, int, int, int>, int> idx;
   std::vector<Group> groups;
   for (int i = 0; i < nmem; ++i) {
-    auto key = std::make_tuple(pm[i].nx, pm[i].ny, pm[i].precision);
+    auto key = std::make_tuple(pm[i].nx, pm[i].ny, pm[i].nz, pm[i].precision);
     auto it = idx.find(key);
     if (it == idx.end()) {
       idx[key] = (int)groups.size();
       Group g;
       g.nx = pm[i].nx;
       g.ny = pm[i].ny;
-      group_sizes(g.nx, g.ny, g);
+      g.nz = pm[i].nz;
+      group_sizes(g.nx, g.ny, g.nz, g);
       g.d.f32 = (pm[i].precision == PTT_MIXED) ? 1 : 0;
       groups.push_back(std::move(g));
       it = idx.find(key);
@@ -412,10 +518,12 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
   const int s = check_params(p);
   if (s) return s;
   if (p.precision != PTT_FP64) return PTT_ENOTSUP;
+  if (p.nz != 1) return PTT_ENOTSUP;
   Group g;
   g.nx = p.nx;
   g.ny = p.ny;
-  group_sizes(p.nx, p.ny, g);
+  g.nz = 1;
+  group_sizes(p.nx, p.ny, 1, g);
   d = g.d;
   d.nb = 1;
   FftPlan* pls[2] = {&d.plP, &d.plMx};
@@ -438,7 +546,7 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
     cis(k, 4LL * d.M, &cc, &ss);
     tw4[k] = make_double2(cc, -ss);
   }
-  prm.lx = p.lx; prm.re = p.re; prm.wi = p.wi; prm.beta = p.beta; prm.eps = p.eps;
+  prm.lx = p.lx; prm.lz = 1.0; prm.re = p.re; prm.wi = p.wi; prm.beta = p.beta; prm.eps = p.eps;
   prm.kappa = p.kappa; prm.dt = p.dt;
   prm.inv_wi = 1.0 / p.wi;
   prm.gam = (1.0 - p.beta) / (p.re * p.wi);
@@ -461,7 +569,9 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
   }
   std::vector<Group> groups = make_groups(pm, nmem);
   for (Group& g : groups) {
-    if (smem_xfused(g.d.Mx, g.d.f32) > 227 * 1024) return PTT_EINVAL;
+    if (g.d.nz == 1 && smem_xfused(g.d.Mx, g.d.f32) > 227 * 1024) return PTT_EINVAL;
+    if (g.d.nz > 1 && (smem_xfused3(g.d.Mx, g.d.f32) > 227 * 1024 || smem_spec3(g.d.N) > 227 * 1024))
+      return PTT_EINVAL;
   }
   Carver cv;
   carve(groups, cv);
@@ -491,14 +601,19 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   c->last_read.assign(nmem, -1);
   int optin = 0;
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-  for (Group& g : c->groups)
-    if (smem_xfused(g.d.Mx, g.d.f32) > (size_t)optin || smem_spec(g.d.N) > (size_t)optin) return PTT_EINVAL;
+  for (Group& g : c->groups) {
+    if (g.d.nz == 1 && (smem_xfused(g.d.Mx, g.d.f32) > (size_t)optin || smem_spec(g.d.N) > (size_t)optin))
+      return PTT_EINVAL;
+    if (g.d.nz > 1 && (smem_xfused3(g.d.Mx, g.d.f32) > (size_t)optin || smem_spec3(g.d.N) > (size_t)optin))
+      return PTT_EINVAL;
+  }
   CK(set_kernel_attributes(optin));
+  CK(set_kernel_attributes3(optin));
   CK(cudaMemsetAsync(d_ws, 0, need - 256, c->stream));
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     Group& g = c->groups[gi];
     GroupDev& d = g.d;
-    const int nb = d.nb, N = d.N, K = d.K;
+    const int nb = d.nb, N = d.N, K = d.KZ, nzz = d.nz;   // K: modes per Chebyshev index
     const size_t NK = (size_t)N * K;
     for (int i = 0; i < nb; ++i) c->where[g.members[i]] = {(int)gi, i};
     // member parameters
@@ -506,7 +621,8 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
     for (int i = 0; i < nb; ++i) {
       const ptt_params& p = pm[g.members[i]];
       MemberPrm& q = mp[i];
-      q.lx = p.lx; q.re = p.re; q.wi = p.wi; q.beta = p.beta; q.eps = p.eps;
+      q.lx = p.lx; q.lz = (p.nz > 1) ? p.lz : 1.0;
+      q.re = p.re; q.wi = p.wi; q.beta = p.beta; q.eps = p.eps;
       q.kappa = p.kappa; q.dt = p.dt;
       q.inv_wi = 1.0 / p.wi;
       q.gam = (1.0 - p.beta) / (p.re * p.wi);
@@ -533,7 +649,12 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
       for (int o = 0; o < 4; ++o) {
         const double a0dt = kSA0[o] / p.dt;
         for (int m = 0; m < K; ++m) {
-          const double km = 2.0 * kPi * m / p.lx, k2 = km * km;
+          // mode m = mx * nz + mz, mz in FFT order (signed wavenumber)
+          const int mx = m / nzz, mzi = m - mx * nzz;
+          const int sz = (mzi < nzz / 2) ? mzi : mzi - nzz;
+          const double kxm = 2.0 * kPi * mx / p.lx;
+          const double kzm = (nzz > 1) ? 2.0 * kPi * sz / p.lz : 0.0;
+          const double k2 = kxm * kxm + kzm * kzm;
           const double al[3] = {a0dt + p.kappa * k2, a0dt + nu * k2, k2};
           const double be[3] = {p.kappa, nu, 1.0};
           for (int ts = 0; ts < 3; ++ts) {
@@ -617,8 +738,8 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
       }
     }
     // twiddle tables
-    FftPlan* pls[5] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe};
-    for (int t = 0; t < 5; ++t) {
+    FftPlan* pls[7] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe, &d.plMz, &d.plNz};
+    for (int t = 0; t < 7; ++t) {
       const int n = pls[t]->n;
       std::vector<double2> tw(n);
       for (int k = 0; k < n; ++k) {
@@ -650,8 +771,9 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   for (size_t gi = 0; gi < c->groups.size() && !le; ++gi) {
     cudaStream_t gs = c->gstreams[gi];
     le = cudaStreamWaitEvent(gs, c->gevents.back(), 0);
-    if (!le) le = launch_step(c->groups[gi].d, gs, &nl);
-    if (!le) le = launch_diag(c->groups[gi].d, gs, &nl);
+    const GroupDev& gd = c->groups[gi].d;
+    if (!le) le = (gd.nz > 1) ? launch_step3(gd, gs, &nl) : launch_step(gd, gs, &nl);
+    if (!le) le = (gd.nz > 1) ? launch_diag3(gd, gs, &nl) : launch_diag(gd, gs, &nl);
     if (!le) le = cudaEventRecord(c->gevents[gi], gs);
     if (!le) le = cudaStreamWaitEvent(c->cap, c->gevents[gi], 0);
   }
@@ -671,10 +793,11 @@ static int member_ok(ptt_ctx* c, int member) {
 static int upload_phys(ptt_ctx* c, int member, const double* h) {
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
-  const size_t n = (size_t)5 * g.d.N * g.d.nx;
+  const bool d3 = g.d.nz > 1;
+  const size_t n = (size_t)(d3 ? 9 : 5) * g.d.N * g.d.nz * g.d.nx;
   CK(cudaMemcpyAsync(g.d.stage, h, n * 8, cudaMemcpyHostToDevice, c->stream));
-  CK(launch_phys_to_state(g.d, b, c->stream));
-  CK(launch_diag(g.d, c->stream, nullptr));
+  CK(d3 ? launch_phys_to_state3(g.d, b, c->stream) : launch_phys_to_state(g.d, b, c->stream));
+  CK(d3 ? launch_diag3(g.d, c->stream, nullptr) : launch_diag(g.d, c->stream, nullptr));
   CK(cudaStreamSynchronize(c->stream));
   c->last_read[member] = -1;
   return PTT_OK;
@@ -683,7 +806,8 @@ static int upload_phys(ptt_ctx* c, int member, const double* h) {
 int ptt_init_state(ptt_ctx* c, int32_t member, uint64_t seed, double amplitude) {
   if (!member_ok(c, member) || !(amplitude >= 0)) return PTT_EINVAL;
   std::vector<double> f;
-  initial_fields(c->prm[member], seed, amplitude, f);
+  if (c->prm[member].nz > 1) initial_fields3(c->prm[member], seed, amplitude, f);
+  else initial_fields(c->prm[member], seed, amplitude, f);
   return upload_phys(c, member, f.data());
 }
 
@@ -696,8 +820,10 @@ int ptt_get_state(ptt_ctx* c, int32_t member, double* h) {
   if (!member_ok(c, member) || !h) return PTT_EINVAL;
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
-  CK(launch_state_to_phys(g.d, b, c->stream));
-  CK(cudaMemcpyAsync(h, g.d.stage, (size_t)5 * g.d.N * g.d.nx * 8, cudaMemcpyDeviceToHost, c->stream));
+  const bool d3 = g.d.nz > 1;
+  CK(d3 ? launch_state_to_phys3(g.d, b, c->stream) : launch_state_to_phys(g.d, b, c->stream));
+  CK(cudaMemcpyAsync(h, g.d.stage, (size_t)(d3 ? 9 : 5) * g.d.N * g.d.nz * g.d.nx * 8,
+                     cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return PTT_OK;
 }
@@ -706,11 +832,13 @@ int ptt_set_spectral(ptt_ctx* c, int32_t member, const double* h) {
   if (!member_ok(c, member) || !h) return PTT_EINVAL;
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
-  const size_t NK = (size_t)g.d.N * g.d.K;
-  CK(cudaMemcpyAsync(g.d.stageS, h, 5 * NK * 16, cudaMemcpyHostToDevice, c->stream));
-  CK(launch_transpose(g.d.stageS, g.d.X + (size_t)b * 5 * NK, 5, g.d.N, g.d.K, c->stream));
-  CK(launch_reset_member(g.d, b, c->stream));
-  CK(launch_diag(g.d, c->stream, nullptr));
+  const bool d3 = g.d.nz > 1;
+  const int nf = d3 ? 9 : 5;
+  const size_t NK = (size_t)g.d.N * g.d.KZ;
+  CK(cudaMemcpyAsync(g.d.stageS, h, nf * NK * 16, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_transpose(g.d.stageS, g.d.X + (size_t)b * nf * NK, nf, g.d.N, g.d.KZ, c->stream));
+  CK(d3 ? launch_reset_member3(g.d, b, c->stream) : launch_reset_member(g.d, b, c->stream));
+  CK(d3 ? launch_diag3(g.d, c->stream, nullptr) : launch_diag(g.d, c->stream, nullptr));
   CK(cudaStreamSynchronize(c->stream));
   c->last_read[member] = -1;
   return PTT_OK;
@@ -720,9 +848,10 @@ int ptt_get_spectral(ptt_ctx* c, int32_t member, double* h) {
   if (!member_ok(c, member) || !h) return PTT_EINVAL;
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
-  const size_t NK = (size_t)g.d.N * g.d.K;
-  CK(launch_transpose(g.d.X + (size_t)b * 5 * NK, g.d.stageS, 5, g.d.K, g.d.N, c->stream));
-  CK(cudaMemcpyAsync(h, g.d.stageS, 5 * NK * 16, cudaMemcpyDeviceToHost, c->stream));
+  const int nf = (g.d.nz > 1) ? 9 : 5;
+  const size_t NK = (size_t)g.d.N * g.d.KZ;
+  CK(launch_transpose(g.d.X + (size_t)b * nf * NK, g.d.stageS, nf, g.d.KZ, g.d.N, c->stream));
+  CK(cudaMemcpyAsync(h, g.d.stageS, nf * NK * 16, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return PTT_OK;
 }
@@ -731,11 +860,14 @@ int ptt_explicit_rhs(ptt_ctx* c, int32_t member, double* h) {
   if (!member_ok(c, member) || !h) return PTT_EINVAL;
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
-  const size_t NK = (size_t)g.d.N * g.d.K;
-  CK(launch_explicit(g.d, c->stream));
-  CK(launch_transpose(g.d.NR + (size_t)b * 5 * NK, g.d.stageS, 3, g.d.K, g.d.N, c->stream));
-  CK(launch_transpose(g.d.Rb + (size_t)b * 4 * NK, g.d.stageS + 3 * NK, 2, g.d.K, g.d.N, c->stream));
-  CK(cudaMemcpyAsync(h, g.d.stageS, 5 * NK * 16, cudaMemcpyDeviceToHost, c->stream));
+  const bool d3 = g.d.nz > 1;
+  const int nf = d3 ? 9 : 5, nc = d3 ? 6 : 3;
+  const size_t NK = (size_t)g.d.N * g.d.KZ;
+  CK(d3 ? launch_explicit3(g.d, c->stream) : launch_explicit(g.d, c->stream));
+  CK(launch_transpose(g.d.NR + (size_t)b * nf * NK, g.d.stageS, nc, g.d.KZ, g.d.N, c->stream));
+  CK(launch_transpose(g.d.Rb + (size_t)b * 4 * NK, g.d.stageS + nc * NK, nf - nc, g.d.KZ, g.d.N,
+                      c->stream));
+  CK(cudaMemcpyAsync(h, g.d.stageS, nf * NK * 16, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return PTT_OK;
 }
@@ -780,8 +912,9 @@ int ptt_diagnostics(ptt_ctx* c, int32_t member, ptt_diag* out, int32_t maxr, int
 }
 
 static size_t ckpt_bytes(const Group& g) {
-  const size_t NK = (size_t)g.d.N * g.d.K;
-  return 64 + (5 + 16 + 16) * NK * 16;
+  const size_t NK = (size_t)g.d.N * g.d.KZ;
+  const size_t nf = (g.d.nz > 1) ? 9 : 5, ne = (g.d.nz > 1) ? 8 : 4;
+  return 64 + (nf + 8 * ne) * NK * 16;
 }
 
 int ptt_checkpoint_size(ptt_ctx* c, int32_t member, size_t* bytes) {
@@ -795,10 +928,11 @@ int ptt_get_checkpoint(ptt_ctx* c, int32_t member, void* h, size_t bytes) {
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
   if (bytes < ckpt_bytes(g)) return PTT_EINVAL;
-  const size_t NK = (size_t)g.d.N * g.d.K, nb = g.d.nb;
+  const size_t NK = (size_t)g.d.N * g.d.KZ, nb = g.d.nb;
+  const size_t nf = (g.d.nz > 1) ? 9 : 5, ne = (g.d.nz > 1) ? 8 : 4;
   char* p = (char*)h;
   CK(cudaStreamSynchronize(c->stream));
-  int64_t hdr[8] = {0x70747463, g.d.nx, g.d.N, 0, 0, 0, 0, 0};
+  int64_t hdr[8] = {0x70747463, g.d.nx, g.d.N, 0, 0, g.d.nz, 0, 0};
   long long cnt;
   int st;
   CK(cudaMemcpy(&cnt, g.d.count + b, 8, cudaMemcpyDeviceToHost));
@@ -807,13 +941,13 @@ int ptt_get_checkpoint(ptt_ctx* c, int32_t member, void* h, size_t bytes) {
   hdr[4] = st;
   std::memcpy(p, hdr, 64);
   p += 64;
-  CK(cudaMemcpy(p, g.d.X + b * 5 * NK, 5 * NK * 16, cudaMemcpyDeviceToHost));
-  p += 5 * NK * 16;
+  CK(cudaMemcpy(p, g.d.X + b * nf * NK, nf * NK * 16, cudaMemcpyDeviceToHost));
+  p += nf * NK * 16;
   for (int s = 0; s < 4; ++s) {
-    CK(cudaMemcpy(p, g.d.Eh + ((size_t)s * nb + b) * 4 * NK, 4 * NK * 16, cudaMemcpyDeviceToHost));
-    p += 4 * NK * 16;
-    CK(cudaMemcpy(p, g.d.Nh + ((size_t)s * nb + b) * 4 * NK, 4 * NK * 16, cudaMemcpyDeviceToHost));
-    p += 4 * NK * 16;
+    CK(cudaMemcpy(p, g.d.Eh + ((size_t)s * nb + b) * ne * NK, ne * NK * 16, cudaMemcpyDeviceToHost));
+    p += ne * NK * 16;
+    CK(cudaMemcpy(p, g.d.Nh + ((size_t)s * nb + b) * ne * NK, ne * NK * 16, cudaMemcpyDeviceToHost));
+    p += ne * NK * 16;
   }
   return PTT_OK;
 }
@@ -823,24 +957,25 @@ int ptt_set_checkpoint(ptt_ctx* c, int32_t member, const void* h, size_t bytes) 
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
   if (bytes < ckpt_bytes(g)) return PTT_EINVAL;
-  const size_t NK = (size_t)g.d.N * g.d.K, nb = g.d.nb;
+  const size_t NK = (size_t)g.d.N * g.d.KZ, nb = g.d.nb;
+  const size_t nf = (g.d.nz > 1) ? 9 : 5, ne = (g.d.nz > 1) ? 8 : 4;
   const char* p = (const char*)h;
   int64_t hdr[8];
   std::memcpy(hdr, p, 64);
-  if (hdr[0] != 0x70747463 || hdr[1] != g.d.nx || hdr[2] != g.d.N) return PTT_EINVAL;
+  if (hdr[0] != 0x70747463 || hdr[1] != g.d.nx || hdr[2] != g.d.N || hdr[5] != g.d.nz) return PTT_EINVAL;
   p += 64;
   CK(cudaStreamSynchronize(c->stream));
   long long cnt = hdr[3];
   int st = (int)hdr[4];
   CK(cudaMemcpy(g.d.count + b, &cnt, 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(g.d.status + b, &st, 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(g.d.X + b * 5 * NK, p, 5 * NK * 16, cudaMemcpyHostToDevice));
-  p += 5 * NK * 16;
+  CK(cudaMemcpy(g.d.X + b * nf * NK, p, nf * NK * 16, cudaMemcpyHostToDevice));
+  p += nf * NK * 16;
   for (int s = 0; s < 4; ++s) {
-    CK(cudaMemcpy(g.d.Eh + ((size_t)s * nb + b) * 4 * NK, p, 4 * NK * 16, cudaMemcpyHostToDevice));
-    p += 4 * NK * 16;
-    CK(cudaMemcpy(g.d.Nh + ((size_t)s * nb + b) * 4 * NK, p, 4 * NK * 16, cudaMemcpyHostToDevice));
-    p += 4 * NK * 16;
+    CK(cudaMemcpy(g.d.Eh + ((size_t)s * nb + b) * ne * NK, p, ne * NK * 16, cudaMemcpyHostToDevice));
+    p += ne * NK * 16;
+    CK(cudaMemcpy(g.d.Nh + ((size_t)s * nb + b) * ne * NK, p, ne * NK * 16, cudaMemcpyHostToDevice));
+    p += ne * NK * 16;
   }
   c->last_read[member] = cnt;
   return PTT_OK;
@@ -857,7 +992,8 @@ int ptt_time_stages(ptt_ctx* c, int32_t nsteps, double* ms) {
       cudaEvent_t* E = &ev[(size_t)gi * (PTT_NSTAGES + 1)];
       cudaError_t e = cudaEventRecord(E[0], c->stream);
       for (int s = 0; s < PTT_NSTAGES && !e; ++s) {
-        e = launch_stage(c->groups[gi].d, s, c->stream, nullptr);
+        const GroupDev& gd = c->groups[gi].d;
+        e = (gd.nz > 1) ? launch_stage3(gd, s, c->stream, nullptr) : launch_stage(gd, s, c->stream, nullptr);
         if (!e) e = cudaEventRecord(E[s + 1], c->stream);
       }
       if (e) { rc = fail_cuda(e, "ptt_time_stages launch", __LINE__); break; }
@@ -885,6 +1021,24 @@ int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) 
   for (int s = 0; s < PTT_NSTAGES; ++s) { flops[s] = 0.0; bytes[s] = 0.0; launches[s] = 0; }
   for (Group& g : c->groups) {
     const GroupDev& d = g.d;
+    if (d.nz > 1) {   // 3D
+      const double nb = d.nb, K = d.K, KZ = d.KZ, N = d.N, NK = N * KZ, M = d.M, Mz = d.Mz, Je = d.Me;
+      const double z = 16.0;
+      flops[0] += nb * (17.0 * KZ * (fft(M) + 8.0 * M) + 8.0 * KZ * N * 4.0 + 26.0 * M * K * fft(Mz));
+      bytes[0] += nb * z * (9.0 * NK + 26.0 * M * Mz * K);
+      flops[1] += nb * M * Mz * (23.0 * fft(d.Mx) + 200.0 * d.Mx);
+      bytes[1] += nb * z * (26.0 + 9.0) * M * Mz * K;
+      flops[2] += nb * (9.0 * M * K * fft(Mz) + 9.0 * KZ * (fft(M) + 8.0 * M));
+      bytes[2] += nb * z * (9.0 * M * Mz * K + 9.0 * NK);
+      flops[3] += nb * NK * (8.0 * 4.0 + 8.0 * 4.0 * 8.0 + 16.0 * 24.0 / 2.0);
+      bytes[3] += nb * (z * NK * (9.0 + 9.0 + 64.0 + 16.0 + 9.0) + 8.0 * NK * 10.0);
+      flops[4] += nb * (KZ * fft(d.Pu) + N * K * fft(d.nz) + N * d.nz * fft(d.nx) +
+                        3.0 * KZ * (fft(Je) + 8.0 * Je) + 8.0 * Je * KZ * 3.0);
+      bytes[4] += nb * (z * (9.0 * NK + 3.0 * 2.0 * Je * KZ) + 8.0 * 2.0 * N * d.nz * d.nx);
+      const int nl3[PTT_NSTAGES] = {4, 1, 3, 2, 10};
+      for (int s = 0; s < PTT_NSTAGES; ++s) launches[s] += nl3[s];
+      continue;
+    }
     const double nb = d.nb, K = d.K, N = d.N, NK = N * K, rows = d.M, Je = d.Me;
     const double z = 16.0, r = 8.0;  // bytes of a complex / real double
     // 0: 9 complex columns, DCT-III on the M Gauss points (one FFT of M) + 4 d/dy

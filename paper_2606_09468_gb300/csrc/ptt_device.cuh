@@ -1,0 +1,714 @@
+// Device building blocks shared by the 2D and 3D kernels of the sPTT channel
+// step: complex arithmetic in double and single precision, mixed-radix
+// Stockham FFTs in shared memory, SBDF coefficients, warp-cooperative
+// Chebyshev recurrences and quasi-tridiagonal tau sweeps, the Chebyshev
+// column transforms (Gauss and Gauss-Lobatto grids) and the Fourier row
+// transforms.  Included by each kernel translation unit (internal linkage).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ptt_internal.h"
+
+namespace ptt {
+namespace {
+
+// ------------------------------------------------------------ complex math
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscl(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 mul_i(double2 a) { return make_double2(-a.y, a.x); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cfma(double s, double2 a, double2 c) {  // s*a + c
+  return make_double2(fma(s, a.x, c.x), fma(s, a.y, c.y));
+}
+__device__ __forceinline__ double2 czero() { return make_double2(0.0, 0.0); }
+
+// single precision twins (mixed-precision transforms)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscl(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cfma(float s, float2 a, float2 c) {
+  return make_float2(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y));
+}
+
+template <typename C2> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+template <typename C2> __device__ __forceinline__ C2 zero2();
+template <> __device__ __forceinline__ double2 zero2<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 zero2<float2>() { return make_float2(0.f, 0.f); }
+template <typename D> __device__ __forceinline__ D cvt2(double2 v);
+template <typename D> __device__ __forceinline__ D cvt2(float2 v);
+template <> __device__ __forceinline__ double2 cvt2<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 cvt2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <> __device__ __forceinline__ double2 cvt2<double2>(float2 v) { return make_double2(v.x, v.y); }
+template <> __device__ __forceinline__ float2 cvt2<float2>(float2 v) { return v; }
+
+// ------------------------------------------------------------ radix DFTs
+// DIR = -1: exp(-2 pi i jk/R) (forward); DIR = +1: exp(+2 pi i jk/R).
+template <int DIR, int R> struct Bfly;
+
+template <int DIR> struct Bfly<DIR, 2> {
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    C2 t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+  }
+};
+
+template <int DIR> struct Bfly<DIR, 4> {
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    C2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    C2 s13 = cadd(v[1], v[3]), d13 = mul_i(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    if (DIR < 0) { v[1] = csub(d02, d13); v[3] = cadd(d02, d13); }
+    else         { v[1] = cadd(d02, d13); v[3] = csub(d02, d13); }
+  }
+};
+
+template <int DIR> struct Bfly<DIR, 3> {
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    using T = typename RealOf<C2>::T;
+    const T s = (T)(DIR * 0.86602540378443864676);  // sin(2 pi / 3), signed
+    C2 t1 = cadd(v[1], v[2]);
+    C2 it2 = mul_i(csub(v[1], v[2]));
+    C2 m = cfma((T)-0.5, t1, v[0]);
+    v[0] = cadd(v[0], t1);
+    v[1] = cfma(s, it2, m);
+    v[2] = cfma(-s, it2, m);
+  }
+};
+
+template <int DIR> struct Bfly<DIR, 5> {
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    using T = typename RealOf<C2>::T;
+    const T c1 = (T)0.30901699437494742410;   // cos(2 pi / 5)
+    const T c2 = (T)-0.80901699437494742410;  // cos(4 pi / 5)
+    const T s1 = (T)(DIR * 0.95105651629515357212);  // sin(2 pi / 5), signed
+    const T s2 = (T)(DIR * 0.58778525229247312917);  // sin(4 pi / 5), signed
+    C2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    C2 t3 = mul_i(csub(v[1], v[4])), t4 = mul_i(csub(v[2], v[3]));
+    C2 b1 = cfma(c1, t1, cfma(c2, t2, v[0]));
+    C2 b2 = cfma(c2, t1, cfma(c1, t2, v[0]));
+    C2 e1 = cfma(s1, t3, cscl(t4, s2));
+    C2 e2 = cfma(s2, t3, cscl(t4, -s1));
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = cadd(b1, e1);
+    v[4] = csub(b1, e1);
+    v[2] = cadd(b2, e2);
+    v[3] = csub(b2, e2);
+  }
+};
+
+// One Stockham pass of radix R over nl lines (line l at offset l*ls).
+template <int DIR, int R, typename C2>
+__device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restrict__ dst,
+                                         int nl, int ls, int n, int Ns,
+                                         const C2* __restrict__ tw) {
+  const int nb = n / R;
+  const int st = n / (Ns * R);
+  const int total = nl * nb;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int l = t / nb;
+    const int j = t - l * nb;
+    const C2* s = src + l * ls;
+    C2* d = dst + l * ls;
+    const int jm = j % Ns;
+    C2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[j + r * nb];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C2 w = __ldg(&tw[jm * r * st]);
+        if (DIR > 0) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    Bfly<DIR, R>::run(v);
+    const int o = (j / Ns) * Ns * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[o + r * Ns] = v[r];
+  }
+}
+
+template <typename C2> __device__ __forceinline__ const C2* plan_tw(const FftPlan& pl);
+template <> __device__ __forceinline__ const double2* plan_tw<double2>(const FftPlan& pl) { return pl.tw; }
+template <> __device__ __forceinline__ const float2* plan_tw<float2>(const FftPlan& pl) { return pl.twf; }
+
+// Unnormalised DFT of nl lines of length pl.n held in `a`, using `b` as the
+// ping-pong buffer.  Returns the buffer holding the result.  Must be called
+// by the whole block after a __syncthreads(); ends with one.
+template <int DIR, typename C2>
+__device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl) {
+  C2* src = a;
+  C2* dst = b;
+  const C2* tw = plan_tw<C2>(pl);
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int R = pl.radix[s];
+    switch (R) {
+      case 2: fft_pass<DIR, 2>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      case 3: fft_pass<DIR, 3>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      case 4: fft_pass<DIR, 4>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      default: fft_pass<DIR, 5>(src, dst, nl, ls, pl.n, Ns, tw); break;
+    }
+    __syncthreads();
+    Ns *= R;
+    C2* t = src; src = dst; dst = t;
+  }
+  return src;
+}
+
+// SBDF coefficients, orders 1..4: a_0..a_4 and b_0..b_3 (Sec. 2: 4th-order
+// semi-implicit BDF; lower orders start the history).
+__constant__ double c_sa[4][5] = {{1.0, -1.0, 0.0, 0.0, 0.0},
+                                  {1.5, -2.0, 0.5, 0.0, 0.0},
+                                  {11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0, 0.0},
+                                  {25.0 / 12.0, -4.0, 3.0, -4.0 / 3.0, 0.25}};
+__constant__ double c_sb[4][4] = {{1.0, 0.0, 0.0, 0.0},
+                                  {2.0, -1.0, 0.0, 0.0},
+                                  {3.0, -3.0, 1.0, 0.0},
+                                  {4.0, -6.0, 4.0, -1.0}};
+
+// ------------------------------------------- warp-cooperative recurrences
+// FP64 runs at a few lanes per clock per SM on this part, so a warp FP64
+// instruction costs the same pipe time whether 1 or 32 lanes are active.
+// The Chebyshev recurrences and the tau sweeps are therefore written as
+// warp scans: each lane takes a contiguous chunk, composes it sequentially,
+// and the chunks are combined with shuffles.
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxChunk = 8;  // tau sweeps: up to 8 rows per lane (ny <= 513)
+
+__device__ __forceinline__ double2 shfl_down2(double2 v, int o) {
+  return make_double2(__shfl_down_sync(kFull, v.x, o), __shfl_down_sync(kFull, v.y, o));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v, int o) {
+  return make_float2(__shfl_down_sync(kFull, v.x, o), __shfl_down_sync(kFull, v.y, o));
+}
+__device__ __forceinline__ double2 shfl_up2(double2 v, int o) {
+  return make_double2(__shfl_up_sync(kFull, v.x, o), __shfl_up_sync(kFull, v.y, o));
+}
+__device__ __forceinline__ double2 warp_allsum2(double2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(kFull, v.x, o);
+    v.y += __shfl_xor_sync(kFull, v.y, o);
+  }
+  return v;
+}
+
+// Chebyshev derivative by one warp: out_n = (2/c_n) sum_{p > n, p + n odd} p a_p
+// (c_0 = 2), as two same-parity suffix sums T(k) = sum_{p >= k, p = k mod 2} p a_p
+// with out_{k-1} = (2/c_{k-1}) T(k).  `out` must not alias `a`.
+template <typename C2>
+__device__ void warp_cheb_deriv(const C2* a, C2* out, int N) {
+  using T = typename RealOf<C2>::T;
+  const int lane = threadIdx.x & 31;
+  for (int par = 0; par < 2; ++par) {
+    const int L = (N - par + 1) / 2;
+    const int c = (L + 31) / 32;
+    const int i0 = min(lane * c, L), i1 = min(i0 + c, L);
+    C2 acc = zero2<C2>();
+    for (int i = i1 - 1; i >= i0; --i) {
+      const int k = par + 2 * i;
+      acc = cfma((T)k, a[k], acc);
+      if (k >= 1) out[k - 1] = cscl(acc, (T)(k == 1 ? 1 : 2));
+    }
+    C2 inc = acc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const C2 v = shfl_down2(inc, o);
+      if (lane + o < 32) inc = cadd(inc, v);
+    }
+    C2 ex = shfl_down2(inc, 1);
+    if (lane == 31) ex = zero2<C2>();
+    for (int i = i0; i < i1; ++i) {
+      const int k = par + 2 * i;
+      if (k >= 1) out[k - 1] = cfma((T)(k == 1 ? 1 : 2), ex, out[k - 1]);
+    }
+  }
+  if (lane == 0) out[N - 1] = zero2<C2>();
+  __syncwarp();
+}
+
+// Warp-cooperative quasi-tridiagonal tau solve (system stated at k_spec): the backward
+// elimination P_i = alpha_i + beta_i P_{i+1} and the forward substitution
+// a_i = P_i + Q_i a_{i-1} are affine recurrences, evaluated as warp scans of
+// affine maps; the boundary sums are warp reductions.  `out` may alias R.
+__device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, double2* out,
+                              const double* Q, const double* inv, const double* F, double G,
+                              const double* w1, const double* w2, const double* w3,
+                              double bcfac, double rsign) {
+  const int lane = threadIdx.x & 31;
+  const int L = (N - p + 1) / 2;  // unknowns a_{p+2i}, i < L; rows i = 1..L-1
+  const int nr = L - 1;
+  const int c = (nr + 31) / 32;
+  const int i0 = min(1 + lane * c, L), i1 = min(i0 + c, L);
+  double2 al[kMaxChunk];
+  double be[kMaxChunk];
+  double2 rs = czero();
+#pragma unroll
+  for (int t = 0; t < kMaxChunk; ++t) {
+    const int i = i0 + t;
+    if (t < c && i < i1) {
+      const int n = p + 2 * i;
+      const double2 Rm2 = cscl(R[n - 2], rsign);
+      const double2 R0 = cscl(R[n], rsign);
+      const double cc = (n == 2) ? 2.0 : 1.0;
+      double2 r = cscl(Rm2, -cc * w1[n]);
+      if (n <= N - 3) r = cfma(w2[n], R0, r);
+      double un = 0.0;
+      if (n <= N - 5) {
+        r = cfma(-w3[n], cscl(R[n + 2], rsign), r);
+        un = -alpha * w3[n];
+      }
+      al[t] = cscl(r, inv[n]);
+      be[t] = -un * inv[n];
+      rs = cadd(rs, R0);
+    } else {
+      al[t] = czero();
+      be[t] = 1.0;
+    }
+  }
+  if (lane == 0) rs = cadd(rs, cscl(R[p], rsign));
+  __syncwarp();
+  // backward: chunk map P_{i0} = A + B P_{i1}
+  double2 A = czero();
+  double B = 1.0;
+#pragma unroll
+  for (int t = kMaxChunk - 1; t >= 0; --t) {
+    if (t < c && i0 + t < i1) {
+      A = cfma(be[t], A, al[t]);
+      B *= be[t];
+    }
+  }
+  double2 SA = A;
+  double SB = B;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double2 hA = shfl_down2(SA, o);
+    const double hB = __shfl_down_sync(kFull, SB, o);
+    if (lane + o < 32) {
+      SA = cfma(SB, hA, SA);
+      SB *= hB;
+    }
+  }
+  double2 Pin = shfl_down2(SA, 1);
+  if (lane == 31) Pin = czero();
+  double2 U = czero();
+  double2 P = Pin;
+#pragma unroll
+  for (int t = kMaxChunk - 1; t >= 0; --t) {
+    const int i = i0 + t;
+    if (t < c && i < i1) {
+      const int n = p + 2 * i;
+      P = cfma(be[t], P, al[t]);
+      out[n] = P;
+      U = cfma(F[n], P, U);
+    }
+  }
+  U = warp_allsum2(U);
+  rs = warp_allsum2(rs);
+  const double2 a0 = cscl(csub(cscl(rs, bcfac), U), G);
+  // forward: chunk map a_{i1-1} = C + D a_{i0-1}
+  double2 Cc = czero();
+  double Dd = 1.0;
+  double2 Pv[kMaxChunk];
+  double Qv[kMaxChunk];
+#pragma unroll
+  for (int t = 0; t < kMaxChunk; ++t) {
+    const int i = i0 + t;
+    if (t < c && i < i1) {
+      const int n = p + 2 * i;
+      Pv[t] = out[n];
+      Qv[t] = Q[n];
+      Cc = cfma(Qv[t], Cc, Pv[t]);
+      Dd *= Qv[t];
+    }
+  }
+  double2 IC = Cc;
+  double ID = Dd;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double2 hC = shfl_up2(IC, o);
+    const double hD = __shfl_up_sync(kFull, ID, o);
+    if (lane >= o) {
+      IC = cfma(ID, hC, IC);
+      ID *= hD;
+    }
+  }
+  double2 EC = shfl_up2(IC, 1);
+  double ED = __shfl_up_sync(kFull, ID, 1);
+  if (lane == 0) { EC = czero(); ED = 1.0; }
+  double2 av = cfma(ED, a0, EC);
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < kMaxChunk; ++t) {
+    const int i = i0 + t;
+    if (t < c && i < i1) {
+      av = cfma(Qv[t], av, Pv[t]);
+      out[p + 2 * i] = av;
+    }
+  }
+  if (lane == 0) out[p] = a0;
+  __syncwarp();
+}
+
+// ---------------------------------------------- per-mode spectral stage
+// ------------------------------------------------------ Chebyshev columns
+// Column transforms along y for a batch of members and fields.  Coefficient
+// side: column m, row n at m*cm + n*cn; value side: column m, row j at
+// m*vm + j*vj (within one field of one member).  Input and output may be in
+// double or single precision independently of the compute type.
+struct YJob {
+  const void* src;
+  void* dst;
+  long long src_mstride, dst_mstride;  // per member (elements)
+  long long src_fstride, dst_fstride;  // per field (elements)
+  int src_field[8];
+  int src_field2[8];  // inverse only: >= 0 adds this field to src_field
+  int src_field3[8];  // inverse only: >= 0 adds a third field
+  int dst_field[8];
+  int deriv[8];       // inverse only: transform d/dy of the field
+  long long cm, cn;   // coefficient-side strides
+  long long vm, vj;   // value-side strides
+  int K;              // columns
+  int N, M;           // Chebyshev modes, grid intervals / points
+  int inverse;        // 1: coefficients -> values; 0: values -> coefficients (N rows)
+  int gauss;          // 0: M+1 Gauss-Lobatto points (DCT-I, FFT length 2M);
+                      // 1: M Gauss points (DCT-II/III, FFT length M, M even)
+  int src_f32, dst_f32;  // element types of src / dst (0: complex double, 1: complex float)
+  const double2* tw4;    // gauss: tw4[k] = exp(-i pi k / (2M)), k < M
+  const float2* tw4f;    // the same in single precision
+  int C;              // columns per block
+  const int* status;  // skip members with status != 0 (may be null)
+  FftPlan pl;
+};
+
+template <typename CT>
+__device__ __forceinline__ CT ld2(const void* p, long long i, int f32) {
+  return f32 ? cvt2<CT>(static_cast<const float2*>(p)[i]) : cvt2<CT>(static_cast<const double2*>(p)[i]);
+}
+template <typename CT>
+__device__ __forceinline__ void st2(void* p, long long i, int f32, CT v) {
+  if (f32) static_cast<float2*>(p)[i] = cvt2<float2>(v);
+  else static_cast<double2*>(p)[i] = cvt2<double2>(v);
+}
+template <typename CT> __device__ __forceinline__ CT ld_tw4(const YJob& J, int k);
+template <> __device__ __forceinline__ double2 ld_tw4<double2>(const YJob& J, int k) { return __ldg(&J.tw4[k]); }
+template <> __device__ __forceinline__ float2 ld_tw4<float2>(const YJob& J, int k) { return __ldg(&J.tw4f[k]); }
+
+// Values at the M Gauss points y_j = cos(pi (2j+1)/(2M)) from coefficients
+// (DCT-III) and back (DCT-II), each as one complex FFT of length M: the
+// output (input) order is permuted v_n = f_{2n}, v_{M-1-n} = f_{2n+1}, and a
+// quarter-period twiddle exp(-+ i pi k/(2M)) maps between the two (Makhoul's
+// construction; the real and imaginary parts of a column ride in one FFT).
+template <typename CT>
+__device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, const void* src3,
+                            void* dst, CT* A, CT* B, int c0, int nc) {
+  using T = typename RealOf<CT>::T;
+  const int C = J.C, N = J.N, Mg = J.M;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int f = blockIdx.y;
+  if (J.inverse) {
+    for (int i = tid; i < Mg * C; i += nt) {
+      const int c = i / Mg, n = i - c * Mg;
+      CT v = zero2<CT>();
+      if (c < nc && n < N) {
+        const long long o = (c0 + c) * J.cm + n * J.cn;
+        v = ld2<CT>(src, o, J.src_f32);
+        if (src2) v = cadd(v, ld2<CT>(src2, o, J.src_f32));
+        if (src3) v = cadd(v, ld2<CT>(src3, o, J.src_f32));
+      }
+      A[i] = v;
+    }
+    __syncthreads();
+    if (J.deriv[f]) {
+      for (int c = tid >> 5; c < C; c += (nt >> 5)) warp_cheb_deriv(A + c * Mg, B + c * Mg, N);
+      __syncthreads();
+      for (int i = tid; i < N * C; i += nt) {
+        const int c = i / N, n = i - c * N;
+        A[c * Mg + n] = B[c * Mg + n];
+      }
+      __syncthreads();
+    }
+    // V_0 = a_0, V_k = (1/2) exp(+i pi k/(2M)) (a_k - i a_{M-k})
+    for (int i = tid; i < Mg * C; i += nt) {
+      const int c = i / Mg, k = i - c * Mg;
+      const CT ak = A[i];
+      CT V;
+      if (k == 0) {
+        V = ak;
+      } else {
+        const CT amk = A[c * Mg + Mg - k];
+        const CT w = cconj(ld_tw4<CT>(J, k));
+        V = cscl(cmul(w, csub(ak, mul_i(amk))), (T)0.5);
+      }
+      B[i] = V;
+    }
+    __syncthreads();
+    CT* res = fft_lines<+1>(B, A, C, Mg, J.pl);
+    for (int i = tid; i < Mg * C; i += nt) {
+      const int j = i / C, c = i - j * C;
+      if (c < nc) {
+        const int pos = (j & 1) ? (Mg - 1 - (j >> 1)) : (j >> 1);
+        st2<CT>(dst, j * J.vj + (c0 + c) * J.vm, J.dst_f32, res[c * Mg + pos]);
+      }
+    }
+  } else {
+    for (int i = tid; i < Mg * C; i += nt) {
+      const int j = i / C, c = i - j * C;
+      const int pos = (j & 1) ? (Mg - 1 - (j >> 1)) : (j >> 1);
+      A[c * Mg + pos] = (c < nc) ? ld2<CT>(src, j * J.vj + (c0 + c) * J.vm, J.src_f32) : zero2<CT>();
+    }
+    __syncthreads();
+    CT* res = fft_lines<-1>(A, B, C, Mg, J.pl);
+    const T s0 = (T)(1.0 / Mg), s1 = (T)(2.0 / Mg);
+    for (int i = tid; i < N * C; i += nt) {
+      const int c = i / N, k = i - c * N;
+      if (c < nc) {
+        const CT Vk = res[c * Mg + k];
+        const CT Vm = cconj(res[c * Mg + (k == 0 ? 0 : Mg - k)]);
+        const CT Vr = cscl(cadd(Vk, Vm), (T)0.5);
+        const CT d = csub(Vk, Vm);
+        CT Vi;
+        Vi.x = (T)0.5 * d.y;
+        Vi.y = (T)-0.5 * d.x;
+        const CT w = ld_tw4<CT>(J, k);
+        const T xr = w.x * Vr.x - w.y * Vr.y;
+        const T xi = w.x * Vi.x - w.y * Vi.y;
+        const T sc = (k == 0) ? s0 : s1;
+        CT o;
+        o.x = sc * xr;
+        o.y = sc * xi;
+        st2<CT>(dst, (c0 + c) * J.cm + k * J.cn, J.dst_f32, o);
+      }
+    }
+  }
+}
+
+// Gauss-Lobatto path (double precision only): DCT-I by the even extension.
+__device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v, const void* src3v,
+                              void* dstv, double2* A, double2* B, double2* a0s, int c0, int nc) {
+  const int C = J.C, N = J.N, M = J.M, P = 2 * J.M;
+  const double2* src = static_cast<const double2*>(srcv);
+  const double2* src2 = static_cast<const double2*>(src2v);
+  const double2* src3 = static_cast<const double2*>(src3v);
+  double2* dst = static_cast<double2*>(dstv);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int f = blockIdx.y;
+  if (J.inverse) {
+    for (int i = tid; i < N * C; i += nt) {
+      const int c = i / N, n = i - c * N;
+      double2 v = czero();
+      if (c < nc) {
+        const long long o = (c0 + c) * J.cm + n * J.cn;
+        v = src[o];
+        if (src2) v = cadd(v, src2[o]);
+        if (src3) v = cadd(v, src3[o]);
+      }
+      A[c * P + n] = v;
+    }
+    __syncthreads();
+    if (J.deriv[f]) {
+      for (int c = tid >> 5; c < C; c += (nt >> 5)) warp_cheb_deriv(A + c * P, B + c * P, N);
+      __syncthreads();
+      for (int i = tid; i < N * C; i += nt) {
+        const int c = i / N, n = i - c * N;
+        A[c * P + n] = B[c * P + n];
+      }
+      __syncthreads();
+    }
+    if (tid < C) {
+      a0s[tid] = A[tid * P];
+      a0s[C + tid] = (N > M) ? A[tid * P + M] : czero();
+    }
+    // even extension: A[n] = a_n (n <= M, zero for n >= N), A[P-n] = a_n
+    for (int i = tid; i < C * P; i += nt) {
+      const int c = i / P, n = i - c * P;
+      if (n >= N && n <= M) A[i] = czero();
+      else if (n > M) { const int r = P - n; A[i] = (r < N) ? A[c * P + r] : czero(); }
+    }
+    __syncthreads();
+    double2* res = fft_lines<-1>(A, B, C, P, J.pl);
+    // f_j = (F_j + a_0 + (-1)^j a_M) / 2
+    for (int i = tid; i < (M + 1) * C; i += nt) {
+      const int j = i / C, c = i - j * C;
+      if (c < nc) {
+        double2 v = cadd(res[c * P + j], a0s[c]);
+        v = (j & 1) ? csub(v, a0s[C + c]) : cadd(v, a0s[C + c]);
+        dst[j * J.vj + (c0 + c) * J.vm] = cscl(v, 0.5);
+      }
+    }
+  } else {
+    for (int i = tid; i < (M + 1) * C; i += nt) {
+      const int j = i / C, c = i - j * C;
+      A[c * P + j] = (c < nc) ? src[j * J.vj + (c0 + c) * J.vm] : czero();
+    }
+    __syncthreads();
+    for (int i = tid; i < C * P; i += nt) {
+      const int c = i / P, j = i - c * P;
+      if (j > M) A[i] = A[c * P + (P - j)];
+    }
+    __syncthreads();
+    double2* res = fft_lines<-1>(A, B, C, P, J.pl);
+    const double inv = 1.0 / M;
+    for (int i = tid; i < N * C; i += nt) {
+      const int c = i / N, n = i - c * N;
+      if (c < nc) {
+        const double s = (n == 0 || n == M) ? 0.5 * inv : inv;
+        dst[(c0 + c) * J.cm + n * J.cn] = cscl(res[c * P + n], s);
+      }
+    }
+  }
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(256) k_ycols(YJob J) {
+  const int b = blockIdx.z;
+  if (J.status && J.status[b]) return;
+  const int f = blockIdx.y;
+  // FFT length per column: M on the Gauss grid, 2M (even extension) on the
+  // Gauss-Lobatto grid; shared memory holds 2 C lines of it (+ 2 C scalars)
+  const int C = J.C, K = J.K, P = J.gauss ? J.M : 2 * J.M;
+  const int c0 = blockIdx.x * C;
+  const int nc = min(C, K - c0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  CT* A = reinterpret_cast<CT*>(smraw);
+  CT* B = A + (size_t)C * P;
+  const size_t es = J.src_f32 ? sizeof(float2) : sizeof(double2);
+  const size_t ed = J.dst_f32 ? sizeof(float2) : sizeof(double2);
+  const void* src = static_cast<const char*>(J.src) + (b * J.src_mstride + J.src_field[f] * J.src_fstride) * es;
+  void* dst = static_cast<char*>(J.dst) + (b * J.dst_mstride + J.dst_field[f] * J.dst_fstride) * ed;
+  const void* src2 = (J.inverse && J.src_field2[f] >= 0)
+      ? static_cast<const char*>(J.src) + (b * J.src_mstride + J.src_field2[f] * J.src_fstride) * es
+      : nullptr;
+  const void* src3 = (J.inverse && J.src_field3[f] >= 0)
+      ? static_cast<const char*>(J.src) + (b * J.src_mstride + J.src_field3[f] * J.src_fstride) * es
+      : nullptr;
+  if (J.gauss) {
+    ycols_gauss<CT>(J, src, src2, src3, dst, A, B, c0, nc);
+  } else if constexpr (sizeof(CT) == sizeof(double2)) {
+    ycols_lobatto(J, src, src2, src3, dst, reinterpret_cast<double2*>(A), reinterpret_cast<double2*>(B),
+                  reinterpret_cast<double2*>(B) + (size_t)C * P, c0, nc);
+  }
+}
+
+// ---------------------------------------------------------- Fourier rows
+// Row transforms along x: complex modes m < K <-> real values at n points,
+// two real fields packed in one complex line.
+struct XJob {
+  const double2* srcC;  // c2r: complex rows
+  const double* srcR;   // r2c: real rows
+  double2* dstC;
+  double* dstR;
+  long long src_mstride, dst_mstride, src_fstride, dst_fstride;
+  int src_rstep, dst_rstep;  // row index multipliers (elements per row = K or n)
+  int nf;                    // fields (packed in pairs, (nf + 1) / 2 lines)
+  int K, n;
+  int c2r;
+  const int* status;
+  FftPlan pl;
+};
+
+__global__ void __launch_bounds__(256) k_xrows(XJob J) {
+  const int b = blockIdx.y;
+  if (J.status && J.status[b]) return;
+  const int row = blockIdx.x;
+  const int K = J.K, n = J.n, nf = J.nf, nl = (nf + 1) / 2;
+  extern __shared__ double2 sm[];
+  double2* A = sm;
+  double2* Bb = sm + (size_t)nl * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (J.c2r) {
+    const double2* src = J.srcC + b * J.src_mstride + (long long)row * J.src_rstep * K;
+    for (int i = tid; i < nl * n; i += nt) {
+      const int l = i / n, k = i - l * n;
+      const int fa = 2 * l, fb = 2 * l + 1;
+      int kk = -1;
+      bool cj = false;
+      if (k < K) kk = k;
+      else if (k > n - K) { kk = n - k; cj = true; }
+      double2 h = czero();
+      if (kk >= 0) {
+        double2 F = src[fa * J.src_fstride + kk];
+        double2 G = (fb < nf) ? src[fb * J.src_fstride + kk] : czero();
+        if (kk == 0) { F.y = 0.0; G.y = 0.0; }
+        if (cj) { F = cconj(F); G = cconj(G); }
+        h = cadd(F, mul_i(G));
+      }
+      A[i] = h;
+    }
+    __syncthreads();
+    double2* res = fft_lines<+1>(A, Bb, nl, n, J.pl);
+    double* dst = J.dstR + b * J.dst_mstride + (long long)row * J.dst_rstep * n;
+    for (int i = tid; i < nl * n; i += nt) {
+      const int l = i / n, x = i - l * n;
+      const double2 h = res[i];
+      dst[(2 * l) * J.dst_fstride + x] = h.x;
+      if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + x] = h.y;
+    }
+  } else {
+    const double* src = J.srcR + b * J.src_mstride + (long long)row * J.src_rstep * n;
+    for (int i = tid; i < nl * n; i += nt) {
+      const int l = i / n, x = i - l * n;
+      const double fa = src[(2 * l) * J.src_fstride + x];
+      const double fb = (2 * l + 1 < nf) ? src[(2 * l + 1) * J.src_fstride + x] : 0.0;
+      A[i] = make_double2(fa, fb);
+    }
+    __syncthreads();
+    double2* res = fft_lines<-1>(A, Bb, nl, n, J.pl);
+    double2* dst = J.dstC + b * J.dst_mstride + (long long)row * J.dst_rstep * K;
+    const double inv = 1.0 / n;
+    for (int i = tid; i < nl * K; i += nt) {
+      const int l = i / K, k = i - l * K;
+      const double2 hk = res[l * n + k];
+      const double2 hm = cconj(res[l * n + (k == 0 ? 0 : n - k)]);
+      // F = (hk + conj(h_{-k}))/2, G = (hk - conj(h_{-k}))/(2i)
+      const double2 F = cscl(cadd(hk, hm), 0.5 * inv);
+      const double2 d = csub(hk, hm);
+      const double2 G = make_double2(0.5 * inv * d.y, -0.5 * inv * d.x);
+      dst[(2 * l) * J.dst_fstride + k] = F;
+      if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + k] = G;
+    }
+  }
+}
+
+
+// ------------------------------------------------------------ reductions
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+  }
+  return s;  // valid in thread 0
+}
+
+__device__ double2 warp_sum2(double2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+}  // namespace ptt

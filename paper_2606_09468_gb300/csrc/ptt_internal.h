@@ -24,7 +24,7 @@ struct FftPlan {
 
 // Per-member physics, resident on the device.
 struct MemberPrm {
-  double lx, re, wi, beta, eps, kappa, dt;
+  double lx, lz, re, wi, beta, eps, kappa, dt;
   double inv_wi, gam, nu, forcing;  // 1/Wi, (1-beta)/(Re Wi), beta/Re, 2/Re
   double trc_max, u_max;
 };
@@ -36,6 +36,7 @@ struct GroupDev {
   int nb;            // members in the group
   int f32;           // 1: mixed precision (FP32 transforms and products)
   int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
+  int nz, Mz, KZ;    // z modes (1 in 2D), padded z points, modes per Chebyshev index (K * nz)
   int Mx, M, P;      // padded x points, padded y Gauss points (= y FFT length), P = M
   int Pu, Me;        // y FFT length of the unpadded grid (2(N-1)); diagnostic Gauss points
   int Ccol, CcolE, CcolU;  // columns per block: padded / diagnostic / unpadded y passes
@@ -49,6 +50,12 @@ struct GroupDev {
   double2* Zp;       // [nb][5][M][K]  products, x-analysed, on the padded y grid
   float2* Ypf;       // mixed groups: Yp in single precision
   float2* Zpf;       // mixed groups: Zp in single precision
+  // 3D: [nb][17][M][KZ], [nb][26][M][Mz][K], [nb][9][M][Mz][K], [nb][9][M][KZ]
+  double2 *Y3, *Z3, *W3, *V3;
+  float2 *Y3f, *Z3f, *W3f, *V3f;
+  double2* DZ;       // 3D: Tr c after z synthesis [nb][N][nz][K]; state staging [9][N][nz][K]
+  double2* DMZ;      // 3D: mid-plane quantities after z synthesis [nb][8][nz][K]
+  double* MV;        // 3D: mid-plane values [nb][8][nz][nx]
   double2* NR;       // [nb][5][K][N]  explicit nonlinear terms, spectral
   double2* Rb;       // [nb][4][K][N]  H_x, H_y of ptt_explicit_rhs
   const double* qt;  // [nb][4 order][3 sys][3 (Q, inv, F)][K][N]
@@ -69,6 +76,7 @@ struct GroupDev {
   const float2* tw4Pf;  // the same in single precision (mixed groups)
   const double2* tw4E;  // [Me] exp(-i pi k/(2Me)), diagnostic Gauss grid
   FftPlan plP, plMx, plNx, plPu, plPe;   // lengths M, Mx, nx, 2(N-1), Me
+  FftPlan plMz, plNz;                    // 3D: lengths Mz, nz
 };
 
 constexpr int kPart = 16;  // values per diagnostics tile
@@ -85,6 +93,17 @@ cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_state_to_phys(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_reset_member(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t set_kernel_attributes(int max_dyn_smem);
+// 3D (ptt_kernels3d.cu)
+cudaError_t set_kernel_attributes3(int max_dyn_smem);
+cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nlaunch);
+cudaError_t launch_step3(const GroupDev& g, cudaStream_t st, int* nlaunch);
+cudaError_t launch_diag3(const GroupDev& g, cudaStream_t st, int* nlaunch);
+cudaError_t launch_explicit3(const GroupDev& g, cudaStream_t st);
+cudaError_t launch_phys_to_state3(const GroupDev& g, int b, cudaStream_t st);
+cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st);
+cudaError_t launch_reset_member3(const GroupDev& g, int b, cudaStream_t st);
+size_t smem_xfused3(int Mx, int f32);
+size_t smem_spec3(int N);
 
 // Host helpers (ptt_capi.cu) used by the workspace-free entry point.
 void set_last_error(const char* msg);

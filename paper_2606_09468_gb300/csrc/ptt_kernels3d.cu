@@ -1,0 +1,981 @@
+// Device code of the 3D pseudo-spectral sPTT channel step (sm_103a).
+//
+// Nine fields u, v, w, c_xx, c_xy, c_xz, c_yy, c_yz, c_zz; spectral arrays
+// [member][field][mode][n] with mode = mx * nz + mz (mx < nx/2, mz in FFT
+// order, the Nyquist slot nz/2 kept zero).  One step (Sec. 2):
+//   k_ycols  (inverse)  17 columns per mode on the padded Gauss y grid
+//                       (9 fields and 8 y-derivatives; d/dy of v follows from
+//                       continuity)
+//   k_zcols  (inverse)  per (y row, mx) line: 26 z syntheses of length Mz
+//                       (the 17 fields and 9 z-derivatives)
+//   k_xfused3           per (y, z) row: 35 physical fields (9 more
+//                       x-derivatives), the products of Eqs. 1-2, 9 forward
+//                       x transforms
+//   k_zcols  (forward), k_ycols (forward): back to truncated spectral terms
+//   k_spec3             per mode: explicit linear terms, SBDF sums, tau solves
+//                       (six c, phi-v with the influence correction, eta; U and
+//                       W on the mean mode), u and w from continuity and eta
+//   k_tick              step counters
+// followed by the Sec. 3 diagnostics over the nx x ny x nz grid and the
+// (x, z) mid-plane.
+#include <cstdio>
+
+#include "ptt_device.cuh"
+
+namespace ptt {
+namespace {
+
+// ------------------------------------------------------------ z lines
+// Inverse: src [field][j][mx*nz + mz] (modes) -> dst [field][j][z][mx] (values
+// at Mz points, optional d/dz).  Forward: src [field][j][z][mx] (values) ->
+// dst [field][j][mx*nz + mz] (modes, truncated, Nyquist slot zero).
+struct ZJob {
+  const void* src;
+  void* dst;
+  int src_f32, dst_f32;
+  long long src_mstride, dst_mstride;  // per member (elements)
+  long long src_fstride, dst_fstride;  // per field (elements)
+  int src_field[32];
+  int dst_field[32];
+  int dz[32];         // inverse: transform d/dz of the field
+  int K, nz, Mz;      // x modes, z modes, z points
+  int inverse;
+  int C;              // mx lines per block
+  int rows;           // y rows per field
+  const int* status;
+  const MemberPrm* prm;
+  FftPlan pl;         // length Mz
+};
+
+template <typename CT>
+__global__ void __launch_bounds__(256) k_zcols(ZJob J) {
+  using T = typename RealOf<CT>::T;
+  const int b = blockIdx.z;
+  if (J.status && J.status[b]) return;
+  const int f = blockIdx.y / J.rows;
+  const int j = blockIdx.y - f * J.rows;
+  const int C = J.C, K = J.K, nz = J.nz, Mz = J.Mz;
+  const int m0 = blockIdx.x * C;
+  const int nc = min(C, K - m0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  CT* A = reinterpret_cast<CT*>(smraw);
+  CT* B = A + (size_t)C * Mz;
+  const size_t es = J.src_f32 ? sizeof(float2) : sizeof(double2);
+  const size_t ed = J.dst_f32 ? sizeof(float2) : sizeof(double2);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int hz = nz / 2;
+  if (J.inverse) {
+    const void* src = static_cast<const char*>(J.src) +
+        (b * J.src_mstride + J.src_field[f] * J.src_fstride + (long long)j * K * nz) * es;
+    void* dst = static_cast<char*>(J.dst) +
+        (b * J.dst_mstride + J.dst_field[f] * J.dst_fstride + (long long)j * Mz * K) * ed;
+    const T kfac = (T)(2.0 * 3.14159265358979323846 / J.prm[b].lz);
+    const int dz = J.dz[f];
+    for (int i = tid; i < C * Mz; i += nt) A[i] = zero2<CT>();
+    __syncthreads();
+    for (int i = tid; i < C * nz; i += nt) {
+      const int c = i / nz, mz = i - c * nz;
+      if (c < nc && mz != hz) {
+        const int s = (mz < hz) ? mz : mz - nz;
+        CT v = ld2<CT>(src, (long long)(m0 + c) * nz + mz, J.src_f32);
+        if (dz) v = cscl(mul_i(v), kfac * (T)s);
+        A[c * Mz + ((s + Mz) % Mz)] = v;
+      }
+    }
+    __syncthreads();
+    CT* res = fft_lines<+1>(A, B, C, Mz, J.pl);
+    for (int i = tid; i < Mz * C; i += nt) {
+      const int z = i / C, c = i - z * C;
+      if (c < nc) st2<CT>(dst, (long long)z * K + m0 + c, J.dst_f32, res[c * Mz + z]);
+    }
+  } else {
+    const void* src = static_cast<const char*>(J.src) +
+        (b * J.src_mstride + J.src_field[f] * J.src_fstride + (long long)j * Mz * K) * es;
+    void* dst = static_cast<char*>(J.dst) +
+        (b * J.dst_mstride + J.dst_field[f] * J.dst_fstride + (long long)j * K * nz) * ed;
+    for (int i = tid; i < Mz * C; i += nt) {
+      const int z = i / C, c = i - z * C;
+      A[c * Mz + z] = (c < nc) ? ld2<CT>(src, (long long)z * K + m0 + c, J.src_f32) : zero2<CT>();
+    }
+    __syncthreads();
+    CT* res = fft_lines<-1>(A, B, C, Mz, J.pl);
+    const T inv = (T)(1.0 / Mz);
+    for (int i = tid; i < C * nz; i += nt) {
+      const int c = i / nz, mz = i - c * nz;
+      if (c < nc) {
+        CT v = zero2<CT>();
+        if (mz != hz) {
+          const int s = (mz < hz) ? mz : mz - nz;
+          v = cscl(res[c * Mz + ((s + Mz) % Mz)], inv);
+        }
+        st2<CT>(dst, (long long)(m0 + c) * nz + mz, J.dst_f32, v);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------ fused x pass + products
+// Z3 fields (26): 0 u, 1 v, 2 w, 3 cxx, 4 cxy, 5 cxz, 6 cyy, 7 cyz, 8 czz,
+// 9 uy, 10 wy, 11-16 c_y (xx, xy, xz, yy, yz, zz), 17 uz, 18 vz, 19 wz,
+// 20-25 c_z.  Physical fields (35): the 26 plus x-derivatives of fields 0-8
+// (26 ux, 27 vx, 28 wx, 29-34 c_x), packed in pairs into 18 complex lines.
+// W3 outputs (9): N_cxx, N_cxy, N_cxz, N_cyy, N_cyz, N_czz, N_u, N_v, N_w.
+template <typename C2> __device__ __forceinline__ const C2* z3_ptr(const GroupDev& g);
+template <> __device__ __forceinline__ const double2* z3_ptr<double2>(const GroupDev& g) { return g.Z3; }
+template <> __device__ __forceinline__ const float2* z3_ptr<float2>(const GroupDev& g) { return g.Z3f; }
+template <typename C2> __device__ __forceinline__ C2* w3_ptr(const GroupDev& g);
+template <> __device__ __forceinline__ double2* w3_ptr<double2>(const GroupDev& g) { return g.W3; }
+template <> __device__ __forceinline__ float2* w3_ptr<float2>(const GroupDev& g) { return g.W3f; }
+
+template <typename C2>
+__global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
+  using T = typename RealOf<C2>::T;
+  const int b = blockIdx.y;
+  if (g.status[b]) return;
+  const int row = blockIdx.x;  // j * Mz + z
+  const int K = g.K, Mx = g.Mx;
+  const long long plane = (long long)g.M * g.Mz * K;  // one field of one member
+  const MemberPrm pr = g.prm[b];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2* A = reinterpret_cast<C2*>(smraw);
+  C2* B = A + 18 * Mx;
+  const C2* Z = z3_ptr<C2>(g) + (size_t)b * 26 * plane + (size_t)row * K;
+  const T kfac = (T)(2.0 * 3.14159265358979323846 / pr.lx);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < 18 * Mx; i += nt) {
+    const int l = i / Mx, k = i - l * Mx;
+    int kk = -1;
+    bool cj = false;
+    if (k < K) kk = k;
+    else if (k > Mx - K) { kk = Mx - k; cj = true; }
+    C2 h = zero2<C2>();
+    if (kk >= 0) {
+      C2 F2[2];
+      for (int q = 0; q < 2; ++q) {
+        const int pf = 2 * l + q;
+        C2 v = zero2<C2>();
+        if (pf < 26) {
+          v = Z[(size_t)pf * plane + kk];
+        } else if (pf < 35) {
+          v = cscl(mul_i(Z[(size_t)(pf - 26) * plane + kk]), kfac * (T)kk);
+        }
+        if (kk == 0) v.y = 0;
+        if (cj) v = cconj(v);
+        F2[q] = v;
+      }
+      h = cadd(F2[0], mul_i(F2[1]));
+    }
+    A[i] = h;
+  }
+  __syncthreads();
+  C2* res = fft_lines<+1>(A, B, 18, Mx, g.plMx);
+  C2* oth = (res == A) ? B : A;
+  const T eps = (T)pr.eps, iwi = (T)pr.inv_wi;
+  for (int x = tid; x < Mx; x += nt) {
+    T q[36];
+#pragma unroll
+    for (int l = 0; l < 18; ++l) {
+      const C2 h = res[l * Mx + x];
+      q[2 * l] = h.x;
+      q[2 * l + 1] = h.y;
+    }
+    const T u = q[0], v = q[1], w = q[2];
+    const T C[3][3] = {{q[3], q[4], q[5]}, {q[4], q[6], q[7]}, {q[5], q[7], q[8]}};
+    const T ux = q[26], vx = q[27], wx = q[28];
+    const T uy = q[9], wy = q[10];
+    const T uz = q[17], vz = q[18], wz = q[19];
+    // L_ij = d u_i / d x_j, L_yy = -ux - wz (Eq. 3)
+    const T L[3][3] = {{ux, uy, uz}, {vx, -ux - wz, vz}, {wx, wy, wz}};
+    const T rw = ((T)1 + eps * (q[3] + q[6] + q[8] - (T)3)) * iwi;
+    // components in storage order xx, xy, xz, yy, yz, zz; gradients in q
+    const int ci[6] = {0, 0, 0, 1, 1, 2}, cj2[6] = {0, 1, 2, 1, 2, 2};
+    T out[9];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const int i = ci[c], jj = cj2[c];
+      const T adv = u * q[29 + c] + v * q[11 + c] + w * q[20 + c];
+      T st = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) st += L[i][k] * C[k][jj] + C[i][k] * L[jj][k];
+      const T dlt = (i == jj) ? (T)1 : (T)0;
+      out[c] = -adv + st - (C[i][jj] - dlt) * rw;
+    }
+    // Eq. 2 advection: -(u . grad) u_i = -sum_k u_k L_ik
+    const T uu[3] = {u, v, w};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[6 + i] = -(uu[0] * L[i][0] + uu[1] * L[i][1] + uu[2] * L[i][2]);
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      C2 o;
+      o.x = out[2 * l];
+      o.y = (2 * l + 1 < 9) ? out[2 * l + 1] : (T)0;
+      oth[l * Mx + x] = o;
+    }
+  }
+  __syncthreads();
+  C2* r2 = fft_lines<-1>(oth, res, 5, Mx, g.plMx);
+  C2* W = w3_ptr<C2>(g) + (size_t)b * 9 * plane + (size_t)row * K;
+  const T inv = (T)(1.0 / Mx);
+  for (int i = tid; i < 5 * K; i += nt) {
+    const int l = i / K, k = i - l * K;
+    const C2 hk = r2[l * Mx + k];
+    const C2 hm = cconj(r2[l * Mx + (k == 0 ? 0 : Mx - k)]);
+    const C2 F = cscl(cadd(hk, hm), (T)0.5 * inv);
+    const C2 d = csub(hk, hm);
+    C2 G;
+    G.x = (T)0.5 * inv * d.y;
+    G.y = (T)-0.5 * inv * d.x;
+    W[(size_t)(2 * l) * plane + k] = F;
+    if (2 * l + 1 < 9) W[(size_t)(2 * l + 1) * plane + k] = G;
+  }
+}
+
+// ---------------------------------------------- per-mode spectral stage
+// One block per (member, mode mx*nz + mz), 16 warps.  Columns in shared
+// memory.  Explicit terms (Eq. 2): H_i = N_u,i + gam (div c)_i (+ 2/Re on the
+// mean mode, x); forcings of the evolved velocity quantities (k != 0):
+// q1 = -D(i kx H_x + i kz H_z) - k^2 H_y (phi = (D^2 - k^2) v),
+// q2 = i kz H_x - i kx H_z (eta = i kz u - i kx w); mean mode: H_x, H_z.
+// Evolved (8): c (6), q1 state, q2 state.  Solves (16 warp tasks): 12 c
+// (component, parity); k != 0: phi->v->influence correction (2 parities),
+// eta (2 parities); k = 0: U (2), W (2).  Then u = i (kx Dv - kz eta)/k^2,
+// w = i (kz Dv + kx eta)/k^2.
+size_t smem_spec3_bytes(int N) { return (size_t)24 * N * sizeof(double2) + (size_t)10 * N * sizeof(double); }
+
+__global__ void __launch_bounds__(512) k_spec3(GroupDev g, int mode) {
+  const int b = blockIdx.y;
+  const int md = blockIdx.x;
+  if (g.status[b]) return;
+  const int KZ = g.KZ, N = g.N, nb = g.nb, nz = g.nz;
+  const int mx = md / nz, mzi = md - mx * nz, hz = nz / 2;
+  const size_t NK = (size_t)N * KZ;
+  const MemberPrm pr = g.prm[b];
+  const long long cnt = g.count[b];
+  const int slot = (int)(cnt & 3);
+  const int o = (cnt < 3) ? (int)cnt : 3;
+  const int sz = (mzi < hz) ? mzi : mzi - nz;
+  const double kx = 2.0 * 3.14159265358979323846 * mx / pr.lx;
+  const double kz = 2.0 * 3.14159265358979323846 * sz / pr.lz;
+  const double k2 = kx * kx + kz * kz;
+  const bool mean = (mx == 0 && mzi == 0);
+  const bool nyq = (mzi == hz);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* sm = reinterpret_cast<double2*>(smraw);
+  double2* sc = sm;               // [6][N] c -> new c
+  double2* su = sm + 6 * N;       // u -> new u
+  double2* sv = sm + 7 * N;       // v -> new v
+  double2* sw = sm + 8 * N;       // w -> new w
+  double2* sH = sm + 9 * N;       // [3][N] N_u -> H
+  double2* sq = sm + 12 * N;      // [2][N] evolved q1, q2
+  double2* sn = sm + 14 * N;      // [2][N] forcings of q1, q2
+  double2* sR = sm + 16 * N;      // [8][N] SBDF sums / temporaries
+  double* tb = reinterpret_cast<double*>(sm + 24 * N);  // [3 sys][Q, inv, F][N], vh[N]
+  const double2* X = g.X + (size_t)b * 9 * NK + (size_t)md * N;
+  const double2* NR = g.NR + (size_t)b * 9 * NK + (size_t)md * N;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  double2* Xw = g.X + (size_t)b * 9 * NK + (size_t)md * N;
+  if (nyq) {   // the dropped Nyquist slot stays zero
+    if (mode == 0) {
+      for (int i = tid; i < 9 * N; i += nt) Xw[(size_t)(i / N) * NK + (i % N)] = czero();
+      double2* E = g.Eh + ((size_t)slot * nb + b) * 8 * NK + (size_t)md * N;
+      double2* Nn = g.Nh + ((size_t)slot * nb + b) * 8 * NK + (size_t)md * N;
+      for (int i = tid; i < 8 * N; i += nt) {
+        E[(size_t)(i / N) * NK + (i % N)] = czero();
+        Nn[(size_t)(i / N) * NK + (i % N)] = czero();
+      }
+    } else {
+      double2* R = g.Rb + (size_t)b * 4 * NK + (size_t)md * N;
+      for (int i = tid; i < 3 * N; i += nt) R[(size_t)(i / N) * NK + (i % N)] = czero();
+    }
+    return;
+  }
+  for (int i = tid; i < N; i += nt) {
+    for (int c = 0; c < 6; ++c) sc[c * N + i] = X[(3 + c) * NK + i];
+    su[i] = X[i];
+    sv[i] = X[NK + i];
+    sw[i] = X[2 * NK + i];
+    for (int c = 0; c < 3; ++c) sH[c * N + i] = NR[(6 + c) * NK + i];
+  }
+  if (mode == 0) {
+    const double* qt = g.qt + ((size_t)b * 4 + o) * 3 * 3 * NK + (size_t)md * N;
+    for (int i = tid; i < 9 * N; i += nt) {
+      const int w = i / N, n = i - w * N;
+      tb[i] = qt[(size_t)w * NK + n];
+    }
+    const double* vh = g.vh + ((size_t)b * 4 + o) * NK + (size_t)md * N;
+    for (int i = tid; i < N; i += nt) tb[9 * N + i] = vh[i];
+  }
+  __syncthreads();
+  // D c_xy -> sR0, D c_yy -> sR1, D c_yz -> sR2; D v -> sR3 -> D^2 v -> sR4
+  if (warp == 0) warp_cheb_deriv(sc + 1 * N, sR, N);
+  else if (warp == 1) warp_cheb_deriv(sc + 3 * N, sR + N, N);
+  else if (warp == 2) warp_cheb_deriv(sc + 4 * N, sR + 2 * N, N);
+  else if (warp == 3 && mode == 0 && !mean) {
+    warp_cheb_deriv(sv, sR + 3 * N, N);
+    warp_cheb_deriv(sR + 3 * N, sR + 4 * N, N);
+  }
+  __syncthreads();
+  const double gam = pr.gam;
+  for (int n = tid; n < N; n += nt) {
+    // (div c)_x = i kx c_xx + D c_xy + i kz c_xz, etc.
+    const double2 dx = cadd(cscl(mul_i(sc[0 * N + n]), kx), cadd(sR[n], cscl(mul_i(sc[2 * N + n]), kz)));
+    const double2 dy = cadd(cscl(mul_i(sc[1 * N + n]), kx), cadd(sR[N + n], cscl(mul_i(sc[4 * N + n]), kz)));
+    const double2 dzv = cadd(cscl(mul_i(sc[2 * N + n]), kx), cadd(sR[2 * N + n], cscl(mul_i(sc[5 * N + n]), kz)));
+    double2 hx = cfma(gam, dx, sH[n]);
+    if (mean && n == 0) hx.x += pr.forcing;
+    sH[n] = hx;
+    sH[N + n] = cfma(gam, dy, sH[N + n]);
+    sH[2 * N + n] = cfma(gam, dzv, sH[2 * N + n]);
+    if (mode == 0) {
+      if (mean) {
+        sq[n] = su[n];
+        sq[N + n] = sw[n];
+      } else {
+        sq[n] = cfma(-k2, sv[n], sR[4 * N + n]);
+        sq[N + n] = csub(cscl(mul_i(su[n]), kz), cscl(mul_i(sw[n]), kx));
+      }
+    }
+  }
+  __syncthreads();
+  if (mode == 1) {
+    double2* R = g.Rb + (size_t)b * 4 * NK + (size_t)md * N;
+    for (int i = tid; i < 3 * N; i += nt) R[(size_t)(i / N) * NK + (i % N)] = sH[i];
+    return;
+  }
+  // forcing of q1: -D(i kx H_x + i kz H_z) - k^2 H_y
+  if (!mean) {
+    for (int n = tid; n < N; n += nt)
+      sR[5 * N + n] = cadd(cscl(mul_i(sH[n]), kx), cscl(mul_i(sH[2 * N + n]), kz));
+    __syncthreads();
+    if (warp == 0) warp_cheb_deriv(sR + 5 * N, sR + 6 * N, N);
+    __syncthreads();
+  }
+  for (int n = tid; n < N; n += nt) {
+    if (mean) {
+      sn[n] = sH[n];
+      sn[N + n] = sH[2 * N + n];
+    } else {
+      sn[n] = csub(cscl(sR[6 * N + n], -1.0), cscl(sH[N + n], k2));
+      sn[N + n] = csub(cscl(mul_i(sH[n]), kz), cscl(mul_i(sH[2 * N + n]), kx));
+    }
+  }
+  __syncthreads();
+  // history slot and SBDF sums of the 8 evolved quantities
+  {
+    double2* E = g.Eh + ((size_t)slot * nb + b) * 8 * NK + (size_t)md * N;
+    double2* Nn = g.Nh + ((size_t)slot * nb + b) * 8 * NK + (size_t)md * N;
+    const double idt = 1.0 / pr.dt;
+    for (int i = tid; i < 8 * N; i += nt) {
+      const int s = i / N, n = i - s * N;
+      const double2 x = (s < 6) ? sc[s * N + n] : sq[(s - 6) * N + n];
+      const double2 nn = (s < 6) ? NR[(size_t)s * NK + n] : sn[(s - 6) * N + n];
+      E[s * NK + n] = x;
+      Nn[s * NK + n] = nn;
+      double2 acc = cfma(c_sb[o][0], nn, cscl(x, -c_sa[o][1] * idt));
+      for (int jj = 1; jj <= o; ++jj) {
+        const size_t sl = (size_t)((slot - jj) & 3);
+        const double2 eo = g.Eh[(sl * nb + b) * 8 * NK + (size_t)s * NK + (size_t)md * N + n];
+        const double2 no = g.Nh[(sl * nb + b) * 8 * NK + (size_t)s * NK + (size_t)md * N + n];
+        acc = cfma(c_sb[o][jj], no, cfma(-c_sa[o][jj + 1] * idt, eo, acc));
+      }
+      sR[s * N + n] = acc;
+    }
+  }
+  __syncthreads();
+  const double* w1 = g.wrow;
+  const double* w2 = g.wrow + N;
+  const double* w3 = g.wrow + 2 * N;
+  const double a0 = c_sa[o][0];
+  const double* T0 = tb;
+  const double* T1 = tb + 3 * N;
+  const double* T2 = tb + 6 * N;
+  auto G = [&](int ts, int p) { return g.qtG[((((size_t)b * 4 + o) * 3 + ts) * 2 + p) * KZ + md]; };
+  if (warp < 12) {            // c components
+    const int comp = warp >> 1, p = warp & 1;
+    double2* out = sc + (size_t)comp * N;
+    const double2* R = sR + (size_t)comp * N;
+    const double alpha = a0 / pr.dt + pr.kappa * k2;
+    if (pr.kappa == 0.0) {
+      const double ia = 1.0 / alpha;
+      for (int n = p + 2 * lane; n < N; n += 64) out[n] = cscl(R[n], ia);
+    } else {
+      warp_qt_solve(N, p, alpha, R, out, T0, T0 + N, T0 + 2 * N, G(0, p), w1, w2, w3, pr.dt / a0, 1.0);
+    }
+  } else if (warp < 14) {     // q1: phi -> v (k != 0) or U (mean)
+    const int p = warp - 12;
+    double2* R1 = sR + 6 * N;
+    if (mean) {
+      warp_qt_solve(N, p, a0 / pr.dt, R1, su, T1, T1 + N, T1 + 2 * N, G(1, p), w1, w2, w3, 0.0, 1.0);
+      for (int n = p + 2 * lane; n < N; n += 64) sv[n] = czero();
+    } else {
+      warp_qt_solve(N, p, a0 / pr.dt + pr.nu * k2, R1, R1, T1, T1 + N, T1 + 2 * N, G(1, p), w1, w2,
+                    w3, 0.0, 1.0);
+      warp_qt_solve(N, p, k2, R1, sv, T2, T2 + N, T2 + 2 * N, G(2, p), w1, w2, w3, 0.0, -1.0);
+      double2 sacc = czero();
+      for (int n = p + 2 * lane; n < N; n += 64) sacc = cfma((double)n * n, sv[n], sacc);
+      sacc = warp_allsum2(sacc);
+      const double* vh = tb + 9 * N;
+      const double2 coef = cscl(sacc, -g.vhS[(((size_t)b * 4 + o) * 2 + p) * KZ + md]);
+      for (int n = p + 2 * lane; n < N; n += 64)
+        sv[n] = make_double2(fma(coef.x, vh[n], sv[n].x), fma(coef.y, vh[n], sv[n].y));
+    }
+  } else {                    // q2: eta (k != 0) or W (mean); eta kept in sR[7]
+    const int p = warp - 14;
+    double2* R2 = sR + 7 * N;
+    const double alpha = mean ? a0 / pr.dt : a0 / pr.dt + pr.nu * k2;
+    double2* out = mean ? sw : R2;
+    warp_qt_solve(N, p, alpha, R2, out, T1, T1 + N, T1 + 2 * N, G(1, p), w1, w2, w3, 0.0, 1.0);
+  }
+  __syncthreads();
+  if (!mean) {   // u, w from D v and eta
+    if (warp == 0) warp_cheb_deriv(sv, sR, N);
+    __syncthreads();
+    const double ik2 = 1.0 / k2;
+    for (int n = tid; n < N; n += nt) {
+      const double2 dv = sR[n], et = sR[7 * N + n];
+      su[n] = cscl(mul_i(csub(cscl(dv, kx), cscl(et, kz))), ik2);
+      sw[n] = cscl(mul_i(cadd(cscl(dv, kz), cscl(et, kx))), ik2);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < N; i += nt) {
+    Xw[i] = su[i];
+    Xw[NK + i] = sv[i];
+    Xw[2 * NK + i] = sw[i];
+    for (int c = 0; c < 6; ++c) Xw[(3 + c) * NK + i] = sc[c * N + i];
+  }
+}
+
+__global__ void k_tick3(GroupDev g) {
+  const int b = threadIdx.x + blockIdx.x * blockDim.x;
+  if (b < g.nb && !g.status[b]) g.count[b] += 1;
+}
+
+// ------------------------------------------------------------ diagnostics
+enum { P_E = 0, P_MIN, P_MAX, P_AMAX, P_BAD, P_C3, P_C0, P_B3, P_B0 };
+
+__device__ __forceinline__ bool nonfinite3(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL;
+}
+
+struct R5 { double s, mn, mx, ma; int bad; };
+__device__ R5 block_r5(R5 r) {
+  __shared__ double ss[32], smn[32], smx[32], sma[32];
+  __shared__ int sbad[32];
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    r.s += __shfl_down_sync(0xffffffffu, r.s, o2);
+    r.mn = fmin(r.mn, __shfl_down_sync(0xffffffffu, r.mn, o2));
+    r.mx = fmax(r.mx, __shfl_down_sync(0xffffffffu, r.mx, o2));
+    r.ma = fmax(r.ma, __shfl_down_sync(0xffffffffu, r.ma, o2));
+    r.bad |= __shfl_down_sync(0xffffffffu, r.bad, o2);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { ss[w] = r.s; smn[w] = r.mn; smx[w] = r.mx; sma[w] = r.ma; sbad[w] = r.bad; }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      r.s += ss[i]; r.mn = fmin(r.mn, smn[i]); r.mx = fmax(r.mx, smx[i]);
+      r.ma = fmax(r.ma, sma[i]); r.bad |= sbad[i];
+    }
+  return r;
+}
+
+// Energy (Fejer in y, Parseval in x and z), extrema of Tr c on the unpadded
+// grid, non-finite test; tiles of kTiles blocks per member.
+__global__ void __launch_bounds__(256) k_diag_part3(GroupDev g) {
+  const int b = blockIdx.y, tile = blockIdx.x;
+  if (g.status[b]) return;
+  const int KZ = g.KZ, N = g.N, nx = g.nx, nz = g.nz, Je = g.Me;
+  const size_t NK = (size_t)N * KZ;
+  const double2* DY = g.DY + (size_t)b * 3 * Je * KZ;
+  R5 r{0.0, 1e308, -1e308, 0.0, 0};
+  {
+    const long long tot = (long long)Je * KZ, per = (tot + kTiles - 1) / kTiles;
+    const long long i0 = tile * per, i1 = min(tot, i0 + per);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const int j = (int)(i / KZ), md = (int)(i - (long long)j * KZ);
+      const int mx = md / nz;
+      double e = 0.0;
+      for (int f = 0; f < 3; ++f) {
+        const double2 a = DY[(size_t)f * Je * KZ + i];
+        e += a.x * a.x + a.y * a.y;
+      }
+      r.s += (mx == 0 ? 1.0 : 2.0) * g.ccw[j] * e;
+    }
+  }
+  {
+    const double* tr = g.DV + (size_t)b * N * nz * nx;
+    const long long tot = (long long)N * nz * nx, per = (tot + kTiles - 1) / kTiles;
+    const long long i0 = tile * per, i1 = min(tot, i0 + per);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const double t = tr[i];
+      r.bad |= nonfinite3(t);
+      r.mn = fmin(r.mn, t);
+      r.mx = fmax(r.mx, t);
+      r.ma = fmax(r.ma, fabs(t));
+    }
+  }
+  {
+    const double* Xd = reinterpret_cast<const double*>(g.X + (size_t)b * 9 * NK);
+    const long long tot = 18LL * NK, per = (tot + kTiles - 1) / kTiles;
+    const long long i0 = tile * per, i1 = min(tot, i0 + per);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) r.bad |= nonfinite3(Xd[i]);
+  }
+  r = block_r5(r);
+  if (threadIdx.x == 0) {
+    double* pp = g.part + ((size_t)b * kTiles + tile) * kPart;
+    pp[P_E] = r.s;
+    pp[P_MIN] = r.mn;
+    pp[P_MAX] = r.mx;
+    pp[P_AMAX] = r.ma;
+    pp[P_BAD] = r.bad ? 1.0 : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_diag_count3(GroupDev g) {
+  const int b = blockIdx.y, tile = blockIdx.x;
+  if (g.status[b]) return;
+  double ma = 0.0;
+  for (int t = 0; t < kTiles; ++t) ma = fmax(ma, g.part[((size_t)b * kTiles + t) * kPart + P_AMAX]);
+  const double tau = 1e-9 * ma;
+  const double* tr = g.DV + (size_t)b * g.N * g.nz * g.nx;
+  const long long tot = (long long)g.N * g.nz * g.nx, per = (tot + kTiles - 1) / kTiles;
+  const long long i0 = tile * per, i1 = min(tot, i0 + per);
+  int c3 = 0, c0 = 0, b3 = 0, b0 = 0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const double t = tr[i];
+    c3 += (t < 3.0);
+    c0 += (t < 0.0);
+    b3 += (fabs(t - 3.0) <= tau);
+    b0 += (fabs(t) <= tau);
+  }
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    c3 += __shfl_down_sync(0xffffffffu, c3, o2);
+    c0 += __shfl_down_sync(0xffffffffu, c0, o2);
+    b3 += __shfl_down_sync(0xffffffffu, b3, o2);
+    b0 += __shfl_down_sync(0xffffffffu, b0, o2);
+  }
+  __shared__ int sc[4][32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sc[0][w] = c3; sc[1][w] = c0; sc[2][w] = b3; sc[3][w] = b0; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t4[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q)
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t4[q] += sc[q][i];
+    double* pp = g.part + ((size_t)b * kTiles + tile) * kPart;
+    for (int q = 0; q < 4; ++q) pp[P_C3 + q] = (double)t4[q];
+  }
+}
+
+// Mid-plane spectra at y = 0 per mode (one warp each): DM[b][q][mode] for
+// q = Tr c, u', w', du/dx, du/dz, dw/dx, dw/dz, v (u', w' without the mean).
+__global__ void __launch_bounds__(256) k_diag_mid3(GroupDev g) {
+  const int b = blockIdx.y;
+  if (g.status[b]) return;
+  const int md = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int KZ = g.KZ, N = g.N, nz = g.nz;
+  if (md >= KZ) return;
+  const size_t NK = (size_t)N * KZ;
+  const double2* X = g.X + (size_t)b * 9 * NK + (size_t)md * N;
+  double2 tr = czero(), u = czero(), v = czero(), w = czero();
+  for (int n = lane; n < N; n += 32) {
+    const int r4 = n & 3;
+    if (r4 == 0 || r4 == 2) {
+      const double s = (r4 == 0) ? 1.0 : -1.0;
+      tr = cfma(s, cadd(X[3 * NK + n], cadd(X[6 * NK + n], X[8 * NK + n])), tr);
+      u = cfma(s, X[n], u);
+      v = cfma(s, X[NK + n], v);
+      w = cfma(s, X[2 * NK + n], w);
+    }
+  }
+  tr = warp_sum2(tr);
+  u = warp_sum2(u);
+  v = warp_sum2(v);
+  w = warp_sum2(w);
+  if (lane == 0) {
+    const MemberPrm pr = g.prm[b];
+    const int mx = md / nz, mzi = md - mx * nz, hz = nz / 2;
+    const int sz = (mzi < hz) ? mzi : mzi - nz;
+    const double kx = 2.0 * 3.14159265358979323846 * mx / pr.lx;
+    const double kz = (mzi == hz) ? 0.0 : 2.0 * 3.14159265358979323846 * sz / pr.lz;
+    double2 q[8] = {tr, u, w, cscl(mul_i(u), kx), cscl(mul_i(u), kz), cscl(mul_i(w), kx),
+                    cscl(mul_i(w), kz), v};
+    if (md == 0) { q[1] = czero(); q[2] = czero(); }
+    double2* D = g.DM + (size_t)b * 8 * KZ + md;
+    for (int k = 0; k < 8; ++k) D[(size_t)k * KZ] = q[k];
+  }
+}
+
+// Per member: reduce the tiles, <Tr c>, mid-plane statistics over the
+// (x, z) plane values MV[b][8][nz][nx], blow-up test, record.
+__global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
+  const int b = blockIdx.x;
+  if (g.status[b]) return;
+  __shared__ double sh[32];
+  const int KZ = g.KZ, N = g.N, nx = g.nx, nz = g.nz;
+  const size_t NK = (size_t)N * KZ;
+  const MemberPrm pr = g.prm[b];
+  const double* pp = g.part + (size_t)b * kTiles * kPart;
+  double ma = 0.0;
+  for (int t = 0; t < kTiles; ++t) ma = fmax(ma, pp[t * kPart + P_AMAX]);
+  const double tau = 1e-9 * ma;
+  const double2* X = g.X + (size_t)b * 9 * NK;
+  double mt = 0.0;
+  for (int n = threadIdx.x; n < N; n += blockDim.x)
+    if ((n & 1) == 0)
+      mt += (X[3 * NK + n].x + X[6 * NK + n].x + X[8 * NK + n].x) * (2.0 / (1.0 - (double)n * n));
+  mt = block_sum(mt, sh);
+  const double* MV = g.MV + (size_t)b * 8 * nz * nx;
+  const int npl = nz * nx;
+  double sums[8][4];
+  long long m3 = 0, m0 = 0, mb3 = 0, mb0 = 0;
+  for (int q = 0; q < 8; ++q) for (int k = 0; k < 4; ++k) sums[q][k] = 0.0;
+  for (int i = threadIdx.x; i < npl; i += blockDim.x) {
+    for (int q = 0; q < 8; ++q) {
+      const double a = MV[(size_t)q * npl + i], a2 = a * a;
+      sums[q][0] += a; sums[q][1] += a2; sums[q][2] += a2 * a; sums[q][3] += a2 * a2;
+      if (q == 0) {
+        m3 += (a < 3.0); m0 += (a < 0.0);
+        mb3 += (fabs(a - 3.0) <= tau); mb0 += (fabs(a) <= tau);
+      }
+    }
+  }
+  double msum[8][4];
+  for (int q = 0; q < 8; ++q) for (int k = 0; k < 4; ++k) msum[q][k] = block_sum(sums[q][k], sh);
+  double mc[4] = {(double)m3, (double)m0, (double)mb3, (double)mb0};
+  double mct[4];
+  for (int q = 0; q < 4; ++q) mct[q] = block_sum(mc[q], sh);
+  if (threadIdx.x == 0) {
+    double e = 0.0, mn = 1e308, mx = -1e308, c4[4] = {0, 0, 0, 0};
+    bool bad = false;
+    for (int t = 0; t < kTiles; ++t) {
+      const double* q = pp + t * kPart;
+      e += q[P_E];
+      mn = fmin(mn, q[P_MIN]);
+      mx = fmax(mx, q[P_MAX]);
+      bad |= (q[P_BAD] != 0.0);
+      for (int k = 0; k < 4; ++k) c4[k] += q[P_C3 + k];
+    }
+    e *= 0.25;
+    const long long step = g.count[b];
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    ptt_diag r;
+    r.step = step;
+    r.t = step * pr.dt;
+    r.energy = e;
+    r.mean_trc = 0.5 * mt;
+    r.min_trc = bad ? qnan : mn;
+    r.max_trc = bad ? qnan : mx;
+    r.n_lt3 = (long long)c4[0]; r.n_lt0 = (long long)c4[1];
+    r.n_band3 = (long long)c4[2]; r.n_band0 = (long long)c4[3];
+    r.n_mid_lt3 = (long long)mct[0]; r.n_mid_lt0 = (long long)mct[1];
+    r.n_mid_band3 = (long long)mct[2]; r.n_mid_band0 = (long long)mct[3];
+    for (int q = 0; q < 8; ++q)
+      for (int k = 0; k < 4; ++k) r.mid_sums[q][k] = msum[q][k];
+    const bool blow = bad || !isfinite(e) || r.max_trc > pr.trc_max || sqrt(2.0 * e) > pr.u_max;
+    r.status = blow ? PTT_BLOWUP : PTT_OK;
+    r.reserved = 0;
+    g.ring[(size_t)b * kRing + (size_t)(step % kRing)] = r;
+    if (blow) g.status[b] = 1;
+  }
+}
+
+__global__ void k_reset3(GroupDev g, int b) {
+  if (threadIdx.x == 0) {
+    g.count[b] = 0;
+    g.status[b] = 0;
+  }
+}
+
+YJob yjob3(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl, const double2* tw4) {
+  YJob J{};
+  J.gauss = tw4 ? 1 : 0;
+  J.tw4 = tw4;
+  J.tw4f = g.tw4Pf;
+  J.K = g.KZ;
+  J.N = g.N;
+  J.M = M;
+  J.inverse = inverse ? 1 : 0;
+  J.C = C;
+  J.pl = pl;
+  J.status = g.status;
+  J.cm = g.N;
+  J.cn = 1;
+  J.vm = 1;
+  J.vj = g.KZ;
+  for (int i = 0; i < 8; ++i) J.src_field2[i] = J.src_field3[i] = -1;
+  return J;
+}
+
+ZJob zjob(const GroupDev& g, bool inverse, int Mz, int rows, const FftPlan& pl) {
+  ZJob Z{};
+  Z.K = g.K;
+  Z.nz = g.nz;
+  Z.Mz = Mz;
+  Z.inverse = inverse ? 1 : 0;
+  Z.C = 8;
+  Z.rows = rows;
+  Z.status = g.status;
+  Z.prm = g.prm;
+  Z.pl = pl;
+  return Z;
+}
+
+size_t smem_zcols(int C, int Mz, int f32) { return (size_t)2 * C * Mz * (f32 ? sizeof(float2) : sizeof(double2)); }
+
+template <typename F>
+cudaError_t optin3(F* fn, int optin_bytes) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, fn);
+  if (e) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin_bytes - (int)a.sharedSizeBytes);
+}
+
+}  // namespace
+
+size_t smem_xfused3(int Mx, int f32) { return (size_t)36 * Mx * (f32 ? sizeof(float2) : sizeof(double2)); }
+size_t smem_spec3(int N) { return smem_spec3_bytes(N); }
+
+cudaError_t set_kernel_attributes3(int optin_bytes) {
+  cudaError_t e;
+  if ((e = optin3(k_ycols<double2>, optin_bytes))) return e;
+  if ((e = optin3(k_ycols<float2>, optin_bytes))) return e;
+  if ((e = optin3(k_zcols<double2>, optin_bytes))) return e;
+  if ((e = optin3(k_zcols<float2>, optin_bytes))) return e;
+  if ((e = optin3(k_xfused3<double2>, optin_bytes))) return e;
+  if ((e = optin3(k_xfused3<float2>, optin_bytes))) return e;
+  if ((e = optin3(k_xrows, optin_bytes))) return e;
+  if ((e = optin3(k_spec3, optin_bytes))) return e;
+  return cudaSuccess;
+}
+
+// Stage s of one 3D step for one group (same numbering as the 2D stages).
+cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl) {
+  const int M = g.M, K = g.K, KZ = g.KZ, Mz = g.Mz;
+  const size_t NK = (size_t)g.N * KZ;
+  const long long yplane = (long long)M * KZ;          // Y3 / V3 field size
+  const long long zplane = (long long)M * Mz * K;      // Z3 / W3 field size
+  const int f32 = g.f32;
+  int n = 0;
+  switch (stage) {
+    case 0: {  // inverse y (17 fields) then inverse z (26 lines)
+      YJob J = yjob3(g, true, M, g.Ccol, g.plP, g.tw4P);
+      J.src = g.X;
+      J.dst = f32 ? (void*)g.Y3f : (void*)g.Y3;
+      J.dst_f32 = f32;
+      J.src_mstride = 9 * NK; J.dst_mstride = 17 * yplane;
+      J.src_fstride = NK; J.dst_fstride = yplane;
+      const int sf[17] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 0, 2, 3, 4, 5, 6, 7, 8};
+      const int dv[17] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1};
+      const size_t sm = smem_ycols(g.Ccol, M, f32);
+      for (int base = 0; base < 17; base += 8) {
+        YJob Jb = J;
+        const int cntf = (17 - base < 8) ? 17 - base : 8;
+        for (int i = 0; i < cntf; ++i) {
+          Jb.src_field[i] = sf[base + i];
+          Jb.dst_field[i] = base + i;
+          Jb.deriv[i] = dv[base + i];
+        }
+        if (f32) k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), cntf, g.nb), 256, sm, st>>>(Jb);
+        else k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), cntf, g.nb), 256, sm, st>>>(Jb);
+        ++n;
+      }
+      ZJob Z = zjob(g, true, Mz, M, g.plMz);
+      Z.src = J.dst; Z.src_f32 = f32;
+      Z.dst = f32 ? (void*)g.Z3f : (void*)g.Z3; Z.dst_f32 = f32;
+      Z.src_mstride = 17 * yplane; Z.dst_mstride = 26 * zplane;
+      Z.src_fstride = yplane; Z.dst_fstride = zplane;
+      for (int i = 0; i < 26; ++i) {
+        Z.src_field[i] = (i < 17) ? i : i - 17;
+        Z.dst_field[i] = i;
+        Z.dz[i] = (i >= 17) ? 1 : 0;
+      }
+      const size_t smz = smem_zcols(Z.C, Mz, f32);
+      if (f32) k_zcols<float2><<<dim3(cdiv(K, Z.C), 26 * M, g.nb), 256, smz, st>>>(Z);
+      else k_zcols<double2><<<dim3(cdiv(K, Z.C), 26 * M, g.nb), 256, smz, st>>>(Z);
+      ++n;
+      break;
+    }
+    case 1:
+      if (f32) k_xfused3<float2><<<dim3(M * Mz, g.nb), 512, smem_xfused3(g.Mx, 1), st>>>(g);
+      else k_xfused3<double2><<<dim3(M * Mz, g.nb), 512, smem_xfused3(g.Mx, 0), st>>>(g);
+      n = 1;
+      break;
+    case 2: {  // forward z (9) then forward y (9)
+      ZJob Z = zjob(g, false, Mz, M, g.plMz);
+      Z.src = f32 ? (const void*)g.W3f : (const void*)g.W3; Z.src_f32 = f32;
+      Z.dst = f32 ? (void*)g.V3f : (void*)g.V3; Z.dst_f32 = f32;
+      Z.src_mstride = 9 * zplane; Z.dst_mstride = 9 * yplane;
+      Z.src_fstride = zplane; Z.dst_fstride = yplane;
+      for (int i = 0; i < 9; ++i) { Z.src_field[i] = i; Z.dst_field[i] = i; Z.dz[i] = 0; }
+      const size_t smz = smem_zcols(Z.C, Mz, f32);
+      if (f32) k_zcols<float2><<<dim3(cdiv(K, Z.C), 9 * M, g.nb), 256, smz, st>>>(Z);
+      else k_zcols<double2><<<dim3(cdiv(K, Z.C), 9 * M, g.nb), 256, smz, st>>>(Z);
+      YJob F = yjob3(g, false, M, g.Ccol, g.plP, g.tw4P);
+      F.src = Z.dst; F.src_f32 = f32;
+      F.dst = g.NR;
+      F.src_mstride = 9 * yplane; F.dst_mstride = 9 * NK;
+      F.src_fstride = yplane; F.dst_fstride = NK;
+      const size_t sm = smem_ycols(g.Ccol, M, f32);
+      for (int base = 0; base < 9; base += 8) {
+        YJob Fb = F;
+        const int cntf = (9 - base < 8) ? 9 - base : 8;
+        for (int i = 0; i < cntf; ++i) { Fb.src_field[i] = base + i; Fb.dst_field[i] = base + i; Fb.deriv[i] = 0; }
+        if (f32) k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), cntf, g.nb), 256, sm, st>>>(Fb);
+        else k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), cntf, g.nb), 256, sm, st>>>(Fb);
+      }
+      n = 3;
+      break;
+    }
+    case 3:
+      k_spec3<<<dim3(KZ, g.nb), 512, smem_spec3(g.N), st>>>(g, 0);
+      k_tick3<<<cdiv(g.nb, 128), 128, 0, st>>>(g);
+      n = 2;
+      break;
+    case 4: {  // diagnostics
+      // Tr c = c_xx + c_yy + c_zz on the unpadded grid: y (Gauss-Lobatto) -> z -> x
+      YJob T = yjob3(g, true, g.N - 1, g.CcolU, g.plPu, nullptr);
+      T.src = g.X; T.dst = g.DT;
+      T.src_mstride = 9 * NK; T.dst_mstride = (long long)NK;
+      T.src_fstride = NK; T.dst_fstride = 0;
+      T.src_field[0] = 3; T.src_field2[0] = 6; T.src_field3[0] = 8; T.dst_field[0] = 0; T.deriv[0] = 0;
+      k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+      ZJob Z = zjob(g, true, g.nz, g.N, g.plNz);
+      Z.src = g.DT; Z.src_f32 = 0; Z.dst = g.DZ; Z.dst_f32 = 0;
+      Z.src_mstride = (long long)NK; Z.dst_mstride = (long long)g.N * g.nz * K;
+      Z.src_fstride = 0; Z.dst_fstride = 0;
+      Z.src_field[0] = 0; Z.dst_field[0] = 0; Z.dz[0] = 0;
+      k_zcols<double2><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), st>>>(Z);
+      XJob X{};
+      X.srcC = g.DZ; X.dstR = g.DV;
+      X.src_mstride = (long long)g.N * g.nz * K; X.dst_mstride = (long long)g.N * g.nz * g.nx;
+      X.src_fstride = 0; X.dst_fstride = 0;
+      X.src_rstep = 1; X.dst_rstep = 1;
+      X.nf = 1; X.K = K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
+      k_xrows<<<dim3(g.N * g.nz, g.nb), 256, smem_xrows(1, g.nx), st>>>(X);
+      // u, v, w on the Me Gauss points (energy)
+      YJob J = yjob3(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
+      J.src = g.X; J.dst = g.DY;
+      J.src_mstride = 9 * NK; J.dst_mstride = 3LL * g.Me * KZ;
+      J.src_fstride = NK; J.dst_fstride = (long long)g.Me * KZ;
+      for (int i = 0; i < 3; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
+      k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
+      k_diag_part3<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
+      k_diag_count3<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
+      // mid-plane: per-mode sums, then z and x syntheses of the 8 quantities
+      k_diag_mid3<<<dim3(cdiv(KZ, 8), g.nb), 256, 0, st>>>(g);
+      ZJob Zm = zjob(g, true, g.nz, 1, g.plNz);
+      Zm.src = g.DM; Zm.src_f32 = 0; Zm.dst = g.DMZ; Zm.dst_f32 = 0;
+      Zm.src_mstride = 8LL * KZ; Zm.dst_mstride = 8LL * g.nz * K;
+      Zm.src_fstride = KZ; Zm.dst_fstride = (long long)g.nz * K;
+      for (int i = 0; i < 8; ++i) { Zm.src_field[i] = i; Zm.dst_field[i] = i; Zm.dz[i] = 0; }
+      k_zcols<double2><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), st>>>(Zm);
+      XJob Xm{};
+      Xm.srcC = g.DMZ; Xm.dstR = g.MV;
+      Xm.src_mstride = 8LL * g.nz * K; Xm.dst_mstride = 8LL * g.nz * g.nx;
+      Xm.src_fstride = (long long)g.nz * K; Xm.dst_fstride = (long long)g.nz * g.nx;
+      Xm.src_rstep = 1; Xm.dst_rstep = 1;
+      Xm.nf = 8; Xm.K = K; Xm.n = g.nx; Xm.c2r = 1; Xm.status = g.status; Xm.pl = g.plNx;
+      k_xrows<<<dim3(g.nz, g.nb), 256, smem_xrows(4, g.nx), st>>>(Xm);
+      k_diag_final3<<<g.nb, 256, 0, st>>>(g);
+      n = 10;
+      break;
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+  if (nl) *nl += n;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step3(const GroupDev& g, cudaStream_t st, int* nl) {
+  for (int s = 0; s < 4; ++s) {
+    cudaError_t e = launch_stage3(g, s, st, nl);
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_diag3(const GroupDev& g, cudaStream_t st, int* nl) { return launch_stage3(g, 4, st, nl); }
+
+cudaError_t launch_explicit3(const GroupDev& g, cudaStream_t st) {
+  for (int s = 0; s < 3; ++s) {
+    cudaError_t e = launch_stage3(g, s, st, nullptr);
+    if (e) return e;
+  }
+  k_spec3<<<dim3(g.KZ, g.nb), 512, smem_spec3(g.N), st>>>(g, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_member3(const GroupDev& g, int b, cudaStream_t st) {
+  k_reset3<<<1, 32, 0, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+// physical staging [9][ny][nz][nx] -> state of member b: x analysis per
+// (y, z) row, z analysis per (y, mx), y analysis (DCT-I) per mode.
+cudaError_t launch_phys_to_state3(const GroupDev& g, int b, cudaStream_t st) {
+  const int K = g.K, KZ = g.KZ, N = g.N, nz = g.nz, nx = g.nx;
+  const size_t NK = (size_t)N * KZ;
+  const long long rowsp = (long long)N * nz;
+  XJob X{};
+  X.srcR = g.stage; X.dstC = g.DZ;   // DZ reused as [9][N][nz][K]
+  X.src_fstride = rowsp * nx; X.dst_fstride = rowsp * K;
+  X.src_rstep = 1; X.dst_rstep = 1;
+  X.nf = 9; X.K = K; X.n = nx; X.c2r = 0; X.status = nullptr; X.pl = g.plNx;
+  k_xrows<<<dim3((unsigned)rowsp, 1), 256, smem_xrows(5, nx), st>>>(X);
+  ZJob Z = zjob(g, false, nz, N, g.plNz);
+  Z.status = nullptr;
+  Z.src = g.DZ; Z.dst = g.stageS;     // stageS reused as [9][N][KZ]
+  Z.src_fstride = rowsp * K; Z.dst_fstride = (long long)N * KZ;
+  for (int i = 0; i < 9; ++i) { Z.src_field[i] = i; Z.dst_field[i] = i; Z.dz[i] = 0; }
+  k_zcols<double2><<<dim3(cdiv(K, Z.C), 9 * N, 1), 256, smem_zcols(Z.C, nz, 0), st>>>(Z);
+  YJob J = yjob3(g, false, N - 1, g.CcolU, g.plPu, nullptr);
+  J.status = nullptr;
+  J.src = g.stageS; J.dst = g.X + (size_t)b * 9 * NK;
+  J.src_fstride = (long long)N * KZ; J.dst_fstride = NK;
+  for (int base = 0; base < 9; base += 8) {
+    YJob Jb = J;
+    const int cntf = (9 - base < 8) ? 9 - base : 8;
+    for (int i = 0; i < cntf; ++i) { Jb.src_field[i] = base + i; Jb.dst_field[i] = base + i; Jb.deriv[i] = 0; }
+    k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), cntf, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(Jb);
+  }
+  k_reset3<<<1, 32, 0, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st) {
+  const int K = g.K, KZ = g.KZ, N = g.N, nz = g.nz, nx = g.nx;
+  const size_t NK = (size_t)N * KZ;
+  const long long rowsp = (long long)N * nz;
+  YJob J = yjob3(g, true, N - 1, g.CcolU, g.plPu, nullptr);
+  J.status = nullptr;
+  J.src = g.X + (size_t)b * 9 * NK; J.dst = g.stageS;
+  J.src_fstride = NK; J.dst_fstride = (long long)N * KZ;
+  for (int base = 0; base < 9; base += 8) {
+    YJob Jb = J;
+    const int cntf = (9 - base < 8) ? 9 - base : 8;
+    for (int i = 0; i < cntf; ++i) { Jb.src_field[i] = base + i; Jb.dst_field[i] = base + i; Jb.deriv[i] = 0; }
+    k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), cntf, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(Jb);
+  }
+  ZJob Z = zjob(g, true, nz, N, g.plNz);
+  Z.status = nullptr;
+  Z.src = g.stageS; Z.dst = g.DZ;
+  Z.src_fstride = (long long)N * KZ; Z.dst_fstride = rowsp * K;
+  for (int i = 0; i < 9; ++i) { Z.src_field[i] = i; Z.dst_field[i] = i; Z.dz[i] = 0; }
+  k_zcols<double2><<<dim3(cdiv(K, Z.C), 9 * N, 1), 256, smem_zcols(Z.C, nz, 0), st>>>(Z);
+  XJob X{};
+  X.srcC = g.DZ; X.dstR = g.stage;
+  X.src_fstride = rowsp * K; X.dst_fstride = rowsp * nx;
+  X.src_rstep = 1; X.dst_rstep = 1;
+  X.nf = 9; X.K = K; X.n = nx; X.c2r = 1; X.status = nullptr; X.pl = g.plNx;
+  k_xrows<<<dim3((unsigned)rowsp, 1), 256, smem_xrows(5, nx), st>>>(X);
+  return cudaGetLastError();
+}
+
+}  // namespace ptt

@@ -59,3 +59,52 @@ def phys_to_abi(fields):
 
 def abi_to_phys(arr):
     return [np.ascontiguousarray(arr[f].T) for f in range(arr.shape[0])]
+
+
+# ------------------------------------------------------------------ 3D --
+def random_spectral3(nx, ny, nz, seed, nmodes_x=None, nmodes_z=None, nmodes_y=None,
+                     scale=1.0, decay=0.0):
+    """Random spectral field a[mx, mz, n] (mx < nx/2, mz in FFT order, n < ny)
+    of a real field: the Nyquist z slot is zero and the mx = 0 plane is
+    Hermitian (a[0, -mz] = conj(a[0, mz]))."""
+    rng = np.random.default_rng(seed)
+    K = nx // 2
+    a = rng.standard_normal((K, nz, ny)) + 1j * rng.standard_normal((K, nz, ny))
+    s = np.arange(nz)
+    s = np.where(s < nz // 2, s, s - nz)
+    a[:, nz // 2] = 0
+    if nmodes_x is not None:
+        a[nmodes_x:] = 0
+    if nmodes_z is not None:
+        a[:, np.abs(s) > nmodes_z] = 0
+    if nmodes_y is not None:
+        a[:, :, nmodes_y:] = 0
+    if decay:
+        a *= np.exp(-decay * np.arange(ny))[None, None, :]
+    for i in range(nz):
+        if s[i] < 0:
+            a[0, i] = np.conj(a[0, (-s[i]) % nz])
+    a[0, 0] = a[0, 0].real
+    return a * scale
+
+
+def spectral3_to_abi(fields):
+    """List of nine a[mx, mz, n] arrays -> ABI double[9][ny][nx/2][nz][2]."""
+    out = np.stack([np.stack([np.transpose(f, (2, 0, 1)).real, np.transpose(f, (2, 0, 1)).imag],
+                             axis=-1) for f in fields])
+    return np.ascontiguousarray(out, dtype=np.float64)
+
+
+def abi_to_spectral3(arr):
+    return [np.ascontiguousarray(np.transpose(arr[f, ..., 0] + 1j * arr[f, ..., 1], (1, 2, 0)))
+            for f in range(arr.shape[0])]
+
+
+def phys3_to_abi(fields):
+    """List of nine f[x, y, z] arrays -> ABI double[9][ny][nz][nx]."""
+    return np.ascontiguousarray(np.stack([np.transpose(f, (1, 2, 0)) for f in fields]),
+                                dtype=np.float64)
+
+
+def abi_to_phys3(arr):
+    return [np.ascontiguousarray(np.transpose(arr[f], (2, 0, 1))) for f in range(arr.shape[0])]

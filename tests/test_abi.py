@@ -38,7 +38,9 @@ def test_status_strings_and_param_checks_without_gpu(lib):
     assert "blow" in P.ptt_status_string(1)
     # host-side validation only (no device call)
     assert P.ptt_workspace_size([P.make_params(nx=64, ny=65)]) > 0
-    for bad in (dict(nx=63), dict(ny=66), dict(nz=4), dict(nx=14), dict(beta=0.0)):
+    assert P.ptt_workspace_size([P.make_params(nx=32, ny=33, nz=16, lz=5.0)]) > 0
+    for bad in (dict(nx=63), dict(ny=66), dict(nx=14), dict(beta=0.0), dict(nz=2), dict(nz=3),
+                dict(nz=14), dict(nz=1024), dict(nz=8, lz=0.0)):
         with pytest.raises(P.PttError):
             P.ptt_workspace_size([P.make_params(**bad)])
 
