@@ -17,19 +17,25 @@
  *
  * Conventions shared by every call
  *  - A "member" is one independent channel run.  A context holds one or more
- *    members (an ensemble); members with equal (nx, ny) are advanced together
- *    by the same kernel launches.
- *  - Only the 2D (z-independent) problem is implemented: nz must be 1.  In 2D
- *    w = 0 and c_zz = 1 exactly; the five fields are u, v, c_xx, c_xy, c_yy.
+ *    members (an ensemble); members with equal (nx, ny, nz, precision) are
+ *    advanced together by the same kernel launches.
+ *  - nz = 1 selects the 2D (z-independent) problem: w = 0 and c_zz = 1
+ *    exactly; the five fields are u, v, c_xx, c_xy, c_yy.  nz > 1 selects the
+ *    3D problem with nine fields u, v, w, c_xx, c_xy, c_xz, c_yy, c_yz, c_zz.
  *  - nx: even, 8 <= nx <= 512, of the form 2^a 3^b 5^c.  ny (Chebyshev
- *    modes): 9 <= ny <= 513 with ny - 1 of the form 2^a 3^b 5^c.
+ *    modes): 9 <= ny <= 513 with ny - 1 of the form 2^a 3^b 5^c.  nz: 1, or
+ *    even with 4 <= nz <= 512 and of the form 2^a 3^b 5^c (then lz > 0).
  *  - Physical layout (host arrays of ptt_set_state / ptt_get_state):
- *    double[5][ny][nx], field-major, then y (Gauss-Lobatto point
- *    y_l = cos(pi l/(ny-1)), l = 0 is the wall y = +1), then x
- *    (x_j = j lx/nx) fastest.
- *  - Spectral layout (ptt_get_spectral / ptt_set_spectral): double[5][ny]
- *    [nx/2][2], field, Chebyshev index n, Fourier index m = 0..nx/2-1
- *    (k_m = 2 pi m / lx; the Nyquist mode is not stored), (re, im).
+ *    2D double[5][ny][nx]; 3D double[9][ny][nz][nx]: field-major, then y
+ *    (Gauss-Lobatto point y_l = cos(pi l/(ny-1)), l = 0 is the wall y = +1),
+ *    then z (z_k = k lz/nz), then x (x_j = j lx/nx) fastest.
+ *  - Spectral layout (ptt_get_spectral / ptt_set_spectral): 2D
+ *    double[5][ny][nx/2][2]; 3D double[9][ny][nx/2][nz][2]: field, Chebyshev
+ *    index n, Fourier index m = 0..nx/2-1 (k_m = 2 pi m / lx; the x Nyquist
+ *    mode is not stored), in 3D the z index q = 0..nz-1 in FFT order (signed
+ *    wavenumber s = q for q < nz/2, q - nz for q > nz/2, k = 2 pi s / lz; the
+ *    slot q = nz/2 of the z Nyquist mode is stored and always zero), (re, im).
+ *    The m = 0 plane of a real field is Hermitian in q.
  *  - Device memory: the caller allocates ONE device workspace of at least
  *    ptt_workspace_size() bytes (256-byte aligned) and owns it; the library
  *    never allocates or frees device memory.  Host pointers are caller-owned
@@ -66,7 +72,8 @@ extern "C" {
  * single fluid, Sec. 2): lx = lz = 10, re = 1e-2, wi = 150, beta = 0.9,
  * eps = 5e-5, kappa = 5e-5, dt = 2.5e-3. */
 typedef struct {
-  int32_t nx, ny, nz;        /* Fourier modes in x, Chebyshev modes in y, nz = 1 */
+  int32_t nx, ny, nz;        /* Fourier modes in x, Chebyshev modes in y, Fourier
+                                modes in z (nz = 1: the 2D problem)             */
   int32_t precision;         /* PTT_FP64 or PTT_MIXED                             */
   double lx, lz;             /* periodic lengths (walls at y = +-1)               */
   double re, wi, beta, eps, kappa;
@@ -76,7 +83,8 @@ typedef struct {
 } ptt_params;
 
 /* One diagnostics record per member and step (Sec. 3).  Counts are over the
- * unpadded grid (nx * ny points) or the mid-plane y = 0 (nx points).  The
+ * unpadded grid (nx * ny * nz points) or the mid-plane y = 0 (nx * nz
+ * points).  The
  * strict counts are the paper's; the band counts give the points with
  * |Tr c - 3| <= tau (resp. |Tr c| <= tau), tau = 1e-9 max|Tr c|, whose side
  * of the threshold rounding decides. */
@@ -88,9 +96,10 @@ typedef struct {
   double min_trc, max_trc;   /* over the unpadded grid                             */
   int64_t n_lt3, n_lt0, n_band3, n_band0;
   int64_t n_mid_lt3, n_mid_lt0, n_mid_band3, n_mid_band0;
-  /* mid-plane power sums: mid_sums[q][p-1] = sum over the nx mid-plane points
-   * of q^p, p = 1..4, for q = Tr c, u' = u - <u>_x, v, du/dx, dv/dx, du/dy
-   * (slots 6, 7 unused in 2D). */
+  /* mid-plane power sums: mid_sums[q][p-1] = sum over the mid-plane points of
+   * q^p, p = 1..4.  2D: q = Tr c, u' = u - <u>_x, v, du/dx, dv/dx, du/dy
+   * (slots 6, 7 unused).  3D: q = Tr c, u' = u - <u>_xz, w' = w - <w>_xz,
+   * du/dx, du/dz, dw/dx, dw/dz, v. */
   double mid_sums[8][4];
   int32_t status;            /* PTT_OK or PTT_BLOWUP                               */
   int32_t reserved;
@@ -113,9 +122,14 @@ int ptt_create(const ptt_params* per_member, int32_t nmembers, void* d_workspace
 
 /* Laminar sPTT state (the kappa = 0 closed form of Eqs. 1-2 for channel flow)
  * plus a seeded divergence-free, no-slip perturbation of maximum grid
- * amplitude `amplitude` (stream function (1 - y^2)^2 g(x, y), g with modes
- * 1 <= m <= 4, n <= 8 drawn from the counter-based splitmix64 stream of
- * `seed`).  Stands in for the paper's turbulent initial snapshot (Sec. 2),
+ * amplitude `amplitude`.  2D: stream function (1 - y^2)^2 g(x, y), g with
+ * modes 1 <= m <= 4, n <= 8.  3D: u' = d psi1/dy, v' = -d psi1/dx -
+ * d psi2/dz, w' = d psi2/dy with psi_c = (1 - y^2)^2 g_c(x, y, z), g_c with
+ * 0 <= mx <= 4, 0 <= mz <= 2, (mx, mz) != (0, 0), n <= 8, scaled so that
+ * max |u'| over the grid is `amplitude`.  Coefficients are uniform in
+ * [-1, 1) from the counter-based splitmix64 stream of `seed`.  The laminar
+ * state depends on y alone: c is not perturbed, and its coefficients at
+ * nonzero wavenumbers are exactly zero.  Stands in for the paper's turbulent initial snapshot (Sec. 2),
  * which is not available.  Resets the step counter and the SBDF history.
  * Synchronous. */
 int ptt_init_state(ptt_ctx* ctx, int32_t member, uint64_t seed, double amplitude);
@@ -149,11 +163,12 @@ int ptt_diagnostics(ptt_ctx* ctx, int32_t member, ptt_diag* h_out, int32_t max_r
                     int32_t* n_written);
 
 /* Dealiased explicit right-hand side of the current state of one member
- * (Eq. 1 without kappa lap c; Eq. 2 without pressure and viscous terms):
- * N_cxx, N_cxy, N_cyy, H_x, H_y in the spectral layout above (5 fields,
- * H_x includes the forcing 2/Re on its mean mode).  Does not advance the
+ * (Eq. 1 without kappa lap c; Eq. 2 without pressure and viscous terms) in
+ * the spectral layout above: 2D N_cxx, N_cxy, N_cyy, H_x, H_y (5 fields);
+ * 3D N_cxx, N_cxy, N_cxz, N_cyy, N_cyz, N_czz, H_x, H_y, H_z (9 fields);
+ * H_x includes the forcing 2/Re on its mean mode.  Does not advance the
  * state.  Synchronous. */
-int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec5);
+int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec);
 
 /* Workspace-free explicit right-hand side, for callers that cannot allocate
  * device memory (an application that owns every device byte and hands this
@@ -162,8 +177,8 @@ int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec5);
  * has no counterpart: this is a deployment variant of ptt_explicit_rhs.
  *
  * Same output as ptt_explicit_rhs for one run with params *p, but from and
- * to device memory the caller passes (FP64 only: PTT_ENOTSUP for
- * PTT_MIXED): d_spec holds the spectral state
+ * to device memory the caller passes (FP64 2D only: PTT_ENOTSUP for
+ * PTT_MIXED or nz > 1): d_spec holds the spectral state
  * double[5][ny][nx/2][2] (u, v, c_xx, c_xy, c_yy), d_out receives
  * double[5][ny][nx/2][2] (N_cxx, N_cxy, N_cyy, H_x, H_y); both 16-byte
  * aligned, distinct.  The intermediates live in a static device array of
@@ -192,10 +207,11 @@ int ptt_get_checkpoint(ptt_ctx* ctx, int32_t member, void* h_buf, size_t bytes);
 int ptt_set_checkpoint(ptt_ctx* ctx, int32_t member, const void* h_buf, size_t bytes);
 
 /* Stages of one step, in launch order: 0 inverse Chebyshev transforms
- * (9 fields, with d/dy), 1 fused x transforms + products of Eqs. 1-2,
- * 2 forward Chebyshev transforms (5 fields), 3 per-mode spectral stage
- * (explicit linear terms, SBDF sums, tau solves, velocity from continuity),
- * 4 diagnostics. */
+ * (2D 9 columns, 3D 17, with d/dy; in 3D followed by the inverse z
+ * transforms), 1 fused x transforms + products of Eqs. 1-2, 2 forward
+ * transforms (3D: z, then Chebyshev; 2D: Chebyshev), 3 per-mode spectral
+ * stage (explicit linear terms, SBDF sums, tau solves, velocity from
+ * continuity), 4 diagnostics. */
 #define PTT_NSTAGES 5
 
 /* Advance every member by nsteps steps with ordinary (non-graph) launches,

@@ -29,8 +29,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .spectral import (cheb_at, cheb_diff_matrix, padded_sizes, to_phys,
-                       to_spec)
+from .spectral import (cheb_at, cheb_diff_matrix, dct1_analysis_matrix, padded_sizes,
+                       to_phys, to_spec)
 
 FIELDS = ("u", "v", "cxx", "cxy", "cyy")
 
@@ -226,13 +226,19 @@ class Channel2D:
 
     def init_state(self, seed, amplitude):
         """Laminar sPTT state plus seeded perturbation (stands in for the
-        paper's turbulent initial condition, which is not available)."""
+        paper's turbulent initial condition, which is not available).
+        The laminar state depends on y alone, so it occupies only the kx = 0
+        mode: its Chebyshev coefficients are placed there directly, and only
+        the perturbation goes through the x transform (c is not perturbed;
+        its kx != 0 coefficients are exactly zero)."""
         y = np.cos(np.pi * np.arange(self.N) / (self.N - 1))
         U, cxx, cxy, cyy = laminar_sptt(y, self.p)
         up, vp = perturbation_2d(self.p, seed, amplitude)
-        one = np.ones((self.p.nx, 1))
-        self.set_physical([one * U[None, :] + up, vp, one * cxx[None, :],
-                           one * cxy[None, :], one * cyy[None, :]])
+        zero = np.zeros((self.p.nx, self.N))
+        self.set_physical([up, vp, zero, zero, zero])
+        A = dct1_analysis_matrix(self.N, self.N - 1)
+        for f, prof in (("u", U), ("cxx", cxx), ("cxy", cxy), ("cyy", cyy)):
+            getattr(self.state, f)[0] += A @ prof
 
     # ------------------------------------------------------ explicit terms
     def explicit_terms(self, s: State):

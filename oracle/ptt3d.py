@@ -215,10 +215,13 @@ class Channel3D:
         y = np.cos(np.pi * np.arange(self.N) / (self.N - 1))
         U, cxx, cxy, cyy = laminar_sptt(y, p)
         up, vp, wp = perturbation_3d(p, seed, amplitude)
-        one = np.ones((p.nx, self.N, p.nz))
-        prof = lambda q: one * q[None, :, None]  # noqa: E731
-        self.set_physical([prof(U) + up, vp, wp, prof(cxx), prof(cxy), 0 * one,
-                           prof(cyy), 0 * one, one])
+        # the laminar state depends on y alone: its coefficients go to the
+        # kx = kz = 0 mode directly; only the perturbation is transformed
+        zero = np.zeros((p.nx, self.N, p.nz))
+        self.set_physical([up, vp, wp] + [zero] * 6)
+        A = dct1_analysis_matrix(self.N, self.N - 1)
+        for f, prof in (("u", U), ("cxx", cxx), ("cxy", cxy), ("cyy", cyy), ("czz", np.ones(self.N))):
+            getattr(self.state, f)[0, 0] += A @ prof
 
     # ------------------------------------------------------ explicit terms
     def explicit_terms(self, s: State3):

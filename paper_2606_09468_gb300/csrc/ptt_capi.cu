@@ -790,13 +790,25 @@ static int member_ok(ptt_ctx* c, int member) {
   return c && member >= 0 && member < (int)c->prm.size();
 }
 
-static int upload_phys(ptt_ctx* c, int member, const double* h) {
+// laminar_c: the c fields of h are the laminar state, a function of y alone;
+// their coefficients at kx, kz != 0 are then set to exactly zero instead of
+// the rounding residue of the x / z analysis of constant rows.
+static int upload_phys(ptt_ctx* c, int member, const double* h, bool laminar_c = false) {
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
   const bool d3 = g.d.nz > 1;
-  const size_t n = (size_t)(d3 ? 9 : 5) * g.d.N * g.d.nz * g.d.nx;
+  const int nf = d3 ? 9 : 5;
+  const size_t n = (size_t)nf * g.d.N * g.d.nz * g.d.nx;
   CK(cudaMemcpyAsync(g.d.stage, h, n * 8, cudaMemcpyHostToDevice, c->stream));
   CK(d3 ? launch_phys_to_state3(g.d, b, c->stream) : launch_phys_to_state(g.d, b, c->stream));
+  if (laminar_c) {
+    // state [member][field][mode][n]: the non-mean modes of a field are the
+    // contiguous range after mode 0
+    const size_t NK = (size_t)g.d.N * g.d.KZ;
+    for (int f = d3 ? 3 : 2; f < nf; ++f)
+      CK(cudaMemsetAsync(g.d.X + ((size_t)b * nf + f) * NK + g.d.N, 0,
+                         (NK - g.d.N) * sizeof(double2), c->stream));
+  }
   CK(d3 ? launch_diag3(g.d, c->stream, nullptr) : launch_diag(g.d, c->stream, nullptr));
   CK(cudaStreamSynchronize(c->stream));
   c->last_read[member] = -1;
@@ -808,7 +820,7 @@ int ptt_init_state(ptt_ctx* c, int32_t member, uint64_t seed, double amplitude) 
   std::vector<double> f;
   if (c->prm[member].nz > 1) initial_fields3(c->prm[member], seed, amplitude, f);
   else initial_fields(c->prm[member], seed, amplitude, f);
-  return upload_phys(c, member, f.data());
+  return upload_phys(c, member, f.data(), true);
 }
 
 int ptt_set_state(ptt_ctx* c, int32_t member, const double* h) {

@@ -126,3 +126,123 @@ def test_mixed_2d_and_3d_runs_in_one_context():
     one.init_state(0, 1, 0.01)
     one.step(3)
     assert np.array_equal(one.get_spectral(0), ctx.get_spectral(0))
+
+
+def _pert(fields):
+    """Perturbation part of physical fields [x, y, z]: minus the (x, z) mean."""
+    return [f - f.mean(axis=(0, 2), keepdims=True) for f in fields]
+
+
+def test_hundred_steps_3d():
+    nx, ny, nz = 24, 25, 12
+    ctx = _ctx([(nx, ny, nz)])
+    ctx.init_state(0, 7, I.AMPLITUDE)
+    ora = _oracle(nx, ny, nz)
+    ora.init_state(7, I.AMPLITUDE)
+    ctx.step(100)
+    assert ctx.synchronize() == 0
+    for _ in range(100):
+        ora.step()
+    g, o = I.abi_to_phys3(ctx.get_state(0)), ora.get_physical()
+    e = _errs(g, o)
+    assert np.all(e <= 1e-9), e
+    # u, v, w perturbations (1e-3 of the base flow) are resolved as well
+    ep = _errs(_pert(g)[:3], _pert(o)[:3])
+    assert np.all(ep <= 1e-7), ep
+
+
+def test_one_step_full_size_3d():
+    # the 3D channel workload at its full size: 128 x 97 x 64, Lx = 10, Lz = 5
+    nx, ny, nz = 128, 97, 64
+    ctx = _ctx([(nx, ny, nz)])
+    ctx.init_state(0, 0, I.AMPLITUDE)
+    ora = _oracle(nx, ny, nz)
+    ora.init_state(0, I.AMPLITUDE)
+    ctx.step(1)
+    assert ctx.synchronize() == 0
+    ora.step()
+    g, o = I.abi_to_phys3(ctx.get_state(0)), ora.get_physical()
+    e = _errs(g, o)
+    assert np.all(e <= 1e-11), e
+    ep = _errs(_pert(g)[:3], _pert(o)[:3])
+    assert np.all(ep <= 1e-8), ep
+    d = ctx.diagnostics(0)[-1]
+    od = ora.diagnostics()
+    assert abs(d["energy"] - od["energy"]) <= 1e-11 * od["energy"]
+    assert abs(d["mean_trc"] - od["mean_trc"]) <= 1e-11 * od["mean_trc"]
+    for k, band in (("n_lt3", "n_band3"), ("n_lt0", "n_band0"), ("n_mid_lt3", "n_mid_band3")):
+        assert abs(d[k] - od[k]) <= od[band], (k, d[k], od[k])
+
+
+def test_stress_diffusion_off_and_oldroyd_b_3d():
+    nx, ny, nz = 16, 17, 8
+    kw = dict(kappa=0.0, eps=0.0, wi=20.0)
+    ctx = _ctx([(nx, ny, nz)], **kw)
+    ctx.init_state(0, 1, 0.01)
+    ora = _oracle(nx, ny, nz, **kw)
+    ora.init_state(1, 0.01)
+    ctx.step(3)
+    for _ in range(3):
+        ora.step()
+    e = _errs(I.abi_to_phys3(ctx.get_state(0)), ora.get_physical())
+    assert np.all(e <= 3e-11), e
+
+
+def test_checkpoint_restart_bitwise_3d():
+    nx, ny, nz = 16, 17, 8
+    a = _ctx([(nx, ny, nz)])
+    a.init_state(0, 3, 0.01)
+    a.step(3)
+    ck = a.checkpoint(0)
+    a.step(4)
+    b = _ctx([(nx, ny, nz)])
+    b.restore(0, ck)
+    b.step(4)
+    assert np.array_equal(a.get_spectral(0), b.get_spectral(0))
+    assert b.diagnostics(0)[-1]["step"] == 7
+
+
+def test_blowup_flag_3d():
+    import paper_2606_09468_gb300 as P
+    nx, ny, nz = 16, 17, 8
+    ctx = _ctx([(nx, ny, nz), (nx, ny, nz)])
+    ctx.init_state(0, 1, 0.01)
+    ctx.init_state(1, 1, 0.01)
+    spec = ctx.get_spectral(1)
+    spec[3, 2, 1, 1, 0] = np.nan
+    ctx.set_spectral(1, spec)
+    ctx.step(3)
+    assert ctx.synchronize() == P.PTT_BLOWUP
+    assert ctx.diagnostics(1)[-1]["status"] == P.PTT_BLOWUP
+    d0 = ctx.diagnostics(0)
+    assert d0[-1]["status"] == P.PTT_OK and d0[-1]["step"] == 3
+
+
+# --------------------------------------------------------- mixed precision --
+@pytest.mark.parametrize("nx,ny,nz", [(32, 33, 16)])
+def test_mixed_3d_errors_vs_oracle(nx, ny, nz):
+    """FP32 transforms and products, FP64 state and solves: stated per-field
+    error against the FP64 oracle after 1 and 100 steps."""
+    import paper_2606_09468_gb300 as P
+    ctx = _ctx([(nx, ny, nz)], precision=P.PTT_MIXED)
+    ctx.init_state(0, 2, I.AMPLITUDE)
+    ora = _oracle(nx, ny, nz)
+    ora.init_state(2, I.AMPLITUDE)
+    ctx.step(1)
+    ora.step()
+    e1 = _errs(I.abi_to_phys3(ctx.get_state(0)), ora.get_physical())
+    # c_xz, c_yz start at zero: after one step they are of the size of the
+    # perturbation's products, held to the FP32 level 1e-6; the others 1e-8
+    assert np.all(e1[[0, 1, 2, 3, 4, 6, 8]] <= 1e-8), e1
+    assert np.all(e1[[5, 7]] <= 1e-6), e1
+    ctx.step(99)
+    assert ctx.synchronize() == 0
+    for _ in range(99):
+        ora.step()
+    g, o = I.abi_to_phys3(ctx.get_state(0)), ora.get_physical()
+    e100 = _errs(g, o)
+    print("mixed 3D errors after 1 step", e1, "after 100 steps", e100)
+    # u, c_xx, c_xy, c_yy, c_zz to 1e-7; v, w, c_xz, c_yz (zero in the base
+    # state: of the size of the 1e-3 perturbation) to 1e-4
+    assert np.all(e100[[0, 3, 4, 6, 8]] <= 1e-7), e100
+    assert np.all(e100[[1, 2, 5, 7]] <= 1e-4), e100
