@@ -11,6 +11,11 @@ side, tau solves, diagnostics).  Synthetic seeded data.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The JSON line also carries, under "workloads", the 3D channel (128x97x64 and
+256x129x128, Lz = 5, FP64 and mixed precision) and the ragged 64-run 2D
+ensemble (uneven Nx, Ny, Wi; mixed precision and FP64), each timed the same
+way on rank 0.  --only NAME runs one of them alone (for profiling).
+
 --impl reference times the FP64 CPU oracle on this machine's host cores (each
 step: one oracle step of one sweep run, cycling through the nine shapes).
 Under torchrun with N > 1 every rank advances its own 27-run ensemble (seeds
@@ -54,6 +59,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-mixed", dest="mixed", action="store_false",
                     help="skip the mixed-precision measurement")
+    ap.add_argument("--no-workloads", dest="workloads", action="store_false",
+                    help="skip the 3D and ensemble workloads")
+    ap.add_argument("--workload-steps", type=int, default=40)
+    ap.add_argument("--only", default=None,
+                    help="run one workload alone (3d_fp64, 3d_mixed, 3d_fp64_large, "
+                         "3d_mixed_large, ensemble_mixed, ensemble_fp64) and print its line; "
+                         "for profiling")
     return ap.parse_args()
 
 
@@ -203,6 +215,129 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------- other workloads
+def _timed(ctx, steps, warmup):
+    """Device milliseconds per step of `steps` graph-launched steps (CUDA
+    events on the context stream) after `warmup` untimed steps."""
+    import torch
+    ctx.step(warmup)
+    ctx.synchronize()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    ctx.step(steps)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _dev(a, b):
+    import numpy as np
+    return [float(np.max(np.abs(x - y)) / np.max(np.abs(y))) for x, y in zip(a, b)]
+
+
+def only_workload(args):
+    """One workload alone, --steps steps after --warmup (for ncu captures)."""
+    import paper_2606_09468_gb300 as P
+    name = args.only
+    prec = P.PTT_MIXED if "mixed" in name else P.PTT_FP64
+    if name.startswith("3d"):
+        nx, ny, nz = I.CHANNEL3D_LARGE if name.endswith("large") else I.CHANNEL3D
+        params = [P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=prec, **I.PAPER)]
+        seeds = [0]
+        pts = nx * ny * nz
+    elif name.startswith("ensemble"):
+        fluid = {k: v for k, v in I.PAPER.items() if k != "wi"}
+        members = I.ensemble_members()
+        params = [P.make_params(nx=a, ny=b, wi=w, dt=I.DT, precision=prec, **fluid)
+                  for a, b, w, _ in members]
+        seeds = [m[3] for m in members]
+        pts = sum(a * b for a, b, _, _ in members)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    ctx = P.Context(params)
+    for i, s in enumerate(seeds):
+        ctx.init_state(i, s, I.AMPLITUDE)
+    ms = _timed(ctx, args.steps, args.warmup)
+    print(json.dumps({"workload": name, "value": pts * 1e3 / ms, "unit": METRIC, "ms_per_step": ms,
+                      "steps": args.steps, "status": P.ptt_status_string(ctx.synchronize())}))
+
+
+def other_workloads(args):
+    """The 3D channel (FP64 and mixed precision) and the ragged 64-run
+    ensemble (mixed precision, with its FP64 form for the factor)."""
+    import paper_2606_09468_gb300 as P
+    steps, warm = args.workload_steps, args.warmup
+    out = {}
+    f3 = ["u", "v", "w", "cxx", "cxy", "cxz", "cyy", "cyz", "czz"]
+
+    def run3(shape, precision, nsteps):
+        nx, ny, nz = shape
+        ctx = P.Context([P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=precision,
+                                       **I.PAPER)])
+        ctx.init_state(0, 0, I.AMPLITUDE)
+        ms = _timed(ctx, nsteps, warm)
+        return ctx, ms
+
+    for shape, precs in ((I.CHANNEL3D, (P.PTT_FP64, P.PTT_MIXED)),
+                         (I.CHANNEL3D_LARGE, (P.PTT_FP64, P.PTT_MIXED))):
+        pts = shape[0] * shape[1] * shape[2]
+        ms_of, states = {}, {}
+        for prec in precs:
+            n = steps if pts <= 1 << 20 else max(steps // 4, 5)
+            ctx, ms = run3(shape, prec, n)
+            ms_of[prec] = (ms, n)
+            # state after the same number of steps from the same initial state
+            ref = P.Context([P.make_params(nx=shape[0], ny=shape[1], nz=shape[2], lz=I.LZ3, dt=I.DT,
+                                           precision=prec, **I.PAPER)])
+            ref.init_state(0, 0, I.AMPLITUDE)
+            ref.step(warm)
+            ref.synchronize()
+            states[prec] = ref.get_state(0)
+            status = P.ptt_status_string(ctx.synchronize())
+            ctx.close()
+            ref.close()
+            name = "3d_%s_%dx%dx%d" % ("fp64" if prec == P.PTT_FP64 else "mixed", *shape)
+            out[name] = {"value": pts * 1e3 / ms, "unit": METRIC, "ms_per_step": ms, "steps": n,
+                         "grid_points": pts, "status": status,
+                         "dtype": "f64" if prec == P.PTT_FP64 else "f32 transforms+products / f64 state+solves",
+                         "workload": "3D sPTT channel %dx%dx%d (x, y, z), Lx=10, Lz=5, paper fluid, "
+                                     "dt=1e-3, laminar + seeded perturbation 1e-3" % shape}
+        if P.PTT_MIXED in states:
+            name = "3d_mixed_%dx%dx%d" % shape
+            out[name]["speedup_vs_fp64"] = ms_of[P.PTT_FP64][0] / ms_of[P.PTT_MIXED][0]
+            out[name]["max_rel_field_dev_vs_fp64_gpu"] = dict(zip(f3, _dev(states[P.PTT_MIXED], states[P.PTT_FP64])))
+            out[name]["dev_after_steps"] = warm
+
+    # ragged ensemble: 64 runs, uneven Nx, Ny, Wi
+    members = I.ensemble_members()
+    fluid = {k: v for k, v in I.PAPER.items() if k != "wi"}
+    pts = sum(nx * ny for nx, ny, _, _ in members)
+    res = {}
+    for prec in (P.PTT_MIXED, P.PTT_FP64):
+        ctx = P.Context([P.make_params(nx=nx, ny=ny, wi=wi, dt=I.DT, precision=prec, **fluid)
+                         for nx, ny, wi, _ in members])
+        for i, m in enumerate(members):
+            ctx.init_state(i, m[3], I.AMPLITUDE)
+        ms = _timed(ctx, steps, warm)
+        res[prec] = (ms, P.ptt_status_string(ctx.synchronize()), ctx.launches_per_step())
+        ctx.close()
+    out["ensemble64_mixed"] = {
+        "value": pts * 1e3 / res[P.PTT_MIXED][0], "unit": METRIC, "ms_per_step": res[P.PTT_MIXED][0],
+        "steps": steps, "grid_points": pts, "runs": len(members),
+        "shape_groups": len({(a, b) for a, b, _, _ in members}),
+        "launches_per_step": res[P.PTT_MIXED][2], "status": res[P.PTT_MIXED][1],
+        "dtype": "f32 transforms+products / f64 state+solves",
+        "fp64_value": pts * 1e3 / res[P.PTT_FP64][0], "fp64_ms_per_step": res[P.PTT_FP64][0],
+        "speedup_vs_fp64": res[P.PTT_FP64][0] / res[P.PTT_MIXED][0],
+        "stated_error_vs_fp64": "tests/test_gpu_ensemble.py: every member, every field, 1 step <= 1e-8",
+        "workload": "64 independent 2D runs, seeds 0-63, Nx in the 5-smooth multiples of 32 in "
+                    "[64, 512], Ny in {65,97,129,161,193,257}, Wi uniform in [50, 200] (splitmix64 "
+                    "draws of the run index), one context, one CUDA graph per step"}
+    return out
+
+
 # ------------------------------------------------------------------- ours
 def run_ours(args):
     import numpy as np
@@ -342,6 +477,7 @@ def run_ours(args):
 
     if rank != 0:
         return
+    workloads = other_workloads(args) if args.workloads else None
     ws = ctx.nbytes
     out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -355,6 +491,8 @@ def run_ours(args):
            "gpu_launches": launches, "roofline": roofline, "clocks": clk, "e2e": e2e}
     if mixed is not None:
         out["mixed"] = mixed
+    if workloads is not None:
+        out["workloads"] = workloads
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))
@@ -362,7 +500,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.only:
+        only_workload(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

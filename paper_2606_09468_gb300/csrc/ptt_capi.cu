@@ -430,7 +430,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.DY = cv.take<double2>((size_t)nb * (d3 ? 3 : 2) * Je * KZ);
     d.DT = cv.take<double2>((size_t)nb * NK);
     d.DV = cv.take<double>((size_t)nb * d.N * nzz * d.nx);
-    d.part = cv.take<double>((size_t)nb * kTiles * kPart);
+    d.ntile = diag_tiles(d.N, d.nx, d.nz);
+    d.part = cv.take<double>((size_t)nb * d.ntile * kPart);
     d.DM = cv.take<double2>((size_t)nb * (d3 ? 8 : 4) * KZ);
     d.DZ = d3 ? cv.take<double2>(std::max((size_t)nb, (size_t)9) * d.N * nzz * K) : nullptr;
     d.DMZ = d3 ? cv.take<double2>((size_t)nb * 8 * nzz * K) : nullptr;

@@ -686,6 +686,60 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
 
 
 // ------------------------------------------------------------ reductions
+// Max of pp[t * kPart + slot] over the ntile tiles of one member; every
+// thread of the block receives it.
+__device__ double block_tiles_max(const double* pp, int ntile, int slot) {
+  __shared__ double sm[32];
+  double m = 0.0;
+  for (int t = threadIdx.x; t < ntile; t += blockDim.x) m = fmax(m, pp[(size_t)t * kPart + slot]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[w] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sm[i]);
+    sm[0] = m;
+  }
+  __syncthreads();
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+// Block sums of NV values at once (fixed order: lanes by shuffles, then
+// warps in index order).  red: shared memory of (blockDim.x / 32) * NV
+// doubles; on return red[k], k < NV, holds the sum of v[k] over the block.
+template <int NV>
+__device__ void block_sum_many(const double (&v)[NV], double* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (l == 0) red[w * NV + k] = x;
+  }
+  __syncthreads();
+  double sum = 0.0;
+  if (threadIdx.x < NV)
+    for (int i = 0; i < nw; ++i) sum += red[i * NV + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x < NV) red[threadIdx.x] = sum;
+  __syncthreads();
+}
+
+// Block-wide max of v (fixed order), valid in thread 0.
+__device__ double block_tiles_max_val(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) v = fmax(v, sh[i]);
+  return v;
+}
+
 __device__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;

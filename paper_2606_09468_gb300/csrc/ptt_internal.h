@@ -34,6 +34,7 @@ struct MemberPrm {
 // arrays of values on a y grid are [member][field][j][m] (m fastest).
 struct GroupDev {
   int nb;            // members in the group
+  int ntile;         // diagnostics tiles per member (diag_tiles)
   int f32;           // 1: mixed precision (FP32 transforms and products)
   int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
   int nz, Mz, KZ;    // z modes (1 in 2D), padded z points, modes per Chebyshev index (K * nz)
@@ -67,7 +68,7 @@ struct GroupDev {
   double2* DY;       // [nb][2][Me][K]  u, v on the diagnostic y grid
   double2* DT;       // [nb][N][K]  cxx+cyy on the unpadded y rows, Fourier modes
   double* DV;        // [nb][N][nx]  cxx+cyy on the unpadded grid
-  double* part;      // [nb][kTiles][kPart]  partial reductions
+  double* part;      // [nb][ntile][kPart]  partial reductions
   double2* DM;       // [nb][4][K]  mid-plane Chebyshev sums per Fourier mode
   ptt_diag* ring;    // [nb][kRing]
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
@@ -79,8 +80,18 @@ struct GroupDev {
   FftPlan plMz, plNz;                    // 3D: lengths Mz, nz
 };
 
-constexpr int kPart = 16;  // values per diagnostics tile
-constexpr int kTiles = 16; // diagnostics tiles per member
+constexpr int kPart = 48;  // values per diagnostics tile
+
+// Diagnostics tiles per member: about 2048 grid points each, so that one
+// member alone still spreads over the SMs; a function of the shape only, so
+// that a member's diagnostics do not depend on the ensemble around it.
+inline int diag_tiles(int N, int nx, int nz) {
+  const long long pts = (long long)N * nx * nz;
+  long long t = (pts + 2047) / 2048;
+  if (t < 1) t = 1;
+  if (t > 1024) t = 1024;
+  return (int)t;
+}
 
 // Launch wrappers (device code in ptt_kernels.cu).  All asynchronous on `st`.
 cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nlaunch);

@@ -330,7 +330,7 @@ __global__ void k_transpose(const double2* __restrict__ src, double2* __restrict
 }
 
 // ------------------------------------------------------------ diagnostics
-// Diagnostics of one step, per member, as tiles (kTiles blocks per member)
+// Diagnostics of one step, per member, as tiles (ntile blocks per member)
 // with partial results in part[member][tile][kPart] reduced in a fixed
 // order (deterministic):
 //   DY: (u, v) on Me >= 2N-1 Gauss points (Fourier modes); DT, DV:
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256) k_diag_part(GroupDev g) {
   Red5 r{0.0, 1e308, -1e308, 0.0, 0};
   // energy: DY fields 0 (u) and 1 (v) on the Me Gauss points (Fejer weights)
   {
-    const long long tot = (long long)Je * K, per = (tot + kTiles - 1) / kTiles;
+    const long long tot = (long long)Je * K, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const int j = (int)(i / K), m = (int)(i - (long long)j * K);
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(256) k_diag_part(GroupDev g) {
   // extrema of Tr c on the unpadded grid
   {
     const double* tr = g.DV + (size_t)b * N * nx;
-    const long long tot = (long long)N * nx, per = (tot + kTiles - 1) / kTiles;
+    const long long tot = (long long)N * nx, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const double t = tr[i] + 1.0;
@@ -404,13 +404,13 @@ __global__ void __launch_bounds__(256) k_diag_part(GroupDev g) {
   // non-finite state values (integer test)
   {
     const double* X = reinterpret_cast<const double*>(g.X + (size_t)b * 5 * NK);
-    const long long tot = 10LL * NK, per = (tot + kTiles - 1) / kTiles;
+    const long long tot = 10LL * NK, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) r.bad |= nonfinite(X[i]);
   }
   r = block_red5(r);
   if (threadIdx.x == 0) {
-    double* pp = g.part + ((size_t)b * kTiles + tile) * kPart;
+    double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
     pp[P_E] = r.s;
     pp[P_MIN] = r.mn;
     pp[P_MAX] = r.mx;
@@ -423,11 +423,9 @@ __global__ void __launch_bounds__(256) k_diag_count(GroupDev g) {
   const int b = blockIdx.y, tile = blockIdx.x;
   if (g.status[b]) return;
   const int N = g.N, nx = g.nx;
-  double ma = 0.0;
-  for (int t = 0; t < kTiles; ++t) ma = fmax(ma, g.part[((size_t)b * kTiles + t) * kPart + P_AMAX]);
-  const double tau = 1e-9 * ma;
+  const double tau = 1e-9 * block_tiles_max(g.part + (size_t)b * g.ntile * kPart, g.ntile, P_AMAX);
   const double* tr = g.DV + (size_t)b * N * nx;
-  const long long tot = (long long)N * nx, per = (tot + kTiles - 1) / kTiles;
+  const long long tot = (long long)N * nx, per = (tot + g.ntile - 1) / g.ntile;
   const long long i0 = tile * per, i1 = min(tot, i0 + per);
   int c3 = 0, c0 = 0, b3 = 0, b0 = 0;
   for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
@@ -451,7 +449,7 @@ __global__ void __launch_bounds__(256) k_diag_count(GroupDev g) {
     long long t4[4] = {0, 0, 0, 0};
     for (int q = 0; q < 4; ++q)
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t4[q] += sc[q][i];
-    double* pp = g.part + ((size_t)b * kTiles + tile) * kPart;
+    double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
     pp[P_C3] = (double)t4[0];
     pp[P_C0] = (double)t4[1];
     pp[P_B3] = (double)t4[2];
@@ -507,13 +505,23 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
   const int K = g.K, N = g.N, nx = g.nx;
   const size_t NK = (size_t)N * K;
   const MemberPrm pr = g.prm[b];
-  const double* pp = g.part + (size_t)b * kTiles * kPart;
-  double tau;
-  {
-    double ma = 0.0;
-    for (int t = 0; t < kTiles; ++t) ma = fmax(ma, pp[t * kPart + P_AMAX]);
-    tau = 1e-9 * ma;
+  const double* pp = g.part + (size_t)b * g.ntile * kPart;
+  const double tau = 1e-9 * block_tiles_max(pp, g.ntile, P_AMAX);
+  // tile results, each thread a fixed set of tiles, then fixed-order trees
+  double te = 0.0, tmn = 1e308, tmx = -1e308, tbad = 0.0, tc[4] = {0, 0, 0, 0};
+  for (int t = threadIdx.x; t < g.ntile; t += blockDim.x) {
+    const double* q = pp + (size_t)t * kPart;
+    te += q[P_E];
+    tmn = fmin(tmn, q[P_MIN]);
+    tmx = fmax(tmx, q[P_MAX]);
+    tbad = fmax(tbad, q[P_BAD]);
+    for (int k = 0; k < 4; ++k) tc[k] += q[P_C3 + k];
   }
+  te = block_sum(te, sh);
+  tmn = -block_tiles_max_val(-tmn, sh);
+  tmx = block_tiles_max_val(tmx, sh);
+  tbad = block_tiles_max_val(tbad, sh);
+  for (int k = 0; k < 4; ++k) tc[k] = block_sum(tc[k], sh);
   const double2* X = g.X + (size_t)b * 5 * NK;
   // <Tr c> = 1/2 int (c_xx + c_yy)_0 dy + 1, int T_n = 2/(1-n^2), n even
   double mt = 0.0;
@@ -559,17 +567,8 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
   double mct[4];
   for (int q = 0; q < 4; ++q) mct[q] = block_sum(mc[q], sh);
   if (threadIdx.x == 0) {
-    double e = 0.0, mn = 1e308, mx = -1e308, c4[4] = {0, 0, 0, 0};
-    bool bad = false;
-    for (int t = 0; t < kTiles; ++t) {
-      const double* q = pp + t * kPart;
-      e += q[P_E];
-      mn = fmin(mn, q[P_MIN]);
-      mx = fmax(mx, q[P_MAX]);
-      bad |= (q[P_BAD] != 0.0);
-      for (int k = 0; k < 4; ++k) c4[k] += q[P_C3 + k];
-    }
-    e *= 0.25;
+    const double e = 0.25 * te, mn = tmn, mx = tmx, *c4 = tc;
+    const bool bad = (tbad != 0.0);
     const long long step = g.count[b];
     const double qnan = __longlong_as_double(0x7ff8000000000000LL);
     ptt_diag r;
@@ -727,8 +726,8 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       X.src_rstep = 1; X.dst_rstep = 1;
       X.nf = 1; X.K = g.K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
       k_xrows<<<dim3(g.N, g.nb), 256, smem_xrows(1, g.nx), st>>>(X);
-      k_diag_part<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
-      k_diag_count<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
+      k_diag_part<<<dim3(g.ntile, g.nb), 256, 0, st>>>(g);
+      k_diag_count<<<dim3(g.ntile, g.nb), 256, 0, st>>>(g);
       k_diag_mid<<<dim3(cdiv(g.K, 8), g.nb), 256, 0, st>>>(g);
       k_diag_final<<<g.nb, 256, smem_xrows(3, g.nx), st>>>(g);
       n = 7;

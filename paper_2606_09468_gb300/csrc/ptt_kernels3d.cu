@@ -453,7 +453,8 @@ __global__ void k_tick3(GroupDev g) {
 }
 
 // ------------------------------------------------------------ diagnostics
-enum { P_E = 0, P_MIN, P_MAX, P_AMAX, P_BAD, P_C3, P_C0, P_B3, P_B0 };
+enum { P_E = 0, P_MIN, P_MAX, P_AMAX, P_BAD, P_C3, P_C0, P_B3, P_B0,
+       P_MC3, P_MC0, P_MB3, P_MB0, P_MS = 16 /* 8 quantities x 4 powers */ };
 
 __device__ __forceinline__ bool nonfinite3(double x) {
   return (__double_as_longlong(x) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL;
@@ -483,7 +484,7 @@ __device__ R5 block_r5(R5 r) {
 }
 
 // Energy (Fejer in y, Parseval in x and z), extrema of Tr c on the unpadded
-// grid, non-finite test; tiles of kTiles blocks per member.
+// grid, non-finite test; ntile blocks per member.
 __global__ void __launch_bounds__(256) k_diag_part3(GroupDev g) {
   const int b = blockIdx.y, tile = blockIdx.x;
   if (g.status[b]) return;
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(256) k_diag_part3(GroupDev g) {
   const double2* DY = g.DY + (size_t)b * 3 * Je * KZ;
   R5 r{0.0, 1e308, -1e308, 0.0, 0};
   {
-    const long long tot = (long long)Je * KZ, per = (tot + kTiles - 1) / kTiles;
+    const long long tot = (long long)Je * KZ, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const int j = (int)(i / KZ), md = (int)(i - (long long)j * KZ);
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(256) k_diag_part3(GroupDev g) {
   }
   {
     const double* tr = g.DV + (size_t)b * N * nz * nx;
-    const long long tot = (long long)N * nz * nx, per = (tot + kTiles - 1) / kTiles;
+    const long long tot = (long long)N * nz * nx, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const double t = tr[i];
@@ -519,13 +520,13 @@ __global__ void __launch_bounds__(256) k_diag_part3(GroupDev g) {
   }
   {
     const double* Xd = reinterpret_cast<const double*>(g.X + (size_t)b * 9 * NK);
-    const long long tot = 18LL * NK, per = (tot + kTiles - 1) / kTiles;
+    const long long tot = 18LL * NK, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) r.bad |= nonfinite3(Xd[i]);
   }
   r = block_r5(r);
   if (threadIdx.x == 0) {
-    double* pp = g.part + ((size_t)b * kTiles + tile) * kPart;
+    double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
     pp[P_E] = r.s;
     pp[P_MIN] = r.mn;
     pp[P_MAX] = r.mx;
@@ -534,39 +535,59 @@ __global__ void __launch_bounds__(256) k_diag_part3(GroupDev g) {
   }
 }
 
+// Counts of Tr c < 3, < 0 and the tie bands over the volume, and over the
+// (x, z) mid-plane values MV[b][8][nz][nx] the same counts and the power
+// sums of the 8 mid-plane quantities; ntile blocks per member.
 __global__ void __launch_bounds__(256) k_diag_count3(GroupDev g) {
   const int b = blockIdx.y, tile = blockIdx.x;
   if (g.status[b]) return;
-  double ma = 0.0;
-  for (int t = 0; t < kTiles; ++t) ma = fmax(ma, g.part[((size_t)b * kTiles + t) * kPart + P_AMAX]);
-  const double tau = 1e-9 * ma;
-  const double* tr = g.DV + (size_t)b * g.N * g.nz * g.nx;
-  const long long tot = (long long)g.N * g.nz * g.nx, per = (tot + kTiles - 1) / kTiles;
-  const long long i0 = tile * per, i1 = min(tot, i0 + per);
-  int c3 = 0, c0 = 0, b3 = 0, b0 = 0;
-  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const double t = tr[i];
-    c3 += (t < 3.0);
-    c0 += (t < 0.0);
-    b3 += (fabs(t - 3.0) <= tau);
-    b0 += (fabs(t) <= tau);
+  const double tau = 1e-9 * block_tiles_max(g.part + (size_t)b * g.ntile * kPart, g.ntile, P_AMAX);
+  long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // volume c3 c0 b3 b0, mid-plane c3 c0 b3 b0
+  {
+    const double* tr = g.DV + (size_t)b * g.N * g.nz * g.nx;
+    const long long tot = (long long)g.N * g.nz * g.nx, per = (tot + g.ntile - 1) / g.ntile;
+    const long long i0 = tile * per, i1 = min(tot, i0 + per);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const double t = tr[i];
+      cnt[0] += (t < 3.0);
+      cnt[1] += (t < 0.0);
+      cnt[2] += (fabs(t - 3.0) <= tau);
+      cnt[3] += (fabs(t) <= tau);
+    }
   }
-  for (int o2 = 16; o2 > 0; o2 >>= 1) {
-    c3 += __shfl_down_sync(0xffffffffu, c3, o2);
-    c0 += __shfl_down_sync(0xffffffffu, c0, o2);
-    b3 += __shfl_down_sync(0xffffffffu, b3, o2);
-    b0 += __shfl_down_sync(0xffffffffu, b0, o2);
+  double sums[8][4];
+  for (int q = 0; q < 8; ++q) for (int k = 0; k < 4; ++k) sums[q][k] = 0.0;
+  {
+    const int npl = g.nz * g.nx;
+    const double* MV = g.MV + (size_t)b * 8 * npl;
+    const int per = (npl + g.ntile - 1) / g.ntile;
+    const int i0 = tile * per, i1 = min(npl, i0 + per);
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const double t = MV[i];
+      cnt[4] += (t < 3.0);
+      cnt[5] += (t < 0.0);
+      cnt[6] += (fabs(t - 3.0) <= tau);
+      cnt[7] += (fabs(t) <= tau);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double a = MV[(size_t)q * npl + i], a2 = a * a;
+        sums[q][0] += a; sums[q][1] += a2; sums[q][2] += a2 * a; sums[q][3] += a2 * a2;
+      }
+    }
   }
-  __shared__ int sc[4][32];
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { sc[0][w] = c3; sc[1][w] = c0; sc[2][w] = b3; sc[3][w] = b0; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long t4[4] = {0, 0, 0, 0};
-    for (int q = 0; q < 4; ++q)
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t4[q] += sc[q][i];
-    double* pp = g.part + ((size_t)b * kTiles + tile) * kPart;
-    for (int q = 0; q < 4; ++q) pp[P_C3 + q] = (double)t4[q];
+  double v[40];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = (double)cnt[k];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[8 + 4 * q + k] = sums[q][k];
+  __shared__ double red[8 * 40];
+  block_sum_many<40>(v, red);
+  double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
+  if (threadIdx.x < 40) {
+    const int k = threadIdx.x;
+    pp[k < 4 ? P_C3 + k : (k < 8 ? P_MC3 + (k - 4) : P_MS + (k - 8))] = red[k];
   }
 }
 
@@ -610,57 +631,48 @@ __global__ void __launch_bounds__(256) k_diag_mid3(GroupDev g) {
   }
 }
 
-// Per member: reduce the tiles, <Tr c>, mid-plane statistics over the
-// (x, z) plane values MV[b][8][nz][nx], blow-up test, record.
+// Per member: reduce the tiles (each thread a fixed set of tiles, then
+// fixed-order trees: deterministic), <Tr c>, blow-up test, record.
 __global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
   const int b = blockIdx.x;
   if (g.status[b]) return;
   __shared__ double sh[32];
-  const int KZ = g.KZ, N = g.N, nx = g.nx, nz = g.nz;
+  const int KZ = g.KZ, N = g.N;
   const size_t NK = (size_t)N * KZ;
   const MemberPrm pr = g.prm[b];
-  const double* pp = g.part + (size_t)b * kTiles * kPart;
-  double ma = 0.0;
-  for (int t = 0; t < kTiles; ++t) ma = fmax(ma, pp[t * kPart + P_AMAX]);
-  const double tau = 1e-9 * ma;
+  const double* pp = g.part + (size_t)b * g.ntile * kPart;
   const double2* X = g.X + (size_t)b * 9 * NK;
   double mt = 0.0;
   for (int n = threadIdx.x; n < N; n += blockDim.x)
     if ((n & 1) == 0)
       mt += (X[3 * NK + n].x + X[6 * NK + n].x + X[8 * NK + n].x) * (2.0 / (1.0 - (double)n * n));
   mt = block_sum(mt, sh);
-  const double* MV = g.MV + (size_t)b * 8 * nz * nx;
-  const int npl = nz * nx;
-  double sums[8][4];
-  long long m3 = 0, m0 = 0, mb3 = 0, mb0 = 0;
-  for (int q = 0; q < 8; ++q) for (int k = 0; k < 4; ++k) sums[q][k] = 0.0;
-  for (int i = threadIdx.x; i < npl; i += blockDim.x) {
-    for (int q = 0; q < 8; ++q) {
-      const double a = MV[(size_t)q * npl + i], a2 = a * a;
-      sums[q][0] += a; sums[q][1] += a2; sums[q][2] += a2 * a; sums[q][3] += a2 * a2;
-      if (q == 0) {
-        m3 += (a < 3.0); m0 += (a < 0.0);
-        mb3 += (fabs(a - 3.0) <= tau); mb0 += (fabs(a) <= tau);
-      }
-    }
+  double te = 0.0, tmn = 1e308, tmx = -1e308, tbad = 0.0;
+  for (int t = threadIdx.x; t < g.ntile; t += blockDim.x) {
+    const double* q = pp + (size_t)t * kPart;
+    te += q[P_E];
+    tmn = fmin(tmn, q[P_MIN]);
+    tmx = fmax(tmx, q[P_MAX]);
+    tbad = fmax(tbad, q[P_BAD]);
   }
-  double msum[8][4];
-  for (int q = 0; q < 8; ++q) for (int k = 0; k < 4; ++k) msum[q][k] = block_sum(sums[q][k], sh);
-  double mc[4] = {(double)m3, (double)m0, (double)mb3, (double)mb0};
-  double mct[4];
-  for (int q = 0; q < 4; ++q) mct[q] = block_sum(mc[q], sh);
+  te = block_sum(te, sh);
+  tmn = -block_tiles_max_val(-tmn, sh);
+  tmx = block_tiles_max_val(tmx, sh);
+  tbad = block_tiles_max_val(tbad, sh);
+  // counts (volume, mid-plane) and mid-plane sums: tile slots 5-8, 9-12, 16-47
+  double v[40];
+#pragma unroll
+  for (int k = 0; k < 40; ++k) v[k] = 0.0;
+  for (int t = threadIdx.x; t < g.ntile; t += blockDim.x) {
+    const double* q = pp + (size_t)t * kPart;
+#pragma unroll
+    for (int k = 0; k < 40; ++k) v[k] += q[k < 4 ? P_C3 + k : (k < 8 ? P_MC3 + (k - 4) : P_MS + (k - 8))];
+  }
+  __shared__ double acc[8 * 40];
+  block_sum_many<40>(v, acc);
   if (threadIdx.x == 0) {
-    double e = 0.0, mn = 1e308, mx = -1e308, c4[4] = {0, 0, 0, 0};
-    bool bad = false;
-    for (int t = 0; t < kTiles; ++t) {
-      const double* q = pp + t * kPart;
-      e += q[P_E];
-      mn = fmin(mn, q[P_MIN]);
-      mx = fmax(mx, q[P_MAX]);
-      bad |= (q[P_BAD] != 0.0);
-      for (int k = 0; k < 4; ++k) c4[k] += q[P_C3 + k];
-    }
-    e *= 0.25;
+    const double e = 0.25 * te;
+    const bool bad = (tbad != 0.0);
     const long long step = g.count[b];
     const double qnan = __longlong_as_double(0x7ff8000000000000LL);
     ptt_diag r;
@@ -668,14 +680,14 @@ __global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
     r.t = step * pr.dt;
     r.energy = e;
     r.mean_trc = 0.5 * mt;
-    r.min_trc = bad ? qnan : mn;
-    r.max_trc = bad ? qnan : mx;
-    r.n_lt3 = (long long)c4[0]; r.n_lt0 = (long long)c4[1];
-    r.n_band3 = (long long)c4[2]; r.n_band0 = (long long)c4[3];
-    r.n_mid_lt3 = (long long)mct[0]; r.n_mid_lt0 = (long long)mct[1];
-    r.n_mid_band3 = (long long)mct[2]; r.n_mid_band0 = (long long)mct[3];
+    r.min_trc = bad ? qnan : tmn;
+    r.max_trc = bad ? qnan : tmx;
+    r.n_lt3 = (long long)acc[0]; r.n_lt0 = (long long)acc[1];
+    r.n_band3 = (long long)acc[2]; r.n_band0 = (long long)acc[3];
+    r.n_mid_lt3 = (long long)acc[4]; r.n_mid_lt0 = (long long)acc[5];
+    r.n_mid_band3 = (long long)acc[6]; r.n_mid_band0 = (long long)acc[7];
     for (int q = 0; q < 8; ++q)
-      for (int k = 0; k < 4; ++k) r.mid_sums[q][k] = msum[q][k];
+      for (int k = 0; k < 4; ++k) r.mid_sums[q][k] = acc[8 + 4 * q + k];
     const bool blow = bad || !isfinite(e) || r.max_trc > pr.trc_max || sqrt(2.0 * e) > pr.u_max;
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
@@ -865,8 +877,6 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       J.src_fstride = NK; J.dst_fstride = (long long)g.Me * KZ;
       for (int i = 0; i < 3; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
       k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
-      k_diag_part3<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
-      k_diag_count3<<<dim3(kTiles, g.nb), 256, 0, st>>>(g);
       // mid-plane: per-mode sums, then z and x syntheses of the 8 quantities
       k_diag_mid3<<<dim3(cdiv(KZ, 8), g.nb), 256, 0, st>>>(g);
       ZJob Zm = zjob(g, true, g.nz, 1, g.plNz);
@@ -882,6 +892,8 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       Xm.src_rstep = 1; Xm.dst_rstep = 1;
       Xm.nf = 8; Xm.K = K; Xm.n = g.nx; Xm.c2r = 1; Xm.status = g.status; Xm.pl = g.plNx;
       k_xrows<<<dim3(g.nz, g.nb), 256, smem_xrows(4, g.nx), st>>>(Xm);
+      k_diag_part3<<<dim3(g.ntile, g.nb), 256, 0, st>>>(g);
+      k_diag_count3<<<dim3(g.ntile, g.nb), 256, 0, st>>>(g);
       k_diag_final3<<<g.nb, 256, 0, st>>>(g);
       n = 10;
       break;

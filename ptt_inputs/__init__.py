@@ -20,6 +20,59 @@ SWEEP_SEEDS = (0, 1, 2)
 SMALL = (64, 65)   # the small parity case (100 steps)
 
 
+# 3D channel workloads: Lz = 5 (Lx = 10), 128 x 97 x 64 in FP64 and mixed
+# precision, 256 x 129 x 128 in mixed precision.
+LZ3 = 5.0
+CHANNEL3D = (128, 97, 64)
+CHANNEL3D_LARGE = (256, 129, 128)
+
+# Ragged ensemble: 64 independent 2D runs, member i with seed i, Nx drawn
+# from the multiples of 32 in [64, 512] that the FFT sizes allow (2^a 3^b 5^c),
+# Ny from {65, 97, 129, 161, 193, 257} (Ny - 1 of the form 2^a 3^b 5^c; 225
+# is not), Wi uniform in [50, 200]; all three from the splitmix64 stream of i.
+ENSEMBLE_SIZE = 64
+ENSEMBLE_NY = (65, 97, 129, 161, 193, 257)
+ENSEMBLE_WI = (50.0, 200.0)
+
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(seed, k):
+    """Output k (k = 0, 1, ...) of the splitmix64 stream of `seed`: the
+    counter-based form mix(seed + (k + 1) * 0x9E3779B97F4A7C15) of Steele,
+    Lea and Flood's generator (the increment is the 64-bit golden ratio)."""
+    z = (seed + (k + 1) * 0x9E3779B97F4A7C15) & _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def splitmix_unit(seed, k):
+    """Uniform double in [0, 1) from the top 53 bits of splitmix64 output k."""
+    return (splitmix64(seed, k) >> 11) * (1.0 / (1 << 53))
+
+
+def _smooth235(n):
+    for q in (2, 3, 5):
+        while n % q == 0:
+            n //= q
+    return n == 1
+
+
+ENSEMBLE_NX = tuple(n for n in range(64, 513, 32) if _smooth235(n))
+
+
+def ensemble_members(size=ENSEMBLE_SIZE):
+    """(nx, ny, wi, seed) of every member of the ragged ensemble."""
+    out = []
+    for i in range(size):
+        nx = ENSEMBLE_NX[int(splitmix_unit(i, 0) * len(ENSEMBLE_NX))]
+        ny = ENSEMBLE_NY[int(splitmix_unit(i, 1) * len(ENSEMBLE_NY))]
+        wi = ENSEMBLE_WI[0] + (ENSEMBLE_WI[1] - ENSEMBLE_WI[0]) * splitmix_unit(i, 2)
+        out.append((nx, ny, wi, i))
+    return out
+
+
 def sweep_members(seeds=SWEEP_SEEDS):
     """(nx, ny, seed) of every member of the 2D sweep ensemble."""
     return [(nx, ny, s) for nx in SWEEP_NX for ny in SWEEP_NY for s in seeds]

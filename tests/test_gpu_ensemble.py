@@ -1,0 +1,79 @@
+"""The ragged 64-member ensemble (uneven Nx, Ny and Wi, seeds 0-63) advanced
+by one context: sampled members against the FP64 oracle, members bitwise
+equal to the same run alone, and the mixed-precision form within its stated
+error of the FP64 form."""
+import numpy as np
+import pytest
+
+import ptt_inputs as I
+from oracle import ptt2d as O
+
+pytestmark = pytest.mark.gpu
+
+MEMBERS = I.ensemble_members()
+FLUID = {k: v for k, v in I.PAPER.items() if k != "wi"}
+
+
+def _params(P, m, precision):
+    nx, ny, wi, _ = m
+    return P.make_params(nx=nx, ny=ny, wi=wi, dt=I.DT, precision=precision, **FLUID)
+
+
+def _ensemble(precision, members=MEMBERS):
+    import paper_2606_09468_gb300 as P
+    P.load_library()
+    ctx = P.Context([_params(P, m, precision) for m in members])
+    for i, m in enumerate(members):
+        ctx.init_state(i, m[3], I.AMPLITUDE)
+    return ctx
+
+
+def _errs(a, b):
+    return np.array([np.max(np.abs(x - y)) / np.max(np.abs(y)) for x, y in zip(a, b)])
+
+
+def _sampled():
+    # the three members with the fewest grid points (the oracle's cost)
+    return sorted(range(len(MEMBERS)), key=lambda i: MEMBERS[i][0] * MEMBERS[i][1])[:3]
+
+
+def test_fp64_ensemble_sampled_members_match_oracle():
+    import paper_2606_09468_gb300 as P
+    ctx = _ensemble(P.PTT_FP64)
+    ctx.step(2)
+    assert ctx.synchronize() == P.PTT_OK
+    for i in _sampled():
+        nx, ny, wi, seed = MEMBERS[i]
+        ora = O.Channel2D(O.Params(nx=nx, ny=ny, wi=wi, dt=I.DT, **FLUID))
+        ora.init_state(seed, I.AMPLITUDE)
+        ora.step()
+        ora.step()
+        e = _errs(I.abi_to_phys(ctx.get_state(i)), ora.get_physical())
+        assert np.all(e <= 2e-11), (i, MEMBERS[i], e)
+        assert ctx.diagnostics(i)[-1]["step"] == 2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ensemble_members_equal_runs_alone(precision):
+    ctx = _ensemble(precision)
+    ctx.step(3)
+    for i in (0, 17, 63):
+        alone = _ensemble(precision, [MEMBERS[i]])
+        alone.step(3)
+        assert np.array_equal(ctx.get_spectral(i), alone.get_spectral(0)), i
+        alone.close()
+
+
+def test_mixed_ensemble_within_stated_error_of_fp64():
+    import paper_2606_09468_gb300 as P
+    f = _ensemble(P.PTT_FP64)
+    m = _ensemble(P.PTT_MIXED)
+    f.step(1)
+    m.step(1)
+    worst = np.zeros(5)
+    for i in range(len(MEMBERS)):
+        e = _errs(I.abi_to_phys(m.get_state(i)), I.abi_to_phys(f.get_state(i)))
+        worst = np.maximum(worst, e)
+    print("mixed vs FP64 ensemble after 1 step, worst member per field", worst)
+    # stated one-step error of the mixed form (FP32 transforms and products)
+    assert np.all(worst <= 1e-8), worst
