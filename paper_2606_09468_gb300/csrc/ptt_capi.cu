@@ -421,6 +421,7 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     }
     d.NR = cv.take<double2>((size_t)nb * nf * NK);
     d.Rb = cv.take<double2>((size_t)nb * 4 * NK);
+    d.SS = d3 ? cv.take<double2>((size_t)nb * spec3_scratch_columns() * NK) : nullptr;
     d.qt = cv.take<double>((size_t)nb * 4 * 3 * 3 * NK);
     d.qtG = cv.take<double>((size_t)nb * 4 * 3 * 2 * KZ);
     d.vh = cv.take<double>((size_t)nb * 4 * NK);
@@ -570,8 +571,9 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
   }
   std::vector<Group> groups = make_groups(pm, nmem);
   for (Group& g : groups) {
-    if (g.d.nz == 1 && smem_xfused(g.d.Mx, g.d.f32) > 227 * 1024) return PTT_EINVAL;
-    if (g.d.nz > 1 && (smem_xfused3(g.d.Mx, g.d.f32) > 227 * 1024 || smem_spec3(g.d.N) > 227 * 1024))
+    if (g.d.nz == 1 && (smem_xfused(g.d.Mx, g.d.f32) > 227 * 1024 || smem_spec(g.d.N) > 227 * 1024))
+      return PTT_EINVAL;
+    if (g.d.nz > 1 && smem_xfused3(g.d.Mx, g.d.f32) > 227 * 1024)
       return PTT_EINVAL;
   }
   Carver cv;
@@ -605,7 +607,7 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   for (Group& g : c->groups) {
     if (g.d.nz == 1 && (smem_xfused(g.d.Mx, g.d.f32) > (size_t)optin || smem_spec(g.d.N) > (size_t)optin))
       return PTT_EINVAL;
-    if (g.d.nz > 1 && (smem_xfused3(g.d.Mx, g.d.f32) > (size_t)optin || smem_spec3(g.d.N) > (size_t)optin))
+    if (g.d.nz > 1 && smem_xfused3(g.d.Mx, g.d.f32) > (size_t)optin)
       return PTT_EINVAL;
   }
   CK(set_kernel_attributes(optin));

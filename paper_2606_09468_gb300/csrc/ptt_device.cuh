@@ -364,6 +364,125 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
   __syncwarp();
 }
 
+// Lane-sequential forms for the per-mode spectral stage: one lane owns one
+// (Fourier mode, Chebyshev parity) pair and walks its ~N/2 coefficients in
+// order, so a warp advances 32 independent recurrences with every lane busy.
+// Columns are indexed by n (stride 1); a lane touches only n = p mod 2 on
+// input and, for the derivative, only n = 1 - p mod 2 on output.
+
+// Chebyshev derivative, parity half: from the inputs a_k, k = p mod 2, the
+// outputs b_{k-1} = (k == 1 ? 1 : 2) sum_{k' >= k, k' = k mod 2} k' a_{k'}
+// (b_{n-1} = b_{n+1} + 2 n a_n, b_0 halved); the lane whose output parity is
+// that of N - 1 also writes b_{N-1} = 0.  The two lanes of one column
+// together produce the whole derivative; `out` must not alias `a`.
+__device__ __forceinline__ void lane_cheb_deriv(const double2* __restrict__ a,
+                                                double2* __restrict__ out, int N, int p) {
+  const int top = ((N - 1 - p) & ~1) + p;   // largest k = p mod 2 below N
+  double2 acc = czero();
+#pragma unroll 4
+  for (int k = top; k >= 1; k -= 2) {
+    acc = cfma((double)k, a[k], acc);
+    out[k - 1] = cscl(acc, k == 1 ? 1.0 : 2.0);
+  }
+  if (((N - 1) & 1) != p) out[N - 1] = czero();
+}
+
+// Quasi-tridiagonal tau solve of one parity (system stated at k_spec):
+// backward elimination P_n = (r_n - u_n P_{n+2}) inv_n with the three-term
+// right-hand side r_n of the twice-integrated rows, accumulating the
+// boundary sum U = sum F_n P_n; the boundary row gives
+// a_p = (bcfac sum_{n = p} rsign R_n - U) G; forward substitution
+// a_n = P_n + Q_n a_{n-2}.  Q, inv, F: the right-hand-side-independent
+// elimination factors of this (alpha, mode, parity), precomputed on the
+// host.  `out` must not alias R (every input is independent of the
+// recurrence, so unrolled iterations keep several loads in flight).
+__device__ __forceinline__ void lane_qt_solve(int N, int p, double alpha,
+                                              const double2* __restrict__ R,
+                                              double2* __restrict__ out,
+                                              const double* __restrict__ Q,
+                                              const double* __restrict__ inv,
+                                              const double* __restrict__ F, double G,
+                                              const double* __restrict__ w1,
+                                              const double* __restrict__ w2,
+                                              const double* __restrict__ w3, double bcfac,
+                                              double rsign) {
+  const int nl = ((N - 1 - p) & ~1) + p;
+  double2 Pn2 = czero(), U = czero(), rs = czero(), Rp2 = czero();
+  double2 R0 = cscl(R[nl], rsign);
+#pragma unroll 4
+  for (int n = nl; n >= p + 2; n -= 2) {
+    const double2 Rm2 = cscl(R[n - 2], rsign);
+    const double cc = (n == 2) ? 2.0 : 1.0;
+    double2 r = cscl(Rm2, -cc * w1[n]);
+    if (n <= N - 3) r = cfma(w2[n], R0, r);
+    double un = 0.0;
+    if (n <= N - 5) {
+      r = cfma(-w3[n], Rp2, r);
+      un = -alpha * w3[n];
+    }
+    const double2 P = cscl(cfma(-un, Pn2, r), inv[n]);
+    out[n] = P;
+    U = cfma(F[n], P, U);
+    rs = cadd(rs, R0);
+    Pn2 = P;
+    Rp2 = R0;
+    R0 = Rm2;
+  }
+  rs = cadd(rs, R0);   // R_p
+  double2 a = cscl(csub(cscl(rs, bcfac), U), G);
+  out[p] = a;
+#pragma unroll 4
+  for (int n = p + 2; n <= nl; n += 2) {
+    a = cfma(Q[n], a, out[n]);
+    out[n] = a;
+  }
+}
+
+// SBDF sum of one evolved column, parity p, order index O (0..3: SBDF1-4):
+// writes the current values x, nn into the history slot (E, Nn) and
+// R = sb_0 nn + sum_j (-sa_{j+1}/dt) x^{n-j} + sum_{j>=1} sb_j N^{n-j}
+// over the O older slots Eo[j-1], No[j-1].
+template <int O>
+__device__ __forceinline__ void lane_sbdf(int N, int p, double idt,
+                                          const double2* __restrict__ x,
+                                          const double2* __restrict__ nn,
+                                          double2* __restrict__ E, double2* __restrict__ Nn,
+                                          const double2* __restrict__ Eo0,
+                                          const double2* __restrict__ Eo1,
+                                          const double2* __restrict__ Eo2,
+                                          const double2* __restrict__ No0,
+                                          const double2* __restrict__ No1,
+                                          const double2* __restrict__ No2,
+                                          double2* __restrict__ R) {
+  const double ca0 = -c_sa[O][1] * idt, cb0 = c_sb[O][0];
+  const double ca1 = (O >= 1) ? -c_sa[O][2] * idt : 0.0, cb1 = (O >= 1) ? c_sb[O][1] : 0.0;
+  const double ca2 = (O >= 2) ? -c_sa[O][3] * idt : 0.0, cb2 = (O >= 2) ? c_sb[O][2] : 0.0;
+  const double ca3 = (O >= 3) ? -c_sa[O][4] * idt : 0.0, cb3 = (O >= 3) ? c_sb[O][3] : 0.0;
+#pragma unroll 4
+  for (int n = p; n < N; n += 2) {
+    const double2 xv = x[n], nv = nn[n];
+    E[n] = xv;
+    Nn[n] = nv;
+    double2 acc = cfma(cb0, nv, cscl(xv, ca0));
+    if (O >= 1) acc = cfma(cb1, No0[n], cfma(ca1, Eo0[n], acc));
+    if (O >= 2) acc = cfma(cb2, No1[n], cfma(ca2, Eo1[n], acc));
+    if (O >= 3) acc = cfma(cb3, No2[n], cfma(ca3, Eo2[n], acc));
+    R[n] = acc;
+  }
+}
+
+__device__ __forceinline__ void lane_sbdf_any(int o, int N, int p, double idt, const double2* x,
+                                              const double2* nn, double2* E, double2* Nn,
+                                              const double2* const* Eo, const double2* const* No,
+                                              double2* R) {
+  switch (o) {
+    case 0: lane_sbdf<0>(N, p, idt, x, nn, E, Nn, Eo[0], Eo[1], Eo[2], No[0], No[1], No[2], R); break;
+    case 1: lane_sbdf<1>(N, p, idt, x, nn, E, Nn, Eo[0], Eo[1], Eo[2], No[0], No[1], No[2], R); break;
+    case 2: lane_sbdf<2>(N, p, idt, x, nn, E, Nn, Eo[0], Eo[1], Eo[2], No[0], No[1], No[2], R); break;
+    default: lane_sbdf<3>(N, p, idt, x, nn, E, Nn, Eo[0], Eo[1], Eo[2], No[0], No[1], No[2], R); break;
+  }
+}
+
 // ---------------------------------------------- per-mode spectral stage
 // ------------------------------------------------------ Chebyshev columns
 // Column transforms along y for a batch of members and fields.  Coefficient

@@ -59,6 +59,7 @@ struct GroupDev {
   double* MV;        // 3D: mid-plane values [nb][8][nz][nx]
   double2* NR;       // [nb][5][K][N]  explicit nonlinear terms, spectral
   double2* Rb;       // [nb][4][K][N]  H_x, H_y of ptt_explicit_rhs
+  double2* SS;       // 3D: [nb][columns][KZ][N]  per-mode scratch of the spectral stage
   const double* qt;  // [nb][4 order][3 sys][3 (Q, inv, F)][K][N]
   const double* qtG; // [nb][4][3][2 parity][K]
   const double* vh;  // [nb][4][K][N]  homogeneous v of the influence step
@@ -114,7 +115,7 @@ cudaError_t launch_phys_to_state3(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_reset_member3(const GroupDev& g, int b, cudaStream_t st);
 size_t smem_xfused3(int Mx, int f32);
-size_t smem_spec3(int N);
+size_t spec3_scratch_columns();
 
 // Host helpers (ptt_capi.cu) used by the workspace-free entry point.
 void set_last_error(const char* msg);

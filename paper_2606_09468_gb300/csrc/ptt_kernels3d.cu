@@ -231,24 +231,44 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
 }
 
 // ---------------------------------------------- per-mode spectral stage
-// One block per (member, mode mx*nz + mz), 16 warps.  Columns in shared
-// memory.  Explicit terms (Eq. 2): H_i = N_u,i + gam (div c)_i (+ 2/Re on the
-// mean mode, x); forcings of the evolved velocity quantities (k != 0):
+// Explicit terms (Eq. 2): H_i = N_u,i + gam (div c)_i (+ 2/Re on the mean
+// mode, x); forcings of the evolved velocity quantities (k != 0):
 // q1 = -D(i kx H_x + i kz H_z) - k^2 H_y (phi = (D^2 - k^2) v),
 // q2 = i kz H_x - i kx H_z (eta = i kz u - i kx w); mean mode: H_x, H_z.
-// Evolved (8): c (6), q1 state, q2 state.  Solves (16 warp tasks): 12 c
-// (component, parity); k != 0: phi->v->influence correction (2 parities),
-// eta (2 parities); k = 0: U (2), W (2).  Then u = i (kx Dv - kz eta)/k^2,
-// w = i (kz Dv + kx eta)/k^2.
-size_t smem_spec3_bytes(int N) { return (size_t)24 * N * sizeof(double2) + (size_t)10 * N * sizeof(double); }
+// Evolved (8): c (6), q1 state, q2 state.  Solves per mode: six c (wall rows
+// of Eq. 1 at kappa = 0), phi -> v -> influence correction (k != 0) or U,
+// eta (k != 0) or W; then u = i (kx Dv - kz eta)/k^2, w = i (kz Dv + kx eta)/k^2.
+//
+// A block takes 16 modes; lane l of every warp owns mode l/2 of the block and
+// Chebyshev parity l%2, and each warp runs one component task of a phase, so
+// all recurrences run lane-sequentially with full warps.  Per-mode scratch
+// columns live in SS (workspace; L2-resident while the block runs):
+enum {
+  S3_DCXY = 0, S3_DCYY, S3_DCYZ, S3_DV, S3_D2V,   // derivatives of the state
+  S3_HX, S3_HY, S3_HZ,                             // explicit momentum terms H
+  S3_Q1, S3_Q2,                                    // evolved q1, q2 (state)
+  S3_F1T, S3_F1, S3_F2,                            // forcings of q1, q2
+  S3_R,                                            // 8 SBDF sums (13..20)
+  S3_DVN = S3_R + 8,                               // D of the new v
+  S3_PHI, S3_ETA,                                  // solved phi, eta
+  kScr3                                            // 24 columns per mode
+};
+constexpr int kModesPerBlock = 16;
 
-__global__ void __launch_bounds__(512) k_spec3(GroupDev g, int mode) {
+__global__ void __launch_bounds__(256) k_spec3(GroupDev g, int mode) {
   const int b = blockIdx.y;
-  const int md = blockIdx.x;
   if (g.status[b]) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = lane & 1;
   const int KZ = g.KZ, N = g.N, nb = g.nb, nz = g.nz;
-  const int mx = md / nz, mzi = md - mx * nz, hz = nz / 2;
   const size_t NK = (size_t)N * KZ;
+  const int md0 = blockIdx.x * kModesPerBlock + (lane >> 1);
+  const bool inb = md0 < KZ;
+  const int md = inb ? md0 : KZ - 1;
+  const int mx = md / nz, mzi = md - mx * nz, hz = nz / 2;
+  const bool nyq = (mzi == hz);
+  const bool act = inb && !nyq;
+  const bool mean = (mx == 0 && mzi == 0);
   const MemberPrm pr = g.prm[b];
   const long long cnt = g.count[b];
   const int slot = (int)(cnt & 3);
@@ -257,193 +277,186 @@ __global__ void __launch_bounds__(512) k_spec3(GroupDev g, int mode) {
   const double kx = 2.0 * 3.14159265358979323846 * mx / pr.lx;
   const double kz = 2.0 * 3.14159265358979323846 * sz / pr.lz;
   const double k2 = kx * kx + kz * kz;
-  const bool mean = (mx == 0 && mzi == 0);
-  const bool nyq = (mzi == hz);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  double2* sm = reinterpret_cast<double2*>(smraw);
-  double2* sc = sm;               // [6][N] c -> new c
-  double2* su = sm + 6 * N;       // u -> new u
-  double2* sv = sm + 7 * N;       // v -> new v
-  double2* sw = sm + 8 * N;       // w -> new w
-  double2* sH = sm + 9 * N;       // [3][N] N_u -> H
-  double2* sq = sm + 12 * N;      // [2][N] evolved q1, q2
-  double2* sn = sm + 14 * N;      // [2][N] forcings of q1, q2
-  double2* sR = sm + 16 * N;      // [8][N] SBDF sums / temporaries
-  double* tb = reinterpret_cast<double*>(sm + 24 * N);  // [3 sys][Q, inv, F][N], vh[N]
-  const double2* X = g.X + (size_t)b * 9 * NK + (size_t)md * N;
-  const double2* NR = g.NR + (size_t)b * 9 * NK + (size_t)md * N;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  double2* Xw = g.X + (size_t)b * 9 * NK + (size_t)md * N;
-  if (nyq) {   // the dropped Nyquist slot stays zero
-    if (mode == 0) {
-      for (int i = tid; i < 9 * N; i += nt) Xw[(size_t)(i / N) * NK + (i % N)] = czero();
-      double2* E = g.Eh + ((size_t)slot * nb + b) * 8 * NK + (size_t)md * N;
-      double2* Nn = g.Nh + ((size_t)slot * nb + b) * 8 * NK + (size_t)md * N;
-      for (int i = tid; i < 8 * N; i += nt) {
-        E[(size_t)(i / N) * NK + (i % N)] = czero();
-        Nn[(size_t)(i / N) * NK + (i % N)] = czero();
-      }
-    } else {
-      double2* R = g.Rb + (size_t)b * 4 * NK + (size_t)md * N;
-      for (int i = tid; i < 3 * N; i += nt) R[(size_t)(i / N) * NK + (i % N)] = czero();
-    }
-    return;
-  }
-  for (int i = tid; i < N; i += nt) {
-    for (int c = 0; c < 6; ++c) sc[c * N + i] = X[(3 + c) * NK + i];
-    su[i] = X[i];
-    sv[i] = X[NK + i];
-    sw[i] = X[2 * NK + i];
-    for (int c = 0; c < 3; ++c) sH[c * N + i] = NR[(6 + c) * NK + i];
-  }
-  if (mode == 0) {
-    const double* qt = g.qt + ((size_t)b * 4 + o) * 3 * 3 * NK + (size_t)md * N;
-    for (int i = tid; i < 9 * N; i += nt) {
-      const int w = i / N, n = i - w * N;
-      tb[i] = qt[(size_t)w * NK + n];
-    }
-    const double* vh = g.vh + ((size_t)b * 4 + o) * NK + (size_t)md * N;
-    for (int i = tid; i < N; i += nt) tb[9 * N + i] = vh[i];
-  }
-  __syncthreads();
-  // D c_xy -> sR0, D c_yy -> sR1, D c_yz -> sR2; D v -> sR3 -> D^2 v -> sR4
-  if (warp == 0) warp_cheb_deriv(sc + 1 * N, sR, N);
-  else if (warp == 1) warp_cheb_deriv(sc + 3 * N, sR + N, N);
-  else if (warp == 2) warp_cheb_deriv(sc + 4 * N, sR + 2 * N, N);
-  else if (warp == 3 && mode == 0 && !mean) {
-    warp_cheb_deriv(sv, sR + 3 * N, N);
-    warp_cheb_deriv(sR + 3 * N, sR + 4 * N, N);
-  }
-  __syncthreads();
+  const size_t col = (size_t)md * N;
+  double2* X = g.X + (size_t)b * 9 * NK + col;          // field f at X + f * NK
+  const double2* NR = g.NR + (size_t)b * 9 * NK + col;
+  double2* S = g.SS + (size_t)b * kScr3 * NK + col;     // scratch column a at S + a * NK
+  auto SC = [&](int a) { return S + (size_t)a * NK; };
   const double gam = pr.gam;
-  for (int n = tid; n < N; n += nt) {
-    // (div c)_x = i kx c_xx + D c_xy + i kz c_xz, etc.
-    const double2 dx = cadd(cscl(mul_i(sc[0 * N + n]), kx), cadd(sR[n], cscl(mul_i(sc[2 * N + n]), kz)));
-    const double2 dy = cadd(cscl(mul_i(sc[1 * N + n]), kx), cadd(sR[N + n], cscl(mul_i(sc[4 * N + n]), kz)));
-    const double2 dzv = cadd(cscl(mul_i(sc[2 * N + n]), kx), cadd(sR[2 * N + n], cscl(mul_i(sc[5 * N + n]), kz)));
-    double2 hx = cfma(gam, dx, sH[n]);
-    if (mean && n == 0) hx.x += pr.forcing;
-    sH[n] = hx;
-    sH[N + n] = cfma(gam, dy, sH[N + n]);
-    sH[2 * N + n] = cfma(gam, dzv, sH[2 * N + n]);
+
+  // the dropped Nyquist slot stays zero
+  if (warp == 0 && inb && nyq) {
     if (mode == 0) {
-      if (mean) {
-        sq[n] = su[n];
-        sq[N + n] = sw[n];
-      } else {
-        sq[n] = cfma(-k2, sv[n], sR[4 * N + n]);
-        sq[N + n] = csub(cscl(mul_i(su[n]), kz), cscl(mul_i(sw[n]), kx));
+      for (int f = 0; f < 9; ++f)
+        for (int n = p; n < N; n += 2) X[f * NK + n] = czero();
+      double2* E = g.Eh + ((size_t)slot * nb + b) * 8 * NK + col;
+      double2* Nn = g.Nh + ((size_t)slot * nb + b) * 8 * NK + col;
+      for (int s2 = 0; s2 < 8; ++s2)
+        for (int n = p; n < N; n += 2) { E[s2 * NK + n] = czero(); Nn[s2 * NK + n] = czero(); }
+    } else {
+      double2* R = g.Rb + (size_t)b * 4 * NK + col;
+      for (int f = 0; f < 3; ++f)
+        for (int n = p; n < N; n += 2) R[f * NK + n] = czero();
+    }
+  }
+  // phase 1: derivatives D c_xy, D c_yy, D c_yz; D v, D^2 v
+  if (act) {
+    if (warp == 0) lane_cheb_deriv(X + 4 * NK, SC(S3_DCXY), N, p);
+    else if (warp == 1) lane_cheb_deriv(X + 6 * NK, SC(S3_DCYY), N, p);
+    else if (warp == 2) lane_cheb_deriv(X + 7 * NK, SC(S3_DCYZ), N, p);
+  }
+  if (warp == 3) {
+    const bool d = act && mode == 0 && !mean;
+    if (d) lane_cheb_deriv(X + NK, SC(S3_DV), N, p);
+    __syncwarp();
+    if (d) lane_cheb_deriv(SC(S3_DV), SC(S3_D2V), N, p);
+  }
+  __syncthreads();
+  // phase 2: H (warps 0-2), evolved q1, q2 (warps 3, 4)
+  if (act) {
+    if (warp < 3) {
+      // (div c)_i = i kx c_xi + D c_yi + i kz c_zi
+      const int cx = (warp == 0) ? 3 : (warp == 1) ? 4 : 5;     // c_xx, c_xy, c_xz
+      const int cz = (warp == 0) ? 5 : (warp == 1) ? 7 : 8;     // c_xz, c_yz, c_zz
+      const double2* __restrict__ cxv = X + (size_t)cx * NK;
+      const double2* __restrict__ czv = X + (size_t)cz * NK;
+      const double2* __restrict__ dcy = SC(S3_DCXY + warp);
+      const double2* __restrict__ nu = NR + (size_t)(6 + warp) * NK;
+      double2* __restrict__ H = SC(S3_HX + warp);
+      const double fx = (warp == 0 && mean) ? pr.forcing : 0.0;
+#pragma unroll 4
+      for (int n = p; n < N; n += 2) {
+        const double2 dv = cadd(cscl(mul_i(cxv[n]), kx), cadd(dcy[n], cscl(mul_i(czv[n]), kz)));
+        double2 h = cfma(gam, dv, nu[n]);
+        if (n == 0) h.x += fx;
+        H[n] = h;
       }
+    } else if (warp == 3 && mode == 0) {
+      double2* __restrict__ q = SC(S3_Q1);
+      const double2* __restrict__ d2v = SC(S3_D2V);
+      const double2* __restrict__ u = X;
+      const double2* __restrict__ v = X + NK;
+#pragma unroll 4
+      for (int n = p; n < N; n += 2) q[n] = mean ? u[n] : cfma(-k2, v[n], d2v[n]);
+    } else if (warp == 4 && mode == 0) {
+      double2* __restrict__ q = SC(S3_Q2);
+      const double2* __restrict__ u = X;
+      const double2* __restrict__ w = X + 2 * NK;
+#pragma unroll 4
+      for (int n = p; n < N; n += 2)
+        q[n] = mean ? w[n] : csub(cscl(mul_i(u[n]), kz), cscl(mul_i(w[n]), kx));
     }
   }
   __syncthreads();
-  if (mode == 1) {
-    double2* R = g.Rb + (size_t)b * 4 * NK + (size_t)md * N;
-    for (int i = tid; i < 3 * N; i += nt) R[(size_t)(i / N) * NK + (i % N)] = sH[i];
+  if (mode == 1) {   // explicit right-hand side only: H -> Rb
+    if (act && warp < 3) {
+      double2* R = g.Rb + (size_t)b * 4 * NK + col + (size_t)warp * NK;
+      const double2* H = SC(S3_HX + warp);
+      for (int n = p; n < N; n += 2) R[n] = H[n];
+    }
     return;
   }
-  // forcing of q1: -D(i kx H_x + i kz H_z) - k^2 H_y
-  if (!mean) {
-    for (int n = tid; n < N; n += nt)
-      sR[5 * N + n] = cadd(cscl(mul_i(sH[n]), kx), cscl(mul_i(sH[2 * N + n]), kz));
-    __syncthreads();
-    if (warp == 0) warp_cheb_deriv(sR + 5 * N, sR + 6 * N, N);
-    __syncthreads();
-  }
-  for (int n = tid; n < N; n += nt) {
-    if (mean) {
-      sn[n] = sH[n];
-      sn[N + n] = sH[2 * N + n];
-    } else {
-      sn[n] = csub(cscl(sR[6 * N + n], -1.0), cscl(sH[N + n], k2));
-      sn[N + n] = csub(cscl(mul_i(sH[n]), kz), cscl(mul_i(sH[2 * N + n]), kx));
-    }
+  // phase 3: forcings of q1 (warp 0), q2 (warp 1)
+  if (warp == 0) {
+    const bool d = act && !mean;
+    const double2* Hx = SC(S3_HX);
+    const double2* Hy = SC(S3_HY);
+    const double2* Hz = SC(S3_HZ);
+    double2* t = SC(S3_F1T);
+    double2* f = SC(S3_F1);
+    if (d)
+      for (int n = p; n < N; n += 2) t[n] = cadd(cscl(mul_i(Hx[n]), kx), cscl(mul_i(Hz[n]), kz));
+    __syncwarp();
+    if (d) lane_cheb_deriv(t, f, N, p);
+    __syncwarp();
+    if (act)
+      for (int n = p; n < N; n += 2) f[n] = mean ? Hx[n] : csub(cscl(f[n], -1.0), cscl(Hy[n], k2));
+  } else if (warp == 1 && act) {
+    const double2* Hx = SC(S3_HX);
+    const double2* Hz = SC(S3_HZ);
+    double2* f = SC(S3_F2);
+    for (int n = p; n < N; n += 2)
+      f[n] = mean ? Hz[n] : csub(cscl(mul_i(Hx[n]), kz), cscl(mul_i(Hz[n]), kx));
   }
   __syncthreads();
-  // history slot and SBDF sums of the 8 evolved quantities
-  {
-    double2* E = g.Eh + ((size_t)slot * nb + b) * 8 * NK + (size_t)md * N;
-    double2* Nn = g.Nh + ((size_t)slot * nb + b) * 8 * NK + (size_t)md * N;
-    const double idt = 1.0 / pr.dt;
-    for (int i = tid; i < 8 * N; i += nt) {
-      const int s = i / N, n = i - s * N;
-      const double2 x = (s < 6) ? sc[s * N + n] : sq[(s - 6) * N + n];
-      const double2 nn = (s < 6) ? NR[(size_t)s * NK + n] : sn[(s - 6) * N + n];
-      E[s * NK + n] = x;
-      Nn[s * NK + n] = nn;
-      double2 acc = cfma(c_sb[o][0], nn, cscl(x, -c_sa[o][1] * idt));
-      for (int jj = 1; jj <= o; ++jj) {
-        const size_t sl = (size_t)((slot - jj) & 3);
-        const double2 eo = g.Eh[(sl * nb + b) * 8 * NK + (size_t)s * NK + (size_t)md * N + n];
-        const double2 no = g.Nh[(sl * nb + b) * 8 * NK + (size_t)s * NK + (size_t)md * N + n];
-        acc = cfma(c_sb[o][jj], no, cfma(-c_sa[o][jj + 1] * idt, eo, acc));
+  // phase 4: history slot and SBDF sums, warp s for evolved quantity s
+  if (act) {
+    const int s2 = warp;
+    const double2* x = (s2 < 6) ? X + (size_t)(3 + s2) * NK : SC(S3_Q1 + (s2 - 6));
+    const double2* nn = (s2 < 6) ? NR + (size_t)s2 * NK : SC(S3_F1 + (s2 - 6));
+    double2* E = g.Eh + ((size_t)slot * nb + b) * 8 * NK + (size_t)s2 * NK + col;
+    double2* Nn = g.Nh + ((size_t)slot * nb + b) * 8 * NK + (size_t)s2 * NK + col;
+    double2* R = SC(S3_R + s2);
+    const double2* Eo[3];
+    const double2* No[3];
+    for (int jj = 1; jj <= 3; ++jj) {
+      const size_t sl = (size_t)((slot - jj) & 3);
+      Eo[jj - 1] = g.Eh + (sl * nb + b) * 8 * NK + (size_t)s2 * NK + col;
+      No[jj - 1] = g.Nh + (sl * nb + b) * 8 * NK + (size_t)s2 * NK + col;
+    }
+    lane_sbdf_any(o, N, p, 1.0 / pr.dt, x, nn, E, Nn, Eo, No, R);
+  }
+  __syncthreads();
+  // phase 5: tau solves; warps 0-5 the c components, 6 q1, 7 q2
+  if (act) {
+    const double* w1 = g.wrow;
+    const double* w2 = g.wrow + N;
+    const double* w3 = g.wrow + 2 * N;
+    const double a0 = c_sa[o][0];
+    const double* qt = g.qt + ((size_t)b * 4 + o) * 3 * 3 * NK + col;
+    auto T = [&](int sys, int k) { return qt + (size_t)(sys * 3 + k) * NK; };
+    auto G = [&](int sys) { return g.qtG[((((size_t)b * 4 + o) * 3 + sys) * 2 + p) * KZ + md]; };
+    if (warp < 6) {
+      const double2* R = SC(S3_R + warp);
+      double2* out = X + (size_t)(3 + warp) * NK;
+      const double alpha = a0 / pr.dt + pr.kappa * k2;
+      if (pr.kappa == 0.0) {
+        const double ia = 1.0 / alpha;
+        for (int n = p; n < N; n += 2) out[n] = cscl(R[n], ia);
+      } else {
+        lane_qt_solve(N, p, alpha, R, out, T(0, 0), T(0, 1), T(0, 2), G(0), w1, w2, w3,
+                      pr.dt / a0, 1.0);
       }
-      sR[s * N + n] = acc;
+    } else if (warp == 6) {
+      double2* R1 = SC(S3_R + 6);
+      if (mean) {
+        lane_qt_solve(N, p, a0 / pr.dt, R1, X, T(1, 0), T(1, 1), T(1, 2), G(1), w1, w2, w3, 0.0, 1.0);
+        for (int n = p; n < N; n += 2) X[NK + n] = czero();
+      } else {
+        double2* v = X + NK;
+        double2* phi = SC(S3_PHI);
+        lane_qt_solve(N, p, a0 / pr.dt + pr.nu * k2, R1, phi, T(1, 0), T(1, 1), T(1, 2), G(1), w1,
+                      w2, w3, 0.0, 1.0);
+        lane_qt_solve(N, p, k2, phi, v, T(2, 0), T(2, 1), T(2, 2), G(2), w1, w2, w3, 0.0, -1.0);
+        double2 sacc = czero();
+        for (int n = p; n < N; n += 2) sacc = cfma((double)n * n, v[n], sacc);
+        const double* vh = g.vh + ((size_t)b * 4 + o) * NK + col;
+        const double2 coef = cscl(sacc, -g.vhS[(((size_t)b * 4 + o) * 2 + p) * KZ + md]);
+        for (int n = p; n < N; n += 2)
+          v[n] = make_double2(fma(coef.x, vh[n], v[n].x), fma(coef.y, vh[n], v[n].y));
+      }
+    } else {
+      double2* R2 = SC(S3_R + 7);
+      const double alpha = mean ? a0 / pr.dt : a0 / pr.dt + pr.nu * k2;
+      double2* out = mean ? X + 2 * NK : SC(S3_ETA);   // W, or eta
+      lane_qt_solve(N, p, alpha, R2, out, T(1, 0), T(1, 1), T(1, 2), G(1), w1, w2, w3, 0.0, 1.0);
     }
   }
   __syncthreads();
-  const double* w1 = g.wrow;
-  const double* w2 = g.wrow + N;
-  const double* w3 = g.wrow + 2 * N;
-  const double a0 = c_sa[o][0];
-  const double* T0 = tb;
-  const double* T1 = tb + 3 * N;
-  const double* T2 = tb + 6 * N;
-  auto G = [&](int ts, int p) { return g.qtG[((((size_t)b * 4 + o) * 3 + ts) * 2 + p) * KZ + md]; };
-  if (warp < 12) {            // c components
-    const int comp = warp >> 1, p = warp & 1;
-    double2* out = sc + (size_t)comp * N;
-    const double2* R = sR + (size_t)comp * N;
-    const double alpha = a0 / pr.dt + pr.kappa * k2;
-    if (pr.kappa == 0.0) {
-      const double ia = 1.0 / alpha;
-      for (int n = p + 2 * lane; n < N; n += 64) out[n] = cscl(R[n], ia);
-    } else {
-      warp_qt_solve(N, p, alpha, R, out, T0, T0 + N, T0 + 2 * N, G(0, p), w1, w2, w3, pr.dt / a0, 1.0);
+  // phase 6: u, w from D v and eta (k != 0)
+  if (warp == 0) {
+    const bool d = act && !mean;
+    double2* dv = SC(S3_DVN);
+    if (d) lane_cheb_deriv(X + NK, dv, N, p);
+    __syncwarp();
+    if (d) {
+      const double2* et = SC(S3_ETA);
+      const double ik2 = 1.0 / k2;
+      for (int n = p; n < N; n += 2) {
+        X[n] = cscl(mul_i(csub(cscl(dv[n], kx), cscl(et[n], kz))), ik2);
+        X[2 * NK + n] = cscl(mul_i(cadd(cscl(dv[n], kz), cscl(et[n], kx))), ik2);
+      }
     }
-  } else if (warp < 14) {     // q1: phi -> v (k != 0) or U (mean)
-    const int p = warp - 12;
-    double2* R1 = sR + 6 * N;
-    if (mean) {
-      warp_qt_solve(N, p, a0 / pr.dt, R1, su, T1, T1 + N, T1 + 2 * N, G(1, p), w1, w2, w3, 0.0, 1.0);
-      for (int n = p + 2 * lane; n < N; n += 64) sv[n] = czero();
-    } else {
-      warp_qt_solve(N, p, a0 / pr.dt + pr.nu * k2, R1, R1, T1, T1 + N, T1 + 2 * N, G(1, p), w1, w2,
-                    w3, 0.0, 1.0);
-      warp_qt_solve(N, p, k2, R1, sv, T2, T2 + N, T2 + 2 * N, G(2, p), w1, w2, w3, 0.0, -1.0);
-      double2 sacc = czero();
-      for (int n = p + 2 * lane; n < N; n += 64) sacc = cfma((double)n * n, sv[n], sacc);
-      sacc = warp_allsum2(sacc);
-      const double* vh = tb + 9 * N;
-      const double2 coef = cscl(sacc, -g.vhS[(((size_t)b * 4 + o) * 2 + p) * KZ + md]);
-      for (int n = p + 2 * lane; n < N; n += 64)
-        sv[n] = make_double2(fma(coef.x, vh[n], sv[n].x), fma(coef.y, vh[n], sv[n].y));
-    }
-  } else {                    // q2: eta (k != 0) or W (mean); eta kept in sR[7]
-    const int p = warp - 14;
-    double2* R2 = sR + 7 * N;
-    const double alpha = mean ? a0 / pr.dt : a0 / pr.dt + pr.nu * k2;
-    double2* out = mean ? sw : R2;
-    warp_qt_solve(N, p, alpha, R2, out, T1, T1 + N, T1 + 2 * N, G(1, p), w1, w2, w3, 0.0, 1.0);
-  }
-  __syncthreads();
-  if (!mean) {   // u, w from D v and eta
-    if (warp == 0) warp_cheb_deriv(sv, sR, N);
-    __syncthreads();
-    const double ik2 = 1.0 / k2;
-    for (int n = tid; n < N; n += nt) {
-      const double2 dv = sR[n], et = sR[7 * N + n];
-      su[n] = cscl(mul_i(csub(cscl(dv, kx), cscl(et, kz))), ik2);
-      sw[n] = cscl(mul_i(cadd(cscl(dv, kz), cscl(et, kx))), ik2);
-    }
-    __syncthreads();
-  }
-  for (int i = tid; i < N; i += nt) {
-    Xw[i] = su[i];
-    Xw[NK + i] = sv[i];
-    Xw[2 * NK + i] = sw[i];
-    for (int c = 0; c < 6; ++c) Xw[(3 + c) * NK + i] = sc[c * N + i];
   }
 }
 
@@ -751,7 +764,7 @@ cudaError_t optin3(F* fn, int optin_bytes) {
 }  // namespace
 
 size_t smem_xfused3(int Mx, int f32) { return (size_t)36 * Mx * (f32 ? sizeof(float2) : sizeof(double2)); }
-size_t smem_spec3(int N) { return smem_spec3_bytes(N); }
+size_t spec3_scratch_columns() { return kScr3; }
 
 cudaError_t set_kernel_attributes3(int optin_bytes) {
   cudaError_t e;
@@ -762,7 +775,6 @@ cudaError_t set_kernel_attributes3(int optin_bytes) {
   if ((e = optin3(k_xfused3<double2>, optin_bytes))) return e;
   if ((e = optin3(k_xfused3<float2>, optin_bytes))) return e;
   if ((e = optin3(k_xrows, optin_bytes))) return e;
-  if ((e = optin3(k_spec3, optin_bytes))) return e;
   return cudaSuccess;
 }
 
@@ -845,7 +857,7 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       break;
     }
     case 3:
-      k_spec3<<<dim3(KZ, g.nb), 512, smem_spec3(g.N), st>>>(g, 0);
+      k_spec3<<<dim3(cdiv(KZ, kModesPerBlock), g.nb), 256, 0, st>>>(g, 0);
       k_tick3<<<cdiv(g.nb, 128), 128, 0, st>>>(g);
       n = 2;
       break;
@@ -920,7 +932,7 @@ cudaError_t launch_explicit3(const GroupDev& g, cudaStream_t st) {
     cudaError_t e = launch_stage3(g, s, st, nullptr);
     if (e) return e;
   }
-  k_spec3<<<dim3(g.KZ, g.nb), 512, smem_spec3(g.N), st>>>(g, 1);
+  k_spec3<<<dim3(cdiv(g.KZ, kModesPerBlock), g.nb), 256, 0, st>>>(g, 1);
   return cudaGetLastError();
 }
 
