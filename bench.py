@@ -260,8 +260,12 @@ def only_workload(args):
     for i, s in enumerate(seeds):
         ctx.init_state(i, s, I.AMPLITUDE)
     ms = _timed(ctx, args.steps, args.warmup)
+    status = P.ptt_status_string(ctx.synchronize())
+    nst = max(args.steps // 2, 2)
+    st = ctx.time_stages(nst)
     print(json.dumps({"workload": name, "value": pts * 1e3 / ms, "unit": METRIC, "ms_per_step": ms,
-                      "steps": args.steps, "status": P.ptt_status_string(ctx.synchronize())}))
+                      "steps": args.steps, "status": status,
+                      "stage_ms_per_step": {P.STAGE_NAMES[i]: st[i] / nst for i in range(P.PTT_NSTAGES)}}))
 
 
 def other_workloads(args):

@@ -113,6 +113,23 @@ template <int DIR> struct Bfly<DIR, 5> {
   }
 };
 
+// Division by a runtime divisor d through a multiply-high: with
+// m = floor((2^32 - 1)/d) + 1 = ceil(2^32/d), floor(x/d) = (x m) >> 32 holds
+// exactly whenever x d < 2^32 (the rounding excess of m contributes less than
+// x/2^32 < 1/d), which covers every index of the transforms here
+// (x < 2^20, d < 2^12).  d = 1 is passed through.
+struct FastDiv {
+  unsigned m;
+  bool one;
+};
+__device__ __forceinline__ FastDiv fast_div(unsigned d) {
+  FastDiv f;
+  f.one = (d == 1u);
+  f.m = f.one ? 0u : 0xFFFFFFFFu / d + 1u;
+  return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned x, FastDiv f) { return f.one ? x : __umulhi(x, f.m); }
+
 // One Stockham pass of radix R over nl lines (line l at offset l*ls).
 template <int DIR, int R, typename C2>
 __device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restrict__ dst,
@@ -121,12 +138,14 @@ __device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restr
   const int nb = n / R;
   const int st = n / (Ns * R);
   const int total = nl * nb;
+  const FastDiv dnb = fast_div((unsigned)nb), dns = fast_div((unsigned)Ns);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int l = t / nb;
+    const int l = (int)fdiv((unsigned)t, dnb);
     const int j = t - l * nb;
     const C2* s = src + l * ls;
     C2* d = dst + l * ls;
-    const int jm = j % Ns;
+    const int jq = (int)fdiv((unsigned)j, dns);
+    const int jm = j - jq * Ns;
     C2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[j + r * nb];
@@ -139,7 +158,7 @@ __device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restr
       }
     }
     Bfly<DIR, R>::run(v);
-    const int o = (j / Ns) * Ns * R + jm;
+    const int o = jq * Ns * R + jm;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[o + r * Ns] = v[r];
   }

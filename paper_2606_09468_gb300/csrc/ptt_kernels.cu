@@ -541,6 +541,7 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
     double2 ux = cscl(mul_i(u), km), vx = cscl(mul_i(v), km);
     if (m == 0) { tr.x += 1.0; u = czero(); tr.y = v.y = uy.y = 0.0; ux = vx = czero(); }
     const double2 F[6] = {tr, u, v, ux, vx, uy};
+#pragma unroll
     for (int l = 0; l < 3; ++l) {
       L[l * nx + m] = cadd(F[2 * l], mul_i(F[2 * l + 1]));
       if (m > 0) L[l * nx + nx - m] = cadd(cconj(F[2 * l]), mul_i(cconj(F[2 * l + 1])));
@@ -548,30 +549,35 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
   }
   __syncthreads();
   double2* res = fft_lines<+1>(L, L2, 3, nx, g.plNx);
-  double sums[6][4];
-  long long m3 = 0, m0 = 0, mb3 = 0, mb0 = 0;
-  for (int q = 0; q < 6; ++q) for (int k = 0; k < 4; ++k) sums[q][k] = 0.0;
+  // mid-plane counts (4) and power sums (6 quantities x 4 powers), one pass
+  double acc[28];
+#pragma unroll
+  for (int k = 0; k < 28; ++k) acc[k] = 0.0;
   for (int x = threadIdx.x; x < nx; x += blockDim.x) {
     double q[6];
+#pragma unroll
     for (int l = 0; l < 3; ++l) { q[2 * l] = res[l * nx + x].x; q[2 * l + 1] = res[l * nx + x].y; }
-    m3 += (q[0] < 3.0); m0 += (q[0] < 0.0);
-    mb3 += (fabs(q[0] - 3.0) <= tau); mb0 += (fabs(q[0]) <= tau);
+    acc[0] += (q[0] < 3.0);
+    acc[1] += (q[0] < 0.0);
+    acc[2] += (fabs(q[0] - 3.0) <= tau);
+    acc[3] += (fabs(q[0]) <= tau);
+#pragma unroll
     for (int qq = 0; qq < 6; ++qq) {
       const double a = q[qq], a2 = a * a;
-      sums[qq][0] += a; sums[qq][1] += a2; sums[qq][2] += a2 * a; sums[qq][3] += a2 * a2;
+      acc[4 + 4 * qq] += a;
+      acc[5 + 4 * qq] += a2;
+      acc[6 + 4 * qq] += a2 * a;
+      acc[7 + 4 * qq] += a2 * a2;
     }
   }
-  double msum[6][4];
-  for (int qq = 0; qq < 6; ++qq) for (int k = 0; k < 4; ++k) msum[qq][k] = block_sum(sums[qq][k], sh);
-  double mc[4] = {(double)m3, (double)m0, (double)mb3, (double)mb0};
-  double mct[4];
-  for (int q = 0; q < 4; ++q) mct[q] = block_sum(mc[q], sh);
+  __shared__ double red[8 * 28];
+  block_sum_many<28>(acc, red);
   if (threadIdx.x == 0) {
     const double e = 0.25 * te, mn = tmn, mx = tmx, *c4 = tc;
     const bool bad = (tbad != 0.0);
     const long long step = g.count[b];
     const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-    ptt_diag r;
+    ptt_diag& r = g.ring[(size_t)b * kRing + (size_t)(step % kRing)];
     r.step = step;
     r.t = step * pr.dt;
     r.energy = e;
@@ -580,14 +586,13 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
     r.max_trc = bad ? qnan : mx;
     r.n_lt3 = (long long)c4[0]; r.n_lt0 = (long long)c4[1];
     r.n_band3 = (long long)c4[2]; r.n_band0 = (long long)c4[3];
-    r.n_mid_lt3 = (long long)mct[0]; r.n_mid_lt0 = (long long)mct[1];
-    r.n_mid_band3 = (long long)mct[2]; r.n_mid_band0 = (long long)mct[3];
+    r.n_mid_lt3 = (long long)red[0]; r.n_mid_lt0 = (long long)red[1];
+    r.n_mid_band3 = (long long)red[2]; r.n_mid_band0 = (long long)red[3];
     for (int qq = 0; qq < 8; ++qq)
-      for (int k = 0; k < 4; ++k) r.mid_sums[qq][k] = (qq < 6) ? msum[qq][k] : 0.0;
+      for (int k = 0; k < 4; ++k) r.mid_sums[qq][k] = (qq < 6) ? red[4 + 4 * qq + k] : 0.0;
     const bool blow = bad || !isfinite(e) || r.max_trc > pr.trc_max || sqrt(2.0 * e) > pr.u_max;
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
-    g.ring[(size_t)b * kRing + (size_t)(step % kRing)] = r;
     if (blow) g.status[b] = 1;
   }
 }

@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
     const bool bad = (tbad != 0.0);
     const long long step = g.count[b];
     const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-    ptt_diag r;
+    ptt_diag& r = g.ring[(size_t)b * kRing + (size_t)(step % kRing)];
     r.step = step;
     r.t = step * pr.dt;
     r.energy = e;
@@ -704,7 +704,6 @@ __global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
     const bool blow = bad || !isfinite(e) || r.max_trc > pr.trc_max || sqrt(2.0 * e) > pr.u_max;
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
-    g.ring[(size_t)b * kRing + (size_t)(step % kRing)] = r;
     if (blow) g.status[b] = 1;
   }
 }
