@@ -146,6 +146,19 @@ int ptt_get_state(ptt_ctx* ctx, int32_t member, double* h_phys);
 int ptt_set_spectral(ptt_ctx* ctx, int32_t member, const double* h_spec);
 int ptt_get_spectral(ptt_ctx* ctx, int32_t member, double* h_spec);
 
+/* Spectral re-interpolation (Sec. 2: a snapshot re-interpolated onto the
+ * grids of runs at other resolutions).  Sets the state of member dst_member
+ * of dst to the current state of member src_member of src, coefficient by
+ * coefficient: Fourier modes (kx, and in 3D kz by signed wavenumber) and
+ * Chebyshev modes present in both shapes are copied, modes only the
+ * destination has are zero, modes only the source has are dropped (the x and
+ * z Nyquist slots stay zero).  Both members must be 2D or both 3D; their
+ * periodic lengths should agree (not checked).  Both contexts must live on
+ * the current device; src and dst may be the same context.  Resets the
+ * destination's step counter and SBDF history and writes its diagnostics
+ * record, as ptt_set_spectral does.  Synchronous (waits for both streams). */
+int ptt_resample(ptt_ctx* dst, int32_t dst_member, ptt_ctx* src, int32_t src_member);
+
 /* Advance every member by nsteps steps (asynchronous on the context stream;
  * each step is one CUDA-graph launch).  A member that blows up stops and
  * keeps its last record's status; the others continue.  Returns PTT_OK or an
@@ -161,6 +174,23 @@ int ptt_synchronize(ptt_ctx* ctx);
  * 1024 steps).  Synchronous. */
 int ptt_diagnostics(ptt_ctx* ctx, int32_t member, ptt_diag* h_out, int32_t max_records,
                     int32_t* n_written);
+
+/* Mid-plane histograms (Sec. 3: the PDFs of Tr c, of the velocity
+ * fluctuations and of the velocity gradients at the mid-plane).  For each of
+ * the 8 mid-plane quantities of ptt_diag.mid_sums (same order), counts over
+ * PTT_HIST_BINS uniform bins on [lo[q], hi[q]): a value x goes to bin
+ * 1 + min(floor((x - lo) * (PTT_HIST_BINS / (hi - lo))), PTT_HIST_BINS - 1)
+ * (both factors in FP64), to slot 0 if x < lo, to slot PTT_HIST_BINS + 1 if
+ * x >= hi or x is not finite.  lo[q] >= hi[q] switches quantity q off.
+ * ptt_set_histograms sets the ranges of one member and zeroes its counts;
+ * from then on every diagnostics record written for the member (each step,
+ * and the record written by ptt_init_state / ptt_set_state /
+ * ptt_set_spectral / ptt_set_checkpoint) adds its nx * nz mid-plane values.
+ * ptt_get_histograms copies the counts, int64_t[8][PTT_HIST_BINS + 2].
+ * Histograms are not part of a checkpoint.  Synchronous. */
+#define PTT_HIST_BINS 256
+int ptt_set_histograms(ptt_ctx* ctx, int32_t member, const double* lo, const double* hi);
+int ptt_get_histograms(ptt_ctx* ctx, int32_t member, int64_t* counts);
 
 /* Dealiased explicit right-hand side of the current state of one member
  * (Eq. 1 without kappa lap c; Eq. 2 without pressure and viscous terms) in

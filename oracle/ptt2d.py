@@ -444,6 +444,7 @@ class Channel2D:
         out["n_mid_band3"] = int(np.sum(np.abs(tr_m - 3.0) <= tau))
         out["n_mid_band0"] = int(np.sum(np.abs(tr_m) <= tau))
         out["mid_sums"] = np.array([[np.sum(qq ** k) for k in range(1, 5)] for qq in q])
+        out["mid_values"] = [np.asarray(qq, dtype=float).ravel() for qq in q]
         # blow-up (the paper reports finite-time blow-up below a resolution
         # threshold, Sec. 2; its criterion is not stated): a non-finite state,
         # max Tr c above a threshold, or an rms velocity sqrt(2E) above one.
@@ -453,3 +454,26 @@ class Channel2D:
             math.sqrt(max(2.0 * out["energy"], 0.0)) > p.blowup_u_max
         out["blowup"] = bool(blow)
         return out
+
+
+HIST_BINS = 256
+
+
+def midplane_histogram(values, lo, hi, nbins=HIST_BINS):
+    """Counts of `values` over nbins uniform bins on [lo, hi) with an
+    underflow slot (x < lo) in front and an overflow slot (x >= hi, or not
+    finite) behind, as the library's mid-plane histograms define them (the
+    PDFs of Sec. 3, Figs. 5-8).  Bin of x: floor((x - lo) * (nbins / (hi - lo))),
+    clamped to nbins - 1, both factors in FP64.  Plain loop over the values."""
+    counts = np.zeros(nbins + 2, dtype=np.int64)
+    if not lo < hi:
+        return counts
+    scale = float(nbins) / (hi - lo)
+    for x in np.asarray(values, dtype=float).ravel():
+        if not math.isfinite(x) or x >= hi:
+            counts[nbins + 1] += 1
+        elif x < lo:
+            counts[0] += 1
+        else:
+            counts[1 + min(int(math.floor((x - lo) * scale)), nbins - 1)] += 1
+    return counts

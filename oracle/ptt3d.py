@@ -409,6 +409,7 @@ class Channel3D:
         out["n_mid_band3"] = int(np.sum(np.abs(trm - 3.0) <= tau))
         out["n_mid_band0"] = int(np.sum(np.abs(trm) <= tau))
         out["mid_sums"] = np.array([[np.sum(qq ** k) for k in range(1, 5)] for qq in q])
+        out["mid_values"] = [np.asarray(qq, dtype=float).ravel() for qq in q]
         finite = all(np.all(np.isfinite(a)) for a in s.as_list())
         out["blowup"] = bool((not finite) or not np.isfinite(out["max_trc"]) or
                              out["max_trc"] > p.blowup_trc_max or

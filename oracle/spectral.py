@@ -19,7 +19,7 @@ __all__ = [
     "gl_points", "cheb_eval_matrix", "cheb_at", "dct1_analysis_matrix",
     "cheb_diff_matrix", "fourier_eval_matrix", "fourier_to_phys",
     "fourier_to_spec", "to_phys", "to_spec", "padded_sizes",
-    "product_dealiased", "product_bruteforce",
+    "product_dealiased", "product_bruteforce", "resample_2d", "resample_3d",
 ]
 
 
@@ -178,3 +178,32 @@ def product_bruteforce(a, b):
                     if abs(p - q) < N:
                         res[m, abs(p - q)] += w
     return res
+
+
+def resample_2d(a, K, N):
+    """Spectral re-interpolation of a 2D field a[m, n] (m < K_src Fourier
+    modes, n < N_src Chebyshev modes) onto K x N modes: coefficients present
+    in both are copied, the others are zero (padding) or dropped
+    (truncation).  The coefficients do not depend on the grid size, so this
+    is the whole re-interpolation (Sec. 2)."""
+    out = np.zeros((K, N), dtype=complex)
+    k, n = min(K, a.shape[0]), min(N, a.shape[1])
+    out[:k, :n] = a[:k, :n]
+    return out
+
+
+def resample_3d(a, K, nz, N):
+    """The same for a 3D field a[mx, mz, n], mz in FFT order (signed
+    wavenumber s = mz for mz < nz/2, mz - nz above; the Nyquist slot nz/2 is
+    not a mode): the mode of signed wavenumber s is copied when |s| < nz/2
+    on both sides."""
+    Ks, nzs, Ns = a.shape
+    out = np.zeros((K, nz, N), dtype=complex)
+    k, n = min(K, Ks), min(N, Ns)
+    for mz in range(nz):
+        if mz == nz // 2:
+            continue
+        s = mz if mz < nz // 2 else mz - nz
+        if -(nzs // 2) < s < nzs // 2:
+            out[:k, mz, :n] = a[:k, s % nzs, :n]
+    return out

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libptt.so")
 PTT_OK, PTT_BLOWUP = 0, 1
 PTT_EINVAL, PTT_ENOMEM, PTT_ECUDA, PTT_TIMEOUT, PTT_ENOTSUP = -1, -2, -3, -4, -5
 PTT_FP64, PTT_MIXED = 0, 1
+PTT_HIST_BINS = 256
 
 
 class ptt_params(ctypes.Structure):
@@ -54,6 +55,9 @@ _SIGS = {
     "ptt_synchronize": [_VP],
     "ptt_diagnostics": [_VP, _I32, ctypes.POINTER(ptt_diag), _I32, ctypes.POINTER(_I32)],
     "ptt_explicit_rhs": [_VP, _I32, _DP],
+    "ptt_set_histograms": [_VP, _I32, _DP, _DP],
+    "ptt_resample": [_VP, _I32, _VP, _I32],
+    "ptt_get_histograms": [_VP, _I32, ctypes.POINTER(ctypes.c_int64)],
     "ptt_explicit_rhs_noalloc": [ctypes.POINTER(ptt_params), _VP, _VP, _VP],
     "ptt_checkpoint_size": [_VP, _I32, ctypes.POINTER(_SZ)],
     "ptt_get_checkpoint": [_VP, _I32, _VP, _SZ],
@@ -172,6 +176,24 @@ def ptt_diagnostics(ctx, member, max_records=1024):
 
 def ptt_explicit_rhs(ctx, member, out):
     _check("ptt_explicit_rhs", load_library().ptt_explicit_rhs(ctx, member, _dptr(out)))
+    return out
+
+
+def ptt_resample(dst_ctx, dst_member, src_ctx, src_member):
+    _check("ptt_resample", load_library().ptt_resample(dst_ctx, dst_member, src_ctx, src_member))
+
+
+def ptt_set_histograms(ctx, member, lo, hi):
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    assert lo.shape == (8,) and hi.shape == (8,)
+    _check("ptt_set_histograms", load_library().ptt_set_histograms(ctx, member, _dptr(lo), _dptr(hi)))
+
+
+def ptt_get_histograms(ctx, member):
+    out = np.zeros((8, PTT_HIST_BINS + 2), dtype=np.int64)
+    _check("ptt_get_histograms", load_library().ptt_get_histograms(
+        ctx, member, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
     return out
 
 
@@ -294,6 +316,17 @@ class Context:
 
     def get_spectral(self, member):
         return ptt_get_spectral(self.ctx, member, self.spec_buffer(member))
+
+    def resample_from(self, member, src, src_member):
+        """State of `member` <- state of `src_member` of context `src`,
+        spectrally re-interpolated onto this member's shape."""
+        ptt_resample(self.ctx, member, src.ctx, src_member)
+
+    def set_histograms(self, member, lo, hi):
+        ptt_set_histograms(self.ctx, member, lo, hi)
+
+    def histograms(self, member):
+        return ptt_get_histograms(self.ctx, member)
 
     def explicit_rhs(self, member):
         return ptt_explicit_rhs(self.ctx, member, self.spec_buffer(member))

@@ -438,6 +438,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.DMZ = d3 ? cv.take<double2>((size_t)nb * 8 * nzz * K) : nullptr;
     d.MV = d3 ? cv.take<double>((size_t)nb * 8 * nzz * d.nx) : nullptr;
     d.ring = cv.take<ptt_diag>((size_t)nb * kRing);
+    d.hist = cv.take<unsigned long long>((size_t)nb * 8 * (PTT_HIST_BINS + 2));
+    d.hrange = cv.take<double>((size_t)nb * 16);
     d.stage = cv.take<double>((size_t)nf * d.N * nzz * d.nx);
     d.stageS = cv.take<double2>((size_t)nf * NK);
     FftPlan* pls[7] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe, &d.plMz, &d.plNz};
@@ -923,6 +925,52 @@ int ptt_diagnostics(ptt_ctx* c, int32_t member, ptt_diag* out, int32_t maxr, int
   }
   if (n > 0) c->last_read[member] = first + n - 1;
   *nw = n;
+  return PTT_OK;
+}
+
+int ptt_resample(ptt_ctx* dst, int32_t dm, ptt_ctx* src, int32_t sm) {
+  if (!member_ok(dst, dm) || !member_ok(src, sm)) return PTT_EINVAL;
+  if (dst->device != src->device) return PTT_EINVAL;
+  auto [dgi, db] = dst->where[dm];
+  auto [sgi, sb] = src->where[sm];
+  const GroupDev& dg = dst->groups[dgi].d;
+  const GroupDev& sg = src->groups[sgi].d;
+  if ((dg.nz > 1) != (sg.nz > 1)) return PTT_EINVAL;
+  if (dst == src && dm == sm) return PTT_OK;
+  CK(cudaStreamSynchronize(src->stream));
+  CK(launch_resample(dg, db, sg, sb, dst->stream));
+  const bool d3 = dg.nz > 1;
+  CK(d3 ? launch_reset_member3(dg, db, dst->stream) : launch_reset_member(dg, db, dst->stream));
+  CK(d3 ? launch_diag3(dg, dst->stream, nullptr) : launch_diag(dg, dst->stream, nullptr));
+  CK(cudaStreamSynchronize(dst->stream));
+  dst->last_read[dm] = -1;
+  return PTT_OK;
+}
+
+int ptt_set_histograms(ptt_ctx* c, int32_t member, const double* lo, const double* hi) {
+  if (!member_ok(c, member) || !lo || !hi) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  double r[16];
+  for (int q = 0; q < 8; ++q) {
+    r[2 * q] = lo[q];
+    r[2 * q + 1] = hi[q];
+  }
+  const size_t nh = (size_t)8 * (PTT_HIST_BINS + 2);
+  CK(cudaMemcpyAsync(const_cast<double*>(g.d.hrange) + (size_t)b * 16, r, sizeof(r),
+                     cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(g.d.hist + (size_t)b * nh, 0, nh * sizeof(unsigned long long), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PTT_OK;
+}
+
+int ptt_get_histograms(ptt_ctx* c, int32_t member, int64_t* counts) {
+  if (!member_ok(c, member) || !counts) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  const size_t nh = (size_t)8 * (PTT_HIST_BINS + 2);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(counts, g.d.hist + (size_t)b * nh, nh * sizeof(int64_t), cudaMemcpyDeviceToHost));
   return PTT_OK;
 }
 

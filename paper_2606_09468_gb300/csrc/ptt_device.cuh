@@ -866,6 +866,17 @@ __device__ void block_sum_many(const double (&v)[NV], double* red) {
   __syncthreads();
 }
 
+// Histogram slot of x for the range [lo, hi) (PTT_HIST_BINS uniform bins,
+// slot 0 below lo, slot PTT_HIST_BINS + 1 at or above hi or not finite);
+// -1 when the quantity is switched off (lo >= hi).
+__device__ __forceinline__ int hist_slot(double x, double lo, double hi) {
+  if (!(lo < hi)) return -1;
+  if (!isfinite(x) || x >= hi) return PTT_HIST_BINS + 1;
+  if (x < lo) return 0;
+  const int k = (int)floor((x - lo) * ((double)PTT_HIST_BINS / (hi - lo)));
+  return 1 + min(k, PTT_HIST_BINS - 1);
+}
+
 // Block-wide max of v (fixed order), valid in thread 0.
 __device__ double block_tiles_max_val(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));

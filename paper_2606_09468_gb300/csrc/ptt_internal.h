@@ -72,6 +72,8 @@ struct GroupDev {
   double* part;      // [nb][ntile][kPart]  partial reductions
   double2* DM;       // [nb][4][K]  mid-plane Chebyshev sums per Fourier mode
   ptt_diag* ring;    // [nb][kRing]
+  unsigned long long* hist;  // [nb][8][PTT_HIST_BINS + 2] mid-plane histograms
+  const double* hrange;      // [nb][8][2] (lo, hi); lo >= hi: quantity off
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
   double2* stageS;   // [5][N][K]  values on the unpadded y grid, x analysed
   const double2* tw4P;  // [M]  exp(-i pi k/(2M)), padded Gauss grid
@@ -105,6 +107,9 @@ cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_state_to_phys(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_reset_member(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t set_kernel_attributes(int max_dyn_smem);
+// state of member bs of group s -> state of member bd of group d, modes
+// copied, padded with zeros or truncated (both 2D or both 3D)
+cudaError_t launch_resample(const GroupDev& d, int bd, const GroupDev& s, int bs, cudaStream_t st);
 // 3D (ptt_kernels3d.cu)
 cudaError_t set_kernel_attributes3(int max_dyn_smem);
 cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nlaunch);

@@ -19,6 +19,7 @@
 // Layouts: spectral arrays [member][field][m][n] (each mode's Chebyshev
 // column contiguous); values on a y grid [member][field][j][m] (each y row's
 // Fourier modes contiguous).
+#include <algorithm>
 #include <cstdio>
 
 #include "ptt_device.cuh"
@@ -549,6 +550,16 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
   }
   __syncthreads();
   double2* res = fft_lines<+1>(L, L2, 3, nx, g.plNx);
+  // mid-plane histograms of the 6 quantities (shared-memory counts)
+  constexpr int HS = PTT_HIST_BINS + 2;
+  __shared__ unsigned int hsm[6 * HS];
+  __shared__ double hr[12];
+  if (threadIdx.x < 12) hr[threadIdx.x] = g.hrange[(size_t)b * 16 + threadIdx.x];
+  for (int i = threadIdx.x; i < 6 * HS; i += blockDim.x) hsm[i] = 0u;
+  __syncthreads();
+  bool hon = false;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) hon |= (hr[2 * q] < hr[2 * q + 1]);
   // mid-plane counts (4) and power sums (6 quantities x 4 powers), one pass
   double acc[28];
 #pragma unroll
@@ -557,6 +568,13 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
     double q[6];
 #pragma unroll
     for (int l = 0; l < 3; ++l) { q[2 * l] = res[l * nx + x].x; q[2 * l + 1] = res[l * nx + x].y; }
+    if (hon) {
+#pragma unroll
+      for (int qq = 0; qq < 6; ++qq) {
+        const int sl = hist_slot(q[qq], hr[2 * qq], hr[2 * qq + 1]);
+        if (sl >= 0) atomicAdd(&hsm[qq * HS + sl], 1u);
+      }
+    }
     acc[0] += (q[0] < 3.0);
     acc[1] += (q[0] < 0.0);
     acc[2] += (fabs(q[0] - 3.0) <= tau);
@@ -571,7 +589,12 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
     }
   }
   __shared__ double red[8 * 28];
-  block_sum_many<28>(acc, red);
+  block_sum_many<28>(acc, red);   // its barriers also complete the shared counts
+  if (hon) {
+    unsigned long long* gh = g.hist + (size_t)b * 8 * HS;
+    for (int i = threadIdx.x; i < 6 * HS; i += blockDim.x)
+      if (hsm[i]) atomicAdd(&gh[i], (unsigned long long)hsm[i]);
+  }
   if (threadIdx.x == 0) {
     const double e = 0.25 * te, mn = tmn, mx = tmx, *c4 = tc;
     const bool bad = (tbad != 0.0);
@@ -594,6 +617,42 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
     if (blow) g.status[b] = 1;
+  }
+}
+
+// Spectral re-interpolation: destination coefficient (field, mode, n) from
+// the source's same Fourier wavenumber(s) and Chebyshev index, zero where the
+// source has none.  Modes: 2D m < K; 3D mx * nz + mz with mz in FFT order.
+struct ResampleJob {
+  const double2* src;   // source member's state [nf][KZs][Ns]
+  double2* dst;         // destination member's state [nf][KZd][Nd]
+  int nf;
+  int Kd, nzd, Nd;      // destination x modes, z slots, Chebyshev modes
+  int Ks, nzs, Ns;
+};
+
+__global__ void __launch_bounds__(256) k_resample(ResampleJob J) {
+  const long long KZd = (long long)J.Kd * J.nzd, NKd = KZd * J.Nd;
+  const long long NKs = (long long)J.Ks * J.nzs * J.Ns;
+  const long long tot = (long long)J.nf * NKd;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(i / NKd);
+    const long long r = i - f * NKd;
+    const int md = (int)(r / J.Nd), n = (int)(r - (long long)md * J.Nd);
+    const int mx = md / J.nzd, mzd = md - mx * J.nzd;
+    double2 v = czero();
+    if (mx < J.Ks && n < J.Ns) {
+      int mzs = -1;
+      if (J.nzd == 1) {
+        mzs = 0;
+      } else if (mzd != J.nzd / 2) {
+        const int sgn = (mzd < J.nzd / 2) ? mzd : mzd - J.nzd;   // signed wavenumber
+        if (sgn > -J.nzs / 2 && sgn < J.nzs / 2) mzs = (sgn >= 0) ? sgn : sgn + J.nzs;
+      }
+      if (mzs >= 0) v = J.src[f * NKs + ((long long)mx * J.nzs + mzs) * J.Ns + n];
+    }
+    J.dst[i] = v;
   }
 }
 
@@ -629,6 +688,20 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl,
 }
 
 }  // namespace
+
+cudaError_t launch_resample(const GroupDev& d, int bd, const GroupDev& s, int bs, cudaStream_t st) {
+  ResampleJob J;
+  J.nf = (d.nz > 1) ? 9 : 5;
+  J.Kd = d.K; J.nzd = d.nz; J.Nd = d.N;
+  J.Ks = s.K; J.nzs = s.nz; J.Ns = s.N;
+  J.src = s.X + (size_t)bs * J.nf * s.N * s.KZ;
+  J.dst = d.X + (size_t)bd * J.nf * d.N * d.KZ;
+  const long long tot = (long long)J.nf * d.KZ * d.N;
+  const unsigned blocks = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 16);
+  k_resample<<<blocks, 256, 0, st>>>(J);
+  return cudaGetLastError();
+}
+
 
 size_t smem_ycols(int C, int P, int f32) {
   return (size_t)(2 * C * P + 2 * C) * (f32 ? sizeof(float2) : sizeof(double2));

@@ -575,7 +575,14 @@ __global__ void __launch_bounds__(256) k_diag_count3(GroupDev g) {
     const double* MV = g.MV + (size_t)b * 8 * npl;
     const int per = (npl + g.ntile - 1) / g.ntile;
     const int i0 = tile * per, i1 = min(npl, i0 + per);
+    const double* hr = g.hrange + (size_t)b * 16;
+    unsigned long long* gh = g.hist + (size_t)b * 8 * (PTT_HIST_BINS + 2);
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {   // mid-plane histograms
+        const int sl = hist_slot(MV[(size_t)q * npl + i], hr[2 * q], hr[2 * q + 1]);
+        if (sl >= 0) atomicAdd(&gh[q * (PTT_HIST_BINS + 2) + sl], 1ULL);
+      }
       const double t = MV[i];
       cnt[4] += (t < 3.0);
       cnt[5] += (t < 0.0);
