@@ -62,10 +62,13 @@ def parse():
     ap.add_argument("--no-workloads", dest="workloads", action="store_false",
                     help="skip the 3D and ensemble workloads")
     ap.add_argument("--workload-steps", type=int, default=40)
+    ap.add_argument("--paper-shapes", action="store_true",
+                    help="also time the paper's A1-A6 shapes (3D, mixed; FP64 where nx <= 256)")
     ap.add_argument("--only", default=None,
                     help="run one workload alone (3d_fp64, 3d_mixed, 3d_fp64_large, "
-                         "3d_mixed_large, ensemble_mixed, ensemble_fp64) and print its line; "
-                         "for profiling")
+                         "3d_mixed_large, ensemble_mixed, ensemble_fp64) and print its line, "
+                         "for profiling; or midplane_stats: mixed vs FP64 mid-plane statistics "
+                         "of the 3D workload over --steps steps")
     return ap.parse_args()
 
 
@@ -237,10 +240,71 @@ def _dev(a, b):
     return [float(np.max(np.abs(x - y)) / np.max(np.abs(y))) for x, y in zip(a, b)]
 
 
+MID3D = ["Tr c", "u'", "w'", "du/dx", "du/dz", "dw/dx", "dw/dz", "v"]
+
+
+def midplane_stats(args):
+    """Mid-plane statistics of the 3D 128x97x64 workload over --steps steps,
+    mixed precision against FP64 from the same initial state: window
+    moments (mean, sigma, skewness, kurtosis) from the per-step power sums
+    and 256-bin histograms of the 8 mid-plane quantities.  Criteria: mean
+    difference / sigma, relative sigma difference, skewness and kurtosis
+    differences / max(1, |FP64 value|) all <= 0.05; histogram L1 distance
+    < 0.05 (the paper judges resolutions by such statistics, Sec. 3)."""
+    import numpy as np
+    import paper_2606_09468_gb300 as P
+    nx, ny, nz = I.CHANNEL3D
+    npts = nx * nz
+    steps = args.steps
+    out = {"workload": "midplane_stats", "shape": [nx, ny, nz], "steps": steps, "quantities": MID3D}
+    lo = hi = None
+    res = {}
+    for prec, tag in ((P.PTT_FP64, "fp64"), (P.PTT_MIXED, "mixed")):
+        ctx = P.Context([P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=prec,
+                                       **I.PAPER)])
+        ctx.init_state(0, 0, I.AMPLITUDE)
+        r0 = ctx.diagnostics(0)
+        if lo is None:
+            m0 = P.midplane_moments(r0, npts)
+            span = np.maximum(8 * m0[:, 1], 1e-6 * np.maximum(1.0, np.abs(m0[:, 0])))
+            lo, hi = m0[:, 0] - span, m0[:, 0] + span
+        ctx.set_histograms(0, lo, hi)
+        recs = []
+        t0 = time.time()
+        done = 0
+        while done < steps:
+            k = min(500, steps - done)
+            ctx.step(k)
+            done += k
+            recs += ctx.diagnostics(0, 1024)
+        status = P.ptt_status_string(ctx.synchronize())
+        res[tag] = {"moments": P.midplane_moments(recs, npts), "hist": ctx.histograms(0),
+                    "records": len(recs), "status": status, "seconds": time.time() - t0}
+        ctx.close()
+    f, m = res["fp64"]["moments"], res["mixed"]["moments"]
+    sd = np.where(f[:, 1] > 0, f[:, 1], 1.0)
+    crit = {
+        "mean_diff_over_sigma": (np.abs(m[:, 0] - f[:, 0]) / sd).tolist(),
+        "sigma_rel_diff": (np.abs(m[:, 1] - f[:, 1]) / sd).tolist(),
+        "skewness_diff": (np.abs(m[:, 2] - f[:, 2]) / np.maximum(1.0, np.abs(f[:, 2]))).tolist(),
+        "kurtosis_diff": (np.abs(m[:, 3] - f[:, 3]) / np.maximum(1.0, np.abs(f[:, 3]))).tolist(),
+        "histogram_l1": [P.histogram_l1(res["mixed"]["hist"][q], res["fp64"]["hist"][q]) for q in range(8)],
+    }
+    worst = max(max(v) for k, v in crit.items() if k != "histogram_l1")
+    out.update({"fp64_moments": f.tolist(), "mixed_moments": m.tolist(), "criteria": crit,
+                "worst_moment_criterion": worst, "worst_histogram_l1": max(crit["histogram_l1"]),
+                "pass": bool(worst <= 0.05 and max(crit["histogram_l1"]) < 0.05),
+                "records": res["fp64"]["records"], "status": [res["fp64"]["status"], res["mixed"]["status"]],
+                "seconds": [res["fp64"]["seconds"], res["mixed"]["seconds"]]})
+    print(json.dumps(out))
+
+
 def only_workload(args):
     """One workload alone, --steps steps after --warmup (for ncu captures)."""
     import paper_2606_09468_gb300 as P
     name = args.only
+    if name == "midplane_stats":
+        return midplane_stats(args)
     prec = P.PTT_MIXED if "mixed" in name else P.PTT_FP64
     if name.startswith("3d"):
         nx, ny, nz = I.CHANNEL3D_LARGE if name.endswith("large") else I.CHANNEL3D
@@ -339,6 +403,45 @@ def other_workloads(args):
         "workload": "64 independent 2D runs, seeds 0-63, Nx in the 5-smooth multiples of 32 in "
                     "[64, 512], Ny in {65,97,129,161,193,257}, Wi uniform in [50, 200] (splitmix64 "
                     "draws of the run index), one context, one CUDA graph per step"}
+    return out
+
+
+def paper_shapes(args):
+    """The paper's production shapes (Table 1) at its box and time step, a few
+    steps each, with the wall time the paper's run length (T/Wi = 68,
+    dt = 2.5e-3) would take at the measured rate on this one GPU.  The
+    paper's own cost, on CPU cores of ARCHER2: A1 2e5 core-hours, A6 1.6e6
+    core-hours (context, not a target)."""
+    import torch
+    import paper_2606_09468_gb300 as P
+    out = {}
+    steps_run = 68 * I.PAPER["wi"] / I.PAPER_DT
+    paper_core_hours = {"A1": 2e5, "A6": 1.6e6}
+    for name, (nx, ny, nz) in I.PAPER_SHAPES.items():
+        pts = nx * ny * nz
+        row = {"shape": [nx, ny, nz], "grid_points": pts}
+        for prec, tag in ((P.PTT_MIXED, "mixed"), (P.PTT_FP64, "fp64")):
+            prm = P.make_params(nx=nx, ny=ny, nz=nz, lz=I.PAPER_LZ, dt=I.PAPER_DT, precision=prec,
+                                **{k: v for k, v in I.PAPER.items()})
+            try:
+                P.ptt_workspace_size([prm])
+            except P.PttError as e:
+                row[tag] = {"unsupported": str(e)}
+                continue
+            ctx = P.Context([prm])
+            ctx.init_state(0, 0, I.AMPLITUDE)
+            ms = _timed(ctx, 5, 2)
+            rate = pts * 1e3 / ms
+            row[tag] = {"value": rate, "unit": METRIC, "ms_per_step": ms, "steps": 5,
+                        "workspace_gib": ctx.nbytes / 2**30,
+                        "status": P.ptt_status_string(ctx.synchronize()),
+                        "hours_for_paper_run": steps_run * ms * 1e-3 / 3600}
+            ctx.close()
+            del ctx
+            torch.cuda.empty_cache()
+        if name in paper_core_hours:
+            row["paper_archer2_core_hours"] = paper_core_hours[name]
+        out[name] = row
     return out
 
 
@@ -482,6 +585,9 @@ def run_ours(args):
     if rank != 0:
         return
     workloads = other_workloads(args) if args.workloads else None
+    if args.paper_shapes:
+        workloads = dict(workloads or {})
+        workloads["paper_shapes"] = paper_shapes(args)
     ws = ctx.nbytes
     out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

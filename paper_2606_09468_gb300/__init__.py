@@ -366,3 +366,35 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------- window statistics (host)
+def midplane_moments(records, npoints):
+    """Window statistics of the mid-plane quantities (Sec. 3, Figs. 5-8) from
+    diagnostics records: the per-step power sums mid_sums[q][p-1] = sum x^p
+    over the npoints mid-plane points are added over the records, then
+    mean, standard deviation, skewness and kurtosis (fourth standardised
+    moment) follow from the raw moments.  Returns an (8, 4) array."""
+    S = np.zeros((8, 4))
+    for r in records:
+        S += np.asarray(r["mid_sums"], dtype=float)
+    n = float(npoints) * len(records)
+    m1, m2, m3, m4 = (S[:, k] / n for k in range(4))
+    var = np.maximum(m2 - m1 * m1, 0.0)
+    sd = np.sqrt(var)
+    c3 = m3 - 3 * m1 * m2 + 2 * m1 ** 3
+    c4 = m4 - 4 * m1 * m3 + 6 * m1 * m1 * m2 - 3 * m1 ** 4
+    with np.errstate(divide="ignore", invalid="ignore"):
+        skew = np.where(sd > 0, c3 / sd ** 3, 0.0)
+        kurt = np.where(sd > 0, c4 / var ** 2, 0.0)
+    return np.stack([m1, sd, skew, kurt], axis=1)
+
+
+def histogram_l1(a, b):
+    """L1 distance between two histograms of one quantity, each normalised
+    to unit total count (0: identical PDFs, 2: disjoint)."""
+    a = np.asarray(a, dtype=float)
+    b = np.asarray(b, dtype=float)
+    if a.sum() == 0 or b.sum() == 0:
+        return 0.0 if a.sum() == b.sum() else 2.0
+    return float(np.abs(a / a.sum() - b / b.sum()).sum())

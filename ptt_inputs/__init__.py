@@ -161,3 +161,12 @@ def phys3_to_abi(fields):
 
 def abi_to_phys3(arr):
     return [np.ascontiguousarray(np.transpose(arr[f], (2, 0, 1))) for f in range(arr.shape[0])]
+
+
+# The paper's production shapes (Table 1, (Nx, Ny, Nz)), with Ny + 1
+# Chebyshev modes: the unpadded Gauss-Lobatto grid wants ny - 1 of the form
+# 2^a 3^b 5^c.  Box Lx = Lz = 10, dt = 2.5e-3, run length T/Wi = 68 (A1, A6).
+PAPER_SHAPES = {"A1": (128, 513, 128), "A2": (512, 129, 128), "A3": (256, 257, 256),
+                "A4": (512, 257, 128), "A5": (512, 129, 256), "A6": (512, 129, 512)}
+PAPER_DT = 2.5e-3
+PAPER_LZ = 10.0
