@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-workloads", dest="workloads", action="store_false",
                     help="skip the 3D and ensemble workloads")
     ap.add_argument("--workload-steps", type=int, default=40)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="time the default launch shapes instead of the autotuned ones")
     ap.add_argument("--paper-shapes", action="store_true",
                     help="also time the paper's A1-A6 shapes (3D, mixed; FP64 where nx <= 256)")
     ap.add_argument("--only", default=None,
@@ -219,10 +221,16 @@ def run_reference(args):
 
 
 # ------------------------------------------------------- other workloads
+AUTOTUNE = True
+
+
 def _timed(ctx, steps, warmup):
     """Device milliseconds per step of `steps` graph-launched steps (CUDA
-    events on the context stream) after `warmup` untimed steps."""
+    events on the context stream) after `warmup` untimed steps; the context's
+    launch shapes are autotuned first unless --no-autotune."""
     import torch
+    if AUTOTUNE:
+        ctx.autotune()
     ctx.step(warmup)
     ctx.synchronize()
     torch.cuda.synchronize()
@@ -462,6 +470,7 @@ def run_ours(args):
     ctx = P.Context(params)
     for i, (_, _, s) in enumerate(members):
         ctx.init_state(i, s, I.AMPLITUDE)
+    tuned = ctx.autotune()[:9].tolist() if args.autotune else None
     points = sum(nx * ny for nx, ny, _ in members)
     stream = ctx.stream
 
@@ -555,6 +564,8 @@ def run_ours(args):
         fctx = P.Context([params[-1]])
         for i, (_, _, s) in enumerate(members):
             mctx.init_state(i, s, I.AMPLITUDE)
+        if args.autotune:
+            mctx.autotune()
         fctx.init_state(0, members[-1][2], I.AMPLITUDE)
         mctx.step(args.warmup)
         fctx.step(args.warmup)
@@ -596,7 +607,9 @@ def run_ours(args):
                       "parallelism": f"ensemble of independent runs per GPU x {world} GPU",
                       "l2": f"inputs larger than L2: workspace {ws / 2**30:.2f} GiB per GPU, "
                             "state + SBDF history re-read every step",
-                      "graph": "one CUDA graph launch per step"},
+                      "graph": "one CUDA graph launch per step",
+                      "launch_shapes": ("autotuned (columns, lines, threads) per shape group: %s" % tuned)
+                      if tuned else "defaults"},
            "status": P.ptt_status_string(status),
            "gpu_launches": launches, "roofline": roofline, "clocks": clk, "e2e": e2e}
     if mixed is not None:
@@ -609,7 +622,9 @@ def run_ours(args):
 
 
 def main():
+    global AUTOTUNE
     args = parse()
+    AUTOTUNE = args.autotune
     if args.only:
         only_workload(args)
     elif args.impl == "reference":

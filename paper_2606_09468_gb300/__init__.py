@@ -57,6 +57,7 @@ _SIGS = {
     "ptt_explicit_rhs": [_VP, _I32, _DP],
     "ptt_set_histograms": [_VP, _I32, _DP, _DP],
     "ptt_resample": [_VP, _I32, _VP, _I32],
+    "ptt_autotune": [_VP, ctypes.POINTER(_I32), _I32],
     "ptt_get_histograms": [_VP, _I32, ctypes.POINTER(ctypes.c_int64)],
     "ptt_explicit_rhs_noalloc": [ctypes.POINTER(ptt_params), _VP, _VP, _VP],
     "ptt_checkpoint_size": [_VP, _I32, ctypes.POINTER(_SZ)],
@@ -176,6 +177,15 @@ def ptt_diagnostics(ctx, member, max_records=1024):
 
 def ptt_explicit_rhs(ctx, member, out):
     _check("ptt_explicit_rhs", load_library().ptt_explicit_rhs(ctx, member, _dptr(out)))
+    return out
+
+
+def ptt_autotune(ctx, max_groups=256):
+    """Tune the launch shapes of every shape group; returns an int array
+    (groups, 3) of the chosen (columns, lines, threads)."""
+    out = np.zeros((max_groups, 3), dtype=np.int32)
+    _check("ptt_autotune", load_library().ptt_autotune(ctx, out.ctypes.data_as(ctypes.POINTER(_I32)),
+                                                       max_groups))
     return out
 
 
@@ -316,6 +326,10 @@ class Context:
 
     def get_spectral(self, member):
         return ptt_get_spectral(self.ctx, member, self.spec_buffer(member))
+
+    def autotune(self):
+        """Launch-shape autotuning of every shape group (results unchanged)."""
+        return ptt_autotune(self.ctx)
 
     def resample_from(self, member, src, src_member):
         """State of `member` <- state of `src_member` of context `src`,

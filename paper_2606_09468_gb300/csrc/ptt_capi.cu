@@ -380,6 +380,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       const int want = (int)((long long)d.KZ * nfields * nb / 304);
       return std::max(1, std::min(c, want));
     };
+    d.xthreads = 512;
+    d.zC = 8;
     d.Ccol = cap(d.Ccol, 9);
     d.CcolE = cap(d.CcolE, 2);
     d.CcolU = cap(d.CcolU, 1);
@@ -584,6 +586,32 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
   return PTT_OK;
 }
 
+// Capture one step of every group (step + diagnostics) as one CUDA graph:
+// a fork per group from the capture stream, a join back (replaces an
+// existing graph).
+static int capture_step_graph(ptt_ctx* c) {
+  if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  int nl = 0;
+  cudaError_t le = cudaEventRecord(c->gevents.back(), c->cap);
+  for (size_t gi = 0; gi < c->groups.size() && !le; ++gi) {
+    cudaStream_t gs = c->gstreams[gi];
+    le = cudaStreamWaitEvent(gs, c->gevents.back(), 0);
+    const GroupDev& gd = c->groups[gi].d;
+    if (!le) le = (gd.nz > 1) ? launch_step3(gd, gs, &nl) : launch_step(gd, gs, &nl);
+    if (!le) le = (gd.nz > 1) ? launch_diag3(gd, gs, &nl) : launch_diag(gd, gs, &nl);
+    if (!le) le = cudaEventRecord(c->gevents[gi], gs);
+    if (!le) le = cudaStreamWaitEvent(c->cap, c->gevents[gi], 0);
+  }
+  cudaError_t ee = cudaStreamEndCapture(c->cap, &c->graph);
+  if (le) return fail_cuda(le, "launch during graph capture", __LINE__);
+  if (ee) return fail_cuda(ee, "cudaStreamEndCapture", __LINE__);
+  CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+  c->launches = nl;
+  return PTT_OK;
+}
+
 int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, void* stream,
                ptt_ctx** out) {
   if (!out) return PTT_EINVAL;
@@ -770,23 +798,10 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   c->gevents.assign(c->groups.size() + 1, nullptr);
   for (auto& s2 : c->gstreams) CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
   for (auto& e2 : c->gevents) CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
-  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-  int nl = 0;
-  cudaError_t le = cudaEventRecord(c->gevents.back(), c->cap);
-  for (size_t gi = 0; gi < c->groups.size() && !le; ++gi) {
-    cudaStream_t gs = c->gstreams[gi];
-    le = cudaStreamWaitEvent(gs, c->gevents.back(), 0);
-    const GroupDev& gd = c->groups[gi].d;
-    if (!le) le = (gd.nz > 1) ? launch_step3(gd, gs, &nl) : launch_step(gd, gs, &nl);
-    if (!le) le = (gd.nz > 1) ? launch_diag3(gd, gs, &nl) : launch_diag(gd, gs, &nl);
-    if (!le) le = cudaEventRecord(c->gevents[gi], gs);
-    if (!le) le = cudaStreamWaitEvent(c->cap, c->gevents[gi], 0);
+  {
+    const int s3 = capture_step_graph(c.get());
+    if (s3) return s3;
   }
-  cudaError_t ee = cudaStreamEndCapture(c->cap, &c->graph);
-  if (le) return fail_cuda(le, "launch during graph capture", __LINE__);
-  if (ee) return fail_cuda(ee, "cudaStreamEndCapture", __LINE__);
-  CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
-  c->launches = nl;
   *out = c.release();
   return PTT_OK;
 }
@@ -945,6 +960,92 @@ int ptt_resample(ptt_ctx* dst, int32_t dm, ptt_ctx* src, int32_t sm) {
   CK(cudaStreamSynchronize(dst->stream));
   dst->last_read[dm] = -1;
   return PTT_OK;
+}
+
+// Device milliseconds of `reps` launches of stages s0..s1 of one group.
+static int time_stages_of(ptt_ctx* c, const GroupDev& d, int s0, int s1, int reps, float* ms) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto run = [&]() -> cudaError_t {
+    for (int s = s0; s <= s1; ++s) {
+      cudaError_t e = (d.nz > 1) ? launch_stage3(d, s, c->stream, nullptr) : launch_stage(d, s, c->stream, nullptr);
+      if (e) return e;
+    }
+    return cudaSuccess;
+  };
+  cudaError_t e = run();                       // warm-up
+  if (!e) e = run();
+  if (!e) e = cudaEventRecord(e0, c->stream);
+  for (int r = 0; r < reps && !e; ++r) e = run();
+  if (!e) e = cudaEventRecord(e1, c->stream);
+  if (!e) e = cudaEventSynchronize(e1);
+  if (!e) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e) return fail_cuda(e, "autotune timing", __LINE__);
+  return PTT_OK;
+}
+
+int ptt_autotune(ptt_ctx* c, int32_t* choices, int32_t max_groups) {
+  if (!c) return PTT_EINVAL;
+  int optin = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  CK(cudaStreamSynchronize(c->stream));
+  const int reps = 4;
+  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+    GroupDev& d = c->groups[gi].d;
+    const bool d3 = d.nz > 1;
+    // threads per block of the fused x pass (stage 1)
+    {
+      int best = d.xthreads;
+      float bt = 1e30f;
+      for (int t = 128; t <= 512; t += 64) {
+        d.xthreads = t;
+        float ms = 0;
+        int s = time_stages_of(c, d, 1, 1, reps, &ms);
+        if (s) return s;
+        if (ms < bt) { bt = ms; best = t; }
+      }
+      d.xthreads = best;
+    }
+    // columns per block of the y passes, then (3D) lines per block of the
+    // z passes (stages 0 and 2)
+    {
+      const int cand[] = {1, 2, 4, 6, 8, 12, 16};
+      int best = d.Ccol;
+      float bt = 1e30f;
+      for (int C : cand) {
+        if (smem_ycols(C, d.M, d.f32) > (size_t)optin) continue;
+        d.Ccol = C;
+        float ms = 0;
+        int s = time_stages_of(c, d, 0, 2, reps, &ms);
+        if (s) return s;
+        if (ms < bt) { bt = ms; best = C; }
+      }
+      d.Ccol = best;
+    }
+    if (d3) {
+      const int cand[] = {1, 2, 4, 8, 16};
+      int best = d.zC;
+      float bt = 1e30f;
+      for (int C : cand) {
+        if (smem_zcols3(C, d.Mz, d.f32) > (size_t)optin) continue;
+        d.zC = C;
+        float ms = 0;
+        int s = time_stages_of(c, d, 0, 2, reps, &ms);
+        if (s) return s;
+        if (ms < bt) { bt = ms; best = C; }
+      }
+      d.zC = best;
+    }
+    if (choices && (int)gi < max_groups) {
+      choices[3 * gi] = d.Ccol;
+      choices[3 * gi + 1] = d3 ? d.zC : 0;
+      choices[3 * gi + 2] = d.xthreads;
+    }
+  }
+  return capture_step_graph(c);
 }
 
 int ptt_set_histograms(ptt_ctx* c, int32_t member, const double* lo, const double* hi) {

@@ -35,6 +35,8 @@ struct MemberPrm {
 struct GroupDev {
   int nb;            // members in the group
   int ntile;         // diagnostics tiles per member (diag_tiles)
+  int xthreads;      // threads per block of the fused x kernels (ptt_autotune)
+  int zC;            // 3D: x-mode lines per block of the z passes (ptt_autotune)
   int f32;           // 1: mixed precision (FP32 transforms and products)
   int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
   int nz, Mz, KZ;    // z modes (1 in 2D), padded z points, modes per Chebyshev index (K * nz)
@@ -121,6 +123,7 @@ cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_reset_member3(const GroupDev& g, int b, cudaStream_t st);
 size_t smem_xfused3(int Mx, int f32);
 size_t spec3_scratch_columns();
+size_t smem_zcols3(int C, int Mz, int f32);
 
 // Host helpers (ptt_capi.cu) used by the workspace-free entry point.
 void set_last_error(const char* msg);

@@ -760,8 +760,8 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       break;
     }
     case 1:
-      if (g.f32) k_xfused<float2><<<dim3(rows, g.nb), 512, smem_xfused(g.Mx, 1), st>>>(g);
-      else k_xfused<double2><<<dim3(rows, g.nb), 512, smem_xfused(g.Mx, 0), st>>>(g);
+      if (g.f32) k_xfused<float2><<<dim3(rows, g.nb), g.xthreads, smem_xfused(g.Mx, 1), st>>>(g);
+      else k_xfused<double2><<<dim3(rows, g.nb), g.xthreads, smem_xfused(g.Mx, 0), st>>>(g);
       n = 1;
       break;
     case 2: {  // forward y of the 5 explicit fields

@@ -771,6 +771,7 @@ cudaError_t optin3(F* fn, int optin_bytes) {
 
 size_t smem_xfused3(int Mx, int f32) { return (size_t)36 * Mx * (f32 ? sizeof(float2) : sizeof(double2)); }
 size_t spec3_scratch_columns() { return kScr3; }
+size_t smem_zcols3(int C, int Mz, int f32) { return smem_zcols(C, Mz, f32); }
 
 cudaError_t set_kernel_attributes3(int optin_bytes) {
   cudaError_t e;
@@ -816,6 +817,7 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
         ++n;
       }
       ZJob Z = zjob(g, true, Mz, M, g.plMz);
+      Z.C = g.zC;
       Z.src = J.dst; Z.src_f32 = f32;
       Z.dst = f32 ? (void*)g.Z3f : (void*)g.Z3; Z.dst_f32 = f32;
       Z.src_mstride = 17 * yplane; Z.dst_mstride = 26 * zplane;
@@ -832,12 +834,13 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       break;
     }
     case 1:
-      if (f32) k_xfused3<float2><<<dim3(M * Mz, g.nb), 512, smem_xfused3(g.Mx, 1), st>>>(g);
-      else k_xfused3<double2><<<dim3(M * Mz, g.nb), 512, smem_xfused3(g.Mx, 0), st>>>(g);
+      if (f32) k_xfused3<float2><<<dim3(M * Mz, g.nb), g.xthreads, smem_xfused3(g.Mx, 1), st>>>(g);
+      else k_xfused3<double2><<<dim3(M * Mz, g.nb), g.xthreads, smem_xfused3(g.Mx, 0), st>>>(g);
       n = 1;
       break;
     case 2: {  // forward z (9) then forward y (9)
       ZJob Z = zjob(g, false, Mz, M, g.plMz);
+      Z.C = g.zC;
       Z.src = f32 ? (const void*)g.W3f : (const void*)g.W3; Z.src_f32 = f32;
       Z.dst = f32 ? (void*)g.V3f : (void*)g.V3; Z.dst_f32 = f32;
       Z.src_mstride = 9 * zplane; Z.dst_mstride = 9 * yplane;
