@@ -359,6 +359,8 @@ void group_sizes(int nx, int ny, int nz, Group& g) {
   d.Ccol = cols(d.M);
   d.CcolE = cols(d.Me);
   d.CcolU = cols(d.Pu);
+  d.xthreads = 512;   // launch-shape defaults (ptt_autotune may change them)
+  d.zC = 8;
   g.hp[0] = make_plan(d.M);
   g.hp[1] = make_plan(d.Mx);
   g.hp[2] = make_plan(nx);
@@ -380,8 +382,6 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       const int want = (int)((long long)d.KZ * nfields * nb / 304);
       return std::max(1, std::min(c, want));
     };
-    d.xthreads = 512;
-    d.zC = 8;
     d.Ccol = cap(d.Ccol, 9);
     d.CcolE = cap(d.CcolE, 2);
     d.CcolU = cap(d.CcolU, 1);

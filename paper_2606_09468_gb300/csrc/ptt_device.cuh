@@ -560,7 +560,7 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
   const int f = blockIdx.y;
   if (J.inverse) {
     for (int i = tid; i < Mg * C; i += nt) {
-      const int c = i / Mg, n = i - c * Mg;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)Mg)), n = i - c * Mg;
       CT v = zero2<CT>();
       if (c < nc && n < N) {
         const long long o = (c0 + c) * J.cm + n * J.cn;
@@ -575,14 +575,14 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
       for (int c = tid >> 5; c < C; c += (nt >> 5)) warp_cheb_deriv(A + c * Mg, B + c * Mg, N);
       __syncthreads();
       for (int i = tid; i < N * C; i += nt) {
-        const int c = i / N, n = i - c * N;
+        const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - c * N;
         A[c * Mg + n] = B[c * Mg + n];
       }
       __syncthreads();
     }
     // V_0 = a_0, V_k = (1/2) exp(+i pi k/(2M)) (a_k - i a_{M-k})
     for (int i = tid; i < Mg * C; i += nt) {
-      const int c = i / Mg, k = i - c * Mg;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)Mg)), k = i - c * Mg;
       const CT ak = A[i];
       CT V;
       if (k == 0) {
@@ -597,7 +597,7 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
     __syncthreads();
     CT* res = fft_lines<+1>(B, A, C, Mg, J.pl);
     for (int i = tid; i < Mg * C; i += nt) {
-      const int j = i / C, c = i - j * C;
+      const int j = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - j * C;
       if (c < nc) {
         const int pos = (j & 1) ? (Mg - 1 - (j >> 1)) : (j >> 1);
         st2<CT>(dst, j * J.vj + (c0 + c) * J.vm, J.dst_f32, res[c * Mg + pos]);
@@ -605,7 +605,7 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
     }
   } else {
     for (int i = tid; i < Mg * C; i += nt) {
-      const int j = i / C, c = i - j * C;
+      const int j = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - j * C;
       const int pos = (j & 1) ? (Mg - 1 - (j >> 1)) : (j >> 1);
       A[c * Mg + pos] = (c < nc) ? ld2<CT>(src, j * J.vj + (c0 + c) * J.vm, J.src_f32) : zero2<CT>();
     }
@@ -613,7 +613,7 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
     CT* res = fft_lines<-1>(A, B, C, Mg, J.pl);
     const T s0 = (T)(1.0 / Mg), s1 = (T)(2.0 / Mg);
     for (int i = tid; i < N * C; i += nt) {
-      const int c = i / N, k = i - c * N;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), k = i - c * N;
       if (c < nc) {
         const CT Vk = res[c * Mg + k];
         const CT Vm = cconj(res[c * Mg + (k == 0 ? 0 : Mg - k)]);
@@ -647,7 +647,7 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
   const int f = blockIdx.y;
   if (J.inverse) {
     for (int i = tid; i < N * C; i += nt) {
-      const int c = i / N, n = i - c * N;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - c * N;
       double2 v = czero();
       if (c < nc) {
         const long long o = (c0 + c) * J.cm + n * J.cn;
@@ -662,7 +662,7 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
       for (int c = tid >> 5; c < C; c += (nt >> 5)) warp_cheb_deriv(A + c * P, B + c * P, N);
       __syncthreads();
       for (int i = tid; i < N * C; i += nt) {
-        const int c = i / N, n = i - c * N;
+        const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - c * N;
         A[c * P + n] = B[c * P + n];
       }
       __syncthreads();
@@ -673,7 +673,7 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
     }
     // even extension: A[n] = a_n (n <= M, zero for n >= N), A[P-n] = a_n
     for (int i = tid; i < C * P; i += nt) {
-      const int c = i / P, n = i - c * P;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)P)), n = i - c * P;
       if (n >= N && n <= M) A[i] = czero();
       else if (n > M) { const int r = P - n; A[i] = (r < N) ? A[c * P + r] : czero(); }
     }
@@ -681,7 +681,7 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
     double2* res = fft_lines<-1>(A, B, C, P, J.pl);
     // f_j = (F_j + a_0 + (-1)^j a_M) / 2
     for (int i = tid; i < (M + 1) * C; i += nt) {
-      const int j = i / C, c = i - j * C;
+      const int j = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - j * C;
       if (c < nc) {
         double2 v = cadd(res[c * P + j], a0s[c]);
         v = (j & 1) ? csub(v, a0s[C + c]) : cadd(v, a0s[C + c]);
@@ -690,19 +690,19 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
     }
   } else {
     for (int i = tid; i < (M + 1) * C; i += nt) {
-      const int j = i / C, c = i - j * C;
+      const int j = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - j * C;
       A[c * P + j] = (c < nc) ? src[j * J.vj + (c0 + c) * J.vm] : czero();
     }
     __syncthreads();
     for (int i = tid; i < C * P; i += nt) {
-      const int c = i / P, j = i - c * P;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)P)), j = i - c * P;
       if (j > M) A[i] = A[c * P + (P - j)];
     }
     __syncthreads();
     double2* res = fft_lines<-1>(A, B, C, P, J.pl);
     const double inv = 1.0 / M;
     for (int i = tid; i < N * C; i += nt) {
-      const int c = i / N, n = i - c * N;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - c * N;
       if (c < nc) {
         const double s = (n == 0 || n == M) ? 0.5 * inv : inv;
         dst[(c0 + c) * J.cm + n * J.cn] = cscl(res[c * P + n], s);
@@ -771,7 +771,7 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
   if (J.c2r) {
     const double2* src = J.srcC + b * J.src_mstride + (long long)row * J.src_rstep * K;
     for (int i = tid; i < nl * n; i += nt) {
-      const int l = i / n, k = i - l * n;
+      const int l = (int)fdiv((unsigned)i, fast_div((unsigned)n)), k = i - l * n;
       const int fa = 2 * l, fb = 2 * l + 1;
       int kk = -1;
       bool cj = false;
@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
     double2* res = fft_lines<+1>(A, Bb, nl, n, J.pl);
     double* dst = J.dstR + b * J.dst_mstride + (long long)row * J.dst_rstep * n;
     for (int i = tid; i < nl * n; i += nt) {
-      const int l = i / n, x = i - l * n;
+      const int l = (int)fdiv((unsigned)i, fast_div((unsigned)n)), x = i - l * n;
       const double2 h = res[i];
       dst[(2 * l) * J.dst_fstride + x] = h.x;
       if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + x] = h.y;
@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
   } else {
     const double* src = J.srcR + b * J.src_mstride + (long long)row * J.src_rstep * n;
     for (int i = tid; i < nl * n; i += nt) {
-      const int l = i / n, x = i - l * n;
+      const int l = (int)fdiv((unsigned)i, fast_div((unsigned)n)), x = i - l * n;
       const double fa = src[(2 * l) * J.src_fstride + x];
       const double fb = (2 * l + 1 < nf) ? src[(2 * l + 1) * J.src_fstride + x] : 0.0;
       A[i] = make_double2(fa, fb);
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
     double2* dst = J.dstC + b * J.dst_mstride + (long long)row * J.dst_rstep * K;
     const double inv = 1.0 / n;
     for (int i = tid; i < nl * K; i += nt) {
-      const int l = i / K, k = i - l * K;
+      const int l = (int)fdiv((unsigned)i, fast_div((unsigned)K)), k = i - l * K;
       const double2 hk = res[l * n + k];
       const double2 hm = cconj(res[l * n + (k == 0 ? 0 : n - k)]);
       // F = (hk + conj(h_{-k}))/2, G = (hk - conj(h_{-k}))/(2i)

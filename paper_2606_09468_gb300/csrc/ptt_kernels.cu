@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
   const T kfac = (T)(2.0 * 3.14159265358979323846 / pr.lx);
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < 7 * Mx; i += nt) {
-    const int l = i / Mx, k = i - l * Mx;
+    const int l = (int)fdiv((unsigned)i, fast_div((unsigned)Mx)), k = i - l * Mx;
     int kk = -1;
     bool cj = false;
     if (k < K) kk = k;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
   C2* Z = zp_ptr<C2>(g) + (size_t)b * 5 * rows * K + (size_t)j * K;
   const T inv = (T)(1.0 / Mx);
   for (int i = tid; i < 3 * K; i += nt) {
-    const int l = i / K, k = i - l * K;
+    const int l = (int)fdiv((unsigned)i, fast_div((unsigned)K)), k = i - l * K;
     const C2 hk = r2[l * Mx + k];
     const C2 hm = cconj(r2[l * Mx + (k == 0 ? 0 : Mx - k)]);
     const C2 F = cscl(cadd(hk, hm), (T)0.5 * inv);
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_spec(GroupDev g, int mode) {
   if (mode == 0) {
     const double* qt = g.qt + ((size_t)b * 4 + o) * 3 * 3 * NK + (size_t)m * N;
     for (int i = tid; i < 9 * N; i += nt) {
-      const int w = i / N, n = i - w * N;
+      const int w = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - w * N;
       tb[i] = qt[(size_t)w * NK + n];
     }
     const double* vh = g.vh + ((size_t)b * 4 + o) * NK + (size_t)m * N;

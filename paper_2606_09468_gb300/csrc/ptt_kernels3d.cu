@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
     for (int i = tid; i < C * Mz; i += nt) A[i] = zero2<CT>();
     __syncthreads();
     for (int i = tid; i < C * nz; i += nt) {
-      const int c = i / nz, mz = i - c * nz;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)nz)), mz = i - c * nz;
       if (c < nc && mz != hz) {
         const int s = (mz < hz) ? mz : mz - nz;
         CT v = ld2<CT>(src, (long long)(m0 + c) * nz + mz, J.src_f32);
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
     __syncthreads();
     CT* res = fft_lines<+1>(A, B, C, Mz, J.pl);
     for (int i = tid; i < Mz * C; i += nt) {
-      const int z = i / C, c = i - z * C;
+      const int z = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - z * C;
       if (c < nc) st2<CT>(dst, (long long)z * K + m0 + c, J.dst_f32, res[c * Mz + z]);
     }
   } else {
@@ -94,14 +94,14 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
     void* dst = static_cast<char*>(J.dst) +
         (b * J.dst_mstride + J.dst_field[f] * J.dst_fstride + (long long)j * K * nz) * ed;
     for (int i = tid; i < Mz * C; i += nt) {
-      const int z = i / C, c = i - z * C;
+      const int z = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - z * C;
       A[c * Mz + z] = (c < nc) ? ld2<CT>(src, (long long)z * K + m0 + c, J.src_f32) : zero2<CT>();
     }
     __syncthreads();
     CT* res = fft_lines<-1>(A, B, C, Mz, J.pl);
     const T inv = (T)(1.0 / Mz);
     for (int i = tid; i < C * nz; i += nt) {
-      const int c = i / nz, mz = i - c * nz;
+      const int c = (int)fdiv((unsigned)i, fast_div((unsigned)nz)), mz = i - c * nz;
       if (c < nc) {
         CT v = zero2<CT>();
         if (mz != hz) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
   const T kfac = (T)(2.0 * 3.14159265358979323846 / pr.lx);
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < 18 * Mx; i += nt) {
-    const int l = i / Mx, k = i - l * Mx;
+    const int l = (int)fdiv((unsigned)i, fast_div((unsigned)Mx)), k = i - l * Mx;
     int kk = -1;
     bool cj = false;
     if (k < K) kk = k;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
   C2* W = w3_ptr<C2>(g) + (size_t)b * 9 * plane + (size_t)row * K;
   const T inv = (T)(1.0 / Mx);
   for (int i = tid; i < 5 * K; i += nt) {
-    const int l = i / K, k = i - l * K;
+    const int l = (int)fdiv((unsigned)i, fast_div((unsigned)K)), k = i - l * K;
     const C2 hk = r2[l * Mx + k];
     const C2 hm = cconj(r2[l * Mx + (k == 0 ? 0 : Mx - k)]);
     const C2 F = cscl(cadd(hk, hm), (T)0.5 * inv);
