@@ -1181,7 +1181,7 @@ int ptt_time_stages(ptt_ctx* c, int32_t nsteps, double* ms) {
 int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) {
   if (!c || !flops || !bytes || !launches) return PTT_EINVAL;
   auto fft = [](double n) { return 5.0 * n * std::log2(n); };
-  const int nlaunch[PTT_NSTAGES] = {2, 1, 1, 2, 7};
+  const int nlaunch[PTT_NSTAGES] = {1, 1, 1, 2, 7};
   for (int s = 0; s < PTT_NSTAGES; ++s) { flops[s] = 0.0; bytes[s] = 0.0; launches[s] = 0; }
   for (Group& g : c->groups) {
     const GroupDev& d = g.d;
@@ -1199,7 +1199,7 @@ int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) 
       flops[4] += nb * (KZ * fft(d.Pu) + N * K * fft(d.nz) + N * d.nz * fft(d.nx) +
                         3.0 * KZ * (fft(Je) + 8.0 * Je) + 8.0 * Je * KZ * 3.0);
       bytes[4] += nb * (z * (9.0 * NK + 3.0 * 2.0 * Je * KZ) + 8.0 * 2.0 * N * d.nz * d.nx);
-      const int nl3[PTT_NSTAGES] = {4, 1, 3, 2, 10};
+      const int nl3[PTT_NSTAGES] = {2, 1, 2, 2, 10};
       for (int s = 0; s < PTT_NSTAGES; ++s) launches[s] += nl3[s];
       continue;
     }

@@ -508,16 +508,17 @@ __device__ __forceinline__ void lane_sbdf_any(int o, int N, int p, double idt, c
 // side: column m, row n at m*cm + n*cn; value side: column m, row j at
 // m*vm + j*vj (within one field of one member).  Input and output may be in
 // double or single precision independently of the compute type.
+constexpr int kYFields = 17;   // columns per launch (blockIdx.y): the 3D inverse pass
 struct YJob {
   const void* src;
   void* dst;
   long long src_mstride, dst_mstride;  // per member (elements)
   long long src_fstride, dst_fstride;  // per field (elements)
-  int src_field[8];
-  int src_field2[8];  // inverse only: >= 0 adds this field to src_field
-  int src_field3[8];  // inverse only: >= 0 adds a third field
-  int dst_field[8];
-  int deriv[8];       // inverse only: transform d/dy of the field
+  int src_field[kYFields];
+  int src_field2[kYFields];  // inverse only: >= 0 adds this field to src_field
+  int src_field3[kYFields];  // inverse only: >= 0 adds a third field
+  int dst_field[kYFields];
+  int deriv[kYFields];       // inverse only: transform d/dy of the field
   long long cm, cn;   // coefficient-side strides
   long long vm, vj;   // value-side strides
   int K;              // columns

@@ -683,7 +683,7 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl,
   J.cn = 1;
   J.vm = 1;
   J.vj = g.K;
-  for (int i = 0; i < 8; ++i) J.src_field2[i] = J.src_field3[i] = -1;
+  for (int i = 0; i < kYFields; ++i) J.src_field2[i] = J.src_field3[i] = -1;
   return J;
 }
 
@@ -737,7 +737,7 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
   const size_t NK = (size_t)g.N * g.K;
   int n = 0;
   switch (stage) {
-    case 0: {  // inverse y: 9 fields on the padded Gauss grid (two launches: 8 + 1)
+    case 0: {  // inverse y: 9 fields on the padded Gauss grid, one launch
       YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4P);
       J.src = g.X; J.dst = g.f32 ? (void*)g.Ypf : (void*)g.Yp;
       J.dst_f32 = g.f32;
@@ -745,18 +745,11 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       J.src_fstride = NK; J.dst_fstride = (long long)rows * g.K;
       const int sf[9] = {0, 1, 0, 2, 3, 4, 2, 3, 4};
       const int dv[9] = {0, 0, 1, 0, 0, 0, 1, 1, 1};
-      for (int i = 0; i < 8; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = dv[i]; }
-      YJob J2 = J;
-      J2.src_field[0] = sf[8]; J2.dst_field[0] = 8; J2.deriv[0] = dv[8];
+      for (int i = 0; i < 9; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = dv[i]; }
       const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
-      if (g.f32) {
-        k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 8, g.nb), 256, sm, st>>>(J);
-        k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 1, g.nb), 256, sm, st>>>(J2);
-      } else {
-        k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 8, g.nb), 256, sm, st>>>(J);
-        k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 1, g.nb), 256, sm, st>>>(J2);
-      }
-      n = 2;
+      if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
+      else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
+      n = 1;
       break;
     }
     case 1:

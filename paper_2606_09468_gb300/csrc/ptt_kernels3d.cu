@@ -738,7 +738,7 @@ YJob yjob3(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl, con
   J.cn = 1;
   J.vm = 1;
   J.vj = g.KZ;
-  for (int i = 0; i < 8; ++i) J.src_field2[i] = J.src_field3[i] = -1;
+  for (int i = 0; i < kYFields; ++i) J.src_field2[i] = J.src_field3[i] = -1;
   return J;
 }
 
@@ -804,18 +804,10 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       const int sf[17] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 0, 2, 3, 4, 5, 6, 7, 8};
       const int dv[17] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1};
       const size_t sm = smem_ycols(g.Ccol, M, f32);
-      for (int base = 0; base < 17; base += 8) {
-        YJob Jb = J;
-        const int cntf = (17 - base < 8) ? 17 - base : 8;
-        for (int i = 0; i < cntf; ++i) {
-          Jb.src_field[i] = sf[base + i];
-          Jb.dst_field[i] = base + i;
-          Jb.deriv[i] = dv[base + i];
-        }
-        if (f32) k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), cntf, g.nb), 256, sm, st>>>(Jb);
-        else k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), cntf, g.nb), 256, sm, st>>>(Jb);
-        ++n;
-      }
+      for (int i = 0; i < 17; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = dv[i]; }
+      if (f32) k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
+      else k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
+      ++n;
       ZJob Z = zjob(g, true, Mz, M, g.plMz);
       Z.C = g.zC;
       Z.src = J.dst; Z.src_f32 = f32;
@@ -855,14 +847,10 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       F.src_mstride = 9 * yplane; F.dst_mstride = 9 * NK;
       F.src_fstride = yplane; F.dst_fstride = NK;
       const size_t sm = smem_ycols(g.Ccol, M, f32);
-      for (int base = 0; base < 9; base += 8) {
-        YJob Fb = F;
-        const int cntf = (9 - base < 8) ? 9 - base : 8;
-        for (int i = 0; i < cntf; ++i) { Fb.src_field[i] = base + i; Fb.dst_field[i] = base + i; Fb.deriv[i] = 0; }
-        if (f32) k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), cntf, g.nb), 256, sm, st>>>(Fb);
-        else k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), cntf, g.nb), 256, sm, st>>>(Fb);
-      }
-      n = 3;
+      for (int i = 0; i < 9; ++i) { F.src_field[i] = i; F.dst_field[i] = i; F.deriv[i] = 0; }
+      if (f32) k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
+      else k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
+      n = 2;
       break;
     }
     case 3:
@@ -972,12 +960,8 @@ cudaError_t launch_phys_to_state3(const GroupDev& g, int b, cudaStream_t st) {
   J.status = nullptr;
   J.src = g.stageS; J.dst = g.X + (size_t)b * 9 * NK;
   J.src_fstride = (long long)N * KZ; J.dst_fstride = NK;
-  for (int base = 0; base < 9; base += 8) {
-    YJob Jb = J;
-    const int cntf = (9 - base < 8) ? 9 - base : 8;
-    for (int i = 0; i < cntf; ++i) { Jb.src_field[i] = base + i; Jb.dst_field[i] = base + i; Jb.deriv[i] = 0; }
-    k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), cntf, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(Jb);
-  }
+  for (int i = 0; i < 9; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
+  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 9, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
   k_reset3<<<1, 32, 0, st>>>(g, b);
   return cudaGetLastError();
 }
@@ -990,12 +974,8 @@ cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st) {
   J.status = nullptr;
   J.src = g.X + (size_t)b * 9 * NK; J.dst = g.stageS;
   J.src_fstride = NK; J.dst_fstride = (long long)N * KZ;
-  for (int base = 0; base < 9; base += 8) {
-    YJob Jb = J;
-    const int cntf = (9 - base < 8) ? 9 - base : 8;
-    for (int i = 0; i < cntf; ++i) { Jb.src_field[i] = base + i; Jb.dst_field[i] = base + i; Jb.deriv[i] = 0; }
-    k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), cntf, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(Jb);
-  }
+  for (int i = 0; i < 9; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
+  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 9, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
   ZJob Z = zjob(g, true, nz, N, g.plNz);
   Z.status = nullptr;
   Z.src = g.stageS; Z.dst = g.DZ;
