@@ -26,9 +26,10 @@
  *    modes): 9 <= ny <= 513 with ny - 1 of the form 2^a 3^b 5^c.  nz: 1, or
  *    even with 4 <= nz <= 512 and of the form 2^a 3^b 5^c (then lz > 0).
  *  - Physical layout (host arrays of ptt_set_state / ptt_get_state):
- *    2D double[5][ny][nx]; 3D double[9][ny][nz][nx]: field-major, then y
- *    (Gauss-Lobatto point y_l = cos(pi l/(ny-1)), l = 0 is the wall y = +1),
- *    then z (z_k = k lz/nz), then x (x_j = j lx/nx) fastest.
+ *    double[nf][nz][ny][nx] (2D: nf = 5, nz = 1; 3D: nf = 9): field-major,
+ *    then z (z_k = k lz/nz), then y (Gauss-Lobatto point
+ *    y_l = cos(pi l/(ny-1)), l = 0 is the wall y = +1), then x
+ *    (x_j = j lx/nx) fastest.
  *  - Spectral layout (ptt_get_spectral / ptt_set_spectral): 2D
  *    double[5][ny][nx/2][2]; 3D double[9][ny][nx/2][nz][2]: field, Chebyshev
  *    index n, Fourier index m = 0..nx/2-1 (k_m = 2 pi m / lx; the x Nyquist
@@ -119,6 +120,11 @@ int ptt_workspace_size(const ptt_params* per_member, int32_t nmembers, size_t* b
  * ptt_set_state.  Synchronous. */
 int ptt_create(const ptt_params* per_member, int32_t nmembers, void* d_workspace,
                size_t bytes, void* cuda_stream, ptt_ctx** out);
+
+/* The same as ptt_create, under the name for a batched ensemble of runs of
+ * uneven shapes and parameters (one params struct per member). */
+int ptt_create_ensemble(const ptt_params* per_member, int32_t nmembers, void* d_workspace,
+                        size_t bytes, void* cuda_stream, ptt_ctx** out);
 
 /* Laminar sPTT state (the kappa = 0 closed form of Eqs. 1-2 for channel flow)
  * plus a seeded divergence-free, no-slip perturbation of maximum grid

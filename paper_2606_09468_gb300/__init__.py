@@ -46,6 +46,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "ptt_workspace_size": [ctypes.POINTER(ptt_params), _I32, ctypes.POINTER(_SZ)],
     "ptt_create": [ctypes.POINTER(ptt_params), _I32, _VP, _SZ, _VP, ctypes.POINTER(_VP)],
+    "ptt_create_ensemble": [ctypes.POINTER(ptt_params), _I32, _VP, _SZ, _VP, ctypes.POINTER(_VP)],
     "ptt_init_state": [_VP, _I32, _U64, ctypes.c_double],
     "ptt_set_state": [_VP, _I32, _DP],
     "ptt_get_state": [_VP, _I32, _DP],
@@ -134,6 +135,14 @@ def ptt_create(per_member, d_workspace_ptr, nbytes, stream_ptr=0):
 def _dptr(a):
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(_DP)
+
+
+def ptt_create_ensemble(per_member, d_workspace_ptr, nbytes, stream_ptr=0):
+    arr = (ptt_params * len(per_member))(*per_member)
+    h = _VP()
+    _check("ptt_create_ensemble", load_library().ptt_create_ensemble(
+        arr, len(per_member), _VP(d_workspace_ptr), nbytes, _VP(stream_ptr), ctypes.byref(h)))
+    return h
 
 
 def ptt_init_state(ctx, member, seed, amplitude):
@@ -295,7 +304,7 @@ class Context:
     def phys_buffer(self, member):
         p = self.params[member]
         if p.nz > 1:
-            return np.empty((9, p.ny, p.nz, p.nx))
+            return np.empty((9, p.nz, p.ny, p.nx))
         return np.empty((5, p.ny, p.nx))
 
     def spec_buffer(self, member):

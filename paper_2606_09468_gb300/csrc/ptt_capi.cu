@@ -806,6 +806,11 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   return PTT_OK;
 }
 
+int ptt_create_ensemble(const ptt_params* per_member, int32_t nmembers, void* d_workspace,
+                        size_t bytes, void* cuda_stream, ptt_ctx** out) {
+  return ptt_create(per_member, nmembers, d_workspace, bytes, cuda_stream, out);
+}
+
 static int member_ok(ptt_ctx* c, int member) {
   return c && member >= 0 && member < (int)c->prm.size();
 }
@@ -843,8 +848,29 @@ int ptt_init_state(ptt_ctx* c, int32_t member, uint64_t seed, double amplitude) 
   return upload_phys(c, member, f.data(), true);
 }
 
+// 3D physical values: the ABI orders them [field][z][y][x], the staging
+// buffer of the transforms [field][y][z][x]; the host reorders at the
+// boundary (to_staging: ABI -> staging).
+static void reorder_zy(const double* src, double* dst, int nf, int ny, int nz, int nx,
+                       bool to_staging) {
+  for (int f = 0; f < nf; ++f)
+    for (int l = 0; l < ny; ++l)
+      for (int k = 0; k < nz; ++k) {
+        const size_t st = (((size_t)f * ny + l) * nz + k) * nx;   // staging row (y, z)
+        const size_t ab = (((size_t)f * nz + k) * ny + l) * nx;   // ABI row (z, y)
+        if (to_staging) std::memcpy(dst + st, src + ab, nx * sizeof(double));
+        else std::memcpy(dst + ab, src + st, nx * sizeof(double));
+      }
+}
+
 int ptt_set_state(ptt_ctx* c, int32_t member, const double* h) {
   if (!member_ok(c, member) || !h) return PTT_EINVAL;
+  const ptt_params& p = c->prm[member];
+  if (p.nz > 1) {
+    std::vector<double> t((size_t)9 * p.ny * p.nz * p.nx);
+    reorder_zy(h, t.data(), 9, p.ny, p.nz, p.nx, true);
+    return upload_phys(c, member, t.data());
+  }
   return upload_phys(c, member, h);
 }
 
@@ -853,9 +879,16 @@ int ptt_get_state(ptt_ctx* c, int32_t member, double* h) {
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
   const bool d3 = g.d.nz > 1;
+  const size_t n = (size_t)(d3 ? 9 : 5) * g.d.N * g.d.nz * g.d.nx;
   CK(d3 ? launch_state_to_phys3(g.d, b, c->stream) : launch_state_to_phys(g.d, b, c->stream));
-  CK(cudaMemcpyAsync(h, g.d.stage, (size_t)(d3 ? 9 : 5) * g.d.N * g.d.nz * g.d.nx * 8,
-                     cudaMemcpyDeviceToHost, c->stream));
+  if (d3) {
+    std::vector<double> t(n);
+    CK(cudaMemcpyAsync(t.data(), g.d.stage, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    reorder_zy(t.data(), h, 9, g.d.N, g.d.nz, g.d.nx, false);
+    return PTT_OK;
+  }
+  CK(cudaMemcpyAsync(h, g.d.stage, n * 8, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return PTT_OK;
 }

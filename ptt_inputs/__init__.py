@@ -154,13 +154,14 @@ def abi_to_spectral3(arr):
 
 
 def phys3_to_abi(fields):
-    """List of nine f[x, y, z] arrays -> ABI double[9][ny][nz][nx]."""
-    return np.ascontiguousarray(np.stack([np.transpose(f, (1, 2, 0)) for f in fields]),
+    """List of nine f[x, y, z] arrays -> ABI double[9][nz][ny][nx]."""
+    return np.ascontiguousarray(np.stack([np.transpose(f, (2, 1, 0)) for f in fields]),
                                 dtype=np.float64)
 
 
 def abi_to_phys3(arr):
-    return [np.ascontiguousarray(np.transpose(arr[f], (2, 0, 1))) for f in range(arr.shape[0])]
+    """ABI double[9][nz][ny][nx] -> list of nine f[x, y, z] arrays."""
+    return [np.ascontiguousarray(np.transpose(arr[f], (2, 1, 0))) for f in range(arr.shape[0])]
 
 
 # The paper's production shapes (Table 1, (Nx, Ny, Nz)), with Ny + 1

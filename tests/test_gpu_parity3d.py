@@ -246,3 +246,23 @@ def test_mixed_3d_errors_vs_oracle(nx, ny, nz):
     # state: of the size of the 1e-3 perturbation) to 1e-4
     assert np.all(e100[[0, 3, 4, 6, 8]] <= 1e-7), e100
     assert np.all(e100[[1, 2, 5, 7]] <= 1e-4), e100
+
+
+def test_physical_layout_is_field_z_y_x():
+    # u = cos(2 pi z / Lz), constant in x and y, given as [field][z][y][x]:
+    # only the kz = +-1 modes of the mean x mode, n = 0, are nonzero (1/2 each)
+    import paper_2606_09468_gb300 as P
+    nx, ny, nz = 16, 17, 8
+    ctx = _ctx([(nx, ny, nz)])
+    phys = np.zeros((9, nz, ny, nx))
+    z = np.arange(nz) * 5.0 / nz
+    phys[0] = np.cos(2 * np.pi * z / 5.0)[:, None, None]
+    ctx.set_state(0, phys)
+    u = I.abi_to_spectral3(ctx.get_spectral(0))[0]     # a[mx, mz, n]
+    ref = np.zeros_like(u)
+    ref[0, 1, 0] = ref[0, nz - 1, 0] = 0.5
+    assert np.max(np.abs(u - ref)) <= 1e-14
+    assert np.array_equal(ctx.get_state(0).shape, (9, nz, ny, nx))
+    assert np.max(np.abs(ctx.get_state(0)[0] - phys[0])) <= 1e-14
+    with pytest.raises(ValueError):
+        ctx.set_state(0, np.zeros((9, ny, nz, nx)))
