@@ -296,6 +296,59 @@ void initial_fields3(const ptt_params& p, uint64_t seed, double amp, std::vector
       }
 }
 
+// Tangent-form twiddle records of an FFT plan (see FftPlan): for each pass
+// s >= 1 of radix 2, 3 or 4 and stride index jm < Ns, the forward twiddles
+// w_r = exp(-2 pi i m_r / n), m_r = jm r st, written as i^k_r c_r (1 + i t_r)
+// with k_r the nearest quarter turn, so that |angle of c_r + i c_r t_r| <=
+// pi/4 (c_r >= 1/sqrt 2, |t_r| <= 1).
+void tangent_tables(const HostPlan& hp, std::vector<double>& tt, std::vector<int>& tk) {
+  const int n = hp.n;
+  int off = 0, Ns = 1;
+  for (size_t st = 0; st < hp.radix.size(); ++st) {
+    if (st > 0) off += Ns;
+    Ns *= hp.radix[st];
+  }
+  tt.assign((size_t)6 * (off + 1), 0.0);
+  tk.assign((size_t)(off + 1), 0);
+  off = 0;
+  Ns = 1;
+  for (size_t st = 0; st < hp.radix.size(); ++st) {
+    const int R = hp.radix[st];
+    if (st > 0) {
+      const long long stride = n / ((long long)Ns * R);
+      for (int jm = 0; jm < Ns; ++jm) {
+        double c[5] = {1, 1, 1, 1, 1}, t[5] = {0, 0, 0, 0, 0};
+        int kp = 0;
+        for (int r = 1; r < R && R <= 4; ++r) {
+          const long long m = ((long long)jm * r * stride) % n;
+          // angle -2 pi m / n = 2 pi (-4 m) / (4 n); quarter turns k = round(-4 m / n)
+          long long k = -(4 * m + n / 2) / n;             // floor((-4 m + n/2) / n) for m >= 0
+          while (-4 * m - k * n > n / 2) ++k;
+          while (-4 * m - k * n < -(n / 2)) --k;
+          const long long e = -4 * m - k * n;             // reduced angle 2 pi e / (4 n)
+          double cc, ss;
+          cis(e, 4LL * n, &cc, &ss);
+          c[r] = cc;
+          t[r] = ss / cc;
+          kp |= (int)(((k % 4) + 4) % 4) << (2 * (r - 1));
+        }
+        double* rec = &tt[(size_t)6 * (off + jm)];
+        if (R == 4) {
+          rec[0] = t[1]; rec[1] = t[2]; rec[2] = t[3]; rec[3] = c[1]; rec[4] = c[2]; rec[5] = c[3] / c[1];
+        } else if (R == 3) {
+          rec[0] = t[1]; rec[1] = t[2]; rec[2] = c[1]; rec[3] = c[2] / c[1]; rec[4] = 0.5 * c[1];
+          rec[5] = 0.86602540378443864676 * c[1];
+        } else if (R == 2) {
+          rec[0] = t[1]; rec[1] = c[1];
+        }
+        tk[off + jm] = kp;
+      }
+      off += Ns;
+    }
+    Ns *= R;
+  }
+}
+
 // ------------------------------------------------------------- layout
 struct Carver {
   size_t off = 0;
@@ -451,6 +504,14 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       for (int s = 0; s < pls[i]->nst; ++s) pls[i]->radix[s] = g.hp[i].radix[s];
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
       pls[i]->twf = (d.f32 && (i < 2 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
+      int off = 0, Ns = 1;
+      for (int st = 0; st < pls[i]->nst; ++st) {
+        pls[i]->toff[st] = off;
+        if (st > 0) off += Ns;
+        Ns *= pls[i]->radix[st];
+      }
+      pls[i]->tt = cv.take<double>((size_t)6 * (off + 1));
+      pls[i]->tk = cv.take<int>((size_t)(off + 1));
     }
     d.tw4P = cv.take<double2>((size_t)d.M);
     d.tw4Pf = d.f32 ? cv.take<float2>((size_t)d.M) : nullptr;
@@ -781,6 +842,16 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
         tw[k] = make_double2(cc, -ss);
       }
       CK(cudaMemcpyAsync((void*)pls[t]->tw, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+      {
+        std::vector<double> tt;
+        std::vector<int> tk;
+        tangent_tables(g.hp[t], tt, tk);
+        CK(cudaMemcpyAsync((void*)pls[t]->tt, tt.data(), tt.size() * sizeof(double),
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync((void*)pls[t]->tk, tk.data(), tk.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+      }
       if (pls[t]->twf) {
         std::vector<float2> twf(n);
         for (int k = 0; k < n; ++k) twf[k] = make_float2((float)tw[k].x, (float)tw[k].y);

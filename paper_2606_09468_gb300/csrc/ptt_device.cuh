@@ -7,6 +7,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "ptt_internal.h"
 
 namespace ptt {
@@ -164,6 +166,83 @@ __device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restr
   }
 }
 
+// ---------------------------------------------- tangent-form FP64 passes
+// A twiddle i^k c (1 + i t) applied as u = v + i t v (two FMAs), the quarter
+// turn i^k by swaps and sign flips (integer operations), and c folded into
+// the butterfly's sums as FMA coefficients: 6, 16 and 22 FP64 operations for
+// a twiddled radix-2, 3 and 4 butterfly against 8, 20 and 28 with plain
+// complex products.  Tables: FftPlan::tt, tk.
+__device__ __forceinline__ double flip_sign(double v, bool c) {
+  return __hiloint2double(__double2hiint(v) ^ (c ? (int)0x80000000 : 0), __double2loint(v));
+}
+__device__ __forceinline__ double2 rot_quarter(double2 u, int k) {   // i^k u, k in 0..3
+  const bool sw = k & 1;
+  const double x = sw ? u.y : u.x, y = sw ? u.x : u.y;
+  return make_double2(flip_sign(x, k == 1 || k == 2), flip_sign(y, k >= 2));
+}
+// i^k (1 + i t) v for the forward twiddle; the inverse uses the conjugate,
+// i^-k (1 - i t) v.
+template <int DIR>
+__device__ __forceinline__ double2 tan_rotate(double2 v, double t, int k) {
+  if (DIR > 0) { t = -t; k = (4 - k) & 3; }
+  return rot_quarter(make_double2(fma(-t, v.y, v.x), fma(t, v.x, v.y)), k);
+}
+
+template <int DIR, int R>
+__device__ __forceinline__ void fft_pass_tan(const double2* __restrict__ src, double2* __restrict__ dst,
+                                             int nl, int ls, int n, int Ns,
+                                             const double* __restrict__ tt,
+                                             const int* __restrict__ tk) {
+  const int nb = n / R;
+  const int total = nl * nb;
+  const FastDiv dnb = fast_div((unsigned)nb), dns = fast_div((unsigned)Ns);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int l = (int)fdiv((unsigned)t, dnb);
+    const int j = t - l * nb;
+    const double2* s = src + l * ls;
+    double2* d = dst + l * ls;
+    const int jq = (int)fdiv((unsigned)j, dns);
+    const int jm = j - jq * Ns;
+    const double* rec = tt + (size_t)6 * jm;
+    const int kp = tk[jm];
+    const int o = jq * Ns * R + jm;
+    const double2 v0 = s[j];
+    if (R == 2) {
+      const double2 u1 = tan_rotate<DIR>(s[j + nb], rec[0], kp & 3);
+      const double c1 = rec[1];
+      d[o] = make_double2(fma(c1, u1.x, v0.x), fma(c1, u1.y, v0.y));
+      d[o + Ns] = make_double2(fma(-c1, u1.x, v0.x), fma(-c1, u1.y, v0.y));
+    } else if (R == 3) {
+      const double2 u1 = tan_rotate<DIR>(s[j + nb], rec[0], kp & 3);
+      const double2 u2 = tan_rotate<DIR>(s[j + 2 * nb], rec[1], (kp >> 2) & 3);
+      const double c1 = rec[2], rho = rec[3], h = rec[4], sc = (DIR > 0) ? rec[5] : -rec[5];
+      const double2 q = make_double2(fma(rho, u2.x, u1.x), fma(rho, u2.y, u1.y));     // (a1 + a2)/c1
+      const double2 qm = make_double2(fma(-rho, u2.x, u1.x), fma(-rho, u2.y, u1.y));  // (a1 - a2)/c1
+      const double2 m = make_double2(fma(-h, q.x, v0.x), fma(-h, q.y, v0.y));
+      d[o] = make_double2(fma(c1, q.x, v0.x), fma(c1, q.y, v0.y));
+      // y1 = m + i s (a1 - a2), y2 = m - i s (a1 - a2), s = DIR sin(2 pi/3)
+      d[o + Ns] = make_double2(fma(-sc, qm.y, m.x), fma(sc, qm.x, m.y));
+      d[o + 2 * Ns] = make_double2(fma(sc, qm.y, m.x), fma(-sc, qm.x, m.y));
+    } else {
+      const double2 u1 = tan_rotate<DIR>(s[j + nb], rec[0], kp & 3);
+      const double2 u2 = tan_rotate<DIR>(s[j + 2 * nb], rec[1], (kp >> 2) & 3);
+      const double2 u3 = tan_rotate<DIR>(s[j + 3 * nb], rec[2], (kp >> 4) & 3);
+      const double c1 = rec[3], c2 = rec[4], rho = rec[5];
+      const double2 s02 = make_double2(fma(c2, u2.x, v0.x), fma(c2, u2.y, v0.y));
+      const double2 d02 = make_double2(fma(-c2, u2.x, v0.x), fma(-c2, u2.y, v0.y));
+      const double2 q = make_double2(fma(rho, u3.x, u1.x), fma(rho, u3.y, u1.y));     // (a1 + a3)/c1
+      const double2 qm = make_double2(fma(-rho, u3.x, u1.x), fma(-rho, u3.y, u1.y));  // (a1 - a3)/c1
+      d[o] = make_double2(fma(c1, q.x, s02.x), fma(c1, q.y, s02.y));
+      d[o + 2 * Ns] = make_double2(fma(-c1, q.x, s02.x), fma(-c1, q.y, s02.y));
+      // d13 = i (a1 - a3) = c1 (-qm.y, qm.x); forward y1 = d02 - d13, y3 = d02 + d13
+      const double2 yA = make_double2(fma(c1, qm.y, d02.x), fma(-c1, qm.x, d02.y));   // d02 - d13
+      const double2 yB = make_double2(fma(-c1, qm.y, d02.x), fma(c1, qm.x, d02.y));   // d02 + d13
+      d[o + Ns] = (DIR < 0) ? yA : yB;
+      d[o + 3 * Ns] = (DIR < 0) ? yB : yA;
+    }
+  }
+}
+
 template <typename C2> __device__ __forceinline__ const C2* plan_tw(const FftPlan& pl);
 template <> __device__ __forceinline__ const double2* plan_tw<double2>(const FftPlan& pl) { return pl.tw; }
 template <> __device__ __forceinline__ const float2* plan_tw<float2>(const FftPlan& pl) { return pl.twf; }
@@ -179,6 +258,19 @@ __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl) {
   int Ns = 1;
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.radix[s];
+    if constexpr (std::is_same<C2, double2>::value) {
+      if (pl.tt && s > 0 && R <= 4) {
+        const double* tt = pl.tt + (size_t)6 * pl.toff[s];
+        const int* tk = pl.tk + pl.toff[s];
+        if (R == 4) fft_pass_tan<DIR, 4>(src, dst, nl, ls, pl.n, Ns, tt, tk);
+        else if (R == 3) fft_pass_tan<DIR, 3>(src, dst, nl, ls, pl.n, Ns, tt, tk);
+        else fft_pass_tan<DIR, 2>(src, dst, nl, ls, pl.n, Ns, tt, tk);
+        __syncthreads();
+        Ns *= R;
+        C2* t = src; src = dst; dst = t;
+        continue;
+      }
+    }
     switch (R) {
       case 2: fft_pass<DIR, 2>(src, dst, nl, ls, pl.n, Ns, tw); break;
       case 3: fft_pass<DIR, 3>(src, dst, nl, ls, pl.n, Ns, tw); break;

@@ -20,6 +20,16 @@ struct FftPlan {
   int radix[kMaxStages];
   const double2* tw;  // tw[k] = exp(-2 pi i k / n), k < n (device)
   const float2* twf;  // the same in single precision (mixed groups), or null
+  // Tangent-form twiddles of the FP64 passes s >= 1 of radix 2, 3, 4 (null:
+  // use tw).  Forward twiddle r of stride index jm:
+  //   exp(-2 pi i jm r st / n) = i^k_r cos(t'_r) (1 + i tan(t'_r)), |t'_r| <= pi/4,
+  // record jm of pass s at tt[6 (toff[s] + jm)], quadrants k_r packed in
+  // tk[toff[s] + jm] (2 bits each).  Records: radix 4 (tan1, tan2, tan3,
+  // cos1, cos2, cos3/cos1); radix 3 (tan1, tan2, cos1, cos2/cos1, cos1/2,
+  // sin(2 pi/3) cos1); radix 2 (tan1, cos1).
+  const double* tt;
+  const int* tk;
+  int toff[kMaxStages];
 };
 
 // Per-member physics, resident on the device.
