@@ -45,9 +45,8 @@ WORKLOAD = ("2D sPTT channel sweep, FP64: Nx in {128,256,512} x Ny in {97,129,25
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); measured DFMA loop: 1.197
 # DRAM read + write bytes per launch, averaged over the 9 shape groups, from
 # ncu counters of the current kernel source (profiles/k_xfused_2d_sweep_fp64.md);
-# reported as roofline.traffic when that kernel dominates (none until counters
-# of the current source are taken).
-NCU_TRAFFIC_PER_LAUNCH = {}
+# reported as roofline.traffic when that kernel dominates.
+NCU_TRAFFIC_PER_LAUNCH = {"k_xfused": 16.23e6}
 
 
 def parse():
