@@ -302,6 +302,9 @@ __constant__ double c_sb[4][4] = {{1.0, 0.0, 0.0, 0.0},
 // warp scans: each lane takes a contiguous chunk, composes it sequentially,
 // and the chunks are combined with shuffles.
 constexpr unsigned kFull = 0xffffffffu;
+// tau solves: above this top elimination factor the top coefficient of a
+// parity is taken from its wall row (see warp_qt_solve)
+constexpr double kTopFromWall = 1e3;
 constexpr int kMaxChunk = 8;  // tau sweeps: up to 8 rows per lane (ny <= 513)
 
 __device__ __forceinline__ double2 shfl_down2(double2 v, int o) {
@@ -462,6 +465,7 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
   double ED = __shfl_up_sync(kFull, ID, 1);
   if (lane == 0) { EC = czero(); ED = 1.0; }
   double2 av = cfma(ED, a0, EC);
+  double2 part = (lane == 0) ? a0 : czero();  // sum of a_{p+2i}, i < L-1
   __syncwarp();
 #pragma unroll
   for (int t = 0; t < kMaxChunk; ++t) {
@@ -469,10 +473,22 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
     if (t < c && i < i1) {
       av = cfma(Qv[t], av, Pv[t]);
       out[p + 2 * i] = av;
+      if (i < L - 1) part = cadd(part, av);
     }
   }
   if (lane == 0) out[p] = a0;
   __syncwarp();
+  // Top coefficient from the wall row when the top elimination factor is
+  // large: with a small diagonal (diffusivity kappa) the forward
+  // substitution forms a_top = P + Q a_{top-2} with |Q| ~ alpha/(4 n^2 kappa)
+  // and amplifies the rounding of a_{top-2}; the wall row of the same system
+  // gives a_top = g - sum of the others with rounding of the sum only.
+  const int nl = p + 2 * (L - 1);
+  if (L > 1 && fabs(Q[nl]) > kTopFromWall) {
+    part = warp_allsum2(part);
+    if (lane == 0) out[nl] = csub(cscl(rs, bcfac), part);
+    __syncwarp();
+  }
 }
 
 // Lane-sequential forms for the per-mode spectral stage: one lane owns one
@@ -546,6 +562,11 @@ __device__ __forceinline__ void lane_qt_solve(int N, int p, double alpha,
   for (int n = p + 2; n <= nl; n += 2) {
     a = cfma(Q[n], a, out[n]);
     out[n] = a;
+  }
+  if (nl > p && fabs(Q[nl]) > kTopFromWall) {   // top coefficient from the wall row
+    double2 part = czero();
+    for (int n = p; n < nl; n += 2) part = cadd(part, out[n]);
+    out[nl] = csub(cscl(rs, bcfac), part);
   }
 }
 

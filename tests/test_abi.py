@@ -39,10 +39,17 @@ def test_status_strings_and_param_checks_without_gpu(lib):
     # host-side validation only (no device call)
     assert P.ptt_workspace_size([P.make_params(nx=64, ny=65)]) > 0
     assert P.ptt_workspace_size([P.make_params(nx=32, ny=33, nz=16, lz=5.0)]) > 0
+    # the largest admitted shapes
+    assert P.ptt_workspace_size([P.make_params(nx=512, ny=513)]) > 0
+    assert P.ptt_workspace_size([P.make_params(nx=8, ny=9, nz=512, lz=5.0)]) > 0
     for bad in (dict(nx=63), dict(ny=66), dict(nx=14), dict(beta=0.0), dict(nz=2), dict(nz=3),
-                dict(nz=14), dict(nz=1024), dict(nz=8, lz=0.0)):
+                dict(nz=14), dict(nz=1024), dict(nz=8, lz=0.0), dict(nx=6), dict(nx=1024),
+                dict(ny=7), dict(ny=1025), dict(dt=0.0), dict(precision=2)):
         with pytest.raises(P.PttError):
             P.ptt_workspace_size([P.make_params(**bad)])
+    # an empty ensemble
+    with pytest.raises(P.PttError):
+        P.ptt_workspace_size([])
 
 
 def test_workspace_grows_with_members(lib):
