@@ -68,7 +68,8 @@ def parse():
                     help="also time the paper's A1-A6 shapes (3D, mixed; FP64 where nx <= 256)")
     ap.add_argument("--only", default=None,
                     help="run one workload alone (3d_fp64, 3d_mixed, 3d_fp64_large, "
-                         "3d_mixed_large, ensemble_mixed, ensemble_fp64) and print its line, "
+                         "3d_mixed_large, ensemble_mixed, ensemble_fp64, 2d_NXxNY[_mixed]: one "
+                         "shape of the 2D sweep, three seeds) and print its line, "
                          "for profiling; or midplane_stats: mixed vs FP64 mid-plane statistics "
                          "of the 3D workload over --steps steps")
     return ap.parse_args()
@@ -319,6 +320,12 @@ def only_workload(args):
         params = [P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=prec, **I.PAPER)]
         seeds = [0]
         pts = nx * ny * nz
+    elif name.startswith("2d_"):
+        # one shape of the 2D sweep: its three seeds, as one shape group
+        nx, ny = (int(v) for v in name[3:].split("_")[0].split("x"))
+        params = [P.make_params(nx=nx, ny=ny, dt=I.DT, precision=prec, **I.PAPER) for _ in range(3)]
+        seeds = [0, 1, 2]
+        pts = 3 * nx * ny
     elif name.startswith("ensemble"):
         fluid = {k: v for k, v in I.PAPER.items() if k != "wi"}
         members = I.ensemble_members()

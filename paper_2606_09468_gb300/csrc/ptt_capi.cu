@@ -55,7 +55,9 @@ HostPlan make_plan(int n) {
   HostPlan p;
   p.n = n;
   int r = n;
-  for (int f : {4, 2, 3, 5})
+  // radix 5 first: the first pass takes no twiddles, and a twiddled radix-5
+  // butterfly costs the most (44 FP64 operations against 36 untwiddled)
+  for (int f : {5, 4, 2, 3})
     while (r % f == 0) { p.radix.push_back(f); r /= f; }
   return p;
 }
@@ -296,30 +298,64 @@ void initial_fields3(const ptt_params& p, uint64_t seed, double amp, std::vector
       }
 }
 
+// Quarter-period twiddles of the Gauss-grid (DCT-II/III) transforms on M
+// points with each direction's constants folded in: fwd[k] = (s_k/2)
+// exp(-i pi k/(2M)) with s_0 = 1/M, s_k = 2/M (the DCT-II normalisation of
+// the coefficients), inv[k] = (1/2) exp(+i pi k/(2M)).
+void quarter_tables(int M, std::vector<double2>& fwd, std::vector<double2>& inv) {
+  fwd.resize(M);
+  inv.resize(M);
+  for (int k = 0; k < M; ++k) {
+    double cc, ss;
+    cis(k, 4LL * M, &cc, &ss);
+    const double h = (k == 0 ? 0.5 : 1.0) / M;
+    fwd[k] = make_double2(h * cc, -h * ss);
+    inv[k] = make_double2(0.5 * cc, 0.5 * ss);
+  }
+}
+
+// Record offsets of the tangent tables: toff[s] in records (tk), tto[s] in
+// doubles (tt); *nrec and *ndbl receive the table sizes (one spare entry).
+void tangent_offsets(const HostPlan& hp, int* toff, int* tto, int* nrec, int* ndbl) {
+  int rec = 0, dbl = 0, Ns = 1;
+  for (size_t st = 0; st < hp.radix.size(); ++st) {
+    const int R = hp.radix[st];
+    toff[st] = rec;
+    tto[st] = dbl;
+    if (st > 0) {
+      rec += Ns;
+      dbl += (R == 5 ? 16 : 6) * Ns;
+    }
+    Ns *= R;
+  }
+  *nrec = rec + 1;
+  *ndbl = dbl + 16;
+}
+
 // Tangent-form twiddle records of an FFT plan (see FftPlan): for each pass
-// s >= 1 of radix 2, 3 or 4 and stride index jm < Ns, the forward twiddles
+// s >= 1 (radix 2 to 5) and stride index jm < Ns, the forward twiddles
 // w_r = exp(-2 pi i m_r / n), m_r = jm r st, written as i^k_r c_r (1 + i t_r)
 // with k_r the nearest quarter turn, so that |angle of c_r + i c_r t_r| <=
 // pi/4 (c_r >= 1/sqrt 2, |t_r| <= 1).
 void tangent_tables(const HostPlan& hp, std::vector<double>& tt, std::vector<int>& tk) {
   const int n = hp.n;
-  int off = 0, Ns = 1;
-  for (size_t st = 0; st < hp.radix.size(); ++st) {
-    if (st > 0) off += Ns;
-    Ns *= hp.radix[st];
-  }
-  tt.assign((size_t)6 * (off + 1), 0.0);
-  tk.assign((size_t)(off + 1), 0);
-  off = 0;
-  Ns = 1;
+  int toff[kMaxStages], tto[kMaxStages], nrec = 0, ndbl = 0;
+  tangent_offsets(hp, toff, tto, &nrec, &ndbl);
+  tt.assign((size_t)ndbl, 0.0);
+  tk.assign((size_t)nrec, 0);
+  double C1, S1, C2, S2;  // cos, sin of 2 pi/5 and 4 pi/5
+  cis(1, 5, &C1, &S1);
+  cis(2, 5, &C2, &S2);
+  int Ns = 1;
   for (size_t st = 0; st < hp.radix.size(); ++st) {
     const int R = hp.radix[st];
     if (st > 0) {
       const long long stride = n / ((long long)Ns * R);
+      const int RS = (R == 5) ? 16 : 6;
       for (int jm = 0; jm < Ns; ++jm) {
         double c[5] = {1, 1, 1, 1, 1}, t[5] = {0, 0, 0, 0, 0};
         int kp = 0;
-        for (int r = 1; r < R && R <= 4; ++r) {
+        for (int r = 1; r < R; ++r) {
           const long long m = ((long long)jm * r * stride) % n;
           // angle -2 pi m / n = 2 pi (-4 m) / (4 n); quarter turns k = round(-4 m / n)
           long long k = -(4 * m + n / 2) / n;             // floor((-4 m + n/2) / n) for m >= 0
@@ -332,8 +368,14 @@ void tangent_tables(const HostPlan& hp, std::vector<double>& tt, std::vector<int
           t[r] = ss / cc;
           kp |= (int)(((k % 4) + 4) % 4) << (2 * (r - 1));
         }
-        double* rec = &tt[(size_t)6 * (off + jm)];
-        if (R == 4) {
+        double* rec = &tt[(size_t)tto[st] + (size_t)RS * jm];
+        if (R == 5) {
+          rec[0] = t[1]; rec[1] = t[2]; rec[2] = t[3]; rec[3] = t[4];
+          rec[4] = c[4] / c[1]; rec[5] = c[3] / c[2];
+          rec[6] = c[1]; rec[7] = c[2];
+          rec[8] = C1 * c[1]; rec[9] = C2 * c[2]; rec[10] = C2 * c[1]; rec[11] = C1 * c[2];
+          rec[12] = S1 * c[1]; rec[13] = S2 * c[2]; rec[14] = S2 * c[1]; rec[15] = S1 * c[2];
+        } else if (R == 4) {
           rec[0] = t[1]; rec[1] = t[2]; rec[2] = t[3]; rec[3] = c[1]; rec[4] = c[2]; rec[5] = c[3] / c[1];
         } else if (R == 3) {
           rec[0] = t[1]; rec[1] = t[2]; rec[2] = c[1]; rec[3] = c[2] / c[1]; rec[4] = 0.5 * c[1];
@@ -341,9 +383,8 @@ void tangent_tables(const HostPlan& hp, std::vector<double>& tt, std::vector<int
         } else if (R == 2) {
           rec[0] = t[1]; rec[1] = c[1];
         }
-        tk[off + jm] = kp;
+        tk[toff[st] + jm] = kp;
       }
-      off += Ns;
     }
     Ns *= R;
   }
@@ -504,17 +545,15 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       for (int s = 0; s < pls[i]->nst; ++s) pls[i]->radix[s] = g.hp[i].radix[s];
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
       pls[i]->twf = (d.f32 && (i < 2 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
-      int off = 0, Ns = 1;
-      for (int st = 0; st < pls[i]->nst; ++st) {
-        pls[i]->toff[st] = off;
-        if (st > 0) off += Ns;
-        Ns *= pls[i]->radix[st];
-      }
-      pls[i]->tt = cv.take<double>((size_t)6 * (off + 1));
-      pls[i]->tk = cv.take<int>((size_t)(off + 1));
+      int nrec = 0, ndbl = 0;
+      tangent_offsets(g.hp[i], pls[i]->toff, pls[i]->tto, &nrec, &ndbl);
+      pls[i]->tt = cv.take<double>((size_t)ndbl);
+      pls[i]->tk = cv.take<int>((size_t)nrec);
     }
     d.tw4P = cv.take<double2>((size_t)d.M);
     d.tw4Pf = d.f32 ? cv.take<float2>((size_t)d.M) : nullptr;
+    d.tw4Pi = cv.take<double2>((size_t)d.M);
+    d.tw4Pif = d.f32 ? cv.take<float2>((size_t)d.M) : nullptr;
     d.tw4E = cv.take<double2>((size_t)d.Me);
   }
 }
@@ -607,12 +646,10 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
       (*tws[i])[k] = make_double2(cc, -ss);
     }
   }
-  tw4.resize(d.M);
-  for (int k = 0; k < d.M; ++k) {
-    double cc, ss;
-    cis(k, 4LL * d.M, &cc, &ss);
-    tw4[k] = make_double2(cc, -ss);
-  }
+  // tw4: the forward table of the Gauss-grid transforms, then the inverse one
+  std::vector<double2> inv;
+  quarter_tables(d.M, tw4, inv);
+  tw4.insert(tw4.end(), inv.begin(), inv.end());
   prm.lx = p.lx; prm.lz = 1.0; prm.re = p.re; prm.wi = p.wi; prm.beta = p.beta; prm.eps = p.eps;
   prm.kappa = p.kappa; prm.dt = p.dt;
   prm.inv_wi = 1.0 / p.wi;
@@ -809,27 +846,28 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
       }
       CK(cudaMemcpyAsync((void*)d.ccw, cw.data(), cw.size() * 8, cudaMemcpyHostToDevice, c->stream));
     }
-    // quarter-period twiddles of the Gauss-grid transforms: exp(-i pi k/(2M))
+    // quarter-period twiddles of the Gauss-grid transforms (forward and
+    // inverse on the padded grid, inverse on the diagnostic grid)
     {
-      const int Ms[2] = {d.M, d.Me};
-      const double2* dst[2] = {d.tw4P, d.tw4E};
-      for (int t = 0; t < 2; ++t) {
-        std::vector<double2> tw(Ms[t]);
-        for (int k = 0; k < Ms[t]; ++k) {
-          double cc, ss;
-          cis(k, 4LL * Ms[t], &cc, &ss);
-          tw[k] = make_double2(cc, -ss);
-        }
+      std::vector<double2> fwd, inv, fwdE, invE;
+      quarter_tables(d.M, fwd, inv);
+      quarter_tables(d.Me, fwdE, invE);
+      const std::vector<double2>* src[3] = {&fwd, &inv, &invE};
+      const double2* dst[3] = {d.tw4P, d.tw4Pi, d.tw4E};
+      const float2* dstf[3] = {d.tw4Pf, d.tw4Pif, nullptr};
+      std::vector<float2> twf[3];
+      for (int t = 0; t < 3; ++t) {
+        const std::vector<double2>& tw = *src[t];
         CK(cudaMemcpyAsync((void*)dst[t], tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice,
                            c->stream));
-        if (t == 0 && d.tw4Pf) {
-          std::vector<float2> twf(tw.size());
-          for (size_t k = 0; k < tw.size(); ++k) twf[k] = make_float2((float)tw[k].x, (float)tw[k].y);
-          CK(cudaMemcpyAsync((void*)d.tw4Pf, twf.data(), twf.size() * sizeof(float2),
+        if (dstf[t]) {
+          twf[t].resize(tw.size());
+          for (size_t k = 0; k < tw.size(); ++k) twf[t][k] = make_float2((float)tw[k].x, (float)tw[k].y);
+          CK(cudaMemcpyAsync((void*)dstf[t], twf[t].data(), twf[t].size() * sizeof(float2),
                              cudaMemcpyHostToDevice, c->stream));
         }
-        CK(cudaStreamSynchronize(c->stream));
       }
+      CK(cudaStreamSynchronize(c->stream));
     }
     // twiddle tables
     FftPlan* pls[7] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe, &d.plMz, &d.plNz};

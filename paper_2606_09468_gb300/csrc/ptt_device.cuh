@@ -169,9 +169,9 @@ __device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restr
 // ---------------------------------------------- tangent-form FP64 passes
 // A twiddle i^k c (1 + i t) applied as u = v + i t v (two FMAs), the quarter
 // turn i^k by swaps and sign flips (integer operations), and c folded into
-// the butterfly's sums as FMA coefficients: 6, 16 and 22 FP64 operations for
-// a twiddled radix-2, 3 and 4 butterfly against 8, 20 and 28 with plain
-// complex products.  Tables: FftPlan::tt, tk.
+// the butterfly's sums as FMA coefficients: 6, 16, 22 and 44 FP64 operations
+// for a twiddled radix-2, 3, 4 and 5 butterfly against 8, 20, 28 and 52 with
+// plain complex products.  Tables: FftPlan::tt, tk.
 __device__ __forceinline__ double flip_sign(double v, bool c) {
   return __hiloint2double(__double2hiint(v) ^ (c ? (int)0x80000000 : 0), __double2loint(v));
 }
@@ -203,7 +203,7 @@ __device__ __forceinline__ void fft_pass_tan(const double2* __restrict__ src, do
     double2* d = dst + l * ls;
     const int jq = (int)fdiv((unsigned)j, dns);
     const int jm = j - jq * Ns;
-    const double* rec = tt + (size_t)6 * jm;
+    const double* rec = tt + (size_t)(R == 5 ? 16 : 6) * jm;
     const int kp = tk[jm];
     const int o = jq * Ns * R + jm;
     const double2 v0 = s[j];
@@ -223,6 +223,35 @@ __device__ __forceinline__ void fft_pass_tan(const double2* __restrict__ src, do
       // y1 = m + i s (a1 - a2), y2 = m - i s (a1 - a2), s = DIR sin(2 pi/3)
       d[o + Ns] = make_double2(fma(-sc, qm.y, m.x), fma(sc, qm.x, m.y));
       d[o + 2 * Ns] = make_double2(fma(sc, qm.y, m.x), fma(-sc, qm.x, m.y));
+    } else if (R == 5) {
+      // a_r = c_r u_r; with t1 = a1 + a4 = c1 q1, d1 = a1 - a4 = c1 m1,
+      // t2 = a2 + a3 = c2 q2, d2 = a2 - a3 = c2 m2 the radix-5 DFT reads
+      // y0 = v0 + t1 + t2, b1 = v0 + C1 t1 + C2 t2, b2 = v0 + C2 t1 + C1 t2,
+      // y1,4 = b1 +- i DIR (S1 d1 + S2 d2), y2,3 = b2 +- i DIR (S2 d1 - S1 d2)
+      const double2 u1 = tan_rotate<DIR>(s[j + nb], rec[0], kp & 3);
+      const double2 u2 = tan_rotate<DIR>(s[j + 2 * nb], rec[1], (kp >> 2) & 3);
+      const double2 u3 = tan_rotate<DIR>(s[j + 3 * nb], rec[2], (kp >> 4) & 3);
+      const double2 u4 = tan_rotate<DIR>(s[j + 4 * nb], rec[3], (kp >> 6) & 3);
+      const double r14 = rec[4], r23 = rec[5];
+      const double2 q1 = make_double2(fma(r14, u4.x, u1.x), fma(r14, u4.y, u1.y));
+      const double2 m1 = make_double2(fma(-r14, u4.x, u1.x), fma(-r14, u4.y, u1.y));
+      const double2 q2 = make_double2(fma(r23, u3.x, u2.x), fma(r23, u3.y, u2.y));
+      const double2 m2 = make_double2(fma(-r23, u3.x, u2.x), fma(-r23, u3.y, u2.y));
+      const double c1 = rec[6], c2 = rec[7];
+      d[o] = make_double2(fma(c1, q1.x, fma(c2, q2.x, v0.x)), fma(c1, q1.y, fma(c2, q2.y, v0.y)));
+      const double2 b1 = make_double2(fma(rec[8], q1.x, fma(rec[9], q2.x, v0.x)),
+                                      fma(rec[8], q1.y, fma(rec[9], q2.y, v0.y)));
+      const double2 b2 = make_double2(fma(rec[10], q1.x, fma(rec[11], q2.x, v0.x)),
+                                      fma(rec[10], q1.y, fma(rec[11], q2.y, v0.y)));
+      const double2 e1 = make_double2(fma(rec[12], m1.x, rec[13] * m2.x), fma(rec[12], m1.y, rec[13] * m2.y));
+      const double2 e2 = make_double2(fma(rec[14], m1.x, -rec[15] * m2.x), fma(rec[14], m1.y, -rec[15] * m2.y));
+      // i e = (-e.y, e.x); DIR < 0: y1 = b1 - i e1, y4 = b1 + i e1 (likewise y2, y3)
+      const double2 p1 = make_double2(b1.x - e1.y, b1.y + e1.x), n1 = make_double2(b1.x + e1.y, b1.y - e1.x);
+      const double2 p2 = make_double2(b2.x - e2.y, b2.y + e2.x), n2 = make_double2(b2.x + e2.y, b2.y - e2.x);
+      d[o + Ns] = (DIR < 0) ? n1 : p1;
+      d[o + 4 * Ns] = (DIR < 0) ? p1 : n1;
+      d[o + 2 * Ns] = (DIR < 0) ? n2 : p2;
+      d[o + 3 * Ns] = (DIR < 0) ? p2 : n2;
     } else {
       const double2 u1 = tan_rotate<DIR>(s[j + nb], rec[0], kp & 3);
       const double2 u2 = tan_rotate<DIR>(s[j + 2 * nb], rec[1], (kp >> 2) & 3);
@@ -259,10 +288,11 @@ __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl) {
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.radix[s];
     if constexpr (std::is_same<C2, double2>::value) {
-      if (pl.tt && s > 0 && R <= 4) {
-        const double* tt = pl.tt + (size_t)6 * pl.toff[s];
+      if (pl.tt && s > 0) {
+        const double* tt = pl.tt + pl.tto[s];
         const int* tk = pl.tk + pl.toff[s];
-        if (R == 4) fft_pass_tan<DIR, 4>(src, dst, nl, ls, pl.n, Ns, tt, tk);
+        if (R == 5) fft_pass_tan<DIR, 5>(src, dst, nl, ls, pl.n, Ns, tt, tk);
+        else if (R == 4) fft_pass_tan<DIR, 4>(src, dst, nl, ls, pl.n, Ns, tt, tk);
         else if (R == 3) fft_pass_tan<DIR, 3>(src, dst, nl, ls, pl.n, Ns, tt, tk);
         else fft_pass_tan<DIR, 2>(src, dst, nl, ls, pl.n, Ns, tt, tk);
         __syncthreads();
@@ -335,11 +365,13 @@ __device__ void warp_cheb_deriv(const C2* a, C2* out, int N) {
     const int L = (N - par + 1) / 2;
     const int c = (L + 31) / 32;
     const int i0 = min(lane * c, L), i1 = min(i0 + c, L);
+    // partial sums carried doubled (2 k a_k): b_{k-1} = acc + ex for k >= 2
+    // and (acc + ex)/2 for k = 1, with no scaling in the sweeps
     C2 acc = zero2<C2>();
     for (int i = i1 - 1; i >= i0; --i) {
       const int k = par + 2 * i;
-      acc = cfma((T)k, a[k], acc);
-      if (k >= 1) out[k - 1] = cscl(acc, (T)(k == 1 ? 1 : 2));
+      acc = cfma((T)(2 * k), a[k], acc);
+      if (k >= 1) out[k - 1] = acc;
     }
     C2 inc = acc;
     for (int o = 1; o < 32; o <<= 1) {
@@ -350,7 +382,8 @@ __device__ void warp_cheb_deriv(const C2* a, C2* out, int N) {
     if (lane == 31) ex = zero2<C2>();
     for (int i = i0; i < i1; ++i) {
       const int k = par + 2 * i;
-      if (k >= 1) out[k - 1] = cfma((T)(k == 1 ? 1 : 2), ex, out[k - 1]);
+      if (k >= 2) out[k - 1] = cadd(ex, out[k - 1]);
+      else if (k == 1) out[0] = cscl(cadd(ex, out[0]), (T)0.5);
     }
   }
   if (lane == 0) out[N - 1] = zero2<C2>();
@@ -640,7 +673,9 @@ struct YJob {
   int gauss;          // 0: M+1 Gauss-Lobatto points (DCT-I, FFT length 2M);
                       // 1: M Gauss points (DCT-II/III, FFT length M, M even)
   int src_f32, dst_f32;  // element types of src / dst (0: complex double, 1: complex float)
-  const double2* tw4;    // gauss: tw4[k] = exp(-i pi k / (2M)), k < M
+  const double2* tw4;    // gauss: quarter-period table of this direction, k < M:
+                         // forward (s_k/2) exp(-i pi k/(2M)) (s_0 = 1/M, s_k = 2/M),
+                         // inverse (1/2) exp(+i pi k/(2M))
   const float2* tw4f;    // the same in single precision
   int C;              // columns per block
   const int* status;  // skip members with status != 0 (may be null)
@@ -694,7 +729,8 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
       }
       __syncthreads();
     }
-    // V_0 = a_0, V_k = (1/2) exp(+i pi k/(2M)) (a_k - i a_{M-k})
+    // V_0 = a_0, V_k = (1/2) exp(+i pi k/(2M)) (a_k - i a_{M-k}), the factor
+    // taken from the inverse table
     for (int i = tid; i < Mg * C; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)Mg)), k = i - c * Mg;
       const CT ak = A[i];
@@ -703,8 +739,10 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
         V = ak;
       } else {
         const CT amk = A[c * Mg + Mg - k];
-        const CT w = cconj(ld_tw4<CT>(J, k));
-        V = cscl(cmul(w, csub(ak, mul_i(amk))), (T)0.5);
+        CT z;
+        z.x = ak.x + amk.y;
+        z.y = ak.y - amk.x;
+        V = cmul(ld_tw4<CT>(J, k), z);
       }
       B[i] = V;
     }
@@ -725,24 +763,20 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
     }
     __syncthreads();
     CT* res = fft_lines<-1>(A, B, C, Mg, J.pl);
-    const T s0 = (T)(1.0 / Mg), s1 = (T)(2.0 / Mg);
+    // with s = V_k + conj V_{M-k}, d = V_k - conj V_{M-k} (the transforms of
+    // the real and imaginary parts, times 2 and 2i) and the forward table
+    // F_k = (s_k/2) exp(-i pi k/(2M)):  a_k = (Re(F_k s), Re(F_k (-i d)))
     for (int i = tid; i < N * C; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), k = i - c * N;
       if (c < nc) {
         const CT Vk = res[c * Mg + k];
-        const CT Vm = cconj(res[c * Mg + (k == 0 ? 0 : Mg - k)]);
-        const CT Vr = cscl(cadd(Vk, Vm), (T)0.5);
-        const CT d = csub(Vk, Vm);
-        CT Vi;
-        Vi.x = (T)0.5 * d.y;
-        Vi.y = (T)-0.5 * d.x;
+        const CT Rm = res[c * Mg + (k == 0 ? 0 : Mg - k)];
+        const T sx = Vk.x + Rm.x, sy = Vk.y - Rm.y;
+        const T dx = Vk.x - Rm.x, dy = Vk.y + Rm.y;
         const CT w = ld_tw4<CT>(J, k);
-        const T xr = w.x * Vr.x - w.y * Vr.y;
-        const T xi = w.x * Vi.x - w.y * Vi.y;
-        const T sc = (k == 0) ? s0 : s1;
         CT o;
-        o.x = sc * xr;
-        o.y = sc * xi;
+        o.x = w.x * sx - w.y * sy;
+        o.y = w.x * dy + w.y * dx;
         st2<CT>(dst, (c0 + c) * J.cm + k * J.cn, J.dst_f32, o);
       }
     }

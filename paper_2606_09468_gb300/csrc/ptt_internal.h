@@ -20,16 +20,20 @@ struct FftPlan {
   int radix[kMaxStages];
   const double2* tw;  // tw[k] = exp(-2 pi i k / n), k < n (device)
   const float2* twf;  // the same in single precision (mixed groups), or null
-  // Tangent-form twiddles of the FP64 passes s >= 1 of radix 2, 3, 4 (null:
-  // use tw).  Forward twiddle r of stride index jm:
+  // Tangent-form twiddles of the FP64 passes s >= 1 (null: use tw).  Forward
+  // twiddle r of stride index jm:
   //   exp(-2 pi i jm r st / n) = i^k_r cos(t'_r) (1 + i tan(t'_r)), |t'_r| <= pi/4,
-  // record jm of pass s at tt[6 (toff[s] + jm)], quadrants k_r packed in
-  // tk[toff[s] + jm] (2 bits each).  Records: radix 4 (tan1, tan2, tan3,
-  // cos1, cos2, cos3/cos1); radix 3 (tan1, tan2, cos1, cos2/cos1, cos1/2,
+  // record jm of pass s at tt[tto[s] + RS jm] (RS = 16 for radix 5, else 6),
+  // quadrants k_r packed in tk[toff[s] + jm] (2 bits each).  Records:
+  // radix 5 (tan1..tan4, cos4/cos1, cos3/cos2, cos1, cos2, C1 cos1, C2 cos2,
+  // C2 cos1, C1 cos2, S1 cos1, S2 cos2, S2 cos1, S1 cos2 with C_q, S_q the
+  // cosine and sine of 2 pi q/5); radix 4 (tan1, tan2, tan3, cos1, cos2,
+  // cos3/cos1); radix 3 (tan1, tan2, cos1, cos2/cos1, cos1/2,
   // sin(2 pi/3) cos1); radix 2 (tan1, cos1).
   const double* tt;
   const int* tk;
   int toff[kMaxStages];
+  int tto[kMaxStages];
 };
 
 // Per-member physics, resident on the device.
@@ -88,9 +92,13 @@ struct GroupDev {
   const double* hrange;      // [nb][8][2] (lo, hi); lo >= hi: quantity off
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
   double2* stageS;   // [5][N][K]  values on the unpadded y grid, x analysed
-  const double2* tw4P;  // [M]  exp(-i pi k/(2M)), padded Gauss grid
-  const float2* tw4Pf;  // the same in single precision (mixed groups)
-  const double2* tw4E;  // [Me] exp(-i pi k/(2Me)), diagnostic Gauss grid
+  // quarter-period twiddles of the Gauss-grid transforms, with the constant
+  // factors of each direction folded in:
+  const double2* tw4P;   // [M]  forward: (s_k/2) exp(-i pi k/(2M)), s_0 = 1/M, s_k = 2/M
+  const float2* tw4Pf;   // the same in single precision (mixed groups)
+  const double2* tw4Pi;  // [M]  inverse: (1/2) exp(+i pi k/(2M))
+  const float2* tw4Pif;  // the same in single precision (mixed groups)
+  const double2* tw4E;   // [Me] inverse on the diagnostic Gauss grid: (1/2) exp(+i pi k/(2Me))
   FftPlan plP, plMx, plNx, plPu, plPe;   // lengths M, Mx, nx, 2(N-1), Me
   FftPlan plMz, plNz;                    // 3D: lengths Mz, nz
 };

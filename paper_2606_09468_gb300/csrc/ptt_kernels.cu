@@ -673,8 +673,8 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl,
                const double2* tw4 = nullptr) {
   YJob J{};
   J.gauss = tw4 ? 1 : 0;
-  J.tw4 = tw4;
-  J.tw4f = g.tw4Pf;
+  J.tw4 = tw4;  // the quarter-period table of this direction
+  J.tw4f = inverse ? g.tw4Pif : g.tw4Pf;
   J.K = g.K;
   J.N = g.N;
   J.M = M;
@@ -741,7 +741,7 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
   int n = 0;
   switch (stage) {
     case 0: {  // inverse y: 9 fields on the padded Gauss grid, one launch
-      YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4P);
+      YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4Pi);
       J.src = g.X; J.dst = g.f32 ? (void*)g.Ypf : (void*)g.Yp;
       J.dst_f32 = g.f32;
       J.src_mstride = 5 * NK; J.dst_mstride = 9LL * rows * g.K;

@@ -725,8 +725,8 @@ __global__ void k_reset3(GroupDev g, int b) {
 YJob yjob3(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl, const double2* tw4) {
   YJob J{};
   J.gauss = tw4 ? 1 : 0;
-  J.tw4 = tw4;
-  J.tw4f = g.tw4Pf;
+  J.tw4 = tw4;  // the quarter-period table of this direction
+  J.tw4f = inverse ? g.tw4Pif : g.tw4Pf;
   J.K = g.KZ;
   J.N = g.N;
   J.M = M;
@@ -795,7 +795,7 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
   int n = 0;
   switch (stage) {
     case 0: {  // inverse y (17 fields) then inverse z (26 lines)
-      YJob J = yjob3(g, true, M, g.Ccol, g.plP, g.tw4P);
+      YJob J = yjob3(g, true, M, g.Ccol, g.plP, g.tw4Pi);
       J.src = g.X;
       J.dst = f32 ? (void*)g.Y3f : (void*)g.Y3;
       J.dst_f32 = f32;

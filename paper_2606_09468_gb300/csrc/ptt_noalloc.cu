@@ -110,7 +110,8 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   g.Zp = (double2*)(b + oZp);
   g.plP.tw = (const double2*)(b + oTP);
   g.plMx.tw = (const double2*)(b + oTM);
-  g.tw4P = (const double2*)(b + oT4);
+  g.tw4P = (const double2*)(b + oT4);                      // forward table, M entries
+  g.tw4Pi = (const double2*)(b + oT4) + tw4.size() / 2;    // inverse table, M entries
   g.prm = (ptt::MemberPrm*)(b + oPr);
   g.status = (int*)(b + oSt);
   g.count = (long long*)(b + oCn);
