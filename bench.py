@@ -417,7 +417,7 @@ def other_workloads(args):
         "stated_error_vs_fp64": "tests/test_gpu_ensemble.py: every member, every field, 1 step <= 1e-8",
         "workload": "64 independent 2D runs, seeds 0-63, Nx in the 5-smooth multiples of 32 in "
                     "[64, 512], Ny in {65,97,129,161,193,257}, Wi uniform in [50, 200] (splitmix64 "
-                    "draws of the run index), one context, one CUDA graph per step"}
+                    "draws of the run index), one context, one CUDA-graph launch per step"}
     return out
 
 
@@ -614,7 +614,7 @@ def run_ours(args):
                       "parallelism": f"ensemble of independent runs per GPU x {world} GPU",
                       "l2": f"inputs larger than L2: workspace {ws / 2**30:.2f} GiB per GPU, "
                             "state + SBDF history re-read every step",
-                      "graph": "one CUDA graph launch per step",
+                      "graph": "one CUDA-graph launch per step (each step's diagnostics beside the next step's transforms) plus one for the last step's diagnostics",
                       "launch_shapes": ("autotuned (columns, lines, threads) per shape group: %s" % tuned)
                       if tuned else "defaults"},
            "status": P.ptt_status_string(status),

@@ -166,9 +166,11 @@ int ptt_get_spectral(ptt_ctx* ctx, int32_t member, double* h_spec);
 int ptt_resample(ptt_ctx* dst, int32_t dst_member, ptt_ctx* src, int32_t src_member);
 
 /* Advance every member by nsteps steps (asynchronous on the context stream;
- * each step is one CUDA-graph launch).  A member that blows up stops and
- * keeps its last record's status; the others continue.  Returns PTT_OK or an
- * error; blow-up is reported by ptt_synchronize / ptt_diagnostics. */
+ * nsteps + 1 CUDA-graph launches: each step's diagnostics run beside the next
+ * step's transforms, and those of the last step in one more launch).  A
+ * member that blows up stops and keeps its last record's status; the others
+ * continue.  Returns PTT_OK or an error; blow-up is reported by
+ * ptt_synchronize / ptt_diagnostics. */
 int ptt_step(ptt_ctx* ctx, int32_t nsteps);
 
 /* Wait for the context stream.  Returns PTT_BLOWUP if any member has blown

@@ -589,10 +589,14 @@ struct ptt_ctx {
   std::vector<long long> last_read;        // last diagnostics step returned
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  // step graphs (see capture_step_graph): 0 first step of a ptt_step call,
+  // 1 later steps, 2 diagnostics of the last step
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaStream_t> gstreams;  // one capture branch per group
+  std::vector<cudaStream_t> dstreams;  // the group's diagnostics branch
   std::vector<cudaEvent_t> gevents;
+  std::vector<cudaEvent_t> devents;
   int launches = 0;
   int device = 0;
 };
@@ -687,26 +691,54 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
 // Capture one step of every group (step + diagnostics) as one CUDA graph:
 // a fork per group from the capture stream, a join back (replaces an
 // existing graph).
-static int capture_step_graph(ptt_ctx* c) {
-  if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
-  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
-  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-  int nl = 0;
+// The step as CUDA graphs, one branch per shape group.  The diagnostics of a
+// state only read it (and write their own buffers), and only the spectral
+// stage of the next step overwrites it, so they run beside the next step's
+// transforms (stages 0-2) on a second branch per group that the spectral
+// stage waits for.  Graph 0 is the first step of a ptt_step call (stages 0-3;
+// the state it starts from was diagnosed when it was made), graph 1 a later
+// step (the previous step's diagnostics beside stages 0-2, then stage 3), and
+// graph 2 the diagnostics of the last step's result (stage 4).
+static cudaError_t capture_kind(ptt_ctx* c, int kind, int* nl) {
   cudaError_t le = cudaEventRecord(c->gevents.back(), c->cap);
   for (size_t gi = 0; gi < c->groups.size() && !le; ++gi) {
-    cudaStream_t gs = c->gstreams[gi];
-    le = cudaStreamWaitEvent(gs, c->gevents.back(), 0);
+    cudaStream_t gs = c->gstreams[gi], ds = c->dstreams[gi];
     const GroupDev& gd = c->groups[gi].d;
-    if (!le) le = (gd.nz > 1) ? launch_step3(gd, gs, &nl) : launch_step(gd, gs, &nl);
-    if (!le) le = (gd.nz > 1) ? launch_diag3(gd, gs, &nl) : launch_diag(gd, gs, &nl);
+    const bool d3 = gd.nz > 1;
+    le = cudaStreamWaitEvent(gs, c->gevents.back(), 0);
+    if (!le && kind == 1) {
+      le = cudaStreamWaitEvent(ds, c->gevents.back(), 0);
+      if (!le) le = d3 ? launch_diag3(gd, ds, nl) : launch_diag(gd, ds, nl);
+      if (!le) le = cudaEventRecord(c->devents[gi], ds);
+    }
+    if (kind == 2) {
+      if (!le) le = d3 ? launch_diag3(gd, gs, nl) : launch_diag(gd, gs, nl);
+    } else {
+      for (int s = 0; s < 3 && !le; ++s) le = d3 ? launch_stage3(gd, s, gs, nl) : launch_stage(gd, s, gs, nl);
+      if (!le && kind == 1) le = cudaStreamWaitEvent(gs, c->devents[gi], 0);
+      if (!le) le = d3 ? launch_stage3(gd, 3, gs, nl) : launch_stage(gd, 3, gs, nl);
+    }
     if (!le) le = cudaEventRecord(c->gevents[gi], gs);
     if (!le) le = cudaStreamWaitEvent(c->cap, c->gevents[gi], 0);
   }
-  cudaError_t ee = cudaStreamEndCapture(c->cap, &c->graph);
-  if (le) return fail_cuda(le, "launch during graph capture", __LINE__);
-  if (ee) return fail_cuda(ee, "cudaStreamEndCapture", __LINE__);
-  CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
-  c->launches = nl;
+  return le;
+}
+
+static int capture_step_graph(ptt_ctx* c) {
+  for (int k = 0; k < 3; ++k) {
+    if (c->exec[k]) { cudaGraphExecDestroy(c->exec[k]); c->exec[k] = nullptr; }
+    if (c->graph[k]) { cudaGraphDestroy(c->graph[k]); c->graph[k] = nullptr; }
+  }
+  for (int k = 0; k < 3; ++k) {
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    int nl = 0;
+    const cudaError_t le = capture_kind(c, k, &nl);
+    const cudaError_t ee = cudaStreamEndCapture(c->cap, &c->graph[k]);
+    if (le) return fail_cuda(le, "launch during graph capture", __LINE__);
+    if (ee) return fail_cuda(ee, "cudaStreamEndCapture", __LINE__);
+    CK(cudaGraphInstantiate(&c->exec[k], c->graph[k], 0));
+    if (k == 1) c->launches = nl;   // every kernel of one step, diagnostics included
+  }
   return PTT_OK;
 }
 
@@ -904,9 +936,13 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   // independent, so each gets its own branch (fork/join through events)
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   c->gstreams.assign(c->groups.size(), nullptr);
+  c->dstreams.assign(c->groups.size(), nullptr);
   c->gevents.assign(c->groups.size() + 1, nullptr);
+  c->devents.assign(c->groups.size(), nullptr);
   for (auto& s2 : c->gstreams) CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+  for (auto& s2 : c->dstreams) CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
   for (auto& e2 : c->gevents) CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+  for (auto& e2 : c->devents) CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
   {
     const int s3 = capture_step_graph(c.get());
     if (s3) return s3;
@@ -1048,7 +1084,10 @@ int ptt_explicit_rhs(ptt_ctx* c, int32_t member, double* h) {
 
 int ptt_step(ptt_ctx* c, int32_t nsteps) {
   if (!c || nsteps < 0) return PTT_EINVAL;
-  for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(c->exec, c->stream));
+  if (nsteps == 0) return PTT_OK;
+  CK(cudaGraphLaunch(c->exec[0], c->stream));
+  for (int i = 1; i < nsteps; ++i) CK(cudaGraphLaunch(c->exec[1], c->stream));
+  CK(cudaGraphLaunch(c->exec[2], c->stream));
   return PTT_OK;
 }
 
@@ -1379,11 +1418,15 @@ int ptt_destroy(ptt_ctx* c) {
   if (!c) return PTT_EINVAL;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  if (c->exec) cudaGraphExecDestroy(c->exec);
-  if (c->graph) cudaGraphDestroy(c->graph);
+  for (int k = 0; k < 3; ++k) {
+    if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
+    if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+  }
   if (c->cap) cudaStreamDestroy(c->cap);
   for (auto s2 : c->gstreams) if (s2) cudaStreamDestroy(s2);
+  for (auto s2 : c->dstreams) if (s2) cudaStreamDestroy(s2);
   for (auto e2 : c->gevents) if (e2) cudaEventDestroy(e2);
+  for (auto e2 : c->devents) if (e2) cudaEventDestroy(e2);
   delete c;
   return PTT_OK;
 }
