@@ -358,42 +358,54 @@ __device__ __forceinline__ double2 warp_allsum2(double2 v) {
 // (c_0 = 2), as two same-parity suffix sums T(k) = sum_{p >= k, p = k mod 2} p a_p
 // with out_{k-1} = (2/c_{k-1}) T(k).  `out` must not alias `a`.
 template <typename C2>
-__device__ void warp_cheb_deriv(const C2* a, C2* out, int N) {
+__device__ void warp_cheb_deriv_par(const C2* a, C2* out, int N, int par) {
   using T = typename RealOf<C2>::T;
   const int lane = threadIdx.x & 31;
-  for (int par = 0; par < 2; ++par) {
-    const int L = (N - par + 1) / 2;
-    const int c = (L + 31) / 32;
-    const int i0 = min(lane * c, L), i1 = min(i0 + c, L);
-    // partial sums carried doubled (2 k a_k): b_{k-1} = acc + ex for k >= 2
-    // and (acc + ex)/2 for k = 1, with no scaling in the sweeps
-    C2 acc = zero2<C2>();
-    for (int i = i1 - 1; i >= i0; --i) {
-      const int k = par + 2 * i;
-      acc = cfma((T)(2 * k), a[k], acc);
-      if (k >= 1) out[k - 1] = acc;
-    }
-    C2 inc = acc;
-    for (int o = 1; o < 32; o <<= 1) {
-      const C2 v = shfl_down2(inc, o);
-      if (lane + o < 32) inc = cadd(inc, v);
-    }
-    C2 ex = shfl_down2(inc, 1);
-    if (lane == 31) ex = zero2<C2>();
-    for (int i = i0; i < i1; ++i) {
-      const int k = par + 2 * i;
-      if (k >= 2) out[k - 1] = cadd(ex, out[k - 1]);
-      else if (k == 1) out[0] = cscl(cadd(ex, out[0]), (T)0.5);
-    }
+  const int L = (N - par + 1) / 2;
+  const int c = (L + 31) / 32;
+  const int i0 = min(lane * c, L), i1 = min(i0 + c, L);
+  // partial sums carried doubled (2 k a_k): b_{k-1} = acc + ex for k >= 2
+  // and (acc + ex)/2 for k = 1, with no scaling in the sweeps
+  C2 acc = zero2<C2>();
+  for (int i = i1 - 1; i >= i0; --i) {
+    const int k = par + 2 * i;
+    acc = cfma((T)(2 * k), a[k], acc);
+    if (k >= 1) out[k - 1] = acc;
   }
-  if (lane == 0) out[N - 1] = zero2<C2>();
+  C2 inc = acc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const C2 v = shfl_down2(inc, o);
+    if (lane + o < 32) inc = cadd(inc, v);
+  }
+  C2 ex = shfl_down2(inc, 1);
+  if (lane == 31) ex = zero2<C2>();
+  for (int i = i0; i < i1; ++i) {
+    const int k = par + 2 * i;
+    if (k >= 2) out[k - 1] = cadd(ex, out[k - 1]);
+    else if (k == 1) out[0] = cscl(cadd(ex, out[0]), (T)0.5);
+  }
+  // out_{N-1} (parity of N - 1) has no term
+  if (lane == 0 && ((N - 1 - par) & 1)) out[N - 1] = zero2<C2>();
   __syncwarp();
+}
+
+template <typename C2>
+__device__ void warp_cheb_deriv(const C2* a, C2* out, int N) {
+  warp_cheb_deriv_par(a, out, N, 0);
+  warp_cheb_deriv_par(a, out, N, 1);
+}
+
+// -x for complex values by sign-bit flips (integer operations, no FP64 work)
+__device__ __forceinline__ double2 cneg_bits(double2 v) {
+  return make_double2(flip_sign(v.x, true), flip_sign(v.y, true));
 }
 
 // Warp-cooperative quasi-tridiagonal tau solve (system stated at k_spec): the backward
 // elimination P_i = alpha_i + beta_i P_{i+1} and the forward substitution
 // a_i = P_i + Q_i a_{i-1} are affine recurrences, evaluated as warp scans of
 // affine maps; the boundary sums are warp reductions.  `out` may alias R.
+// CH >= the rows per lane, ceil((L - 1)/32) (register arrays of that size).
+template <int CH>
 __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, double2* out,
                               const double* Q, const double* inv, const double* F, double G,
                               const double* w1, const double* w2, const double* w3,
@@ -403,22 +415,22 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
   const int nr = L - 1;
   const int c = (nr + 31) / 32;
   const int i0 = min(1 + lane * c, L), i1 = min(i0 + c, L);
-  double2 al[kMaxChunk];
-  double be[kMaxChunk];
+  double2 al[CH];
+  double be[CH];
   double2 rs = czero();
 #pragma unroll
-  for (int t = 0; t < kMaxChunk; ++t) {
+  for (int t = 0; t < CH; ++t) {
     const int i = i0 + t;
     if (t < c && i < i1) {
       const int n = p + 2 * i;
-      const double2 Rm2 = cscl(R[n - 2], rsign);
-      const double2 R0 = cscl(R[n], rsign);
+      const double2 Rm2 = R[n - 2];
+      const double2 R0 = R[n];
       const double cc = (n == 2) ? 2.0 : 1.0;
       double2 r = cscl(Rm2, -cc * w1[n]);
       if (n <= N - 3) r = cfma(w2[n], R0, r);
       double un = 0.0;
       if (n <= N - 5) {
-        r = cfma(-w3[n], cscl(R[n + 2], rsign), r);
+        r = cfma(-w3[n], R[n + 2], r);
         un = -alpha * w3[n];
       }
       al[t] = cscl(r, inv[n]);
@@ -429,13 +441,13 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
       be[t] = 1.0;
     }
   }
-  if (lane == 0) rs = cadd(rs, cscl(R[p], rsign));
+  if (lane == 0) rs = cadd(rs, R[p]);
   __syncwarp();
   // backward: chunk map P_{i0} = A + B P_{i1}
   double2 A = czero();
   double B = 1.0;
 #pragma unroll
-  for (int t = kMaxChunk - 1; t >= 0; --t) {
+  for (int t = CH - 1; t >= 0; --t) {
     if (t < c && i0 + t < i1) {
       A = cfma(be[t], A, al[t]);
       B *= be[t];
@@ -456,7 +468,7 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
   double2 U = czero();
   double2 P = Pin;
 #pragma unroll
-  for (int t = kMaxChunk - 1; t >= 0; --t) {
+  for (int t = CH - 1; t >= 0; --t) {
     const int i = i0 + t;
     if (t < c && i < i1) {
       const int n = p + 2 * i;
@@ -471,10 +483,10 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
   // forward: chunk map a_{i1-1} = C + D a_{i0-1}
   double2 Cc = czero();
   double Dd = 1.0;
-  double2 Pv[kMaxChunk];
-  double Qv[kMaxChunk];
+  double2 Pv[CH];
+  double Qv[CH];
 #pragma unroll
-  for (int t = 0; t < kMaxChunk; ++t) {
+  for (int t = 0; t < CH; ++t) {
     const int i = i0 + t;
     if (t < c && i < i1) {
       const int n = p + 2 * i;
@@ -501,7 +513,7 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
   double2 part = (lane == 0) ? a0 : czero();  // sum of a_{p+2i}, i < L-1
   __syncwarp();
 #pragma unroll
-  for (int t = 0; t < kMaxChunk; ++t) {
+  for (int t = 0; t < CH; ++t) {
     const int i = i0 + t;
     if (t < c && i < i1) {
       av = cfma(Qv[t], av, Pv[t]);
@@ -520,6 +532,12 @@ __device__ void warp_qt_solve(int N, int p, double alpha, const double2* R, doub
   if (L > 1 && fabs(Q[nl]) > kTopFromWall) {
     part = warp_allsum2(part);
     if (lane == 0) out[nl] = csub(cscl(rs, bcfac), part);
+    __syncwarp();
+  }
+  // the solve above is of (alpha - beta D^2) a = R; the system's right-hand
+  // side is rsign R, so a flips sign with it
+  if (rsign < 0.0) {
+    for (int i = lane; i < L; i += 32) out[p + 2 * i] = cneg_bits(out[p + 2 * i]);
     __syncwarp();
   }
 }
@@ -551,11 +569,13 @@ __device__ __forceinline__ void lane_cheb_deriv(const double2* __restrict__ a,
 // backward elimination P_n = (r_n - u_n P_{n+2}) inv_n with the three-term
 // right-hand side r_n of the twice-integrated rows, accumulating the
 // boundary sum U = sum F_n P_n; the boundary row gives
-// a_p = (bcfac sum_{n = p} rsign R_n - U) G; forward substitution
+// a_p = (bcfac sum_{n = p} R_n - U) G; forward substitution
 // a_n = P_n + Q_n a_{n-2}.  Q, inv, F: the right-hand-side-independent
 // elimination factors of this (alpha, mode, parity), precomputed on the
-// host.  `out` must not alias R (every input is independent of the
-// recurrence, so unrolled iterations keep several loads in flight).
+// host.  The solve runs on R and flips the result's sign when the system's
+// right-hand side is rsign R with rsign = -1.  `out` must not alias R (every
+// input is independent of the recurrence, so unrolled iterations keep
+// several loads in flight).
 __device__ __forceinline__ void lane_qt_solve(int N, int p, double alpha,
                                               const double2* __restrict__ R,
                                               double2* __restrict__ out,
@@ -568,10 +588,10 @@ __device__ __forceinline__ void lane_qt_solve(int N, int p, double alpha,
                                               double rsign) {
   const int nl = ((N - 1 - p) & ~1) + p;
   double2 Pn2 = czero(), U = czero(), rs = czero(), Rp2 = czero();
-  double2 R0 = cscl(R[nl], rsign);
+  double2 R0 = R[nl];
 #pragma unroll 4
   for (int n = nl; n >= p + 2; n -= 2) {
-    const double2 Rm2 = cscl(R[n - 2], rsign);
+    const double2 Rm2 = R[n - 2];
     const double cc = (n == 2) ? 2.0 : 1.0;
     double2 r = cscl(Rm2, -cc * w1[n]);
     if (n <= N - 3) r = cfma(w2[n], R0, r);
@@ -601,6 +621,9 @@ __device__ __forceinline__ void lane_qt_solve(int N, int p, double alpha,
     for (int n = p; n < nl; n += 2) part = cadd(part, out[n]);
     out[nl] = csub(cscl(rs, bcfac), part);
   }
+  // solved for R; the right-hand side is rsign R
+  if (rsign < 0.0)
+    for (int n = p; n <= nl; n += 2) out[n] = cneg_bits(out[n]);
 }
 
 // SBDF sum of one evolved column, parity p, order index O (0..3: SBDF1-4):

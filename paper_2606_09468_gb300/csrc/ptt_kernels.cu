@@ -142,9 +142,11 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
 //     phi-Helmholtz, v-Poisson and the influence correction v'(+-1) = 0
 //   u = i (D v) / k from continuity (Eq. 3)
 // mode 1: only H_x, H_y into Rb[0], Rb[1] (explicit right-hand side).
-// Two blocks per SM (128 registers, a few hundred bytes of spills) run the
+// CH: tau-scan rows per lane (register arrays of the solves; launch_spec
+// picks the smallest of 2, 4, 8 that holds ny).  Two blocks per SM run the
 // stage about 25 % faster than one block at the ~160 registers ptxas picks
 // unbounded.
+template <int CH>
 __global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) {
   const int b = blockIdx.y;
   const int m = blockIdx.x;
@@ -190,15 +192,17 @@ __global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) {
     for (int i = tid; i < N; i += nt) tb[9 * N + i] = vh[i];
   }
   __syncthreads();
-  // derivatives, one warp each: D c_xy -> sR[0], D c_yy -> sR[1], D v -> sR[2] -> D^2 v -> sq
+  // derivatives, one warp per (column, parity): D c_xy -> sR[0], D c_yy -> sR[1],
+  // D v -> sR[2], then D^2 v -> sq
   {
-    const int warp = tid >> 5;
-    if (warp == 0) warp_cheb_deriv(sc1, sR, N);
-    else if (warp == 1) warp_cheb_deriv(sc2, sR + N, N);
-    else if (warp == 2 && mode == 0 && m != 0) {
-      warp_cheb_deriv(sv, sR + 2 * N, N);
-      warp_cheb_deriv(sR + 2 * N, sq, N);
-    }
+    const int warp = tid >> 5, par = warp & 1, col = warp >> 1;
+    if (col == 0) warp_cheb_deriv_par(sc1, sR, N, par);
+    else if (col == 1) warp_cheb_deriv_par(sc2, sR + N, N, par);
+    else if (col == 2 && mode == 0 && m != 0) warp_cheb_deriv_par(sv, sR + 2 * N, N, par);
+  }
+  if (mode == 0 && m != 0) {
+    __syncthreads();
+    if (tid < 64) warp_cheb_deriv_par(sR + 2 * N, sq, N, tid >> 5);
   }
   __syncthreads();
   for (int n = tid; n < N; n += nt) {
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) {
     return;
   }
   // forcing of q: m >= 1: -D(i k H_x) - k^2 H_y; m = 0: H_x
-  if (m != 0 && tid < 32) warp_cheb_deriv(shx, sR, N);
+  if (m != 0 && tid < 64) warp_cheb_deriv_par(shx, sR, N, tid >> 5);
   __syncthreads();
   for (int n = tid; n < N; n += nt)
     snq[n] = (m == 0) ? shx[n] : csub(cscl(mul_i(sR[n]), -km), cscl(shy[n], km2));
@@ -269,18 +273,18 @@ __global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) {
         const double ia = 1.0 / alpha;
         for (int n = p + 2 * lane; n < N; n += 64) out[n] = cscl(R[n], ia);
       } else {
-        warp_qt_solve(N, p, alpha, R, out, T0, T0 + N, T0 + 2 * N, G(0), w1, w2, w3, pr.dt / a0,
+        warp_qt_solve<CH>(N, p, alpha, R, out, T0, T0 + N, T0 + 2 * N, G(0), w1, w2, w3, pr.dt / a0,
                       1.0);
       }
     } else if (m == 0) {
-      warp_qt_solve(N, p, a0 / pr.dt, sR + 3 * N, shy, T1, T1 + N, T1 + 2 * N, G(1), w1, w2, w3,
+      warp_qt_solve<CH>(N, p, a0 / pr.dt, sR + 3 * N, shy, T1, T1 + N, T1 + 2 * N, G(1), w1, w2, w3,
                     0.0, 1.0);
       for (int n = p + 2 * lane; n < N; n += 64) sv[n] = czero();
     } else {
       double2* Rv = sR + 3 * N;
-      warp_qt_solve(N, p, a0 / pr.dt + pr.nu * km2, Rv, Rv, T1, T1 + N, T1 + 2 * N, G(1), w1, w2,
+      warp_qt_solve<CH>(N, p, a0 / pr.dt + pr.nu * km2, Rv, Rv, T1, T1 + N, T1 + 2 * N, G(1), w1, w2,
                     w3, 0.0, 1.0);
-      warp_qt_solve(N, p, km2, Rv, sv, T2, T2 + N, T2 + 2 * N, G(2), w1, w2, w3, 0.0, -1.0);
+      warp_qt_solve<CH>(N, p, km2, Rv, sv, T2, T2 + N, T2 + 2 * N, G(2), w1, w2, w3, 0.0, -1.0);
       double2 sacc = czero();
       for (int n = p + 2 * lane; n < N; n += 64) sacc = cfma((double)n * n, sv[n], sacc);
       sacc = warp_allsum2(sacc);
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) {
   __syncthreads();
   // u = i (D v) / k (m >= 1), continuity
   if (m != 0) {
-    if (tid < 32) warp_cheb_deriv(sv, sR, N);
+    if (tid < 64) warp_cheb_deriv_par(sv, sR, N, tid >> 5);
     __syncthreads();
     const double ik = 1.0 / km;
     for (int n = tid; n < N; n += nt) shy[n] = cscl(mul_i(sR[n]), ik);
@@ -729,9 +733,22 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
   if ((e = optin(k_xfused<double2>, optin_bytes))) return e;
   if ((e = optin(k_xfused<float2>, optin_bytes))) return e;
   if ((e = optin(k_xrows, optin_bytes))) return e;
-  if ((e = optin(k_spec, optin_bytes))) return e;
+  if ((e = optin(k_spec<2>, optin_bytes))) return e;
+  if ((e = optin(k_spec<4>, optin_bytes))) return e;
+  if ((e = optin(k_spec<8>, optin_bytes))) return e;
   if ((e = optin(k_diag_final, optin_bytes))) return e;
   return cudaSuccess;
+}
+
+// k_spec with the smallest tau-scan chunk that holds the group's rows:
+// ceil((L - 1)/32) rows per lane with L = (ny + 1)/2 coefficients of parity 0.
+static void launch_spec(const GroupDev& g, int mode, cudaStream_t st) {
+  const int rows = ((g.N + 1) / 2 - 1 + 31) / 32;
+  const dim3 grid(g.K, g.nb);
+  const size_t sm = smem_spec(g.N);
+  if (rows <= 2) k_spec<2><<<grid, 256, sm, st>>>(g, mode);
+  else if (rows <= 4) k_spec<4><<<grid, 256, sm, st>>>(g, mode);
+  else k_spec<8><<<grid, 256, sm, st>>>(g, mode);
 }
 
 // Stage s of one step for one group (see ptt.h: PTT_NSTAGES).
@@ -774,7 +791,7 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       break;
     }
     case 3:
-      k_spec<<<dim3(g.K, g.nb), 256, smem_spec(g.N), st>>>(g, 0);
+      launch_spec(g, 0, st);
       k_tick<<<cdiv(g.nb, 128), 128, 0, st>>>(g);
       n = 2;
       break;
@@ -819,7 +836,7 @@ cudaError_t launch_explicit(const GroupDev& g, cudaStream_t st) {
     cudaError_t e = launch_stage(g, s, st, nullptr);
     if (e) return e;
   }
-  k_spec<<<dim3(g.K, g.nb), 256, smem_spec(g.N), st>>>(g, 1);
+  launch_spec(g, 1, st);
   return cudaGetLastError();
 }
 
