@@ -595,8 +595,10 @@ struct ptt_ctx {
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaStream_t> gstreams;  // one capture branch per group
   std::vector<cudaStream_t> dstreams;  // the group's diagnostics branch
+  std::vector<cudaStream_t> pstreams;  // [2 per group] its energy and mid-plane parts
   std::vector<cudaEvent_t> gevents;
   std::vector<cudaEvent_t> devents;
+  std::vector<cudaEvent_t> pevents;    // [3 per group] fork / join of those parts
   int launches = 0;
   int device = 0;
 };
@@ -698,7 +700,9 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
 // stage waits for.  Graph 0 is the first step of a ptt_step call (stages 0-3;
 // the state it starts from was diagnosed when it was made), graph 1 a later
 // step (the previous step's diagnostics beside stages 0-2, then stage 3), and
-// graph 2 the diagnostics of the last step's result (stage 4).
+// graph 2 the diagnostics of the last step's result (stage 4).  Within the
+// diagnostics, the energy transform and the mid-plane sums run on branches of
+// their own beside the Tr c chain (launch_diag_split).
 static cudaError_t capture_kind(ptt_ctx* c, int kind, int* nl) {
   cudaError_t le = cudaEventRecord(c->gevents.back(), c->cap);
   for (size_t gi = 0; gi < c->groups.size() && !le; ++gi) {
@@ -706,13 +710,18 @@ static cudaError_t capture_kind(ptt_ctx* c, int kind, int* nl) {
     const GroupDev& gd = c->groups[gi].d;
     const bool d3 = gd.nz > 1;
     le = cudaStreamWaitEvent(gs, c->gevents.back(), 0);
+    auto diag = [&](cudaStream_t s0) {
+      const DiagStreams d{{s0, c->pstreams[2 * gi], c->pstreams[2 * gi + 1]},
+                          {c->pevents[3 * gi], c->pevents[3 * gi + 1], c->pevents[3 * gi + 2]}};
+      return d3 ? launch_diag_split3(gd, d, nl) : launch_diag_split(gd, d, nl);
+    };
     if (!le && kind == 1) {
       le = cudaStreamWaitEvent(ds, c->gevents.back(), 0);
-      if (!le) le = d3 ? launch_diag3(gd, ds, nl) : launch_diag(gd, ds, nl);
+      if (!le) le = diag(ds);
       if (!le) le = cudaEventRecord(c->devents[gi], ds);
     }
     if (kind == 2) {
-      if (!le) le = d3 ? launch_diag3(gd, gs, nl) : launch_diag(gd, gs, nl);
+      if (!le) le = diag(gs);
     } else {
       for (int s = 0; s < 3 && !le; ++s) le = d3 ? launch_stage3(gd, s, gs, nl) : launch_stage(gd, s, gs, nl);
       if (!le && kind == 1) le = cudaStreamWaitEvent(gs, c->devents[gi], 0);
@@ -937,12 +946,16 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   c->gstreams.assign(c->groups.size(), nullptr);
   c->dstreams.assign(c->groups.size(), nullptr);
+  c->pstreams.assign(2 * c->groups.size(), nullptr);
   c->gevents.assign(c->groups.size() + 1, nullptr);
   c->devents.assign(c->groups.size(), nullptr);
+  c->pevents.assign(3 * c->groups.size(), nullptr);
   for (auto& s2 : c->gstreams) CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
   for (auto& s2 : c->dstreams) CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+  for (auto& s2 : c->pstreams) CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
   for (auto& e2 : c->gevents) CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
   for (auto& e2 : c->devents) CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+  for (auto& e2 : c->pevents) CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
   {
     const int s3 = capture_step_graph(c.get());
     if (s3) return s3;
@@ -1425,8 +1438,10 @@ int ptt_destroy(ptt_ctx* c) {
   if (c->cap) cudaStreamDestroy(c->cap);
   for (auto s2 : c->gstreams) if (s2) cudaStreamDestroy(s2);
   for (auto s2 : c->dstreams) if (s2) cudaStreamDestroy(s2);
+  for (auto s2 : c->pstreams) if (s2) cudaStreamDestroy(s2);
   for (auto e2 : c->gevents) if (e2) cudaEventDestroy(e2);
   for (auto e2 : c->devents) if (e2) cudaEventDestroy(e2);
+  for (auto e2 : c->pevents) if (e2) cudaEventDestroy(e2);
   delete c;
   return PTT_OK;
 }

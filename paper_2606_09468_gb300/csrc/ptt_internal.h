@@ -120,6 +120,18 @@ inline int diag_tiles(int N, int nx, int nz) {
 cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nlaunch);
 cudaError_t launch_step(const GroupDev& g, cudaStream_t st, int* nlaunch);
 cudaError_t launch_diag(const GroupDev& g, cudaStream_t st, int* nlaunch);
+
+// The diagnostics stage as three independent parts and a reduction: the Tr c
+// chain (unpadded y grid, then z and x), the energy transform, the mid-plane
+// sums; the reduction (tiles, counts, histograms, record) reads all three.
+// s[0] runs the Tr c chain and the reduction; with s[1], s[2] distinct from
+// s[0] the other two parts fork onto them (ev[0] forks, ev[1], ev[2] join),
+// as branches of a captured graph.
+struct DiagStreams {
+  cudaStream_t s[3];
+  cudaEvent_t ev[3];
+};
+cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nlaunch);
 cudaError_t launch_explicit(const GroupDev& g, cudaStream_t st);
 // physical staging [5][N][nx] -> state of member b (resets counter/status)
 cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st);
@@ -135,6 +147,7 @@ cudaError_t set_kernel_attributes3(int max_dyn_smem);
 cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nlaunch);
 cudaError_t launch_step3(const GroupDev& g, cudaStream_t st, int* nlaunch);
 cudaError_t launch_diag3(const GroupDev& g, cudaStream_t st, int* nlaunch);
+cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nlaunch);
 cudaError_t launch_explicit3(const GroupDev& g, cudaStream_t st);
 cudaError_t launch_phys_to_state3(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st);

@@ -858,59 +858,86 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       k_tick3<<<cdiv(g.nb, 128), 128, 0, st>>>(g);
       n = 2;
       break;
-    case 4: {  // diagnostics
-      // Tr c = c_xx + c_yy + c_zz on the unpadded grid: y (Gauss-Lobatto) -> z -> x
-      YJob T = yjob3(g, true, g.N - 1, g.CcolU, g.plPu, nullptr);
-      T.src = g.X; T.dst = g.DT;
-      T.src_mstride = 9 * NK; T.dst_mstride = (long long)NK;
-      T.src_fstride = NK; T.dst_fstride = 0;
-      T.src_field[0] = 3; T.src_field2[0] = 6; T.src_field3[0] = 8; T.dst_field[0] = 0; T.deriv[0] = 0;
-      k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
-      ZJob Z = zjob(g, true, g.nz, g.N, g.plNz);
-      Z.src = g.DT; Z.src_f32 = 0; Z.dst = g.DZ; Z.dst_f32 = 0;
-      Z.src_mstride = (long long)NK; Z.dst_mstride = (long long)g.N * g.nz * K;
-      Z.src_fstride = 0; Z.dst_fstride = 0;
-      Z.src_field[0] = 0; Z.dst_field[0] = 0; Z.dz[0] = 0;
-      k_zcols<double2><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), st>>>(Z);
-      XJob X{};
-      X.srcC = g.DZ; X.dstR = g.DV;
-      X.src_mstride = (long long)g.N * g.nz * K; X.dst_mstride = (long long)g.N * g.nz * g.nx;
-      X.src_fstride = 0; X.dst_fstride = 0;
-      X.src_rstep = 1; X.dst_rstep = 1;
-      X.nf = 1; X.K = K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
-      k_xrows<<<dim3(g.N * g.nz, g.nb), 256, smem_xrows(1, g.nx), st>>>(X);
-      // u, v, w on the Me Gauss points (energy)
-      YJob J = yjob3(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
-      J.src = g.X; J.dst = g.DY;
-      J.src_mstride = 9 * NK; J.dst_mstride = 3LL * g.Me * KZ;
-      J.src_fstride = NK; J.dst_fstride = (long long)g.Me * KZ;
-      for (int i = 0; i < 3; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-      k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
-      // mid-plane: per-mode sums, then z and x syntheses of the 8 quantities
-      k_diag_mid3<<<dim3(cdiv(KZ, 8), g.nb), 256, 0, st>>>(g);
-      ZJob Zm = zjob(g, true, g.nz, 1, g.plNz);
-      Zm.src = g.DM; Zm.src_f32 = 0; Zm.dst = g.DMZ; Zm.dst_f32 = 0;
-      Zm.src_mstride = 8LL * KZ; Zm.dst_mstride = 8LL * g.nz * K;
-      Zm.src_fstride = KZ; Zm.dst_fstride = (long long)g.nz * K;
-      for (int i = 0; i < 8; ++i) { Zm.src_field[i] = i; Zm.dst_field[i] = i; Zm.dz[i] = 0; }
-      k_zcols<double2><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), st>>>(Zm);
-      XJob Xm{};
-      Xm.srcC = g.DMZ; Xm.dstR = g.MV;
-      Xm.src_mstride = 8LL * g.nz * K; Xm.dst_mstride = 8LL * g.nz * g.nx;
-      Xm.src_fstride = (long long)g.nz * K; Xm.dst_fstride = (long long)g.nz * g.nx;
-      Xm.src_rstep = 1; Xm.dst_rstep = 1;
-      Xm.nf = 8; Xm.K = K; Xm.n = g.nx; Xm.c2r = 1; Xm.status = g.status; Xm.pl = g.plNx;
-      k_xrows<<<dim3(g.nz, g.nb), 256, smem_xrows(4, g.nx), st>>>(Xm);
-      k_diag_part3<<<dim3(g.ntile, g.nb), 256, 0, st>>>(g);
-      k_diag_count3<<<dim3(g.ntile, g.nb), 256, 0, st>>>(g);
-      k_diag_final3<<<g.nb, 256, 0, st>>>(g);
-      n = 10;
-      break;
+    case 4: {  // diagnostics, in order on one stream
+      const DiagStreams d{{st, st, st}, {nullptr, nullptr, nullptr}};
+      return launch_diag_split3(g, d, nl);
     }
     default:
       return cudaErrorInvalidValue;
   }
   if (nl) *nl += n;
+  return cudaGetLastError();
+}
+
+// Fork d.s[1], d.s[2] off d.s[0] (when distinct) before the parts, join after.
+static cudaError_t diag_fork3(const DiagStreams& d) {
+  if (d.s[1] == d.s[0]) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(d.ev[0], d.s[0]);
+  if (!e) e = cudaStreamWaitEvent(d.s[1], d.ev[0], 0);
+  if (!e) e = cudaStreamWaitEvent(d.s[2], d.ev[0], 0);
+  return e;
+}
+static cudaError_t diag_join3(const DiagStreams& d) {
+  if (d.s[1] == d.s[0]) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(d.ev[1], d.s[1]);
+  if (!e) e = cudaEventRecord(d.ev[2], d.s[2]);
+  if (!e) e = cudaStreamWaitEvent(d.s[0], d.ev[1], 0);
+  if (!e) e = cudaStreamWaitEvent(d.s[0], d.ev[2], 0);
+  return e;
+}
+
+cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl) {
+  const int KZ = g.KZ, K = g.K;
+  const size_t NK = (size_t)g.N * KZ;
+  cudaError_t e = diag_fork3(d);
+  if (e) return e;
+  // energy: u, v, w on the Me Gauss points
+  YJob J = yjob3(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
+  J.src = g.X; J.dst = g.DY;
+  J.src_mstride = 9 * NK; J.dst_mstride = 3LL * g.Me * KZ;
+  J.src_fstride = NK; J.dst_fstride = (long long)g.Me * KZ;
+  for (int i = 0; i < 3; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
+  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), d.s[1]>>>(J);
+  // mid-plane: per-mode sums, then z and x syntheses of the 8 quantities
+  k_diag_mid3<<<dim3(cdiv(KZ, 8), g.nb), 256, 0, d.s[2]>>>(g);
+  ZJob Zm = zjob(g, true, g.nz, 1, g.plNz);
+  Zm.src = g.DM; Zm.src_f32 = 0; Zm.dst = g.DMZ; Zm.dst_f32 = 0;
+  Zm.src_mstride = 8LL * KZ; Zm.dst_mstride = 8LL * g.nz * K;
+  Zm.src_fstride = KZ; Zm.dst_fstride = (long long)g.nz * K;
+  for (int i = 0; i < 8; ++i) { Zm.src_field[i] = i; Zm.dst_field[i] = i; Zm.dz[i] = 0; }
+  k_zcols<double2><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
+  XJob Xm{};
+  Xm.srcC = g.DMZ; Xm.dstR = g.MV;
+  Xm.src_mstride = 8LL * g.nz * K; Xm.dst_mstride = 8LL * g.nz * g.nx;
+  Xm.src_fstride = (long long)g.nz * K; Xm.dst_fstride = (long long)g.nz * g.nx;
+  Xm.src_rstep = 1; Xm.dst_rstep = 1;
+  Xm.nf = 8; Xm.K = K; Xm.n = g.nx; Xm.c2r = 1; Xm.status = g.status; Xm.pl = g.plNx;
+  k_xrows<<<dim3(g.nz, g.nb), 256, smem_xrows(4, g.nx), d.s[2]>>>(Xm);
+  // Tr c = c_xx + c_yy + c_zz on the unpadded grid: y (Gauss-Lobatto) -> z -> x
+  YJob T = yjob3(g, true, g.N - 1, g.CcolU, g.plPu, nullptr);
+  T.src = g.X; T.dst = g.DT;
+  T.src_mstride = 9 * NK; T.dst_mstride = (long long)NK;
+  T.src_fstride = NK; T.dst_fstride = 0;
+  T.src_field[0] = 3; T.src_field2[0] = 6; T.src_field3[0] = 8; T.dst_field[0] = 0; T.deriv[0] = 0;
+  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), d.s[0]>>>(T);
+  ZJob Z = zjob(g, true, g.nz, g.N, g.plNz);
+  Z.src = g.DT; Z.src_f32 = 0; Z.dst = g.DZ; Z.dst_f32 = 0;
+  Z.src_mstride = (long long)NK; Z.dst_mstride = (long long)g.N * g.nz * K;
+  Z.src_fstride = 0; Z.dst_fstride = 0;
+  Z.src_field[0] = 0; Z.dst_field[0] = 0; Z.dz[0] = 0;
+  k_zcols<double2><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
+  XJob X{};
+  X.srcC = g.DZ; X.dstR = g.DV;
+  X.src_mstride = (long long)g.N * g.nz * K; X.dst_mstride = (long long)g.N * g.nz * g.nx;
+  X.src_fstride = 0; X.dst_fstride = 0;
+  X.src_rstep = 1; X.dst_rstep = 1;
+  X.nf = 1; X.K = K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
+  k_xrows<<<dim3(g.N * g.nz, g.nb), 256, smem_xrows(1, g.nx), d.s[0]>>>(X);
+  if ((e = cudaGetLastError()) || (e = diag_join3(d))) return e;
+  k_diag_part3<<<dim3(g.ntile, g.nb), 256, 0, d.s[0]>>>(g);
+  k_diag_count3<<<dim3(g.ntile, g.nb), 256, 0, d.s[0]>>>(g);
+  k_diag_final3<<<g.nb, 256, 0, d.s[0]>>>(g);
+  if (nl) *nl += 10;
   return cudaGetLastError();
 }
 
