@@ -268,11 +268,13 @@ int ptt_stage_work(ptt_ctx* ctx, double* flops, double* bytes, int32_t* launches
 /* Launch-shape autotuner.  For every shape group of the context, times
  * (CUDA events, a few launches each) the candidate launch shapes of the
  * transform stages and keeps the fastest: threads per block of the fused x
- * pass (128..512), Chebyshev columns per block of the y passes (1..16, as
- * shared memory allows) and, in 3D, x-mode lines per block of the z passes
- * (1..16); then re-captures the step graph.  These stages read the state
- * without changing it and a launch shape changes only which thread computes
- * what, so results are bitwise the same before and after.  choices (may be
+ * pass (128..512), Chebyshev columns per block of the y passes and of the
+ * diagnostics' two y transforms (1..16, as shared memory allows) and, in 3D,
+ * x-mode lines per block of the z passes (1..16); then re-captures the step
+ * graph.  These launches read the state without changing it (the
+ * diagnostics' records and histograms are not touched) and a launch shape
+ * changes only which thread computes what, so results are bitwise the same
+ * before and after.  choices (may be
  * NULL) receives, per group in creation order (at most max_groups), the
  * chosen (columns, lines, threads); groups are the distinct (nx, ny, nz,
  * precision) of the members in order of first appearance.  Synchronous. */

@@ -1157,11 +1157,14 @@ int ptt_resample(ptt_ctx* dst, int32_t dm, ptt_ctx* src, int32_t sm) {
 }
 
 // Device milliseconds of `reps` launches of stages s0..s1 of one group.
+// Time stages s0..s1 of one group (s0 < 0: only the diagnostics' two y
+// transforms, which write scratch only).
 static int time_stages_of(ptt_ctx* c, const GroupDev& d, int s0, int s1, int reps, float* ms) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   auto run = [&]() -> cudaError_t {
+    if (s0 < 0) return (d.nz > 1) ? launch_diag_transforms3(d, c->stream) : launch_diag_transforms(d, c->stream);
     for (int s = s0; s <= s1; ++s) {
       cudaError_t e = (d.nz > 1) ? launch_stage3(d, s, c->stream, nullptr) : launch_stage(d, s, c->stream, nullptr);
       if (e) return e;
@@ -1218,6 +1221,25 @@ int ptt_autotune(ptt_ctx* c, int32_t* choices, int32_t max_groups) {
         if (ms < bt) { bt = ms; best = C; }
       }
       d.Ccol = best;
+    }
+    // columns per block of the diagnostics' y transforms (energy grid, then
+    // unpadded grid); only those two launches run, so records and
+    // histograms are untouched
+    for (int which = 0; which < 2; ++which) {
+      const int cand[] = {1, 2, 4, 6, 8, 12, 16};
+      int& cc = which == 0 ? d.CcolE : d.CcolU;
+      const int P = which == 0 ? d.Me : d.Pu;
+      int best = cc;
+      float bt = 1e30f;
+      for (int C : cand) {
+        if (smem_ycols(C, P, 0) > (size_t)optin) continue;
+        cc = C;
+        float ms = 0;
+        int s = time_stages_of(c, d, -1, -1, reps, &ms);
+        if (s) return s;
+        if (ms < bt) { bt = ms; best = C; }
+      }
+      cc = best;
     }
     if (d3) {
       const int cand[] = {1, 2, 4, 8, 16};

@@ -926,6 +926,9 @@ struct XJob {
   int nf;                    // fields (packed in pairs, (nf + 1) / 2 lines)
   int K, n;
   int c2r;
+  // c2r with nf = 1: block r synthesises rows 2r and 2r + 1 (< nrows) as the
+  // real and imaginary parts of one line (grid over ceil(nrows / 2) rows)
+  int pair_rows, nrows;
   const int* status;
   FftPlan pl;
 };
@@ -940,7 +943,13 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
   double2* Bb = sm + (size_t)nl * n;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (J.c2r) {
-    const double2* src = J.srcC + b * J.src_mstride + (long long)row * J.src_rstep * K;
+    // paired rows: the second line's source and destination are the next row
+    const bool pr = J.pair_rows != 0;
+    const int r0 = pr ? 2 * row : row;
+    const int nfe = pr ? ((r0 + 1 < J.nrows) ? 2 : 1) : nf;
+    const long long sfs = pr ? (long long)J.src_rstep * K : J.src_fstride;
+    const long long dfs = pr ? (long long)J.dst_rstep * n : J.dst_fstride;
+    const double2* src = J.srcC + b * J.src_mstride + (long long)r0 * J.src_rstep * K;
     for (int i = tid; i < nl * n; i += nt) {
       const int l = (int)fdiv((unsigned)i, fast_div((unsigned)n)), k = i - l * n;
       const int fa = 2 * l, fb = 2 * l + 1;
@@ -950,8 +959,8 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
       else if (k > n - K) { kk = n - k; cj = true; }
       double2 h = czero();
       if (kk >= 0) {
-        double2 F = src[fa * J.src_fstride + kk];
-        double2 G = (fb < nf) ? src[fb * J.src_fstride + kk] : czero();
+        double2 F = src[fa * sfs + kk];
+        double2 G = (fb < nfe) ? src[fb * sfs + kk] : czero();
         if (kk == 0) { F.y = 0.0; G.y = 0.0; }
         if (cj) { F = cconj(F); G = cconj(G); }
         h = cadd(F, mul_i(G));
@@ -960,12 +969,12 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
     }
     __syncthreads();
     double2* res = fft_lines<+1>(A, Bb, nl, n, J.pl);
-    double* dst = J.dstR + b * J.dst_mstride + (long long)row * J.dst_rstep * n;
+    double* dst = J.dstR + b * J.dst_mstride + (long long)r0 * J.dst_rstep * n;
     for (int i = tid; i < nl * n; i += nt) {
       const int l = (int)fdiv((unsigned)i, fast_div((unsigned)n)), x = i - l * n;
       const double2 h = res[i];
-      dst[(2 * l) * J.dst_fstride + x] = h.x;
-      if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + x] = h.y;
+      dst[(2 * l) * dfs + x] = h.x;
+      if (2 * l + 1 < nfe) dst[(2 * l + 1) * dfs + x] = h.y;
     }
   } else {
     const double* src = J.srcR + b * J.src_mstride + (long long)row * J.src_rstep * n;

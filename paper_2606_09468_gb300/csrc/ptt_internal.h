@@ -132,6 +132,9 @@ struct DiagStreams {
   cudaEvent_t ev[3];
 };
 cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nlaunch);
+// Only the diagnostics' two y transforms (energy grid, unpadded grid); they
+// write scratch only (for launch-shape timing).
+cudaError_t launch_diag_transforms(const GroupDev& g, cudaStream_t st);
 cudaError_t launch_explicit(const GroupDev& g, cudaStream_t st);
 // physical staging [5][N][nx] -> state of member b (resets counter/status)
 cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st);
@@ -148,6 +151,7 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
 cudaError_t launch_step3(const GroupDev& g, cudaStream_t st, int* nlaunch);
 cudaError_t launch_diag3(const GroupDev& g, cudaStream_t st, int* nlaunch);
 cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nlaunch);
+cudaError_t launch_diag_transforms3(const GroupDev& g, cudaStream_t st);
 cudaError_t launch_explicit3(const GroupDev& g, cudaStream_t st);
 cudaError_t launch_phys_to_state3(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st);

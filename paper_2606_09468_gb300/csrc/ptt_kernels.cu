@@ -823,33 +823,51 @@ static cudaError_t diag_join(const DiagStreams& d) {
   return e;
 }
 
-cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nl) {
+// The diagnostics' y transforms (they write only DY, DT): u, v on the Me
+// Gauss points of the energy quadrature; c_xx + c_yy on the unpadded
+// Gauss-Lobatto rows (DCT-I).
+static void diag_energy_y(const GroupDev& g, cudaStream_t st) {
   const size_t NK = (size_t)g.N * g.K;
-  cudaError_t e = diag_fork(d);
-  if (e) return e;
-  // energy: u, v on the Me Gauss points of the energy quadrature
   YJob J = make_yjob(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
   J.src = g.X; J.dst = g.DY;
   J.src_mstride = 5 * NK; J.dst_mstride = 2LL * g.Me * g.K;
   J.src_fstride = NK; J.dst_fstride = (long long)g.Me * g.K;
   for (int i = 0; i < 2; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), d.s[1]>>>(J);
-  // mid-plane sums per Fourier mode
-  k_diag_mid<<<dim3(cdiv(g.K, 8), g.nb), 256, 0, d.s[2]>>>(g);
-  // Tr c: c_xx + c_yy on the unpadded Gauss-Lobatto rows (DCT-I), then x
+  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
+}
+static void diag_trc_y(const GroupDev& g, cudaStream_t st) {
+  const size_t NK = (size_t)g.N * g.K;
   YJob T = make_yjob(g, true, g.N - 1, g.CcolU, g.plPu);
   T.src = g.X; T.dst = g.DT;
   T.src_mstride = 5 * NK; T.dst_mstride = (long long)NK;
   T.src_fstride = NK; T.dst_fstride = 0;
   T.src_field[0] = 2; T.src_field2[0] = 4; T.dst_field[0] = 0; T.deriv[0] = 0;
-  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), d.s[0]>>>(T);
+  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+}
+
+cudaError_t launch_diag_transforms(const GroupDev& g, cudaStream_t st) {
+  diag_energy_y(g, st);
+  diag_trc_y(g, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nl) {
+  const size_t NK = (size_t)g.N * g.K;
+  cudaError_t e = diag_fork(d);
+  if (e) return e;
+  diag_energy_y(g, d.s[1]);
+  // mid-plane sums per Fourier mode
+  k_diag_mid<<<dim3(cdiv(g.K, 8), g.nb), 256, 0, d.s[2]>>>(g);
+  // Tr c on the unpadded grid: y, then x
+  diag_trc_y(g, d.s[0]);
   XJob X{};
   X.srcC = g.DT; X.dstR = g.DV;
   X.src_mstride = (long long)NK; X.dst_mstride = (long long)g.N * g.nx;
   X.src_fstride = 0; X.dst_fstride = 0;
   X.src_rstep = 1; X.dst_rstep = 1;
   X.nf = 1; X.K = g.K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
-  k_xrows<<<dim3(g.N, g.nb), 256, smem_xrows(1, g.nx), d.s[0]>>>(X);
+  X.pair_rows = 1; X.nrows = g.N;
+  k_xrows<<<dim3(cdiv(g.N, 2), g.nb), 256, smem_xrows(1, g.nx), d.s[0]>>>(X);
   if ((e = cudaGetLastError()) || (e = diag_join(d))) return e;
   k_diag_part<<<dim3(g.ntile, g.nb), 256, 0, d.s[0]>>>(g);
   k_diag_count<<<dim3(g.ntile, g.nb), 256, 0, d.s[0]>>>(g);

@@ -886,18 +886,41 @@ static cudaError_t diag_join3(const DiagStreams& d) {
   return e;
 }
 
-cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl) {
-  const int KZ = g.KZ, K = g.K;
+// The diagnostics' y transforms (they write only DY, DT): u, v, w on the Me
+// Gauss points; c_xx + c_yy + c_zz on the unpadded Gauss-Lobatto rows.
+static void diag_energy_y3(const GroupDev& g, cudaStream_t st) {
+  const int KZ = g.KZ;
   const size_t NK = (size_t)g.N * KZ;
-  cudaError_t e = diag_fork3(d);
-  if (e) return e;
-  // energy: u, v, w on the Me Gauss points
   YJob J = yjob3(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
   J.src = g.X; J.dst = g.DY;
   J.src_mstride = 9 * NK; J.dst_mstride = 3LL * g.Me * KZ;
   J.src_fstride = NK; J.dst_fstride = (long long)g.Me * KZ;
   for (int i = 0; i < 3; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), d.s[1]>>>(J);
+  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
+}
+static void diag_trc_y3(const GroupDev& g, cudaStream_t st) {
+  const int KZ = g.KZ;
+  const size_t NK = (size_t)g.N * KZ;
+  YJob T = yjob3(g, true, g.N - 1, g.CcolU, g.plPu, nullptr);
+  T.src = g.X; T.dst = g.DT;
+  T.src_mstride = 9 * NK; T.dst_mstride = (long long)NK;
+  T.src_fstride = NK; T.dst_fstride = 0;
+  T.src_field[0] = 3; T.src_field2[0] = 6; T.src_field3[0] = 8; T.dst_field[0] = 0; T.deriv[0] = 0;
+  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+}
+
+cudaError_t launch_diag_transforms3(const GroupDev& g, cudaStream_t st) {
+  diag_energy_y3(g, st);
+  diag_trc_y3(g, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl) {
+  const int KZ = g.KZ, K = g.K;
+  const size_t NK = (size_t)g.N * KZ;
+  cudaError_t e = diag_fork3(d);
+  if (e) return e;
+  diag_energy_y3(g, d.s[1]);
   // mid-plane: per-mode sums, then z and x syntheses of the 8 quantities
   k_diag_mid3<<<dim3(cdiv(KZ, 8), g.nb), 256, 0, d.s[2]>>>(g);
   ZJob Zm = zjob(g, true, g.nz, 1, g.plNz);
@@ -914,12 +937,7 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   Xm.nf = 8; Xm.K = K; Xm.n = g.nx; Xm.c2r = 1; Xm.status = g.status; Xm.pl = g.plNx;
   k_xrows<<<dim3(g.nz, g.nb), 256, smem_xrows(4, g.nx), d.s[2]>>>(Xm);
   // Tr c = c_xx + c_yy + c_zz on the unpadded grid: y (Gauss-Lobatto) -> z -> x
-  YJob T = yjob3(g, true, g.N - 1, g.CcolU, g.plPu, nullptr);
-  T.src = g.X; T.dst = g.DT;
-  T.src_mstride = 9 * NK; T.dst_mstride = (long long)NK;
-  T.src_fstride = NK; T.dst_fstride = 0;
-  T.src_field[0] = 3; T.src_field2[0] = 6; T.src_field3[0] = 8; T.dst_field[0] = 0; T.deriv[0] = 0;
-  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), d.s[0]>>>(T);
+  diag_trc_y3(g, d.s[0]);
   ZJob Z = zjob(g, true, g.nz, g.N, g.plNz);
   Z.src = g.DT; Z.src_f32 = 0; Z.dst = g.DZ; Z.dst_f32 = 0;
   Z.src_mstride = (long long)NK; Z.dst_mstride = (long long)g.N * g.nz * K;
@@ -932,7 +950,8 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   X.src_fstride = 0; X.dst_fstride = 0;
   X.src_rstep = 1; X.dst_rstep = 1;
   X.nf = 1; X.K = K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
-  k_xrows<<<dim3(g.N * g.nz, g.nb), 256, smem_xrows(1, g.nx), d.s[0]>>>(X);
+  X.pair_rows = 1; X.nrows = g.N * g.nz;
+  k_xrows<<<dim3(cdiv(g.N * g.nz, 2), g.nb), 256, smem_xrows(1, g.nx), d.s[0]>>>(X);
   if ((e = cudaGetLastError()) || (e = diag_join3(d))) return e;
   k_diag_part3<<<dim3(g.ntile, g.nb), 256, 0, d.s[0]>>>(g);
   k_diag_count3<<<dim3(g.ntile, g.nb), 256, 0, d.s[0]>>>(g);
