@@ -312,39 +312,38 @@ __global__ void __launch_bounds__(256) k_spec3(GroupDev g, int mode) {
     if (d) lane_cheb_deriv(SC(S3_DV), SC(S3_D2V), N, p);
   }
   __syncthreads();
-  // phase 2: H (warps 0-2), evolved q1, q2 (warps 3, 4)
+  // Element-wise phases split the lane's column over the eight warps: warp w
+  // takes elements [w c8, (w + 1) c8) of its lane's parity (n = p + 2 i), so
+  // every warp keeps loads in flight (one warp per column waited on each
+  // element in turn).
+  const int Lp = (N - p + 1) / 2;
+  const int c8 = (Lp + 7) / 8;
+  const int e0 = min(Lp, warp * c8), e1 = min(Lp, e0 + c8);
+  // phase 2: H (all three components), evolved q1, q2
   if (act) {
-    if (warp < 3) {
-      // (div c)_i = i kx c_xi + D c_yi + i kz c_zi
-      const int cx = (warp == 0) ? 3 : (warp == 1) ? 4 : 5;     // c_xx, c_xy, c_xz
-      const int cz = (warp == 0) ? 5 : (warp == 1) ? 7 : 8;     // c_xz, c_yz, c_zz
-      const double2* __restrict__ cxv = X + (size_t)cx * NK;
-      const double2* __restrict__ czv = X + (size_t)cz * NK;
-      const double2* __restrict__ dcy = SC(S3_DCXY + warp);
-      const double2* __restrict__ nu = NR + (size_t)(6 + warp) * NK;
-      double2* __restrict__ H = SC(S3_HX + warp);
-      const double fx = (warp == 0 && mean) ? pr.forcing : 0.0;
-#pragma unroll 4
-      for (int n = p; n < N; n += 2) {
-        const double2 dv = cadd(cscl(mul_i(cxv[n]), kx), cadd(dcy[n], cscl(mul_i(czv[n]), kz)));
-        double2 h = cfma(gam, dv, nu[n]);
-        if (n == 0) h.x += fx;
-        H[n] = h;
+    const double2* __restrict__ Xc = X;
+    const double2* __restrict__ Sd = S;
+    double2* __restrict__ Sw = S;
+    const double fx = mean ? pr.forcing : 0.0;
+    for (int i = e0; i < e1; ++i) {
+      const int n = p + 2 * i;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        // (div c)_i = i kx c_xi + D c_yi + i kz c_zi
+        const int cx = (t == 0) ? 3 : (t == 1) ? 4 : 5;     // c_xx, c_xy, c_xz
+        const int cz = (t == 0) ? 5 : (t == 1) ? 7 : 8;     // c_xz, c_yz, c_zz
+        const double2 dv = cadd(cscl(mul_i(Xc[(size_t)cx * NK + n]), kx),
+                                cadd(Sd[(size_t)(S3_DCXY + t) * NK + n],
+                                     cscl(mul_i(Xc[(size_t)cz * NK + n]), kz)));
+        double2 h = cfma(gam, dv, NR[(size_t)(6 + t) * NK + n]);
+        if (t == 0 && n == 0) h.x += fx;
+        Sw[(size_t)(S3_HX + t) * NK + n] = h;
       }
-    } else if (warp == 3 && mode == 0) {
-      double2* __restrict__ q = SC(S3_Q1);
-      const double2* __restrict__ d2v = SC(S3_D2V);
-      const double2* __restrict__ u = X;
-      const double2* __restrict__ v = X + NK;
-#pragma unroll 4
-      for (int n = p; n < N; n += 2) q[n] = mean ? u[n] : cfma(-k2, v[n], d2v[n]);
-    } else if (warp == 4 && mode == 0) {
-      double2* __restrict__ q = SC(S3_Q2);
-      const double2* __restrict__ u = X;
-      const double2* __restrict__ w = X + 2 * NK;
-#pragma unroll 4
-      for (int n = p; n < N; n += 2)
-        q[n] = mean ? w[n] : csub(cscl(mul_i(u[n]), kz), cscl(mul_i(w[n]), kx));
+      if (mode == 0) {
+        Sw[(size_t)S3_Q1 * NK + n] = mean ? Xc[n] : cfma(-k2, Xc[NK + n], Sd[(size_t)S3_D2V * NK + n]);
+        Sw[(size_t)S3_Q2 * NK + n] =
+            mean ? Xc[2 * NK + n] : csub(cscl(mul_i(Xc[n]), kz), cscl(mul_i(Xc[2 * NK + n]), kx));
+      }
     }
   }
   __syncthreads();
@@ -356,27 +355,30 @@ __global__ void __launch_bounds__(256) k_spec3(GroupDev g, int mode) {
     }
     return;
   }
-  // phase 3: forcings of q1 (warp 0), q2 (warp 1)
-  if (warp == 0) {
-    const bool d = act && !mean;
-    const double2* Hx = SC(S3_HX);
-    const double2* Hy = SC(S3_HY);
-    const double2* Hz = SC(S3_HZ);
-    double2* t = SC(S3_F1T);
-    double2* f = SC(S3_F1);
-    if (d)
-      for (int n = p; n < N; n += 2) t[n] = cadd(cscl(mul_i(Hx[n]), kx), cscl(mul_i(Hz[n]), kz));
-    __syncwarp();
-    if (d) lane_cheb_deriv(t, f, N, p);
-    __syncwarp();
+  // phase 3: forcings of q1 = -D(i kx H_x + i kz H_z) - k^2 H_y and of
+  // q2 = i kz H_x - i kx H_z (mean mode: H_x, H_z): the element-wise parts
+  // over all warps, the derivative on warp 0
+  {
+    const double2* __restrict__ Hx = SC(S3_HX);
+    const double2* __restrict__ Hy = SC(S3_HY);
+    const double2* __restrict__ Hz = SC(S3_HZ);
+    double2* __restrict__ t = SC(S3_F1T);
+    double2* __restrict__ f2 = SC(S3_F2);
     if (act)
-      for (int n = p; n < N; n += 2) f[n] = mean ? Hx[n] : csub(cscl(f[n], -1.0), cscl(Hy[n], k2));
-  } else if (warp == 1 && act) {
-    const double2* Hx = SC(S3_HX);
-    const double2* Hz = SC(S3_HZ);
-    double2* f = SC(S3_F2);
-    for (int n = p; n < N; n += 2)
-      f[n] = mean ? Hz[n] : csub(cscl(mul_i(Hx[n]), kz), cscl(mul_i(Hz[n]), kx));
+      for (int i = e0; i < e1; ++i) {
+        const int n = p + 2 * i;
+        if (!mean) t[n] = cadd(cscl(mul_i(Hx[n]), kx), cscl(mul_i(Hz[n]), kz));
+        f2[n] = mean ? Hz[n] : csub(cscl(mul_i(Hx[n]), kz), cscl(mul_i(Hz[n]), kx));
+      }
+    __syncthreads();
+    if (warp == 0 && act && !mean) lane_cheb_deriv(SC(S3_F1T), SC(S3_F1), N, p);
+    __syncthreads();
+    double2* __restrict__ f = SC(S3_F1);
+    if (act)
+      for (int i = e0; i < e1; ++i) {
+        const int n = p + 2 * i;
+        f[n] = mean ? Hx[n] : csub(cscl(f[n], -1.0), cscl(Hy[n], k2));
+      }
   }
   __syncthreads();
   // phase 4: history slot and SBDF sums, warp s for evolved quantity s
@@ -443,19 +445,21 @@ __global__ void __launch_bounds__(256) k_spec3(GroupDev g, int mode) {
     }
   }
   __syncthreads();
-  // phase 6: u, w from D v and eta (k != 0)
-  if (warp == 0) {
-    const bool d = act && !mean;
-    double2* dv = SC(S3_DVN);
-    if (d) lane_cheb_deriv(X + NK, dv, N, p);
-    __syncwarp();
-    if (d) {
-      const double2* et = SC(S3_ETA);
-      const double ik2 = 1.0 / k2;
-      for (int n = p; n < N; n += 2) {
-        X[n] = cscl(mul_i(csub(cscl(dv[n], kx), cscl(et[n], kz))), ik2);
-        X[2 * NK + n] = cscl(mul_i(cadd(cscl(dv[n], kz), cscl(et[n], kx))), ik2);
-      }
+  // phase 6: u, w from D v and eta (k != 0): the derivative on warp 0, the
+  // element-wise part over all warps
+  const bool dvw = act && !mean;
+  if (warp == 0 && dvw) lane_cheb_deriv(X + NK, SC(S3_DVN), N, p);
+  __syncthreads();
+  if (dvw) {
+    const double2* __restrict__ dv = SC(S3_DVN);
+    const double2* __restrict__ et = SC(S3_ETA);
+    double2* __restrict__ u = X;
+    double2* __restrict__ w = X + 2 * NK;
+    const double ik2 = 1.0 / k2;
+    for (int i = e0; i < e1; ++i) {
+      const int n = p + 2 * i;
+      u[n] = cscl(mul_i(csub(cscl(dv[n], kx), cscl(et[n], kz))), ik2);
+      w[n] = cscl(mul_i(cadd(cscl(dv[n], kz), cscl(et[n], kx))), ik2);
     }
   }
 }
