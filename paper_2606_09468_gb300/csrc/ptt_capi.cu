@@ -1121,17 +1121,25 @@ int ptt_diagnostics(ptt_ctx* c, int32_t member, ptt_diag* out, int32_t maxr, int
   *nw = 0;
   auto [gi, b] = c->where[member];
   Group& g = c->groups[gi];
-  CK(cudaStreamSynchronize(c->stream));
   long long cnt = 0;
-  CK(cudaMemcpy(&cnt, g.d.count + b, sizeof(long long), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&cnt, g.d.count + b, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   long long first = c->last_read[member] + 1;
   if (first < cnt - kRing + 1) first = cnt - kRing + 1;
   if (first < 0) first = 0;
-  int n = 0;
-  for (long long s = first; s <= cnt && n < maxr; ++s, ++n) {
-    CK(cudaMemcpy(out + n, g.d.ring + (size_t)b * kRing + (size_t)(s % kRing), sizeof(ptt_diag),
-                  cudaMemcpyDeviceToHost));
-  }
+  const long long avail = cnt - first + 1;
+  const int n = (int)(avail < maxr ? (avail > 0 ? avail : 0) : maxr);
+  // records first .. first + n - 1 sit in ring slots s mod kRing: at most two
+  // contiguous pieces
+  const ptt_diag* ring = g.d.ring + (size_t)b * kRing;
+  const int s0 = (int)(first % kRing);
+  const int n1 = std::min(n, kRing - s0);
+  if (n1 > 0)
+    CK(cudaMemcpyAsync(out, ring + s0, (size_t)n1 * sizeof(ptt_diag), cudaMemcpyDeviceToHost, c->stream));
+  if (n > n1)
+    CK(cudaMemcpyAsync(out + n1, ring, (size_t)(n - n1) * sizeof(ptt_diag), cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   if (n > 0) c->last_read[member] = first + n - 1;
   *nw = n;
   return PTT_OK;
@@ -1303,6 +1311,9 @@ int ptt_checkpoint_size(ptt_ctx* c, int32_t member, size_t* bytes) {
   return PTT_OK;
 }
 
+// Checkpoint copies: one cudaMemcpyAsync per array on the context stream
+// (ordered after the steps already launched), then one synchronisation, so
+// the calls return with the copies done, as their contract states.
 int ptt_get_checkpoint(ptt_ctx* c, int32_t member, void* h, size_t bytes) {
   if (!member_ok(c, member) || !h) return PTT_EINVAL;
   auto [gi, b] = c->where[member];
@@ -1311,24 +1322,23 @@ int ptt_get_checkpoint(ptt_ctx* c, int32_t member, void* h, size_t bytes) {
   const size_t NK = (size_t)g.d.N * g.d.KZ, nb = g.d.nb;
   const size_t nf = (g.d.nz > 1) ? 9 : 5, ne = (g.d.nz > 1) ? 8 : 4;
   char* p = (char*)h;
-  CK(cudaStreamSynchronize(c->stream));
-  int64_t hdr[8] = {0x70747463, g.d.nx, g.d.N, 0, 0, g.d.nz, 0, 0};
-  long long cnt;
-  int st;
-  CK(cudaMemcpy(&cnt, g.d.count + b, 8, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&st, g.d.status + b, 4, cudaMemcpyDeviceToHost));
-  hdr[3] = cnt;
-  hdr[4] = st;
-  std::memcpy(p, hdr, 64);
-  p += 64;
-  CK(cudaMemcpy(p, g.d.X + b * nf * NK, nf * NK * 16, cudaMemcpyDeviceToHost));
-  p += nf * NK * 16;
-  for (int s = 0; s < 4; ++s) {
-    CK(cudaMemcpy(p, g.d.Eh + ((size_t)s * nb + b) * ne * NK, ne * NK * 16, cudaMemcpyDeviceToHost));
-    p += ne * NK * 16;
-    CK(cudaMemcpy(p, g.d.Nh + ((size_t)s * nb + b) * ne * NK, ne * NK * 16, cudaMemcpyDeviceToHost));
-    p += ne * NK * 16;
+  long long cnt = 0;
+  int st = 0;
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(&cnt, g.d.count + b, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&st, g.d.status + b, 4, cudaMemcpyDeviceToHost, s));
+  char* q = p + 64;
+  CK(cudaMemcpyAsync(q, g.d.X + b * nf * NK, nf * NK * 16, cudaMemcpyDeviceToHost, s));
+  q += nf * NK * 16;
+  for (int k = 0; k < 4; ++k) {
+    CK(cudaMemcpyAsync(q, g.d.Eh + ((size_t)k * nb + b) * ne * NK, ne * NK * 16, cudaMemcpyDeviceToHost, s));
+    q += ne * NK * 16;
+    CK(cudaMemcpyAsync(q, g.d.Nh + ((size_t)k * nb + b) * ne * NK, ne * NK * 16, cudaMemcpyDeviceToHost, s));
+    q += ne * NK * 16;
   }
+  CK(cudaStreamSynchronize(s));
+  int64_t hdr[8] = {0x70747463, g.d.nx, g.d.N, cnt, st, g.d.nz, 0, 0};
+  std::memcpy(p, hdr, 64);
   return PTT_OK;
 }
 
@@ -1344,19 +1354,22 @@ int ptt_set_checkpoint(ptt_ctx* c, int32_t member, const void* h, size_t bytes) 
   std::memcpy(hdr, p, 64);
   if (hdr[0] != 0x70747463 || hdr[1] != g.d.nx || hdr[2] != g.d.N || hdr[5] != g.d.nz) return PTT_EINVAL;
   p += 64;
-  CK(cudaStreamSynchronize(c->stream));
-  long long cnt = hdr[3];
-  int st = (int)hdr[4];
-  CK(cudaMemcpy(g.d.count + b, &cnt, 8, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(g.d.status + b, &st, 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(g.d.X + b * nf * NK, p, nf * NK * 16, cudaMemcpyHostToDevice));
+  const long long cnt = hdr[3];
+  const int st = (int)hdr[4];
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(g.d.count + b, &cnt, 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g.d.status + b, &st, 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g.d.X + b * nf * NK, p, nf * NK * 16, cudaMemcpyHostToDevice, s));
   p += nf * NK * 16;
-  for (int s = 0; s < 4; ++s) {
-    CK(cudaMemcpy(g.d.Eh + ((size_t)s * nb + b) * ne * NK, p, ne * NK * 16, cudaMemcpyHostToDevice));
+  for (int k = 0; k < 4; ++k) {
+    CK(cudaMemcpyAsync(g.d.Eh + ((size_t)k * nb + b) * ne * NK, p, ne * NK * 16, cudaMemcpyHostToDevice, s));
     p += ne * NK * 16;
-    CK(cudaMemcpy(g.d.Nh + ((size_t)s * nb + b) * ne * NK, p, ne * NK * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(g.d.Nh + ((size_t)k * nb + b) * ne * NK, p, ne * NK * 16, cudaMemcpyHostToDevice, s));
     p += ne * NK * 16;
   }
+  // the sources (cnt, st on this stack frame; the caller's buffer) must stay
+  // valid until the copies have run
+  CK(cudaStreamSynchronize(s));
   c->last_read[member] = cnt;
   return PTT_OK;
 }
