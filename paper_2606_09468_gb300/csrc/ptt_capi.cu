@@ -690,10 +690,8 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
   return PTT_OK;
 }
 
-// Capture one step of every group (step + diagnostics) as one CUDA graph:
-// a fork per group from the capture stream, a join back (replaces an
-// existing graph).
-// The step as CUDA graphs, one branch per shape group.  The diagnostics of a
+// The step as CUDA graphs, one branch per shape group (a fork per group from
+// the capture stream, a join back; re-capturing replaces existing graphs).  The diagnostics of a
 // state only read it (and write their own buffers), and only the spectral
 // stage of the next step overwrites it, so they run beside the next step's
 // transforms (stages 0-2) on a second branch per group that the spectral

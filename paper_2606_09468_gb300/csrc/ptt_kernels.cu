@@ -735,7 +735,7 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
   if ((e = optin(k_xrows, optin_bytes))) return e;
   if ((e = optin(k_spec<2>, optin_bytes))) return e;
   if ((e = optin(k_spec<4>, optin_bytes))) return e;
-  if ((e = optin(k_spec<8>, optin_bytes))) return e;
+  if ((e = optin(k_spec<kMaxChunk>, optin_bytes))) return e;
   if ((e = optin(k_diag_final, optin_bytes))) return e;
   return cudaSuccess;
 }
@@ -748,7 +748,7 @@ static void launch_spec(const GroupDev& g, int mode, cudaStream_t st) {
   const size_t sm = smem_spec(g.N);
   if (rows <= 2) k_spec<2><<<grid, 256, sm, st>>>(g, mode);
   else if (rows <= 4) k_spec<4><<<grid, 256, sm, st>>>(g, mode);
-  else k_spec<8><<<grid, 256, sm, st>>>(g, mode);
+  else k_spec<kMaxChunk><<<grid, 256, sm, st>>>(g, mode);
 }
 
 // Stage s of one step for one group (see ptt.h: PTT_NSTAGES).
