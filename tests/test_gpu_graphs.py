@@ -97,3 +97,27 @@ def test_step_n_equals_n_single_steps(shape):
     assert len(blown) == 1 and 1 <= blown[0] < STEPS, [(r["step"], r["status"]) for r in d0]
     assert d0[-1]["step"] == blown[0]
     assert d1[-1]["step"] == STEPS and all(r["status"] == P.PTT_OK for r in d1)
+
+
+def test_diagnostics_ring_reads_across_the_wrap():
+    """Records live in a ring of 1024 per run; a read that crosses the ring's
+    end comes back in step order, max_records caps a read, and a backlog
+    longer than the ring returns its newest 1024 records."""
+    import paper_2606_09468_gb300 as P
+    ctx = P.Context(_params((32, 33, 1)))
+    ctx.init_state(0, 1, I.AMPLITUDE)
+    ctx.init_state(1, 2, I.AMPLITUDE)
+    ctx.step(1000)
+    ctx.synchronize()
+    r = ctx.diagnostics(0)
+    assert [x["step"] for x in r] == list(range(0, 1001))
+    ctx.step(100)                                  # steps 1001 .. 1100: slots 1001 .. 1023, 0 .. 76
+    r = ctx.diagnostics(0, 30)
+    assert [x["step"] for x in r] == list(range(1001, 1031))
+    r = ctx.diagnostics(0)
+    assert [x["step"] for x in r] == list(range(1031, 1101))
+    assert all(x["status"] == P.PTT_OK for x in r)
+    # run 1 was not read since step 0: only the newest 1024 records remain
+    r1 = ctx.diagnostics(1)
+    assert [x["step"] for x in r1] == list(range(1100 - 1023, 1101))
+    ctx.close()
