@@ -106,7 +106,7 @@ typedef struct {
   int32_t reserved;
 } ptt_diag;
 
-typedef struct ptt_ctx ptt_ctx; /* opaque: host metadata, CUDA graph, no data */
+typedef struct ptt_ctx ptt_ctx; /* opaque: host metadata and the step graphs, no data */
 
 /* Bytes of device workspace needed by nmembers members with these params
  * (one params struct per member).  Returns PTT_EINVAL / PTT_ENOTSUP for
