@@ -272,21 +272,59 @@ __device__ __forceinline__ void fft_pass_tan(const double2* __restrict__ src, do
   }
 }
 
+// First pass of radix 3 (no twiddles) for lines that are zero in their
+// middle third [n/3, 2n/3) -- the inverse transforms of spectra padded to
+// n >= 3K points for K kept modes: with v1 = 0 the butterfly is
+// y0 = v0 + v2, y1,2 = v0 - v2/2 -+ DIR sin(2 pi/3) i v2 (8 operations).
+template <int DIR, typename C2>
+__device__ __forceinline__ void fft_pass_r3_zmid(const C2* __restrict__ src, C2* __restrict__ dst,
+                                                 int nl, int ls, int n) {
+  using T = typename RealOf<C2>::T;
+  const int nb = n / 3;
+  const int total = nl * nb;
+  const FastDiv dnb = fast_div((unsigned)nb);
+  const T sn = (T)(DIR * 0.86602540378443864676);  // sin(2 pi / 3), signed
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int l = (int)fdiv((unsigned)t, dnb);
+    const int j = t - l * nb;
+    const C2 v0 = src[l * ls + j], v2 = src[l * ls + j + 2 * nb];
+    C2 m, y1, y2;
+    m.x = fma((T)-0.5, v2.x, v0.x);
+    m.y = fma((T)-0.5, v2.y, v0.y);
+    y1.x = fma(sn, v2.y, m.x);
+    y1.y = fma(-sn, v2.x, m.y);
+    y2.x = fma(-sn, v2.y, m.x);
+    y2.y = fma(sn, v2.x, m.y);
+    C2* d = dst + l * ls + 3 * j;
+    d[0] = cadd(v0, v2);
+    d[1] = y1;
+    d[2] = y2;
+  }
+}
+
 template <typename C2> __device__ __forceinline__ const C2* plan_tw(const FftPlan& pl);
 template <> __device__ __forceinline__ const double2* plan_tw<double2>(const FftPlan& pl) { return pl.tw; }
 template <> __device__ __forceinline__ const float2* plan_tw<float2>(const FftPlan& pl) { return pl.twf; }
 
 // Unnormalised DFT of nl lines of length pl.n held in `a`, using `b` as the
 // ping-pong buffer.  Returns the buffer holding the result.  Must be called
-// by the whole block after a __syncthreads(); ends with one.
+// by the whole block after a __syncthreads(); ends with one.  zero_mid: the
+// lines are zero in their middle third and the plan starts with radix 3.
 template <int DIR, typename C2>
-__device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl) {
+__device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl, bool zero_mid = false) {
   C2* src = a;
   C2* dst = b;
   const C2* tw = plan_tw<C2>(pl);
   int Ns = 1;
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.radix[s];
+    if (s == 0 && zero_mid && R == 3) {
+      fft_pass_r3_zmid<DIR>(src, dst, nl, ls, pl.n);
+      __syncthreads();
+      Ns = 3;
+      C2* t = src; src = dst; dst = t;
+      continue;
+    }
     if constexpr (std::is_same<C2, double2>::value) {
       if (pl.tt && s > 0) {
         const double* tt = pl.tt + pl.tto[s];

@@ -78,7 +78,9 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
     A[i] = h;
   }
   __syncthreads();
-  C2* res = fft_lines<+1>(A, B, 7, Mx, g.plMx);
+  // the padded modes K .. Mx - K are zero (plans of Mx start with radix 3
+  // when Mx has no factor 5)
+  C2* res = fft_lines<+1>(A, B, 7, Mx, g.plMx, g.plMx.radix[0] == 3);
   C2* oth = (res == A) ? B : A;
   const T eps = (T)pr.eps, iwi = (T)pr.inv_wi;
   for (int x = tid; x < Mx; x += nt) {

@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
       }
     }
     __syncthreads();
-    CT* res = fft_lines<+1>(A, B, C, Mz, J.pl);
+    // padded synthesis (Mz >= 3 nz/2): the slots nz/2 .. Mz - nz/2 are zero
+    CT* res = fft_lines<+1>(A, B, C, Mz, J.pl, J.pl.radix[0] == 3 && Mz >= 3 * hz);
     for (int i = tid; i < Mz * C; i += nt) {
       const int z = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - z * C;
       if (c < nc) st2<CT>(dst, (long long)z * K + m0 + c, J.dst_f32, res[c * Mz + z]);
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
     A[i] = h;
   }
   __syncthreads();
-  C2* res = fft_lines<+1>(A, B, 18, Mx, g.plMx);
+  C2* res = fft_lines<+1>(A, B, 18, Mx, g.plMx, g.plMx.radix[0] == 3);
   C2* oth = (res == A) ? B : A;
   const T eps = (T)pr.eps, iwi = (T)pr.inv_wi;
   for (int x = tid; x < Mx; x += nt) {
