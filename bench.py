@@ -46,7 +46,7 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); measure
 # DRAM read + write bytes per launch, averaged over the 9 shape groups, from
 # ncu counters of the current kernel source (profiles/k_xfused_2d_sweep_fp64.md);
 # reported as roofline.traffic when that kernel dominates.
-NCU_TRAFFIC_PER_LAUNCH = {"k_xfused": 16.23e6}
+NCU_TRAFFIC_PER_LAUNCH = {"k_xfused": 16.22e6}
 
 
 def parse():
