@@ -395,3 +395,41 @@ def test_initial_perturbation_is_solenoidal_no_slip_and_scaled():
     # laminar value 3 and u'(x, 0) has zero mean
     d = ch.diagnostics()
     assert abs(d["mid_sums"][1][0]) < 1e-15
+
+
+def test_diagnostics_closed_forms_on_a_constructed_field():
+    # u = (1 - y^2)(1 + A cos t) + G y, v = B (2 y^2 - 1) sin t, t = kx x;
+    # c = I + diag(f, 0) with f = 10 (y^2 - 0.31)(1 + cos(t)/2): exactly
+    # representable, no grid point on the tie bands of 3 or 0.
+    A, B, G = 0.3, 0.2, 0.15
+    ch = _ch(nx=16, ny=17)
+    kx = 2 * math.pi / ch.p.lx
+    x = np.arange(ch.p.nx) * ch.p.lx / ch.p.nx
+    y = np.cos(np.pi * np.arange(ch.N) / (ch.N - 1))
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    u = (1 - Y ** 2) * (1 + A * np.cos(kx * X)) + G * Y
+    v = B * (2 * Y ** 2 - 1) * np.sin(kx * X)
+    f = 10.0 * (Y ** 2 - 0.31) * (1 + 0.5 * np.cos(kx * X))
+    ch.set_physical([u, v, 1 + f, 0 * X, 0 * X + 1])
+    d = ch.diagnostics()
+    tr = 3.0 + f
+    assert d["n_lt3"] == int(np.sum(tr < 3.0)) > 0
+    assert d["n_lt0"] == int(np.sum(tr < 0.0)) > 0
+    assert d["n_band3"] == d["n_band0"] == 0
+    # volume averages (dy/2 on [-1, 1], uniform in x): <(1 - y^2)^2> = 8/15,
+    # <y^2> = 1/3, <(2 y^2 - 1)^2> = 7/15, <sin^2> = 1/2, odd terms vanish
+    e = 0.5 * (8.0 / 15.0 * (1 + A * A / 2) + G * G / 3.0 + B * B * 7.0 / 15.0 / 2.0)
+    assert abs(d["energy"] - e) <= 1e-14
+    assert abs(d["mean_trc"] - (3.0 + 10.0 * (1.0 / 3.0 - 0.31))) <= 1e-13
+    # mid-plane y = 0: Tr c, u' = A cos t, v = -B sin t, du/dx = -A kx sin t,
+    # dv/dx = -B kx cos t, du/dy = G
+    n = ch.p.nx
+    t = kx * x
+    q = [3.0 - 3.1 * (1 + 0.5 * np.cos(t)), A * np.cos(t), -B * np.sin(t), -A * kx * np.sin(t),
+         -B * kx * np.cos(t), np.full(n, G)]
+    want = np.array([[np.sum(qq ** k) for k in range(1, 5)] for qq in q])
+    assert np.all(np.abs(d["mid_sums"] - want) <= 1e-12 * np.maximum(np.abs(want), 1.0))
+    for j, s2 in ((1, A * A * n / 2), (2, B * B * n / 2), (3, (A * kx) ** 2 * n / 2),
+                  (4, (B * kx) ** 2 * n / 2), (5, G * G * n)):
+        assert abs(d["mid_sums"][j][1] - s2) <= 1e-12 * max(s2, 1.0)
+    assert d["n_mid_lt0"] == int(np.sum(q[0] < 0.0)) == 9
