@@ -155,6 +155,27 @@ class Clocks:
 CPU_SAMPLE = "one SBDF step (from the initial state) of one run of each of the 9 sweep shapes, seed 0"
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu's, else /proc/cpuinfo's, else the
+    machine type)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline():
     """The oracle, as it stands, timed on this machine's host cores in a
     subprocess with an explicit BLAS thread count."""
@@ -176,10 +197,10 @@ def cpu_baseline():
         "print(json.dumps({'points': pts, 'seconds': sec}))\n")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
-        return {"value": None, "unit": METRIC, "cores": cores, "kind": "oracle",
+        return {"value": None, "unit": METRIC, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                 "sample": CPU_SAMPLE, "error": r.stderr[-300:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["points"] / d["seconds"], "unit": METRIC, "cores": cores,
+    return {"value": d["points"] / d["seconds"], "unit": METRIC, "cores": cores, "cpu": cpu_model(),
             "kind": "oracle", "sample": CPU_SAMPLE, "seconds": round(d["seconds"], 3)}
 
 
@@ -214,7 +235,8 @@ def run_reference(args):
            "ms_per_step": 1e3 * sec / max(args.steps, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "parallelism": "host cores (oracle)"},
-           "cpu_baseline": {"value": val, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "cpu_baseline": {"value": val, "unit": METRIC, "cores": cores, "cpu": cpu_model(),
+                            "kind": "oracle",
                             "sample": "each step: one oracle SBDF step of one sweep run, "
                                       "cycling through the 9 shapes (seed 0)"},
            "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
