@@ -63,7 +63,7 @@ extern "C" {
 #define PTT_ENOMEM (-2)    /* workspace too small                                */
 #define PTT_ECUDA (-3)     /* a CUDA runtime call failed                         */
 #define PTT_TIMEOUT (-4)   /* a bounded wait expired                             */
-#define PTT_ENOTSUP (-5)   /* valid request this build does not implement        */
+#define PTT_ENOTSUP (-5)   /* valid request this library does not implement      */
 
 #define PTT_FP64 0         /* every step of the path in FP64                     */
 #define PTT_MIXED 1        /* FP32 transforms and products; FP64 state, SBDF sums,

@@ -1494,7 +1494,7 @@ const char* ptt_status_string(int s) {
     case PTT_ENOMEM: return "workspace too small";
     case PTT_ECUDA: return "CUDA runtime error";
     case PTT_TIMEOUT: return "bounded wait expired";
-    case PTT_ENOTSUP: return "not supported by this build";
+    case PTT_ENOTSUP: return "not supported by this library";
     default: return "unknown status";
   }
 }
