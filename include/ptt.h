@@ -173,9 +173,19 @@ int ptt_resample(ptt_ctx* dst, int32_t dst_member, ptt_ctx* src, int32_t src_mem
  * ptt_synchronize / ptt_diagnostics. */
 int ptt_step(ptt_ctx* ctx, int32_t nsteps);
 
-/* Wait for the context stream.  Returns PTT_BLOWUP if any member has blown
- * up, PTT_OK otherwise, or PTT_ECUDA. */
+/* Wait for the context stream, polling it (cudaStreamQuery) for at most the
+ * context's wall-clock limit (ptt_set_timeout; 3600 s unless set).  Returns
+ * PTT_BLOWUP if any member has blown up, PTT_OK otherwise, PTT_TIMEOUT if the
+ * limit passed with work still in flight (nothing is cancelled: the work
+ * goes on and a later call waits for it again), or PTT_ECUDA. */
 int ptt_synchronize(ptt_ctx* ctx);
+
+/* ptt_synchronize with an explicit limit of `seconds` (< 0: no limit; 0:
+ * PTT_TIMEOUT at once unless the stream is idle). */
+int ptt_synchronize_for(ptt_ctx* ctx, double seconds);
+
+/* Set the wall-clock limit of ptt_synchronize (seconds; <= 0: no limit). */
+int ptt_set_timeout(ptt_ctx* ctx, double seconds);
 
 /* Copy out the diagnostics records of `member` written since the previous
  * call (oldest first; at most max_records, the device ring keeps the last
@@ -199,6 +209,38 @@ int ptt_diagnostics(ptt_ctx* ctx, int32_t member, ptt_diag* h_out, int32_t max_r
 #define PTT_HIST_BINS 256
 int ptt_set_histograms(ptt_ctx* ctx, int32_t member, const double* lo, const double* hi);
 int ptt_get_histograms(ptt_ctx* ctx, int32_t member, int64_t* counts);
+
+/* Window statistics of the mid-plane quantities (Sec. 3: the paper judges
+ * runs by the moments and PDFs of the mid-plane Tr c, velocity fluctuations
+ * and velocity gradients over a time window).  Every diagnostics record
+ * written for a member (each step, and the record written by ptt_init_state
+ * / ptt_set_state / ptt_set_spectral / ptt_set_checkpoint) adds its power
+ * sums ptt_diag.mid_sums to the member's window accumulator on the device;
+ * ptt_reset_moments zeroes it (ptt_create starts it at zero).  The
+ * accumulator is not part of a checkpoint.
+ * ptt_midplane_moments computes on the device, in FP64, for each of the 8
+ * quantities q (order of ptt_diag.mid_sums), with n = nx nz records samples
+ * and raw moments m_p = S_p / n of the accumulated sums S_p:
+ *   moments[q][0] = mean m_1, moments[q][1] = standard deviation
+ *   sd = sqrt(m_2 - m_1^2), moments[q][2] = skewness
+ *   (m_3 - 3 m_1 m_2 + 2 m_1^3) / sd^3, moments[q][3] = kurtosis
+ *   (m_4 - 4 m_1 m_3 + 6 m_1^2 m_2 - 3 m_1^4) / sd^4
+ * (skewness and kurtosis 0 where sd = 0); moments is double[8][4], nrecords
+ * (may be NULL) receives the number of records in the window.  The raw-moment
+ * form loses relative accuracy in sd when sd is many orders of magnitude
+ * below |mean| (about 1e-16 |mean|^2 / sd^2).  Synchronous. */
+int ptt_reset_moments(ptt_ctx* ctx, int32_t member);
+int ptt_midplane_moments(ptt_ctx* ctx, int32_t member, double* moments, int64_t* nrecords);
+
+/* L1 distance between the mid-plane histograms of two members (of the same
+ * or different contexts on the current device), per quantity:
+ * l1[q] = sum over the PTT_HIST_BINS + 2 slots of |a_i / A - b_i / B|, A and
+ * B the total counts (0: identical PDFs, 2: disjoint; 0 if both are empty and
+ * 2 if only one is).  The two histograms should have been set with the same
+ * ranges (not checked).  Computed on the device in FP64 on ctx_a's stream
+ * after ctx_b's stream is idle; double[8].  Synchronous. */
+int ptt_histogram_l1(ptt_ctx* ctx_a, int32_t member_a, ptt_ctx* ctx_b, int32_t member_b,
+                     double* l1);
 
 /* Dealiased explicit right-hand side of the current state of one member
  * (Eq. 1 without kappa lap c; Eq. 2 without pressure and viscous terms) in
@@ -227,13 +269,17 @@ int ptt_explicit_rhs(ptt_ctx* ctx, int32_t member, double* h_spec);
  * not) return PTT_ENOMEM with the sizes in ptt_last_error().  No device
  * memory is allocated or freed.
  *
- * The first call on a device, with that device current, looks up the
- * array's device address and sets the kernels' shared-memory limits; make
- * that first call before any stream capture.  Every call on a device shares
- * the one array and rewrites what it needs (the array keeps the last call's
- * contents), so calls that overlap on the GPU -- from different host threads
- * or streams -- race and must be serialised by the caller.  Runs on
- * cuda_stream (a cudaStream_t as void*) and returns after synchronising it. */
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing) and, the first time an
+ * address is seen on a device, sets the kernels' shared-memory limits.  The
+ * call copies its tables from host memory and synchronises its stream, so it
+ * must not be made while cuda_stream is being captured into a CUDA graph
+ * (PTT_EINVAL).  Every call on a device shares the one array and rewrites
+ * what it needs (the array keeps the last call's contents), so calls that
+ * overlap on the GPU -- from different host threads or streams -- race and
+ * must be serialised by the caller.  The kernels and FFT passes are those of
+ * ptt_explicit_rhs.  Runs on cuda_stream (a cudaStream_t as void*) and
+ * returns after synchronising it. */
 int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spec, double* d_out,
                              void* cuda_stream);
 

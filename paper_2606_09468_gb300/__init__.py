@@ -54,6 +54,11 @@ _SIGS = {
     "ptt_get_spectral": [_VP, _I32, _DP],
     "ptt_step": [_VP, _I32],
     "ptt_synchronize": [_VP],
+    "ptt_synchronize_for": [_VP, ctypes.c_double],
+    "ptt_set_timeout": [_VP, ctypes.c_double],
+    "ptt_reset_moments": [_VP, _I32],
+    "ptt_midplane_moments": [_VP, _I32, _DP, ctypes.POINTER(ctypes.c_int64)],
+    "ptt_histogram_l1": [_VP, _I32, _VP, _I32, _DP],
     "ptt_diagnostics": [_VP, _I32, ctypes.POINTER(ptt_diag), _I32, ctypes.POINTER(_I32)],
     "ptt_explicit_rhs": [_VP, _I32, _DP],
     "ptt_set_histograms": [_VP, _I32, _DP, _DP],
@@ -175,6 +180,36 @@ def ptt_step(ctx, nsteps):
 
 def ptt_synchronize(ctx):
     return _check("ptt_synchronize", load_library().ptt_synchronize(ctx), allow=(PTT_OK, PTT_BLOWUP))
+
+
+def ptt_synchronize_for(ctx, seconds):
+    return _check("ptt_synchronize_for", load_library().ptt_synchronize_for(ctx, seconds),
+                  allow=(PTT_OK, PTT_BLOWUP, PTT_TIMEOUT))
+
+
+def ptt_set_timeout(ctx, seconds):
+    _check("ptt_set_timeout", load_library().ptt_set_timeout(ctx, seconds))
+
+
+def ptt_reset_moments(ctx, member):
+    _check("ptt_reset_moments", load_library().ptt_reset_moments(ctx, member))
+
+
+def ptt_midplane_moments(ctx, member):
+    """(double[8][4] mean, sd, skewness, kurtosis per mid-plane quantity,
+    number of records in the window)."""
+    out = np.zeros((8, 4))
+    n = ctypes.c_int64()
+    _check("ptt_midplane_moments", load_library().ptt_midplane_moments(ctx, member, _dptr(out),
+                                                                       ctypes.byref(n)))
+    return out, n.value
+
+
+def ptt_histogram_l1(ctx_a, member_a, ctx_b, member_b):
+    out = np.zeros(8)
+    _check("ptt_histogram_l1", load_library().ptt_histogram_l1(ctx_a, member_a, ctx_b, member_b,
+                                                               _dptr(out)))
+    return out
 
 
 def ptt_diagnostics(ctx, member, max_records=1024):
@@ -357,8 +392,28 @@ class Context:
     def step(self, n=1):
         ptt_step(self.ctx, n)
 
-    def synchronize(self):
-        return ptt_synchronize(self.ctx)
+    def synchronize(self, seconds=None):
+        """Wait for the context stream (PTT_OK / PTT_BLOWUP, or PTT_TIMEOUT
+        when `seconds` is given and passes with work in flight)."""
+        if seconds is None:
+            return ptt_synchronize(self.ctx)
+        return ptt_synchronize_for(self.ctx, seconds)
+
+    def set_timeout(self, seconds):
+        ptt_set_timeout(self.ctx, seconds)
+
+    def reset_moments(self, member):
+        ptt_reset_moments(self.ctx, member)
+
+    def moments(self, member):
+        """Window moments of the mid-plane quantities since the last
+        reset_moments (or creation): ((8, 4) array, record count)."""
+        return ptt_midplane_moments(self.ctx, member)
+
+    def histogram_l1(self, member, other, other_member):
+        """L1 distances (8,) between this member's mid-plane histograms and
+        those of `other_member` of context `other`."""
+        return ptt_histogram_l1(self.ctx, member, other.ctx, other_member)
 
     def diagnostics(self, member, max_records=1024):
         return [diag_to_dict(r) for r in ptt_diagnostics(self.ctx, member, max_records)]
@@ -389,35 +444,3 @@ class Context:
             self.close()
         except Exception:
             pass
-
-
-# ------------------------------------------------- window statistics (host)
-def midplane_moments(records, npoints):
-    """Window statistics of the mid-plane quantities (Sec. 3, Figs. 5-8) from
-    diagnostics records: the per-step power sums mid_sums[q][p-1] = sum x^p
-    over the npoints mid-plane points are added over the records, then
-    mean, standard deviation, skewness and kurtosis (fourth standardised
-    moment) follow from the raw moments.  Returns an (8, 4) array."""
-    S = np.zeros((8, 4))
-    for r in records:
-        S += np.asarray(r["mid_sums"], dtype=float)
-    n = float(npoints) * len(records)
-    m1, m2, m3, m4 = (S[:, k] / n for k in range(4))
-    var = np.maximum(m2 - m1 * m1, 0.0)
-    sd = np.sqrt(var)
-    c3 = m3 - 3 * m1 * m2 + 2 * m1 ** 3
-    c4 = m4 - 4 * m1 * m3 + 6 * m1 * m1 * m2 - 3 * m1 ** 4
-    with np.errstate(divide="ignore", invalid="ignore"):
-        skew = np.where(sd > 0, c3 / sd ** 3, 0.0)
-        kurt = np.where(sd > 0, c4 / var ** 2, 0.0)
-    return np.stack([m1, sd, skew, kurt], axis=1)
-
-
-def histogram_l1(a, b):
-    """L1 distance between two histograms of one quantity, each normalised
-    to unit total count (0: identical PDFs, 2: disjoint)."""
-    a = np.asarray(a, dtype=float)
-    b = np.asarray(b, dtype=float)
-    if a.sum() == 0 or b.sum() == 0:
-        return 0.0 if a.sum() == b.sum() else 2.0
-    return float(np.abs(a / a.sum() - b / b.sum()).sum())

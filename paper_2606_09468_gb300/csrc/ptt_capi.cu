@@ -1,6 +1,8 @@
 // Host side of the sPTT channel library: parameter checks, plans, operator
 // tables, workspace carving, initial condition, CUDA-graph step, C ABI.
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -541,6 +543,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.ring = cv.take<ptt_diag>((size_t)nb * kRing);
     d.hist = cv.take<unsigned long long>((size_t)nb * 8 * (PTT_HIST_BINS + 2));
     d.hrange = cv.take<double>((size_t)nb * 16);
+    d.macc = cv.take<double>((size_t)nb * kMacc);
+    d.statout = cv.take<double>((size_t)kMacc);
     d.stage = cv.take<double>((size_t)nf * d.N * nzz * d.nx);
     d.stageS = cv.take<double2>((size_t)nf * NK);
     FftPlan* pls[7] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe, &d.plMz, &d.plNz};
@@ -606,6 +610,7 @@ struct ptt_ctx {
   std::vector<cudaEvent_t> pevents;    // [3 per group] fork / join of those parts
   int launches = 0;
   int device = 0;
+  double timeout_s = 3600.0;           // wall-clock limit of ptt_synchronize (<= 0: none)
 };
 
 thread_local char g_last_error[512] = "";
@@ -631,7 +636,8 @@ void set_last_error(const char* msg) {
 }
 
 int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
-               std::vector<double2>& twMx, std::vector<double2>& tw4, MemberPrm& prm) {
+               std::vector<double2>& twMx, std::vector<double2>& tw4, MemberPrm& prm,
+               std::vector<double>* tt, std::vector<int>* tk) {
   const int s = check_params(p);
   if (s) return s;
   if (p.precision != PTT_FP64) return PTT_ENOTSUP;
@@ -643,6 +649,8 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
   group_sizes(p.nx, p.ny, 1, g);
   d = g.d;
   d.nb = 1;
+  // columns per block as carve() caps them for one member
+  d.Ccol = std::max(1, std::min(d.Ccol, (int)((long long)d.KZ * 9 / 304)));
   FftPlan* pls[2] = {&d.plP, &d.plMx};
   std::vector<double2>* tws[2] = {&twP, &twMx};
   for (int i = 0; i < 2; ++i) {
@@ -650,6 +658,11 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
     pls[i]->n = hp.n;
     pls[i]->nst = (int)hp.radix.size();
     for (int k = 0; k < pls[i]->nst; ++k) pls[i]->radix[k] = hp.radix[k];
+    // tangent-form twiddle records of the FP64 passes (device pointers are
+    // set by the caller once the tables have a home)
+    int nrec = 0, ndbl = 0;
+    tangent_offsets(hp, pls[i]->toff, pls[i]->tto, &nrec, &ndbl);
+    tangent_tables(hp, tt[i], tk[i]);
     tws[i]->resize(hp.n);
     for (int k = 0; k < hp.n; ++k) {
       double cc, ss;
@@ -1107,9 +1120,35 @@ int ptt_step(ptt_ctx* c, int32_t nsteps) {
   return PTT_OK;
 }
 
-int ptt_synchronize(ptt_ctx* c) {
-  if (!c) return PTT_EINVAL;
-  CK(cudaStreamSynchronize(c->stream));
+// Poll the context stream until its work is done or `seconds` of wall-clock
+// time have passed (seconds < 0: no limit): spin for the first 0.2 ms, then
+// sleep in steps of at most 0.1 ms between queries.
+static int wait_stream(ptt_ctx* c, double seconds) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int it = 0;; ++it) {
+    const cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaSuccess) return PTT_OK;
+    if (e != cudaErrorNotReady) return fail_cuda(e, "cudaStreamQuery", __LINE__);
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (seconds >= 0.0 && el >= seconds) {
+      std::snprintf(g_last_error, sizeof(g_last_error),
+                    "ptt_synchronize: work still in flight after %.3f s", el);
+      return PTT_TIMEOUT;
+    }
+    if (el > 2e-4) std::this_thread::sleep_for(std::chrono::microseconds(el > 1e-3 ? 100 : 20));
+  }
+}
+
+int ptt_set_timeout(ptt_ctx* c, double seconds) {
+  if (!c || seconds != seconds) return PTT_EINVAL;
+  c->timeout_s = seconds;
+  return PTT_OK;
+}
+
+int ptt_synchronize_for(ptt_ctx* c, double seconds) {
+  if (!c || seconds != seconds) return PTT_EINVAL;
+  const int w = wait_stream(c, seconds);
+  if (w) return w;
   int blown = 0;
   for (Group& g : c->groups) {
     std::vector<int> st(g.d.nb);
@@ -1117,6 +1156,11 @@ int ptt_synchronize(ptt_ctx* c) {
     for (int v : st) blown |= (v != 0);
   }
   return blown ? PTT_BLOWUP : PTT_OK;
+}
+
+int ptt_synchronize(ptt_ctx* c) {
+  if (!c) return PTT_EINVAL;
+  return ptt_synchronize_for(c, c->timeout_s > 0.0 ? c->timeout_s : -1.0);
 }
 
 int ptt_diagnostics(ptt_ctx* c, int32_t member, ptt_diag* out, int32_t maxr, int32_t* nw) {
@@ -1299,6 +1343,44 @@ int ptt_get_histograms(ptt_ctx* c, int32_t member, int64_t* counts) {
   const size_t nh = (size_t)8 * (PTT_HIST_BINS + 2);
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(counts, g.d.hist + (size_t)b * nh, nh * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  return PTT_OK;
+}
+
+int ptt_reset_moments(ptt_ctx* c, int32_t member) {
+  if (!member_ok(c, member)) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  CK(cudaMemsetAsync(g.d.macc + (size_t)b * kMacc, 0, kMacc * sizeof(double), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PTT_OK;
+}
+
+int ptt_midplane_moments(ptt_ctx* c, int32_t member, double* moments, int64_t* nrecords) {
+  if (!member_ok(c, member) || !moments) return PTT_EINVAL;
+  auto [gi, b] = c->where[member];
+  Group& g = c->groups[gi];
+  double out[kMacc];
+  CK(launch_window_moments(g.d, b, (double)g.d.nx * g.d.nz, c->stream));
+  CK(cudaMemcpyAsync(out, g.d.statout, sizeof(out), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < 32; ++i) moments[i] = out[i];
+  if (nrecords) *nrecords = (int64_t)out[32];
+  return PTT_OK;
+}
+
+int ptt_histogram_l1(ptt_ctx* a, int32_t member_a, ptt_ctx* b, int32_t member_b, double* l1) {
+  if (!member_ok(a, member_a) || !member_ok(b, member_b) || !l1) return PTT_EINVAL;
+  auto [ga, ia] = a->where[member_a];
+  auto [gb, ib] = b->where[member_b];
+  const size_t nh = (size_t)8 * (PTT_HIST_BINS + 2);
+  const GroupDev& da = a->groups[ga].d;
+  const GroupDev& db = b->groups[gb].d;
+  double out[8];
+  if (b != a) CK(cudaStreamSynchronize(b->stream));
+  CK(launch_hist_l1(da.hist + (size_t)ia * nh, db.hist + (size_t)ib * nh, da.statout, a->stream));
+  CK(cudaMemcpyAsync(out, da.statout, sizeof(out), cudaMemcpyDeviceToHost, a->stream));
+  CK(cudaStreamSynchronize(a->stream));
+  for (int q = 0; q < 8; ++q) l1[q] = out[q];
   return PTT_OK;
 }
 

@@ -115,7 +115,9 @@ template <int DIR> struct Bfly<DIR, 5> {
   }
 };
 
-// Division by a runtime divisor d through a multiply-high: with
+// Division by a runtime divisor d through a multiply-high (the method of
+// Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, in its round-up form): with
 // m = floor((2^32 - 1)/d) + 1 = ceil(2^32/d), floor(x/d) = (x m) >> 32 holds
 // exactly whenever x d < 2^32 (the rounding excess of m contributes less than
 // x/2^32 < 1/d), which covers every index of the transforms here

@@ -90,6 +90,8 @@ struct GroupDev {
   ptt_diag* ring;    // [nb][kRing]
   unsigned long long* hist;  // [nb][8][PTT_HIST_BINS + 2] mid-plane histograms
   const double* hrange;      // [nb][8][2] (lo, hi); lo >= hi: quantity off
+  double* macc;      // [nb][kMacc] window sums: mid_sums[8][4] of every record, then the record count
+  double* statout;   // [kMacc] results of the window-statistics kernels (one call at a time)
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
   double2* stageS;   // [5][N][K]  values on the unpadded y grid, x analysed
   // quarter-period twiddles of the Gauss-grid transforms, with the constant
@@ -104,6 +106,15 @@ struct GroupDev {
 };
 
 constexpr int kPart = 48;  // values per diagnostics tile
+constexpr int kMacc = 33;  // window accumulator per member: 8 x 4 power sums + record count
+
+// Adds one diagnostics record's mid-plane power sums to its member's window
+// accumulator (called by the thread that writes the record).
+__device__ __forceinline__ void window_add(double* acc, const ptt_diag& r) {
+  for (int q = 0; q < 8; ++q)
+    for (int k = 0; k < 4; ++k) acc[4 * q + k] += r.mid_sums[q][k];
+  acc[32] += 1.0;
+}
 
 // Diagnostics tiles per member: about 2048 grid points each, so that one
 // member alone still spreads over the SMs; a function of the shape only, so
@@ -145,6 +156,14 @@ cudaError_t set_kernel_attributes(int max_dyn_smem);
 // state of member bs of group s -> state of member bd of group d, modes
 // copied, padded with zeros or truncated (both 2D or both 3D)
 cudaError_t launch_resample(const GroupDev& d, int bd, const GroupDev& s, int bs, cudaStream_t st);
+// Window moments of member b (mean, standard deviation, skewness, kurtosis
+// of each mid-plane quantity, from its accumulator; npoints mid-plane points
+// per record) into g.statout[0..31], the record count into g.statout[32].
+cudaError_t launch_window_moments(const GroupDev& g, int b, double npoints, cudaStream_t st);
+// L1 distance between the normalised mid-plane histograms ha and hb (each
+// [8][PTT_HIST_BINS + 2]) of every quantity into out[0..7].
+cudaError_t launch_hist_l1(const unsigned long long* ha, const unsigned long long* hb, double* out,
+                           cudaStream_t st);
 // 3D (ptt_kernels3d.cu)
 cudaError_t set_kernel_attributes3(int max_dyn_smem);
 cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nlaunch);
@@ -162,8 +181,11 @@ size_t smem_zcols3(int C, int Mz, int f32);
 
 // Host helpers (ptt_capi.cu) used by the workspace-free entry point.
 void set_last_error(const char* msg);
+// tt[0], tk[0] / tt[1], tk[1]: tangent-form twiddle records of the padded
+// Chebyshev and padded x plans (FftPlan::tt, ::tk).
 int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
-               std::vector<double2>& twMx, std::vector<double2>& tw4, MemberPrm& prm);
+               std::vector<double2>& twMx, std::vector<double2>& tw4, MemberPrm& prm,
+               std::vector<double>* tt, std::vector<int>* tk);
 
 size_t smem_ycols(int C, int P, int f32);
 size_t smem_xfused(int Mx, int f32);

@@ -626,6 +626,7 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
     if (blow) g.status[b] = 1;
+    window_add(g.macc + (size_t)b * kMacc, r);
   }
 }
 
@@ -663,6 +664,58 @@ __global__ void __launch_bounds__(256) k_resample(ResampleJob J) {
     }
     J.dst[i] = v;
   }
+}
+
+// Window statistics (Sec. 3: the moments of the mid-plane PDFs over a time
+// window).  With n = npoints x records samples and raw moments
+// m_p = S_p / n of the accumulated power sums S_p:
+//   mean = m_1, var = m_2 - m_1^2, sd = sqrt(var),
+//   skewness = (m_3 - 3 m_1 m_2 + 2 m_1^3) / sd^3,
+//   kurtosis = (m_4 - 4 m_1 m_3 + 6 m_1^2 m_2 - 3 m_1^4) / var^2,
+// (0 for both where var = 0), all in FP64; one thread per quantity.
+__global__ void k_window_moments(const double* __restrict__ acc, double npoints,
+                                 double* __restrict__ out) {
+  const int q = threadIdx.x;
+  const double nrec = acc[32];
+  if (q < 8) {
+    const double n = npoints * nrec;
+    const double m1 = acc[4 * q] / n, m2 = acc[4 * q + 1] / n;
+    const double m3 = acc[4 * q + 2] / n, m4 = acc[4 * q + 3] / n;
+    const double var = fmax(m2 - m1 * m1, 0.0), sd = sqrt(var);
+    const double c3 = m3 - 3.0 * m1 * m2 + 2.0 * m1 * m1 * m1;
+    const double c4 = m4 - 4.0 * m1 * m3 + 6.0 * m1 * m1 * m2 - 3.0 * m1 * m1 * m1 * m1;
+    out[4 * q] = m1;
+    out[4 * q + 1] = sd;
+    out[4 * q + 2] = sd > 0.0 ? c3 / (sd * sd * sd) : 0.0;
+    out[4 * q + 3] = sd > 0.0 ? c4 / (var * var) : 0.0;
+  }
+  if (q == 0) out[32] = nrec;
+}
+
+// L1 distance between two histograms of each quantity, each normalised to
+// unit total count: sum_i |a_i / A - b_i / B| over every slot (under- and
+// overflow included); 0 if both are empty, 2 if only one is.  One warp per
+// quantity, fixed-order shuffle trees.
+__global__ void k_hist_l1(const unsigned long long* __restrict__ ha,
+                          const unsigned long long* __restrict__ hb, double* __restrict__ out) {
+  constexpr int HS = PTT_HIST_BINS + 2;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long* a = ha + (size_t)q * HS;
+  const unsigned long long* b = hb + (size_t)q * HS;
+  double A = 0.0, B = 0.0;
+  for (int i = lane; i < HS; i += 32) {
+    A += (double)a[i];
+    B += (double)b[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    A += __shfl_xor_sync(0xffffffffu, A, o);
+    B += __shfl_xor_sync(0xffffffffu, B, o);
+  }
+  double d = 0.0;
+  if (A > 0.0 && B > 0.0)
+    for (int i = lane; i < HS; i += 32) d += fabs((double)a[i] / A - (double)b[i] / B);
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if (lane == 0) out[q] = (A > 0.0 && B > 0.0) ? d : ((A > 0.0) == (B > 0.0) ? 0.0 : 2.0);
 }
 
 __global__ void k_reset(GroupDev g, int b) {
@@ -708,6 +761,17 @@ cudaError_t launch_resample(const GroupDev& d, int bd, const GroupDev& s, int bs
   const long long tot = (long long)J.nf * d.KZ * d.N;
   const unsigned blocks = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 16);
   k_resample<<<blocks, 256, 0, st>>>(J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_moments(const GroupDev& g, int b, double npoints, cudaStream_t st) {
+  k_window_moments<<<1, 32, 0, st>>>(g.macc + (size_t)b * kMacc, npoints, g.statout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist_l1(const unsigned long long* ha, const unsigned long long* hb, double* out,
+                           cudaStream_t st) {
+  k_hist_l1<<<1, 256, 0, st>>>(ha, hb, out);
   return cudaGetLastError();
 }
 

@@ -717,6 +717,7 @@ __global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
     if (blow) g.status[b] = 1;
+    window_add(g.macc + (size_t)b * kMacc, r);
   }
 }
 

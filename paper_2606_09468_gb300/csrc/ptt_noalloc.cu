@@ -10,8 +10,8 @@
 // on which the library is loaded holds those bytes until the process exits.
 //
 // In host code the name g_noalloc_scratch is a host-side stand-in, not a
-// device address; the device address is obtained once per device with
-// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// device address; the device address is looked up with cudaGetSymbolAddress
+// on every call (with the caller's device current) and passed to the kernels.
 #include <cstdio>
 #include <mutex>
 #include <vector>
@@ -26,12 +26,15 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_mu;
-void* g_dev_ptr[kMaxDevices] = {};
+void* g_dev_ptr[kMaxDevices] = {};   // address the kernels' attributes were last set for
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Device address of the scratch array on the current device; first call per
-// device also raises the kernels' dynamic shared-memory limit.
+// Device address of the scratch array on the current device, looked up on
+// every call (cudaGetSymbolAddress allocates nothing), so that a device reset
+// or another context on the same ordinal never leaves a stale address
+// behind.  Whenever the address differs from the one seen before on this
+// ordinal, the kernels' dynamic shared-memory limit is raised again.
 int scratch_for_current_device(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -40,17 +43,17 @@ int scratch_for_current_device(void** out) {
     return PTT_ECUDA;
   }
   if (dev < 0 || dev >= kMaxDevices) return PTT_EINVAL;
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    char msg[256];
+    std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress(g_noalloc_scratch): %s",
+                  cudaGetErrorString(e));
+    ptt::set_last_error(msg);
+    return PTT_ECUDA;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_dev_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      char msg[256];
-      std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress(g_noalloc_scratch): %s",
-                    cudaGetErrorString(e));
-      ptt::set_last_error(msg);
-      return PTT_ECUDA;
-    }
+  if (g_dev_ptr[dev] != p) {
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!e) e = ptt::set_kernel_attributes(optin);
@@ -60,7 +63,7 @@ int scratch_for_current_device(void** out) {
     }
     g_dev_ptr[dev] = p;
   }
-  *out = g_dev_ptr[dev];
+  *out = p;
   return PTT_OK;
 }
 
@@ -73,8 +76,28 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   ptt::GroupDev g{};
   ptt::MemberPrm prm{};
   std::vector<double2> twP, twMx, tw4;
-  int s = ptt::shape_plan(*p, g, twP, twMx, tw4, prm);
+  std::vector<double> tt[2];
+  std::vector<int> tk[2];
+  int s = ptt::shape_plan(*p, g, twP, twMx, tw4, prm, tt, tk);
   if (s) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  {
+    // the host-to-device copies and the final synchronisation below are not
+    // allowed while the stream is being captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) {
+      char msg[256];
+      std::snprintf(msg, sizeof(msg), "ptt_explicit_rhs_noalloc: cudaStreamIsCapturing: %s",
+                    cudaGetErrorString(e));
+      ptt::set_last_error(msg);
+      return PTT_ECUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) {
+      ptt::set_last_error("ptt_explicit_rhs_noalloc: the stream is being captured");
+      return PTT_EINVAL;
+    }
+  }
   const size_t rows = (size_t)g.M, K = g.K, NK = (size_t)g.N * K;
   // layout of the scratch array
   size_t off = 0;
@@ -86,6 +109,11 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   const size_t oTP = off; off = align256(off + twP.size() * sizeof(double2));
   const size_t oTM = off; off = align256(off + twMx.size() * sizeof(double2));
   const size_t oT4 = off; off = align256(off + tw4.size() * sizeof(double2));
+  size_t oTT[2], oTK[2];
+  for (int i = 0; i < 2; ++i) {
+    oTT[i] = off; off = align256(off + tt[i].size() * sizeof(double));
+    oTK[i] = off; off = align256(off + tk[i].size() * sizeof(int));
+  }
   const size_t oPr = off; off = align256(off + sizeof(ptt::MemberPrm));
   const size_t oSt = off; off = align256(off + sizeof(int));
   const size_t oCn = off; off = align256(off + sizeof(long long));
@@ -102,7 +130,6 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   s = scratch_for_current_device(&base);
   if (s) return s;
   char* b = (char*)base;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   g.X = (double2*)(b + oX);     // input in the kernels' mode-major layout
   g.NR = (double2*)(b + oNR);   // N_cxx, N_cxy, N_cyy, N_u, N_v
   g.Rb = (double2*)(b + oRb);   // H_x, H_y
@@ -110,28 +137,42 @@ extern "C" int ptt_explicit_rhs_noalloc(const ptt_params* p, const double* d_spe
   g.Zp = (double2*)(b + oZp);
   g.plP.tw = (const double2*)(b + oTP);
   g.plMx.tw = (const double2*)(b + oTM);
+  ptt::FftPlan* pls[2] = {&g.plP, &g.plMx};
+  for (int i = 0; i < 2; ++i) {
+    pls[i]->tt = (const double*)(b + oTT[i]);
+    pls[i]->tk = (const int*)(b + oTK[i]);
+  }
   g.tw4P = (const double2*)(b + oT4);                      // forward table, M entries
   g.tw4Pi = (const double2*)(b + oT4) + tw4.size() / 2;    // inverse table, M entries
   g.prm = (ptt::MemberPrm*)(b + oPr);
   g.status = (int*)(b + oSt);
   g.count = (long long*)(b + oCn);
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   // status and step counter must read zero; tables and parameters are
   // rewritten on every call (the array keeps the previous call's contents)
-  if ((e = cudaMemsetAsync(b + oSt, 0, sizeof(int), st)) ||
-      (e = cudaMemsetAsync(b + oCn, 0, sizeof(long long), st)) ||
-      (e = cudaMemcpyAsync(b + oTP, twP.data(), twP.size() * sizeof(double2),
-                           cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(b + oTM, twMx.data(), twMx.size() * sizeof(double2),
-                           cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(b + oT4, tw4.data(), tw4.size() * sizeof(double2),
-                           cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(b + oPr, &prm, sizeof(prm), cudaMemcpyHostToDevice, st)) ||
-      (e = ptt::launch_transpose((const double2*)d_spec, g.X, 5, g.N, g.K, st)) ||
-      (e = ptt::launch_explicit(g, st)) ||
-      (e = ptt::launch_transpose(g.NR, (double2*)d_out, 3, g.K, g.N, st)) ||
-      (e = ptt::launch_transpose(g.Rb, (double2*)d_out + 3 * NK, 2, g.K, g.N, st)) ||
-      (e = cudaStreamSynchronize(st))) {
+  e = cudaMemsetAsync(b + oSt, 0, sizeof(int), st);
+  if (!e) e = cudaMemsetAsync(b + oCn, 0, sizeof(long long), st);
+  if (!e) e = cudaMemcpyAsync(b + oTP, twP.data(), twP.size() * sizeof(double2),
+                              cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(b + oTM, twMx.data(), twMx.size() * sizeof(double2),
+                              cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(b + oT4, tw4.data(), tw4.size() * sizeof(double2),
+                              cudaMemcpyHostToDevice, st);
+  for (int i = 0; i < 2 && !e; ++i) {
+    e = cudaMemcpyAsync(b + oTT[i], tt[i].data(), tt[i].size() * sizeof(double),
+                        cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(b + oTK[i], tk[i].data(), tk[i].size() * sizeof(int),
+                                cudaMemcpyHostToDevice, st);
+  }
+  if (!e) e = cudaMemcpyAsync(b + oPr, &prm, sizeof(prm), cudaMemcpyHostToDevice, st);
+  if (!e) e = ptt::launch_transpose((const double2*)d_spec, g.X, 5, g.N, g.K, st);
+  if (!e) e = ptt::launch_explicit(g, st);
+  if (!e) e = ptt::launch_transpose(g.NR, (double2*)d_out, 3, g.K, g.N, st);
+  if (!e) e = ptt::launch_transpose(g.Rb, (double2*)d_out + 3 * NK, 2, g.K, g.N, st);
+  // the host tables must outlive the copies above
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (!e) e = es;
+  if (e) {
     char msg[256];
     std::snprintf(msg, sizeof(msg), "ptt_explicit_rhs_noalloc: %s", cudaGetErrorString(e));
     ptt::set_last_error(msg);

@@ -58,3 +58,25 @@ def test_workspace_grows_with_members(lib):
     two = P.ptt_workspace_size([P.make_params(nx=64, ny=65)] * 2)
     rag = P.ptt_workspace_size([P.make_params(nx=64, ny=65), P.make_params(nx=128, ny=97)])
     assert one < two < rag
+
+
+def test_noalloc_argument_checks_without_gpu(lib):
+    """ptt_explicit_rhs_noalloc rejects bad arguments on the host, before any
+    device call: the pointers below are never dereferenced."""
+    import paper_2606_09468_gb300 as P
+    ok = P.make_params(nx=64, ny=65)
+    a, b = 1 << 20, 2 << 20          # 16-byte aligned stand-ins
+    cases = [
+        (ok, 0, b, P.PTT_EINVAL),                              # null input
+        (ok, a, 0, P.PTT_EINVAL),                              # null output
+        (ok, a + 8, b, P.PTT_EINVAL),                          # misaligned input
+        (ok, a, b + 4, P.PTT_EINVAL),                          # misaligned output
+        (ok, a, a, P.PTT_EINVAL),                              # in place
+        (P.make_params(nx=63, ny=65), a, b, P.PTT_EINVAL),     # inadmissible shape
+        (P.make_params(nx=64, ny=65, precision=P.PTT_MIXED), a, b, P.PTT_ENOTSUP),
+        (P.make_params(nx=32, ny=33, nz=16, lz=5.0), a, b, P.PTT_ENOTSUP),
+    ]
+    for prm, din, dout, code in cases:
+        with pytest.raises(P.PttError) as ei:
+            P.ptt_explicit_rhs_noalloc(prm, din, dout, 0)
+        assert ei.value.code == code, (prm.nx, prm.nz, prm.precision, din, dout)

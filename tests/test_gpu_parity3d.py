@@ -106,11 +106,29 @@ def test_diagnostics_3d_match_oracle():
     for k, band in (("n_lt3", "n_band3"), ("n_lt0", "n_band0"),
                     ("n_mid_lt3", "n_mid_band3"), ("n_mid_lt0", "n_mid_band0")):
         assert abs(g[k] - o[k]) <= o[band], (k, g[k], o[k])
+    _mid_sums_compare(g, o, nx, nz, ora, rel=1e-11)
+
+
+def _mid_sums_compare(g, o, nx, nz, ora, rel):
+    """Mid-plane power sums sum_(x,z) q^p against the oracle, with the bound
+    of the 2D parity tests: a point error dq moves the sum by at most
+    nx nz p qmax^(p-1) dq, qmax <= (sum q^4)^(1/4), and the point errors
+    follow the field errors: dq = 2 rel S_q with S_q = max|Tr c| for Tr c,
+    u_max = max|u| for u', w', v, u_max kx_max for d/dx and u_max kz_max for
+    d/dz (Bernstein's inequality for the retained Fourier modes)."""
+    ph = ora.get_physical()
+    u_max = float(np.max(np.sqrt(ph[0] ** 2 + ph[1] ** 2 + ph[2] ** 2)))
+    scale = max(abs(o["max_trc"]), abs(o["min_trc"]))
+    kx = 2 * np.pi * (nx // 2 - 1) / ora.p.lx
+    kz = 2 * np.pi * (nz // 2 - 1) / ora.p.lz
+    # q: Tr c, u', w', du/dx, du/dz, dw/dx, dw/dz, v
+    S = [scale, u_max, u_max, u_max * kx, u_max * kz, u_max * kx, u_max * kz, u_max]
     ms = o["mid_sums"]
     for q in range(8):
-        qmax = abs(ms[q][3]) ** 0.25 + 1e-300
+        qmax = abs(ms[q][3]) ** 0.25
+        dq = 2 * rel * S[q]
         for p in range(4):
-            tol = 1e-9 * nx * nz * (p + 1) * qmax ** (p + 1) + 1e-300
+            tol = nx * nz * (p + 1) * qmax ** p * dq + 1e-300
             assert abs(g["mid_sums"][q][p] - ms[q][p]) <= tol, (q, p, g["mid_sums"][q][p], ms[q][p])
 
 
@@ -149,6 +167,56 @@ def test_hundred_steps_3d():
     # u, v, w perturbations (1e-3 of the base flow) are resolved as well
     ep = _errs(_pert(g)[:3], _pert(o)[:3])
     assert np.all(ep <= 1e-7), ep
+
+
+@pytest.fixture(scope="module")
+def oracle_97():
+    """Oracle run at 16 x 97 x 8 (ny = 97: the padded Chebyshev length
+    M = 150 of the 128 x 97 x 64 workload), states after 1 and 100 steps."""
+    nx, ny, nz = 16, 97, 8
+    ora = _oracle(nx, ny, nz)
+    ora.init_state(11, I.AMPLITUDE)
+    ora.step()
+    one = ora.get_physical()
+    for _ in range(99):
+        ora.step()
+    return (nx, ny, nz), one, ora.get_physical()
+
+
+def test_hundred_steps_3d_full_size_chebyshev_plan(oracle_97):
+    (nx, ny, nz), one, hundred = oracle_97
+    ctx = _ctx([(nx, ny, nz)])
+    ctx.init_state(0, 11, I.AMPLITUDE)
+    ctx.step(1)
+    e1 = _errs(I.abi_to_phys3(ctx.get_state(0)), one)
+    ctx.step(99)
+    assert ctx.synchronize() == 0
+    g = I.abi_to_phys3(ctx.get_state(0))
+    e = _errs(g, hundred)
+    print("FP64 3D 16x97x8 errors after 1 step", e1, "after 100 steps", e)
+    assert np.all(e1 <= 1e-11), e1
+    assert np.all(e <= 1e-9), e
+    ep = _errs(_pert(g)[:3], _pert(hundred)[:3])
+    assert np.all(ep <= 1e-7), ep
+
+
+def test_mixed_3d_full_size_chebyshev_plan(oracle_97):
+    """The mixed form against the FP64 oracle after 1 and 100 steps at the
+    workload's Chebyshev length (stated per-field errors, as at 32 x 33 x 16)."""
+    import paper_2606_09468_gb300 as P
+    (nx, ny, nz), one, hundred = oracle_97
+    ctx = _ctx([(nx, ny, nz)], precision=P.PTT_MIXED)
+    ctx.init_state(0, 11, I.AMPLITUDE)
+    ctx.step(1)
+    e1 = _errs(I.abi_to_phys3(ctx.get_state(0)), one)
+    ctx.step(99)
+    assert ctx.synchronize() == 0
+    e100 = _errs(I.abi_to_phys3(ctx.get_state(0)), hundred)
+    print("mixed 3D 16x97x8 errors after 1 step", e1, "after 100 steps", e100)
+    assert np.all(e1[[0, 1, 2, 3, 4, 6, 8]] <= 1e-8), e1
+    assert np.all(e1[[5, 7]] <= 1e-6), e1
+    assert np.all(e100[[0, 3, 4, 6, 8]] <= 1e-7), e100
+    assert np.all(e100[[1, 2, 5, 7]] <= 1e-4), e100
 
 
 def test_one_step_full_size_3d():

@@ -1,6 +1,7 @@
 """The workspace-free entry point ptt_explicit_rhs_noalloc, for callers that
-cannot allocate device memory, against the workspace entry point
-ptt_explicit_rhs on the same states.
+cannot allocate device memory, against the FP64 oracle's explicit right-hand
+side and against the workspace entry point ptt_explicit_rhs on the same
+states.
 
 Collected last on purpose (file name), so that a run that stops at the first
 failure has already run every other test; it also passes alone."""
@@ -15,11 +16,14 @@ TOL = 1e-12   # the explicit-right-hand-side tolerance of the parity tests
 
 
 def _state(nx, ny, seed):
-    from oracle.ptt2d import Channel2D, Params
+    """A perturbed laminar state (ABI spectral layout) and the oracle's
+    explicit right-hand side of it (N_cxx, N_cxy, N_cyy, H_x, H_y)."""
+    from oracle.ptt2d import Channel2D, Params, State
     ora = Channel2D(Params(nx=nx, ny=ny, dt=I.DT, **I.PAPER))
     ora.init_state(seed, 0.05)
     extra = [I.random_spectral(nx, ny, seed=seed + f, decay=0.3, scale=0.01) for f in range(5)]
-    return I.spectral_to_abi([a + e for a, e in zip(ora.state.as_list(), extra)])
+    st = State(*[a + e for a, e in zip(ora.state.as_list(), extra)])
+    return I.spectral_to_abi(st.as_list()), ora.explicit_terms(st)
 
 
 def test_noalloc_matches_workspace_entry_point_on_two_calls():
@@ -32,7 +36,7 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls():
     # see the first call's leftovers in the shared static array
     for nx, ny, seed in ((64, 65, 11), (128, 97, 12)):
         prm = P.make_params(nx=nx, ny=ny, dt=I.DT, **I.PAPER)
-        spec = _state(nx, ny, seed)
+        spec, oracle_rhs = _state(nx, ny, seed)
         ctx = P.Context([prm])
         ctx.set_spectral(0, spec)
         ref = ctx.explicit_rhs(0)
@@ -45,6 +49,11 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls():
         for f in range(5):
             err = np.max(np.abs(got[f] - ref[f])) / np.max(np.abs(ref[f]))
             assert err <= TOL, (nx, ny, f, err)
+        # and against the oracle, field by field, at the same tolerance
+        got_s = I.abi_to_spectral(got)
+        for f in range(5):
+            err = np.max(np.abs(got_s[f] - oracle_rhs[f])) / np.max(np.abs(oracle_rhs[f]))
+            assert err <= TOL, ("oracle", nx, ny, f, err)
         # the input is left untouched
         assert np.array_equal(d_in.cpu().numpy(), spec)
 
