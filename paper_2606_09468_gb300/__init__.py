@@ -179,7 +179,8 @@ def ptt_step(ctx, nsteps):
 
 
 def ptt_synchronize(ctx):
-    return _check("ptt_synchronize", load_library().ptt_synchronize(ctx), allow=(PTT_OK, PTT_BLOWUP))
+    return _check("ptt_synchronize", load_library().ptt_synchronize(ctx),
+                  allow=(PTT_OK, PTT_BLOWUP, PTT_TIMEOUT))
 
 
 def ptt_synchronize_for(ctx, seconds):
