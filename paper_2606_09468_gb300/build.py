@@ -1,6 +1,6 @@
 """Build the in-tree CUDA library ``libptt.so`` for sm_103a with nvcc.
 
-Four translation units compiled in parallel, linked with the static CUDA
+Five translation units compiled in parallel, linked with the static CUDA
 runtime.  Usage: ``python -m paper_2606_09468_gb300.build`` or ``build()``."""
 import concurrent.futures as cf
 import os
@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libptt.so")
-SOURCES = ["ptt_kernels.cu", "ptt_kernels3d.cu", "ptt_capi.cu", "ptt_noalloc.cu"]
+SOURCES = ["ptt_kernels.cu", "ptt_kernels3d.cu", "ptt_capi.cu", "ptt_noalloc.cu", "ptt_mma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

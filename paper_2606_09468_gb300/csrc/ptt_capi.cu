@@ -420,7 +420,8 @@ struct Group {
 int check_params(const ptt_params& p) {
   if (p.nz != 1 && (p.nz < 4 || p.nz > 512 || (p.nz & 1) || !smooth235(p.nz))) return PTT_EINVAL;
   if (p.nz > 1 && !(p.lz > 0)) return PTT_EINVAL;
-  if (p.precision != PTT_FP64 && p.precision != PTT_MIXED) return PTT_ENOTSUP;
+  if (p.precision != PTT_FP64 && p.precision != PTT_MIXED && p.precision != PTT_MIXED_FFT)
+    return PTT_ENOTSUP;
   if (p.nx < 8 || p.nx > 512 || (p.nx & 1) || !smooth235(p.nx)) return PTT_EINVAL;
   if (p.ny < 9 || p.ny > 513 || !smooth235(p.ny - 1)) return PTT_EINVAL;
   if (!(p.lx > 0) || !(p.re > 0) || !(p.wi > 0) || !(p.dt > 0)) return PTT_EINVAL;
@@ -545,6 +546,12 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.hrange = cv.take<double>((size_t)nb * 16);
     d.macc = cv.take<double>((size_t)nb * kMacc);
     d.statout = cv.take<double>((size_t)kMacc);
+    // mixed groups: pre-split tables of the tensor-core Chebyshev passes
+    const bool mma = d.f32 && d.ymma && cheb_mma_supported(d.M, d.N);
+    d.Wyi = mma ? cv.take<uint16_t>(cheb_mma_table_bytes(d.M, d.N, 1) / 2) : nullptr;
+    d.Wyf = mma ? cv.take<uint16_t>(cheb_mma_table_bytes(d.M, d.N, 0) / 2) : nullptr;
+    d.mma_err = cv.take<int>(1);
+    d.ymma = mma ? 1 : 0;
     d.stage = cv.take<double>((size_t)nf * d.N * nzz * d.nx);
     d.stageS = cv.take<double2>((size_t)nf * NK);
     FftPlan* pls[7] = {&d.plP, &d.plMx, &d.plNx, &d.plPu, &d.plPe, &d.plMz, &d.plNz};
@@ -580,7 +587,8 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
       g.ny = pm[i].ny;
       g.nz = pm[i].nz;
       group_sizes(g.nx, g.ny, g.nz, g);
-      g.d.f32 = (pm[i].precision == PTT_MIXED) ? 1 : 0;
+      g.d.f32 = (pm[i].precision != PTT_FP64) ? 1 : 0;
+      g.d.ymma = (pm[i].precision == PTT_MIXED) ? 1 : 0;   // requested; carve() checks the shape
       groups.push_back(std::move(g));
       it = idx.find(key);
     }
@@ -797,6 +805,9 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   }
   CK(set_kernel_attributes(optin));
   CK(set_kernel_attributes3(optin));
+  CK(set_cheb_mma_attributes(optin));
+  int nsm = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   CK(cudaMemsetAsync(d_ws, 0, need - 256, c->stream));
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     Group& g = c->groups[gi];
@@ -804,6 +815,16 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
     const int nb = d.nb, N = d.N, K = d.KZ, nzz = d.nz;   // K: modes per Chebyshev index
     const size_t NK = (size_t)N * K;
     for (int i = 0; i < nb; ++i) c->where[g.members[i]] = {(int)gi, i};
+    d.nsm = nsm;
+    if (d.Wyi) {
+      for (int inv = 0; inv < 2; ++inv) {
+        std::vector<uint16_t> tab;
+        cheb_mma_tables(d.M, d.N, 1 - inv, tab);
+        CK(cudaMemcpyAsync((void*)(inv ? d.Wyf : d.Wyi), tab.data(), tab.size() * sizeof(uint16_t),
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+      }
+    }
     // member parameters
     std::vector<MemberPrm> mp(nb);
     for (int i = 0; i < nb; ++i) {

@@ -90,6 +90,14 @@ struct GroupDev {
   ptt_diag* ring;    // [nb][kRing]
   unsigned long long* hist;  // [nb][8][PTT_HIST_BINS + 2] mid-plane histograms
   const double* hrange;      // [nb][8][2] (lo, hi); lo >= hi: quantity off
+  // mixed groups: the Chebyshev passes of the step as tensor-core contractions
+  // (ymma = 1; see ptt_mma.cu) with their pre-split BF16 tables, inverse and
+  // forward, or as FP32 FFTs (ymma = 0)
+  int ymma;
+  int nsm;           // streaming multiprocessors of the device (persistent grids)
+  const uint16_t* Wyi;
+  const uint16_t* Wyf;
+  int* mma_err;      // set by a tensor-core pass whose bounded wait ran out
   double* macc;      // [nb][kMacc] window sums: mid_sums[8][4] of every record, then the record count
   double* statout;   // [kMacc] results of the window-statistics kernels (one call at a time)
   double* stage;     // [5][N][nx] host<->device staging (one member at a time)
@@ -178,6 +186,13 @@ cudaError_t launch_reset_member3(const GroupDev& g, int b, cudaStream_t st);
 size_t smem_xfused3(int Mx, int f32);
 size_t spec3_scratch_columns();
 size_t smem_zcols3(int C, int Mz, int f32);
+
+// Tensor-core Chebyshev passes of mixed groups (ptt_mma.cu).
+bool cheb_mma_supported(int M, int N);
+size_t cheb_mma_table_bytes(int M, int N, int inverse);
+void cheb_mma_tables(int M, int N, int inverse, std::vector<uint16_t>& out);
+cudaError_t set_cheb_mma_attributes(int optin_bytes);
+cudaError_t launch_cheb_mma(const GroupDev& g, bool inverse, cudaStream_t st, int sms);
 
 // Host helpers (ptt_capi.cu) used by the workspace-free entry point.
 void set_last_error(const char* msg);

@@ -824,6 +824,12 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
   int n = 0;
   switch (stage) {
     case 0: {  // inverse y: 9 fields on the padded Gauss grid, one launch
+      if (g.f32 && g.ymma) {
+        cudaError_t e = launch_cheb_mma(g, true, st, g.nsm);
+        if (e) return e;
+        n = 1;
+        break;
+      }
       YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4Pi);
       J.src = g.X; J.dst = g.f32 ? (void*)g.Ypf : (void*)g.Yp;
       J.dst_f32 = g.f32;
@@ -844,6 +850,12 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       n = 1;
       break;
     case 2: {  // forward y of the 5 explicit fields
+      if (g.f32 && g.ymma) {
+        cudaError_t e = launch_cheb_mma(g, false, st, g.nsm);
+        if (e) return e;
+        n = 1;
+        break;
+      }
       YJob F = make_yjob(g, false, g.M, g.Ccol, g.plP, g.tw4P);
       F.src = g.f32 ? (const void*)g.Zpf : (const void*)g.Zp; F.dst = g.NR;
       F.src_f32 = g.f32;

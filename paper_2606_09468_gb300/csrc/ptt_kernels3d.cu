@@ -811,8 +811,14 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       const int dv[17] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1};
       const size_t sm = smem_ycols(g.Ccol, M, f32);
       for (int i = 0; i < 17; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = dv[i]; }
-      if (f32) k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
-      else k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
+      if (f32 && g.ymma) {
+        cudaError_t e = launch_cheb_mma(g, true, st, g.nsm);
+        if (e) return e;
+      } else if (f32) {
+        k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
+      } else {
+        k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
+      }
       ++n;
       ZJob Z = zjob(g, true, Mz, M, g.plMz);
       Z.C = g.zC;
@@ -854,8 +860,14 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       F.src_fstride = yplane; F.dst_fstride = NK;
       const size_t sm = smem_ycols(g.Ccol, M, f32);
       for (int i = 0; i < 9; ++i) { F.src_field[i] = i; F.dst_field[i] = i; F.deriv[i] = 0; }
-      if (f32) k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
-      else k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
+      if (f32 && g.ymma) {
+        cudaError_t e = launch_cheb_mma(g, false, st, g.nsm);
+        if (e) return e;
+      } else if (f32) {
+        k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
+      } else {
+        k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
+      }
       n = 2;
       break;
     }

@@ -44,7 +44,7 @@ def test_status_strings_and_param_checks_without_gpu(lib):
     assert P.ptt_workspace_size([P.make_params(nx=8, ny=9, nz=512, lz=5.0)]) > 0
     for bad in (dict(nx=63), dict(ny=66), dict(nx=14), dict(beta=0.0), dict(nz=2), dict(nz=3),
                 dict(nz=14), dict(nz=1024), dict(nz=8, lz=0.0), dict(nx=6), dict(nx=1024),
-                dict(ny=7), dict(ny=1025), dict(dt=0.0), dict(precision=2)):
+                dict(ny=7), dict(ny=1025), dict(dt=0.0), dict(precision=3)):
         with pytest.raises(P.PttError):
             P.ptt_workspace_size([P.make_params(**bad)])
     # an empty ensemble
