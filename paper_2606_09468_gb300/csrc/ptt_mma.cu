@@ -1,6 +1,5 @@
 // Chebyshev transforms of the mixed-precision step as dense contractions on
-// the tensor cores (tcgen05, sm_103a), with split-BF16 compensated products
-// accumulated in FP32.
+// the tensor cores (tcgen05, sm_103a): BF16 operands, FP32 accumulation.
 //
 // Along y the method (Sec. 2: Fourier-Chebyshev pseudo-spectral) maps the
 // Chebyshev coefficients a_n (n < N) of every Fourier column to values on the
@@ -9,34 +8,51 @@
 //            T_n(y_j) = cos(n theta_j),  T_n'(y_j) = n sin(n theta_j) / sin(theta_j)
 //   forward  a_k  = s_k sum_j cos(k theta_j) f_j  (k < N; s_0 = 1/M, s_k = 2/M),
 // i.e. one matrix W (M x N, or N x M) applied to every column.  With the
-// columns' real and imaginary parts as the rows of the data operand D
-// (128 per tile), each transform is OUT[128 x nout] = D[128 x kin] W^T.
+// columns' real and imaginary parts as the rows of the data operand X
+// (128 per tile), each transform is OUT[128 x nout] = X[128 x kin] W^T.
 //
-// Precision: every FP32 value x (FP64 inputs are first truncated to FP32 by
-// integer operations on their bits) is split exactly into three BF16 pieces
-// x = x0 + x1 + x2 (x0 = x with the low 16 bits cleared, x1 the same of
-// x - x0, x2 = x - x0 - x1, which has at most 8 significant bits).  The
-// tables are split the same way on the host.  Of the nine products the six
-// with i + j <= 2 are accumulated in FP32 in tensor memory: the dropped ones
-// are below 2^-24 of |x||w|, so the contraction keeps FP32 accuracy.  Each
-// column is split relative to its own values, so a fluctuation column keeps
-// its own relative accuracy however large the mean-mode column (the base
-// state, whose stretch components reach 10^4) is.
+// Precision (a fixed-point split in the manner of Ozaki's scheme).  Each data
+// row r is scaled by a power of two 2^(7 - e_r), 2^e_r > max_i |x_ri|, and cut
+// into four slices of integers in [-128, 128]:
+//   x 2^(7 - e_r) = X0 + X1/2^8 + X2/2^16 + X3/2^24 + (|rest| <= 2^-25),
+// each slice exact in BF16 (8 significant bits).  The tables are cut the same
+// way on the host, row o scaled by a power of two sigma_o > max_i |w_oi|
+// (W0 .. W3).  Then
+//   out = 2^(e_r - 14) sigma_o (A0 + A1/2^8),
+//   A0 = sum_i X0 W0                      (|A0| <= 2^14 kin < 2^24: every
+//                                          partial sum is an integer held
+//                                          exactly in FP32, whatever rounding
+//                                          the tensor core's accumulator uses)
+//   A1 = sum_i (X0 W1 + X1 W0) + (X0 W2 + X1 W1 + X2 W0)/2^8
+//              + (X0 W3 + X1 W2 + X2 W1 + X3 W0)/2^16
+// in two FP32 accumulators in tensor memory (the powers of two ride on
+// pre-scaled slices, X2/2^8, X3/2^16, W1/2^8, W2/2^8, W2/2^16, W3/2^16, all
+// exact in BF16).  The accumulation error of A1 enters 2^-8 smaller, and the
+// dropped products are below 2^-31 of each row's scale.  A fourth slice is
+// needed because the derivative table grows like n^2 while the coefficients
+// decay: a 24-bit cut of the data loses up to 1e-4 of the derivative at
+// ny = 257, the 32-bit cut keeps FP32 accuracy.  Each Fourier column is
+// scaled by its own largest coefficient, so the fluctuation columns keep
+// their own relative accuracy however large the mean column (the base state,
+// stretch components 10^4).
 //
 // Kernel structure (k_cheb_mma): persistent, one CTA of 256 threads per SM,
-// each CTA walking tiles (member, field, 64 Fourier columns).  Per tile the
+// walking tiles (member, field, 64 Fourier columns).  Per tile a first pass
+// over the input finds each row's exponent; then, per pass (a set of output
+// subtiles whose two accumulators fit the 512 tensor-memory columns), the
 // contraction runs in chunks of 32 along kin through a two-stage ring in
 // shared memory: all threads load the chunk's data (coalesced along the
-// contiguous direction of the input), split it and store the three pieces
-// in the canonical K-major layout (core matrices of 8 rows x 16 bytes), while
-// thread 0 brings the chunk of the pre-split table with a bulk copy
+// input's contiguous direction), slice it and store the slices in the
+// canonical K-major layout (core matrices of 8 rows x 16 bytes), while
+// thread 0 brings the chunk of the pre-sliced table with bulk copies
 // (cp.async.bulk, completion on an mbarrier) and issues the tcgen05.mma
-// instructions of the previous chunk; tcgen05.commit on a per-stage mbarrier
-// frees the stage.  The epilogue reads the FP32 accumulators with
-// tcgen05.ld: inverse outputs ([j][column], FP32) go straight to global
-// memory, forward outputs ([column][k], FP64) through shared memory so that
-// the writes are contiguous.  Every wait is bounded; a wait that runs out
-// sets *err and the CTA stops after a bounded wait for its own copies.
+// instructions; tcgen05.commit on a per-stage mbarrier frees the stage.  The
+// epilogue reads the accumulators with tcgen05.ld: inverse outputs
+// ([j][column], FP32) go straight to global memory, forward outputs
+// ([column][k], FP64) through shared memory so that the writes are
+// contiguous.  Every wait is bounded; a wait that runs out sets *err and the
+// CTA stops after a bounded wait for its own copies.
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -51,11 +67,17 @@ constexpr int kThreads = 256;
 constexpr int kRows = 128;                 // data rows per tile (64 complex columns)
 constexpr int kCols = 64;                  // complex columns per tile
 constexpr int kChunk = 32;                 // contraction elements per chunk (2 MMA k-steps)
-constexpr int kPieceA = kRows * kChunk * 2;  // bytes of one BF16 piece of the data chunk
+constexpr int kPieceA = kRows * kChunk * 2;  // bytes of one BF16 slice of the data chunk
+constexpr int kNPA = 4;                    // data slices: X0, X1, X2/2^8, X3/2^16
+constexpr int kNPB = 6;                    // table slices: W0, W1, W1/2^8, W2/2^8, W2/2^16, W3/2^16
+constexpr int kMaxW = 208;                 // widest output subtile (two stages fit shared memory)
 constexpr int kLBO = 128;                  // core-matrix stride along K (bytes)
 constexpr int kSBO = 512;                  // core-matrix stride along rows (4 core matrices of K)
 constexpr long long kSpin = 1LL << 26;     // iteration limit of every wait
 constexpr int kSmemLimit = 227 * 1024 - 4096;  // dynamic shared memory of one CTA
+constexpr int kTmemCols = 512;
+constexpr int kMaxUnits = 8;               // (table, subtile) units
+constexpr int kMaxPass = 8;
 
 struct MmaJob {
   const void* in;
@@ -63,22 +85,23 @@ struct MmaJob {
   long long in_ms, in_fs, in_cs, in_is;    // complex-element strides: member, field, column, index
   long long out_ms, out_fs, out_cs, out_os;
   int in_f64, out_f64;
-  int col_fast;        // 1: input contiguous along columns (forward), 0: along the index (inverse)
   int ncol, kin, nout;
   int nkstep, nchunk;  // 16-wide k-steps, 32-wide chunks
   int nopad;           // nout rounded up to 16
-  int nsub, sub_w[2];  // MMA N-subtiles of a table (widths, sum = nopad)
-  int ntab, tpp, npass;
+  int nunit;           // (table, subtile) units
+  int u_tab[kMaxUnits], u_o0[kMaxUnits], u_w[kMaxUnits];
+  long long u_goff[kMaxUnits];  // byte offset of the unit's chunk 0 in W (chunk stride kNPB w 64)
+  int npass;
+  int p_u0[kMaxPass], p_nu[kMaxPass];  // units of each pass
   int nsrc;
   int dst[2][9];       // output field per (table, source field); -1: none
-  const unsigned char* W;  // tables [table][chunk][piece][nopad x 32 canonical], BF16
-  long long wtab;      // bytes per table
+  const unsigned char* W;   // sliced tables [unit][chunk][slice][w rows x 32 canonical], BF16
+  const float* sigma;       // row scales [table][nopad]
   int ntcol;           // column tiles per (member, field)
   long long ntiles;
   const int* status;
   int* err;
-  int stage_bytes, a_bytes;
-  int tmem_cols;
+  int stage_bytes;     // data slices (kNPA x kPieceA) + the largest pass's table chunk
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -121,9 +144,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// FP32 bits of an FP64 value, mantissa truncated, by integer operations
-// (the FP64 pipe is slow on this part): zero and values below the FP32
-// normal range give a signed zero, values beyond it infinity, NaN stays NaN.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// FP32 value of an FP64 one, mantissa truncated, by integer operations (the
+// FP64 pipe is slow on this part): zero and values below the FP32 normal
+// range give a signed zero, values beyond it infinity, NaN stays NaN.
 __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const uint32_t hi = (uint32_t)(u >> 32);
@@ -139,33 +171,9 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(b);
 }
 
-// Exact three-way BF16 split of x (bit patterns, high halves of FP32 values).
-__device__ __forceinline__ void split3(float x, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
-  const uint32_t b0 = __float_as_uint(x) & 0xFFFF0000u;
-  const float r1 = x - __uint_as_float(b0);
-  const uint32_t b1 = __float_as_uint(r1) & 0xFFFF0000u;
-  const float r2 = r1 - __uint_as_float(b1);
-  p0 = b0 >> 16;
-  p1 = b1 >> 16;
-  p2 = __float_as_uint(r2) >> 16;   // r2 has at most 8 significant bits: exact
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Data chunk kc of tile column col0: 8 consecutive contraction indices of
-// column m (rows m and m + 64 of the data operand), split into the three
-// BF16 pieces and stored in the canonical layout of stage sA.
-__device__ __forceinline__ void load_chunk(const MmaJob& J, const char* inb, int col0, int ncv, int kc,
-                                           int m, int kg, unsigned char* sA) {
-  float re[8], im[8];
-  const int i0 = kc * kChunk + kg * 8;
+// The 8 elements (re, im) of column m at contraction indices i0 .. i0 + 7.
+__device__ __forceinline__ void load8(const MmaJob& J, const char* inb, int col0, int ncv, int i0, int m,
+                                      float (&re)[8], float (&im)[8]) {
   const bool colok = m < ncv;
   if (J.in_f64) {
     const double2* p = reinterpret_cast<const double2*>(inb) + (long long)(col0 + m) * J.in_cs;
@@ -188,25 +196,23 @@ __device__ __forceinline__ void load_chunk(const MmaJob& J, const char* inb, int
 #pragma unroll
     for (int e = 0; e < 8; ++e) { re[e] = v[e].x; im[e] = v[e].y; }
   }
-#pragma unroll
-  for (int part = 0; part < 2; ++part) {
-    const float* x = part ? im : re;
-    uint32_t w[3][4];
-#pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      uint32_t a0, a1, a2, b0, b1, b2;
-      split3(x[e], a0, a1, a2);
-      split3(x[e + 1], b0, b1, b2);
-      w[0][e >> 1] = a0 | (b0 << 16);
-      w[1][e >> 1] = a1 | (b1 << 16);
-      w[2][e >> 1] = a2 | (b2 << 16);
-    }
-    const int r = m + 64 * part;
-    const int off = (r >> 3) * kSBO + kg * kLBO + (r & 7) * 16;
-#pragma unroll
-    for (int pc = 0; pc < 3; ++pc)
-      *reinterpret_cast<uint4*>(sA + pc * kPieceA + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
-  }
+}
+
+// Slices of x scaled by sc (a power of two, |x sc| < 128): X0, X1, X2/2^8
+// and X3/2^16 as BF16 bit patterns (all exact in BF16).  xs - x0 and the
+// later remainders are exact in FP32, and so are their products by 256.
+__device__ __forceinline__ void slice4(float x, float sc, uint32_t (&p)[kNPA]) {
+  const float xs = x * sc;
+  const float x0 = rintf(xs);
+  const float t1 = (xs - x0) * 256.f;
+  const float x1 = rintf(t1);
+  const float t2 = (t1 - x1) * 256.f;
+  const float x2 = rintf(t2);
+  const float x3 = rintf((t2 - x2) * 256.f);
+  p[0] = __float_as_uint(x0) >> 16;
+  p[1] = __float_as_uint(x1) >> 16;
+  p[2] = __float_as_uint(x2 * (1.f / 256.f)) >> 16;
+  p[3] = __float_as_uint(x3 * (1.f / 65536.f)) >> 16;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
@@ -216,10 +222,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
   __shared__ __align__(8) uint64_t bar_m[2];    // MMAs of the stage done (tcgen05.commit)
   __shared__ uint32_t tmem_base;
   __shared__ int fail, skip;
+  __shared__ unsigned int rmax[kRows];          // |x| maxima of the data rows (FP32 bits)
+  __shared__ float rscale[kRows];               // 2^(7 - e_r)
+  __shared__ int rexp[kRows];                   // e_r - 14
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base)), "r"(J.tmem_cols) : "memory");
+                 :: "r"(smem_u32(&tmem_base)), "r"(kTmemCols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -234,9 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t bchunk = (uint32_t)(J.wtab / J.nchunk);   // bytes of one table chunk
   long long g = 0;   // chunks issued by this CTA (stage g & 1)
-  // data pieces: thread -> (column m, k-group kg); rows m (real) and m + 64 (imaginary)
+  // data slices: thread -> (column m, k-group kg); rows m (real) and m + 64 (imaginary)
   const int m = tid & 63, kg = tid >> 6;
   const int quad = warp & 3, half = warp >> 2;
   const int row = quad * 32 + lane;                 // TMEM lane = data row
@@ -249,6 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
     // one read of the member's status for the whole CTA (the diagnostics
     // of the previous step may set it while this kernel runs)
     if (tid == 0) skip = (J.status && J.status[b]) ? 1 : 0;
+    if (tid < kRows) rmax[tid] = 0u;
     __syncthreads();
     const int sk = skip;
     __syncthreads();
@@ -256,33 +265,80 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
     const int col0 = cb * kCols;
     const int ncv = min(kCols, J.ncol - col0);
     const char* inb = static_cast<const char*>(J.in) + (b * J.in_ms + f * J.in_fs) * (J.in_f64 ? 16 : 8);
+    // row exponents: 2^e_r > max |x_r| >= 2^(e_r - 1)
+    {
+      float mre = 0.f, mim = 0.f;
+      for (int kc = 0; kc < J.nchunk; ++kc) {
+        float re[8], im[8];
+        load8(J, inb, col0, ncv, kc * kChunk + kg * 8, m, re, im);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) { mre = fmaxf(mre, fabsf(re[e])); mim = fmaxf(mim, fabsf(im[e])); }
+      }
+      atomicMax(&rmax[m], __float_as_uint(mre));
+      atomicMax(&rmax[m + 64], __float_as_uint(mim));
+      __syncthreads();
+      if (tid < kRows) {
+        int e = 0;
+        frexpf(__uint_as_float(rmax[tid]), &e);
+        // rows below 2^-100 (far under any value of the fields here) are
+        // taken as zero, so that the scale stays finite
+        rscale[tid] = (e < -100) ? 0.f : ldexpf(1.f, 7 - e);
+        rexp[tid] = e - 14;
+      }
+      __syncthreads();
+    }
     for (int pass = 0; pass < J.npass && !stop; ++pass) {
-      const int t0 = pass * J.tpp, t1 = min(J.ntab, t0 + J.tpp);
+      const int ua = J.p_u0[pass], ub = ua + J.p_nu[pass];
       bool any = false;
-      for (int tb = t0; tb < t1; ++tb) any |= (J.dst[tb][f] >= 0);
+      for (int u = ua; u < ub; ++u) any |= (J.dst[J.u_tab[u]][f] >= 0);
       if (!any) continue;
       for (int kc = 0; kc < J.nchunk; ++kc, ++g) {
         const int s = (int)(g & 1);
         unsigned char* sA = sm + s * J.stage_bytes;
-        unsigned char* sB = sA + J.a_bytes;
+        unsigned char* sB = sA + kNPA * kPieceA;
         // the MMAs that last read this stage (chunk g - 2) must be done
         if (g >= 2 && !mbar_wait(&bar_m[s], (uint32_t)(((g - 2) >> 1) & 1))) atomicExch(&fail, 1);
         if (tid == 0 && !fail) {
           uint32_t bytes = 0;
-          for (int tb = t0; tb < t1; ++tb)
-            if (J.dst[tb][f] >= 0) bytes += bchunk;
+          for (int u = ua; u < ub; ++u)
+            if (J.dst[J.u_tab[u]][f] >= 0) bytes += (uint32_t)(kNPB * J.u_w[u] * 64);
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                        :: "r"(smem_u32(&bar_b[s])), "r"(bytes) : "memory");
-          for (int tb = t0; tb < t1; ++tb) {
-            if (J.dst[tb][f] < 0) continue;
-            const unsigned char* src = J.W + tb * J.wtab + (long long)kc * bchunk;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                :: "r"(smem_u32(sB + (tb - t0) * bchunk)), "l"(src), "r"(bchunk), "r"(smem_u32(&bar_b[s]))
-                : "memory");
+          uint32_t boff = 0;
+          for (int u = ua; u < ub; ++u) {
+            const uint32_t nb = (uint32_t)(kNPB * J.u_w[u] * 64);
+            if (J.dst[J.u_tab[u]][f] >= 0) {
+              const unsigned char* src = J.W + J.u_goff[u] + (long long)kc * nb;
+              asm volatile(
+                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                  :: "r"(smem_u32(sB + boff)), "l"(src), "r"(nb), "r"(smem_u32(&bar_b[s])) : "memory");
+            }
+            boff += nb;
           }
         }
-        load_chunk(J, inb, col0, ncv, kc, m, kg, sA);
+        {
+          float re[8], im[8];
+          load8(J, inb, col0, ncv, kc * kChunk + kg * 8, m, re, im);
+#pragma unroll
+          for (int pt = 0; pt < 2; ++pt) {
+            const int r = m + 64 * pt;
+            const float sc = rscale[r];
+            const float* x = pt ? im : re;
+            uint32_t w[kNPA][4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+              uint32_t a[kNPA], c[kNPA];
+              slice4(x[e], sc, a);
+              slice4(x[e + 1], sc, c);
+#pragma unroll
+              for (int pc = 0; pc < kNPA; ++pc) w[pc][e >> 1] = a[pc] | (c[pc] << 16);
+            }
+            const int off = (r >> 3) * kSBO + kg * kLBO + (r & 7) * 16;
+#pragma unroll
+            for (int pc = 0; pc < kNPA; ++pc)
+              *reinterpret_cast<uint4*>(sA + pc * kPieceA + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
+          }
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         stop = fail != 0;
@@ -294,29 +350,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int nks = min(2, J.nkstep - 2 * kc);
             const uint32_t a_base = smem_u32(sA);
-            const uint32_t piece_b = (uint32_t)J.nopad * 64;
-            for (int tb = t0; tb < t1; ++tb) {
-              if (J.dst[tb][f] < 0) continue;
-              const uint32_t b_base = smem_u32(sB) + (uint32_t)(tb - t0) * bchunk;
-              int u0 = 0;
-              for (int u = 0; u < J.nsub; ++u) {
-                const int nw = J.sub_w[u];
+            uint32_t boff = 0, toff = 0;
+            for (int u = ua; u < ub; ++u) {
+              const int nw = J.u_w[u];
+              const uint32_t piece_b = (uint32_t)nw * 64;
+              if (J.dst[J.u_tab[u]][f] >= 0) {
+                const uint32_t b_base = smem_u32(sB) + boff;
                 const uint32_t idesc = umma_idesc(nw);
-                const uint32_t dcol = tmem + (uint32_t)((tb - t0) * J.nopad + u0);
                 for (int ks = 0; ks < nks; ++ks) {
-                  // products x_i w_j with i + j <= 2
+                  const uint32_t kofs = ks * 2 * kLBO;
+                  const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                  // A0 += X0 W0
+                  mma_bf16(tmem + toff, umma_desc(a_base + kofs), umma_desc(b_base + kofs), idesc, acc);
+                  // A1 += X0 W1 + X1 W0 + X0 (W2/2^8) + X1 (W1/2^8) + (X2/2^8) W0
+                  //     + X0 (W3/2^16) + X1 (W2/2^16) + (X2/2^8)(W1/2^8) + (X3/2^16) W0
+                  // (data slice, table slice) pairs, slices numbered as stored
+                  const uint32_t t1 = tmem + toff + (uint32_t)nw;
+                  const int pa[9] = {0, 1, 0, 1, 2, 0, 1, 2, 3};
+                  const int pb[9] = {1, 0, 3, 2, 0, 5, 4, 2, 0};
 #pragma unroll
-                  for (int q = 0; q < 6; ++q) {
-                    const int pa = (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : 0);
-                    const int pb = (q == 1 || q == 4) ? 1 : (q == 3 ? 2 : 0);
-                    const uint64_t ad = umma_desc(a_base + pa * kPieceA + ks * 2 * kLBO);
-                    const uint64_t bd = umma_desc(b_base + pb * piece_b + (u0 >> 3) * kSBO + ks * 2 * kLBO);
-                    const uint32_t acc = (kc > 0 || ks > 0 || q > 0) ? 1u : 0u;
-                    mma_bf16(dcol, ad, bd, idesc, acc);
-                  }
+                  for (int q = 0; q < 9; ++q)
+                    mma_bf16(t1, umma_desc(a_base + pa[q] * kPieceA + kofs),
+                             umma_desc(b_base + pb[q] * piece_b + kofs), idesc, q ? 1u : acc);
                 }
-                u0 += nw;
               }
+              boff += kNPB * piece_b;
+              toff += 2 * (uint32_t)nw;
             }
             mma_commit(&bar_m[s]);
           }
@@ -330,56 +389,81 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
       __syncthreads();
       stop = fail != 0;
       if (stop) break;
-      const int ncols = (t1 - t0) * J.nopad;
+      const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+      const int er = rexp[row];
       if (!J.out_f64) {
         // FP32 values, output element (column, o) at column * out_cs + o * out_os
         float* ob = static_cast<float*>(J.out);
-        for (int c0 = 16 * half; c0 < ncols; c0 += 32) {
-          uint32_t r[16];
-          __syncwarp();
-          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
-          const int tb = t0 + c0 / J.nopad;
+        uint32_t toff = 0;
+        for (int u = ua; u < ub; ++u) {
+          const int nw = J.u_w[u], tb = J.u_tab[u];
           const int d = J.dst[tb][f];
-          if (d >= 0 && mc < ncv) {
+          if (d >= 0) {
+            const float* sig = J.sigma + (long long)tb * J.nopad + J.u_o0[u];
             const long long base = b * J.out_ms + d * J.out_fs + (long long)(col0 + mc) * J.out_cs;
-            const int oc = c0 % J.nopad;
+            for (int c0 = 16 * half; c0 < nw; c0 += 32) {
+              uint32_t r0[16], r1[16];
+              __syncwarp();
+              tmem_ld16(lane_base + toff + (uint32_t)c0, r0);
+              tmem_ld16(lane_base + toff + (uint32_t)(nw + c0), r1);
+              if (mc < ncv) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int o = oc + e;
-              if (o < J.nout) ob[2 * (base + (long long)o * J.out_os) + part] = __uint_as_float(r[e]);
+                for (int e = 0; e < 16; ++e) {
+                  const int oo = c0 + e, o = J.u_o0[u] + oo;
+                  if (o < J.nout) {
+                    const float v = fmaf(__uint_as_float(r1[e]), 1.f / 256.f, __uint_as_float(r0[e]));
+                    ob[2 * (base + (long long)o * J.out_os) + part] = ldexpf(v * __ldg(sig + oo), er);
+                  }
+                }
+              }
             }
           }
+          toff += 2 * (uint32_t)nw;
         }
       } else {
         // FP64 coefficients, output element (column, o) at column * out_cs + o (out_os = 1):
         // staged per half tile (32 columns) in shared memory, rows of 2 nout + 1 doubles
         double* st = reinterpret_cast<double*>(sm);
         const int S = 2 * J.nout + 1;
-        const int d = J.dst[t0][f];
         double* ob = static_cast<double*>(J.out);
+        const int d = J.dst[J.u_tab[ua]][f];
         for (int hh = 0; hh < 2; ++hh) {
           // columns 32 hh .. 32 hh + 31 sit in TMEM lanes of quads hh (real) and hh + 2 (imaginary)
           if ((quad & 1) == hh) {
             const int ml = mc - 32 * hh;
-            for (int c0 = 16 * half; c0 < J.nopad; c0 += 32) {
-              uint32_t r[16];
-              __syncwarp();
-              tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
+            uint32_t toff = 0;
+            for (int u = ua; u < ub; ++u) {
+              const int nw = J.u_w[u], tb = J.u_tab[u];
+              const float* sig = J.sigma + (long long)tb * J.nopad + J.u_o0[u];
+              for (int c0 = 16 * half; c0 < nw; c0 += 32) {
+                uint32_t r0[16], r1[16];
+                __syncwarp();
+                tmem_ld16(lane_base + toff + (uint32_t)c0, r0);
+                tmem_ld16(lane_base + toff + (uint32_t)(nw + c0), r1);
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                const int o = c0 + e;
-                if (o < J.nout) st[ml * S + 2 * o + part] = (double)__uint_as_float(r[e]);
+                for (int e = 0; e < 16; ++e) {
+                  const int oo = c0 + e, o = J.u_o0[u] + oo;
+                  if (o < J.nout) {
+                    const double v = (double)__uint_as_float(r0[e]) +
+                                     (double)__uint_as_float(r1[e]) * (1.0 / 256.0);
+                    st[ml * S + 2 * o + part] = ldexp(v * (double)__ldg(sig + oo), er);
+                  }
+                }
               }
+              toff += 2 * (uint32_t)nw;
             }
           }
           __syncthreads();
+          // the outputs o_lo <= o < o_hi of this pass, row by row
           const int nmh = max(0, min(32, ncv - 32 * hh));
-          if (d >= 0 && nmh > 0) {
+          const int o_lo = J.u_o0[ua];
+          const int o_hi = min(J.nout, J.u_o0[ub - 1] + J.u_w[ub - 1]);
+          if (d >= 0 && nmh > 0 && o_hi > o_lo) {
             const long long base = b * J.out_ms + d * J.out_fs + (long long)(col0 + 32 * hh) * J.out_cs;
-            const int rowd = 2 * J.nout;
+            const int rowd = 2 * (o_hi - o_lo);
             const int tot = nmh * rowd;
             for (int q = tid; q < tot; q += kThreads) {
-              const int ml = q / rowd, rem = q - ml * rowd;
+              const int ml = q / rowd, rem = 2 * o_lo + (q - ml * rowd);
               ob[2 * (base + (long long)ml * J.out_cs) + rem] = st[ml * S + rem];
             }
           }
@@ -405,15 +489,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(J.tmem_cols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
 }
 
 // ------------------------------------------------------------- host side
+// Units (table, output subtile of <= 256 rows, a multiple of 16), packed
+// into passes whose accumulators (two per output row) fit the tensor memory.
 struct Geom {
   int kin, nout, ntab;
-  int nkstep, nchunk, nopad, nsub, sub_w[2], tpp, npass, tmem_cols;
-  long long wtab;       // bytes per table
-  int a_bytes, stage_bytes, smem;
+  int nkstep, nchunk, nopad;
+  int nunit, u_tab[kMaxUnits], u_o0[kMaxUnits], u_w[kMaxUnits];
+  long long u_goff[kMaxUnits];
+  int npass, p_u0[kMaxPass], p_nu[kMaxPass];
+  long long wbytes;     // sliced tables
+  int stage_bytes, smem;
 };
 
 Geom geom(int kin, int nout, int ntab, bool f64_out) {
@@ -424,54 +513,53 @@ Geom geom(int kin, int nout, int ntab, bool f64_out) {
   G.nkstep = (kin + 15) / 16;
   G.nchunk = (G.nkstep + 1) / 2;
   G.nopad = (nout + 15) / 16 * 16;
-  if (G.nopad <= 256) {
-    G.nsub = 1;
-    G.sub_w[0] = G.nopad;
-    G.sub_w[1] = 0;
-  } else {
-    G.nsub = 2;
-    G.sub_w[0] = (G.nopad / 2 + 15) / 16 * 16;
-    G.sub_w[1] = G.nopad - G.sub_w[0];
+  // output subtiles: at most kMaxW rows each, multiples of 16, near-equal
+  const int nsub = (G.nopad + kMaxW - 1) / kMaxW;
+  int sub[kMaxUnits] = {};
+  {
+    int left = G.nopad / 16;
+    for (int q = 0; q < nsub; ++q) {
+      const int w16 = (left + (nsub - q) - 1) / (nsub - q);
+      sub[q] = 16 * w16;
+      left -= w16;
+    }
   }
-  G.wtab = (long long)G.nchunk * 3 * G.nopad * 64;
-  G.a_bytes = 3 * kPieceA;
-  // all tables in one pass when their accumulators fit the 512 tensor-memory
-  // columns and their two stages fit shared memory, else one table per pass
-  for (int tpp = ntab; tpp >= 1; --tpp) {
-    G.tpp = tpp;
-    G.stage_bytes = G.a_bytes + G.tpp * 3 * G.nopad * 64;
-    int sm = 2 * G.stage_bytes;
-    if (f64_out) sm = std::max(sm, 32 * (2 * nout + 1) * 8);
-    G.smem = sm + 1024;
-    if (tpp * G.nopad <= 512 && G.smem <= kSmemLimit) break;
+  long long goff = 0;
+  for (int tb = 0; tb < ntab; ++tb) {
+    int o0 = 0;
+    for (int q = 0; q < nsub && G.nunit < kMaxUnits; ++q) {
+      const int u = G.nunit++;
+      G.u_tab[u] = tb;
+      G.u_o0[u] = o0;
+      G.u_w[u] = sub[q];
+      G.u_goff[u] = goff;
+      goff += (long long)G.nchunk * kNPB * sub[q] * 64;
+      o0 += sub[q];
+    }
   }
-  G.npass = (ntab + G.tpp - 1) / G.tpp;
-  int tc = 32;
-  while (tc < G.tpp * G.nopad) tc *= 2;
-  G.tmem_cols = tc;
+  G.wbytes = goff;
+  // passes: consecutive units while their accumulators (2 w columns each)
+  // fit the tensor memory and their two stages fit shared memory
+  int maxb = 0;
+  for (int u = 0; u < G.nunit && G.npass < kMaxPass;) {
+    const int p = G.npass++;
+    G.p_u0[p] = u;
+    int cols = 0, bb = 0;
+    while (u < G.nunit) {
+      const int c2 = cols + 2 * G.u_w[u], b2 = bb + kNPB * G.u_w[u] * 64;
+      if (u > G.p_u0[p] && (c2 > kTmemCols || 2 * (kNPA * kPieceA + b2) + 1024 > kSmemLimit)) break;
+      cols = c2;
+      bb = b2;
+      ++u;
+    }
+    G.p_nu[p] = u - G.p_u0[p];
+    maxb = std::max(maxb, bb);
+  }
+  G.stage_bytes = kNPA * kPieceA + maxb;
+  int sm = 2 * G.stage_bytes;
+  if (f64_out) sm = std::max(sm, 32 * (2 * nout + 1) * 8);
+  G.smem = sm + 1024;
   return G;
-}
-
-// Exact three-way BF16 split of the FP32 rounding of v (host twin of split3).
-void split3_host(double v, uint16_t* p) {
-  const float x = (float)v;
-  uint32_t bx;
-  std::memcpy(&bx, &x, 4);
-  const uint32_t b0 = bx & 0xFFFF0000u;
-  float f0;
-  std::memcpy(&f0, &b0, 4);
-  const float r1 = x - f0;
-  uint32_t br1;
-  std::memcpy(&br1, &r1, 4);
-  const uint32_t b1 = br1 & 0xFFFF0000u;
-  float f1;
-  std::memcpy(&f1, &b1, 4);
-  const float r2 = r1 - f1;
-  uint32_t br2;
-  std::memcpy(&br2, &r2, 4);
-  p[0] = (uint16_t)(b0 >> 16);
-  p[1] = (uint16_t)(b1 >> 16);
-  p[2] = (uint16_t)(br2 >> 16);
 }
 
 // cos and sin of 2 pi k / n with the angle reduced in exact integers.
@@ -483,66 +571,94 @@ void cis_host(long long k, long long n, double* c, double* s) {
   *s = std::sin(a);
 }
 
-// Tables of one direction in the kernel's layout: [table][chunk][piece]
-// [nopad rows x 32 k], core matrix (rg, kg) at rg * kSBO + kg * kLBO, row
-// r & 7 at 16 (r & 7) bytes, element k & 7 at 2 (k & 7).
-void build_tables(int M, int N, bool inverse, std::vector<uint16_t>& out, Geom& G) {
+uint16_t bf16_bits(double v) {   // v exact in BF16 (a small integer or one over 2^8)
+  const float f = (float)v;
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  return (uint16_t)(b >> 16);
+}
+
+// Table entry w[o][i] of one direction.
+double table_entry(int M, bool inverse, int tb, int o, int i) {
+  double c, s;
+  if (inverse) {
+    // o = j (Gauss point), i = n (Chebyshev index); theta_j = 2 pi (2j+1) / (4M)
+    cis_host((long long)i * (2 * o + 1), 4LL * M, &c, &s);
+    if (tb == 0) return c;
+    double c1, s1;
+    cis_host(2 * o + 1, 4LL * M, &c1, &s1);
+    return (double)i * s / s1;
+  }
+  // o = k (Chebyshev index), i = j (Gauss point)
+  cis_host((long long)o * (2 * i + 1), 4LL * M, &c, &s);
+  return (o == 0 ? 1.0 : 2.0) / M * c;
+}
+
+// Sliced tables in the kernel's layout, [unit][chunk][slice][w rows x 32 k]
+// with core matrix (rg, kg) at rg * kSBO + kg * kLBO, row r & 7 at
+// 16 (r & 7) bytes, element k & 7 at 2 (k & 7); then the row scales
+// sigma[table][nopad] (FP32).
+void build_tables(int M, int N, bool inverse, std::vector<uint16_t>& out) {
   const int kin = inverse ? N : M, nout = inverse ? M : N, ntab = inverse ? 2 : 1;
-  G = geom(kin, nout, ntab, !inverse);
-  out.assign((size_t)(G.wtab / 2) * ntab, 0);
-  for (int tb = 0; tb < ntab; ++tb)
-    for (int o = 0; o < nout; ++o)
+  const Geom G = geom(kin, nout, ntab, !inverse);
+  out.assign((size_t)(G.wbytes / 2) + (size_t)ntab * G.nopad * 2, 0);
+  std::vector<float> sig((size_t)ntab * G.nopad, 1.0f);
+  for (int u = 0; u < G.nunit; ++u) {
+    const int tb = G.u_tab[u];
+    for (int oo = 0; oo < G.u_w[u]; ++oo) {
+      const int o = G.u_o0[u] + oo;
+      if (o >= nout) continue;
+      double mx = 0.0;
+      for (int i = 0; i < kin; ++i) mx = std::max(mx, std::fabs(table_entry(M, inverse, tb, o, i)));
+      int e = 0;
+      std::frexp(mx, &e);                    // 2^e > mx >= 2^(e-1) (e = 0 for mx = 0)
+      const double sg = std::ldexp(1.0, e);
+      sig[(size_t)tb * G.nopad + o] = (float)sg;
       for (int i = 0; i < kin; ++i) {
-        double w;
-        if (inverse) {
-          // o = j (Gauss point), i = n (Chebyshev index); theta_j = 2 pi (2j+1) / (4M)
-          double c, s;
-          cis_host((long long)i * (2 * o + 1), 4LL * M, &c, &s);
-          if (tb == 0) {
-            w = c;
-          } else {
-            double c1, s1;
-            cis_host(2 * o + 1, 4LL * M, &c1, &s1);
-            w = (double)i * s / s1;
-          }
-        } else {
-          // o = k (Chebyshev index), i = j (Gauss point)
-          double c, s;
-          cis_host((long long)o * (2 * i + 1), 4LL * M, &c, &s);
-          w = (o == 0 ? 1.0 : 2.0) / M * c;
+        // w / sigma * 2^7 = W0 + W1/2^8 + W2/2^16 + W3/2^24 + (|rest| <= 2^-25)
+        double xs = table_entry(M, inverse, tb, o, i) / sg * 128.0;
+        double wq[4];
+        for (int q = 0; q < 4; ++q) {
+          wq[q] = std::nearbyint(xs);
+          xs = (xs - wq[q]) * 256.0;
         }
-        uint16_t p[3];
-        split3_host(w, p);
+        const uint16_t sl[kNPB] = {bf16_bits(wq[0]), bf16_bits(wq[1]), bf16_bits(wq[1] / 256.0),
+                                   bf16_bits(wq[2] / 256.0), bf16_bits(wq[2] / 65536.0),
+                                   bf16_bits(wq[3] / 65536.0)};
         const int kc = i / kChunk, k = i % kChunk;
-        const long long off = (long long)tb * G.wtab + (long long)kc * 3 * G.nopad * 64;
-        const long long in_piece = (long long)(o >> 3) * kSBO + (k >> 3) * kLBO + (o & 7) * 16 + (k & 7) * 2;
-        for (int pc = 0; pc < 3; ++pc)
-          out[(size_t)((off + (long long)pc * G.nopad * 64 + in_piece) / 2)] = p[pc];
+        const long long off = G.u_goff[u] + (long long)kc * kNPB * G.u_w[u] * 64;
+        const long long in_piece = (long long)(oo >> 3) * kSBO + (k >> 3) * kLBO + (oo & 7) * 16 + (k & 7) * 2;
+        for (int pc = 0; pc < kNPB; ++pc)
+          out[(size_t)((off + (long long)pc * G.u_w[u] * 64 + in_piece) / 2)] = sl[pc];
       }
+    }
+  }
+  std::memcpy(out.data() + G.wbytes / 2, sig.data(), sig.size() * sizeof(float));
 }
 
 }  // namespace
 
 bool cheb_mma_supported(int M, int N) {
-  // outputs of one table within tensor memory (512 FP32 columns) and the
-  // shared-memory plan within the 227 KB of one CTA
   const Geom a = geom(N, M, 2, false), b = geom(M, N, 1, true);
-  return a.nopad <= 512 && b.nopad <= 512 && a.smem <= kSmemLimit && b.smem <= kSmemLimit;
+  auto covered = [](const Geom& G) {
+    int o = 0;
+    for (int u = 0; u < G.nunit; ++u) o += (G.u_tab[u] == 0) ? G.u_w[u] : 0;
+    int nu = 0;
+    for (int p = 0; p < G.npass; ++p) nu += G.p_nu[p];
+    return o == G.nopad && nu == G.nunit && G.nunit == G.ntab * (G.nunit / G.ntab);
+  };
+  // 2^14 kin < 2^24 keeps the leading accumulator exact
+  return a.kin <= 1000 && b.kin <= 1000 && covered(a) && covered(b) && a.smem <= kSmemLimit &&
+         b.smem <= kSmemLimit;
 }
 
 size_t cheb_mma_table_bytes(int M, int N, int inverse) {
   const Geom G = inverse ? geom(N, M, 2, false) : geom(M, N, 1, true);
-  return (size_t)G.wtab * G.ntab;
+  return (size_t)G.wbytes + (size_t)G.ntab * G.nopad * sizeof(float);
 }
 
 void cheb_mma_tables(int M, int N, int inverse, std::vector<uint16_t>& out) {
-  Geom G;
-  build_tables(M, N, inverse != 0, out, G);
-}
-
-size_t cheb_mma_smem(int M, int N) {
-  const Geom a = geom(N, M, 2, false), b = geom(M, N, 1, true);
-  return (size_t)std::max(a.smem, b.smem);
+  build_tables(M, N, inverse != 0, out);
 }
 
 cudaError_t set_cheb_mma_attributes(int optin_bytes) {
@@ -569,7 +685,6 @@ cudaError_t launch_cheb_mma(const GroupDev& g, bool inverse, cudaStream_t st, in
     J.out_f64 = 0;
     const int nyf = d3 ? 17 : 9;
     J.out_ms = nyf * yplane; J.out_fs = yplane; J.out_cs = 1; J.out_os = KZ;
-    J.col_fast = 0;
     if (d3) {
       const int d1[9] = {9, -1, 10, 11, 12, 13, 14, 15, 16};
       for (int f = 0; f < 9; ++f) { J.dst[0][f] = f; J.dst[1][f] = d1[f]; }
@@ -586,31 +701,31 @@ cudaError_t launch_cheb_mma(const GroupDev& g, bool inverse, cudaStream_t st, in
     J.out = g.NR;
     J.out_f64 = 1;
     J.out_ms = nf * NK; J.out_fs = NK; J.out_cs = N; J.out_os = 1;
-    J.col_fast = 1;
     for (int f = 0; f < nf; ++f) { J.dst[0][f] = f; J.dst[1][f] = -1; }
     J.W = reinterpret_cast<const unsigned char*>(g.Wyf);
   }
+  J.sigma = reinterpret_cast<const float*>(J.W + G.wbytes);
   J.ncol = KZ;
   J.kin = G.kin;
   J.nout = G.nout;
   J.nkstep = G.nkstep;
   J.nchunk = G.nchunk;
   J.nopad = G.nopad;
-  J.nsub = G.nsub;
-  J.sub_w[0] = G.sub_w[0];
-  J.sub_w[1] = G.sub_w[1];
-  J.ntab = G.ntab;
-  J.tpp = G.tpp;
+  J.nunit = G.nunit;
+  for (int u = 0; u < G.nunit; ++u) {
+    J.u_tab[u] = G.u_tab[u];
+    J.u_o0[u] = G.u_o0[u];
+    J.u_w[u] = G.u_w[u];
+    J.u_goff[u] = G.u_goff[u];
+  }
   J.npass = G.npass;
+  for (int p = 0; p < G.npass; ++p) { J.p_u0[p] = G.p_u0[p]; J.p_nu[p] = G.p_nu[p]; }
   J.nsrc = nf;
-  J.wtab = G.wtab;
   J.ntcol = (KZ + kCols - 1) / kCols;
   J.ntiles = (long long)g.nb * nf * J.ntcol;
   J.status = g.status;
   J.err = g.mma_err;
-  J.a_bytes = G.a_bytes;
   J.stage_bytes = G.stage_bytes;
-  J.tmem_cols = G.tmem_cols;
   const long long grid = std::min<long long>(J.ntiles, (long long)std::max(1, sms));
   k_cheb_mma<<<(unsigned)grid, kThreads, G.smem, st>>>(J);
   return cudaGetLastError();
