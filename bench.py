@@ -73,9 +73,10 @@ def parse():
     ap.add_argument("--only", default=None,
                     help="run one workload alone (3d_fp64, 3d_mixed, 3d_fp64_large, "
                          "3d_mixed_large, ensemble_mixed, ensemble_fp64, 2d_NXxNY[_mixed]: one "
-                         "shape of the 2D sweep, three seeds) and print its line, "
-                         "for profiling; or midplane_stats: mixed vs FP64 mid-plane statistics "
-                         "of the 3D workload over --steps steps")
+                         "shape of the 2D sweep, three seeds; 'mixedfft' in place of 'mixed' "
+                         "selects the FP32-FFT Chebyshev passes instead of the tensor-core ones) "
+                         "and print its line, for profiling; or midplane_stats: mixed vs FP64 "
+                         "mid-plane statistics of the 3D workload over --steps steps")
     return ap.parse_args()
 
 
@@ -344,7 +345,7 @@ def only_workload(args):
     name = args.only
     if name == "midplane_stats":
         return midplane_stats(args)
-    prec = P.PTT_MIXED if "mixed" in name else P.PTT_FP64
+    prec = (P.PTT_MIXED_FFT if "mixedfft" in name else P.PTT_MIXED if "mixed" in name else P.PTT_FP64)
     if name.startswith("3d"):
         nx, ny, nz = I.CHANNEL3D_LARGE if name.endswith("large") else I.CHANNEL3D
         params = [P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=prec, **I.PAPER)]
