@@ -55,6 +55,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "ptt_internal.h"
@@ -102,6 +103,7 @@ struct MmaJob {
   const int* status;
   int* err;
   int stage_bytes;     // data slices (kNPA x kPieceA) + the largest pass's table chunk
+  int split;           // 1: one work item per (tile, pass)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -171,30 +173,39 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(b);
 }
 
-// The 8 elements (re, im) of column m at contraction indices i0 .. i0 + 7.
-__device__ __forceinline__ void load8(const MmaJob& J, const char* inb, int col0, int ncv, int i0, int m,
-                                      float (&re)[8], float (&im)[8]) {
+// Raw input of one thread for one chunk: 8 complex elements of column m at
+// contraction indices i0 .. i0 + 7 (zero outside the field), loaded ahead of
+// their use so that the next chunk's loads overlap this chunk's work.
+template <bool F64> struct Raw;
+template <> struct Raw<true> { double2 v[8]; };
+template <> struct Raw<false> { float2 v[8]; };
+
+template <bool F64>
+__device__ __forceinline__ void load_raw(const MmaJob& J, const char* inb, int col0, int ncv, int i0, int m,
+                                         Raw<F64>& r) {
+  using C = decltype(r.v[0]);
+  using CT = typename std::remove_reference<C>::type;
   const bool colok = m < ncv;
-  if (J.in_f64) {
-    const double2* p = reinterpret_cast<const double2*>(inb) + (long long)(col0 + m) * J.in_cs;
-    double2 v[8];
+  const CT* p = reinterpret_cast<const CT*>(inb) + (long long)(col0 + m) * J.in_cs;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int i = i0 + e;
-      v[e] = (colok && i < J.kin) ? __ldg(p + (long long)i * J.in_is) : make_double2(0.0, 0.0);
+  for (int e = 0; e < 8; ++e) {
+    const int i = i0 + e;
+    CT z{};
+    r.v[e] = (colok && i < J.kin) ? __ldg(p + (long long)i * J.in_is) : z;
+  }
+}
+
+template <bool F64>
+__device__ __forceinline__ void raw_values(const Raw<F64>& r, float (&re)[8], float (&im)[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    if constexpr (F64) {
+      re[e] = f64_to_f32_trunc(r.v[e].x);
+      im[e] = f64_to_f32_trunc(r.v[e].y);
+    } else {
+      re[e] = r.v[e].x;
+      im[e] = r.v[e].y;
     }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) { re[e] = f64_to_f32_trunc(v[e].x); im[e] = f64_to_f32_trunc(v[e].y); }
-  } else {
-    const float2* p = reinterpret_cast<const float2*>(inb) + (long long)(col0 + m) * J.in_cs;
-    float2 v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int i = i0 + e;
-      v[e] = (colok && i < J.kin) ? __ldg(p + (long long)i * J.in_is) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) { re[e] = v[e].x; im[e] = v[e].y; }
   }
 }
 
@@ -215,6 +226,7 @@ __device__ __forceinline__ void slice4(float x, float sc, uint32_t (&p)[kNPA]) {
   p[3] = __float_as_uint(x3 * (1.f / 65536.f)) >> 16;
 }
 
+template <bool F64>
 __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -250,7 +262,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
   const int row = quad * 32 + lane;                 // TMEM lane = data row
   const int mc = row & 63, part = row >> 6;         // tile column, real / imaginary part
   bool stop = false;
-  for (long long t = blockIdx.x; t < J.ntiles && !stop; t += gridDim.x) {
+  // work items: tiles, or (tile, pass) pairs when tiles are too few to fill the GPU
+  const long long nitems = J.ntiles * (J.split ? J.npass : 1);
+  for (long long it = blockIdx.x; it < nitems && !stop; it += gridDim.x) {
+    const long long t = J.split ? it / J.npass : it;
+    const int pass0 = J.split ? (int)(it % J.npass) : 0;
+    const int pass1 = J.split ? pass0 + 1 : J.npass;
     const int cb = (int)(t % J.ntcol);
     const long long bf = t / J.ntcol;
     const int f = (int)(bf % J.nsrc), b = (int)(bf / J.nsrc);
@@ -262,15 +279,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
     const int sk = skip;
     __syncthreads();
     if (sk) continue;
+    bool any = false;
+    for (int pass = pass0; pass < pass1; ++pass)
+      for (int u = J.p_u0[pass]; u < J.p_u0[pass] + J.p_nu[pass]; ++u) any |= (J.dst[J.u_tab[u]][f] >= 0);
+    if (!any) continue;
     const int col0 = cb * kCols;
     const int ncv = min(kCols, J.ncol - col0);
-    const char* inb = static_cast<const char*>(J.in) + (b * J.in_ms + f * J.in_fs) * (J.in_f64 ? 16 : 8);
-    // row exponents: 2^e_r > max |x_r| >= 2^(e_r - 1)
+    const char* inb = static_cast<const char*>(J.in) + (b * J.in_ms + f * J.in_fs) * (F64 ? 16 : 8);
+    // row exponents: 2^e_r > max |x_r| >= 2^(e_r - 1); two chunks in flight
     {
       float mre = 0.f, mim = 0.f;
-      for (int kc = 0; kc < J.nchunk; ++kc) {
+      for (int kc = 0; kc < J.nchunk; kc += 2) {
+        Raw<F64> r0, r1;
+        load_raw<F64>(J, inb, col0, ncv, kc * kChunk + kg * 8, m, r0);
+        load_raw<F64>(J, inb, col0, ncv, (kc + 1) * kChunk + kg * 8, m, r1);
         float re[8], im[8];
-        load8(J, inb, col0, ncv, kc * kChunk + kg * 8, m, re, im);
+        raw_values<F64>(r0, re, im);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) { mre = fmaxf(mre, fabsf(re[e])); mim = fmaxf(mim, fabsf(im[e])); }
+        raw_values<F64>(r1, re, im);
 #pragma unroll
         for (int e = 0; e < 8; ++e) { mre = fmaxf(mre, fabsf(re[e])); mim = fmaxf(mim, fabsf(im[e])); }
       }
@@ -287,11 +314,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
       }
       __syncthreads();
     }
-    for (int pass = 0; pass < J.npass && !stop; ++pass) {
+    for (int pass = pass0; pass < pass1 && !stop; ++pass) {
       const int ua = J.p_u0[pass], ub = ua + J.p_nu[pass];
-      bool any = false;
-      for (int u = ua; u < ub; ++u) any |= (J.dst[J.u_tab[u]][f] >= 0);
-      if (!any) continue;
+      bool anyp = false;
+      for (int u = ua; u < ub; ++u) anyp |= (J.dst[J.u_tab[u]][f] >= 0);
+      if (!anyp) continue;
+      Raw<F64> cur;
+      load_raw<F64>(J, inb, col0, ncv, kg * 8, m, cur);
       for (int kc = 0; kc < J.nchunk; ++kc, ++g) {
         const int s = (int)(g & 1);
         unsigned char* sA = sm + s * J.stage_bytes;
@@ -317,8 +346,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
           }
         }
         {
+          // this chunk's values, then the next chunk's loads go out before
+          // this chunk is sliced, stored and multiplied
           float re[8], im[8];
-          load8(J, inb, col0, ncv, kc * kChunk + kg * 8, m, re, im);
+          raw_values<F64>(cur, re, im);
+          if (kc + 1 < J.nchunk) load_raw<F64>(J, inb, col0, ncv, (kc + 1) * kChunk + kg * 8, m, cur);
 #pragma unroll
           for (int pt = 0; pt < 2; ++pt) {
             const int r = m + 64 * pt;
@@ -662,7 +694,11 @@ void cheb_mma_tables(int M, int N, int inverse, std::vector<uint16_t>& out) {
 }
 
 cudaError_t set_cheb_mma_attributes(int optin_bytes) {
-  return cudaFuncSetAttribute(k_cheb_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, optin_bytes - 4096);
+  cudaError_t e = cudaFuncSetAttribute(k_cheb_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       optin_bytes - 4096);
+  if (!e) e = cudaFuncSetAttribute(k_cheb_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   optin_bytes - 4096);
+  return e;
 }
 
 // One Chebyshev pass of a mixed group on the tensor cores (see the file
@@ -726,8 +762,12 @@ cudaError_t launch_cheb_mma(const GroupDev& g, bool inverse, cudaStream_t st, in
   J.status = g.status;
   J.err = g.mma_err;
   J.stage_bytes = G.stage_bytes;
-  const long long grid = std::min<long long>(J.ntiles, (long long)std::max(1, sms));
-  k_cheb_mma<<<(unsigned)grid, kThreads, G.smem, st>>>(J);
+  // tiles too few for two waves over the GPU: one work item per (tile, pass)
+  J.split = (J.npass > 1 && J.ntiles < 2LL * std::max(1, sms)) ? 1 : 0;
+  const long long items = J.ntiles * (J.split ? J.npass : 1);
+  const long long grid = std::min<long long>(items, (long long)std::max(1, sms));
+  if (inverse) k_cheb_mma<true><<<(unsigned)grid, kThreads, G.smem, st>>>(J);
+  else k_cheb_mma<false><<<(unsigned)grid, kThreads, G.smem, st>>>(J);
   return cudaGetLastError();
 }
 
