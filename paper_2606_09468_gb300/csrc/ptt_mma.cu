@@ -75,7 +75,7 @@ constexpr int kMaxW = 208;                 // widest output subtile (two stages 
 constexpr int kLBO = 128;                  // core-matrix stride along K (bytes)
 constexpr int kSBO = 512;                  // core-matrix stride along rows (4 core matrices of K)
 constexpr long long kSpin = 1LL << 26;     // iteration limit of every wait
-constexpr int kSmemLimit = 227 * 1024 - 4096;  // dynamic shared memory of one CTA
+constexpr int kSmemLimit = 227 * 1024 - 6144;  // dynamic shared memory of one CTA (6 KB static)
 constexpr int kTmemCols = 512;
 constexpr int kMaxUnits = 8;               // (table, subtile) units
 constexpr int kMaxPass = 8;
@@ -94,7 +94,7 @@ struct MmaJob {
   long long u_goff[kMaxUnits];  // byte offset of the unit's chunk 0 in W (chunk stride kNPB w 64)
   int npass;
   int p_u0[kMaxPass], p_nu[kMaxPass];  // units of each pass
-  int nsrc;
+  int nsrc, ntab;
   int dst[2][9];       // output field per (table, source field); -1: none
   const unsigned char* W;   // sliced tables [unit][chunk][slice][w rows x 32 canonical], BF16
   const float* sigma;       // row scales [table][nopad]
@@ -146,13 +146,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// Both accumulators of 16 output columns of this warp's 32 TMEM lanes (one
+// wait for the two loads).
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, uint32_t (&r)[16], uint32_t (&s)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]),
+        "=r"(s[8]), "=r"(s[9]), "=r"(s[10]), "=r"(s[11]), "=r"(s[12]), "=r"(s[13]), "=r"(s[14]), "=r"(s[15])
+      : "r"(tb));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// FP64 value of an FP32 one by integer operations (exact for normal values;
+// zero and subnormals give a signed zero, infinities stay, NaN is NaN).
+__device__ __forceinline__ double f32_to_f64_bits(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  unsigned long long r;
+  if (e == 0u) r = (unsigned long long)sign << 32;
+  else if (e == 255u) r = ((unsigned long long)(sign | 0x7FF00000u | (m ? 0x80000u : 0u))) << 32;
+  else r = ((unsigned long long)(sign | ((e + 896u) << 20) | (m >> 3)) << 32) | ((unsigned long long)(m & 7u) << 29);
+  return __longlong_as_double((long long)r);
 }
 
 // FP32 value of an FP64 one, mantissa truncated, by integer operations (the
@@ -236,7 +255,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
   __shared__ int fail, skip;
   __shared__ unsigned int rmax[kRows];          // |x| maxima of the data rows (FP32 bits)
   __shared__ float rscale[kRows];               // 2^(7 - e_r)
-  __shared__ int rexp[kRows];                   // e_r - 14
+  __shared__ float rout[kRows];                 // 2^(e_r - 14)
+  __shared__ float ssig[2 * 512];               // table row scales sigma[table][o]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -251,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
     asm volatile("fence.mbarrier_init.release.cluster;");
     fail = 0;
   }
+  for (int i = tid; i < J.ntab * J.nopad; i += kThreads) ssig[i] = __ldg(J.sigma + i);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -286,20 +307,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
     const int col0 = cb * kCols;
     const int ncv = min(kCols, J.ncol - col0);
     const char* inb = static_cast<const char*>(J.in) + (b * J.in_ms + f * J.in_fs) * (F64 ? 16 : 8);
-    // row exponents: 2^e_r > max |x_r| >= 2^(e_r - 1); two chunks in flight
+    // row exponents: 2^e_r > max |x_r| >= 2^(e_r - 1), from the largest
+    // magnitude's bit pattern (two chunks in flight)
     {
       float mre = 0.f, mim = 0.f;
       for (int kc = 0; kc < J.nchunk; kc += 2) {
         Raw<F64> r0, r1;
         load_raw<F64>(J, inb, col0, ncv, kc * kChunk + kg * 8, m, r0);
         load_raw<F64>(J, inb, col0, ncv, (kc + 1) * kChunk + kg * 8, m, r1);
-        float re[8], im[8];
-        raw_values<F64>(r0, re, im);
+        if constexpr (F64) {
+          unsigned long long ar = 0ull, ai = 0ull;
+          const unsigned long long mask = 0x7FFFFFFFFFFFFFFFull;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) { mre = fmaxf(mre, fabsf(re[e])); mim = fmaxf(mim, fabsf(im[e])); }
-        raw_values<F64>(r1, re, im);
+          for (int e = 0; e < 8; ++e) {
+            ar = max(ar, (unsigned long long)__double_as_longlong(r0.v[e].x) & mask);
+            ai = max(ai, (unsigned long long)__double_as_longlong(r0.v[e].y) & mask);
+            ar = max(ar, (unsigned long long)__double_as_longlong(r1.v[e].x) & mask);
+            ai = max(ai, (unsigned long long)__double_as_longlong(r1.v[e].y) & mask);
+          }
+          mre = fmaxf(mre, f64_to_f32_trunc(__longlong_as_double((long long)ar)));
+          mim = fmaxf(mim, f64_to_f32_trunc(__longlong_as_double((long long)ai)));
+        } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) { mre = fmaxf(mre, fabsf(re[e])); mim = fmaxf(mim, fabsf(im[e])); }
+          for (int e = 0; e < 8; ++e) {
+            mre = fmaxf(mre, fmaxf(fabsf(r0.v[e].x), fabsf(r1.v[e].x)));
+            mim = fmaxf(mim, fmaxf(fabsf(r0.v[e].y), fabsf(r1.v[e].y)));
+          }
+        }
       }
       atomicMax(&rmax[m], __float_as_uint(mre));
       atomicMax(&rmax[m + 64], __float_as_uint(mim));
@@ -310,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
         // rows below 2^-100 (far under any value of the fields here) are
         // taken as zero, so that the scale stays finite
         rscale[tid] = (e < -100) ? 0.f : ldexpf(1.f, 7 - e);
-        rexp[tid] = e - 14;
+        rout[tid] = ldexpf(1.f, max(e, -100) - 14);
       }
       __syncthreads();
     }
@@ -422,31 +456,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
       stop = fail != 0;
       if (stop) break;
       const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-      const int er = rexp[row];
+      // out = (A0 + A1/2^8) sigma_o 2^(e_r - 14), both scales powers of two
+      const float so = rout[row];
       if (!J.out_f64) {
         // FP32 values, output element (column, o) at column * out_cs + o * out_os
         float* ob = static_cast<float*>(J.out);
+        const long long ostep = 2 * J.out_os;
         uint32_t toff = 0;
         for (int u = ua; u < ub; ++u) {
           const int nw = J.u_w[u], tb = J.u_tab[u];
           const int d = J.dst[tb][f];
           if (d >= 0) {
-            const float* sig = J.sigma + (long long)tb * J.nopad + J.u_o0[u];
+            const float* sig = ssig + tb * J.nopad + J.u_o0[u];
             const long long base = b * J.out_ms + d * J.out_fs + (long long)(col0 + mc) * J.out_cs;
             for (int c0 = 16 * half; c0 < nw; c0 += 32) {
               uint32_t r0[16], r1[16];
               __syncwarp();
-              tmem_ld16(lane_base + toff + (uint32_t)c0, r0);
-              tmem_ld16(lane_base + toff + (uint32_t)(nw + c0), r1);
+              tmem_ld16x2(lane_base + toff + (uint32_t)c0, lane_base + toff + (uint32_t)(nw + c0), r0, r1);
               if (mc < ncv) {
+                const int o0 = J.u_o0[u] + c0;
+                float* op = ob + 2 * (base + (long long)o0 * J.out_os) + part;
+                const int ne = min(16, J.nout - o0);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                  const int oo = c0 + e, o = J.u_o0[u] + oo;
-                  if (o < J.nout) {
-                    const float v = fmaf(__uint_as_float(r1[e]), 1.f / 256.f, __uint_as_float(r0[e]));
-                    ob[2 * (base + (long long)o * J.out_os) + part] = ldexpf(v * __ldg(sig + oo), er);
-                  }
-                }
+                for (int e = 0; e < 16; ++e)
+                  if (e < ne)
+                    op[e * ostep] = fmaf(__uint_as_float(r1[e]), 1.f / 256.f, __uint_as_float(r0[e])) *
+                                    (sig[c0 + e] * so);
               }
             }
           }
@@ -466,21 +501,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
             uint32_t toff = 0;
             for (int u = ua; u < ub; ++u) {
               const int nw = J.u_w[u], tb = J.u_tab[u];
-              const float* sig = J.sigma + (long long)tb * J.nopad + J.u_o0[u];
+              const float* sig = ssig + tb * J.nopad + J.u_o0[u];
               for (int c0 = 16 * half; c0 < nw; c0 += 32) {
                 uint32_t r0[16], r1[16];
                 __syncwarp();
-                tmem_ld16(lane_base + toff + (uint32_t)c0, r0);
-                tmem_ld16(lane_base + toff + (uint32_t)(nw + c0), r1);
+                tmem_ld16x2(lane_base + toff + (uint32_t)c0, lane_base + toff + (uint32_t)(nw + c0), r0, r1);
+                const int o0 = J.u_o0[u] + c0;
+                const int ne = min(16, J.nout - o0);
+                double* sp = st + ml * S + 2 * o0 + part;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                  const int oo = c0 + e, o = J.u_o0[u] + oo;
-                  if (o < J.nout) {
-                    const double v = (double)__uint_as_float(r0[e]) +
-                                     (double)__uint_as_float(r1[e]) * (1.0 / 256.0);
-                    st[ml * S + 2 * o + part] = ldexp(v * (double)__ldg(sig + oo), er);
-                  }
-                }
+                for (int e = 0; e < 16; ++e)
+                  if (e < ne)
+                    sp[2 * e] = f32_to_f64_bits(fmaf(__uint_as_float(r1[e]), 1.f / 256.f,
+                                                     __uint_as_float(r0[e])) * (sig[c0 + e] * so));
               }
               toff += 2 * (uint32_t)nw;
             }
@@ -492,11 +525,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
           const int o_hi = min(J.nout, J.u_o0[ub - 1] + J.u_w[ub - 1]);
           if (d >= 0 && nmh > 0 && o_hi > o_lo) {
             const long long base = b * J.out_ms + d * J.out_fs + (long long)(col0 + 32 * hh) * J.out_cs;
-            const int rowd = 2 * (o_hi - o_lo);
-            const int tot = nmh * rowd;
-            for (int q = tid; q < tot; q += kThreads) {
-              const int ml = q / rowd, rem = 2 * o_lo + (q - ml * rowd);
-              ob[2 * (base + (long long)ml * J.out_cs) + rem] = st[ml * S + rem];
+            // one warp per row, lanes along the row
+            for (int ml = warp; ml < nmh; ml += kThreads / 32) {
+              double* orow = ob + 2 * (base + (long long)ml * J.out_cs);
+              const double* srow = st + ml * S;
+              for (int rem = 2 * o_lo + lane; rem < 2 * o_hi; rem += 32) orow[rem] = srow[rem];
             }
           }
           __syncthreads();
@@ -680,8 +713,9 @@ bool cheb_mma_supported(int M, int N) {
     return o == G.nopad && nu == G.nunit && G.nunit == G.ntab * (G.nunit / G.ntab);
   };
   // 2^14 kin < 2^24 keeps the leading accumulator exact
+  // the row scales of all tables sit in shared memory (1024 floats)
   return a.kin <= 1000 && b.kin <= 1000 && covered(a) && covered(b) && a.smem <= kSmemLimit &&
-         b.smem <= kSmemLimit;
+         b.smem <= kSmemLimit && a.ntab * a.nopad <= 1024 && b.ntab * b.nopad <= 1024;
 }
 
 size_t cheb_mma_table_bytes(int M, int N, int inverse) {
@@ -693,11 +727,18 @@ void cheb_mma_tables(int M, int N, int inverse, std::vector<uint16_t>& out) {
   build_tables(M, N, inverse != 0, out);
 }
 
+template <bool F64>
+cudaError_t optin_mma(int optin_bytes) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, k_cheb_mma<F64>);
+  if (e) return e;
+  return cudaFuncSetAttribute(k_cheb_mma<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              std::min(kSmemLimit, optin_bytes - (int)a.sharedSizeBytes));
+}
+
 cudaError_t set_cheb_mma_attributes(int optin_bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_cheb_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       optin_bytes - 4096);
-  if (!e) e = cudaFuncSetAttribute(k_cheb_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   optin_bytes - 4096);
+  cudaError_t e = optin_mma<true>(optin_bytes);
+  if (!e) e = optin_mma<false>(optin_bytes);
   return e;
 }
 
@@ -757,6 +798,7 @@ cudaError_t launch_cheb_mma(const GroupDev& g, bool inverse, cudaStream_t st, in
   J.npass = G.npass;
   for (int p = 0; p < G.npass; ++p) { J.p_u0[p] = G.p_u0[p]; J.p_nu[p] = G.p_nu[p]; }
   J.nsrc = nf;
+  J.ntab = G.ntab;
   J.ntcol = (KZ + kCols - 1) / kCols;
   J.ntiles = (long long)g.nb * nf * J.ntcol;
   J.status = g.status;
