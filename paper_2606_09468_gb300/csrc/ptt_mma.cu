@@ -64,7 +64,8 @@ namespace ptt {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kVals = 4;                   // contraction indices per thread and chunk
 constexpr int kRows = 128;                 // data rows per tile (64 complex columns)
 constexpr int kCols = 64;                  // complex columns per tile
 constexpr int kChunk = 32;                 // contraction elements per chunk (2 MMA k-steps)
@@ -192,12 +193,13 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(b);
 }
 
-// Raw input of one thread for one chunk: 8 complex elements of column m at
-// contraction indices i0 .. i0 + 7 (zero outside the field), loaded ahead of
-// their use so that the next chunk's loads overlap this chunk's work.
+// Raw input of one thread for one chunk: kVals complex elements of column m
+// at contraction indices i0 .. i0 + kVals - 1 (zero outside the field),
+// loaded ahead of their use so that the next chunk's loads overlap this
+// chunk's work.
 template <bool F64> struct Raw;
-template <> struct Raw<true> { double2 v[8]; };
-template <> struct Raw<false> { float2 v[8]; };
+template <> struct Raw<true> { double2 v[kVals]; };
+template <> struct Raw<false> { float2 v[kVals]; };
 
 template <bool F64>
 __device__ __forceinline__ void load_raw(const MmaJob& J, const char* inb, int col0, int ncv, int i0, int m,
@@ -207,7 +209,7 @@ __device__ __forceinline__ void load_raw(const MmaJob& J, const char* inb, int c
   const bool colok = m < ncv;
   const CT* p = reinterpret_cast<const CT*>(inb) + (long long)(col0 + m) * J.in_cs;
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
+  for (int e = 0; e < kVals; ++e) {
     const int i = i0 + e;
     CT z{};
     r.v[e] = (colok && i < J.kin) ? __ldg(p + (long long)i * J.in_is) : z;
@@ -215,9 +217,9 @@ __device__ __forceinline__ void load_raw(const MmaJob& J, const char* inb, int c
 }
 
 template <bool F64>
-__device__ __forceinline__ void raw_values(const Raw<F64>& r, float (&re)[8], float (&im)[8]) {
+__device__ __forceinline__ void raw_values(const Raw<F64>& r, float (&re)[kVals], float (&im)[kVals]) {
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
+  for (int e = 0; e < kVals; ++e) {
     if constexpr (F64) {
       re[e] = f64_to_f32_trunc(r.v[e].x);
       im[e] = f64_to_f32_trunc(r.v[e].y);
@@ -229,9 +231,9 @@ __device__ __forceinline__ void raw_values(const Raw<F64>& r, float (&re)[8], fl
 }
 
 // Slices of x scaled by sc (a power of two, |x sc| < 128): X0, X1, X2/2^8
-// and X3/2^16 as BF16 bit patterns (all exact in BF16).  xs - x0 and the
-// later remainders are exact in FP32, and so are their products by 256.
-__device__ __forceinline__ void slice4(float x, float sc, uint32_t (&p)[kNPA]) {
+// and X3/2^16, each exact in BF16.  xs - x0 and the later remainders are
+// exact in FP32, and so are their products by 256.
+__device__ __forceinline__ void slice4(float x, float sc, float (&p)[kNPA]) {
   const float xs = x * sc;
   const float x0 = rintf(xs);
   const float t1 = (xs - x0) * 256.f;
@@ -239,10 +241,17 @@ __device__ __forceinline__ void slice4(float x, float sc, uint32_t (&p)[kNPA]) {
   const float t2 = (t1 - x1) * 256.f;
   const float x2 = rintf(t2);
   const float x3 = rintf((t2 - x2) * 256.f);
-  p[0] = __float_as_uint(x0) >> 16;
-  p[1] = __float_as_uint(x1) >> 16;
-  p[2] = __float_as_uint(x2 * (1.f / 256.f)) >> 16;
-  p[3] = __float_as_uint(x3 * (1.f / 65536.f)) >> 16;
+  p[0] = x0;
+  p[1] = x1;
+  p[2] = x2 * (1.f / 256.f);
+  p[3] = x3 * (1.f / 65536.f);
+}
+
+// Two exact-in-BF16 values as one BF16x2 word (a in the low half).
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
 }
 
 template <bool F64>
@@ -278,8 +287,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
   const uint32_t tmem = tmem_base;
   long long g = 0;   // chunks issued by this CTA (stage g & 1)
   // data slices: thread -> (column m, k-group kg); rows m (real) and m + 64 (imaginary)
-  const int m = tid & 63, kg = tid >> 6;
-  const int quad = warp & 3, half = warp >> 2;
+  // thread -> (column m, k-group kg of 8, half kh of it); a half-warp covers
+  // the 8 rows x 16 bytes of one core matrix, so its stores do not conflict
+  const int kh = tid & 1, m = (tid >> 1) & 63, kg = tid >> 7;
+  const int i_th = kg * 8 + kh * kVals;            // first contraction index in the chunk
+  const int quad = warp & 3, q4 = warp >> 2;       // TMEM lane group, column quarter
   const int row = quad * 32 + lane;                 // TMEM lane = data row
   const int mc = row & 63, part = row >> 6;         // tile column, real / imaginary part
   bool stop = false;
@@ -313,13 +325,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
       float mre = 0.f, mim = 0.f;
       for (int kc = 0; kc < J.nchunk; kc += 2) {
         Raw<F64> r0, r1;
-        load_raw<F64>(J, inb, col0, ncv, kc * kChunk + kg * 8, m, r0);
-        load_raw<F64>(J, inb, col0, ncv, (kc + 1) * kChunk + kg * 8, m, r1);
+        load_raw<F64>(J, inb, col0, ncv, kc * kChunk + i_th, m, r0);
+        load_raw<F64>(J, inb, col0, ncv, (kc + 1) * kChunk + i_th, m, r1);
         if constexpr (F64) {
           unsigned long long ar = 0ull, ai = 0ull;
           const unsigned long long mask = 0x7FFFFFFFFFFFFFFFull;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
+          for (int e = 0; e < kVals; ++e) {
             ar = max(ar, (unsigned long long)__double_as_longlong(r0.v[e].x) & mask);
             ai = max(ai, (unsigned long long)__double_as_longlong(r0.v[e].y) & mask);
             ar = max(ar, (unsigned long long)__double_as_longlong(r1.v[e].x) & mask);
@@ -329,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
           mim = fmaxf(mim, f64_to_f32_trunc(__longlong_as_double((long long)ai)));
         } else {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
+          for (int e = 0; e < kVals; ++e) {
             mre = fmaxf(mre, fmaxf(fabsf(r0.v[e].x), fabsf(r1.v[e].x)));
             mim = fmaxf(mim, fmaxf(fabsf(r0.v[e].y), fabsf(r1.v[e].y)));
           }
@@ -354,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
       for (int u = ua; u < ub; ++u) anyp |= (J.dst[J.u_tab[u]][f] >= 0);
       if (!anyp) continue;
       Raw<F64> cur;
-      load_raw<F64>(J, inb, col0, ncv, kg * 8, m, cur);
+      load_raw<F64>(J, inb, col0, ncv, i_th, m, cur);
       for (int kc = 0; kc < J.nchunk; ++kc, ++g) {
         const int s = (int)(g & 1);
         unsigned char* sA = sm + s * J.stage_bytes;
@@ -382,27 +394,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
         {
           // this chunk's values, then the next chunk's loads go out before
           // this chunk is sliced, stored and multiplied
-          float re[8], im[8];
+          float re[kVals], im[kVals];
           raw_values<F64>(cur, re, im);
-          if (kc + 1 < J.nchunk) load_raw<F64>(J, inb, col0, ncv, (kc + 1) * kChunk + kg * 8, m, cur);
+          if (kc + 1 < J.nchunk) load_raw<F64>(J, inb, col0, ncv, (kc + 1) * kChunk + i_th, m, cur);
 #pragma unroll
           for (int pt = 0; pt < 2; ++pt) {
             const int r = m + 64 * pt;
             const float sc = rscale[r];
             const float* x = pt ? im : re;
-            uint32_t w[kNPA][4];
+            uint32_t w[kNPA][kVals / 2];
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-              uint32_t a[kNPA], c[kNPA];
+            for (int e = 0; e < kVals; e += 2) {
+              float a[kNPA], c[kNPA];
               slice4(x[e], sc, a);
               slice4(x[e + 1], sc, c);
 #pragma unroll
-              for (int pc = 0; pc < kNPA; ++pc) w[pc][e >> 1] = a[pc] | (c[pc] << 16);
+              for (int pc = 0; pc < kNPA; ++pc) w[pc][e >> 1] = pack_bf16x2(a[pc], c[pc]);
             }
-            const int off = (r >> 3) * kSBO + kg * kLBO + (r & 7) * 16;
+            const int off = (r >> 3) * kSBO + kg * kLBO + (r & 7) * 16 + kh * 8;
 #pragma unroll
             for (int pc = 0; pc < kNPA; ++pc)
-              *reinterpret_cast<uint4*>(sA + pc * kPieceA + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
+              *reinterpret_cast<uint2*>(sA + pc * kPieceA + off) = make_uint2(w[pc][0], w[pc][1]);
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -469,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
           if (d >= 0) {
             const float* sig = ssig + tb * J.nopad + J.u_o0[u];
             const long long base = b * J.out_ms + d * J.out_fs + (long long)(col0 + mc) * J.out_cs;
-            for (int c0 = 16 * half; c0 < nw; c0 += 32) {
+            for (int c0 = 16 * q4; c0 < nw; c0 += 64) {
               uint32_t r0[16], r1[16];
               __syncwarp();
               tmem_ld16x2(lane_base + toff + (uint32_t)c0, lane_base + toff + (uint32_t)(nw + c0), r0, r1);
@@ -502,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cheb_mma(MmaJob J) {
             for (int u = ua; u < ub; ++u) {
               const int nw = J.u_w[u], tb = J.u_tab[u];
               const float* sig = ssig + tb * J.nopad + J.u_o0[u];
-              for (int c0 = 16 * half; c0 < nw; c0 += 32) {
+              for (int c0 = 16 * q4; c0 < nw; c0 += 64) {
                 uint32_t r0[16], r1[16];
                 __syncwarp();
                 tmem_ld16x2(lane_base + toff + (uint32_t)c0, lane_base + toff + (uint32_t)(nw + c0), r0, r1);
