@@ -73,8 +73,8 @@ def parse():
     ap.add_argument("--only", default=None,
                     help="run one workload alone (3d_fp64, 3d_mixed, 3d_fp64_large, "
                          "3d_mixed_large, ensemble_mixed, ensemble_fp64, 2d_NXxNY[_mixed]: one "
-                         "shape of the 2D sweep, three seeds; 'mixedfft' in place of 'mixed' "
-                         "selects the FP32-FFT Chebyshev passes instead of the tensor-core ones) "
+                         "shape of the 2D sweep, three seeds; 'mixedtc' in place of 'mixed' "
+                         "selects the tensor-core Chebyshev passes instead of the FP32 FFTs) "
                          "and print its line, for profiling; or midplane_stats: mixed vs FP64 "
                          "mid-plane statistics of the 3D workload over --steps steps")
     return ap.parse_args()
@@ -345,7 +345,7 @@ def only_workload(args):
     name = args.only
     if name == "midplane_stats":
         return midplane_stats(args)
-    prec = (P.PTT_MIXED_FFT if "mixedfft" in name else P.PTT_MIXED if "mixed" in name else P.PTT_FP64)
+    prec = (P.PTT_MIXED_TC if "mixedtc" in name else P.PTT_MIXED if "mixed" in name else P.PTT_FP64)
     if name.startswith("3d"):
         nx, ny, nz = I.CHANNEL3D_LARGE if name.endswith("large") else I.CHANNEL3D
         params = [P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=prec, **I.PAPER)]
@@ -394,8 +394,9 @@ def other_workloads(args):
         ms = _timed(ctx, nsteps, warm)
         return ctx, ms
 
-    for shape, precs in ((I.CHANNEL3D, (P.PTT_FP64, P.PTT_MIXED)),
-                         (I.CHANNEL3D_LARGE, (P.PTT_FP64, P.PTT_MIXED))):
+    tags = {P.PTT_FP64: "fp64", P.PTT_MIXED: "mixed", P.PTT_MIXED_TC: "mixedtc"}
+    for shape, precs in ((I.CHANNEL3D, (P.PTT_FP64, P.PTT_MIXED, P.PTT_MIXED_TC)),
+                         (I.CHANNEL3D_LARGE, (P.PTT_FP64, P.PTT_MIXED, P.PTT_MIXED_TC))):
         pts = shape[0] * shape[1] * shape[2]
         ms_of, states = {}, {}
         for prec in precs:
@@ -412,16 +413,19 @@ def other_workloads(args):
             status = P.ptt_status_string(ctx.synchronize())
             ctx.close()
             ref.close()
-            name = "3d_%s_%dx%dx%d" % ("fp64" if prec == P.PTT_FP64 else "mixed", *shape)
+            name = "3d_%s_%dx%dx%d" % (tags[prec], *shape)
             out[name] = {"value": pts * 1e3 / ms, "unit": METRIC, "ms_per_step": ms, "steps": n,
                          "grid_points": pts, "status": status,
-                         "dtype": "f64" if prec == P.PTT_FP64 else "f32 transforms+products / f64 state+solves",
+                         "dtype": {P.PTT_FP64: "f64",
+                                   P.PTT_MIXED: "f32 transforms+products / f64 state+solves",
+                                   P.PTT_MIXED_TC: "f32 x/z transforms+products, tensor-core "
+                                                   "Chebyshev contractions / f64 state+solves"}[prec],
                          "workload": "3D sPTT channel %dx%dx%d (x, y, z), Lx=10, Lz=5, paper fluid, "
                                      "dt=1e-3, laminar + seeded perturbation 1e-3" % shape}
-        if P.PTT_MIXED in states:
-            name = "3d_mixed_%dx%dx%d" % shape
-            out[name]["speedup_vs_fp64"] = ms_of[P.PTT_FP64][0] / ms_of[P.PTT_MIXED][0]
-            out[name]["max_rel_field_dev_vs_fp64_gpu"] = dict(zip(f3, _dev(states[P.PTT_MIXED], states[P.PTT_FP64])))
+        for prec in (P.PTT_MIXED, P.PTT_MIXED_TC):
+            name = "3d_%s_%dx%dx%d" % (tags[prec], *shape)
+            out[name]["speedup_vs_fp64"] = ms_of[P.PTT_FP64][0] / ms_of[prec][0]
+            out[name]["max_rel_field_dev_vs_fp64_gpu"] = dict(zip(f3, _dev(states[prec], states[P.PTT_FP64])))
             out[name]["dev_after_steps"] = warm
 
     # ragged ensemble: 64 runs, uneven Nx, Ny, Wi
@@ -591,12 +595,13 @@ def run_ours(args):
     e2e = {"value": whole_job_rate(world, points, args.e2e_steps, e2e_s), "unit": METRIC,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
 
-    # mixed precision form (FP32 transforms and products, FP64 state and
-    # solves) of the same workload: rate, and its deviation from the FP64 GPU
-    # path after the warm-up steps from the same initial state
-    mixed = None
-    if args.mixed:
-        mparams = [P.make_params(nx=nx, ny=ny, dt=I.DT, precision=P.PTT_MIXED, **I.PAPER)
+    # mixed precision forms (FP32 transforms and products, FP64 state and
+    # solves) of the same workload: rate, and deviation from the FP64 GPU path
+    # after the warm-up steps from the same initial state.  PTT_MIXED takes
+    # the Chebyshev transforms as FP32 FFTs, PTT_MIXED_TC as tensor-core
+    # contractions.
+    def mixed_form(prec):
+        mparams = [P.make_params(nx=nx, ny=ny, dt=I.DT, precision=prec, **I.PAPER)
                    for nx, ny, _ in members]
         mctx = P.Context(mparams)
         fctx = P.Context([params[-1]])
@@ -622,14 +627,25 @@ def run_ours(args):
         torch.cuda.synchronize()
         mms = max_over_ranks(m0.elapsed_time(m1), "cuda")
         mval = whole_job_rate(world, points, args.steps, mms * 1e-3)
-        mixed = {"value": mval, "unit": METRIC, "ms_per_step": mms / args.steps,
-                 "speedup_vs_fp64": mval / value, "dtype": "f32 transforms / f64 state+solves",
-                 "status": P.ptt_status_string(mctx.synchronize()),
-                 "max_rel_field_dev_vs_fp64_gpu": dict(zip(["u", "v", "cxx", "cxy", "cyy"], dev)),
-                 "dev_after_steps": args.warmup, "dev_member": "512x257",
-                 "stated_error_vs_oracle": "tests/test_gpu_mixed.py: 1 step <= 1e-8; 100 steps "
-                                           "<= 1e-7 (u, c), <= 1e-4 (v, the 1e-3 perturbation)"}
+        res = {"value": mval, "unit": METRIC, "ms_per_step": mms / args.steps,
+               "speedup_vs_fp64": mval / value,
+               "status": P.ptt_status_string(mctx.synchronize()),
+               "max_rel_field_dev_vs_fp64_gpu": dict(zip(["u", "v", "cxx", "cxy", "cyy"], dev)),
+               "dev_after_steps": args.warmup, "dev_member": "512x257"}
         mctx.close()
+        return res
+
+    mixed = mixed_tc = None
+    if args.mixed:
+        mixed = mixed_form(P.PTT_MIXED)
+        mixed.update({"dtype": "f32 transforms (Chebyshev as FFTs) / f64 state+solves",
+                      "stated_error_vs_oracle": "tests/test_gpu_mixed.py: 1 step <= 1e-8; 100 steps "
+                                                "<= 1e-7 (u, c), <= 1e-4 (v, the 1e-3 perturbation)"})
+        mixed_tc = mixed_form(P.PTT_MIXED_TC)
+        mixed_tc.update({"dtype": "f32 x transforms, bf16-sliced tensor-core Chebyshev contractions "
+                                  "with f32 accumulation / f64 state+solves",
+                         "stated_error_vs_oracle": "tests/test_gpu_mma.py: explicit rhs <= 1e-6 "
+                                                   "(measured 0.9-1.6e-7 in 2D, as the FFT form)"})
 
     if rank != 0:
         return
@@ -652,6 +668,7 @@ def run_ours(args):
            "gpu_launches": launches, "roofline": roofline, "clocks": clk, "e2e": e2e}
     if mixed is not None:
         out["mixed"] = mixed
+        out["mixed_tc"] = mixed_tc
     if workloads is not None:
         out["workloads"] = workloads
     if not args.no_cpu_baseline and world == 1:

@@ -66,13 +66,15 @@ extern "C" {
 #define PTT_ENOTSUP (-5)   /* valid request this library does not implement      */
 
 #define PTT_FP64 0         /* every step of the path in FP64                     */
-#define PTT_MIXED 1        /* FP32 Fourier transforms and products; the Chebyshev
-                              transforms as split-BF16 tensor-core contractions
-                              with FP32 accumulation (FP32 FFTs for the shapes
-                              that contraction does not cover, ny > 257); FP64
+#define PTT_MIXED 1        /* FP32 Fourier and Chebyshev transforms (FFTs; the
+                              Chebyshev ones as DCT-II/III) and products; FP64
                               state, SBDF sums, tau solves and diagnostics      */
-#define PTT_MIXED_FFT 2    /* as PTT_MIXED, with the Chebyshev transforms as FP32
-                              FFTs (DCT-II/III) for every shape                  */
+#define PTT_MIXED_TC 2     /* as PTT_MIXED, with the Chebyshev transforms as dense
+                              contractions on the tensor cores: BF16 slices of a
+                              fixed-point split, FP32 accumulation (FP32 FFTs for
+                              the shapes that contraction does not cover,
+                              ny > 321); same accuracy as PTT_MIXED, slower on
+                              this part at the shapes measured               */
 
 /* Physical and numerical parameters of one member.  Defaults (the paper's
  * single fluid, Sec. 2): lx = lz = 10, re = 1e-2, wi = 150, beta = 0.9,
@@ -80,7 +82,7 @@ extern "C" {
 typedef struct {
   int32_t nx, ny, nz;        /* Fourier modes in x, Chebyshev modes in y, Fourier
                                 modes in z (nz = 1: the 2D problem)             */
-  int32_t precision;         /* PTT_FP64, PTT_MIXED or PTT_MIXED_FFT              */
+  int32_t precision;         /* PTT_FP64, PTT_MIXED or PTT_MIXED_TC               */
   double lx, lz;             /* periodic lengths (walls at y = +-1)               */
   double re, wi, beta, eps, kappa;
   double dt;                 /* fixed time step                                   */

@@ -420,7 +420,7 @@ struct Group {
 int check_params(const ptt_params& p) {
   if (p.nz != 1 && (p.nz < 4 || p.nz > 512 || (p.nz & 1) || !smooth235(p.nz))) return PTT_EINVAL;
   if (p.nz > 1 && !(p.lz > 0)) return PTT_EINVAL;
-  if (p.precision != PTT_FP64 && p.precision != PTT_MIXED && p.precision != PTT_MIXED_FFT)
+  if (p.precision != PTT_FP64 && p.precision != PTT_MIXED && p.precision != PTT_MIXED_TC)
     return PTT_ENOTSUP;
   if (p.nx < 8 || p.nx > 512 || (p.nx & 1) || !smooth235(p.nx)) return PTT_EINVAL;
   if (p.ny < 9 || p.ny > 513 || !smooth235(p.ny - 1)) return PTT_EINVAL;
@@ -588,7 +588,7 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
       g.nz = pm[i].nz;
       group_sizes(g.nx, g.ny, g.nz, g);
       g.d.f32 = (pm[i].precision != PTT_FP64) ? 1 : 0;
-      g.d.ymma = (pm[i].precision == PTT_MIXED) ? 1 : 0;   // requested; carve() checks the shape
+      g.d.ymma = (pm[i].precision == PTT_MIXED_TC) ? 1 : 0;   // requested; carve() checks the shape
       groups.push_back(std::move(g));
       it = idx.find(key);
     }

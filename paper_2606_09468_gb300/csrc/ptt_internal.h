@@ -91,8 +91,8 @@ struct GroupDev {
   unsigned long long* hist;  // [nb][8][PTT_HIST_BINS + 2] mid-plane histograms
   const double* hrange;      // [nb][8][2] (lo, hi); lo >= hi: quantity off
   // mixed groups: the Chebyshev passes of the step as tensor-core contractions
-  // (ymma = 1; see ptt_mma.cu) with their pre-split BF16 tables, inverse and
-  // forward, or as FP32 FFTs (ymma = 0)
+  // (ymma = 1, PTT_MIXED_TC; see ptt_mma.cu) with their pre-sliced BF16
+  // tables, inverse and forward, or as FP32 FFTs (ymma = 0, PTT_MIXED)
   int ymma;
   int nsm;           // streaming multiprocessors of the device (persistent grids)
   const uint16_t* Wyi;

@@ -1,5 +1,6 @@
-// Chebyshev transforms of the mixed-precision step as dense contractions on
-// the tensor cores (tcgen05, sm_103a): BF16 operands, FP32 accumulation.
+// Chebyshev transforms of the mixed-precision step (PTT_MIXED_TC) as dense
+// contractions on the tensor cores (tcgen05, sm_103a): BF16 operands, FP32
+// accumulation.
 //
 // Along y the method (Sec. 2: Fourier-Chebyshev pseudo-spectral) maps the
 // Chebyshev coefficients a_n (n < N) of every Fourier column to values on the
@@ -36,7 +37,7 @@
 // their own relative accuracy however large the mean column (the base state,
 // stretch components 10^4).
 //
-// Kernel structure (k_cheb_mma): persistent, one CTA of 256 threads per SM,
+// Kernel structure (k_cheb_mma): persistent, one CTA of 512 threads per SM,
 // walking tiles (member, field, 64 Fourier columns).  Per tile a first pass
 // over the input finds each row's exponent; then, per pass (a set of output
 // subtiles whose two accumulators fit the 512 tensor-memory columns), the

@@ -1,6 +1,6 @@
-"""The tensor-core Chebyshev passes of PTT_MIXED (BF16 slices of a
+"""The tensor-core Chebyshev passes of PTT_MIXED_TC (BF16 slices of a
 fixed-point split, FP32 accumulation, tcgen05) against the FP64 oracle and
-against the FP32-FFT passes of PTT_MIXED_FFT.
+against the FP32-FFT passes of PTT_MIXED.
 
 Tolerance: the explicit right-hand side to 1e-6 of each field's maximum (the
 mixed form's stated bar); the two mixed forms differ from each other by FP32
@@ -44,14 +44,14 @@ def test_tensor_core_rhs_2d_matches_oracle(nx, ny):
     st, ref = _state2(nx, ny, 7)
     spec = I.spectral_to_abi(st.as_list())
     out = {}
-    for prec in (P.PTT_MIXED, P.PTT_MIXED_FFT):
+    for prec in (P.PTT_MIXED_TC, P.PTT_MIXED):
         ctx = P.Context([P.make_params(nx=nx, ny=ny, precision=prec, dt=I.DT, **I.PAPER)])
         ctx.set_spectral(0, spec)
         out[prec] = I.abi_to_spectral(ctx.explicit_rhs(0))
         ctx.close()
-    e_mma = _errs(out[P.PTT_MIXED], ref)
-    e_fft = _errs(out[P.PTT_MIXED_FFT], ref)
-    e_pair = _errs(out[P.PTT_MIXED], out[P.PTT_MIXED_FFT])
+    e_mma = _errs(out[P.PTT_MIXED_TC], ref)
+    e_fft = _errs(out[P.PTT_MIXED], ref)
+    e_pair = _errs(out[P.PTT_MIXED_TC], out[P.PTT_MIXED])
     print(f"2D {nx}x{ny} rhs errors: tensor-core {e_mma}, FP32 FFT {e_fft}, between {e_pair}")
     assert np.all(e_mma <= TOL_RHS), e_mma
     assert np.all(e_pair <= 2 * TOL_RHS), e_pair
@@ -67,16 +67,16 @@ def test_tensor_core_rhs_3d_matches_oracle(nx, ny, nz):
     st = O3.State3(*(a + e for a, e in zip(ora.state.as_list(), extra)))
     Nc, H = ora.explicit_terms(st)
     e = {}
-    for prec in (P.PTT_MIXED, P.PTT_MIXED_FFT):
+    for prec in (P.PTT_MIXED_TC, P.PTT_MIXED):
         ctx = P.Context([P.make_params(nx=nx, ny=ny, nz=nz, precision=prec, **kw)])
         ctx.set_spectral(0, I.spectral3_to_abi(st.as_list()))
         e[prec] = _errs(I.abi_to_spectral3(ctx.explicit_rhs(0)), Nc + H)
         ctx.close()
-    print(f"3D {nx}x{ny}x{nz} rhs errors: tensor-core {e[P.PTT_MIXED]}, FP32 FFT {e[P.PTT_MIXED_FFT]}")
+    print(f"3D {nx}x{ny}x{nz} rhs errors: tensor-core {e[P.PTT_MIXED_TC]}, FP32 FFT {e[P.PTT_MIXED]}")
     # the 3D stretch terms carry the FP32 rounding of the products on both
     # forms alike: the tensor-core form within the bar, or within twice the
     # FFT form's error field by field
-    assert np.all(e[P.PTT_MIXED] <= np.maximum(TOL_RHS, 2 * e[P.PTT_MIXED_FFT])), e
+    assert np.all(e[P.PTT_MIXED_TC] <= np.maximum(TOL_RHS, 2 * e[P.PTT_MIXED])), e
 
 
 def test_tensor_core_steps_match_fft_form_and_mask_blown_members():
@@ -87,7 +87,7 @@ def test_tensor_core_steps_match_fft_form_and_mask_blown_members():
     P = _P()
     nx, ny = 128, 97
     kw = dict(I.PAPER, dt=I.DT)
-    ens = P.Context([P.make_params(nx=nx, ny=ny, precision=P.PTT_MIXED, **kw)] * 3)
+    ens = P.Context([P.make_params(nx=nx, ny=ny, precision=P.PTT_MIXED_TC, **kw)] * 3)
     for i in range(3):
         ens.init_state(i, 30 + i, 0.01)
     phys = ens.get_state(1)
@@ -96,12 +96,12 @@ def test_tensor_core_steps_match_fft_form_and_mask_blown_members():
     ens.step(20)
     assert ens.synchronize() == P.PTT_BLOWUP
     for i in (0, 2):
-        one = P.Context([P.make_params(nx=nx, ny=ny, precision=P.PTT_MIXED, **kw)])
+        one = P.Context([P.make_params(nx=nx, ny=ny, precision=P.PTT_MIXED_TC, **kw)])
         one.init_state(0, 30 + i, 0.01)
         one.step(20)
         assert one.synchronize() == P.PTT_OK
         assert np.array_equal(one.get_spectral(0), ens.get_spectral(i))
-        fft = P.Context([P.make_params(nx=nx, ny=ny, precision=P.PTT_MIXED_FFT, **kw)])
+        fft = P.Context([P.make_params(nx=nx, ny=ny, precision=P.PTT_MIXED, **kw)])
         fft.init_state(0, 30 + i, 0.01)
         fft.step(20)
         e = _errs(I.abi_to_phys(ens.get_state(i)), I.abi_to_phys(fft.get_state(0)))
