@@ -70,13 +70,17 @@ def parse():
                     help="perturbation amplitude of the midplane_stats runs")
     ap.add_argument("--stats-wi", type=float, default=I.PAPER["wi"],
                     help="Weissenberg number of the midplane_stats runs")
+    ap.add_argument("--record", default=None,
+                    help="longrun_2d / longrun_3d: write the per-step series here (JSON lines)")
     ap.add_argument("--only", default=None,
                     help="run one workload alone (3d_fp64, 3d_mixed, 3d_fp64_large, "
                          "3d_mixed_large, ensemble_mixed, ensemble_fp64, 2d_NXxNY[_mixed]: one "
                          "shape of the 2D sweep, three seeds; 'mixedtc' in place of 'mixed' "
                          "selects the tensor-core Chebyshev passes instead of the FP32 FFTs) "
                          "and print its line, for profiling; or midplane_stats: mixed vs FP64 "
-                         "mid-plane statistics of the 3D workload over --steps steps")
+                         "mid-plane statistics of the 3D workload over --steps steps; or "
+                         "longrun_2d / longrun_3d: per-step admissibility records of the 2D "
+                         "sweep / the 3D channel over --steps steps")
     return ap.parse_args()
 
 
@@ -339,12 +343,76 @@ def midplane_stats(args):
     print(json.dumps(out))
 
 
+def longrun(args):
+    """Long runs with per-step admissibility records (the quantities of the
+    paper's Table 1 and Sec. 3): longrun_2d advances the 27-run 2D sweep,
+    longrun_3d the 3D 128x97x64 channel, both in FP64, for --steps steps,
+    reading each run's diagnostics records at most 1000 steps apart (the
+    device ring keeps 1024).  Per step and run: volume fractions of Tr c < 3
+    and Tr c < 0, the same at the mid-plane, E and max Tr c; the first
+    blown-up step per run.  The full per-step series go to --record (JSON
+    lines, one per run) when given; the printed line carries per-run
+    summaries."""
+    import numpy as np
+    import paper_2606_09468_gb300 as P
+    if args.only == "longrun_3d":
+        nx, ny, nz = I.CHANNEL3D
+        runs = [(nx, ny, nz, 0)]
+        params = [P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, **I.PAPER)]
+    else:
+        runs = [(nx, ny, 1, s) for nx, ny, s in I.sweep_members()]
+        params = [P.make_params(nx=nx, ny=ny, dt=I.DT, **I.PAPER) for nx, ny, _, _ in runs]
+    ctx = P.Context(params)
+    for i, r in enumerate(runs):
+        ctx.init_state(i, r[3], I.AMPLITUDE)
+    series = [[] for _ in runs]
+    for i in range(len(runs)):
+        ctx.diagnostics(i)                       # the initial state's record
+    t0 = time.time()
+    done = 0
+    while done < args.steps:
+        k = min(1000, args.steps - done)
+        ctx.step(k)
+        done += k
+        for i, (nx, ny, nz, _) in enumerate(runs):
+            for d in ctx.diagnostics(i, 1024):
+                vol, mid = nx * ny * nz, nx * nz
+                series[i].append([d["step"], d["n_lt3"] / vol, d["n_lt0"] / vol, d["n_mid_lt3"] / mid,
+                                  d["n_mid_lt0"] / mid, d["energy"], d["max_trc"], d["status"]])
+    status = P.ptt_status_string(ctx.synchronize())
+    seconds = time.time() - t0
+    ctx.close()
+    summary = []
+    for (nx, ny, nz, seed), ser in zip(runs, series):
+        a = np.array([row[:7] for row in ser]) if ser else np.zeros((0, 7))
+        blown = [row[0] for row in ser if row[7] == P.PTT_BLOWUP]
+        summary.append({"shape": [nx, ny, nz], "seed": seed, "records": len(ser),
+                        "last_step": int(a[-1, 0]) if len(a) else 0,
+                        "blowup_step": int(blown[0]) if blown else None,
+                        "frac_lt3_min_mean_max": [float(a[:, 1].min()), float(a[:, 1].mean()), float(a[:, 1].max())],
+                        "frac_lt0_max": float(a[:, 2].max()),
+                        "mid_frac_lt3_max": float(a[:, 3].max()),
+                        "energy_first_last": [float(a[0, 5]), float(a[-1, 5])],
+                        "max_trc_first_last": [float(a[0, 6]), float(a[-1, 6])]})
+    if args.record:
+        with open(args.record, "w") as fh:
+            for (nx, ny, nz, seed), ser in zip(runs, series):
+                fh.write(json.dumps({"shape": [nx, ny, nz], "seed": seed,
+                                     "columns": ["step", "frac_lt3", "frac_lt0", "mid_frac_lt3",
+                                                 "mid_frac_lt0", "energy", "max_trc", "status"],
+                                     "rows": ser}) + "\n")
+    print(json.dumps({"workload": args.only, "steps": args.steps, "dt": I.DT, "status": status,
+                      "seconds": seconds, "runs": summary}))
+
+
 def only_workload(args):
     """One workload alone, --steps steps after --warmup (for ncu captures)."""
     import paper_2606_09468_gb300 as P
     name = args.only
     if name == "midplane_stats":
         return midplane_stats(args)
+    if name in ("longrun_2d", "longrun_3d"):
+        return longrun(args)
     prec = (P.PTT_MIXED_TC if "mixedtc" in name else P.PTT_MIXED if "mixed" in name else P.PTT_FP64)
     if name.startswith("3d"):
         nx, ny, nz = I.CHANNEL3D_LARGE if name.endswith("large") else I.CHANNEL3D
