@@ -70,6 +70,11 @@ def parse():
                     help="perturbation amplitude of the midplane_stats runs")
     ap.add_argument("--stats-wi", type=float, default=I.PAPER["wi"],
                     help="Weissenberg number of the midplane_stats runs")
+    ap.add_argument("--stats-cpert", type=float, default=0.0,
+                    help="amplitude of a seeded polymer-stress perturbation added to the "
+                         "midplane_stats initial state (0: none)")
+    ap.add_argument("--stats-shape", default=None,
+                    help="NXxNYxNZ of the midplane_stats runs (default: the 3D workload)")
     ap.add_argument("--record", default=None,
                     help="longrun_2d / longrun_3d: write the per-step series here (JSON lines)")
     ap.add_argument("--only", default=None,
@@ -301,11 +306,23 @@ def midplane_stats(args):
     out = {"workload": "midplane_stats", "shape": [nx, ny, nz], "steps": steps, "quantities": MID3D,
            "amplitude": amp, "wi": wi}
     fluid = dict(I.PAPER, wi=wi)
+    if args.stats_shape:
+        nx, ny, nz = (int(v) for v in args.stats_shape.split("x"))
+        out["shape"] = [nx, ny, nz]
+    out["c_perturbation"] = args.stats_cpert
     # both runs in one context (two shape groups: FP64 and mixed)
     ctx = P.Context([P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=prec, **fluid)
                      for prec in (P.PTT_FP64, P.PTT_MIXED)])
     for b in (0, 1):
         ctx.init_state(b, 0, amp)
+    if args.stats_cpert > 0:
+        # a seeded perturbation of the polymer stress, which relaxes on the
+        # Wi time scale and keeps driving velocity fluctuations (a velocity
+        # perturbation alone decays viscously within ~1e3 steps at Re = 1e-2)
+        phys = ctx.get_state(0)
+        phys += I.stress_perturbation3(nx, ny, nz, I.LZ3, seed=1, amplitude=args.stats_cpert)
+        for b in (0, 1):
+            ctx.set_state(b, phys)
     m0, _ = ctx.moments(0)           # the initial state's record sets the bin ranges
     span = np.maximum(8 * m0[:, 1], 1e-6 * np.maximum(1.0, np.abs(m0[:, 0])))
     lo, hi = m0[:, 0] - span, m0[:, 0] + span

@@ -22,9 +22,10 @@
  *  - nz = 1 selects the 2D (z-independent) problem: w = 0 and c_zz = 1
  *    exactly; the five fields are u, v, c_xx, c_xy, c_yy.  nz > 1 selects the
  *    3D problem with nine fields u, v, w, c_xx, c_xy, c_xz, c_yy, c_yz, c_zz.
- *  - nx: even, 8 <= nx <= 512, of the form 2^a 3^b 5^c.  ny (Chebyshev
- *    modes): 9 <= ny <= 513 with ny - 1 of the form 2^a 3^b 5^c.  nz: 1, or
- *    even with 4 <= nz <= 512 and of the form 2^a 3^b 5^c (then lz > 0).
+ *  - nx: even, 8 <= nx <= 512, of the form 2^a 3^b 5^c 7^d 11^e 13^f.  ny
+ *    (Chebyshev modes): 9 <= ny <= 513 with ny - 1 of that form.  nz: 1, or
+ *    even with 4 <= nz <= 512 and of that form (then lz > 0).  (Every
+ *    multiple of 32 from 64 to 512 is admitted, and so is ny = 225.)
  *  - Physical layout (host arrays of ptt_set_state / ptt_get_state):
  *    double[nf][nz][ny][nx] (2D: nf = 5, nz = 1; 3D: nf = 9): field-major,
  *    then z (z_k = k lz/nz), then y (Gauss-Lobatto point

@@ -28,6 +28,16 @@ bool smooth235(long long n) {
   return n == 1;
 }
 
+// Admitted unpadded lengths: 13-smooth (one FFT pass per prime factor;
+// radices 7, 11 and 13 take direct butterflies).  Padded lengths are chosen
+// 5-smooth (next_smooth), where the passes are cheapest.
+bool smooth13(long long n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5, 7, 11, 13})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
 int next_smooth(int n) {
   while (!smooth235(n)) ++n;
   return n;
@@ -64,7 +74,9 @@ HostPlan make_plan(int n, bool three_first = false) {
   if (three_first && n % 3 == 0 && n % 5 != 0) { p.radix.push_back(3); r /= 3; }
   // radix 5 first: the first pass takes no twiddles, and a twiddled radix-5
   // butterfly costs the most (44 FP64 operations against 36 untwiddled)
-  for (int f : {5, 4, 2, 3})
+  // radices 13, 11, 7 (unpadded lengths only) first: their butterflies are
+  // the costliest, and the first pass takes no twiddles
+  for (int f : {13, 11, 7, 5, 4, 2, 3})
     while (r % f == 0) { p.radix.push_back(f); r /= f; }
   return p;
 }
@@ -329,7 +341,7 @@ void tangent_offsets(const HostPlan& hp, int* toff, int* tto, int* nrec, int* nd
     const int R = hp.radix[st];
     toff[st] = rec;
     tto[st] = dbl;
-    if (st > 0) {
+    if (st > 0 && R <= 5) {   // radices 7, 11, 13 keep plain twiddles
       rec += Ns;
       dbl += (R == 5 ? 16 : 6) * Ns;
     }
@@ -356,7 +368,7 @@ void tangent_tables(const HostPlan& hp, std::vector<double>& tt, std::vector<int
   int Ns = 1;
   for (size_t st = 0; st < hp.radix.size(); ++st) {
     const int R = hp.radix[st];
-    if (st > 0) {
+    if (st > 0 && R <= 5) {
       const long long stride = n / ((long long)Ns * R);
       const int RS = (R == 5) ? 16 : 6;
       for (int jm = 0; jm < Ns; ++jm) {
@@ -418,12 +430,12 @@ struct Group {
 };
 
 int check_params(const ptt_params& p) {
-  if (p.nz != 1 && (p.nz < 4 || p.nz > 512 || (p.nz & 1) || !smooth235(p.nz))) return PTT_EINVAL;
+  if (p.nz != 1 && (p.nz < 4 || p.nz > 512 || (p.nz & 1) || !smooth13(p.nz))) return PTT_EINVAL;
   if (p.nz > 1 && !(p.lz > 0)) return PTT_EINVAL;
   if (p.precision != PTT_FP64 && p.precision != PTT_MIXED && p.precision != PTT_MIXED_TC)
     return PTT_ENOTSUP;
-  if (p.nx < 8 || p.nx > 512 || (p.nx & 1) || !smooth235(p.nx)) return PTT_EINVAL;
-  if (p.ny < 9 || p.ny > 513 || !smooth235(p.ny - 1)) return PTT_EINVAL;
+  if (p.nx < 8 || p.nx > 512 || (p.nx & 1) || !smooth13(p.nx)) return PTT_EINVAL;
+  if (p.ny < 9 || p.ny > 513 || !smooth13(p.ny - 1)) return PTT_EINVAL;
   if (!(p.lx > 0) || !(p.re > 0) || !(p.wi > 0) || !(p.dt > 0)) return PTT_EINVAL;
   if (!(p.beta > 0 && p.beta <= 1) || !(p.eps >= 0) || !(p.kappa >= 0)) return PTT_EINVAL;
   return PTT_OK;

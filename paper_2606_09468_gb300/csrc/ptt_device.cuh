@@ -115,6 +115,72 @@ template <int DIR> struct Bfly<DIR, 5> {
   }
 };
 
+// Odd prime radices 7, 11, 13 (the unpadded lengths nx, 2 (ny - 1) and nz
+// may carry one such factor).  With H = (R - 1)/2, t_k = v_k + v_{R-k},
+// d_k = v_k - v_{R-k} (k = 1..H) and w = exp(DIR 2 pi i / R):
+//   y_0 = v_0 + sum_k t_k,
+//   y_j, y_{R-j} = b_j +- i DIR e_j,  b_j = v_0 + sum_k cos(2 pi jk/R) t_k,
+//                                     e_j = sum_k sin(2 pi jk/R) d_k  (j = 1..H),
+// the cosines and sines of 2 pi m / R (m = 1..H) as literals, the others by
+// symmetry (jk reduced mod R).
+// cos and sin of 2 pi m / R, m = 1 .. (R - 1)/2 (folded to constants once
+// the butterfly's loops are unrolled).
+__device__ __forceinline__ constexpr double odd_cos(int R, int m) {
+  constexpr double c7[3] = {0.6234898018587335305250, -0.2225209339563144042890, -0.9009688679024191262361};
+  constexpr double c11[5] = {0.8412535328311811688618, 0.4154150130018864255292, -0.1423148382732851404438,
+                             -0.6548607339452850640569, -0.9594929736144973898904};
+  constexpr double c13[6] = {0.8854560256532098959003, 0.5680647467311558025118, 0.1205366802553230533490,
+                             -0.3546048870425356259696, -0.7485107481711010986346, -0.9709418174260520271570};
+  return R == 7 ? c7[m - 1] : R == 11 ? c11[m - 1] : c13[m - 1];
+}
+__device__ __forceinline__ constexpr double odd_sin(int R, int m) {
+  constexpr double s7[3] = {0.7818314824680298087084, 0.9749279121818236070181, 0.4338837391175581204757};
+  constexpr double s11[5] = {0.5406408174555975821076, 0.9096319953545183714117, 0.9898214418809327323760,
+                             0.7557495743542582837740, 0.2817325568414296977114};
+  constexpr double s13[6] = {0.4647231720437685456560, 0.8229838658936563945796, 0.9927088740980539928007,
+                             0.9350162426854148234397, 0.6631226582407952023767, 0.2393156642875577671487};
+  return R == 7 ? s7[m - 1] : R == 11 ? s11[m - 1] : s13[m - 1];
+}
+
+template <int DIR, int R> struct BflyOdd {
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    using T = typename RealOf<C2>::T;
+    constexpr int H = (R - 1) / 2;
+    C2 t[H], d[H];
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+      t[k - 1] = cadd(v[k], v[R - k]);
+      d[k - 1] = csub(v[k], v[R - k]);
+    }
+    C2 y[R];
+    y[0] = v[0];
+#pragma unroll
+    for (int k = 0; k < H; ++k) y[0] = cadd(y[0], t[k]);
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+      C2 b = v[0], e = zero2<C2>();
+#pragma unroll
+      for (int k = 1; k <= H; ++k) {
+        const int mm = (j * k) % R;                  // 1 .. R-1
+        const int mi = (mm <= H) ? mm : R - mm;      // cos even, sin odd about R/2
+        const T c = (T)odd_cos(R, mi);
+        const T sn = (T)((mm <= H) ? odd_sin(R, mi) : -odd_sin(R, mi));
+        b = cfma(c, t[k - 1], b);
+        e = cfma(sn, d[k - 1], e);
+      }
+      const C2 ie = cscl(mul_i(e), (T)DIR);
+      y[j] = cadd(b, ie);
+      y[R - j] = csub(b, ie);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = y[r];
+  }
+};
+template <int DIR> struct Bfly<DIR, 7> : BflyOdd<DIR, 7> {};
+template <int DIR> struct Bfly<DIR, 11> : BflyOdd<DIR, 11> {};
+template <int DIR> struct Bfly<DIR, 13> : BflyOdd<DIR, 13> {};
+
 // Division by a runtime divisor d through a multiply-high (the method of
 // Granlund and Montgomery, "Division by invariant integers using
 // multiplication", PLDI 1994, in its round-up form): with
@@ -312,7 +378,11 @@ template <> __device__ __forceinline__ const float2* plan_tw<float2>(const FftPl
 // ping-pong buffer.  Returns the buffer holding the result.  Must be called
 // by the whole block after a __syncthreads(); ends with one.  zero_mid: the
 // lines are zero in their middle third and the plan starts with radix 3.
-template <int DIR, typename C2>
+// BIG: the plan may hold radices 7, 11, 13 (unpadded lengths); without it
+// only 2 to 5 are compiled in (the padded lengths, chosen 5-smooth), which
+// keeps the register budget of the hot transform kernels, and a pass of
+// another radix is skipped (the launch code never gives such a plan).
+template <int DIR, typename C2, bool BIG = false>
 __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl, bool zero_mid = false) {
   C2* src = a;
   C2* dst = b;
@@ -328,7 +398,7 @@ __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl, bool z
       continue;
     }
     if constexpr (std::is_same<C2, double2>::value) {
-      if (pl.tt && s > 0) {
+      if (pl.tt && s > 0 && R <= 5) {
         const double* tt = pl.tt + pl.tto[s];
         const int* tk = pl.tk + pl.toff[s];
         if (R == 5) fft_pass_tan<DIR, 5>(src, dst, nl, ls, pl.n, Ns, tt, tk);
@@ -345,7 +415,14 @@ __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl, bool z
       case 2: fft_pass<DIR, 2>(src, dst, nl, ls, pl.n, Ns, tw); break;
       case 3: fft_pass<DIR, 3>(src, dst, nl, ls, pl.n, Ns, tw); break;
       case 4: fft_pass<DIR, 4>(src, dst, nl, ls, pl.n, Ns, tw); break;
-      default: fft_pass<DIR, 5>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      case 5: fft_pass<DIR, 5>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      default:
+        if constexpr (BIG) {
+          if (R == 7) fft_pass<DIR, 7>(src, dst, nl, ls, pl.n, Ns, tw);
+          else if (R == 11) fft_pass<DIR, 11>(src, dst, nl, ls, pl.n, Ns, tw);
+          else if (R == 13) fft_pass<DIR, 13>(src, dst, nl, ls, pl.n, Ns, tw);
+        }
+        break;
     }
     __syncthreads();
     Ns *= R;
@@ -889,7 +966,7 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
       else if (n > M) { const int r = P - n; A[i] = (r < N) ? A[c * P + r] : czero(); }
     }
     __syncthreads();
-    double2* res = fft_lines<-1>(A, B, C, P, J.pl);
+    double2* res = fft_lines<-1, double2, true>(A, B, C, P, J.pl);
     // f_j = (F_j + a_0 + (-1)^j a_M) / 2
     for (int i = tid; i < (M + 1) * C; i += nt) {
       const int j = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - j * C;
@@ -910,7 +987,7 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
       if (j > M) A[i] = A[c * P + (P - j)];
     }
     __syncthreads();
-    double2* res = fft_lines<-1>(A, B, C, P, J.pl);
+    double2* res = fft_lines<-1, double2, true>(A, B, C, P, J.pl);
     const double inv = 1.0 / M;
     for (int i = tid; i < N * C; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - c * N;
@@ -922,7 +999,9 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
   }
 }
 
-template <typename CT>
+// BIG: the Gauss-Lobatto (unpadded) path, whose FFT length 2 (ny - 1) may
+// hold radices 7, 11, 13; the Gauss (padded) path runs without it.
+template <typename CT, bool BIG = false>
 __global__ void __launch_bounds__(256) k_ycols(YJob J) {
   const int b = blockIdx.z;
   if (J.status && J.status[b]) return;
@@ -947,7 +1026,7 @@ __global__ void __launch_bounds__(256) k_ycols(YJob J) {
       : nullptr;
   if (J.gauss) {
     ycols_gauss<CT>(J, src, src2, src3, dst, A, B, c0, nc);
-  } else if constexpr (sizeof(CT) == sizeof(double2)) {
+  } else if constexpr (sizeof(CT) == sizeof(double2) && BIG) {
     ycols_lobatto(J, src, src2, src3, dst, reinterpret_cast<double2*>(A), reinterpret_cast<double2*>(B),
                   reinterpret_cast<double2*>(B) + (size_t)C * P, c0, nc);
   }
@@ -1008,7 +1087,7 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
       A[i] = h;
     }
     __syncthreads();
-    double2* res = fft_lines<+1>(A, Bb, nl, n, J.pl);
+    double2* res = fft_lines<+1, double2, true>(A, Bb, nl, n, J.pl);
     double* dst = J.dstR + b * J.dst_mstride + (long long)r0 * J.dst_rstep * n;
     for (int i = tid; i < nl * n; i += nt) {
       const int l = (int)fdiv((unsigned)i, fast_div((unsigned)n)), x = i - l * n;
@@ -1025,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
       A[i] = make_double2(fa, fb);
     }
     __syncthreads();
-    double2* res = fft_lines<-1>(A, Bb, nl, n, J.pl);
+    double2* res = fft_lines<-1, double2, true>(A, Bb, nl, n, J.pl);
     double2* dst = J.dstC + b * J.dst_mstride + (long long)row * J.dst_rstep * K;
     const double inv = 1.0 / n;
     for (int i = tid; i < nl * K; i += nt) {

@@ -13,14 +13,15 @@ constexpr int kMaxStages = 16;
 constexpr int kRing = 1024;       // diagnostics records kept per member
 constexpr int kNumHist = 4;       // SBDF4 history depth
 
-// Mixed-radix (2, 3, 4, 5) Stockham FFT plan of length n.
+// Mixed-radix (2, 3, 4, 5, 7, 11, 13) Stockham FFT plan of length n.
 struct FftPlan {
   int n;
   int nst;
   int radix[kMaxStages];
   const double2* tw;  // tw[k] = exp(-2 pi i k / n), k < n (device)
   const float2* twf;  // the same in single precision (mixed groups), or null
-  // Tangent-form twiddles of the FP64 passes s >= 1 (null: use tw).  Forward
+  // Tangent-form twiddles of the FP64 passes s >= 1 of radix 2 to 5 (null:
+  // use tw; passes of radix 7, 11, 13 always use tw).  Forward
   // twiddle r of stride index jm:
   //   exp(-2 pi i jm r st / n) = i^k_r cos(t'_r) (1 + i tan(t'_r)), |t'_r| <= pi/4,
   // record jm of pass s at tt[tto[s] + RS jm] (RS = 16 for radix 5, else 6),

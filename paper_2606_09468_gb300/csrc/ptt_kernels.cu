@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
     }
   }
   __syncthreads();
-  double2* res = fft_lines<+1>(L, L2, 3, nx, g.plNx);
+  double2* res = fft_lines<+1, double2, true>(L, L2, 3, nx, g.plNx);
   // mid-plane histograms of the 6 quantities (shared-memory counts)
   constexpr int HS = PTT_HIST_BINS + 2;
   __shared__ unsigned int hsm[6 * HS];
@@ -796,6 +796,7 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
   cudaError_t e;
   if ((e = optin(k_ycols<double2>, optin_bytes))) return e;
   if ((e = optin(k_ycols<float2>, optin_bytes))) return e;
+  if ((e = optin(k_ycols<double2, true>, optin_bytes))) return e;
   if ((e = optin(k_xfused<double2>, optin_bytes))) return e;
   if ((e = optin(k_xfused<float2>, optin_bytes))) return e;
   if ((e = optin(k_xrows, optin_bytes))) return e;
@@ -920,7 +921,7 @@ static void diag_trc_y(const GroupDev& g, cudaStream_t st) {
   T.src_mstride = 5 * NK; T.dst_mstride = (long long)NK;
   T.src_fstride = NK; T.dst_fstride = 0;
   T.src_field[0] = 2; T.src_field2[0] = 4; T.dst_field[0] = 0; T.deriv[0] = 0;
-  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+  k_ycols<double2, true><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
 }
 
 cudaError_t launch_diag_transforms(const GroupDev& g, cudaStream_t st) {
@@ -1001,7 +1002,7 @@ cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st) {
   J.src = g.stageS; J.dst = g.X + (size_t)b * 5 * NK;
   J.src_fstride = NK; J.dst_fstride = NK;
   for (int i = 0; i < 5; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
+  k_ycols<double2, true><<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
   k_reset<<<1, 32, 0, st>>>(g, b);
   return cudaGetLastError();
 }
@@ -1013,7 +1014,7 @@ cudaError_t launch_state_to_phys(const GroupDev& g, int b, cudaStream_t st) {
   J.src = g.X + (size_t)b * 5 * NK; J.dst = g.stageS;
   J.src_fstride = NK; J.dst_fstride = NK;
   for (int i = 0; i < 5; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
+  k_ycols<double2, true><<<dim3(cdiv(g.K, g.CcolU), 5, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
   XJob X{};
   X.srcC = g.stageS; X.dstR = g.stage;
   X.src_fstride = NK; X.dst_fstride = (long long)g.N * g.nx;

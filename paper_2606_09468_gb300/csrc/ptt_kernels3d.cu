@@ -47,7 +47,9 @@ struct ZJob {
   FftPlan pl;         // length Mz
 };
 
-template <typename CT>
+// BIG: unpadded z length nz (radices 7, 11, 13 possible); the padded length
+// Mz of the step runs without it.
+template <typename CT, bool BIG = false>
 __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
   using T = typename RealOf<CT>::T;
   const int b = blockIdx.z;
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
     }
     __syncthreads();
     // padded synthesis (Mz >= 3 nz/2): the slots nz/2 .. Mz - nz/2 are zero
-    CT* res = fft_lines<+1>(A, B, C, Mz, J.pl, J.pl.radix[0] == 3 && Mz >= 3 * hz);
+    CT* res = fft_lines<+1, CT, BIG>(A, B, C, Mz, J.pl, J.pl.radix[0] == 3 && Mz >= 3 * hz);
     for (int i = tid; i < Mz * C; i += nt) {
       const int z = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - z * C;
       if (c < nc) st2<CT>(dst, (long long)z * K + m0 + c, J.dst_f32, res[c * Mz + z]);
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
       A[c * Mz + z] = (c < nc) ? ld2<CT>(src, (long long)z * K + m0 + c, J.src_f32) : zero2<CT>();
     }
     __syncthreads();
-    CT* res = fft_lines<-1>(A, B, C, Mz, J.pl);
+    CT* res = fft_lines<-1, CT, BIG>(A, B, C, Mz, J.pl);
     const T inv = (T)(1.0 / Mz);
     for (int i = tid; i < C * nz; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)nz)), mz = i - c * nz;
@@ -785,6 +787,8 @@ cudaError_t set_kernel_attributes3(int optin_bytes) {
   if ((e = optin3(k_ycols<float2>, optin_bytes))) return e;
   if ((e = optin3(k_zcols<double2>, optin_bytes))) return e;
   if ((e = optin3(k_zcols<float2>, optin_bytes))) return e;
+  if ((e = optin3(k_zcols<double2, true>, optin_bytes))) return e;
+  if ((e = optin3(k_ycols<double2, true>, optin_bytes))) return e;
   if ((e = optin3(k_xfused3<double2>, optin_bytes))) return e;
   if ((e = optin3(k_xfused3<float2>, optin_bytes))) return e;
   if ((e = optin3(k_xrows, optin_bytes))) return e;
@@ -924,7 +928,7 @@ static void diag_trc_y3(const GroupDev& g, cudaStream_t st) {
   T.src_mstride = 9 * NK; T.dst_mstride = (long long)NK;
   T.src_fstride = NK; T.dst_fstride = 0;
   T.src_field[0] = 3; T.src_field2[0] = 6; T.src_field3[0] = 8; T.dst_field[0] = 0; T.deriv[0] = 0;
-  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+  k_ycols<double2, true><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
 }
 
 cudaError_t launch_diag_transforms3(const GroupDev& g, cudaStream_t st) {
@@ -946,7 +950,7 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   Zm.src_mstride = 8LL * KZ; Zm.dst_mstride = 8LL * g.nz * K;
   Zm.src_fstride = KZ; Zm.dst_fstride = (long long)g.nz * K;
   for (int i = 0; i < 8; ++i) { Zm.src_field[i] = i; Zm.dst_field[i] = i; Zm.dz[i] = 0; }
-  k_zcols<double2><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
+  k_zcols<double2, true><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
   XJob Xm{};
   Xm.srcC = g.DMZ; Xm.dstR = g.MV;
   Xm.src_mstride = 8LL * g.nz * K; Xm.dst_mstride = 8LL * g.nz * g.nx;
@@ -961,7 +965,7 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   Z.src_mstride = (long long)NK; Z.dst_mstride = (long long)g.N * g.nz * K;
   Z.src_fstride = 0; Z.dst_fstride = 0;
   Z.src_field[0] = 0; Z.dst_field[0] = 0; Z.dz[0] = 0;
-  k_zcols<double2><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
+  k_zcols<double2, true><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
   XJob X{};
   X.srcC = g.DZ; X.dstR = g.DV;
   X.src_mstride = (long long)g.N * g.nz * K; X.dst_mstride = (long long)g.N * g.nz * g.nx;
@@ -1019,13 +1023,13 @@ cudaError_t launch_phys_to_state3(const GroupDev& g, int b, cudaStream_t st) {
   Z.src = g.DZ; Z.dst = g.stageS;     // stageS reused as [9][N][KZ]
   Z.src_fstride = rowsp * K; Z.dst_fstride = (long long)N * KZ;
   for (int i = 0; i < 9; ++i) { Z.src_field[i] = i; Z.dst_field[i] = i; Z.dz[i] = 0; }
-  k_zcols<double2><<<dim3(cdiv(K, Z.C), 9 * N, 1), 256, smem_zcols(Z.C, nz, 0), st>>>(Z);
+  k_zcols<double2, true><<<dim3(cdiv(K, Z.C), 9 * N, 1), 256, smem_zcols(Z.C, nz, 0), st>>>(Z);
   YJob J = yjob3(g, false, N - 1, g.CcolU, g.plPu, nullptr);
   J.status = nullptr;
   J.src = g.stageS; J.dst = g.X + (size_t)b * 9 * NK;
   J.src_fstride = (long long)N * KZ; J.dst_fstride = NK;
   for (int i = 0; i < 9; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 9, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
+  k_ycols<double2, true><<<dim3(cdiv(KZ, g.CcolU), 9, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
   k_reset3<<<1, 32, 0, st>>>(g, b);
   return cudaGetLastError();
 }
@@ -1039,13 +1043,13 @@ cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st) {
   J.src = g.X + (size_t)b * 9 * NK; J.dst = g.stageS;
   J.src_fstride = NK; J.dst_fstride = (long long)N * KZ;
   for (int i = 0; i < 9; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolU), 9, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
+  k_ycols<double2, true><<<dim3(cdiv(KZ, g.CcolU), 9, 1), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(J);
   ZJob Z = zjob(g, true, nz, N, g.plNz);
   Z.status = nullptr;
   Z.src = g.stageS; Z.dst = g.DZ;
   Z.src_fstride = (long long)N * KZ; Z.dst_fstride = rowsp * K;
   for (int i = 0; i < 9; ++i) { Z.src_field[i] = i; Z.dst_field[i] = i; Z.dz[i] = 0; }
-  k_zcols<double2><<<dim3(cdiv(K, Z.C), 9 * N, 1), 256, smem_zcols(Z.C, nz, 0), st>>>(Z);
+  k_zcols<double2, true><<<dim3(cdiv(K, Z.C), 9 * N, 1), 256, smem_zcols(Z.C, nz, 0), st>>>(Z);
   XJob X{};
   X.srcC = g.DZ; X.dstR = g.stage;
   X.src_fstride = rowsp * K; X.dst_fstride = rowsp * nx;

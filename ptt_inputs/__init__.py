@@ -27,11 +27,10 @@ CHANNEL3D = (128, 97, 64)
 CHANNEL3D_LARGE = (256, 129, 128)
 
 # Ragged ensemble: 64 independent 2D runs, member i with seed i, Nx drawn
-# from the multiples of 32 in [64, 512] that the FFT sizes allow (2^a 3^b 5^c),
-# Ny from {65, 97, 129, 161, 193, 257} (Ny - 1 of the form 2^a 3^b 5^c; 225
-# is not), Wi uniform in [50, 200]; all three from the splitmix64 stream of i.
+# from the multiples of 32 in [64, 512], Ny from {65, 97, 129, 161, 193, 225,
+# 257}, Wi uniform in [50, 200]; all three from the splitmix64 stream of i.
 ENSEMBLE_SIZE = 64
-ENSEMBLE_NY = (65, 97, 129, 161, 193, 257)
+ENSEMBLE_NY = (65, 97, 129, 161, 193, 225, 257)
 ENSEMBLE_WI = (50.0, 200.0)
 
 _MASK64 = (1 << 64) - 1
@@ -52,14 +51,7 @@ def splitmix_unit(seed, k):
     return (splitmix64(seed, k) >> 11) * (1.0 / (1 << 53))
 
 
-def _smooth235(n):
-    for q in (2, 3, 5):
-        while n % q == 0:
-            n //= q
-    return n == 1
-
-
-ENSEMBLE_NX = tuple(n for n in range(64, 513, 32) if _smooth235(n))
+ENSEMBLE_NX = tuple(range(64, 513, 32))
 
 
 def ensemble_members(size=ENSEMBLE_SIZE):
@@ -171,3 +163,27 @@ PAPER_SHAPES = {"A1": (128, 513, 128), "A2": (512, 129, 128), "A3": (256, 257, 2
                 "A4": (512, 257, 128), "A5": (512, 129, 256), "A6": (512, 129, 512)}
 PAPER_DT = 2.5e-3
 PAPER_LZ = 10.0
+
+
+def stress_perturbation3(nx, ny, nz, lz, seed, amplitude, lx=10.0):
+    """A smooth seeded perturbation of the six conformation components of a
+    3D state, physical values in the ABI layout [9][nz][ny][nx] (velocity
+    slots zero): each component is amplitude (1 - y^2) sum_{mx, mz <= 2}
+    a cos(kx x + kz z + phi) with uniform a in [-1, 1) and phases from a
+    numpy generator.  Input data only (no arithmetic of the method)."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) * lx / nx
+    y = np.cos(np.pi * np.arange(ny) / (ny - 1))
+    z = np.arange(nz) * lz / nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    out = np.zeros((9, nz, ny, nx))
+    for f in range(3, 9):
+        acc = np.zeros_like(X)
+        for mx in range(3):
+            for mz in range(3):
+                if mx == 0 and mz == 0:
+                    continue
+                a, ph = rng.uniform(-1, 1), rng.uniform(0, 2 * np.pi)
+                acc += a * np.cos(2 * np.pi * mx * X / lx + 2 * np.pi * mz * Z / lz + ph)
+        out[f] = amplitude * (1 - Y ** 2) * acc
+    return out

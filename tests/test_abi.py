@@ -42,8 +42,12 @@ def test_status_strings_and_param_checks_without_gpu(lib):
     # the largest admitted shapes
     assert P.ptt_workspace_size([P.make_params(nx=512, ny=513)]) > 0
     assert P.ptt_workspace_size([P.make_params(nx=8, ny=9, nz=512, lz=5.0)]) > 0
-    for bad in (dict(nx=63), dict(ny=66), dict(nx=14), dict(beta=0.0), dict(nz=2), dict(nz=3),
-                dict(nz=14), dict(nz=1024), dict(nz=8, lz=0.0), dict(nx=6), dict(nx=1024),
+    # the admitted lengths are 13-smooth: 14 = 2 7, ny - 1 = 65 = 5 13 pass; 34 = 2 17 does not
+    for ok in (dict(nx=14), dict(ny=66), dict(nx=224), dict(nx=352), dict(nx=416), dict(ny=225),
+               dict(nz=14, lz=5.0), dict(nz=26, lz=5.0)):
+        assert P.ptt_workspace_size([P.make_params(**ok)]) > 0, ok
+    for bad in (dict(nx=63), dict(ny=39), dict(nx=34), dict(beta=0.0), dict(nz=2), dict(nz=3),
+                dict(nz=34), dict(nz=1024), dict(nz=8, lz=0.0), dict(nx=6), dict(nx=1024),
                 dict(ny=7), dict(ny=1025), dict(dt=0.0), dict(precision=3)):
         with pytest.raises(P.PttError):
             P.ptt_workspace_size([P.make_params(**bad)])

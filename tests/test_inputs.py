@@ -28,3 +28,8 @@ def test_ensemble_draws_cover_the_ranges():
     assert len(nx) >= 8 and len(ny) >= 5
     assert 50.0 <= min(wi) and max(wi) <= 200.0
     assert all(n % 32 == 0 and 64 <= n <= 512 for n in nx)
+    # the full sets of the configuration: every multiple of 32, Ny up to 257
+    # with 225 (ny - 1 = 2^5 7), and the draws reach the radix-7/11/13 sizes
+    assert I.ENSEMBLE_NX == tuple(range(64, 513, 32))
+    assert I.ENSEMBLE_NY == (65, 97, 129, 161, 193, 225, 257)
+    assert nx & {224, 352, 416, 448} and 225 in ny
