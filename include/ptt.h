@@ -334,6 +334,18 @@ int ptt_stage_work(ptt_ctx* ctx, double* flops, double* bytes, int32_t* launches
  * precision) of the members in order of first appearance.  Synchronous. */
 int ptt_autotune(ptt_ctx* ctx, int32_t* choices, int32_t max_groups);
 
+/* Launch mode of the step graphs.  0 (the default): every shape group of
+ * the context is its own branch of the graph, with its own launches.  1: one
+ * launch per kernel of each stage over all groups, each group's blocks
+ * found from a table of per-group block counts (a work list over (group,
+ * block)), so that a step makes the same dozen or so launches however many
+ * shape groups the ensemble holds.  Mode 1 needs 2 to 64 groups, all 2D (nz
+ * = 1), of one precision and without tensor-core passes (PTT_ENOTSUP
+ * otherwise).  The arithmetic of every block is that of the same block of
+ * its group's own launch, so states, records and histograms are bitwise the
+ * same in both modes.  Re-captures the step graphs.  Synchronous. */
+int ptt_set_launch_mode(ptt_ctx* ctx, int32_t mode);
+
 /* Number of kernel launches one step makes (for launch accounting). */
 int ptt_launches_per_step(ptt_ctx* ctx, int32_t* n);
 

@@ -72,6 +72,7 @@ _SIGS = {
     "ptt_time_stages": [_VP, _I32, _DP],
     "ptt_stage_work": [_VP, _DP, _DP, ctypes.POINTER(_I32)],
     "ptt_launches_per_step": [_VP, ctypes.POINTER(_I32)],
+    "ptt_set_launch_mode": [_VP, _I32],
     "ptt_destroy": [_VP],
     "ptt_status_string": [ctypes.c_int],
     "ptt_last_error": [],
@@ -296,6 +297,10 @@ def ptt_stage_work(ctx):
     return fl, by, np.array(list(nl))
 
 
+def ptt_set_launch_mode(ctx, mode):
+    _check("ptt_set_launch_mode", load_library().ptt_set_launch_mode(ctx, mode))
+
+
 def ptt_launches_per_step(ctx):
     n = _I32()
     _check("ptt_launches_per_step", load_library().ptt_launches_per_step(ctx, ctypes.byref(n)))
@@ -434,6 +439,11 @@ class Context:
 
     def launches_per_step(self):
         return ptt_launches_per_step(self.ctx)
+
+    def set_launch_mode(self, mode):
+        """0: one graph branch per shape group; 1: one launch per kernel and
+        stage over all groups (2D contexts)."""
+        ptt_set_launch_mode(self.ctx, mode)
 
     def close(self):
         if self.ctx:

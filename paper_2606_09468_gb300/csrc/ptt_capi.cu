@@ -609,6 +609,16 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
   return groups;
 }
 
+// A context can take one launch per stage over all its groups when they
+// are all 2D, of one precision, without tensor-core passes, 2 to
+// multi2d_max_groups() of them.
+bool multi_eligible(const std::vector<Group>& groups) {
+  if (groups.size() < 2 || (int)groups.size() > multi2d_max_groups()) return false;
+  for (const Group& g : groups)
+    if (g.d.nz != 1 || g.d.ymma || g.d.f32 != groups[0].d.f32) return false;
+  return true;
+}
+
 }  // namespace
 
 struct ptt_ctx {
@@ -631,6 +641,11 @@ struct ptt_ctx {
   int launches = 0;
   int device = 0;
   double timeout_s = 3600.0;           // wall-clock limit of ptt_synchronize (<= 0: none)
+  // launch mode of the step graphs: 0 one branch per shape group, 1 one
+  // launch per kernel of each stage over all groups (2D contexts)
+  int launch_mode = 0;
+  void* multi_dev = nullptr;           // workspace region of the plan (null: not eligible)
+  Multi2DPlan* multi = nullptr;
 };
 
 thread_local char g_last_error[512] = "";
@@ -724,6 +739,7 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
   }
   Carver cv;
   carve(groups, cv);
+  if (multi_eligible(groups)) cv.take<char>(multi2d_bytes((int)groups.size()));
   *bytes = cv.off + 256;
   return PTT_OK;
 }
@@ -739,7 +755,32 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
 // graph 2 the diagnostics of the last step's result (stage 4).  Within the
 // diagnostics, the energy transform and the mid-plane sums run on branches of
 // their own beside the Tr c chain (launch_diag_split).
+// The same with one launch per kernel and stage over all groups (launch
+// mode 1): the diagnostics of the previous step on one branch beside the
+// next step's transforms.
+static cudaError_t capture_kind_multi(ptt_ctx* c, int kind, int* nl) {
+  const Multi2DPlan* p = c->multi;
+  auto diag = [&](cudaStream_t s0) {
+    const DiagStreams d{{s0, c->pstreams[0], c->pstreams[1]}, {c->pevents[0], c->pevents[1], c->pevents[2]}};
+    return launch_diag_multi(p, d, nl);
+  };
+  if (kind == 2) return diag(c->cap);
+  cudaError_t le = cudaSuccess;
+  cudaStream_t ds = c->dstreams[0];
+  if (kind == 1) {
+    le = cudaEventRecord(c->gevents.back(), c->cap);
+    if (!le) le = cudaStreamWaitEvent(ds, c->gevents.back(), 0);
+    if (!le) le = diag(ds);
+    if (!le) le = cudaEventRecord(c->devents[0], ds);
+  }
+  for (int s = 0; s < 3 && !le; ++s) le = launch_stage_multi(p, s, c->cap, nl);
+  if (!le && kind == 1) le = cudaStreamWaitEvent(c->cap, c->devents[0], 0);
+  if (!le) le = launch_stage_multi(p, 3, c->cap, nl);
+  return le;
+}
+
 static cudaError_t capture_kind(ptt_ctx* c, int kind, int* nl) {
+  if (c->launch_mode == 1) return capture_kind_multi(c, kind, nl);
   cudaError_t le = cudaEventRecord(c->gevents.back(), c->cap);
   for (size_t gi = 0; gi < c->groups.size() && !le; ++gi) {
     cudaStream_t gs = c->gstreams[gi], ds = c->dstreams[gi];
@@ -774,6 +815,15 @@ static int capture_step_graph(ptt_ctx* c) {
     if (c->exec[k]) { cudaGraphExecDestroy(c->exec[k]); c->exec[k] = nullptr; }
     if (c->graph[k]) { cudaGraphDestroy(c->graph[k]); c->graph[k] = nullptr; }
   }
+  if (c->multi) { multi2d_destroy(c->multi); c->multi = nullptr; }
+  if (c->launch_mode == 1) {
+    // the plan copies the groups as they are now (launch shapes included)
+    std::vector<const GroupDev*> gs;
+    for (const Group& g : c->groups) gs.push_back(&g.d);
+    cudaError_t e = cudaSuccess;
+    c->multi = multi2d_create(gs, c->multi_dev, c->stream, &e);
+    if (!c->multi) return fail_cuda(e ? e : cudaErrorInvalidValue, "multi2d_create", __LINE__);
+  }
   for (int k = 0; k < 3; ++k) {
     CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     int nl = 0;
@@ -805,6 +855,7 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   Carver cv;
   cv.base = (char*)d_ws;
   carve(c->groups, cv);
+  if (multi_eligible(c->groups)) c->multi_dev = cv.take<char>(multi2d_bytes((int)c->groups.size()));
   c->where.assign(nmem, {0, 0});
   c->last_read.assign(nmem, -1);
   int optin = 0;
@@ -1574,6 +1625,14 @@ int ptt_stage_work(ptt_ctx* c, double* flops, double* bytes, int32_t* launches) 
   return PTT_OK;
 }
 
+int ptt_set_launch_mode(ptt_ctx* c, int32_t mode) {
+  if (!c || (mode != 0 && mode != 1)) return PTT_EINVAL;
+  if (mode == 1 && !c->multi_dev) return PTT_ENOTSUP;
+  CK(cudaStreamSynchronize(c->stream));
+  c->launch_mode = mode;
+  return capture_step_graph(c);
+}
+
 int ptt_launches_per_step(ptt_ctx* c, int32_t* n) {
   if (!c || !n) return PTT_EINVAL;
   *n = c->launches;
@@ -1595,6 +1654,7 @@ int ptt_destroy(ptt_ctx* c) {
   for (auto e2 : c->gevents) if (e2) cudaEventDestroy(e2);
   for (auto e2 : c->devents) if (e2) cudaEventDestroy(e2);
   for (auto e2 : c->pevents) if (e2) cudaEventDestroy(e2);
+  if (c->multi) multi2d_destroy(c->multi);
   delete c;
   return PTT_OK;
 }

@@ -14,6 +14,40 @@
 namespace ptt {
 namespace {
 
+// Block coordinates of one launch, explicit so that a kernel body can also
+// run as one block of a launch over several shape groups (MultiMap).
+struct Blk {
+  int x, y, z;
+};
+__device__ __forceinline__ Blk this_blk() { return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z}; }
+
+// One launch over the shape groups of a context: group q contributes
+// gx[q] * gy[q] * gz[q] blocks, numbered from start[q] in x-fastest order,
+// so that each group's blocks see the coordinates of its own launch.
+constexpr int kMaxGroupsMulti = 64;
+struct MultiMap {
+  int ng;
+  int gid[kMaxGroupsMulti];      // index of entry q among the context's groups
+  int gx[kMaxGroupsMulti], gy[kMaxGroupsMulti], gz[kMaxGroupsMulti];
+  unsigned start[kMaxGroupsMulti + 1];
+};
+// The group of this block (its index among the context's groups) and the
+// block's coordinates within that group's launch.
+__device__ __forceinline__ int multi_locate(const MultiMap& mm, Blk& bk) {
+  const unsigned v = blockIdx.x;
+  int lo = 0, hi = mm.ng - 1;   // the entry q with start[q] <= v < start[q + 1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (mm.start[mid] <= v) lo = mid; else hi = mid - 1;
+  }
+  const unsigned l = v - mm.start[lo];
+  const unsigned gx = (unsigned)mm.gx[lo], gy = (unsigned)mm.gy[lo];
+  bk.x = (int)(l % gx);
+  bk.y = (int)((l / gx) % gy);
+  bk.z = (int)(l / (gx * gy));
+  return mm.gid[lo];
+}
+
 // ------------------------------------------------------------ complex math
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -842,11 +876,10 @@ template <> __device__ __forceinline__ float2 ld_tw4<float2>(const YJob& J, int 
 // construction; the real and imaginary parts of a column ride in one FFT).
 template <typename CT>
 __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, const void* src3,
-                            void* dst, CT* A, CT* B, int c0, int nc) {
+                            void* dst, CT* A, CT* B, int c0, int nc, int f) {
   using T = typename RealOf<CT>::T;
   const int C = J.C, N = J.N, Mg = J.M;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int f = blockIdx.y;
   if (J.inverse) {
     for (int i = tid; i < Mg * C; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)Mg)), n = i - c * Mg;
@@ -925,14 +958,13 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
 
 // Gauss-Lobatto path (double precision only): DCT-I by the even extension.
 __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v, const void* src3v,
-                              void* dstv, double2* A, double2* B, double2* a0s, int c0, int nc) {
+                              void* dstv, double2* A, double2* B, double2* a0s, int c0, int nc, int f) {
   const int C = J.C, N = J.N, M = J.M, P = 2 * J.M;
   const double2* src = static_cast<const double2*>(srcv);
   const double2* src2 = static_cast<const double2*>(src2v);
   const double2* src3 = static_cast<const double2*>(src3v);
   double2* dst = static_cast<double2*>(dstv);
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int f = blockIdx.y;
   if (J.inverse) {
     for (int i = tid; i < N * C; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - c * N;
@@ -1002,14 +1034,14 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
 // BIG: the Gauss-Lobatto (unpadded) path, whose FFT length 2 (ny - 1) may
 // hold radices 7, 11, 13; the Gauss (padded) path runs without it.
 template <typename CT, bool BIG = false>
-__global__ void __launch_bounds__(256) k_ycols(YJob J) {
-  const int b = blockIdx.z;
+__device__ __forceinline__ void ycols_block(const YJob& J, Blk bk) {
+  const int b = bk.z;
   if (J.status && J.status[b]) return;
-  const int f = blockIdx.y;
+  const int f = bk.y;
   // FFT length per column: M on the Gauss grid, 2M (even extension) on the
   // Gauss-Lobatto grid; shared memory holds 2 C lines of it (+ 2 C scalars)
   const int C = J.C, K = J.K, P = J.gauss ? J.M : 2 * J.M;
-  const int c0 = blockIdx.x * C;
+  const int c0 = bk.x * C;
   const int nc = min(C, K - c0);
   extern __shared__ __align__(16) unsigned char smraw[];
   CT* A = reinterpret_cast<CT*>(smraw);
@@ -1025,11 +1057,24 @@ __global__ void __launch_bounds__(256) k_ycols(YJob J) {
       ? static_cast<const char*>(J.src) + (b * J.src_mstride + J.src_field3[f] * J.src_fstride) * es
       : nullptr;
   if (J.gauss) {
-    ycols_gauss<CT>(J, src, src2, src3, dst, A, B, c0, nc);
+    ycols_gauss<CT>(J, src, src2, src3, dst, A, B, c0, nc, f);
   } else if constexpr (sizeof(CT) == sizeof(double2) && BIG) {
     ycols_lobatto(J, src, src2, src3, dst, reinterpret_cast<double2*>(A), reinterpret_cast<double2*>(B),
-                  reinterpret_cast<double2*>(B) + (size_t)C * P, c0, nc);
+                  reinterpret_cast<double2*>(B) + (size_t)C * P, c0, nc, f);
   }
+}
+
+template <typename CT, bool BIG = false>
+__global__ void __launch_bounds__(256) k_ycols(YJob J) {
+  ycols_block<CT, BIG>(J, this_blk());
+}
+
+// The same over the shape groups of a context (job q of jobs for group q).
+template <typename CT, bool BIG = false>
+__global__ void __launch_bounds__(256) k_ycols_multi(const YJob* __restrict__ jobs, MultiMap mm) {
+  Blk bk;
+  const int q = multi_locate(mm, bk);
+  ycols_block<CT, BIG>(jobs[q], bk);
 }
 
 // ---------------------------------------------------------- Fourier rows
@@ -1052,10 +1097,10 @@ struct XJob {
   FftPlan pl;
 };
 
-__global__ void __launch_bounds__(256) k_xrows(XJob J) {
-  const int b = blockIdx.y;
+__device__ __forceinline__ void xrows_block(const XJob& J, Blk bk) {
+  const int b = bk.y;
   if (J.status && J.status[b]) return;
-  const int row = blockIdx.x;
+  const int row = bk.x;
   const int K = J.K, n = J.n, nf = J.nf, nl = (nf + 1) / 2;
   extern __shared__ double2 sm[];
   double2* A = sm;
@@ -1119,6 +1164,15 @@ __global__ void __launch_bounds__(256) k_xrows(XJob J) {
       if (2 * l + 1 < nf) dst[(2 * l + 1) * J.dst_fstride + k] = G;
     }
   }
+}
+
+
+__global__ void __launch_bounds__(256) k_xrows(XJob J) { xrows_block(J, this_blk()); }
+
+__global__ void __launch_bounds__(256) k_xrows_multi(const XJob* __restrict__ jobs, MultiMap mm) {
+  Blk bk;
+  const int q = multi_locate(mm, bk);
+  xrows_block(jobs[q], bk);
 }
 
 

@@ -156,6 +156,23 @@ cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nlau
 // write scratch only (for launch-shape timing).
 cudaError_t launch_diag_transforms(const GroupDev& g, cudaStream_t st);
 cudaError_t launch_explicit(const GroupDev& g, cudaStream_t st);
+
+// One launch per kernel of each stage over all 2D groups of a context (in
+// place of one per group): the plan holds the grids of every launch and the
+// device copies of the groups and of their transform jobs (in `dev`, at
+// least multi2d_bytes(ng) bytes of the workspace, 256-byte aligned).  Groups
+// must all be 2D, of one precision, without tensor-core passes, at most
+// multi2d_max_groups() of them.  Results are bitwise those of the per-group
+// launches (each block computes what the same block of its group's own
+// launch computes).
+struct Multi2DPlan;
+int multi2d_max_groups();
+size_t multi2d_bytes(int ng);
+Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* dev, cudaStream_t st,
+                            cudaError_t* err);
+void multi2d_destroy(Multi2DPlan* p);
+cudaError_t launch_stage_multi(const Multi2DPlan* p, int stage, cudaStream_t st, int* nlaunch);
+cudaError_t launch_diag_multi(const Multi2DPlan* p, const DiagStreams& d, int* nlaunch);
 // physical staging [5][N][nx] -> state of member b (resets counter/status)
 cudaError_t launch_phys_to_state(const GroupDev& g, int b, cudaStream_t st);
 // state of member b -> physical staging [5][N][nx]

@@ -44,11 +44,11 @@ template <> __device__ __forceinline__ float2* zp_ptr<float2>(const GroupDev& g)
 // C2 = double2: the FP64 path; C2 = float2: the mixed path (FP32 transforms
 // and products, FP64 state and solves).
 template <typename C2>
-__global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
+__device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   using T = typename RealOf<C2>::T;
-  const int b = blockIdx.y;
+  const int b = bk.y;
   if (g.status[b]) return;
-  const int j = blockIdx.x;
+  const int j = bk.x;
   const int K = g.K, Mx = g.Mx, rows = g.M;
   const MemberPrm pr = g.prm[b];
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -124,6 +124,16 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
   }
 }
 
+template <typename C2>
+__global__ void __launch_bounds__(512) k_xfused(GroupDev g) { xfused_block<C2>(g, this_blk()); }
+
+template <typename C2>
+__global__ void __launch_bounds__(512) k_xfused_multi(const GroupDev* __restrict__ gs, MultiMap mm) {
+  Blk bk;
+  const int q = multi_locate(mm, bk);
+  xfused_block<C2>(gs[q], bk);
+}
+
 // The tau system solved per (mode, system, parity) by warp_qt_solve:
 //   (alpha - beta D^2) a = rsign * R   on tau rows n <= N-3,
 //   sum_{n = p mod 2} a_n = bcfac * sum_{n = p mod 2} rsign * R_n,
@@ -149,9 +159,9 @@ __global__ void __launch_bounds__(512) k_xfused(GroupDev g) {
 // stage about 25 % faster than one block at the ~160 registers ptxas picks
 // unbounded.
 template <int CH>
-__global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) {
-  const int b = blockIdx.y;
-  const int m = blockIdx.x;
+__device__ __forceinline__ void spec_block(const GroupDev& g, int mode, Blk bk) {
+  const int b = bk.y;
+  const int m = bk.x;
   if (g.status[b]) return;
   const int K = g.K, N = g.N, nb = g.nb;
   const size_t NK = (size_t)N * K;
@@ -315,10 +325,29 @@ __global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) {
   }
 }
 
+template <int CH>
+__global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) { spec_block<CH>(g, mode, this_blk()); }
+
+template <int CH>
+__global__ void __launch_bounds__(256, 2) k_spec_multi(const GroupDev* __restrict__ gs, MultiMap mm, int mode) {
+  Blk bk;
+  const int q = multi_locate(mm, bk);
+  spec_block<CH>(gs[q], mode, bk);
+}
+
 // Advance the step counters (after every block of k_spec has read them).
 __global__ void k_tick(GroupDev g) {
   const int b = threadIdx.x + blockIdx.x * blockDim.x;
   if (b < g.nb && !g.status[b]) g.count[b] += 1;
+}
+
+// The same for ng groups, one block per group.
+__global__ void k_tick_multi(const GroupDev* __restrict__ gs, int ng) {
+  const int q = blockIdx.x;
+  if (q >= ng) return;
+  const GroupDev& g = gs[q];
+  for (int b = threadIdx.x; b < g.nb; b += blockDim.x)
+    if (!g.status[b]) g.count[b] += 1;
 }
 
 // Complex transpose of nf fields: dst[f][c][r] = src[f][r][c] (rows x cols).
@@ -380,8 +409,8 @@ __device__ Red5 block_red5(Red5 r) {
   return r;
 }
 
-__global__ void __launch_bounds__(256) k_diag_part(GroupDev g) {
-  const int b = blockIdx.y, tile = blockIdx.x;
+__device__ __forceinline__ void diag_part_block(const GroupDev& g, Blk bk) {
+  const int b = bk.y, tile = bk.x;
   if (g.status[b]) return;
   const int K = g.K, N = g.N, nx = g.nx, Je = g.Me;
   const size_t NK = (size_t)N * K;
@@ -429,8 +458,8 @@ __global__ void __launch_bounds__(256) k_diag_part(GroupDev g) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_diag_count(GroupDev g) {
-  const int b = blockIdx.y, tile = blockIdx.x;
+__device__ __forceinline__ void diag_count_block(const GroupDev& g, Blk bk) {
+  const int b = bk.y, tile = bk.x;
   if (g.status[b]) return;
   const int N = g.N, nx = g.nx;
   const double tau = 1e-9 * block_tiles_max(g.part + (size_t)b * g.ntile * kPart, g.ntile, P_AMAX);
@@ -470,10 +499,10 @@ __global__ void __launch_bounds__(256) k_diag_count(GroupDev g) {
 // Mid-plane spectra at y = 0, one warp per (member, Fourier mode):
 // T_n(0) = cos(n pi/2), T_n'(0) = n sin(n pi/2).  DM[b][q][m], q = Tr c, u, v,
 // du/dy (Chebyshev sums; x derivatives and the mean are applied later).
-__global__ void __launch_bounds__(256) k_diag_mid(GroupDev g) {
-  const int b = blockIdx.y;
+__device__ __forceinline__ void diag_mid_block(const GroupDev& g, Blk bk) {
+  const int b = bk.y;
   if (g.status[b]) return;
-  const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int m = bk.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   const int K = g.K, N = g.N;
   if (m >= K) return;
@@ -507,8 +536,8 @@ __global__ void __launch_bounds__(256) k_diag_mid(GroupDev g) {
 
 // Per member: reduce the tiles, <Tr c> from the mean mode, mid-plane
 // statistics, blow-up test, record.
-__global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
-  const int b = blockIdx.x;
+__device__ __forceinline__ void diag_final_block(const GroupDev& g, Blk bk) {
+  const int b = bk.x;
   if (g.status[b]) return;
   __shared__ double sh[32];
   extern __shared__ double2 dsm[];
@@ -628,6 +657,31 @@ __global__ void __launch_bounds__(256) k_diag_final(GroupDev g) {
     if (blow) g.status[b] = 1;
     window_add(g.macc + (size_t)b * kMacc, r);
   }
+}
+
+__global__ void __launch_bounds__(256) k_diag_part(GroupDev g) { diag_part_block(g, this_blk()); }
+__global__ void __launch_bounds__(256) k_diag_part_multi(const GroupDev* __restrict__ gs, MultiMap mm) {
+  Blk bk;
+  const int q = multi_locate(mm, bk);
+  diag_part_block(gs[q], bk);
+}
+__global__ void __launch_bounds__(256) k_diag_count(GroupDev g) { diag_count_block(g, this_blk()); }
+__global__ void __launch_bounds__(256) k_diag_count_multi(const GroupDev* __restrict__ gs, MultiMap mm) {
+  Blk bk;
+  const int q = multi_locate(mm, bk);
+  diag_count_block(gs[q], bk);
+}
+__global__ void __launch_bounds__(256) k_diag_mid(GroupDev g) { diag_mid_block(g, this_blk()); }
+__global__ void __launch_bounds__(256) k_diag_mid_multi(const GroupDev* __restrict__ gs, MultiMap mm) {
+  Blk bk;
+  const int q = multi_locate(mm, bk);
+  diag_mid_block(gs[q], bk);
+}
+__global__ void __launch_bounds__(256) k_diag_final(GroupDev g) { diag_final_block(g, this_blk()); }
+__global__ void __launch_bounds__(256) k_diag_final_multi(const GroupDev* __restrict__ gs, MultiMap mm) {
+  Blk bk;
+  const int q = multi_locate(mm, bk);
+  diag_final_block(gs[q], bk);
 }
 
 // Spectral re-interpolation: destination coefficient (field, mode, n) from
@@ -797,6 +851,16 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
   if ((e = optin(k_ycols<double2>, optin_bytes))) return e;
   if ((e = optin(k_ycols<float2>, optin_bytes))) return e;
   if ((e = optin(k_ycols<double2, true>, optin_bytes))) return e;
+  if ((e = optin(k_ycols_multi<double2>, optin_bytes))) return e;
+  if ((e = optin(k_ycols_multi<float2>, optin_bytes))) return e;
+  if ((e = optin(k_ycols_multi<double2, true>, optin_bytes))) return e;
+  if ((e = optin(k_xfused_multi<double2>, optin_bytes))) return e;
+  if ((e = optin(k_xfused_multi<float2>, optin_bytes))) return e;
+  if ((e = optin(k_spec_multi<2>, optin_bytes))) return e;
+  if ((e = optin(k_spec_multi<4>, optin_bytes))) return e;
+  if ((e = optin(k_spec_multi<kMaxChunk>, optin_bytes))) return e;
+  if ((e = optin(k_xrows_multi, optin_bytes))) return e;
+  if ((e = optin(k_diag_final_multi, optin_bytes))) return e;
   if ((e = optin(k_xfused<double2>, optin_bytes))) return e;
   if ((e = optin(k_xfused<float2>, optin_bytes))) return e;
   if ((e = optin(k_xrows, optin_bytes))) return e;
@@ -809,8 +873,11 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
 
 // k_spec with the smallest tau-scan chunk that holds the group's rows:
 // ceil((L - 1)/32) rows per lane with L = (ny + 1)/2 coefficients of parity 0.
+// Tau-scan rows per lane of k_spec for a group's Chebyshev count.
+static int spec_rows(const GroupDev& g) { return ((g.N + 1) / 2 - 1 + 31) / 32; }
+
 static void launch_spec(const GroupDev& g, int mode, cudaStream_t st) {
-  const int rows = ((g.N + 1) / 2 - 1 + 31) / 32;
+  const int rows = spec_rows(g);
   const dim3 grid(g.K, g.nb);
   const size_t sm = smem_spec(g.N);
   if (rows <= 2) k_spec<2><<<grid, 256, sm, st>>>(g, mode);
@@ -818,10 +885,63 @@ static void launch_spec(const GroupDev& g, int mode, cudaStream_t st) {
   else k_spec<kMaxChunk><<<grid, 256, sm, st>>>(g, mode);
 }
 
+// Jobs of the y transforms and the Tr c x synthesis of a 2D group (shared by
+// the per-group launches and the launches over all groups).
+static YJob yjob_inverse(const GroupDev& g) {   // 9 fields on the padded Gauss grid
+  const size_t NK = (size_t)g.N * g.K;
+  YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4Pi);
+  J.src = g.X; J.dst = g.f32 ? (void*)g.Ypf : (void*)g.Yp;
+  J.dst_f32 = g.f32;
+  J.src_mstride = 5 * NK; J.dst_mstride = 9LL * g.M * g.K;
+  J.src_fstride = NK; J.dst_fstride = (long long)g.M * g.K;
+  const int sf[9] = {0, 1, 0, 2, 3, 4, 2, 3, 4};
+  const int dv[9] = {0, 0, 1, 0, 0, 0, 1, 1, 1};
+  for (int i = 0; i < 9; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = dv[i]; }
+  return J;
+}
+static YJob yjob_forward(const GroupDev& g) {   // the 5 explicit fields to coefficients
+  const size_t NK = (size_t)g.N * g.K;
+  YJob F = make_yjob(g, false, g.M, g.Ccol, g.plP, g.tw4P);
+  F.src = g.f32 ? (const void*)g.Zpf : (const void*)g.Zp; F.dst = g.NR;
+  F.src_f32 = g.f32;
+  F.src_mstride = 5LL * g.M * g.K; F.dst_mstride = 5 * NK;
+  F.src_fstride = (long long)g.M * g.K; F.dst_fstride = NK;
+  for (int i = 0; i < 5; ++i) { F.src_field[i] = i; F.dst_field[i] = i; F.deriv[i] = 0; }
+  return F;
+}
+static YJob yjob_energy(const GroupDev& g) {    // u, v on the Me Gauss points
+  const size_t NK = (size_t)g.N * g.K;
+  YJob J = make_yjob(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
+  J.src = g.X; J.dst = g.DY;
+  J.src_mstride = 5 * NK; J.dst_mstride = 2LL * g.Me * g.K;
+  J.src_fstride = NK; J.dst_fstride = (long long)g.Me * g.K;
+  for (int i = 0; i < 2; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
+  return J;
+}
+static YJob yjob_trc(const GroupDev& g) {       // c_xx + c_yy on the unpadded rows (DCT-I)
+  const size_t NK = (size_t)g.N * g.K;
+  YJob T = make_yjob(g, true, g.N - 1, g.CcolU, g.plPu);
+  T.src = g.X; T.dst = g.DT;
+  T.src_mstride = 5 * NK; T.dst_mstride = (long long)NK;
+  T.src_fstride = NK; T.dst_fstride = 0;
+  T.src_field[0] = 2; T.src_field2[0] = 4; T.dst_field[0] = 0; T.deriv[0] = 0;
+  return T;
+}
+static XJob xjob_trc(const GroupDev& g) {       // Tr c rows to the unpadded x grid
+  XJob X{};
+  X.srcC = g.DT; X.dstR = g.DV;
+  X.src_mstride = (long long)g.N * g.K; X.dst_mstride = (long long)g.N * g.nx;
+  X.src_fstride = 0; X.dst_fstride = 0;
+  X.src_rstep = 1; X.dst_rstep = 1;
+  X.nf = 1; X.K = g.K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
+  X.pair_rows = 1; X.nrows = g.N;
+  return X;
+}
+
+
 // Stage s of one step for one group (see ptt.h: PTT_NSTAGES).
 cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl) {
   const int rows = g.M;
-  const size_t NK = (size_t)g.N * g.K;
   int n = 0;
   switch (stage) {
     case 0: {  // inverse y: 9 fields on the padded Gauss grid, one launch
@@ -831,14 +951,7 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
         n = 1;
         break;
       }
-      YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4Pi);
-      J.src = g.X; J.dst = g.f32 ? (void*)g.Ypf : (void*)g.Yp;
-      J.dst_f32 = g.f32;
-      J.src_mstride = 5 * NK; J.dst_mstride = 9LL * rows * g.K;
-      J.src_fstride = NK; J.dst_fstride = (long long)rows * g.K;
-      const int sf[9] = {0, 1, 0, 2, 3, 4, 2, 3, 4};
-      const int dv[9] = {0, 0, 1, 0, 0, 0, 1, 1, 1};
-      for (int i = 0; i < 9; ++i) { J.src_field[i] = sf[i]; J.dst_field[i] = i; J.deriv[i] = dv[i]; }
+      const YJob J = yjob_inverse(g);
       const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
       if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
       else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
@@ -857,12 +970,7 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
         n = 1;
         break;
       }
-      YJob F = make_yjob(g, false, g.M, g.Ccol, g.plP, g.tw4P);
-      F.src = g.f32 ? (const void*)g.Zpf : (const void*)g.Zp; F.dst = g.NR;
-      F.src_f32 = g.f32;
-      F.src_mstride = 5LL * rows * g.K; F.dst_mstride = 5 * NK;
-      F.src_fstride = (long long)rows * g.K; F.dst_fstride = NK;
-      for (int i = 0; i < 5; ++i) { F.src_field[i] = i; F.dst_field[i] = i; F.deriv[i] = 0; }
+      const YJob F = yjob_forward(g);
       const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
       if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
       else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
@@ -906,22 +1014,12 @@ static cudaError_t diag_join(const DiagStreams& d) {
 // Gauss points of the energy quadrature; c_xx + c_yy on the unpadded
 // Gauss-Lobatto rows (DCT-I).
 static void diag_energy_y(const GroupDev& g, cudaStream_t st) {
-  const size_t NK = (size_t)g.N * g.K;
-  YJob J = make_yjob(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
-  J.src = g.X; J.dst = g.DY;
-  J.src_mstride = 5 * NK; J.dst_mstride = 2LL * g.Me * g.K;
-  J.src_fstride = NK; J.dst_fstride = (long long)g.Me * g.K;
-  for (int i = 0; i < 2; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
+  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(
+      yjob_energy(g));
 }
 static void diag_trc_y(const GroupDev& g, cudaStream_t st) {
-  const size_t NK = (size_t)g.N * g.K;
-  YJob T = make_yjob(g, true, g.N - 1, g.CcolU, g.plPu);
-  T.src = g.X; T.dst = g.DT;
-  T.src_mstride = 5 * NK; T.dst_mstride = (long long)NK;
-  T.src_fstride = NK; T.dst_fstride = 0;
-  T.src_field[0] = 2; T.src_field2[0] = 4; T.dst_field[0] = 0; T.deriv[0] = 0;
-  k_ycols<double2, true><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+  k_ycols<double2, true><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(
+      yjob_trc(g));
 }
 
 cudaError_t launch_diag_transforms(const GroupDev& g, cudaStream_t st) {
@@ -931,7 +1029,6 @@ cudaError_t launch_diag_transforms(const GroupDev& g, cudaStream_t st) {
 }
 
 cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nl) {
-  const size_t NK = (size_t)g.N * g.K;
   cudaError_t e = diag_fork(d);
   if (e) return e;
   diag_energy_y(g, d.s[1]);
@@ -939,18 +1036,160 @@ cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nl) 
   k_diag_mid<<<dim3(cdiv(g.K, 8), g.nb), 256, 0, d.s[2]>>>(g);
   // Tr c on the unpadded grid: y, then x
   diag_trc_y(g, d.s[0]);
-  XJob X{};
-  X.srcC = g.DT; X.dstR = g.DV;
-  X.src_mstride = (long long)NK; X.dst_mstride = (long long)g.N * g.nx;
-  X.src_fstride = 0; X.dst_fstride = 0;
-  X.src_rstep = 1; X.dst_rstep = 1;
-  X.nf = 1; X.K = g.K; X.n = g.nx; X.c2r = 1; X.status = g.status; X.pl = g.plNx;
-  X.pair_rows = 1; X.nrows = g.N;
-  k_xrows<<<dim3(cdiv(g.N, 2), g.nb), 256, smem_xrows(1, g.nx), d.s[0]>>>(X);
+  k_xrows<<<dim3(cdiv(g.N, 2), g.nb), 256, smem_xrows(1, g.nx), d.s[0]>>>(xjob_trc(g));
   if ((e = cudaGetLastError()) || (e = diag_join(d))) return e;
   k_diag_part<<<dim3(g.ntile, g.nb), 256, 0, d.s[0]>>>(g);
   k_diag_count<<<dim3(g.ntile, g.nb), 256, 0, d.s[0]>>>(g);
   k_diag_final<<<g.nb, 256, smem_xrows(3, g.nx), d.s[0]>>>(g);
+  if (nl) *nl += 7;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- launches over all groups
+struct Multi2DPlan {
+  int ng = 0, f32 = 0;
+  const GroupDev* dg = nullptr;
+  const YJob* dyj = nullptr;     // [4][ng]: inverse, forward, energy, Tr c
+  const XJob* dxj = nullptr;     // [ng]: Tr c x synthesis
+  MultiMap inv, fwd, xf, spec[3], ye, yt, xr, mid, part, cnt, fin;
+  size_t sm_inv = 0, sm_fwd = 0, sm_xf = 0, sm_spec[3] = {0, 0, 0}, sm_ye = 0, sm_yt = 0, sm_xr = 0,
+         sm_fin = 0;
+};
+
+int multi2d_max_groups() { return kMaxGroupsMulti; }
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t multi2d_bytes(int ng) {
+  return align256((size_t)ng * sizeof(GroupDev)) + align256((size_t)4 * ng * sizeof(YJob)) +
+         align256((size_t)ng * sizeof(XJob));
+}
+
+// Append group q with a launch grid (gx, gy, gz) to map mm.
+static void mm_add(MultiMap& mm, int q, unsigned gx, unsigned gy, unsigned gz) {
+  const int e = mm.ng++;
+  mm.gid[e] = q;
+  mm.gx[e] = (int)gx;
+  mm.gy[e] = (int)gy;
+  mm.gz[e] = (int)gz;
+  mm.start[e + 1] = mm.start[e] + gx * gy * gz;
+}
+
+Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* dev, cudaStream_t st,
+                            cudaError_t* err) {
+  *err = cudaSuccess;
+  const int ng = (int)groups.size();
+  if (ng < 1 || ng > kMaxGroupsMulti) { *err = cudaErrorInvalidValue; return nullptr; }
+  Multi2DPlan* p = new Multi2DPlan();
+  p->ng = ng;
+  p->f32 = groups[0]->f32;
+  std::vector<GroupDev> hg(ng);
+  std::vector<YJob> hy(4 * (size_t)ng);
+  std::vector<XJob> hx(ng);
+  MultiMap* maps[] = {&p->inv, &p->fwd, &p->xf, &p->spec[0], &p->spec[1], &p->spec[2], &p->ye,
+                      &p->yt, &p->xr, &p->mid, &p->part, &p->cnt, &p->fin};
+  for (MultiMap* m : maps) { m->ng = 0; m->start[0] = 0; }
+  for (int q = 0; q < ng; ++q) {
+    const GroupDev& g = *groups[q];
+    if (g.nz != 1 || g.f32 != p->f32 || g.ymma) { delete p; *err = cudaErrorInvalidValue; return nullptr; }
+    hg[q] = g;
+    hy[q] = yjob_inverse(g);
+    hy[ng + q] = yjob_forward(g);
+    hy[2 * (size_t)ng + q] = yjob_energy(g);
+    hy[3 * (size_t)ng + q] = yjob_trc(g);
+    hx[q] = xjob_trc(g);
+    mm_add(p->inv, q, cdiv(g.K, g.Ccol), 9, g.nb);
+    mm_add(p->fwd, q, cdiv(g.K, g.Ccol), 5, g.nb);
+    mm_add(p->xf, q, g.M, g.nb, 1);
+    const int rows = spec_rows(g);
+    const int cls = (rows <= 2) ? 0 : (rows <= 4) ? 1 : 2;
+    mm_add(p->spec[cls], q, g.K, g.nb, 1);
+    mm_add(p->ye, q, cdiv(g.K, g.CcolE), 2, g.nb);
+    mm_add(p->yt, q, cdiv(g.K, g.CcolU), 1, g.nb);
+    mm_add(p->xr, q, cdiv(g.N, 2), g.nb, 1);
+    mm_add(p->mid, q, cdiv(g.K, 8), g.nb, 1);
+    mm_add(p->part, q, g.ntile, g.nb, 1);
+    mm_add(p->cnt, q, g.ntile, g.nb, 1);
+    mm_add(p->fin, q, g.nb, 1, 1);
+    p->sm_inv = std::max(p->sm_inv, smem_ycols(g.Ccol, g.M, g.f32));
+    p->sm_fwd = p->sm_inv;
+    p->sm_xf = std::max(p->sm_xf, smem_xfused(g.Mx, g.f32));
+    p->sm_spec[cls] = std::max(p->sm_spec[cls], smem_spec(g.N));
+    p->sm_ye = std::max(p->sm_ye, smem_ycols(g.CcolE, g.Me, 0));
+    p->sm_yt = std::max(p->sm_yt, smem_ycols(g.CcolU, g.Pu, 0));
+    p->sm_xr = std::max(p->sm_xr, smem_xrows(1, g.nx));
+    p->sm_fin = std::max(p->sm_fin, smem_xrows(3, g.nx));
+  }
+  char* b = static_cast<char*>(dev);
+  p->dg = reinterpret_cast<const GroupDev*>(b);
+  p->dyj = reinterpret_cast<const YJob*>(b + align256((size_t)ng * sizeof(GroupDev)));
+  p->dxj = reinterpret_cast<const XJob*>(b + align256((size_t)ng * sizeof(GroupDev)) +
+                                          align256((size_t)4 * ng * sizeof(YJob)));
+  cudaError_t e = cudaMemcpyAsync((void*)p->dg, hg.data(), hg.size() * sizeof(GroupDev),
+                                  cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync((void*)p->dyj, hy.data(), hy.size() * sizeof(YJob), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync((void*)p->dxj, hx.data(), hx.size() * sizeof(XJob), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaStreamSynchronize(st);   // the host vectors go out of scope
+  if (e) { delete p; *err = e; return nullptr; }
+  return p;
+}
+
+void multi2d_destroy(Multi2DPlan* p) { delete p; }
+
+static unsigned mm_blocks(const MultiMap& m) { return m.start[m.ng]; }
+
+cudaError_t launch_stage_multi(const Multi2DPlan* p, int stage, cudaStream_t st, int* nl) {
+  int n = 0;
+  const int ng = p->ng;
+  switch (stage) {
+    case 0:
+      if (p->f32) k_ycols_multi<float2><<<mm_blocks(p->inv), 256, p->sm_inv, st>>>(p->dyj, p->inv);
+      else k_ycols_multi<double2><<<mm_blocks(p->inv), 256, p->sm_inv, st>>>(p->dyj, p->inv);
+      n = 1;
+      break;
+    case 1:
+      if (p->f32) k_xfused_multi<float2><<<mm_blocks(p->xf), 512, p->sm_xf, st>>>(p->dg, p->xf);
+      else k_xfused_multi<double2><<<mm_blocks(p->xf), 512, p->sm_xf, st>>>(p->dg, p->xf);
+      n = 1;
+      break;
+    case 2:
+      if (p->f32) k_ycols_multi<float2><<<mm_blocks(p->fwd), 256, p->sm_fwd, st>>>(p->dyj + ng, p->fwd);
+      else k_ycols_multi<double2><<<mm_blocks(p->fwd), 256, p->sm_fwd, st>>>(p->dyj + ng, p->fwd);
+      n = 1;
+      break;
+    case 3:
+      if (p->spec[0].ng) { k_spec_multi<2><<<mm_blocks(p->spec[0]), 256, p->sm_spec[0], st>>>(p->dg, p->spec[0], 0); ++n; }
+      if (p->spec[1].ng) { k_spec_multi<4><<<mm_blocks(p->spec[1]), 256, p->sm_spec[1], st>>>(p->dg, p->spec[1], 0); ++n; }
+      if (p->spec[2].ng) {
+        k_spec_multi<kMaxChunk><<<mm_blocks(p->spec[2]), 256, p->sm_spec[2], st>>>(p->dg, p->spec[2], 0);
+        ++n;
+      }
+      k_tick_multi<<<ng, 128, 0, st>>>(p->dg, ng);
+      ++n;
+      break;
+    case 4: {
+      const DiagStreams d{{st, st, st}, {nullptr, nullptr, nullptr}};
+      return launch_diag_multi(p, d, nl);
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+  if (nl) *nl += n;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_multi(const Multi2DPlan* p, const DiagStreams& d, int* nl) {
+  const int ng = p->ng;
+  cudaError_t e = diag_fork(d);
+  if (e) return e;
+  k_ycols_multi<double2><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
+  k_diag_mid_multi<<<mm_blocks(p->mid), 256, 0, d.s[2]>>>(p->dg, p->mid);
+  k_ycols_multi<double2, true><<<mm_blocks(p->yt), 256, p->sm_yt, d.s[0]>>>(p->dyj + 3 * ng, p->yt);
+  k_xrows_multi<<<mm_blocks(p->xr), 256, p->sm_xr, d.s[0]>>>(p->dxj, p->xr);
+  if ((e = cudaGetLastError()) || (e = diag_join(d))) return e;
+  k_diag_part_multi<<<mm_blocks(p->part), 256, 0, d.s[0]>>>(p->dg, p->part);
+  k_diag_count_multi<<<mm_blocks(p->cnt), 256, 0, d.s[0]>>>(p->dg, p->cnt);
+  k_diag_final_multi<<<mm_blocks(p->fin), 256, p->sm_fin, d.s[0]>>>(p->dg, p->fin);
   if (nl) *nl += 7;
   return cudaGetLastError();
 }
