@@ -46,7 +46,7 @@ def test_launch_modes_are_bitwise_equal(precision):
     (s0, d0, h0, n0), (s1, d1, h1, n1) = out
     for i in range(len(SHAPES)):
         assert np.array_equal(s0[i], s1[i]), i
-        assert len(d0[i]) == len(d1[i]) == 5
+        assert len(d0[i]) == len(d1[i]) == 6          # the initial record and 5 steps
         for a, b in zip(d0[i], d1[i]):
             for k, v in a.items():
                 assert np.array_equal(np.asarray(v), np.asarray(b[k])), (i, k)
