@@ -1089,6 +1089,10 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
   MultiMap* maps[] = {&p->inv, &p->fwd, &p->xf, &p->spec[0], &p->spec[1], &p->spec[2], &p->ye,
                       &p->yt, &p->xr, &p->mid, &p->part, &p->cnt, &p->fin};
   for (MultiMap* m : maps) { m->ng = 0; m->start[0] = 0; }
+  // Each launch lists the groups with the costliest blocks first, so that
+  // the blocks dispatched last, which set the launch's tail, are short ones.
+  struct Ent { double cost; int q; unsigned gx, gy, gz; };
+  std::vector<Ent> e_inv, e_fwd, e_xf, e_spec[3], e_ye, e_yt, e_xr, e_mid, e_part, e_fin;
   for (int q = 0; q < ng; ++q) {
     const GroupDev& g = *groups[q];
     if (g.nz != 1 || g.f32 != p->f32 || g.ymma) { delete p; *err = cudaErrorInvalidValue; return nullptr; }
@@ -1098,19 +1102,18 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
     hy[2 * (size_t)ng + q] = yjob_energy(g);
     hy[3 * (size_t)ng + q] = yjob_trc(g);
     hx[q] = xjob_trc(g);
-    mm_add(p->inv, q, cdiv(g.K, g.Ccol), 9, g.nb);
-    mm_add(p->fwd, q, cdiv(g.K, g.Ccol), 5, g.nb);
-    mm_add(p->xf, q, g.M, g.nb, 1);
+    e_inv.push_back({(double)g.Ccol * g.M, q, cdiv(g.K, g.Ccol), 9, (unsigned)g.nb});
+    e_fwd.push_back({(double)g.Ccol * g.M, q, cdiv(g.K, g.Ccol), 5, (unsigned)g.nb});
+    e_xf.push_back({(double)g.Mx, q, (unsigned)g.M, (unsigned)g.nb, 1});
     const int rows = spec_rows(g);
     const int cls = (rows <= 2) ? 0 : (rows <= 4) ? 1 : 2;
-    mm_add(p->spec[cls], q, g.K, g.nb, 1);
-    mm_add(p->ye, q, cdiv(g.K, g.CcolE), 2, g.nb);
-    mm_add(p->yt, q, cdiv(g.K, g.CcolU), 1, g.nb);
-    mm_add(p->xr, q, cdiv(g.N, 2), g.nb, 1);
-    mm_add(p->mid, q, cdiv(g.K, 8), g.nb, 1);
-    mm_add(p->part, q, g.ntile, g.nb, 1);
-    mm_add(p->cnt, q, g.ntile, g.nb, 1);
-    mm_add(p->fin, q, g.nb, 1, 1);
+    e_spec[cls].push_back({(double)g.N, q, (unsigned)g.K, (unsigned)g.nb, 1});
+    e_ye.push_back({(double)g.CcolE * g.Me, q, cdiv(g.K, g.CcolE), 2, (unsigned)g.nb});
+    e_yt.push_back({(double)g.CcolU * g.Pu, q, cdiv(g.K, g.CcolU), 1, (unsigned)g.nb});
+    e_xr.push_back({(double)g.nx, q, cdiv(g.N, 2), (unsigned)g.nb, 1});
+    e_mid.push_back({(double)g.N, q, cdiv(g.K, 8), (unsigned)g.nb, 1});
+    e_part.push_back({(double)g.N * g.nx / g.ntile, q, (unsigned)g.ntile, (unsigned)g.nb, 1});
+    e_fin.push_back({(double)g.nx + g.ntile, q, (unsigned)g.nb, 1, 1});
     p->sm_inv = std::max(p->sm_inv, smem_ycols(g.Ccol, g.M, g.f32));
     p->sm_fwd = p->sm_inv;
     p->sm_xf = std::max(p->sm_xf, smem_xfused(g.Mx, g.f32));
@@ -1120,6 +1123,22 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
     p->sm_xr = std::max(p->sm_xr, smem_xrows(1, g.nx));
     p->sm_fin = std::max(p->sm_fin, smem_xrows(3, g.nx));
   }
+  auto fill = [](MultiMap& m, std::vector<Ent>& v) {
+    std::stable_sort(v.begin(), v.end(), [](const Ent& a, const Ent& b) { return a.cost > b.cost; });
+    for (const Ent& x : v) mm_add(m, x.q, x.gx, x.gy, x.gz);
+  };
+  fill(p->inv, e_inv);
+  fill(p->fwd, e_fwd);
+  fill(p->xf, e_xf);
+  for (int c = 0; c < 3; ++c) fill(p->spec[c], e_spec[c]);
+  fill(p->ye, e_ye);
+  fill(p->yt, e_yt);
+  fill(p->xr, e_xr);
+  fill(p->mid, e_mid);
+  fill(p->part, e_part);
+  std::vector<Ent> e_cnt = e_part;
+  fill(p->cnt, e_cnt);
+  fill(p->fin, e_fin);
   char* b = static_cast<char*>(dev);
   p->dg = reinterpret_cast<const GroupDev*>(b);
   p->dyj = reinterpret_cast<const YJob*>(b + align256((size_t)ng * sizeof(GroupDev)));
