@@ -335,8 +335,12 @@ def midplane_stats(args):
         k = min(500, steps - done)
         ctx.step(k)
         done += k
-        r = ctx.diagnostics(0, 1024)[-1]
-        trace.append([done, r["energy"], float(np.sqrt(max(r["mid_sums"][1][1], 0.0) / (nx * nz)))])
+        recs = ctx.diagnostics(0, 1024)
+        if not recs:            # the FP64 run has stopped (blow-up): no new records
+            break
+        r = recs[-1]
+        trace.append([done, r["energy"], float(np.sqrt(max(r["mid_sums"][1][1], 0.0) / (nx * nz))),
+                      r["max_trc"], r["min_trc"], r["status"]])
     status = [P.ptt_status_string(ctx.synchronize())]
     seconds = time.time() - t0
     f, nrec = ctx.moments(0)
@@ -356,7 +360,7 @@ def midplane_stats(args):
                 "worst_moment_criterion": worst, "worst_histogram_l1": float(max(l1)),
                 "pass": bool(worst <= 0.05 and max(l1) < 0.05),
                 "records": nrec, "status": status, "seconds": seconds,
-                "trace_step_energy_urms_mid": trace})
+                "trace_step_energy_urms_mid_maxtrc_mintrc_status": trace})
     print(json.dumps(out))
 
 
