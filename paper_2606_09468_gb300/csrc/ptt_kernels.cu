@@ -57,25 +57,47 @@ __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   const C2* Y = yp_ptr<C2>(g) + (size_t)b * 9 * rows * K + (size_t)j * K;
   const T kfac = (T)(2.0 * 3.14159265358979323846 / pr.lx);
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < 7 * Mx; i += nt) {
-    const int l = (int)fdiv((unsigned)i, fast_div((unsigned)Mx)), k = i - l * Mx;
-    int kk = -1;
-    bool cj = false;
-    if (k < K) kk = k;
-    else if (k > Mx - K) { kk = Mx - k; cj = true; }
-    C2 h = zero2<C2>();
-    if (kk >= 0) {
-      const int fa = 2 * l, fb = 2 * l + 1;
-      C2 F = Y[(size_t)c_xsrc[fa] * rows * K + kk];
-      C2 G = Y[(size_t)c_xsrc[fb] * rows * K + kk];
-      if (kk == 0) { F.y = 0; G.y = 0; }
-      const T km = kfac * kk;
-      if (c_xik[fa]) F = cscl(mul_i(F), km);
-      if (c_xik[fb]) G = cscl(mul_i(G), km);
-      if (cj) { F = cconj(F); G = cconj(G); }
-      h = cadd(F, mul_i(G));
+  // the padded middle K <= k <= Mx - K of every line is zero
+  {
+    const int nmid = Mx - 2 * K + 1;
+    for (int i = tid; i < 7 * nmid; i += nt) {
+      const int l = (int)fdiv((unsigned)i, fast_div((unsigned)nmid)), k = K + (i - l * nmid);
+      A[l * Mx + k] = zero2<C2>();
     }
-    A[i] = h;
+  }
+  // items (line l, mode kk): the line's two fields loaded by one thread,
+  // coalesced along kk, a batch of items in flight at once, then written
+  // at k = kk and (conjugated) at Mx - kk
+  {
+    constexpr int kB = 4;   // items in flight per thread
+    const int nitem = 7 * K;
+    const FastDiv dK = fast_div((unsigned)K);
+    for (int i0 = tid; i0 < nitem; i0 += kB * nt) {
+      C2 F[kB], G[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int it = i0 + u * nt;
+        F[u] = G[u] = zero2<C2>();
+        if (it < nitem) {
+          const int l = (int)fdiv((unsigned)it, dK), kk = it - l * K;
+          F[u] = Y[(size_t)c_xsrc[2 * l] * rows * K + kk];
+          G[u] = Y[(size_t)c_xsrc[2 * l + 1] * rows * K + kk];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int it = i0 + u * nt;
+        if (it >= nitem) continue;
+        const int l = (int)fdiv((unsigned)it, dK), kk = it - l * K;
+        C2 f = F[u], gg = G[u];
+        if (kk == 0) { f.y = 0; gg.y = 0; }
+        const T km = kfac * kk;
+        if (c_xik[2 * l]) f = cscl(mul_i(f), km);
+        if (c_xik[2 * l + 1]) gg = cscl(mul_i(gg), km);
+        A[l * Mx + kk] = cadd(f, mul_i(gg));
+        if (kk > 0) A[l * Mx + Mx - kk] = cadd(cconj(f), mul_i(cconj(gg)));
+      }
+    }
   }
   __syncthreads();
   // the padded modes K .. Mx - K are zero (plans of Mx start with radix 3

@@ -145,30 +145,55 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
   const C2* Z = z3_ptr<C2>(g) + (size_t)b * 26 * plane + (size_t)row * K;
   const T kfac = (T)(2.0 * 3.14159265358979323846 / pr.lx);
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < 18 * Mx; i += nt) {
-    const int l = (int)fdiv((unsigned)i, fast_div((unsigned)Mx)), k = i - l * Mx;
-    int kk = -1;
-    bool cj = false;
-    if (k < K) kk = k;
-    else if (k > Mx - K) { kk = Mx - k; cj = true; }
-    C2 h = zero2<C2>();
-    if (kk >= 0) {
-      C2 F2[2];
-      for (int q = 0; q < 2; ++q) {
-        const int pf = 2 * l + q;
-        C2 v = zero2<C2>();
-        if (pf < 26) {
-          v = Z[(size_t)pf * plane + kk];
-        } else if (pf < 35) {
-          v = cscl(mul_i(Z[(size_t)(pf - 26) * plane + kk]), kfac * (T)kk);
-        }
-        if (kk == 0) v.y = 0;
-        if (cj) v = cconj(v);
-        F2[q] = v;
-      }
-      h = cadd(F2[0], mul_i(F2[1]));
+  // the padded middle K <= k <= Mx - K of every line is zero
+  {
+    const int nmid = Mx - 2 * K + 1;
+    for (int i = tid; i < 18 * nmid; i += nt) {
+      const int l = (int)fdiv((unsigned)i, fast_div((unsigned)nmid)), k = K + (i - l * nmid);
+      A[l * Mx + k] = zero2<C2>();
     }
-    A[i] = h;
+  }
+  // lines 0-12: the 26 loaded fields in pairs (2l, 2l+1); line 13 + r
+  // (r < 5): their x-derivatives i k (fields 2r, 2r+1; line 17 field 8
+  // alone).  Items (l < 13, mode kk): both fields' coefficients loaded by
+  // one thread, coalesced along kk, a batch of items in flight at once, then
+  // written at k = kk and (conjugated) at Mx - kk.
+  {
+    constexpr int kB = 4;   // items in flight per thread
+    const int nitem = 13 * K;
+    const FastDiv dK = fast_div((unsigned)K);
+    for (int i0 = tid; i0 < nitem; i0 += kB * nt) {
+      C2 F[kB], G[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int it = i0 + u * nt;
+        F[u] = G[u] = zero2<C2>();
+        if (it < nitem) {
+          const int l = (int)fdiv((unsigned)it, dK), kk = it - l * K;
+          F[u] = Z[(size_t)(2 * l) * plane + kk];
+          G[u] = Z[(size_t)(2 * l + 1) * plane + kk];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int it = i0 + u * nt;
+        if (it >= nitem) continue;
+        const int l = (int)fdiv((unsigned)it, dK), kk = it - l * K;
+        C2 f = F[u], gg = G[u];
+        if (kk == 0) { f.y = 0; gg.y = 0; }
+        A[l * Mx + kk] = cadd(f, mul_i(gg));
+        if (kk > 0) A[l * Mx + Mx - kk] = cadd(cconj(f), mul_i(cconj(gg)));
+        if (l < 5) {
+          const T fk = kfac * (T)kk;
+          C2 df = cscl(mul_i(F[u]), fk), dg = cscl(mul_i(G[u]), fk);
+          if (l == 4) dg = zero2<C2>();
+          if (kk == 0) { df.y = 0; dg.y = 0; }
+          const int ld = 13 + l;
+          A[ld * Mx + kk] = cadd(df, mul_i(dg));
+          if (kk > 0) A[ld * Mx + Mx - kk] = cadd(cconj(df), mul_i(cconj(dg)));
+        }
+      }
+    }
   }
   __syncthreads();
   C2* res = fft_lines<+1>(A, B, 18, Mx, g.plMx, g.plMx.radix[0] == 3);
