@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the default launch shapes instead of the autotuned ones")
     ap.add_argument("--paper-shapes", action="store_true",
-                    help="also time the paper's A1-A6 shapes (3D, mixed; FP64 where nx <= 256)")
+                    help="also time the paper's A1-A6 shapes (3D, mixed and FP64)")
     ap.add_argument("--stats-amplitude", type=float, default=I.AMPLITUDE,
                     help="perturbation amplitude of the midplane_stats runs")
     ap.add_argument("--stats-wi", type=float, default=I.PAPER["wi"],

@@ -324,7 +324,7 @@ int ptt_stage_work(ptt_ctx* ctx, double* flops, double* bytes, int32_t* launches
  * transform stages and keeps the fastest: threads per block of the fused x
  * pass (128..512), Chebyshev columns per block of the y passes and of the
  * diagnostics' two y transforms (1..16, as shared memory allows) and, in 3D,
- * x-mode lines per block of the z passes (1..16); then re-captures the step
+ * x-mode lines per block of the z passes (1..64); then re-captures the step
  * graph.  These launches read the state without changing it (the
  * diagnostics' records and histograms are not touched) and a launch shape
  * changes only which thread computes what, so results are bitwise the same

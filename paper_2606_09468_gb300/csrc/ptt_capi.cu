@@ -734,7 +734,7 @@ int ptt_workspace_size(const ptt_params* pm, int32_t nmem, size_t* bytes) {
   for (Group& g : groups) {
     if (g.d.nz == 1 && (smem_xfused(g.d.Mx, g.d.f32) > 227 * 1024 || smem_spec(g.d.N) > 227 * 1024))
       return PTT_EINVAL;
-    if (g.d.nz > 1 && smem_xfused3(g.d.Mx, g.d.f32) > 227 * 1024)
+    if (g.d.nz > 1 && smem_xfused3(g.d.Mx, g.d.f32) == 0)
       return PTT_EINVAL;
   }
   Carver cv;
@@ -863,7 +863,7 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
   for (Group& g : c->groups) {
     if (g.d.nz == 1 && (smem_xfused(g.d.Mx, g.d.f32) > (size_t)optin || smem_spec(g.d.N) > (size_t)optin))
       return PTT_EINVAL;
-    if (g.d.nz > 1 && smem_xfused3(g.d.Mx, g.d.f32) > (size_t)optin)
+    if (g.d.nz > 1 && (smem_xfused3(g.d.Mx, g.d.f32) == 0 || smem_xfused3(g.d.Mx, g.d.f32) > (size_t)optin))
       return PTT_EINVAL;
   }
   CK(set_kernel_attributes(optin));
@@ -1332,8 +1332,9 @@ int ptt_autotune(ptt_ctx* c, int32_t* choices, int32_t max_groups) {
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     GroupDev& d = c->groups[gi].d;
     const bool d3 = d.nz > 1;
-    // threads per block of the fused x pass (stage 1)
-    {
+    // threads per block of the fused x pass (stage 1); the in-place 3D
+    // form runs 512
+    if (!(d3 && xfused3_inplace(d.Mx, d.f32))) {
       int best = d.xthreads;
       float bt = 1e30f;
       for (int t = 128; t <= 512; t += 64) {
@@ -1381,11 +1382,12 @@ int ptt_autotune(ptt_ctx* c, int32_t* choices, int32_t max_groups) {
       cc = best;
     }
     if (d3) {
-      const int cand[] = {1, 2, 4, 8, 16};
+      // up to every x mode of a row in one block (whole 512-byte rows in and out)
+      const int cand[] = {1, 2, 4, 8, 16, 32, 64};
       int best = d.zC;
       float bt = 1e30f;
       for (int C : cand) {
-        if (smem_zcols3(C, d.Mz, d.f32) > (size_t)optin) continue;
+        if (C > d.K || smem_zcols3(C, d.Mz, d.f32) > (size_t)optin) continue;
         d.zC = C;
         float ms = 0;
         int s = time_stages_of(c, d, 0, 2, reps, &ms);

@@ -465,6 +465,87 @@ __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl, bool z
   return src;
 }
 
+// ---------------------------------------------- in-place FFT passes
+// For lines too long for two buffers in shared memory (the FP64 3D x pass
+// at Mx = 768): each pass gathers its butterflies' inputs into registers,
+// waits for the whole block, and writes the outputs over the same buffer.
+// Lines go in groups of at most kIpLines, so that a thread holds at most
+// ip_maxb(R) butterflies with blockDim.x = kIpThreads and n <= kIpMaxN.
+// Plain twiddles (FftPlan::tw).
+constexpr int kIpThreads = 512, kIpLines = 3, kIpMaxN = 768;
+__host__ __device__ constexpr int ip_maxb(int R) {
+  return (kIpLines * kIpMaxN / R + kIpThreads - 1) / kIpThreads;
+}
+
+template <int DIR, int R, typename C2>
+__device__ __forceinline__ void fft_pass_ip(C2* a, int nl, int ls, int n, int Ns,
+                                            const C2* __restrict__ tw, bool zmid) {
+  constexpr int MB = ip_maxb(R);
+  const int nb = n / R;
+  const int st = n / (Ns * R);
+  const int total = nl * nb;
+  const FastDiv dnb = fast_div((unsigned)nb), dns = fast_div((unsigned)Ns);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  C2 v[MB][R];
+#pragma unroll
+  for (int q = 0; q < MB; ++q) {
+    const int t = tid + q * nt;
+    if (t < total) {
+      const int l = (int)fdiv((unsigned)t, dnb), j = t - l * nb;
+      const C2* s = a + l * ls;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = (zmid && r == 1) ? zero2<C2>() : s[j + r * nb];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < MB; ++q) {
+    const int t = tid + q * nt;
+    if (t < total) {
+      const int l = (int)fdiv((unsigned)t, dnb), j = t - l * nb;
+      C2* d = a + l * ls;
+      const int jq = (int)fdiv((unsigned)j, dns), jm = j - jq * Ns;
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C2 w = __ldg(&tw[jm * r * st]);
+          if (DIR > 0) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      Bfly<DIR, R>::run(v[q]);
+      const int o = jq * Ns * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) d[o + r * Ns] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// In-place unnormalised DFT of nl lines of length pl.n (radices 2 to 5) in
+// `a`; zero_mid as for fft_lines.  Called by the whole block (kIpThreads
+// threads) after a __syncthreads(); ends with one.
+template <int DIR, typename C2>
+__device__ void fft_lines_inplace(C2* a, int nl, int ls, const FftPlan& pl, bool zero_mid = false) {
+  const C2* tw = plan_tw<C2>(pl);
+  for (int l0 = 0; l0 < nl; l0 += kIpLines) {
+    const int g = min(kIpLines, nl - l0);
+    C2* base = a + (size_t)l0 * ls;
+    int Ns = 1;
+    for (int s = 0; s < pl.nst; ++s) {
+      const int R = pl.radix[s];
+      const bool zm = (s == 0 && zero_mid && R == 3);
+      switch (R) {
+        case 2: fft_pass_ip<DIR, 2>(base, g, ls, pl.n, Ns, tw, false); break;
+        case 3: fft_pass_ip<DIR, 3>(base, g, ls, pl.n, Ns, tw, zm); break;
+        case 4: fft_pass_ip<DIR, 4>(base, g, ls, pl.n, Ns, tw, false); break;
+        default: fft_pass_ip<DIR, 5>(base, g, ls, pl.n, Ns, tw, false); break;
+      }
+      Ns *= R;
+    }
+  }
+}
+
 // SBDF coefficients, orders 1..4: a_0..a_4 and b_0..b_3 (Sec. 2: 4th-order
 // semi-implicit BDF; lower orders start the history).
 __constant__ double c_sa[4][5] = {{1.0, -1.0, 0.0, 0.0, 0.0},

@@ -201,7 +201,11 @@ cudaError_t launch_explicit3(const GroupDev& g, cudaStream_t st);
 cudaError_t launch_phys_to_state3(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_state_to_phys3(const GroupDev& g, int b, cudaStream_t st);
 cudaError_t launch_reset_member3(const GroupDev& g, int b, cudaStream_t st);
+// Shared memory of the 3D fused x pass: two buffers of 18 lines, or one
+// (in-place passes, 512 threads) where two do not fit and one does (FP64,
+// Mx <= 768); 0 when neither fits.
 size_t smem_xfused3(int Mx, int f32);
+bool xfused3_inplace(int Mx, int f32);
 size_t spec3_scratch_columns();
 size_t smem_zcols3(int C, int Mz, int f32);
 

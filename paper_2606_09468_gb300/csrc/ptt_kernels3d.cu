@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
         const int s = (mz < hz) ? mz : mz - nz;
         CT v = ld2<CT>(src, (long long)(m0 + c) * nz + mz, J.src_f32);
         if (dz) v = cscl(mul_i(v), kfac * (T)s);
-        A[c * Mz + ((s + Mz) % Mz)] = v;
+        A[c * Mz + (s >= 0 ? s : s + Mz)] = v;
       }
     }
     __syncthreads();
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
         CT v = zero2<CT>();
         if (mz != hz) {
           const int s = (mz < hz) ? mz : mz - nz;
-          v = cscl(res[c * Mz + ((s + Mz) % Mz)], inv);
+          v = cscl(res[c * Mz + (s >= 0 ? s : s + Mz)], inv);
         }
         st2<CT>(dst, (long long)(m0 + c) * nz + mz, J.dst_f32, v);
       }
@@ -130,7 +130,10 @@ template <typename C2> __device__ __forceinline__ C2* w3_ptr(const GroupDev& g);
 template <> __device__ __forceinline__ double2* w3_ptr<double2>(const GroupDev& g) { return g.W3; }
 template <> __device__ __forceinline__ float2* w3_ptr<float2>(const GroupDev& g) { return g.W3f; }
 
-template <typename C2>
+// IP: the lines stay in one buffer and every FFT pass works in place
+// (fft_lines_inplace; kIpThreads threads), for the FP64 lines too long for
+// two buffers in shared memory (Mx up to kIpMaxN).
+template <typename C2, bool IP = false>
 __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
   using T = typename RealOf<C2>::T;
   const int b = blockIdx.y;
@@ -196,8 +199,15 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
     }
   }
   __syncthreads();
-  C2* res = fft_lines<+1>(A, B, 18, Mx, g.plMx, g.plMx.radix[0] == 3);
-  C2* oth = (res == A) ? B : A;
+  C2* res;
+  C2* oth;
+  if constexpr (IP) {
+    fft_lines_inplace<+1>(A, 18, Mx, g.plMx, g.plMx.radix[0] == 3);
+    res = oth = A;   // each column x is read and rewritten by one thread
+  } else {
+    res = fft_lines<+1>(A, B, 18, Mx, g.plMx, g.plMx.radix[0] == 3);
+    oth = (res == A) ? B : A;
+  }
   const T eps = (T)pr.eps, iwi = (T)pr.inv_wi;
   for (int x = tid; x < Mx; x += nt) {
     T q[36];
@@ -241,7 +251,13 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
     }
   }
   __syncthreads();
-  C2* r2 = fft_lines<-1>(oth, res, 5, Mx, g.plMx);
+  C2* r2;
+  if constexpr (IP) {
+    fft_lines_inplace<-1>(oth, 5, Mx, g.plMx);
+    r2 = oth;
+  } else {
+    r2 = fft_lines<-1>(oth, res, 5, Mx, g.plMx);
+  }
   C2* W = w3_ptr<C2>(g) + (size_t)b * 9 * plane + (size_t)row * K;
   const T inv = (T)(1.0 / Mx);
   for (int i = tid; i < 5 * K; i += nt) {
@@ -802,7 +818,17 @@ cudaError_t optin3(F* fn, int optin_bytes) {
 
 }  // namespace
 
-size_t smem_xfused3(int Mx, int f32) { return (size_t)36 * Mx * (f32 ? sizeof(float2) : sizeof(double2)); }
+namespace {
+constexpr size_t kXfusedSmemMax = 227 * 1024;
+}
+bool xfused3_inplace(int Mx, int f32) {
+  return !f32 && (size_t)36 * Mx * sizeof(double2) > kXfusedSmemMax && Mx <= kIpMaxN;
+}
+size_t smem_xfused3(int Mx, int f32) {
+  const size_t es = f32 ? sizeof(float2) : sizeof(double2);
+  const size_t b = (xfused3_inplace(Mx, f32) ? 18 : 36) * (size_t)Mx * es;
+  return b <= kXfusedSmemMax ? b : 0;
+}
 size_t spec3_scratch_columns() { return kScr3; }
 size_t smem_zcols3(int C, int Mz, int f32) { return smem_zcols(C, Mz, f32); }
 
@@ -816,6 +842,7 @@ cudaError_t set_kernel_attributes3(int optin_bytes) {
   if ((e = optin3(k_ycols<double2, true>, optin_bytes))) return e;
   if ((e = optin3(k_xfused3<double2>, optin_bytes))) return e;
   if ((e = optin3(k_xfused3<float2>, optin_bytes))) return e;
+  if ((e = optin3(k_xfused3<double2, true>, optin_bytes))) return e;
   if ((e = optin3(k_xrows, optin_bytes))) return e;
   return cudaSuccess;
 }
@@ -868,6 +895,8 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
     }
     case 1:
       if (f32) k_xfused3<float2><<<dim3(M * Mz, g.nb), g.xthreads, smem_xfused3(g.Mx, 1), st>>>(g);
+      else if (xfused3_inplace(g.Mx, 0))
+        k_xfused3<double2, true><<<dim3(M * Mz, g.nb), kIpThreads, smem_xfused3(g.Mx, 0), st>>>(g);
       else k_xfused3<double2><<<dim3(M * Mz, g.nb), g.xthreads, smem_xfused3(g.Mx, 0), st>>>(g);
       n = 1;
       break;

@@ -42,6 +42,9 @@ def test_status_strings_and_param_checks_without_gpu(lib):
     # the largest admitted shapes
     assert P.ptt_workspace_size([P.make_params(nx=512, ny=513)]) > 0
     assert P.ptt_workspace_size([P.make_params(nx=8, ny=9, nz=512, lz=5.0)]) > 0
+    # 3D at nx = 512 in FP64 (the in-place x pass) and in mixed precision
+    for prec in (0, 1, 2):
+        assert P.ptt_workspace_size([P.make_params(nx=512, ny=17, nz=8, lz=5.0, precision=prec)]) > 0
     # the admitted lengths are 13-smooth: 14 = 2 7, ny - 1 = 65 = 5 13 pass; 34 = 2 17 does not
     for ok in (dict(nx=14), dict(ny=66), dict(nx=224), dict(nx=352), dict(nx=416), dict(ny=225),
                dict(nz=14, lz=5.0), dict(nz=26, lz=5.0)):

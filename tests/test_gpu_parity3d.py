@@ -334,3 +334,30 @@ def test_physical_layout_is_field_z_y_x():
     assert np.max(np.abs(ctx.get_state(0)[0] - phys[0])) <= 1e-14
     with pytest.raises(ValueError):
         ctx.set_state(0, np.zeros((9, ny, nz, nx)))
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(512, 17, 8), (480, 9, 4), (352, 13, 6)])
+def test_in_place_x_pass_fp64(nx, ny, nz):
+    """FP64 3D shapes whose fused x pass takes the in-place FFT form (one
+    buffer of 18 lines: padded Mx = 768, 720, 540, beyond two buffers in
+    shared memory): explicit right-hand side to 1e-12 and steps to k x 1e-11
+    against the oracle, as for the two-buffer form."""
+    ctx = _ctx([(nx, ny, nz)])
+    ora = _oracle(nx, ny, nz)
+    ora.init_state(6, 0.05)
+    extra = [I.random_spectral3(nx, ny, nz, seed=90 + f, decay=0.2, scale=0.01) for f in range(9)]
+    st = O3.State3(*(a + e for a, e in zip(ora.state.as_list(), extra)))
+    ctx.set_spectral(0, I.spectral3_to_abi(st.as_list()))
+    Nc, H = ora.explicit_terms(st)
+    e = _errs(I.abi_to_spectral3(ctx.explicit_rhs(0)), Nc + H)
+    assert np.all(e <= 1e-12), e
+    ctx.init_state(0, 4, 0.01)
+    ora.init_state(4, 0.01)
+    for k in range(1, 4):
+        ctx.step(1)
+        ora.step()
+        e = _errs(I.abi_to_phys3(ctx.get_state(0)), ora.get_physical())
+        assert np.all(e <= k * 1e-11), (k, e)
+    assert ctx.synchronize() == 0
+    d, od = ctx.diagnostics(0)[-1], ora.diagnostics()
+    assert abs(d["energy"] - od["energy"]) <= 1e-11 * od["energy"]
