@@ -81,7 +81,8 @@ def parse():
                     help="run one workload alone (3d_fp64, 3d_mixed, 3d_fp64_large, "
                          "3d_mixed_large, ensemble_mixed, ensemble_fp64, 2d_NXxNY[_mixed]: one "
                          "shape of the 2D sweep, three seeds; 'mixedtc' in place of 'mixed' "
-                         "selects the tensor-core Chebyshev passes instead of the FP32 FFTs) "
+                         "selects the tensor-core Chebyshev passes instead of the FP32 FFTs; "
+                         "3d_NXxNYxNZ[_mixed]: one 3D shape; paper_shapes: the A1-A6 timings) "
                          "and print its line, for profiling; or midplane_stats: mixed vs FP64 "
                          "mid-plane statistics of the 3D workload over --steps steps; or "
                          "longrun_2d / longrun_3d: per-step admissibility records of the 2D "
@@ -434,9 +435,15 @@ def only_workload(args):
         return midplane_stats(args)
     if name in ("longrun_2d", "longrun_3d"):
         return longrun(args)
+    if name == "paper_shapes":
+        print(json.dumps({"workload": name, "shapes": paper_shapes(args)}))
+        return
     prec = (P.PTT_MIXED_TC if "mixedtc" in name else P.PTT_MIXED if "mixed" in name else P.PTT_FP64)
     if name.startswith("3d"):
         nx, ny, nz = I.CHANNEL3D_LARGE if name.endswith("large") else I.CHANNEL3D
+        dims = name.split("_")[1]
+        if "x" in dims:   # 3d_NXxNYxNZ[_mixed]: one 3D shape
+            nx, ny, nz = (int(v) for v in dims.split("x"))
         params = [P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=prec, **I.PAPER)]
         seeds = [0]
         pts = nx * ny * nz
