@@ -442,7 +442,7 @@ def only_workload(args):
     if name.startswith("3d"):
         nx, ny, nz = I.CHANNEL3D_LARGE if name.endswith("large") else I.CHANNEL3D
         dims = name.split("_")[1]
-        if "x" in dims:   # 3d_NXxNYxNZ[_mixed]: one 3D shape
+        if dims[:1].isdigit():   # 3d_NXxNYxNZ[_mixed]: one 3D shape
             nx, ny, nz = (int(v) for v in dims.split("x"))
         params = [P.make_params(nx=nx, ny=ny, nz=nz, lz=I.LZ3, dt=I.DT, precision=prec, **I.PAPER)]
         seeds = [0]
