@@ -455,6 +455,8 @@ void group_sizes(int nx, int ny, int nz, Group& g) {
   d.KZ = d.K * nz;
   d.Mz = (nz > 1) ? next_smooth(3 * nz / 2 - 2) : 1;
   d.Mx = next_smooth(3 * nx / 2 - 2);
+  d.invMx = 1.0 / d.Mx;
+  d.invMxf = (float)d.invMx;
   int M = (3 * ny - 2 + 1) / 2;
   while ((M & 1) || !smooth235(M)) ++M;
   d.M = M;
@@ -709,15 +711,26 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
   std::vector<double2> inv;
   quarter_tables(d.M, tw4, inv);
   tw4.insert(tw4.end(), inv.begin(), inv.end());
-  prm.lx = p.lx; prm.lz = 1.0; prm.re = p.re; prm.wi = p.wi; prm.beta = p.beta; prm.eps = p.eps;
-  prm.kappa = p.kappa; prm.dt = p.dt;
-  prm.inv_wi = 1.0 / p.wi;
-  prm.gam = (1.0 - p.beta) / (p.re * p.wi);
-  prm.nu = p.beta / p.re;
-  prm.forcing = 2.0 / p.re;
-  prm.trc_max = p.blowup_trc_max > 0 ? p.blowup_trc_max : 1e300;
-  prm.u_max = p.blowup_u_max > 0 ? p.blowup_u_max : 1e300;
+  member_prm(p, prm);
   return PTT_OK;
+}
+
+void member_prm(const ptt_params& p, MemberPrm& q) {
+  q.lx = p.lx; q.lz = (p.nz > 1) ? p.lz : 1.0;
+  q.re = p.re; q.wi = p.wi; q.beta = p.beta; q.eps = p.eps;
+  q.kappa = p.kappa; q.dt = p.dt;
+  q.inv_wi = 1.0 / p.wi;
+  q.gam = (1.0 - p.beta) / (p.re * p.wi);
+  q.nu = p.beta / p.re;
+  q.forcing = 2.0 / p.re;
+  q.trc_max = p.blowup_trc_max > 0 ? p.blowup_trc_max : 1e300;
+  q.u_max = p.blowup_u_max > 0 ? p.blowup_u_max : 1e300;
+  q.kx1 = 2.0 * kPi / q.lx;
+  q.kz1 = 2.0 * kPi / q.lz;
+  q.kx1f = (float)q.kx1;
+  q.kz1f = (float)q.kz1;
+  q.epsf = (float)q.eps;
+  q.inv_wif = (float)q.inv_wi;
 }
 
 }  // namespace ptt
@@ -891,17 +904,7 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
     // member parameters
     std::vector<MemberPrm> mp(nb);
     for (int i = 0; i < nb; ++i) {
-      const ptt_params& p = pm[g.members[i]];
-      MemberPrm& q = mp[i];
-      q.lx = p.lx; q.lz = (p.nz > 1) ? p.lz : 1.0;
-      q.re = p.re; q.wi = p.wi; q.beta = p.beta; q.eps = p.eps;
-      q.kappa = p.kappa; q.dt = p.dt;
-      q.inv_wi = 1.0 / p.wi;
-      q.gam = (1.0 - p.beta) / (p.re * p.wi);
-      q.nu = p.beta / p.re;
-      q.forcing = 2.0 / p.re;
-      q.trc_max = p.blowup_trc_max > 0 ? p.blowup_trc_max : 1e300;
-      q.u_max = p.blowup_u_max > 0 ? p.blowup_u_max : 1e300;
+      member_prm(pm[g.members[i]], mp[i]);
     }
     CK(cudaMemcpyAsync(d.prm, mp.data(), nb * sizeof(MemberPrm), cudaMemcpyHostToDevice, c->stream));
     // row weights of the quasi-tridiagonal form

@@ -1258,6 +1258,161 @@ __global__ void __launch_bounds__(256) k_xrows_multi(const XJob* __restrict__ jo
 
 
 // ------------------------------------------------------------ reductions
+// The diagnostics compare, bound and count doubles through order-preserving
+// integer keys: FP64 compares, min/max and additions run at the FP64 rate
+// (about 1/64 of the FP32 rate here), integer ones at the ALU rate.
+// key(x) < key(y) exactly when x < y, for x, y not NaN, except -0 < +0.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dkey_val(long long k) {   // inverse of dkey
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ bool isnan_bits(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+
+// Extrema of Tr c as keys (min, max) and |Tr c| as bits (a non-negative
+// double orders as its bit pattern); NaN values are left out, as fmin and
+// fmax leave them out.  Empty: min LLONG_MAX, max LLONG_MIN, amax 0.
+struct KeyExt {
+  long long mn, mx, ma;
+};
+__device__ __forceinline__ KeyExt keyext_empty() {
+  return KeyExt{0x7fffffffffffffffLL, (long long)0x8000000000000000ULL, 0LL};
+}
+__device__ __forceinline__ void keyext_add(KeyExt& e, double t) {
+  if (isnan_bits(t)) return;
+  const long long k = dkey(t);
+  e.mn = min(e.mn, k);
+  e.mx = max(e.mx, k);
+  e.ma = max(e.ma, __double_as_longlong(t) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ void keyext_merge(KeyExt& e, const KeyExt& o) {
+  e.mn = min(e.mn, o.mn);
+  e.mx = max(e.mx, o.mx);
+  e.ma = max(e.ma, o.ma);
+}
+__device__ __forceinline__ KeyExt keyext_shfl_down(const KeyExt& e, int o) {
+  return KeyExt{__shfl_down_sync(0xffffffffu, e.mn, o), __shfl_down_sync(0xffffffffu, e.mx, o),
+                __shfl_down_sync(0xffffffffu, e.ma, o)};
+}
+
+// The counts of t < 3, t < 0, |t - 3| <= tau and |t| <= tau on keys.  For
+// tau <= 1.5, t - 3 is exact wherever |t - 3| <= tau can hold (Sterbenz's
+// lemma), so the band is the closed interval [RU(3 - tau), RD(3 + tau)] of
+// doubles; |t| <= tau is [-tau, tau] exactly.  A larger tau (a field far
+// past any physical value) takes the FP64 test.  NaN counts nowhere, as in
+// the FP64 comparisons.
+struct TrBands {
+  long long k3, lo3, hi3, lo0, hi0;
+  double tau;
+  bool exact;
+};
+__device__ __forceinline__ TrBands tr_bands(double tau) {
+  TrBands B;
+  B.tau = tau;
+  B.exact = (tau <= 1.5);
+  B.k3 = dkey(3.0);
+  B.lo3 = dkey(__dsub_ru(3.0, tau));
+  B.hi3 = dkey(__dadd_rd(3.0, tau));
+  B.lo0 = dkey(-tau);
+  B.hi0 = dkey(tau);
+  return B;
+}
+struct TrCounts {
+  int c3, c0, b3, b0;
+};
+__device__ __forceinline__ void tr_count(TrCounts& c, double t, const TrBands& B) {
+  if (isnan_bits(t)) return;
+  const long long k = dkey(t);
+  c.c3 += (k < B.k3);
+  c.c0 += (k < -1LL);   // below key(-0.0) = -1: negative and nonzero
+  if (B.exact) {
+    c.b3 += (k >= B.lo3 && k <= B.hi3);
+    c.b0 += (k >= B.lo0 && k <= B.hi0);
+  } else {
+    c.b3 += (fabs(t - 3.0) <= B.tau);
+    c.b0 += (fabs(t) <= B.tau);
+  }
+}
+
+// Block-wide sums of 64-bit integers and merges of extrema (fixed order).
+// sh: shared memory of at least 3 * 32 long longs; the results are valid in
+// every thread.
+__device__ long long block_isum(long long v, long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  long long s = 0;
+  for (int i = 0; i < nw; ++i) s += sh[i];
+  __syncthreads();
+  return s;
+}
+__device__ KeyExt block_keyext(KeyExt e, long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) keyext_merge(e, keyext_shfl_down(e, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) { sh[w] = e.mn; sh[32 + w] = e.mx; sh[64 + w] = e.ma; }
+  __syncthreads();
+  KeyExt r = keyext_empty();
+  for (int i = 0; i < nw; ++i) keyext_merge(r, KeyExt{sh[i], sh[32 + i], sh[64 + i]});
+  __syncthreads();
+  return r;
+}
+
+// Sums of 32 per-thread values over the block, one total per value: a
+// reduce-scatter across the lanes (at each of five levels a lane keeps half
+// of its values and adds its partner's copies of them: 31 additions per
+// lane, against 5 per value for a tree per value), then across the warps in
+// index order.  v is consumed; on return red[k], k < 32, holds the total of
+// v[k] (a fixed order: deterministic).  red: 32 * (blockDim.x / 32) doubles
+// of shared memory.
+__device__ void block_sum_scatter(double (&v)[32], double* red) {
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (l & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const double send = up ? v[i] : v[i + s];
+      const double keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  // lane l holds its warp's total of value l (index bits kept level by level)
+  __syncthreads();
+  red[w * 32 + l] = v[0];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = red[threadIdx.x];
+    for (int i = 1; i < nw; ++i) t += red[i * 32 + threadIdx.x];
+    red[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// Max of the non-negative doubles stored as bits in pp[t * kPart + slot]
+// over the ntile tiles of one member, on their bit patterns; every thread of
+// the block receives it.
+__device__ double block_tiles_amax(const double* pp, int ntile, int slot) {
+  __shared__ long long smk[32];
+  const long long* q = reinterpret_cast<const long long*>(pp);
+  long long m = 0;
+  for (int t = threadIdx.x; t < ntile; t += blockDim.x) m = max(m, q[(size_t)t * kPart + slot]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) smk[w] = m;
+  __syncthreads();
+  for (int i = 0; i < nw; ++i) m = max(m, smk[i]);
+  __syncthreads();
+  return __longlong_as_double(m);
+}
+
 // Max of pp[t * kPart + slot] over the ntile tiles of one member; every
 // thread of the block receives it.
 __device__ double block_tiles_max(const double* pp, int ntile, int slot) {

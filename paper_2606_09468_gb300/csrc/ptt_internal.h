@@ -42,7 +42,19 @@ struct MemberPrm {
   double lx, lz, re, wi, beta, eps, kappa, dt;
   double inv_wi, gam, nu, forcing;  // 1/Wi, (1-beta)/(Re Wi), beta/Re, 2/Re
   double trc_max, u_max;
+  // 2 pi / Lx, 2 pi / Lz and their FP32 roundings, computed on the host: a
+  // division per thread would cost the FP32 kernels tens of FP64 operations
+  double kx1, kz1;
+  float kx1f, kz1f;
+  float epsf, inv_wif;              // FP32 roundings of eps, 1/Wi
 };
+// Fills every field of q from p (lz = 1 in 2D).
+void member_prm(const ptt_params& p, MemberPrm& q);
+// A host-computed constant in the compute precision T: d, or its FP32
+// rounding f (no FP64 arithmetic or conversion in the FP32 kernels).
+template <typename T> __host__ __device__ __forceinline__ T as_prec(double d, float f);
+template <> __host__ __device__ __forceinline__ double as_prec<double>(double d, float) { return d; }
+template <> __host__ __device__ __forceinline__ float as_prec<float>(double, float f) { return f; }
 
 // Device view of one group: nb members with equal (nx, ny).
 // Spectral arrays are [member][field][m][n] (n fastest), complex double;
@@ -55,6 +67,8 @@ struct GroupDev {
   int f32;           // 1: mixed precision (FP32 transforms and products)
   int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
   int nz, Mz, KZ;    // z modes (1 in 2D), padded z points, modes per Chebyshev index (K * nz)
+  double invMx;      // 1 / Mx (host-computed), and its FP32 rounding
+  float invMxf;
   int Mx, M, P;      // padded x points, padded y Gauss points (= y FFT length), P = M
   int Pu, Me;        // y FFT length of the unpadded grid (2(N-1)); diagnostic Gauss points
   int Ccol, CcolE, CcolU;  // columns per block: padded / diagnostic / unpadded y passes

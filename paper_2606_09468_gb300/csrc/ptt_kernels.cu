@@ -55,7 +55,7 @@ __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   C2* A = reinterpret_cast<C2*>(smraw);
   C2* B = A + 7 * Mx;
   const C2* Y = yp_ptr<C2>(g) + (size_t)b * 9 * rows * K + (size_t)j * K;
-  const T kfac = (T)(2.0 * 3.14159265358979323846 / pr.lx);
+  const T kfac = as_prec<T>(pr.kx1, pr.kx1f);
   const int tid = threadIdx.x, nt = blockDim.x;
   // the padded middle K <= k <= Mx - K of every line is zero
   {
@@ -104,7 +104,7 @@ __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   // when Mx has no factor 5)
   C2* res = fft_lines<+1>(A, B, 7, Mx, g.plMx, g.plMx.radix[0] == 3);
   C2* oth = (res == A) ? B : A;
-  const T eps = (T)pr.eps, iwi = (T)pr.inv_wi;
+  const T eps = as_prec<T>(pr.eps, pr.epsf), iwi = as_prec<T>(pr.inv_wi, pr.inv_wif);
   for (int x = tid; x < Mx; x += nt) {
     const C2 h0 = res[x], h1 = res[Mx + x], h2 = res[2 * Mx + x], h3 = res[3 * Mx + x];
     const C2 h4 = res[4 * Mx + x], h5 = res[5 * Mx + x], h6 = res[6 * Mx + x];
@@ -131,7 +131,7 @@ __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   __syncthreads();
   C2* r2 = fft_lines<-1>(oth, res, 3, Mx, g.plMx);
   C2* Z = zp_ptr<C2>(g) + (size_t)b * 5 * rows * K + (size_t)j * K;
-  const T inv = (T)(1.0 / Mx);
+  const T inv = as_prec<T>(g.invMx, g.invMxf);
   for (int i = tid; i < 3 * K; i += nt) {
     const int l = (int)fdiv((unsigned)i, fast_div((unsigned)K)), k = i - l * K;
     const C2 hk = r2[l * Mx + k];
@@ -401,34 +401,16 @@ __global__ void k_transpose(const double2* __restrict__ src, double2* __restrict
 //   the state on the bit patterns; then the counts of Tr c < 3, < 0 and the
 //   tie bands |Tr c - 3|, |Tr c| <= tau = 1e-9 max|Tr c|.
 enum { P_E = 0, P_MIN, P_MAX, P_AMAX, P_BAD, P_C3, P_C0, P_B3, P_B0 };
+constexpr int kMidLanes = 8, kMidModesPerBlock = 256 / kMidLanes;   // k_diag_mid, 256 threads
+// Slot contents: P_E a double; P_MIN, P_MAX keys (dkey) of Tr c; P_AMAX the
+// bits of max |Tr c|; P_BAD and the counts 64-bit integers.
+__device__ __forceinline__ long long* islots(double* pp) { return reinterpret_cast<long long*>(pp); }
+__device__ __forceinline__ const long long* islots(const double* pp) {
+  return reinterpret_cast<const long long*>(pp);
+}
 
 __device__ __forceinline__ bool nonfinite(double x) {
   return (__double_as_longlong(x) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL;
-}
-
-// block-wide (sum, min, max, max, or) reduction, result valid in thread 0
-struct Red5 { double s, mn, mx, ma; int bad; };
-__device__ Red5 block_red5(Red5 r) {
-  __shared__ double ss[32], smn[32], smx[32], sma[32];
-  __shared__ int sbad[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    r.s += __shfl_down_sync(0xffffffffu, r.s, o);
-    r.mn = fmin(r.mn, __shfl_down_sync(0xffffffffu, r.mn, o));
-    r.mx = fmax(r.mx, __shfl_down_sync(0xffffffffu, r.mx, o));
-    r.ma = fmax(r.ma, __shfl_down_sync(0xffffffffu, r.ma, o));
-    r.bad |= __shfl_down_sync(0xffffffffu, r.bad, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) { ss[w] = r.s; smn[w] = r.mn; smx[w] = r.mx; sma[w] = r.ma; sbad[w] = r.bad; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-      r.s += ss[i]; r.mn = fmin(r.mn, smn[i]); r.mx = fmax(r.mx, smx[i]);
-      r.ma = fmax(r.ma, sma[i]); r.bad |= sbad[i];
-    }
-  }
-  return r;
 }
 
 __device__ __forceinline__ void diag_part_block(const GroupDev& g, Blk bk) {
@@ -437,29 +419,34 @@ __device__ __forceinline__ void diag_part_block(const GroupDev& g, Blk bk) {
   const int K = g.K, N = g.N, nx = g.nx, Je = g.Me;
   const size_t NK = (size_t)N * K;
   const double2* DY = g.DY + (size_t)b * 2 * Je * K;
-  Red5 r{0.0, 1e308, -1e308, 0.0, 0};
-  // energy: DY fields 0 (u) and 1 (v) on the Me Gauss points (Fejer weights)
+  double e = 0.0;
+  KeyExt ext = keyext_empty();
+  int bad = 0;
+  // energy: DY fields 0 (u) and 1 (v) on the Me Gauss points (Fejer
+  // weights); the modes m > 0 count twice (Parseval over +-m)
   {
-    const long long tot = (long long)Je * K, per = (tot + g.ntile - 1) / g.ntile;
-    const long long i0 = tile * per, i1 = min(tot, i0 + per);
-    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const int j = (int)(i / K), m = (int)(i - (long long)j * K);
+    const unsigned tot = (unsigned)Je * K, per = (tot + g.ntile - 1) / g.ntile;
+    const unsigned i0 = tile * per, i1 = min(tot, i0 + per);
+    const FastDiv dK = fast_div((unsigned)K);
+    double e0 = 0.0, e1 = 0.0;
+    for (unsigned i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const unsigned j = fdiv(i, dK), m = i - j * K;
       const double2 uu = DY[i], vv = DY[(size_t)Je * K + i];
-      const double w = (m == 0 ? 1.0 : 2.0) * g.ccw[j];
-      r.s += w * (uu.x * uu.x + uu.y * uu.y + vv.x * vv.x + vv.y * vv.y);
+      const double q = fma(uu.x, uu.x, fma(uu.y, uu.y, fma(vv.x, vv.x, vv.y * vv.y)));
+      if (m == 0) e0 = fma(g.ccw[j], q, e0);
+      else e1 = fma(g.ccw[j], q, e1);
     }
+    e = fma(2.0, e1, e0);
   }
-  // extrema of Tr c on the unpadded grid
+  // extrema of Tr c = (c_xx + c_yy) + 1 on the unpadded grid
   {
     const double* tr = g.DV + (size_t)b * N * nx;
     const long long tot = (long long)N * nx, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const double t = tr[i] + 1.0;
-      r.bad |= nonfinite(t);
-      r.mn = fmin(r.mn, t);
-      r.mx = fmax(r.mx, t);
-      r.ma = fmax(r.ma, fabs(t));
+      bad |= nonfinite(t);
+      keyext_add(ext, t);
     }
   }
   // non-finite state values (integer test)
@@ -467,16 +454,20 @@ __device__ __forceinline__ void diag_part_block(const GroupDev& g, Blk bk) {
     const double* X = reinterpret_cast<const double*>(g.X + (size_t)b * 5 * NK);
     const long long tot = 10LL * NK, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
-    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) r.bad |= nonfinite(X[i]);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) bad |= nonfinite(X[i]);
   }
-  r = block_red5(r);
+  __shared__ double sh[32];
+  __shared__ long long shk[96];
+  e = block_sum(e, sh);
+  ext = block_keyext(ext, shk);
+  bad = (int)block_isum(bad, shk);
   if (threadIdx.x == 0) {
     double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
-    pp[P_E] = r.s;
-    pp[P_MIN] = r.mn;
-    pp[P_MAX] = r.mx;
-    pp[P_AMAX] = r.ma;
-    pp[P_BAD] = r.bad ? 1.0 : 0.0;
+    pp[P_E] = e;
+    islots(pp)[P_MIN] = ext.mn;
+    islots(pp)[P_MAX] = ext.mx;
+    islots(pp)[P_AMAX] = ext.ma;
+    islots(pp)[P_BAD] = bad ? 1 : 0;
   }
 }
 
@@ -484,70 +475,66 @@ __device__ __forceinline__ void diag_count_block(const GroupDev& g, Blk bk) {
   const int b = bk.y, tile = bk.x;
   if (g.status[b]) return;
   const int N = g.N, nx = g.nx;
-  const double tau = 1e-9 * block_tiles_max(g.part + (size_t)b * g.ntile * kPart, g.ntile, P_AMAX);
+  const TrBands B = tr_bands(1e-9 * block_tiles_amax(g.part + (size_t)b * g.ntile * kPart, g.ntile, P_AMAX));
   const double* tr = g.DV + (size_t)b * N * nx;
   const long long tot = (long long)N * nx, per = (tot + g.ntile - 1) / g.ntile;
   const long long i0 = tile * per, i1 = min(tot, i0 + per);
-  int c3 = 0, c0 = 0, b3 = 0, b0 = 0;
-  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const double t = tr[i] + 1.0;
-    c3 += (t < 3.0);
-    c0 += (t < 0.0);
-    b3 += (fabs(t - 3.0) <= tau);
-    b0 += (fabs(t) <= tau);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    c3 += __shfl_down_sync(0xffffffffu, c3, o);
-    c0 += __shfl_down_sync(0xffffffffu, c0, o);
-    b3 += __shfl_down_sync(0xffffffffu, b3, o);
-    b0 += __shfl_down_sync(0xffffffffu, b0, o);
-  }
-  __shared__ int sc[4][32];
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { sc[0][w] = c3; sc[1][w] = c0; sc[2][w] = b3; sc[3][w] = b0; }
-  __syncthreads();
+  TrCounts c{0, 0, 0, 0};
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) tr_count(c, tr[i] + 1.0, B);
+  __shared__ long long shk[32];
+  const long long c3 = block_isum(c.c3, shk), c0 = block_isum(c.c0, shk);
+  const long long b3 = block_isum(c.b3, shk), b0 = block_isum(c.b0, shk);
   if (threadIdx.x == 0) {
-    long long t4[4] = {0, 0, 0, 0};
-    for (int q = 0; q < 4; ++q)
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t4[q] += sc[q][i];
-    double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
-    pp[P_C3] = (double)t4[0];
-    pp[P_C0] = (double)t4[1];
-    pp[P_B3] = (double)t4[2];
-    pp[P_B0] = (double)t4[3];
+    long long* pp = islots(g.part + ((size_t)b * g.ntile + tile) * kPart);
+    pp[P_C3] = c3;
+    pp[P_C0] = c0;
+    pp[P_B3] = b3;
+    pp[P_B0] = b0;
   }
 }
 
-// Mid-plane spectra at y = 0, one warp per (member, Fourier mode):
+// Mid-plane spectra at y = 0, kMidLanes lanes per (member, Fourier mode):
 // T_n(0) = cos(n pi/2), T_n'(0) = n sin(n pi/2).  DM[b][q][m], q = Tr c, u, v,
 // du/dy (Chebyshev sums; x derivatives and the mean are applied later).
+// A mode's partial sums meet over its lanes only (three shuffle levels).
+__device__ __forceinline__ double2 seg_sum2(double2 v) {
+#pragma unroll
+  for (int o = kMidLanes / 2; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o, kMidLanes);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o, kMidLanes);
+  }
+  return v;
+}
 __device__ __forceinline__ void diag_mid_block(const GroupDev& g, Blk bk) {
   const int b = bk.y;
   if (g.status[b]) return;
-  const int m = bk.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+  const int sub = threadIdx.x & (kMidLanes - 1);
+  const int m = bk.x * (blockDim.x / kMidLanes) + (threadIdx.x / kMidLanes);
   const int K = g.K, N = g.N;
-  if (m >= K) return;
+  const bool on = m < K;   // every lane takes part in the shuffles
   const size_t NK = (size_t)N * K;
-  const double2* X = g.X + (size_t)b * 5 * NK + (size_t)m * N;
+  const double2* X = g.X + (size_t)b * 5 * NK + (size_t)(on ? m : 0) * N;
   double2 tr = czero(), u = czero(), v = czero(), uy = czero();
-  for (int n = lane; n < N; n += 32) {
-    const int r4 = n & 3;
+  if (on) {
+    // n = sub (mod kMidLanes): one residue of n mod 4 per lane
+    const int r4 = sub & 3;
     if (r4 == 0 || r4 == 2) {
       const double s = (r4 == 0) ? 1.0 : -1.0;
-      tr = cfma(s, cadd(X[2 * NK + n], X[4 * NK + n]), tr);
-      u = cfma(s, X[n], u);
-      v = cfma(s, X[NK + n], v);
+      for (int n = sub; n < N; n += kMidLanes) {
+        tr = cfma(s, cadd(X[2 * NK + n], X[4 * NK + n]), tr);
+        u = cfma(s, X[n], u);
+        v = cfma(s, X[NK + n], v);
+      }
     } else {
-      const double s = (r4 == 1) ? (double)n : -(double)n;
-      uy = cfma(s, X[n], uy);
+      const double s = (r4 == 1) ? 1.0 : -1.0;
+      for (int n = sub; n < N; n += kMidLanes) uy = cfma(s * n, X[n], uy);
     }
   }
-  tr = warp_sum2(tr);
-  u = warp_sum2(u);
-  v = warp_sum2(v);
-  uy = warp_sum2(uy);
-  if (lane == 0) {
+  tr = seg_sum2(tr);
+  u = seg_sum2(u);
+  v = seg_sum2(v);
+  uy = seg_sum2(uy);
+  if (on && sub == 0) {
     double2* D = g.DM + (size_t)b * 4 * K + m;
     D[0] = tr;
     D[K] = u;
@@ -567,22 +554,25 @@ __device__ __forceinline__ void diag_final_block(const GroupDev& g, Blk bk) {
   const size_t NK = (size_t)N * K;
   const MemberPrm pr = g.prm[b];
   const double* pp = g.part + (size_t)b * g.ntile * kPart;
-  const double tau = 1e-9 * block_tiles_max(pp, g.ntile, P_AMAX);
   // tile results, each thread a fixed set of tiles, then fixed-order trees
-  double te = 0.0, tmn = 1e308, tmx = -1e308, tbad = 0.0, tc[4] = {0, 0, 0, 0};
+  // (the energy in FP64, extrema and counts on integers)
+  __shared__ long long shk[96];
+  double te = 0.0;
+  KeyExt ext = keyext_empty();
+  long long tbad = 0, tc[4] = {0, 0, 0, 0};
   for (int t = threadIdx.x; t < g.ntile; t += blockDim.x) {
     const double* q = pp + (size_t)t * kPart;
+    const long long* qi = islots(q);
     te += q[P_E];
-    tmn = fmin(tmn, q[P_MIN]);
-    tmx = fmax(tmx, q[P_MAX]);
-    tbad = fmax(tbad, q[P_BAD]);
-    for (int k = 0; k < 4; ++k) tc[k] += q[P_C3 + k];
+    keyext_merge(ext, KeyExt{qi[P_MIN], qi[P_MAX], qi[P_AMAX]});
+    tbad |= qi[P_BAD];
+    for (int k = 0; k < 4; ++k) tc[k] += qi[P_C3 + k];
   }
   te = block_sum(te, sh);
-  tmn = -block_tiles_max_val(-tmn, sh);
-  tmx = block_tiles_max_val(tmx, sh);
-  tbad = block_tiles_max_val(tbad, sh);
-  for (int k = 0; k < 4; ++k) tc[k] = block_sum(tc[k], sh);
+  ext = block_keyext(ext, shk);
+  tbad = block_isum(tbad, shk);
+  for (int k = 0; k < 4; ++k) tc[k] = block_isum(tc[k], shk);
+  const TrBands B = tr_bands(1e-9 * __longlong_as_double(ext.ma));
   const double2* X = g.X + (size_t)b * 5 * NK;
   // <Tr c> = 1/2 int (c_xx + c_yy)_0 dy + 1, int T_n = 2/(1-n^2), n even
   double mt = 0.0;
@@ -620,10 +610,12 @@ __device__ __forceinline__ void diag_final_block(const GroupDev& g, Blk bk) {
   bool hon = false;
 #pragma unroll
   for (int q = 0; q < 6; ++q) hon |= (hr[2 * q] < hr[2 * q + 1]);
-  // mid-plane counts (4) and power sums (6 quantities x 4 powers), one pass
-  double acc[28];
+  // mid-plane counts (4, on integer keys) and power sums (6 quantities x 4
+  // powers, padded to 32 for the reduce-scatter), one pass
+  double acc[32];
 #pragma unroll
-  for (int k = 0; k < 28; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+  TrCounts mc{0, 0, 0, 0};
   for (int x = threadIdx.x; x < nx; x += blockDim.x) {
     double q[6];
 #pragma unroll
@@ -635,29 +627,28 @@ __device__ __forceinline__ void diag_final_block(const GroupDev& g, Blk bk) {
         if (sl >= 0) atomicAdd(&hsm[qq * HS + sl], 1u);
       }
     }
-    acc[0] += (q[0] < 3.0);
-    acc[1] += (q[0] < 0.0);
-    acc[2] += (fabs(q[0] - 3.0) <= tau);
-    acc[3] += (fabs(q[0]) <= tau);
+    tr_count(mc, q[0], B);
 #pragma unroll
     for (int qq = 0; qq < 6; ++qq) {
       const double a = q[qq], a2 = a * a;
-      acc[4 + 4 * qq] += a;
-      acc[5 + 4 * qq] += a2;
-      acc[6 + 4 * qq] += a2 * a;
-      acc[7 + 4 * qq] += a2 * a2;
+      acc[4 * qq] += a;
+      acc[4 * qq + 1] += a2;
+      acc[4 * qq + 2] += a2 * a;
+      acc[4 * qq + 3] += a2 * a2;
     }
   }
-  __shared__ double red[8 * 28];
-  block_sum_many<28>(acc, red);   // its barriers also complete the shared counts
+  __shared__ double red[8 * 32];
+  block_sum_scatter(acc, red);   // its barriers also complete the shared counts
+  const long long m3 = block_isum(mc.c3, shk), m0 = block_isum(mc.c0, shk);
+  const long long mb3 = block_isum(mc.b3, shk), mb0 = block_isum(mc.b0, shk);
   if (hon) {
     unsigned long long* gh = g.hist + (size_t)b * 8 * HS;
     for (int i = threadIdx.x; i < 6 * HS; i += blockDim.x)
       if (hsm[i]) atomicAdd(&gh[i], (unsigned long long)hsm[i]);
   }
   if (threadIdx.x == 0) {
-    const double e = 0.25 * te, mn = tmn, mx = tmx, *c4 = tc;
-    const bool bad = (tbad != 0.0);
+    const double e = 0.25 * te;
+    const bool bad = (tbad != 0);
     const long long step = g.count[b];
     const double qnan = __longlong_as_double(0x7ff8000000000000LL);
     ptt_diag& r = g.ring[(size_t)b * kRing + (size_t)(step % kRing)];
@@ -665,14 +656,14 @@ __device__ __forceinline__ void diag_final_block(const GroupDev& g, Blk bk) {
     r.t = step * pr.dt;
     r.energy = e;
     r.mean_trc = 0.5 * mt + 1.0;
-    r.min_trc = bad ? qnan : mn;
-    r.max_trc = bad ? qnan : mx;
-    r.n_lt3 = (long long)c4[0]; r.n_lt0 = (long long)c4[1];
-    r.n_band3 = (long long)c4[2]; r.n_band0 = (long long)c4[3];
-    r.n_mid_lt3 = (long long)red[0]; r.n_mid_lt0 = (long long)red[1];
-    r.n_mid_band3 = (long long)red[2]; r.n_mid_band0 = (long long)red[3];
+    r.min_trc = bad ? qnan : dkey_val(ext.mn);
+    r.max_trc = bad ? qnan : dkey_val(ext.mx);
+    r.n_lt3 = tc[0]; r.n_lt0 = tc[1];
+    r.n_band3 = tc[2]; r.n_band0 = tc[3];
+    r.n_mid_lt3 = m3; r.n_mid_lt0 = m0;
+    r.n_mid_band3 = mb3; r.n_mid_band0 = mb0;
     for (int qq = 0; qq < 8; ++qq)
-      for (int k = 0; k < 4; ++k) r.mid_sums[qq][k] = (qq < 6) ? red[4 + 4 * qq + k] : 0.0;
+      for (int k = 0; k < 4; ++k) r.mid_sums[qq][k] = (qq < 6) ? red[4 * qq + k] : 0.0;
     const bool blow = bad || !isfinite(e) || r.max_trc > pr.trc_max || sqrt(2.0 * e) > pr.u_max;
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
@@ -1055,7 +1046,7 @@ cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nl) 
   if (e) return e;
   diag_energy_y(g, d.s[1]);
   // mid-plane sums per Fourier mode
-  k_diag_mid<<<dim3(cdiv(g.K, 8), g.nb), 256, 0, d.s[2]>>>(g);
+  k_diag_mid<<<dim3(cdiv(g.K, kMidModesPerBlock), g.nb), 256, 0, d.s[2]>>>(g);
   // Tr c on the unpadded grid: y, then x
   diag_trc_y(g, d.s[0]);
   k_xrows<<<dim3(cdiv(g.N, 2), g.nb), 256, smem_xrows(1, g.nx), d.s[0]>>>(xjob_trc(g));
@@ -1133,7 +1124,7 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
     e_ye.push_back({(double)g.CcolE * g.Me, q, cdiv(g.K, g.CcolE), 2, (unsigned)g.nb});
     e_yt.push_back({(double)g.CcolU * g.Pu, q, cdiv(g.K, g.CcolU), 1, (unsigned)g.nb});
     e_xr.push_back({(double)g.nx, q, cdiv(g.N, 2), (unsigned)g.nb, 1});
-    e_mid.push_back({(double)g.N, q, cdiv(g.K, 8), (unsigned)g.nb, 1});
+    e_mid.push_back({(double)g.N, q, cdiv(g.K, kMidModesPerBlock), (unsigned)g.nb, 1});
     e_part.push_back({(double)g.N * g.nx / g.ntile, q, (unsigned)g.ntile, (unsigned)g.nb, 1});
     e_fin.push_back({(double)g.nx + g.ntile, q, (unsigned)g.nb, 1, 1});
     p->sm_inv = std::max(p->sm_inv, smem_ycols(g.Ccol, g.M, g.f32));

@@ -39,6 +39,8 @@ struct ZJob {
   int dst_field[32];
   int dz[32];         // inverse: transform d/dz of the field
   int K, nz, Mz;      // x modes, z modes, z points
+  double inv;         // forward: 1 / Mz (host-computed), and its FP32 rounding
+  float invf;
   int inverse;
   int C;              // mx lines per block
   int rows;           // y rows per field
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
         (b * J.src_mstride + J.src_field[f] * J.src_fstride + (long long)j * K * nz) * es;
     void* dst = static_cast<char*>(J.dst) +
         (b * J.dst_mstride + J.dst_field[f] * J.dst_fstride + (long long)j * Mz * K) * ed;
-    const T kfac = (T)(2.0 * 3.14159265358979323846 / J.prm[b].lz);
+    const T kfac = as_prec<T>(J.prm[b].kz1, J.prm[b].kz1f);
     const int dz = J.dz[f];
     for (int i = tid; i < C * Mz; i += nt) A[i] = zero2<CT>();
     __syncthreads();
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
     }
     __syncthreads();
     CT* res = fft_lines<-1, CT, BIG>(A, B, C, Mz, J.pl);
-    const T inv = (T)(1.0 / Mz);
+    const T inv = as_prec<T>(J.inv, J.invf);
     for (int i = tid; i < C * nz; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)nz)), mz = i - c * nz;
       if (c < nc) {
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
   C2* A = reinterpret_cast<C2*>(smraw);
   C2* B = A + 18 * Mx;
   const C2* Z = z3_ptr<C2>(g) + (size_t)b * 26 * plane + (size_t)row * K;
-  const T kfac = (T)(2.0 * 3.14159265358979323846 / pr.lx);
+  const T kfac = as_prec<T>(pr.kx1, pr.kx1f);
   const int tid = threadIdx.x, nt = blockDim.x;
   // the padded middle K <= k <= Mx - K of every line is zero
   {
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
     res = fft_lines<+1>(A, B, 18, Mx, g.plMx, g.plMx.radix[0] == 3);
     oth = (res == A) ? B : A;
   }
-  const T eps = (T)pr.eps, iwi = (T)pr.inv_wi;
+  const T eps = as_prec<T>(pr.eps, pr.epsf), iwi = as_prec<T>(pr.inv_wi, pr.inv_wif);
   for (int x = tid; x < Mx; x += nt) {
     T q[36];
 #pragma unroll
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
     r2 = fft_lines<-1>(oth, res, 5, Mx, g.plMx);
   }
   C2* W = w3_ptr<C2>(g) + (size_t)b * 9 * plane + (size_t)row * K;
-  const T inv = (T)(1.0 / Mx);
+  const T inv = as_prec<T>(g.invMx, g.invMxf);
   for (int i = tid; i < 5 * K; i += nt) {
     const int l = (int)fdiv((unsigned)i, fast_div((unsigned)K)), k = i - l * K;
     const C2 hk = r2[l * Mx + k];
@@ -514,34 +516,29 @@ __global__ void k_tick3(GroupDev g) {
 }
 
 // ------------------------------------------------------------ diagnostics
+// Tile slots: P_E a double; P_MIN, P_MAX keys (dkey) of Tr c; P_AMAX the
+// bits of max |Tr c|; P_BAD and the counts 64-bit integers; P_MS the
+// mid-plane power sums (doubles, in the first mid_tiles tiles only).
 enum { P_E = 0, P_MIN, P_MAX, P_AMAX, P_BAD, P_C3, P_C0, P_B3, P_B0,
        P_MC3, P_MC0, P_MB3, P_MB0, P_MS = 16 /* 8 quantities x 4 powers */ };
+constexpr int kMidLanes3 = 8, kMidModesPerBlock3 = 256 / kMidLanes3;   // k_diag_mid3
+constexpr int kMidTilePts = 2048;   // mid-plane points per tile of k_diag_count3
 
+__device__ __forceinline__ long long* islots3(double* pp) { return reinterpret_cast<long long*>(pp); }
+__device__ __forceinline__ const long long* islots3(const double* pp) {
+  return reinterpret_cast<const long long*>(pp);
+}
 __device__ __forceinline__ bool nonfinite3(double x) {
   return (__double_as_longlong(x) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL;
 }
-
-struct R5 { double s, mn, mx, ma; int bad; };
-__device__ R5 block_r5(R5 r) {
-  __shared__ double ss[32], smn[32], smx[32], sma[32];
-  __shared__ int sbad[32];
-  for (int o2 = 16; o2 > 0; o2 >>= 1) {
-    r.s += __shfl_down_sync(0xffffffffu, r.s, o2);
-    r.mn = fmin(r.mn, __shfl_down_sync(0xffffffffu, r.mn, o2));
-    r.mx = fmax(r.mx, __shfl_down_sync(0xffffffffu, r.mx, o2));
-    r.ma = fmax(r.ma, __shfl_down_sync(0xffffffffu, r.ma, o2));
-    r.bad |= __shfl_down_sync(0xffffffffu, r.bad, o2);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) { ss[w] = r.s; smn[w] = r.mn; smx[w] = r.mx; sma[w] = r.ma; sbad[w] = r.bad; }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-      r.s += ss[i]; r.mn = fmin(r.mn, smn[i]); r.mx = fmax(r.mx, smx[i]);
-      r.ma = fmax(r.ma, sma[i]); r.bad |= sbad[i];
-    }
-  return r;
+// mid-plane points per tile (at least kMidTilePts, and all npl points within
+// the ntile tiles) and the number of tiles that carry them
+__device__ __forceinline__ int mid_per(int npl, int ntile) {
+  return max(kMidTilePts, (npl + ntile - 1) / ntile);
+}
+__device__ __forceinline__ int mid_tiles(int npl, int ntile) {
+  const int per = mid_per(npl, ntile);
+  return (npl + per - 1) / per;
 }
 
 // Energy (Fejer in y, Parseval in x and z), extrema of Tr c on the unpadded
@@ -552,20 +549,24 @@ __global__ void __launch_bounds__(256) k_diag_part3(GroupDev g) {
   const int KZ = g.KZ, N = g.N, nx = g.nx, nz = g.nz, Je = g.Me;
   const size_t NK = (size_t)N * KZ;
   const double2* DY = g.DY + (size_t)b * 3 * Je * KZ;
-  R5 r{0.0, 1e308, -1e308, 0.0, 0};
+  double e = 0.0;
+  KeyExt ext = keyext_empty();
+  int bad = 0;
   {
-    const long long tot = (long long)Je * KZ, per = (tot + g.ntile - 1) / g.ntile;
-    const long long i0 = tile * per, i1 = min(tot, i0 + per);
-    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const int j = (int)(i / KZ), md = (int)(i - (long long)j * KZ);
-      const int mx = md / nz;
-      double e = 0.0;
-      for (int f = 0; f < 3; ++f) {
-        const double2 a = DY[(size_t)f * Je * KZ + i];
-        e += a.x * a.x + a.y * a.y;
-      }
-      r.s += (mx == 0 ? 1.0 : 2.0) * g.ccw[j] * e;
+    // modes mx > 0 count twice (Parseval over +-kx)
+    const unsigned tot = (unsigned)Je * KZ, per = (tot + g.ntile - 1) / g.ntile;
+    const unsigned i0 = tile * per, i1 = min(tot, i0 + per);
+    const FastDiv dKZ = fast_div((unsigned)KZ);
+    double e0 = 0.0, e1 = 0.0;
+    for (unsigned i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const unsigned j = fdiv(i, dKZ), md = i - j * KZ;
+      const double2 a0 = DY[i], a1 = DY[(size_t)Je * KZ + i], a2 = DY[(size_t)2 * Je * KZ + i];
+      const double q = fma(a0.x, a0.x, fma(a0.y, a0.y, fma(a1.x, a1.x, fma(a1.y, a1.y,
+                           fma(a2.x, a2.x, a2.y * a2.y)))));
+      if (md < (unsigned)nz) e0 = fma(g.ccw[j], q, e0);   // mx = 0
+      else e1 = fma(g.ccw[j], q, e1);
     }
+    e = fma(2.0, e1, e0);
   }
   {
     const double* tr = g.DV + (size_t)b * N * nz * nx;
@@ -573,55 +574,62 @@ __global__ void __launch_bounds__(256) k_diag_part3(GroupDev g) {
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const double t = tr[i];
-      r.bad |= nonfinite3(t);
-      r.mn = fmin(r.mn, t);
-      r.mx = fmax(r.mx, t);
-      r.ma = fmax(r.ma, fabs(t));
+      bad |= nonfinite3(t);
+      keyext_add(ext, t);
     }
   }
   {
     const double* Xd = reinterpret_cast<const double*>(g.X + (size_t)b * 9 * NK);
     const long long tot = 18LL * NK, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
-    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) r.bad |= nonfinite3(Xd[i]);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) bad |= nonfinite3(Xd[i]);
   }
-  r = block_r5(r);
+  __shared__ double sh[32];
+  __shared__ long long shk[96];
+  e = block_sum(e, sh);
+  ext = block_keyext(ext, shk);
+  bad = (int)block_isum(bad, shk);
   if (threadIdx.x == 0) {
     double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
-    pp[P_E] = r.s;
-    pp[P_MIN] = r.mn;
-    pp[P_MAX] = r.mx;
-    pp[P_AMAX] = r.ma;
-    pp[P_BAD] = r.bad ? 1.0 : 0.0;
+    pp[P_E] = e;
+    islots3(pp)[P_MIN] = ext.mn;
+    islots3(pp)[P_MAX] = ext.mx;
+    islots3(pp)[P_AMAX] = ext.ma;
+    islots3(pp)[P_BAD] = bad ? 1 : 0;
   }
 }
 
-// Counts of Tr c < 3, < 0 and the tie bands over the volume, and over the
-// (x, z) mid-plane values MV[b][8][nz][nx] the same counts and the power
-// sums of the 8 mid-plane quantities; ntile blocks per member.
+// Counts of Tr c < 3, < 0 and the tie bands over the volume (every tile)
+// and, in the first mid_tiles tiles, over the (x, z) mid-plane values
+// MV[b][8][nz][nx] the same counts and the power sums of the 8 mid-plane
+// quantities (histograms too); ntile blocks per member.
 __global__ void __launch_bounds__(256) k_diag_count3(GroupDev g) {
   const int b = blockIdx.y, tile = blockIdx.x;
   if (g.status[b]) return;
-  const double tau = 1e-9 * block_tiles_max(g.part + (size_t)b * g.ntile * kPart, g.ntile, P_AMAX);
-  long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // volume c3 c0 b3 b0, mid-plane c3 c0 b3 b0
+  const TrBands B = tr_bands(1e-9 * block_tiles_amax(g.part + (size_t)b * g.ntile * kPart, g.ntile, P_AMAX));
+  TrCounts c{0, 0, 0, 0}, mc{0, 0, 0, 0};
   {
     const double* tr = g.DV + (size_t)b * g.N * g.nz * g.nx;
     const long long tot = (long long)g.N * g.nz * g.nx, per = (tot + g.ntile - 1) / g.ntile;
     const long long i0 = tile * per, i1 = min(tot, i0 + per);
-    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const double t = tr[i];
-      cnt[0] += (t < 3.0);
-      cnt[1] += (t < 0.0);
-      cnt[2] += (fabs(t - 3.0) <= tau);
-      cnt[3] += (fabs(t) <= tau);
-    }
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) tr_count(c, tr[i], B);
   }
-  double sums[8][4];
-  for (int q = 0; q < 8; ++q) for (int k = 0; k < 4; ++k) sums[q][k] = 0.0;
+  __shared__ long long shk[32];
+  const long long c3 = block_isum(c.c3, shk), c0 = block_isum(c.c0, shk);
+  const long long b3 = block_isum(c.b3, shk), b0 = block_isum(c.b0, shk);
+  double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
+  if (threadIdx.x == 0) {
+    islots3(pp)[P_C3] = c3; islots3(pp)[P_C0] = c0;
+    islots3(pp)[P_B3] = b3; islots3(pp)[P_B0] = b0;
+  }
+  const int npl = g.nz * g.nx;
+  if (tile >= mid_tiles(npl, g.ntile)) return;   // block-uniform
+  double sums[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) sums[k] = 0.0;
   {
-    const int npl = g.nz * g.nx;
     const double* MV = g.MV + (size_t)b * 8 * npl;
-    const int per = (npl + g.ntile - 1) / g.ntile;
+    const int per = mid_per(npl, g.ntile);
     const int i0 = tile * per, i1 = min(npl, i0 + per);
     const double* hr = g.hrange + (size_t)b * 16;
     unsigned long long* gh = g.hist + (size_t)b * 8 * (PTT_HIST_BINS + 2);
@@ -631,66 +639,66 @@ __global__ void __launch_bounds__(256) k_diag_count3(GroupDev g) {
         const int sl = hist_slot(MV[(size_t)q * npl + i], hr[2 * q], hr[2 * q + 1]);
         if (sl >= 0) atomicAdd(&gh[q * (PTT_HIST_BINS + 2) + sl], 1ULL);
       }
-      const double t = MV[i];
-      cnt[4] += (t < 3.0);
-      cnt[5] += (t < 0.0);
-      cnt[6] += (fabs(t - 3.0) <= tau);
-      cnt[7] += (fabs(t) <= tau);
+      tr_count(mc, MV[i], B);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const double a = MV[(size_t)q * npl + i], a2 = a * a;
-        sums[q][0] += a; sums[q][1] += a2; sums[q][2] += a2 * a; sums[q][3] += a2 * a2;
+        sums[4 * q] += a; sums[4 * q + 1] += a2; sums[4 * q + 2] += a2 * a; sums[4 * q + 3] += a2 * a2;
       }
     }
   }
-  double v[40];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = (double)cnt[k];
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[8 + 4 * q + k] = sums[q][k];
-  __shared__ double red[8 * 40];
-  block_sum_many<40>(v, red);
-  double* pp = g.part + ((size_t)b * g.ntile + tile) * kPart;
-  if (threadIdx.x < 40) {
-    const int k = threadIdx.x;
-    pp[k < 4 ? P_C3 + k : (k < 8 ? P_MC3 + (k - 4) : P_MS + (k - 8))] = red[k];
+  __shared__ double red[8 * 32];
+  block_sum_scatter(sums, red);
+  const long long m3 = block_isum(mc.c3, shk), m0 = block_isum(mc.c0, shk);
+  const long long mb3 = block_isum(mc.b3, shk), mb0 = block_isum(mc.b0, shk);
+  if (threadIdx.x < 32) pp[P_MS + threadIdx.x] = red[threadIdx.x];
+  if (threadIdx.x == 0) {
+    islots3(pp)[P_MC3] = m3; islots3(pp)[P_MC0] = m0;
+    islots3(pp)[P_MB3] = mb3; islots3(pp)[P_MB0] = mb0;
   }
 }
 
-// Mid-plane spectra at y = 0 per mode (one warp each): DM[b][q][mode] for
-// q = Tr c, u', w', du/dx, du/dz, dw/dx, dw/dz, v (u', w' without the mean).
+// Mid-plane spectra at y = 0 per mode (kMidLanes3 lanes each): DM[b][q][mode]
+// for q = Tr c, u', w', du/dx, du/dz, dw/dx, dw/dz, v (u', w' without the
+// mean).
+__device__ __forceinline__ double2 seg_sum2_3(double2 v) {
+#pragma unroll
+  for (int o = kMidLanes3 / 2; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o, kMidLanes3);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o, kMidLanes3);
+  }
+  return v;
+}
 __global__ void __launch_bounds__(256) k_diag_mid3(GroupDev g) {
   const int b = blockIdx.y;
   if (g.status[b]) return;
-  const int md = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+  const int sub = threadIdx.x & (kMidLanes3 - 1);
+  const int md = blockIdx.x * (blockDim.x / kMidLanes3) + (threadIdx.x / kMidLanes3);
   const int KZ = g.KZ, N = g.N, nz = g.nz;
-  if (md >= KZ) return;
+  const bool on = md < KZ;   // every lane takes part in the shuffles
   const size_t NK = (size_t)N * KZ;
-  const double2* X = g.X + (size_t)b * 9 * NK + (size_t)md * N;
+  const double2* X = g.X + (size_t)b * 9 * NK + (size_t)(on ? md : 0) * N;
   double2 tr = czero(), u = czero(), v = czero(), w = czero();
-  for (int n = lane; n < N; n += 32) {
-    const int r4 = n & 3;
-    if (r4 == 0 || r4 == 2) {
-      const double s = (r4 == 0) ? 1.0 : -1.0;
+  const int r4 = sub & 3;   // n = sub (mod kMidLanes3): one residue of n mod 4 per lane
+  if (on && (r4 == 0 || r4 == 2)) {
+    const double s = (r4 == 0) ? 1.0 : -1.0;
+    for (int n = sub; n < N; n += kMidLanes3) {
       tr = cfma(s, cadd(X[3 * NK + n], cadd(X[6 * NK + n], X[8 * NK + n])), tr);
       u = cfma(s, X[n], u);
       v = cfma(s, X[NK + n], v);
       w = cfma(s, X[2 * NK + n], w);
     }
   }
-  tr = warp_sum2(tr);
-  u = warp_sum2(u);
-  v = warp_sum2(v);
-  w = warp_sum2(w);
-  if (lane == 0) {
+  tr = seg_sum2_3(tr);
+  u = seg_sum2_3(u);
+  v = seg_sum2_3(v);
+  w = seg_sum2_3(w);
+  if (on && sub == 0) {
     const MemberPrm pr = g.prm[b];
     const int mx = md / nz, mzi = md - mx * nz, hz = nz / 2;
     const int sz = (mzi < hz) ? mzi : mzi - nz;
-    const double kx = 2.0 * 3.14159265358979323846 * mx / pr.lx;
-    const double kz = (mzi == hz) ? 0.0 : 2.0 * 3.14159265358979323846 * sz / pr.lz;
+    const double kx = pr.kx1 * mx;
+    const double kz = (mzi == hz) ? 0.0 : pr.kz1 * sz;
     double2 q[8] = {tr, u, w, cscl(mul_i(u), kx), cscl(mul_i(u), kz), cscl(mul_i(w), kx),
                     cscl(mul_i(w), kz), v};
     if (md == 0) { q[1] = czero(); q[2] = czero(); }
@@ -700,11 +708,13 @@ __global__ void __launch_bounds__(256) k_diag_mid3(GroupDev g) {
 }
 
 // Per member: reduce the tiles (each thread a fixed set of tiles, then
-// fixed-order trees: deterministic), <Tr c>, blow-up test, record.
+// fixed-order trees: deterministic; the energy and the mid-plane sums in
+// FP64, extrema and counts on integers), <Tr c>, blow-up test, record.
 __global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
   const int b = blockIdx.x;
   if (g.status[b]) return;
   __shared__ double sh[32];
+  __shared__ long long shk[96];
   const int KZ = g.KZ, N = g.N;
   const size_t NK = (size_t)N * KZ;
   const MemberPrm pr = g.prm[b];
@@ -715,32 +725,35 @@ __global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
     if ((n & 1) == 0)
       mt += (X[3 * NK + n].x + X[6 * NK + n].x + X[8 * NK + n].x) * (2.0 / (1.0 - (double)n * n));
   mt = block_sum(mt, sh);
-  double te = 0.0, tmn = 1e308, tmx = -1e308, tbad = 0.0;
+  double te = 0.0;
+  KeyExt ext = keyext_empty();
+  long long tbad = 0, cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int t = threadIdx.x; t < g.ntile; t += blockDim.x) {
     const double* q = pp + (size_t)t * kPart;
+    const long long* qi = islots3(q);
     te += q[P_E];
-    tmn = fmin(tmn, q[P_MIN]);
-    tmx = fmax(tmx, q[P_MAX]);
-    tbad = fmax(tbad, q[P_BAD]);
+    keyext_merge(ext, KeyExt{qi[P_MIN], qi[P_MAX], qi[P_AMAX]});
+    tbad |= qi[P_BAD];
+    for (int k = 0; k < 4; ++k) cnt[k] += qi[P_C3 + k];
   }
+  const int nmt = mid_tiles(g.nz * g.nx, g.ntile);
+  for (int t = threadIdx.x; t < nmt; t += blockDim.x)
+    for (int k = 0; k < 4; ++k) cnt[4 + k] += islots3(pp + (size_t)t * kPart)[P_MC3 + k];
   te = block_sum(te, sh);
-  tmn = -block_tiles_max_val(-tmn, sh);
-  tmx = block_tiles_max_val(tmx, sh);
-  tbad = block_tiles_max_val(tbad, sh);
-  // counts (volume, mid-plane) and mid-plane sums: tile slots 5-8, 9-12, 16-47
-  double v[40];
-#pragma unroll
-  for (int k = 0; k < 40; ++k) v[k] = 0.0;
-  for (int t = threadIdx.x; t < g.ntile; t += blockDim.x) {
-    const double* q = pp + (size_t)t * kPart;
-#pragma unroll
-    for (int k = 0; k < 40; ++k) v[k] += q[k < 4 ? P_C3 + k : (k < 8 ? P_MC3 + (k - 4) : P_MS + (k - 8))];
+  ext = block_keyext(ext, shk);
+  tbad = block_isum(tbad, shk);
+  for (int k = 0; k < 8; ++k) cnt[k] = block_isum(cnt[k], shk);
+  // mid-plane sums: thread k < 32 adds slot k over the mid tiles in order
+  __shared__ double ms[32];
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int t = 0; t < nmt; ++t) a += pp[(size_t)t * kPart + P_MS + threadIdx.x];
+    ms[threadIdx.x] = a;
   }
-  __shared__ double acc[8 * 40];
-  block_sum_many<40>(v, acc);
+  __syncthreads();
   if (threadIdx.x == 0) {
     const double e = 0.25 * te;
-    const bool bad = (tbad != 0.0);
+    const bool bad = (tbad != 0);
     const long long step = g.count[b];
     const double qnan = __longlong_as_double(0x7ff8000000000000LL);
     ptt_diag& r = g.ring[(size_t)b * kRing + (size_t)(step % kRing)];
@@ -748,14 +761,14 @@ __global__ void __launch_bounds__(256) k_diag_final3(GroupDev g) {
     r.t = step * pr.dt;
     r.energy = e;
     r.mean_trc = 0.5 * mt;
-    r.min_trc = bad ? qnan : tmn;
-    r.max_trc = bad ? qnan : tmx;
-    r.n_lt3 = (long long)acc[0]; r.n_lt0 = (long long)acc[1];
-    r.n_band3 = (long long)acc[2]; r.n_band0 = (long long)acc[3];
-    r.n_mid_lt3 = (long long)acc[4]; r.n_mid_lt0 = (long long)acc[5];
-    r.n_mid_band3 = (long long)acc[6]; r.n_mid_band0 = (long long)acc[7];
+    r.min_trc = bad ? qnan : dkey_val(ext.mn);
+    r.max_trc = bad ? qnan : dkey_val(ext.mx);
+    r.n_lt3 = cnt[0]; r.n_lt0 = cnt[1];
+    r.n_band3 = cnt[2]; r.n_band0 = cnt[3];
+    r.n_mid_lt3 = cnt[4]; r.n_mid_lt0 = cnt[5];
+    r.n_mid_band3 = cnt[6]; r.n_mid_band0 = cnt[7];
     for (int q = 0; q < 8; ++q)
-      for (int k = 0; k < 4; ++k) r.mid_sums[q][k] = acc[8 + 4 * q + k];
+      for (int k = 0; k < 4; ++k) r.mid_sums[q][k] = ms[4 * q + k];
     const bool blow = bad || !isfinite(e) || r.max_trc > pr.trc_max || sqrt(2.0 * e) > pr.u_max;
     r.status = blow ? PTT_BLOWUP : PTT_OK;
     r.reserved = 0;
@@ -796,6 +809,8 @@ ZJob zjob(const GroupDev& g, bool inverse, int Mz, int rows, const FftPlan& pl) 
   Z.K = g.K;
   Z.nz = g.nz;
   Z.Mz = Mz;
+  Z.inv = 1.0 / Mz;
+  Z.invf = (float)Z.inv;
   Z.inverse = inverse ? 1 : 0;
   Z.C = 8;
   Z.rows = rows;
@@ -998,7 +1013,7 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   if (e) return e;
   diag_energy_y3(g, d.s[1]);
   // mid-plane: per-mode sums, then z and x syntheses of the 8 quantities
-  k_diag_mid3<<<dim3(cdiv(KZ, 8), g.nb), 256, 0, d.s[2]>>>(g);
+  k_diag_mid3<<<dim3(cdiv(KZ, kMidModesPerBlock3), g.nb), 256, 0, d.s[2]>>>(g);
   ZJob Zm = zjob(g, true, g.nz, 1, g.plNz);
   Zm.src = g.DM; Zm.src_f32 = 0; Zm.dst = g.DMZ; Zm.dst_f32 = 0;
   Zm.src_mstride = 8LL * KZ; Zm.dst_mstride = 8LL * g.nz * K;
