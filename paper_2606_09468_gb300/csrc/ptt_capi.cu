@@ -573,6 +573,7 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       pls[i]->n = g.hp[i].n;
       pls[i]->nst = (int)g.hp[i].radix.size();
       for (int s = 0; s < pls[i]->nst; ++s) pls[i]->radix[s] = g.hp[i].radix[s];
+      plan_pass_consts(*pls[i]);
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
       pls[i]->twf = (d.f32 && (i < 2 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
       int nrec = 0, ndbl = 0;
@@ -695,6 +696,7 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
     pls[i]->n = hp.n;
     pls[i]->nst = (int)hp.radix.size();
     for (int k = 0; k < pls[i]->nst; ++k) pls[i]->radix[k] = hp.radix[k];
+    plan_pass_consts(*pls[i]);
     // tangent-form twiddle records of the FP64 passes (device pointers are
     // set by the caller once the tables have a home)
     int nrec = 0, ndbl = 0;
@@ -713,6 +715,21 @@ int shape_plan(const ptt_params& p, GroupDev& d, std::vector<double2>& twP,
   tw4.insert(tw4.end(), inv.begin(), inv.end());
   member_prm(p, prm);
   return PTT_OK;
+}
+
+void plan_pass_consts(FftPlan& pl) {
+  // the same multiply-high reciprocal as the device's fast_div
+  auto magic = [](unsigned d) { return d == 1u ? 0u : 0xFFFFFFFFu / d + 1u; };
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int R = pl.radix[s];
+    pl.pnb[s] = pl.n / R;
+    pl.pst[s] = pl.n / (Ns * R);
+    pl.pns[s] = Ns;
+    pl.pmb[s] = magic((unsigned)pl.pnb[s]);
+    pl.pms[s] = magic((unsigned)Ns);
+    Ns *= R;
+  }
 }
 
 void member_prm(const ptt_params& p, MemberPrm& q) {

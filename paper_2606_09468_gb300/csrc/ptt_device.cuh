@@ -234,15 +234,30 @@ __device__ __forceinline__ FastDiv fast_div(unsigned d) {
 }
 __device__ __forceinline__ unsigned fdiv(unsigned x, FastDiv f) { return f.one ? x : __umulhi(x, f.m); }
 
+// Constants of pass s of a plan, read from the plan (host-computed): the
+// passes divide nothing at run time.
+struct PassC {
+  int nb, st, Ns;
+  FastDiv dnb, dns;
+};
+__device__ __forceinline__ PassC pass_c(const FftPlan& pl, int s) {
+  PassC c;
+  c.nb = pl.pnb[s];
+  c.st = pl.pst[s];
+  c.Ns = pl.pns[s];
+  c.dnb = FastDiv{pl.pmb[s], pl.pmb[s] == 0u};
+  c.dns = FastDiv{pl.pms[s], pl.pms[s] == 0u};
+  return c;
+}
+
 // One Stockham pass of radix R over nl lines (line l at offset l*ls).
 template <int DIR, int R, typename C2>
 __device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restrict__ dst,
-                                         int nl, int ls, int n, int Ns,
+                                         int nl, int ls, const PassC& c,
                                          const C2* __restrict__ tw) {
-  const int nb = n / R;
-  const int st = n / (Ns * R);
+  const int nb = c.nb, st = c.st, Ns = c.Ns;
   const int total = nl * nb;
-  const FastDiv dnb = fast_div((unsigned)nb), dns = fast_div((unsigned)Ns);
+  const FastDiv dnb = c.dnb, dns = c.dns;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int l = (int)fdiv((unsigned)t, dnb);
     const int j = t - l * nb;
@@ -292,12 +307,12 @@ __device__ __forceinline__ double2 tan_rotate(double2 v, double t, int k) {
 
 template <int DIR, int R>
 __device__ __forceinline__ void fft_pass_tan(const double2* __restrict__ src, double2* __restrict__ dst,
-                                             int nl, int ls, int n, int Ns,
+                                             int nl, int ls, const PassC& c,
                                              const double* __restrict__ tt,
                                              const int* __restrict__ tk) {
-  const int nb = n / R;
+  const int nb = c.nb, Ns = c.Ns;
   const int total = nl * nb;
-  const FastDiv dnb = fast_div((unsigned)nb), dns = fast_div((unsigned)Ns);
+  const FastDiv dnb = c.dnb, dns = c.dns;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int l = (int)fdiv((unsigned)t, dnb);
     const int j = t - l * nb;
@@ -380,11 +395,11 @@ __device__ __forceinline__ void fft_pass_tan(const double2* __restrict__ src, do
 // y0 = v0 + v2, y1,2 = v0 - v2/2 -+ DIR sin(2 pi/3) i v2 (8 operations).
 template <int DIR, typename C2>
 __device__ __forceinline__ void fft_pass_r3_zmid(const C2* __restrict__ src, C2* __restrict__ dst,
-                                                 int nl, int ls, int n) {
+                                                 int nl, int ls, const PassC& c) {
   using T = typename RealOf<C2>::T;
-  const int nb = n / 3;
+  const int nb = c.nb;
   const int total = nl * nb;
-  const FastDiv dnb = fast_div((unsigned)nb);
+  const FastDiv dnb = c.dnb;
   const T sn = (T)(DIR * 0.86602540378443864676);  // sin(2 pi / 3), signed
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int l = (int)fdiv((unsigned)t, dnb);
@@ -421,13 +436,12 @@ __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl, bool z
   C2* src = a;
   C2* dst = b;
   const C2* tw = plan_tw<C2>(pl);
-  int Ns = 1;
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.radix[s];
+    const PassC c = pass_c(pl, s);
     if (s == 0 && zero_mid && R == 3) {
-      fft_pass_r3_zmid<DIR>(src, dst, nl, ls, pl.n);
+      fft_pass_r3_zmid<DIR>(src, dst, nl, ls, c);
       __syncthreads();
-      Ns = 3;
       C2* t = src; src = dst; dst = t;
       continue;
     }
@@ -435,31 +449,29 @@ __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl, bool z
       if (pl.tt && s > 0 && R <= 5) {
         const double* tt = pl.tt + pl.tto[s];
         const int* tk = pl.tk + pl.toff[s];
-        if (R == 5) fft_pass_tan<DIR, 5>(src, dst, nl, ls, pl.n, Ns, tt, tk);
-        else if (R == 4) fft_pass_tan<DIR, 4>(src, dst, nl, ls, pl.n, Ns, tt, tk);
-        else if (R == 3) fft_pass_tan<DIR, 3>(src, dst, nl, ls, pl.n, Ns, tt, tk);
-        else fft_pass_tan<DIR, 2>(src, dst, nl, ls, pl.n, Ns, tt, tk);
+        if (R == 5) fft_pass_tan<DIR, 5>(src, dst, nl, ls, c, tt, tk);
+        else if (R == 4) fft_pass_tan<DIR, 4>(src, dst, nl, ls, c, tt, tk);
+        else if (R == 3) fft_pass_tan<DIR, 3>(src, dst, nl, ls, c, tt, tk);
+        else fft_pass_tan<DIR, 2>(src, dst, nl, ls, c, tt, tk);
         __syncthreads();
-        Ns *= R;
         C2* t = src; src = dst; dst = t;
         continue;
       }
     }
     switch (R) {
-      case 2: fft_pass<DIR, 2>(src, dst, nl, ls, pl.n, Ns, tw); break;
-      case 3: fft_pass<DIR, 3>(src, dst, nl, ls, pl.n, Ns, tw); break;
-      case 4: fft_pass<DIR, 4>(src, dst, nl, ls, pl.n, Ns, tw); break;
-      case 5: fft_pass<DIR, 5>(src, dst, nl, ls, pl.n, Ns, tw); break;
+      case 2: fft_pass<DIR, 2>(src, dst, nl, ls, c, tw); break;
+      case 3: fft_pass<DIR, 3>(src, dst, nl, ls, c, tw); break;
+      case 4: fft_pass<DIR, 4>(src, dst, nl, ls, c, tw); break;
+      case 5: fft_pass<DIR, 5>(src, dst, nl, ls, c, tw); break;
       default:
         if constexpr (BIG) {
-          if (R == 7) fft_pass<DIR, 7>(src, dst, nl, ls, pl.n, Ns, tw);
-          else if (R == 11) fft_pass<DIR, 11>(src, dst, nl, ls, pl.n, Ns, tw);
-          else if (R == 13) fft_pass<DIR, 13>(src, dst, nl, ls, pl.n, Ns, tw);
+          if (R == 7) fft_pass<DIR, 7>(src, dst, nl, ls, c, tw);
+          else if (R == 11) fft_pass<DIR, 11>(src, dst, nl, ls, c, tw);
+          else if (R == 13) fft_pass<DIR, 13>(src, dst, nl, ls, c, tw);
         }
         break;
     }
     __syncthreads();
-    Ns *= R;
     C2* t = src; src = dst; dst = t;
   }
   return src;
@@ -478,13 +490,12 @@ __host__ __device__ constexpr int ip_maxb(int R) {
 }
 
 template <int DIR, int R, typename C2>
-__device__ __forceinline__ void fft_pass_ip(C2* a, int nl, int ls, int n, int Ns,
+__device__ __forceinline__ void fft_pass_ip(C2* a, int nl, int ls, const PassC& c,
                                             const C2* __restrict__ tw, bool zmid) {
   constexpr int MB = ip_maxb(R);
-  const int nb = n / R;
-  const int st = n / (Ns * R);
+  const int nb = c.nb, st = c.st, Ns = c.Ns;
   const int total = nl * nb;
-  const FastDiv dnb = fast_div((unsigned)nb), dns = fast_div((unsigned)Ns);
+  const FastDiv dnb = c.dnb, dns = c.dns;
   const int tid = threadIdx.x, nt = blockDim.x;
   C2 v[MB][R];
 #pragma unroll
@@ -531,17 +542,16 @@ __device__ void fft_lines_inplace(C2* a, int nl, int ls, const FftPlan& pl, bool
   for (int l0 = 0; l0 < nl; l0 += kIpLines) {
     const int g = min(kIpLines, nl - l0);
     C2* base = a + (size_t)l0 * ls;
-    int Ns = 1;
     for (int s = 0; s < pl.nst; ++s) {
       const int R = pl.radix[s];
+      const PassC c = pass_c(pl, s);
       const bool zm = (s == 0 && zero_mid && R == 3);
       switch (R) {
-        case 2: fft_pass_ip<DIR, 2>(base, g, ls, pl.n, Ns, tw, false); break;
-        case 3: fft_pass_ip<DIR, 3>(base, g, ls, pl.n, Ns, tw, zm); break;
-        case 4: fft_pass_ip<DIR, 4>(base, g, ls, pl.n, Ns, tw, false); break;
-        default: fft_pass_ip<DIR, 5>(base, g, ls, pl.n, Ns, tw, false); break;
+        case 2: fft_pass_ip<DIR, 2>(base, g, ls, c, tw, false); break;
+        case 3: fft_pass_ip<DIR, 3>(base, g, ls, c, tw, zm); break;
+        case 4: fft_pass_ip<DIR, 4>(base, g, ls, c, tw, false); break;
+        default: fft_pass_ip<DIR, 5>(base, g, ls, c, tw, false); break;
       }
-      Ns *= R;
     }
   }
 }

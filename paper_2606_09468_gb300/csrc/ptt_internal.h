@@ -35,7 +35,14 @@ struct FftPlan {
   const int* tk;
   int toff[kMaxStages];
   int tto[kMaxStages];
+  // Per-pass constants (plan_pass_consts): butterflies per line n/R, twiddle
+  // stride n/(Ns R), span Ns before the pass, and the multiply-high
+  // reciprocals of n/R and Ns (0 for 1), so that a pass divides nothing.
+  int pnb[kMaxStages], pst[kMaxStages], pns[kMaxStages];
+  unsigned pmb[kMaxStages], pms[kMaxStages];
 };
+// Fills the per-pass constants of pl from pl.n, pl.nst and pl.radix.
+void plan_pass_consts(FftPlan& pl);
 
 // Per-member physics, resident on the device.
 struct MemberPrm {
