@@ -575,7 +575,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       for (int s = 0; s < pls[i]->nst; ++s) pls[i]->radix[s] = g.hp[i].radix[s];
       plan_pass_consts(*pls[i]);
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
-      pls[i]->twf = (d.f32 && (i < 2 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
+      // single-precision tables: the step's padded lengths and the energy grid
+      pls[i]->twf = (d.f32 && (i < 2 || i == 4 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
       int nrec = 0, ndbl = 0;
       tangent_offsets(g.hp[i], pls[i]->toff, pls[i]->tto, &nrec, &ndbl);
       pls[i]->tt = cv.take<double>((size_t)ndbl);
@@ -586,6 +587,7 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.tw4Pi = cv.take<double2>((size_t)d.M);
     d.tw4Pif = d.f32 ? cv.take<float2>((size_t)d.M) : nullptr;
     d.tw4E = cv.take<double2>((size_t)d.Me);
+    d.tw4Ef = d.f32 ? cv.take<float2>((size_t)d.Me) : nullptr;
   }
 }
 
@@ -1015,7 +1017,7 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
       quarter_tables(d.Me, fwdE, invE);
       const std::vector<double2>* src[3] = {&fwd, &inv, &invE};
       const double2* dst[3] = {d.tw4P, d.tw4Pi, d.tw4E};
-      const float2* dstf[3] = {d.tw4Pf, d.tw4Pif, nullptr};
+      const float2* dstf[3] = {d.tw4Pf, d.tw4Pif, d.tw4Ef};
       std::vector<float2> twf[3];
       for (int t = 0; t < 3; ++t) {
         const std::vector<double2>& tw = *src[t];

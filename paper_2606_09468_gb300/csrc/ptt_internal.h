@@ -131,6 +131,7 @@ struct GroupDev {
   const double2* tw4Pi;  // [M]  inverse: (1/2) exp(+i pi k/(2M))
   const float2* tw4Pif;  // the same in single precision (mixed groups)
   const double2* tw4E;   // [Me] inverse on the diagnostic Gauss grid: (1/2) exp(+i pi k/(2Me))
+  const float2* tw4Ef;   // the same in single precision (mixed groups: FP32 energy transform)
   FftPlan plP, plMx, plNx, plPu, plPe;   // lengths M, Mx, nx, 2(N-1), Me
   FftPlan plMz, plNz;                    // 3D: lengths Mz, nz
 };

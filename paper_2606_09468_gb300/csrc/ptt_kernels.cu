@@ -925,6 +925,7 @@ static YJob yjob_forward(const GroupDev& g) {   // the 5 explicit fields to coef
 static YJob yjob_energy(const GroupDev& g) {    // u, v on the Me Gauss points
   const size_t NK = (size_t)g.N * g.K;
   YJob J = make_yjob(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
+  J.tw4f = g.tw4Ef;   // mixed groups transform in FP32 (the sums stay FP64)
   J.src = g.X; J.dst = g.DY;
   J.src_mstride = 5 * NK; J.dst_mstride = 2LL * g.Me * g.K;
   J.src_fstride = NK; J.dst_fstride = (long long)g.Me * g.K;
@@ -1027,8 +1028,12 @@ static cudaError_t diag_join(const DiagStreams& d) {
 // Gauss points of the energy quadrature; c_xx + c_yy on the unpadded
 // Gauss-Lobatto rows (DCT-I).
 static void diag_energy_y(const GroupDev& g, cudaStream_t st) {
-  k_ycols<double2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(
-      yjob_energy(g));
+  if (g.f32)
+    k_ycols<float2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 1), st>>>(
+        yjob_energy(g));
+  else
+    k_ycols<double2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(
+        yjob_energy(g));
 }
 static void diag_trc_y(const GroupDev& g, cudaStream_t st) {
   k_ycols<double2, true><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(
@@ -1131,7 +1136,7 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
     p->sm_fwd = p->sm_inv;
     p->sm_xf = std::max(p->sm_xf, smem_xfused(g.Mx, g.f32));
     p->sm_spec[cls] = std::max(p->sm_spec[cls], smem_spec(g.N));
-    p->sm_ye = std::max(p->sm_ye, smem_ycols(g.CcolE, g.Me, 0));
+    p->sm_ye = std::max(p->sm_ye, smem_ycols(g.CcolE, g.Me, g.f32));
     p->sm_yt = std::max(p->sm_yt, smem_ycols(g.CcolU, g.Pu, 0));
     p->sm_xr = std::max(p->sm_xr, smem_xrows(1, g.nx));
     p->sm_fin = std::max(p->sm_fin, smem_xrows(3, g.nx));
@@ -1214,7 +1219,8 @@ cudaError_t launch_diag_multi(const Multi2DPlan* p, const DiagStreams& d, int* n
   const int ng = p->ng;
   cudaError_t e = diag_fork(d);
   if (e) return e;
-  k_ycols_multi<double2><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
+  if (p->f32) k_ycols_multi<float2><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
+  else k_ycols_multi<double2><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
   k_diag_mid_multi<<<mm_blocks(p->mid), 256, 0, d.s[2]>>>(p->dg, p->mid);
   k_ycols_multi<double2, true><<<mm_blocks(p->yt), 256, p->sm_yt, d.s[0]>>>(p->dyj + 3 * ng, p->yt);
   k_xrows_multi<<<mm_blocks(p->xr), 256, p->sm_xr, d.s[0]>>>(p->dxj, p->xr);

@@ -983,11 +983,13 @@ static void diag_energy_y3(const GroupDev& g, cudaStream_t st) {
   const int KZ = g.KZ;
   const size_t NK = (size_t)g.N * KZ;
   YJob J = yjob3(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
+  J.tw4f = g.tw4Ef;   // mixed groups transform in FP32 (the sums stay FP64)
   J.src = g.X; J.dst = g.DY;
   J.src_mstride = 9 * NK; J.dst_mstride = 3LL * g.Me * KZ;
   J.src_fstride = NK; J.dst_fstride = (long long)g.Me * KZ;
   for (int i = 0; i < 3; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
-  k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
+  if (g.f32) k_ycols<float2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 1), st>>>(J);
+  else k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
 }
 static void diag_trc_y3(const GroupDev& g, cudaStream_t st) {
   const int KZ = g.KZ;

@@ -1,5 +1,6 @@
 """Mixed precision (PTT_MIXED): FP32 transforms and products, FP64 state,
-SBDF sums, tau solves and diagnostics, against the FP64 oracle.
+SBDF sums and tau solves, against the FP64 oracle.  Diagnostics: Tr c in
+FP64 throughout; the energy's y transform in FP32, its sums in FP64.
 
 Stated errors (per field, max|f - f_oracle| / max|f_oracle| on the unpadded
 grid; the paper's fluid, laminar state + perturbation 1e-3, dt = 1e-3):
@@ -77,3 +78,23 @@ def test_mixed_and_fp64_runs_coexist_in_one_context():
     a, b = ctx.get_state(0), ctx.get_state(1)
     e = _errs(I.abi_to_phys(b), I.abi_to_phys(a))
     assert np.all(e <= np.array([1e-8, 1e-5, 1e-8, 1e-8, 1e-8])) and np.any(e > 0), e
+
+
+def test_mixed_diagnostics_against_oracle():
+    """One mixed step of 128 x 97: energy (FP32 transform, FP64 sums) to
+    1e-6 of the oracle's, <Tr c> and the Tr c extrema (FP64 from a state
+    within 1e-8 of the oracle's) to 1e-7."""
+    import paper_2606_09468_gb300 as P
+    nx, ny = 128, 97
+    ctx = _ctx(nx, ny, P.PTT_MIXED)
+    ctx.init_state(0, 3, I.AMPLITUDE)
+    ora = Channel2D(Params(nx=nx, ny=ny, dt=I.DT, **I.PAPER))
+    ora.init_state(3, I.AMPLITUDE)
+    ctx.step(1)
+    ora.step()
+    assert ctx.synchronize() == P.PTT_OK
+    d, o = ctx.diagnostics(0)[-1], ora.diagnostics()
+    print("mixed diagnostics", {k: (d[k], o[k]) for k in ("energy", "mean_trc", "min_trc", "max_trc")})
+    assert abs(d["energy"] - o["energy"]) <= 1e-6 * o["energy"]
+    for k in ("mean_trc", "min_trc", "max_trc"):
+        assert abs(d[k] - o[k]) <= 1e-7 * abs(o[k]), k
