@@ -12,8 +12,9 @@ side, tau solves, diagnostics).  Synthetic seeded data.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 The JSON line also carries, under "workloads", the 3D channel (128x97x64 and
-256x129x128, Lz = 5, FP64 and mixed precision) and the ragged 64-run 2D
-ensemble (uneven Nx, Ny, Wi; mixed precision and FP64), each timed the same
+256x129x128, Lz = 5, FP64 and mixed precision), the ragged 64-run 2D
+ensemble (uneven Nx, Ny, Wi; mixed precision and FP64; both launch modes)
+and the paper's A1-A6 shapes (Table 1; mixed and FP64), each timed the same
 way on rank 0.  --only NAME runs one of them alone (for profiling).
 
 --impl reference times the FP64 CPU oracle on this machine's host cores (each
@@ -64,8 +65,10 @@ def parse():
     ap.add_argument("--workload-steps", type=int, default=40)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the default launch shapes instead of the autotuned ones")
-    ap.add_argument("--paper-shapes", action="store_true",
-                    help="also time the paper's A1-A6 shapes (3D, mixed and FP64)")
+    ap.add_argument("--paper-shapes", dest="paper_shapes", action="store_true", default=True,
+                    help="time the paper's A1-A6 shapes (3D, mixed and FP64; the default)")
+    ap.add_argument("--no-paper-shapes", dest="paper_shapes", action="store_false",
+                    help="skip the A1-A6 timings")
     ap.add_argument("--stats-amplitude", type=float, default=I.AMPLITUDE,
                     help="perturbation amplitude of the midplane_stats runs")
     ap.add_argument("--stats-wi", type=float, default=I.PAPER["wi"],
@@ -262,12 +265,12 @@ def run_reference(args):
 AUTOTUNE = True
 
 
-def _timed(ctx, steps, warmup):
+def _timed(ctx, steps, warmup, tune=True):
     """Device milliseconds per step of `steps` graph-launched steps (CUDA
     events on the context stream) after `warmup` untimed steps; the context's
-    launch shapes are autotuned first unless --no-autotune."""
+    launch shapes are autotuned first unless --no-autotune (or tune=False)."""
     import torch
-    if AUTOTUNE:
+    if AUTOTUNE and tune:
         ctx.autotune()
     ctx.step(warmup)
     ctx.synchronize()
@@ -528,27 +531,39 @@ def other_workloads(args):
     members = I.ensemble_members()
     fluid = {k: v for k, v in I.PAPER.items() if k != "wi"}
     pts = sum(nx * ny for nx, ny, _, _ in members)
+    # each precision in both launch modes: 0, every shape group its own graph
+    # branch; 1, one launch per kernel and stage over all groups (work list)
     res = {}
     for prec in (P.PTT_MIXED, P.PTT_FP64):
         ctx = P.Context([P.make_params(nx=nx, ny=ny, wi=wi, dt=I.DT, precision=prec, **fluid)
                          for nx, ny, wi, _ in members])
         for i, m in enumerate(members):
             ctx.init_state(i, m[3], I.AMPLITUDE)
-        ms = _timed(ctx, steps, warm)
-        res[prec] = (ms, P.ptt_status_string(ctx.synchronize()), ctx.launches_per_step())
+        for mode in (0, 1):
+            ctx.set_launch_mode(mode)
+            ms = _timed(ctx, steps, warm, tune=(mode == 0))
+            res[prec, mode] = (ms, P.ptt_status_string(ctx.synchronize()), ctx.launches_per_step())
         ctx.close()
+    best = {prec: min((0, 1), key=lambda m: res[prec, m][0]) for prec in (P.PTT_MIXED, P.PTT_FP64)}
+    bm, bf = res[P.PTT_MIXED, best[P.PTT_MIXED]], res[P.PTT_FP64, best[P.PTT_FP64]]
     out["ensemble64_mixed"] = {
-        "value": pts * 1e3 / res[P.PTT_MIXED][0], "unit": METRIC, "ms_per_step": res[P.PTT_MIXED][0],
+        "value": pts * 1e3 / bm[0], "unit": METRIC, "ms_per_step": bm[0],
         "steps": steps, "grid_points": pts, "runs": len(members),
         "shape_groups": len({(a, b) for a, b, _, _ in members}),
-        "launches_per_step": res[P.PTT_MIXED][2], "status": res[P.PTT_MIXED][1],
+        "launch_mode": best[P.PTT_MIXED], "launches_per_step": bm[2], "status": bm[1],
+        "modes": {str(m): {"value": pts * 1e3 / res[P.PTT_MIXED, m][0], "ms_per_step": res[P.PTT_MIXED, m][0],
+                           "launches_per_step": res[P.PTT_MIXED, m][2]} for m in (0, 1)},
         "dtype": "f32 transforms+products / f64 state+solves",
-        "fp64_value": pts * 1e3 / res[P.PTT_FP64][0], "fp64_ms_per_step": res[P.PTT_FP64][0],
-        "speedup_vs_fp64": res[P.PTT_FP64][0] / res[P.PTT_MIXED][0],
+        "fp64_value": pts * 1e3 / bf[0], "fp64_ms_per_step": bf[0], "fp64_launch_mode": best[P.PTT_FP64],
+        "fp64_modes": {str(m): {"value": pts * 1e3 / res[P.PTT_FP64, m][0], "ms_per_step": res[P.PTT_FP64, m][0],
+                                "launches_per_step": res[P.PTT_FP64, m][2]} for m in (0, 1)},
+        "speedup_vs_fp64": bf[0] / bm[0],
         "stated_error_vs_fp64": "tests/test_gpu_ensemble.py: every member, every field, 1 step <= 1e-8",
-        "workload": "64 independent 2D runs, seeds 0-63, Nx in the 5-smooth multiples of 32 in "
-                    "[64, 512], Ny in {65,97,129,161,193,257}, Wi uniform in [50, 200] (splitmix64 "
-                    "draws of the run index), one context, one CUDA-graph launch per step"}
+        "workload": "64 independent 2D runs, seeds 0-63, Nx every multiple of 32 in [64, 512], "
+                    "Ny in {65,97,129,161,193,225,257}, Wi uniform in [50, 200] (splitmix64 "
+                    "draws of the run index), one context, one CUDA-graph launch per step; "
+                    "launch mode 0 (a graph branch per shape group) and 1 (one launch per "
+                    "kernel and stage over all groups), the faster one as value"}
     return out
 
 
@@ -746,7 +761,7 @@ def run_ours(args):
     if rank != 0:
         return
     workloads = other_workloads(args) if args.workloads else None
-    if args.paper_shapes:
+    if args.paper_shapes and args.workloads:
         workloads = dict(workloads or {})
         workloads["paper_shapes"] = paper_shapes(args)
     ws = ctx.nbytes
