@@ -84,7 +84,8 @@ def parse():
                     help="run one workload alone (3d_fp64, 3d_mixed, 3d_fp64_large, "
                          "3d_mixed_large, ensemble_mixed, ensemble_fp64, 2d_NXxNY[_mixed]: one "
                          "shape of the 2D sweep, three seeds; 'mixedtc' in place of 'mixed' "
-                         "selects the tensor-core Chebyshev passes instead of the FP32 FFTs; "
+                         "selects the tensor-core Chebyshev passes instead of the FP32 FFTs, a "
+                         "'_ds' suffix the double-single form (PTT_FP64_DS); "
                          "3d_NXxNYxNZ[_mixed]: one 3D shape; paper_shapes: the A1-A6 timings) "
                          "and print its line, for profiling; or midplane_stats: mixed vs FP64 "
                          "mid-plane statistics of the 3D workload over --steps steps; or "
@@ -441,7 +442,8 @@ def only_workload(args):
     if name == "paper_shapes":
         print(json.dumps({"workload": name, "shapes": paper_shapes(args)}))
         return
-    prec = (P.PTT_MIXED_TC if "mixedtc" in name else P.PTT_MIXED if "mixed" in name else P.PTT_FP64)
+    prec = (P.PTT_MIXED_TC if "mixedtc" in name else P.PTT_MIXED if "mixed" in name
+            else P.PTT_FP64_DS if name.endswith("_ds") else P.PTT_FP64)
     if name.startswith("3d"):
         nx, ny, nz = I.CHANNEL3D_LARGE if name.endswith("large") else I.CHANNEL3D
         dims = name.split("_")[1]
@@ -493,9 +495,9 @@ def other_workloads(args):
         ms = _timed(ctx, nsteps, warm)
         return ctx, ms
 
-    tags = {P.PTT_FP64: "fp64", P.PTT_MIXED: "mixed", P.PTT_MIXED_TC: "mixedtc"}
-    for shape, precs in ((I.CHANNEL3D, (P.PTT_FP64, P.PTT_MIXED, P.PTT_MIXED_TC)),
-                         (I.CHANNEL3D_LARGE, (P.PTT_FP64, P.PTT_MIXED, P.PTT_MIXED_TC))):
+    tags = {P.PTT_FP64: "fp64", P.PTT_MIXED: "mixed", P.PTT_MIXED_TC: "mixedtc", P.PTT_FP64_DS: "fp64ds"}
+    allp = (P.PTT_FP64, P.PTT_MIXED, P.PTT_MIXED_TC, P.PTT_FP64_DS)
+    for shape, precs in ((I.CHANNEL3D, allp), (I.CHANNEL3D_LARGE, allp)):
         pts = shape[0] * shape[1] * shape[2]
         ms_of, states = {}, {}
         for prec in precs:
@@ -518,10 +520,12 @@ def other_workloads(args):
                          "dtype": {P.PTT_FP64: "f64",
                                    P.PTT_MIXED: "f32 transforms+products / f64 state+solves",
                                    P.PTT_MIXED_TC: "f32 x/z transforms+products, tensor-core "
-                                                   "Chebyshev contractions / f64 state+solves"}[prec],
+                                                   "Chebyshev contractions / f64 state+solves",
+                                   P.PTT_FP64_DS: "double-single transforms+products / f64 "
+                                                  "state+solves"}[prec],
                          "workload": "3D sPTT channel %dx%dx%d (x, y, z), Lx=10, Lz=5, paper fluid, "
                                      "dt=1e-3, laminar + seeded perturbation 1e-3" % shape}
-        for prec in (P.PTT_MIXED, P.PTT_MIXED_TC):
+        for prec in (P.PTT_MIXED, P.PTT_MIXED_TC, P.PTT_FP64_DS):
             name = "3d_%s_%dx%dx%d" % (tags[prec], *shape)
             out[name]["speedup_vs_fp64"] = ms_of[P.PTT_FP64][0] / ms_of[prec][0]
             out[name]["max_rel_field_dev_vs_fp64_gpu"] = dict(zip(f3, _dev(states[prec], states[P.PTT_FP64])))
@@ -746,7 +750,7 @@ def run_ours(args):
         mctx.close()
         return res
 
-    mixed = mixed_tc = None
+    mixed = mixed_tc = fp64_ds = None
     if args.mixed:
         mixed = mixed_form(P.PTT_MIXED)
         mixed.update({"dtype": "f32 transforms (Chebyshev as FFTs) / f64 state+solves",
@@ -757,6 +761,11 @@ def run_ours(args):
                                   "with f32 accumulation / f64 state+solves",
                          "stated_error_vs_oracle": "tests/test_gpu_mma.py: explicit rhs <= 1e-6 "
                                                    "(measured 0.9-1.6e-7 in 2D, as the FFT form)"})
+        fp64_ds = mixed_form(P.PTT_FP64_DS)
+        fp64_ds.update({"dtype": "double-single (pairs of f32, 48 bits) transforms+products / "
+                                 "f64 state+solves+diagnostics",
+                        "stated_error_vs_oracle": "tests/test_gpu_ds.py: the FP64 bars, 1 step <= 1e-11, "
+                                                  "100 steps <= 1e-9"})
 
     if rank != 0:
         return
@@ -780,6 +789,7 @@ def run_ours(args):
     if mixed is not None:
         out["mixed"] = mixed
         out["mixed_tc"] = mixed_tc
+        out["fp64_ds"] = fp64_ds
     if workloads is not None:
         out["workloads"] = workloads
     if not args.no_cpu_baseline and world == 1:

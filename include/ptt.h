@@ -76,6 +76,15 @@ extern "C" {
                               the shapes that contraction does not cover,
                               ny > 321); same accuracy as PTT_MIXED, slower on
                               this part at the shapes measured               */
+#define PTT_FP64_DS 3      /* FP64-accurate: the Fourier and Chebyshev transforms
+                              and the products in double-single arithmetic
+                              (each value the unevaluated sum of two FP32
+                              numbers, 48 significant bits) on the FP32 pipe;
+                              FP64 state, SBDF sums, tau solves and
+                              diagnostics.  Holds the FP64 path's bars against
+                              the FP64 solution (1e-11 after one step, 1e-9
+                              after 100); GB300's FP64 pipe is 1/64 of its
+                              FP32 pipe per instruction                      */
 
 /* Physical and numerical parameters of one member.  Defaults (the paper's
  * single fluid, Sec. 2): lx = lz = 10, re = 1e-2, wi = 150, beta = 0.9,
@@ -83,7 +92,7 @@ extern "C" {
 typedef struct {
   int32_t nx, ny, nz;        /* Fourier modes in x, Chebyshev modes in y, Fourier
                                 modes in z (nz = 1: the 2D problem)             */
-  int32_t precision;         /* PTT_FP64, PTT_MIXED or PTT_MIXED_TC               */
+  int32_t precision;         /* PTT_FP64, PTT_MIXED, PTT_MIXED_TC or PTT_FP64_DS  */
   double lx, lz;             /* periodic lengths (walls at y = +-1)               */
   double re, wi, beta, eps, kappa;
   double dt;                 /* fixed time step                                   */

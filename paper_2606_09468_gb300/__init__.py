@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libptt.so")
 
 PTT_OK, PTT_BLOWUP = 0, 1
 PTT_EINVAL, PTT_ENOMEM, PTT_ECUDA, PTT_TIMEOUT, PTT_ENOTSUP = -1, -2, -3, -4, -5
-PTT_FP64, PTT_MIXED, PTT_MIXED_TC = 0, 1, 2
+PTT_FP64, PTT_MIXED, PTT_MIXED_TC, PTT_FP64_DS = 0, 1, 2, 3
 PTT_HIST_BINS = 256
 
 

@@ -321,6 +321,13 @@ void initial_fields3(const ptt_params& p, uint64_t seed, double amp, std::vector
 // points with each direction's constants folded in: fwd[k] = (s_k/2)
 // exp(-i pi k/(2M)) with s_0 = 1/M, s_k = 2/M (the DCT-II normalisation of
 // the coefficients), inv[k] = (1/2) exp(+i pi k/(2M)).
+// A complex double as double-single parts (re.h, re.l, im.h, im.l): h the FP32
+// rounding, l the FP32 rounding of the remainder (48 significant bits).
+float4 ds_split(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
 void quarter_tables(int M, std::vector<double2>& fwd, std::vector<double2>& inv) {
   fwd.resize(M);
   inv.resize(M);
@@ -432,7 +439,8 @@ struct Group {
 int check_params(const ptt_params& p) {
   if (p.nz != 1 && (p.nz < 4 || p.nz > 512 || (p.nz & 1) || !smooth13(p.nz))) return PTT_EINVAL;
   if (p.nz > 1 && !(p.lz > 0)) return PTT_EINVAL;
-  if (p.precision != PTT_FP64 && p.precision != PTT_MIXED && p.precision != PTT_MIXED_TC)
+  if (p.precision != PTT_FP64 && p.precision != PTT_MIXED && p.precision != PTT_MIXED_TC &&
+      p.precision != PTT_FP64_DS)
     return PTT_ENOTSUP;
   if (p.nx < 8 || p.nx > 512 || (p.nx & 1) || !smooth13(p.nx)) return PTT_EINVAL;
   if (p.ny < 9 || p.ny > 513 || !smooth13(p.ny - 1)) return PTT_EINVAL;
@@ -577,6 +585,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
       // single-precision tables: the step's padded lengths and the energy grid
       pls[i]->twf = (d.f32 && (i < 2 || i == 4 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
+      // double-single tables: the step's padded lengths
+      pls[i]->twd = (d.ds && (i < 2 || i == 5)) ? cv.take<float4>((size_t)g.hp[i].n) : nullptr;
       int nrec = 0, ndbl = 0;
       tangent_offsets(g.hp[i], pls[i]->toff, pls[i]->tto, &nrec, &ndbl);
       pls[i]->tt = cv.take<double>((size_t)ndbl);
@@ -588,6 +598,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.tw4Pif = d.f32 ? cv.take<float2>((size_t)d.M) : nullptr;
     d.tw4E = cv.take<double2>((size_t)d.Me);
     d.tw4Ef = d.f32 ? cv.take<float2>((size_t)d.Me) : nullptr;
+    d.tw4Pd = d.ds ? cv.take<float4>((size_t)d.M) : nullptr;
+    d.tw4Pid = d.ds ? cv.take<float4>((size_t)d.M) : nullptr;
   }
 }
 
@@ -604,7 +616,8 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
       g.ny = pm[i].ny;
       g.nz = pm[i].nz;
       group_sizes(g.nx, g.ny, g.nz, g);
-      g.d.f32 = (pm[i].precision != PTT_FP64) ? 1 : 0;
+      g.d.f32 = (pm[i].precision == PTT_MIXED || pm[i].precision == PTT_MIXED_TC) ? 1 : 0;
+      g.d.ds = (pm[i].precision == PTT_FP64_DS) ? 1 : 0;
       g.d.ymma = (pm[i].precision == PTT_MIXED_TC) ? 1 : 0;   // requested; carve() checks the shape
       groups.push_back(std::move(g));
       it = idx.find(key);
@@ -620,7 +633,7 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
 bool multi_eligible(const std::vector<Group>& groups) {
   if (groups.size() < 2 || (int)groups.size() > multi2d_max_groups()) return false;
   for (const Group& g : groups)
-    if (g.d.nz != 1 || g.d.ymma || g.d.f32 != groups[0].d.f32) return false;
+    if (g.d.nz != 1 || g.d.ymma || g.d.ds || g.d.f32 != groups[0].d.f32) return false;
   return true;
 }
 
@@ -1018,7 +1031,9 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
       const std::vector<double2>* src[3] = {&fwd, &inv, &invE};
       const double2* dst[3] = {d.tw4P, d.tw4Pi, d.tw4E};
       const float2* dstf[3] = {d.tw4Pf, d.tw4Pif, d.tw4Ef};
+      const float4* dstd[3] = {d.tw4Pd, d.tw4Pid, nullptr};
       std::vector<float2> twf[3];
+      std::vector<float4> twd[3];
       for (int t = 0; t < 3; ++t) {
         const std::vector<double2>& tw = *src[t];
         CK(cudaMemcpyAsync((void*)dst[t], tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice,
@@ -1027,6 +1042,12 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
           twf[t].resize(tw.size());
           for (size_t k = 0; k < tw.size(); ++k) twf[t][k] = make_float2((float)tw[k].x, (float)tw[k].y);
           CK(cudaMemcpyAsync((void*)dstf[t], twf[t].data(), twf[t].size() * sizeof(float2),
+                             cudaMemcpyHostToDevice, c->stream));
+        }
+        if (dstd[t]) {
+          twd[t].resize(tw.size());
+          for (size_t k = 0; k < tw.size(); ++k) twd[t][k] = ds_split(tw[k]);
+          CK(cudaMemcpyAsync((void*)dstd[t], twd[t].data(), twd[t].size() * sizeof(float4),
                              cudaMemcpyHostToDevice, c->stream));
         }
       }
@@ -1057,6 +1078,13 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
         std::vector<float2> twf(n);
         for (int k = 0; k < n; ++k) twf[k] = make_float2((float)tw[k].x, (float)tw[k].y);
         CK(cudaMemcpyAsync((void*)pls[t]->twf, twf.data(), n * sizeof(float2), cudaMemcpyHostToDevice,
+                           c->stream));
+      }
+      std::vector<float4> twd;
+      if (pls[t]->twd) {
+        twd.resize(n);
+        for (int k = 0; k < n; ++k) twd[k] = ds_split(tw[k]);
+        CK(cudaMemcpyAsync((void*)pls[t]->twd, twd.data(), n * sizeof(float4), cudaMemcpyHostToDevice,
                            c->stream));
       }
       CK(cudaStreamSynchronize(c->stream));

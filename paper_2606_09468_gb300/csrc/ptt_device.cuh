@@ -9,6 +9,7 @@
 
 #include <type_traits>
 
+#include "ptt_ds.cuh"
 #include "ptt_internal.h"
 
 namespace ptt {
@@ -75,18 +76,32 @@ __device__ __forceinline__ float2 cfma(float s, float2 a, float2 c) {
   return make_float2(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y));
 }
 
+// compute types: double2 (FP64 path), float2 (mixed path), dsc (double-single:
+// the FP64-accurate path on the FP32 pipe, PTT_FP64_DS; see ptt_ds.cuh)
 template <typename C2> struct RealOf;
 template <> struct RealOf<double2> { using T = double; };
 template <> struct RealOf<float2> { using T = float; };
+template <> struct RealOf<dsc> { using T = dsf; };
 template <typename C2> __device__ __forceinline__ C2 zero2();
 template <> __device__ __forceinline__ double2 zero2<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 zero2<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ dsc zero2<dsc>() { return mk_dsc(dsf(0.f, 0.f), dsf(0.f, 0.f)); }
 template <typename D> __device__ __forceinline__ D cvt2(double2 v);
 template <typename D> __device__ __forceinline__ D cvt2(float2 v);
+template <typename D> __device__ __forceinline__ D cvt2(dsc v);
 template <> __device__ __forceinline__ double2 cvt2<double2>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 cvt2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 template <> __device__ __forceinline__ double2 cvt2<double2>(float2 v) { return make_double2(v.x, v.y); }
 template <> __device__ __forceinline__ float2 cvt2<float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ dsc cvt2<dsc>(double2 v) { return dsc_from_double2(v); }
+template <> __device__ __forceinline__ dsc cvt2<dsc>(float2 v) {
+  return mk_dsc(dsf(v.x, 0.f), dsf(v.y, 0.f));
+}
+template <> __device__ __forceinline__ dsc cvt2<dsc>(dsc v) { return v; }
+template <> __device__ __forceinline__ double2 cvt2<double2>(dsc v) { return dsc_to_double2(v); }
+template <> __device__ __forceinline__ float2 cvt2<float2>(dsc v) {
+  return make_float2(__fadd_rn(v.x.h, v.x.l), __fadd_rn(v.y.h, v.y.l));
+}
 
 // ------------------------------------------------------------ radix DFTs
 // DIR = -1: exp(-2 pi i jk/R) (forward); DIR = +1: exp(+2 pi i jk/R).
@@ -250,6 +265,14 @@ __device__ __forceinline__ PassC pass_c(const FftPlan& pl, int s) {
   return c;
 }
 
+// read-only table loads (the double-single table as one 16-byte load)
+__device__ __forceinline__ double2 ldg_tw(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldg_tw(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ dsc ldg_tw(const dsc* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return mk_dsc(dsf(v.x, v.y), dsf(v.z, v.w));
+}
+
 // One Stockham pass of radix R over nl lines (line l at offset l*ls).
 template <int DIR, int R, typename C2>
 __device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restrict__ dst,
@@ -271,7 +294,7 @@ __device__ __forceinline__ void fft_pass(const C2* __restrict__ src, C2* __restr
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        C2 w = __ldg(&tw[jm * r * st]);
+        C2 w = ldg_tw(&tw[jm * r * st]);
         if (DIR > 0) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
@@ -422,6 +445,9 @@ __device__ __forceinline__ void fft_pass_r3_zmid(const C2* __restrict__ src, C2*
 template <typename C2> __device__ __forceinline__ const C2* plan_tw(const FftPlan& pl);
 template <> __device__ __forceinline__ const double2* plan_tw<double2>(const FftPlan& pl) { return pl.tw; }
 template <> __device__ __forceinline__ const float2* plan_tw<float2>(const FftPlan& pl) { return pl.twf; }
+template <> __device__ __forceinline__ const dsc* plan_tw<dsc>(const FftPlan& pl) {
+  return reinterpret_cast<const dsc*>(pl.twd);
+}
 
 // Unnormalised DFT of nl lines of length pl.n held in `a`, using `b` as the
 // ping-pong buffer.  Returns the buffer holding the result.  Must be called
@@ -519,7 +545,7 @@ __device__ __forceinline__ void fft_pass_ip(C2* a, int nl, int ls, const PassC& 
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          C2 w = __ldg(&tw[jm * r * st]);
+          C2 w = ldg_tw(&tw[jm * r * st]);
           if (DIR > 0) w.y = -w.y;
           v[q][r] = cmul(v[q][r], w);
         }
@@ -942,23 +968,39 @@ struct YJob {
                          // forward (s_k/2) exp(-i pi k/(2M)) (s_0 = 1/M, s_k = 2/M),
                          // inverse (1/2) exp(+i pi k/(2M))
   const float2* tw4f;    // the same in single precision
+  const float4* tw4d;    // the same in double-single (re.h, re.l, im.h, im.l)
   int C;              // columns per block
   const int* status;  // skip members with status != 0 (may be null)
   FftPlan pl;
 };
 
+// Element formats of transform inputs and outputs (YJob / ZJob src_f32,
+// dst_f32): 0 complex double, 1 complex float, kFmtDS double-single as
+// computed (the intermediates of PTT_FP64_DS groups, in their FP64 arrays:
+// the same 16 bytes per element).  Only the double-single kernels read or
+// write kFmtDS.
+constexpr int kFmtDS = 2;
 template <typename CT>
 __device__ __forceinline__ CT ld2(const void* p, long long i, int f32) {
+  if constexpr (std::is_same<CT, dsc>::value) {
+    if (f32 == kFmtDS) return static_cast<const dsc*>(p)[i];
+  }
   return f32 ? cvt2<CT>(static_cast<const float2*>(p)[i]) : cvt2<CT>(static_cast<const double2*>(p)[i]);
 }
 template <typename CT>
 __device__ __forceinline__ void st2(void* p, long long i, int f32, CT v) {
+  if constexpr (std::is_same<CT, dsc>::value) {
+    if (f32 == kFmtDS) { static_cast<dsc*>(p)[i] = v; return; }
+  }
   if (f32) static_cast<float2*>(p)[i] = cvt2<float2>(v);
   else static_cast<double2*>(p)[i] = cvt2<double2>(v);
 }
 template <typename CT> __device__ __forceinline__ CT ld_tw4(const YJob& J, int k);
 template <> __device__ __forceinline__ double2 ld_tw4<double2>(const YJob& J, int k) { return __ldg(&J.tw4[k]); }
 template <> __device__ __forceinline__ float2 ld_tw4<float2>(const YJob& J, int k) { return __ldg(&J.tw4f[k]); }
+template <> __device__ __forceinline__ dsc ld_tw4<dsc>(const YJob& J, int k) {
+  return ldg_tw(reinterpret_cast<const dsc*>(J.tw4d) + k);
+}
 
 // Values at the M Gauss points y_j = cos(pi (2j+1)/(2M)) from coefficients
 // (DCT-III) and back (DCT-II), each as one complex FFT of length M: the
@@ -1137,8 +1179,8 @@ __device__ __forceinline__ void ycols_block(const YJob& J, Blk bk) {
   extern __shared__ __align__(16) unsigned char smraw[];
   CT* A = reinterpret_cast<CT*>(smraw);
   CT* B = A + (size_t)C * P;
-  const size_t es = J.src_f32 ? sizeof(float2) : sizeof(double2);
-  const size_t ed = J.dst_f32 ? sizeof(float2) : sizeof(double2);
+  const size_t es = (J.src_f32 == 1) ? sizeof(float2) : sizeof(double2);
+  const size_t ed = (J.dst_f32 == 1) ? sizeof(float2) : sizeof(double2);
   const void* src = static_cast<const char*>(J.src) + (b * J.src_mstride + J.src_field[f] * J.src_fstride) * es;
   void* dst = static_cast<char*>(J.dst) + (b * J.dst_mstride + J.dst_field[f] * J.dst_fstride) * ed;
   const void* src2 = (J.inverse && J.src_field2[f] >= 0)
@@ -1149,7 +1191,7 @@ __device__ __forceinline__ void ycols_block(const YJob& J, Blk bk) {
       : nullptr;
   if (J.gauss) {
     ycols_gauss<CT>(J, src, src2, src3, dst, A, B, c0, nc, f);
-  } else if constexpr (sizeof(CT) == sizeof(double2) && BIG) {
+  } else if constexpr (std::is_same<CT, double2>::value && BIG) {
     ycols_lobatto(J, src, src2, src3, dst, reinterpret_cast<double2*>(A), reinterpret_cast<double2*>(B),
                   reinterpret_cast<double2*>(B) + (size_t)C * P, c0, nc, f);
   }

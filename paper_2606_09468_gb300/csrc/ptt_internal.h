@@ -20,6 +20,8 @@ struct FftPlan {
   int radix[kMaxStages];
   const double2* tw;  // tw[k] = exp(-2 pi i k / n), k < n (device)
   const float2* twf;  // the same in single precision (mixed groups), or null
+  const float4* twd;  // the same in double-single, (re.h, re.l, im.h, im.l) with
+                      // re = re.h + re.l (PTT_FP64_DS groups), or null
   // Tangent-form twiddles of the FP64 passes s >= 1 of radix 2 to 5 (null:
   // use tw; passes of radix 7, 11, 13 always use tw).  Forward
   // twiddle r of stride index jm:
@@ -72,6 +74,10 @@ struct GroupDev {
   int xthreads;      // threads per block of the fused x kernels (ptt_autotune)
   int zC;            // 3D: x-mode lines per block of the z passes (ptt_autotune)
   int f32;           // 1: mixed precision (FP32 transforms and products)
+  int ds;            // 1: FP64-accurate transforms and products in double-single
+                     //    arithmetic on the FP32 pipe (PTT_FP64_DS); the arrays are
+                     //    those of an FP64 group, the padded-grid intermediates
+                     //    holding double-single values
   int nx, K, N;      // Fourier points / modes (K = nx/2), Chebyshev modes
   int nz, Mz, KZ;    // z modes (1 in 2D), padded z points, modes per Chebyshev index (K * nz)
   double invMx;      // 1 / Mx (host-computed), and its FP32 rounding
@@ -132,6 +138,8 @@ struct GroupDev {
   const float2* tw4Pif;  // the same in single precision (mixed groups)
   const double2* tw4E;   // [Me] inverse on the diagnostic Gauss grid: (1/2) exp(+i pi k/(2Me))
   const float2* tw4Ef;   // the same in single precision (mixed groups: FP32 energy transform)
+  const float4* tw4Pd;   // double-single forward and inverse tables (PTT_FP64_DS groups)
+  const float4* tw4Pid;
   FftPlan plP, plMx, plNx, plPu, plPe;   // lengths M, Mx, nx, 2(N-1), Me
   FftPlan plMz, plNz;                    // 3D: lengths Mz, nz
 };

@@ -37,12 +37,17 @@ __constant__ int c_xik[14] = {0, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 1, 1, 1};
 template <typename C2> __device__ __forceinline__ const C2* yp_ptr(const GroupDev& g);
 template <> __device__ __forceinline__ const double2* yp_ptr<double2>(const GroupDev& g) { return g.Yp; }
 template <> __device__ __forceinline__ const float2* yp_ptr<float2>(const GroupDev& g) { return g.Ypf; }
+template <> __device__ __forceinline__ const dsc* yp_ptr<dsc>(const GroupDev& g) {
+  return reinterpret_cast<const dsc*>(g.Yp);
+}
 template <typename C2> __device__ __forceinline__ C2* zp_ptr(const GroupDev& g);
 template <> __device__ __forceinline__ double2* zp_ptr<double2>(const GroupDev& g) { return g.Zp; }
 template <> __device__ __forceinline__ float2* zp_ptr<float2>(const GroupDev& g) { return g.Zpf; }
+template <> __device__ __forceinline__ dsc* zp_ptr<dsc>(const GroupDev& g) { return reinterpret_cast<dsc*>(g.Zp); }
 
 // C2 = double2: the FP64 path; C2 = float2: the mixed path (FP32 transforms
-// and products, FP64 state and solves).
+// and products, FP64 state and solves); C2 = dsc: the double-single path
+// (FP64-accurate transforms and products on the FP32 pipe, PTT_FP64_DS).
 template <typename C2>
 __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   using T = typename RealOf<C2>::T;
@@ -801,6 +806,7 @@ YJob make_yjob(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl,
   J.gauss = tw4 ? 1 : 0;
   J.tw4 = tw4;  // the quarter-period table of this direction
   J.tw4f = inverse ? g.tw4Pif : g.tw4Pf;
+  J.tw4d = inverse ? g.tw4Pid : g.tw4Pd;
   J.K = g.K;
   J.N = g.N;
   J.M = M;
@@ -863,6 +869,7 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
   cudaError_t e;
   if ((e = optin(k_ycols<double2>, optin_bytes))) return e;
   if ((e = optin(k_ycols<float2>, optin_bytes))) return e;
+  if ((e = optin(k_ycols<dsc>, optin_bytes))) return e;
   if ((e = optin(k_ycols<double2, true>, optin_bytes))) return e;
   if ((e = optin(k_ycols_multi<double2>, optin_bytes))) return e;
   if ((e = optin(k_ycols_multi<float2>, optin_bytes))) return e;
@@ -876,6 +883,7 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
   if ((e = optin(k_diag_final_multi, optin_bytes))) return e;
   if ((e = optin(k_xfused<double2>, optin_bytes))) return e;
   if ((e = optin(k_xfused<float2>, optin_bytes))) return e;
+  if ((e = optin(k_xfused<dsc>, optin_bytes))) return e;
   if ((e = optin(k_xrows, optin_bytes))) return e;
   if ((e = optin(k_spec<2>, optin_bytes))) return e;
   if ((e = optin(k_spec<4>, optin_bytes))) return e;
@@ -904,7 +912,7 @@ static YJob yjob_inverse(const GroupDev& g) {   // 9 fields on the padded Gauss 
   const size_t NK = (size_t)g.N * g.K;
   YJob J = make_yjob(g, true, g.M, g.Ccol, g.plP, g.tw4Pi);
   J.src = g.X; J.dst = g.f32 ? (void*)g.Ypf : (void*)g.Yp;
-  J.dst_f32 = g.f32;
+  J.dst_f32 = g.ds ? kFmtDS : g.f32;
   J.src_mstride = 5 * NK; J.dst_mstride = 9LL * g.M * g.K;
   J.src_fstride = NK; J.dst_fstride = (long long)g.M * g.K;
   const int sf[9] = {0, 1, 0, 2, 3, 4, 2, 3, 4};
@@ -916,7 +924,7 @@ static YJob yjob_forward(const GroupDev& g) {   // the 5 explicit fields to coef
   const size_t NK = (size_t)g.N * g.K;
   YJob F = make_yjob(g, false, g.M, g.Ccol, g.plP, g.tw4P);
   F.src = g.f32 ? (const void*)g.Zpf : (const void*)g.Zp; F.dst = g.NR;
-  F.src_f32 = g.f32;
+  F.src_f32 = g.ds ? kFmtDS : g.f32;
   F.src_mstride = 5LL * g.M * g.K; F.dst_mstride = 5 * NK;
   F.src_fstride = (long long)g.M * g.K; F.dst_fstride = NK;
   for (int i = 0; i < 5; ++i) { F.src_field[i] = i; F.dst_field[i] = i; F.deriv[i] = 0; }
@@ -968,12 +976,14 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       const YJob J = yjob_inverse(g);
       const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
       if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
+      else if (g.ds) k_ycols<dsc><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
       else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
       n = 1;
       break;
     }
     case 1:
       if (g.f32) k_xfused<float2><<<dim3(rows, g.nb), g.xthreads, smem_xfused(g.Mx, 1), st>>>(g);
+      else if (g.ds) k_xfused<dsc><<<dim3(rows, g.nb), g.xthreads, smem_xfused(g.Mx, 0), st>>>(g);
       else k_xfused<double2><<<dim3(rows, g.nb), g.xthreads, smem_xfused(g.Mx, 0), st>>>(g);
       n = 1;
       break;
@@ -987,6 +997,7 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
       const YJob F = yjob_forward(g);
       const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
       if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
+      else if (g.ds) k_ycols<dsc><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
       else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
       n = 1;
       break;

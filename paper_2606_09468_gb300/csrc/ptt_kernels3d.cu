@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
   extern __shared__ __align__(16) unsigned char smraw[];
   CT* A = reinterpret_cast<CT*>(smraw);
   CT* B = A + (size_t)C * Mz;
-  const size_t es = J.src_f32 ? sizeof(float2) : sizeof(double2);
-  const size_t ed = J.dst_f32 ? sizeof(float2) : sizeof(double2);
+  const size_t es = (J.src_f32 == 1) ? sizeof(float2) : sizeof(double2);
+  const size_t ed = (J.dst_f32 == 1) ? sizeof(float2) : sizeof(double2);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int hz = nz / 2;
   if (J.inverse) {
@@ -128,9 +128,13 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
 template <typename C2> __device__ __forceinline__ const C2* z3_ptr(const GroupDev& g);
 template <> __device__ __forceinline__ const double2* z3_ptr<double2>(const GroupDev& g) { return g.Z3; }
 template <> __device__ __forceinline__ const float2* z3_ptr<float2>(const GroupDev& g) { return g.Z3f; }
+template <> __device__ __forceinline__ const dsc* z3_ptr<dsc>(const GroupDev& g) {
+  return reinterpret_cast<const dsc*>(g.Z3);
+}
 template <typename C2> __device__ __forceinline__ C2* w3_ptr(const GroupDev& g);
 template <> __device__ __forceinline__ double2* w3_ptr<double2>(const GroupDev& g) { return g.W3; }
 template <> __device__ __forceinline__ float2* w3_ptr<float2>(const GroupDev& g) { return g.W3f; }
+template <> __device__ __forceinline__ dsc* w3_ptr<dsc>(const GroupDev& g) { return reinterpret_cast<dsc*>(g.W3); }
 
 // IP: the lines stay in one buffer and every FFT pass works in place
 // (fft_lines_inplace; kIpThreads threads), for the FP64 lines too long for
@@ -789,6 +793,7 @@ YJob yjob3(const GroupDev& g, bool inverse, int M, int C, const FftPlan& pl, con
   J.gauss = tw4 ? 1 : 0;
   J.tw4 = tw4;  // the quarter-period table of this direction
   J.tw4f = inverse ? g.tw4Pif : g.tw4Pf;
+  J.tw4d = inverse ? g.tw4Pid : g.tw4Pd;
   J.K = g.KZ;
   J.N = g.N;
   J.M = M;
@@ -851,6 +856,10 @@ cudaError_t set_kernel_attributes3(int optin_bytes) {
   cudaError_t e;
   if ((e = optin3(k_ycols<double2>, optin_bytes))) return e;
   if ((e = optin3(k_ycols<float2>, optin_bytes))) return e;
+  if ((e = optin3(k_ycols<dsc>, optin_bytes))) return e;
+  if ((e = optin3(k_zcols<dsc>, optin_bytes))) return e;
+  if ((e = optin3(k_xfused3<dsc>, optin_bytes))) return e;
+  if ((e = optin3(k_xfused3<dsc, true>, optin_bytes))) return e;
   if ((e = optin3(k_zcols<double2>, optin_bytes))) return e;
   if ((e = optin3(k_zcols<float2>, optin_bytes))) return e;
   if ((e = optin3(k_zcols<double2, true>, optin_bytes))) return e;
@@ -869,13 +878,16 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
   const long long yplane = (long long)M * KZ;          // Y3 / V3 field size
   const long long zplane = (long long)M * Mz * K;      // Z3 / W3 field size
   const int f32 = g.f32;
+  // element format of the padded-grid intermediates (double-single values
+  // in the FP64 arrays of PTT_FP64_DS groups)
+  const int fmt = g.ds ? kFmtDS : f32;
   int n = 0;
   switch (stage) {
     case 0: {  // inverse y (17 fields) then inverse z (26 lines)
       YJob J = yjob3(g, true, M, g.Ccol, g.plP, g.tw4Pi);
       J.src = g.X;
       J.dst = f32 ? (void*)g.Y3f : (void*)g.Y3;
-      J.dst_f32 = f32;
+      J.dst_f32 = fmt;
       J.src_mstride = 9 * NK; J.dst_mstride = 17 * yplane;
       J.src_fstride = NK; J.dst_fstride = yplane;
       const int sf[17] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 0, 2, 3, 4, 5, 6, 7, 8};
@@ -887,14 +899,16 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
         if (e) return e;
       } else if (f32) {
         k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
+      } else if (g.ds) {
+        k_ycols<dsc><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
       } else {
         k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
       }
       ++n;
       ZJob Z = zjob(g, true, Mz, M, g.plMz);
       Z.C = g.zC;
-      Z.src = J.dst; Z.src_f32 = f32;
-      Z.dst = f32 ? (void*)g.Z3f : (void*)g.Z3; Z.dst_f32 = f32;
+      Z.src = J.dst; Z.src_f32 = fmt;
+      Z.dst = f32 ? (void*)g.Z3f : (void*)g.Z3; Z.dst_f32 = fmt;
       Z.src_mstride = 17 * yplane; Z.dst_mstride = 26 * zplane;
       Z.src_fstride = yplane; Z.dst_fstride = zplane;
       for (int i = 0; i < 26; ++i) {
@@ -904,12 +918,16 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       }
       const size_t smz = smem_zcols(Z.C, Mz, f32);
       if (f32) k_zcols<float2><<<dim3(cdiv(K, Z.C), 26 * M, g.nb), 256, smz, st>>>(Z);
+      else if (g.ds) k_zcols<dsc><<<dim3(cdiv(K, Z.C), 26 * M, g.nb), 256, smz, st>>>(Z);
       else k_zcols<double2><<<dim3(cdiv(K, Z.C), 26 * M, g.nb), 256, smz, st>>>(Z);
       ++n;
       break;
     }
     case 1:
       if (f32) k_xfused3<float2><<<dim3(M * Mz, g.nb), g.xthreads, smem_xfused3(g.Mx, 1), st>>>(g);
+      else if (g.ds && xfused3_inplace(g.Mx, 0))
+        k_xfused3<dsc, true><<<dim3(M * Mz, g.nb), kIpThreads, smem_xfused3(g.Mx, 0), st>>>(g);
+      else if (g.ds) k_xfused3<dsc><<<dim3(M * Mz, g.nb), g.xthreads, smem_xfused3(g.Mx, 0), st>>>(g);
       else if (xfused3_inplace(g.Mx, 0))
         k_xfused3<double2, true><<<dim3(M * Mz, g.nb), kIpThreads, smem_xfused3(g.Mx, 0), st>>>(g);
       else k_xfused3<double2><<<dim3(M * Mz, g.nb), g.xthreads, smem_xfused3(g.Mx, 0), st>>>(g);
@@ -918,16 +936,17 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
     case 2: {  // forward z (9) then forward y (9)
       ZJob Z = zjob(g, false, Mz, M, g.plMz);
       Z.C = g.zC;
-      Z.src = f32 ? (const void*)g.W3f : (const void*)g.W3; Z.src_f32 = f32;
-      Z.dst = f32 ? (void*)g.V3f : (void*)g.V3; Z.dst_f32 = f32;
+      Z.src = f32 ? (const void*)g.W3f : (const void*)g.W3; Z.src_f32 = fmt;
+      Z.dst = f32 ? (void*)g.V3f : (void*)g.V3; Z.dst_f32 = fmt;
       Z.src_mstride = 9 * zplane; Z.dst_mstride = 9 * yplane;
       Z.src_fstride = zplane; Z.dst_fstride = yplane;
       for (int i = 0; i < 9; ++i) { Z.src_field[i] = i; Z.dst_field[i] = i; Z.dz[i] = 0; }
       const size_t smz = smem_zcols(Z.C, Mz, f32);
       if (f32) k_zcols<float2><<<dim3(cdiv(K, Z.C), 9 * M, g.nb), 256, smz, st>>>(Z);
+      else if (g.ds) k_zcols<dsc><<<dim3(cdiv(K, Z.C), 9 * M, g.nb), 256, smz, st>>>(Z);
       else k_zcols<double2><<<dim3(cdiv(K, Z.C), 9 * M, g.nb), 256, smz, st>>>(Z);
       YJob F = yjob3(g, false, M, g.Ccol, g.plP, g.tw4P);
-      F.src = Z.dst; F.src_f32 = f32;
+      F.src = Z.dst; F.src_f32 = fmt;
       F.dst = g.NR;
       F.src_mstride = 9 * yplane; F.dst_mstride = 9 * NK;
       F.src_fstride = yplane; F.dst_fstride = NK;
@@ -938,6 +957,8 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
         if (e) return e;
       } else if (f32) {
         k_ycols<float2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
+      } else if (g.ds) {
+        k_ycols<dsc><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
       } else {
         k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
       }

@@ -43,7 +43,7 @@ def test_status_strings_and_param_checks_without_gpu(lib):
     assert P.ptt_workspace_size([P.make_params(nx=512, ny=513)]) > 0
     assert P.ptt_workspace_size([P.make_params(nx=8, ny=9, nz=512, lz=5.0)]) > 0
     # 3D at nx = 512 in FP64 (the in-place x pass) and in mixed precision
-    for prec in (0, 1, 2):
+    for prec in (0, 1, 2, 3):
         assert P.ptt_workspace_size([P.make_params(nx=512, ny=17, nz=8, lz=5.0, precision=prec)]) > 0
     # the admitted lengths are 13-smooth: 14 = 2 7, ny - 1 = 65 = 5 13 pass; 34 = 2 17 does not
     for ok in (dict(nx=14), dict(ny=66), dict(nx=224), dict(nx=352), dict(nx=416), dict(ny=225),
@@ -51,7 +51,7 @@ def test_status_strings_and_param_checks_without_gpu(lib):
         assert P.ptt_workspace_size([P.make_params(**ok)]) > 0, ok
     for bad in (dict(nx=63), dict(ny=39), dict(nx=34), dict(beta=0.0), dict(nz=2), dict(nz=3),
                 dict(nz=34), dict(nz=1024), dict(nz=8, lz=0.0), dict(nx=6), dict(nx=1024),
-                dict(ny=7), dict(ny=1025), dict(dt=0.0), dict(precision=3)):
+                dict(ny=7), dict(ny=1025), dict(dt=0.0), dict(precision=4), dict(precision=-1)):
         with pytest.raises(P.PttError):
             P.ptt_workspace_size([P.make_params(**bad)])
     # an empty ensemble
