@@ -573,8 +573,9 @@ def other_workloads(args):
 
 def paper_shapes(args):
     """The paper's production shapes (Table 1) at its box and time step, a few
-    steps each, with the wall time the paper's run length (T/Wi = 68,
-    dt = 2.5e-3) would take at the measured rate on this one GPU.  The
+    steps each, in mixed precision, FP64 and double-single, with the wall time
+    the paper's run length (T/Wi = 68, dt = 2.5e-3) would take at the measured
+    rate on this one GPU.  The
     paper's own cost, on CPU cores of ARCHER2: A1 2e5 core-hours, A6 1.6e6
     core-hours (context, not a target)."""
     import torch
@@ -585,7 +586,7 @@ def paper_shapes(args):
     for name, (nx, ny, nz) in I.PAPER_SHAPES.items():
         pts = nx * ny * nz
         row = {"shape": [nx, ny, nz], "grid_points": pts}
-        for prec, tag in ((P.PTT_MIXED, "mixed"), (P.PTT_FP64, "fp64")):
+        for prec, tag in ((P.PTT_MIXED, "mixed"), (P.PTT_FP64, "fp64"), (P.PTT_FP64_DS, "fp64_ds")):
             prm = P.make_params(nx=nx, ny=ny, nz=nz, lz=I.PAPER_LZ, dt=I.PAPER_DT, precision=prec,
                                 **{k: v for k, v in I.PAPER.items()})
             try:

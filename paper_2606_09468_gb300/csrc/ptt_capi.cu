@@ -585,8 +585,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
       // single-precision tables: the step's padded lengths and the energy grid
       pls[i]->twf = (d.f32 && (i < 2 || i == 4 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
-      // double-single tables: the step's padded lengths
-      pls[i]->twd = (d.ds && (i < 2 || i == 5)) ? cv.take<float4>((size_t)g.hp[i].n) : nullptr;
+      // double-single tables (the step's and the diagnostics' lengths)
+      pls[i]->twd = d.ds ? cv.take<float4>((size_t)g.hp[i].n) : nullptr;
       int nrec = 0, ndbl = 0;
       tangent_offsets(g.hp[i], pls[i]->toff, pls[i]->tto, &nrec, &ndbl);
       pls[i]->tt = cv.take<double>((size_t)ndbl);
@@ -600,6 +600,7 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.tw4Ef = d.f32 ? cv.take<float2>((size_t)d.Me) : nullptr;
     d.tw4Pd = d.ds ? cv.take<float4>((size_t)d.M) : nullptr;
     d.tw4Pid = d.ds ? cv.take<float4>((size_t)d.M) : nullptr;
+    d.tw4Ed = d.ds ? cv.take<float4>((size_t)d.Me) : nullptr;
   }
 }
 
@@ -633,7 +634,7 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
 bool multi_eligible(const std::vector<Group>& groups) {
   if (groups.size() < 2 || (int)groups.size() > multi2d_max_groups()) return false;
   for (const Group& g : groups)
-    if (g.d.nz != 1 || g.d.ymma || g.d.ds || g.d.f32 != groups[0].d.f32) return false;
+    if (g.d.nz != 1 || g.d.ymma || g.d.f32 != groups[0].d.f32 || g.d.ds != groups[0].d.ds) return false;
   return true;
 }
 
@@ -1031,7 +1032,7 @@ int ptt_create(const ptt_params* pm, int32_t nmem, void* d_ws, size_t bytes, voi
       const std::vector<double2>* src[3] = {&fwd, &inv, &invE};
       const double2* dst[3] = {d.tw4P, d.tw4Pi, d.tw4E};
       const float2* dstf[3] = {d.tw4Pf, d.tw4Pif, d.tw4Ef};
-      const float4* dstd[3] = {d.tw4Pd, d.tw4Pid, nullptr};
+      const float4* dstd[3] = {d.tw4Pd, d.tw4Pid, d.tw4Ed};
       std::vector<float2> twf[3];
       std::vector<float4> twd[3];
       for (int t = 0; t < 3; ++t) {

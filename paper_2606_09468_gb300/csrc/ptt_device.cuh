@@ -1089,24 +1089,23 @@ __device__ void ycols_gauss(const YJob& J, const void* src, const void* src2, co
   }
 }
 
-// Gauss-Lobatto path (double precision only): DCT-I by the even extension.
-__device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v, const void* src3v,
-                              void* dstv, double2* A, double2* B, double2* a0s, int c0, int nc, int f) {
+// Gauss-Lobatto path (FP64, or double-single in PTT_FP64_DS groups; FP64
+// arrays in and out): DCT-I by the even extension.
+template <typename CT>
+__device__ void ycols_lobatto(const YJob& J, const void* src, const void* src2, const void* src3,
+                              void* dst, CT* A, CT* B, CT* a0s, int c0, int nc, int f) {
+  using T = typename RealOf<CT>::T;
   const int C = J.C, N = J.N, M = J.M, P = 2 * J.M;
-  const double2* src = static_cast<const double2*>(srcv);
-  const double2* src2 = static_cast<const double2*>(src2v);
-  const double2* src3 = static_cast<const double2*>(src3v);
-  double2* dst = static_cast<double2*>(dstv);
   const int tid = threadIdx.x, nt = blockDim.x;
   if (J.inverse) {
     for (int i = tid; i < N * C; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - c * N;
-      double2 v = czero();
+      CT v = zero2<CT>();
       if (c < nc) {
         const long long o = (c0 + c) * J.cm + n * J.cn;
-        v = src[o];
-        if (src2) v = cadd(v, src2[o]);
-        if (src3) v = cadd(v, src3[o]);
+        v = ld2<CT>(src, o, 0);
+        if (src2) v = cadd(v, ld2<CT>(src2, o, 0));
+        if (src3) v = cadd(v, ld2<CT>(src3, o, 0));
       }
       A[c * P + n] = v;
     }
@@ -1122,29 +1121,29 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
     }
     if (tid < C) {
       a0s[tid] = A[tid * P];
-      a0s[C + tid] = (N > M) ? A[tid * P + M] : czero();
+      a0s[C + tid] = (N > M) ? A[tid * P + M] : zero2<CT>();
     }
     // even extension: A[n] = a_n (n <= M, zero for n >= N), A[P-n] = a_n
     for (int i = tid; i < C * P; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)P)), n = i - c * P;
-      if (n >= N && n <= M) A[i] = czero();
-      else if (n > M) { const int r = P - n; A[i] = (r < N) ? A[c * P + r] : czero(); }
+      if (n >= N && n <= M) A[i] = zero2<CT>();
+      else if (n > M) { const int r = P - n; A[i] = (r < N) ? A[c * P + r] : zero2<CT>(); }
     }
     __syncthreads();
-    double2* res = fft_lines<-1, double2, true>(A, B, C, P, J.pl);
+    CT* res = fft_lines<-1, CT, true>(A, B, C, P, J.pl);
     // f_j = (F_j + a_0 + (-1)^j a_M) / 2
     for (int i = tid; i < (M + 1) * C; i += nt) {
       const int j = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - j * C;
       if (c < nc) {
-        double2 v = cadd(res[c * P + j], a0s[c]);
+        CT v = cadd(res[c * P + j], a0s[c]);
         v = (j & 1) ? csub(v, a0s[C + c]) : cadd(v, a0s[C + c]);
-        dst[j * J.vj + (c0 + c) * J.vm] = cscl(v, 0.5);
+        st2<CT>(dst, j * J.vj + (c0 + c) * J.vm, 0, cscl(v, (T)0.5));
       }
     }
   } else {
     for (int i = tid; i < (M + 1) * C; i += nt) {
       const int j = (int)fdiv((unsigned)i, fast_div((unsigned)C)), c = i - j * C;
-      A[c * P + j] = (c < nc) ? src[j * J.vj + (c0 + c) * J.vm] : czero();
+      A[c * P + j] = (c < nc) ? ld2<CT>(src, j * J.vj + (c0 + c) * J.vm, 0) : zero2<CT>();
     }
     __syncthreads();
     for (int i = tid; i < C * P; i += nt) {
@@ -1152,13 +1151,13 @@ __device__ void ycols_lobatto(const YJob& J, const void* srcv, const void* src2v
       if (j > M) A[i] = A[c * P + (P - j)];
     }
     __syncthreads();
-    double2* res = fft_lines<-1, double2, true>(A, B, C, P, J.pl);
-    const double inv = 1.0 / M;
+    CT* res = fft_lines<-1, CT, true>(A, B, C, P, J.pl);
+    const T inv = T(1.0 / M);
     for (int i = tid; i < N * C; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)N)), n = i - c * N;
       if (c < nc) {
-        const double s = (n == 0 || n == M) ? 0.5 * inv : inv;
-        dst[(c0 + c) * J.cm + n * J.cn] = cscl(res[c * P + n], s);
+        const T s = (n == 0 || n == M) ? (T)0.5 * inv : inv;
+        st2<CT>(dst, (c0 + c) * J.cm + n * J.cn, 0, cscl(res[c * P + n], s));
       }
     }
   }
@@ -1191,9 +1190,8 @@ __device__ __forceinline__ void ycols_block(const YJob& J, Blk bk) {
       : nullptr;
   if (J.gauss) {
     ycols_gauss<CT>(J, src, src2, src3, dst, A, B, c0, nc, f);
-  } else if constexpr (std::is_same<CT, double2>::value && BIG) {
-    ycols_lobatto(J, src, src2, src3, dst, reinterpret_cast<double2*>(A), reinterpret_cast<double2*>(B),
-                  reinterpret_cast<double2*>(B) + (size_t)C * P, c0, nc, f);
+  } else if constexpr (!std::is_same<CT, float2>::value && BIG) {
+    ycols_lobatto<CT>(J, src, src2, src3, dst, A, B, B + (size_t)C * P, c0, nc, f);
   }
 }
 

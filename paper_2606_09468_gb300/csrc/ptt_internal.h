@@ -138,8 +138,9 @@ struct GroupDev {
   const float2* tw4Pif;  // the same in single precision (mixed groups)
   const double2* tw4E;   // [Me] inverse on the diagnostic Gauss grid: (1/2) exp(+i pi k/(2Me))
   const float2* tw4Ef;   // the same in single precision (mixed groups: FP32 energy transform)
-  const float4* tw4Pd;   // double-single forward and inverse tables (PTT_FP64_DS groups)
-  const float4* tw4Pid;
+  const float4* tw4Pd;   // double-single forward, inverse and diagnostic tables
+  const float4* tw4Pid;  // (PTT_FP64_DS groups)
+  const float4* tw4Ed;
   FftPlan plP, plMx, plNx, plPu, plPe;   // lengths M, Mx, nx, 2(N-1), Me
   FftPlan plMz, plNz;                    // 3D: lengths Mz, nz
 };

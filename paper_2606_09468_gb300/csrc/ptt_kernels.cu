@@ -871,11 +871,15 @@ cudaError_t set_kernel_attributes(int optin_bytes) {
   if ((e = optin(k_ycols<float2>, optin_bytes))) return e;
   if ((e = optin(k_ycols<dsc>, optin_bytes))) return e;
   if ((e = optin(k_ycols<double2, true>, optin_bytes))) return e;
+  if ((e = optin(k_ycols<dsc, true>, optin_bytes))) return e;
   if ((e = optin(k_ycols_multi<double2>, optin_bytes))) return e;
   if ((e = optin(k_ycols_multi<float2>, optin_bytes))) return e;
   if ((e = optin(k_ycols_multi<double2, true>, optin_bytes))) return e;
   if ((e = optin(k_xfused_multi<double2>, optin_bytes))) return e;
   if ((e = optin(k_xfused_multi<float2>, optin_bytes))) return e;
+  if ((e = optin(k_xfused_multi<dsc>, optin_bytes))) return e;
+  if ((e = optin(k_ycols_multi<dsc>, optin_bytes))) return e;
+  if ((e = optin(k_ycols_multi<dsc, true>, optin_bytes))) return e;
   if ((e = optin(k_spec_multi<2>, optin_bytes))) return e;
   if ((e = optin(k_spec_multi<4>, optin_bytes))) return e;
   if ((e = optin(k_spec_multi<kMaxChunk>, optin_bytes))) return e;
@@ -934,6 +938,7 @@ static YJob yjob_energy(const GroupDev& g) {    // u, v on the Me Gauss points
   const size_t NK = (size_t)g.N * g.K;
   YJob J = make_yjob(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
   J.tw4f = g.tw4Ef;   // mixed groups transform in FP32 (the sums stay FP64)
+  J.tw4d = g.tw4Ed;   // double-single groups in double-single
   J.src = g.X; J.dst = g.DY;
   J.src_mstride = 5 * NK; J.dst_mstride = 2LL * g.Me * g.K;
   J.src_fstride = NK; J.dst_fstride = (long long)g.Me * g.K;
@@ -1042,13 +1047,20 @@ static void diag_energy_y(const GroupDev& g, cudaStream_t st) {
   if (g.f32)
     k_ycols<float2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 1), st>>>(
         yjob_energy(g));
+  else if (g.ds)
+    k_ycols<dsc><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(
+        yjob_energy(g));
   else
     k_ycols<double2><<<dim3(cdiv(g.K, g.CcolE), 2, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(
         yjob_energy(g));
 }
 static void diag_trc_y(const GroupDev& g, cudaStream_t st) {
-  k_ycols<double2, true><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(
-      yjob_trc(g));
+  if (g.ds)
+    k_ycols<dsc, true><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(
+        yjob_trc(g));
+  else
+    k_ycols<double2, true><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(
+        yjob_trc(g));
 }
 
 cudaError_t launch_diag_transforms(const GroupDev& g, cudaStream_t st) {
@@ -1076,7 +1088,7 @@ cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nl) 
 
 // ------------------------------------------------- launches over all groups
 struct Multi2DPlan {
-  int ng = 0, f32 = 0;
+  int ng = 0, f32 = 0, ds = 0;
   const GroupDev* dg = nullptr;
   const YJob* dyj = nullptr;     // [4][ng]: inverse, forward, energy, Tr c
   const XJob* dxj = nullptr;     // [ng]: Tr c x synthesis
@@ -1112,6 +1124,7 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
   Multi2DPlan* p = new Multi2DPlan();
   p->ng = ng;
   p->f32 = groups[0]->f32;
+  p->ds = groups[0]->ds;
   std::vector<GroupDev> hg(ng);
   std::vector<YJob> hy(4 * (size_t)ng);
   std::vector<XJob> hx(ng);
@@ -1124,7 +1137,11 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
   std::vector<Ent> e_inv, e_fwd, e_xf, e_spec[3], e_ye, e_yt, e_xr, e_mid, e_part, e_fin;
   for (int q = 0; q < ng; ++q) {
     const GroupDev& g = *groups[q];
-    if (g.nz != 1 || g.f32 != p->f32 || g.ymma) { delete p; *err = cudaErrorInvalidValue; return nullptr; }
+    if (g.nz != 1 || g.f32 != p->f32 || g.ds != p->ds || g.ymma) {
+      delete p;
+      *err = cudaErrorInvalidValue;
+      return nullptr;
+    }
     hg[q] = g;
     hy[q] = yjob_inverse(g);
     hy[ng + q] = yjob_forward(g);
@@ -1192,16 +1209,19 @@ cudaError_t launch_stage_multi(const Multi2DPlan* p, int stage, cudaStream_t st,
   switch (stage) {
     case 0:
       if (p->f32) k_ycols_multi<float2><<<mm_blocks(p->inv), 256, p->sm_inv, st>>>(p->dyj, p->inv);
+      else if (p->ds) k_ycols_multi<dsc><<<mm_blocks(p->inv), 256, p->sm_inv, st>>>(p->dyj, p->inv);
       else k_ycols_multi<double2><<<mm_blocks(p->inv), 256, p->sm_inv, st>>>(p->dyj, p->inv);
       n = 1;
       break;
     case 1:
       if (p->f32) k_xfused_multi<float2><<<mm_blocks(p->xf), 512, p->sm_xf, st>>>(p->dg, p->xf);
+      else if (p->ds) k_xfused_multi<dsc><<<mm_blocks(p->xf), 512, p->sm_xf, st>>>(p->dg, p->xf);
       else k_xfused_multi<double2><<<mm_blocks(p->xf), 512, p->sm_xf, st>>>(p->dg, p->xf);
       n = 1;
       break;
     case 2:
       if (p->f32) k_ycols_multi<float2><<<mm_blocks(p->fwd), 256, p->sm_fwd, st>>>(p->dyj + ng, p->fwd);
+      else if (p->ds) k_ycols_multi<dsc><<<mm_blocks(p->fwd), 256, p->sm_fwd, st>>>(p->dyj + ng, p->fwd);
       else k_ycols_multi<double2><<<mm_blocks(p->fwd), 256, p->sm_fwd, st>>>(p->dyj + ng, p->fwd);
       n = 1;
       break;
@@ -1231,9 +1251,11 @@ cudaError_t launch_diag_multi(const Multi2DPlan* p, const DiagStreams& d, int* n
   cudaError_t e = diag_fork(d);
   if (e) return e;
   if (p->f32) k_ycols_multi<float2><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
+  else if (p->ds) k_ycols_multi<dsc><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
   else k_ycols_multi<double2><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
   k_diag_mid_multi<<<mm_blocks(p->mid), 256, 0, d.s[2]>>>(p->dg, p->mid);
-  k_ycols_multi<double2, true><<<mm_blocks(p->yt), 256, p->sm_yt, d.s[0]>>>(p->dyj + 3 * ng, p->yt);
+  if (p->ds) k_ycols_multi<dsc, true><<<mm_blocks(p->yt), 256, p->sm_yt, d.s[0]>>>(p->dyj + 3 * ng, p->yt);
+  else k_ycols_multi<double2, true><<<mm_blocks(p->yt), 256, p->sm_yt, d.s[0]>>>(p->dyj + 3 * ng, p->yt);
   k_xrows_multi<<<mm_blocks(p->xr), 256, p->sm_xr, d.s[0]>>>(p->dxj, p->xr);
   if ((e = cudaGetLastError()) || (e = diag_join(d))) return e;
   k_diag_part_multi<<<mm_blocks(p->part), 256, 0, d.s[0]>>>(p->dg, p->part);

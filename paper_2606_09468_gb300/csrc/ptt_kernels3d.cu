@@ -863,6 +863,8 @@ cudaError_t set_kernel_attributes3(int optin_bytes) {
   if ((e = optin3(k_zcols<double2>, optin_bytes))) return e;
   if ((e = optin3(k_zcols<float2>, optin_bytes))) return e;
   if ((e = optin3(k_zcols<double2, true>, optin_bytes))) return e;
+  if ((e = optin3(k_zcols<dsc, true>, optin_bytes))) return e;
+  if ((e = optin3(k_ycols<dsc, true>, optin_bytes))) return e;
   if ((e = optin3(k_ycols<double2, true>, optin_bytes))) return e;
   if ((e = optin3(k_xfused3<double2>, optin_bytes))) return e;
   if ((e = optin3(k_xfused3<float2>, optin_bytes))) return e;
@@ -1005,11 +1007,13 @@ static void diag_energy_y3(const GroupDev& g, cudaStream_t st) {
   const size_t NK = (size_t)g.N * KZ;
   YJob J = yjob3(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
   J.tw4f = g.tw4Ef;   // mixed groups transform in FP32 (the sums stay FP64)
+  J.tw4d = g.tw4Ed;   // double-single groups in double-single
   J.src = g.X; J.dst = g.DY;
   J.src_mstride = 9 * NK; J.dst_mstride = 3LL * g.Me * KZ;
   J.src_fstride = NK; J.dst_fstride = (long long)g.Me * KZ;
   for (int i = 0; i < 3; ++i) { J.src_field[i] = i; J.dst_field[i] = i; J.deriv[i] = 0; }
   if (g.f32) k_ycols<float2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 1), st>>>(J);
+  else if (g.ds) k_ycols<dsc><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
   else k_ycols<double2><<<dim3(cdiv(KZ, g.CcolE), 3, g.nb), 256, smem_ycols(g.CcolE, g.Me, 0), st>>>(J);
 }
 static void diag_trc_y3(const GroupDev& g, cudaStream_t st) {
@@ -1020,7 +1024,8 @@ static void diag_trc_y3(const GroupDev& g, cudaStream_t st) {
   T.src_mstride = 9 * NK; T.dst_mstride = (long long)NK;
   T.src_fstride = NK; T.dst_fstride = 0;
   T.src_field[0] = 3; T.src_field2[0] = 6; T.src_field3[0] = 8; T.dst_field[0] = 0; T.deriv[0] = 0;
-  k_ycols<double2, true><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+  if (g.ds) k_ycols<dsc, true><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+  else k_ycols<double2, true><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
 }
 
 cudaError_t launch_diag_transforms3(const GroupDev& g, cudaStream_t st) {
@@ -1042,7 +1047,8 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   Zm.src_mstride = 8LL * KZ; Zm.dst_mstride = 8LL * g.nz * K;
   Zm.src_fstride = KZ; Zm.dst_fstride = (long long)g.nz * K;
   for (int i = 0; i < 8; ++i) { Zm.src_field[i] = i; Zm.dst_field[i] = i; Zm.dz[i] = 0; }
-  k_zcols<double2, true><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
+  if (g.ds) k_zcols<dsc, true><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
+  else k_zcols<double2, true><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
   XJob Xm{};
   Xm.srcC = g.DMZ; Xm.dstR = g.MV;
   Xm.src_mstride = 8LL * g.nz * K; Xm.dst_mstride = 8LL * g.nz * g.nx;
@@ -1057,7 +1063,8 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   Z.src_mstride = (long long)NK; Z.dst_mstride = (long long)g.N * g.nz * K;
   Z.src_fstride = 0; Z.dst_fstride = 0;
   Z.src_field[0] = 0; Z.dst_field[0] = 0; Z.dz[0] = 0;
-  k_zcols<double2, true><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
+  if (g.ds) k_zcols<dsc, true><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
+  else k_zcols<double2, true><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
   XJob X{};
   X.srcC = g.DZ; X.dstR = g.DV;
   X.src_mstride = (long long)g.N * g.nz * K; X.dst_mstride = (long long)g.N * g.nz * g.nx;

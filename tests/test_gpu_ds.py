@@ -116,3 +116,61 @@ def test_ds_and_fp64_agree_at_sweep_shapes():
     for i, sh in enumerate(shapes):
         e = _errs(out[P.PTT_FP64_DS][i], out[P.PTT_FP64][i])
         assert np.all(e <= TOL_1), (sh, e)
+
+
+def test_ds_diagnostics_match_oracle_2d():
+    """The diagnostics of a double-single run (its transforms to the grids in
+    double-single, the sums in FP64) at the FP64 diagnostics' bounds."""
+    from test_gpu_parity import _diag_compare, _umax
+    nx, ny = I.SMALL
+    ctx = _ctx2(nx, ny)
+    ctx.init_state(0, 3, I.AMPLITUDE)
+    ora = Channel2D(Params(nx=nx, ny=ny, dt=I.DT, **I.PAPER))
+    ora.init_state(3, I.AMPLITUDE)
+    recs = ctx.diagnostics(0)
+    _diag_compare(recs[0], ora.diagnostics(), nx, ny, ora.p.lx, _umax(ora))
+    for _ in range(3):
+        ora.step()
+    ctx.step(3)
+    recs = ctx.diagnostics(0)
+    assert [r["step"] for r in recs] == [1, 2, 3] and all(r["status"] == 0 for r in recs)
+    _diag_compare(recs[-1], ora.diagnostics(), nx, ny, ora.p.lx, _umax(ora))
+
+
+def test_ds_diagnostics_match_oracle_3d():
+    from test_gpu_parity3d import _mid_sums_compare
+    nx, ny, nz = 32, 33, 16
+    ctx = _ctx3(nx, ny, nz)
+    ctx.init_state(0, 3, 0.01)
+    ora = O3.Channel3D(O3.Params3(nx=nx, ny=ny, nz=nz, **PAPER3))
+    ora.init_state(3, 0.01)
+    for _ in range(2):
+        ora.step()
+    ctx.step(2)
+    g = ctx.diagnostics(0)[-1]
+    o = ora.diagnostics()
+    assert g["step"] == 2 and g["status"] == 0
+    for k in ("energy", "mean_trc"):
+        assert abs(g[k] - o[k]) <= 1e-11 * abs(o[k]), (k, g[k], o[k])
+    sc = max(abs(o["max_trc"]), abs(o["min_trc"]))
+    for k in ("min_trc", "max_trc"):
+        assert abs(g[k] - o[k]) <= 1e-11 * sc, (k, g[k], o[k])
+    for k, band in (("n_lt3", "n_band3"), ("n_lt0", "n_band0"),
+                    ("n_mid_lt3", "n_mid_band3"), ("n_mid_lt0", "n_mid_band0")):
+        assert abs(g[k] - o[k]) <= o[band], (k, g[k], o[k])
+    _mid_sums_compare(g, o, nx, nz, ora, rel=1e-11)
+
+
+def test_ds_blowup_flag_matches_fp64():
+    """A NaN planted in the state is caught on the next record, as in FP64."""
+    import paper_2606_09468_gb300 as P
+    nx, ny = 32, 33
+    ctx = _ctx2(nx, ny)
+    ctx.init_state(0, 1, I.AMPLITUDE)
+    phys = ctx.get_state(0)
+    phys[2, ny // 2, nx // 2] = np.nan
+    ctx.set_state(0, phys)
+    ctx.step(2)
+    assert ctx.synchronize() == P.PTT_BLOWUP
+    recs = ctx.diagnostics(0)
+    assert recs[-1]["status"] == P.PTT_BLOWUP

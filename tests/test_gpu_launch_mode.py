@@ -29,7 +29,7 @@ def _ctx(P, shapes, precision, mode):
     return ctx
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 3])   # FP64, mixed, double-single
 def test_launch_modes_are_bitwise_equal(precision):
     import paper_2606_09468_gb300 as P
     P.load_library()
@@ -92,6 +92,11 @@ def test_launch_mode_eligibility():
                        P.make_params(nx=64, ny=65, precision=P.PTT_MIXED, **kw)])
     with pytest.raises(P.PttError) as ei:
         mixed.set_launch_mode(1)          # two precisions
+    assert ei.value.code == P.PTT_ENOTSUP
+    fds = P.Context([P.make_params(nx=64, ny=65, **kw),
+                     P.make_params(nx=64, ny=65, precision=P.PTT_FP64_DS, **kw)])
+    with pytest.raises(P.PttError) as ei:
+        fds.set_launch_mode(1)            # FP64 and double-single
     assert ei.value.code == P.PTT_ENOTSUP
     with pytest.raises(P.PttError):
         one.set_launch_mode(2)
