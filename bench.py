@@ -748,6 +748,10 @@ def run_ours(args):
                "status": P.ptt_status_string(mctx.synchronize()),
                "max_rel_field_dev_vs_fp64_gpu": dict(zip(["u", "v", "cxx", "cxy", "cyy"], dev)),
                "dev_after_steps": args.warmup, "dev_member": "512x257"}
+        if rank == 0:
+            nst = max(args.steps // 4, 5)
+            st = mctx.time_stages(nst)
+            res["stage_ms_per_step"] = {P.STAGE_NAMES[i]: st[i] / nst for i in range(P.PTT_NSTAGES)}
         mctx.close()
         return res
 

@@ -69,7 +69,9 @@ extern "C" {
 #define PTT_FP64 0         /* every step of the path in FP64                     */
 #define PTT_MIXED 1        /* FP32 Fourier and Chebyshev transforms (FFTs; the
                               Chebyshev ones as DCT-II/III) and products; FP64
-                              state, SBDF sums, tau solves and diagnostics      */
+                              state, SBDF sums, tau solves and diagnostic sums
+                              (the energy's transform in FP32, the Tr c and
+                              mid-plane transforms in double-single)          */
 #define PTT_MIXED_TC 2     /* as PTT_MIXED, with the Chebyshev transforms as dense
                               contractions on the tensor cores: BF16 slices of a
                               fixed-point split, FP32 accumulation (FP32 FFTs for

@@ -585,8 +585,9 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       pls[i]->tw = cv.take<double2>((size_t)g.hp[i].n);
       // single-precision tables: the step's padded lengths and the energy grid
       pls[i]->twf = (d.f32 && (i < 2 || i == 4 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
-      // double-single tables (the step's and the diagnostics' lengths)
-      pls[i]->twd = d.ds ? cv.take<float4>((size_t)g.hp[i].n) : nullptr;
+      // double-single tables: every length of a double-single group; the
+      // unpadded y and z lengths of a mixed group (its Tr c transforms)
+      pls[i]->twd = (d.ds || (d.f32 && (i == 3 || i == 6))) ? cv.take<float4>((size_t)g.hp[i].n) : nullptr;
       int nrec = 0, ndbl = 0;
       tangent_offsets(g.hp[i], pls[i]->toff, pls[i]->tto, &nrec, &ndbl);
       pls[i]->tt = cv.take<double>((size_t)ndbl);

@@ -1055,7 +1055,7 @@ static void diag_energy_y(const GroupDev& g, cudaStream_t st) {
         yjob_energy(g));
 }
 static void diag_trc_y(const GroupDev& g, cudaStream_t st) {
-  if (g.ds)
+  if (g.ds || g.f32)   // double-single (FP64 in and out, FP64 sums downstream)
     k_ycols<dsc, true><<<dim3(cdiv(g.K, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(
         yjob_trc(g));
   else
@@ -1254,7 +1254,8 @@ cudaError_t launch_diag_multi(const Multi2DPlan* p, const DiagStreams& d, int* n
   else if (p->ds) k_ycols_multi<dsc><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
   else k_ycols_multi<double2><<<mm_blocks(p->ye), 256, p->sm_ye, d.s[1]>>>(p->dyj + 2 * ng, p->ye);
   k_diag_mid_multi<<<mm_blocks(p->mid), 256, 0, d.s[2]>>>(p->dg, p->mid);
-  if (p->ds) k_ycols_multi<dsc, true><<<mm_blocks(p->yt), 256, p->sm_yt, d.s[0]>>>(p->dyj + 3 * ng, p->yt);
+  if (p->ds || p->f32)
+    k_ycols_multi<dsc, true><<<mm_blocks(p->yt), 256, p->sm_yt, d.s[0]>>>(p->dyj + 3 * ng, p->yt);
   else k_ycols_multi<double2, true><<<mm_blocks(p->yt), 256, p->sm_yt, d.s[0]>>>(p->dyj + 3 * ng, p->yt);
   k_xrows_multi<<<mm_blocks(p->xr), 256, p->sm_xr, d.s[0]>>>(p->dxj, p->xr);
   if ((e = cudaGetLastError()) || (e = diag_join(d))) return e;

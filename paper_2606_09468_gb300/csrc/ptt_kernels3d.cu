@@ -1024,7 +1024,8 @@ static void diag_trc_y3(const GroupDev& g, cudaStream_t st) {
   T.src_mstride = 9 * NK; T.dst_mstride = (long long)NK;
   T.src_fstride = NK; T.dst_fstride = 0;
   T.src_field[0] = 3; T.src_field2[0] = 6; T.src_field3[0] = 8; T.dst_field[0] = 0; T.deriv[0] = 0;
-  if (g.ds) k_ycols<dsc, true><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
+  if (g.ds || g.f32)   // double-single (FP64 in and out, FP64 sums downstream)
+    k_ycols<dsc, true><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
   else k_ycols<double2, true><<<dim3(cdiv(KZ, g.CcolU), 1, g.nb), 256, smem_ycols(g.CcolU, g.Pu, 0), st>>>(T);
 }
 
@@ -1047,7 +1048,8 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   Zm.src_mstride = 8LL * KZ; Zm.dst_mstride = 8LL * g.nz * K;
   Zm.src_fstride = KZ; Zm.dst_fstride = (long long)g.nz * K;
   for (int i = 0; i < 8; ++i) { Zm.src_field[i] = i; Zm.dst_field[i] = i; Zm.dz[i] = 0; }
-  if (g.ds) k_zcols<dsc, true><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
+  if (g.ds || g.f32)
+    k_zcols<dsc, true><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
   else k_zcols<double2, true><<<dim3(cdiv(K, Zm.C), 8, g.nb), 256, smem_zcols(Zm.C, g.nz, 0), d.s[2]>>>(Zm);
   XJob Xm{};
   Xm.srcC = g.DMZ; Xm.dstR = g.MV;
@@ -1063,7 +1065,8 @@ cudaError_t launch_diag_split3(const GroupDev& g, const DiagStreams& d, int* nl)
   Z.src_mstride = (long long)NK; Z.dst_mstride = (long long)g.N * g.nz * K;
   Z.src_fstride = 0; Z.dst_fstride = 0;
   Z.src_field[0] = 0; Z.dst_field[0] = 0; Z.dz[0] = 0;
-  if (g.ds) k_zcols<dsc, true><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
+  if (g.ds || g.f32)
+    k_zcols<dsc, true><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
   else k_zcols<double2, true><<<dim3(cdiv(K, Z.C), g.N, g.nb), 256, smem_zcols(Z.C, g.nz, 0), d.s[0]>>>(Z);
   XJob X{};
   X.srcC = g.DZ; X.dstR = g.DV;

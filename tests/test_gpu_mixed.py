@@ -1,6 +1,7 @@
 """Mixed precision (PTT_MIXED): FP32 transforms and products, FP64 state,
-SBDF sums and tau solves, against the FP64 oracle.  Diagnostics: Tr c in
-FP64 throughout; the energy's y transform in FP32, its sums in FP64.
+SBDF sums and tau solves, against the FP64 oracle.  Diagnostics: the Tr c
+and mid-plane transforms in double-single (48 bits), the energy's y
+transform in FP32, every sum in FP64.
 
 Stated errors (per field, max|f - f_oracle| / max|f_oracle| on the unpadded
 grid; the paper's fluid, laminar state + perturbation 1e-3, dt = 1e-3):
