@@ -86,7 +86,8 @@ def parse():
                          "shape of the 2D sweep, three seeds; 'mixedtc' in place of 'mixed' "
                          "selects the tensor-core Chebyshev passes instead of the FP32 FFTs, a "
                          "'_ds' suffix the double-single form (PTT_FP64_DS); "
-                         "3d_NXxNYxNZ[_mixed]: one 3D shape; paper_shapes: the A1-A6 timings) "
+                         "3d_NXxNYxNZ[_mixed]: one 3D shape; sweep[_mixed|_ds]: the 27-run 2D "
+                         "sweep; paper_shapes: the A1-A6 timings) "
                          "and print its line, for profiling; or midplane_stats: mixed vs FP64 "
                          "mid-plane statistics of the 3D workload over --steps steps; or "
                          "longrun_2d / longrun_3d: per-step admissibility records of the 2D "
@@ -458,6 +459,12 @@ def only_workload(args):
         params = [P.make_params(nx=nx, ny=ny, dt=I.DT, precision=prec, **I.PAPER) for _ in range(3)]
         seeds = [0, 1, 2]
         pts = 3 * nx * ny
+    elif name.startswith("sweep"):
+        # the 27-run 2D sweep of the headline in one precision form
+        members = I.sweep_members()
+        params = [P.make_params(nx=nx, ny=ny, dt=I.DT, precision=prec, **I.PAPER) for nx, ny, _ in members]
+        seeds = [s for _, _, s in members]
+        pts = sum(nx * ny for nx, ny, _ in members)
     elif name.startswith("ensemble"):
         fluid = {k: v for k, v in I.PAPER.items() if k != "wi"}
         members = I.ensemble_members()
