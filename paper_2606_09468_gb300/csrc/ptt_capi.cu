@@ -67,7 +67,12 @@ struct HostPlan {
 // Their inverse lines are zero in the middle third [n/3, 2n/3), so a first
 // pass of radix 3 has one zero input (8 FP64 operations per butterfly
 // against 12); used where n has no factor 5.
-HostPlan make_plan(int n, bool three_first = false) {
+// wide: the plans of FP32 groups may take radix-8 passes (fewer passes,
+// each a shared-memory round trip; their transforms are bound by
+// instruction issue, not arithmetic); the FP64 plans keep radices up to 5,
+// whose tangent-form twiddles save FP64 operations, and so do the
+// double-single ones (measured slower with radix 8: register pressure).
+HostPlan make_plan(int n, bool three_first = false, bool wide = false) {
   HostPlan p;
   p.n = n;
   int r = n;
@@ -76,7 +81,11 @@ HostPlan make_plan(int n, bool three_first = false) {
   // butterfly costs the most (44 FP64 operations against 36 untwiddled)
   // radices 13, 11, 7 (unpadded lengths only) first: their butterflies are
   // the costliest, and the first pass takes no twiddles
-  for (int f : {13, 11, 7, 5, 4, 2, 3})
+  for (int f : {13, 11, 7, 5})
+    while (r % f == 0) { p.radix.push_back(f); r /= f; }
+  if (wide)
+    while (r % 8 == 0) { p.radix.push_back(8); r /= 8; }
+  for (int f : {4, 2, 3})
     while (r % f == 0) { p.radix.push_back(f); r /= f; }
   return p;
 }
@@ -494,6 +503,19 @@ void group_sizes(int nx, int ny, int nz, Group& g) {
   g.hp[6] = make_plan(nz);
 }
 
+// The plans of an FP32 group with radix-8 passes: those of the padded
+// lengths (M, Mx, Mz) and of the energy grid (Me), which only FP32 kernels
+// use in such groups.  The unpadded lengths (nx, 2 (ny - 1), nz) keep radices
+// up to 5 (and 7, 11, 13): the FP64 state transforms (set and get state, the
+// x synthesis of Tr c) and the double-single Tr c transforms use them.
+void wide_plans(Group& g) {
+  const int n[7] = {g.d.M, g.d.Mx, g.d.nx, g.d.Pu, g.d.Me, g.d.Mz, g.d.nz};
+  const bool three[7] = {false, true, false, false, false, true, false};
+  const bool widen[7] = {true, true, false, false, true, true, false};
+  for (int i = 0; i < 7; ++i)
+    if (widen[i]) g.hp[i] = make_plan(n[i], three[i], true);
+}
+
 // Carve (or, with base == nullptr, size) all device arrays.
 void carve(std::vector<Group>& groups, Carver& cv) {
   for (Group& g : groups) {
@@ -620,6 +642,7 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
       group_sizes(g.nx, g.ny, g.nz, g);
       g.d.f32 = (pm[i].precision == PTT_MIXED || pm[i].precision == PTT_MIXED_TC) ? 1 : 0;
       g.d.ds = (pm[i].precision == PTT_FP64_DS) ? 1 : 0;
+      if (g.d.f32) wide_plans(g);
       g.d.ymma = (pm[i].precision == PTT_MIXED_TC) ? 1 : 0;   // requested; carve() checks the shape
       groups.push_back(std::move(g));
       it = idx.find(key);

@@ -164,6 +164,53 @@ template <int DIR> struct Bfly<DIR, 5> {
   }
 };
 
+// Radix 8 (the FP32 plans; the FP64 plans keep radices up to 5 and their
+// tangent-form twiddles, the double-single ones too: there the eight
+// double-single values per butterfly cost more registers than the saved
+// pass gains, measured): with w = exp(DIR 2 pi i / 8),
+// a_r = v_r + v_{r+4}, b_r = (v_r - v_{r+4}) w^r (r < 4), the even outputs
+// are the 4-point DFT of a and the odd ones that of b:
+//   y_{2k} = sum_r a_r w^{2rk},  y_{2k+1} = sum_r b_r w^{2rk}.
+template <int DIR> struct Bfly<DIR, 8> {
+  template <typename C2>
+  static __device__ __forceinline__ void run(C2* v) {
+    using T = typename RealOf<C2>::T;
+    const T h = (T)0.70710678118654752440;   // cos(pi/4)
+    C2 a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      a[r] = cadd(v[r], v[r + 4]);
+      b[r] = csub(v[r], v[r + 4]);
+    }
+    // w = (1 + DIR i)/sqrt 2, w^2 = DIR i, w^3 = (-1 + DIR i)/sqrt 2
+    {
+      const C2 ib1 = mul_i(b[1]), ib3 = mul_i(b[3]);
+      if (DIR > 0) {
+        b[1] = cscl(cadd(b[1], ib1), h);
+        b[2] = mul_i(b[2]);
+        b[3] = cscl(csub(ib3, b[3]), h);
+      } else {
+        b[1] = cscl(csub(b[1], ib1), h);
+        C2 t;
+        t.x = b[2].y;
+        t.y = -b[2].x;
+        b[2] = t;
+        const C2 s3 = cadd(b[3], ib3);
+        t.x = -s3.x;
+        t.y = -s3.y;
+        b[3] = cscl(t, h);
+      }
+    }
+    Bfly<DIR, 4>::run(a);
+    Bfly<DIR, 4>::run(b);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = a[k];
+      v[2 * k + 1] = b[k];
+    }
+  }
+};
+
 // Odd prime radices 7, 11, 13 (the unpadded lengths nx, 2 (ny - 1) and nz
 // may carry one such factor).  With H = (R - 1)/2, t_k = v_k + v_{R-k},
 // d_k = v_k - v_{R-k} (k = 1..H) and w = exp(DIR 2 pi i / R):
@@ -489,6 +536,11 @@ __device__ C2* fft_lines(C2* a, C2* b, int nl, int ls, const FftPlan& pl, bool z
       case 3: fft_pass<DIR, 3>(src, dst, nl, ls, c, tw); break;
       case 4: fft_pass<DIR, 4>(src, dst, nl, ls, c, tw); break;
       case 5: fft_pass<DIR, 5>(src, dst, nl, ls, c, tw); break;
+      case 8:   // plans of FP32 groups only (see wide_plans); compiled for
+                // FP32 alone, so the FP64 and double-single kernels keep
+                // their register budgets
+        if constexpr (std::is_same<C2, float2>::value) fft_pass<DIR, 8>(src, dst, nl, ls, c, tw);
+        break;
       default:
         if constexpr (BIG) {
           if (R == 7) fft_pass<DIR, 7>(src, dst, nl, ls, c, tw);
