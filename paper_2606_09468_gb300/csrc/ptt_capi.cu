@@ -443,6 +443,7 @@ struct Group {
   std::vector<int> members;  // global member ids
   GroupDev d{};
   HostPlan hp[7];            // M, Mx, nx, Pu, Me, Mz, nz
+  HostPlan hpn;              // M with radices up to 5 (mixed groups: the mean column)
 };
 
 int check_params(const ptt_params& p) {
@@ -567,6 +568,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
         d.V3 = cv.take<double2>((size_t)nb * 9 * yp);
       }
     }
+    d.Ym = d.f32 ? cv.take<double2>((size_t)nb * (d3 ? 17 : 9) * rows) : nullptr;
+    d.Zm = d.f32 ? cv.take<double2>((size_t)nb * nf * rows) : nullptr;
     d.NR = cv.take<double2>((size_t)nb * nf * NK);
     d.Rb = cv.take<double2>((size_t)nb * 4 * NK);
     d.SS = d3 ? cv.take<double2>((size_t)nb * spec3_scratch_columns() * NK) : nullptr;
@@ -609,7 +612,8 @@ void carve(std::vector<Group>& groups, Carver& cv) {
       pls[i]->twf = (d.f32 && (i < 2 || i == 4 || i == 5)) ? cv.take<float2>((size_t)g.hp[i].n) : nullptr;
       // double-single tables: every length of a double-single group; the
       // unpadded y and z lengths of a mixed group (its Tr c transforms)
-      pls[i]->twd = (d.ds || (d.f32 && (i == 3 || i == 6))) ? cv.take<float4>((size_t)g.hp[i].n) : nullptr;
+      pls[i]->twd = (d.ds || (d.f32 && (i == 0 || i == 3 || i == 6))) ? cv.take<float4>((size_t)g.hp[i].n)
+                                                                   : nullptr;
       int nrec = 0, ndbl = 0;
       tangent_offsets(g.hp[i], pls[i]->toff, pls[i]->tto, &nrec, &ndbl);
       pls[i]->tt = cv.take<double>((size_t)ndbl);
@@ -621,8 +625,15 @@ void carve(std::vector<Group>& groups, Carver& cv) {
     d.tw4Pif = d.f32 ? cv.take<float2>((size_t)d.M) : nullptr;
     d.tw4E = cv.take<double2>((size_t)d.Me);
     d.tw4Ef = d.f32 ? cv.take<float2>((size_t)d.Me) : nullptr;
-    d.tw4Pd = d.ds ? cv.take<float4>((size_t)d.M) : nullptr;
-    d.tw4Pid = d.ds ? cv.take<float4>((size_t)d.M) : nullptr;
+    d.tw4Pd = (d.ds || d.f32) ? cv.take<float4>((size_t)d.M) : nullptr;
+    d.tw4Pid = (d.ds || d.f32) ? cv.take<float4>((size_t)d.M) : nullptr;
+    // mixed groups: the narrow plan of M shares plP's tables
+    d.plPn = d.plP;
+    if (d.f32) {
+      d.plPn.nst = (int)g.hpn.radix.size();
+      for (int s = 0; s < d.plPn.nst; ++s) d.plPn.radix[s] = g.hpn.radix[s];
+      plan_pass_consts(d.plPn);
+    }
     d.tw4Ed = d.ds ? cv.take<float4>((size_t)d.Me) : nullptr;
   }
 }
@@ -642,7 +653,7 @@ std::vector<Group> make_groups(const ptt_params* pm, int nmem) {
       group_sizes(g.nx, g.ny, g.nz, g);
       g.d.f32 = (pm[i].precision == PTT_MIXED || pm[i].precision == PTT_MIXED_TC) ? 1 : 0;
       g.d.ds = (pm[i].precision == PTT_FP64_DS) ? 1 : 0;
-      if (g.d.f32) wide_plans(g);
+      if (g.d.f32) { g.hpn = g.hp[0]; wide_plans(g); }
       g.d.ymma = (pm[i].precision == PTT_MIXED_TC) ? 1 : 0;   // requested; carve() checks the shape
       groups.push_back(std::move(g));
       it = idx.find(key);

@@ -103,6 +103,31 @@ template <> __device__ __forceinline__ float2 cvt2<float2>(dsc v) {
   return make_float2(__fadd_rn(v.x.h, v.x.l), __fadd_rn(v.y.h, v.y.l));
 }
 
+// ------------------------------------------- mean / fluctuation products
+// The mixed form's products split every field on the padded grid into its
+// mean over the periodic directions, a(y), and the fluctuation a'.  The
+// products' mean part (a b with both means) is the same at every point of a
+// row and is formed once per row in FP64; at each point only the
+// fluctuation part a b' + a' b + a' b' is formed, in FP32 with the means
+// rounded to FP32 as multipliers.  The FP32 rounding then scales with the
+// fluctuations, not with the O(10^4) stretch components of the base state.
+// mfl carries (mean as FP32 multiplier, fluctuation) through the same
+// product code as the plain types; only its fluctuation part is used.
+struct mfl {
+  float m, f;
+  mfl() = default;
+  __host__ __device__ constexpr mfl(float m_, float f_) : m(m_), f(f_) {}
+  __host__ __device__ constexpr mfl(int v) : m((float)v), f(0.f) {}        // a constant
+  __host__ __device__ explicit constexpr mfl(double v) : m((float)v), f(0.f) {}
+};
+__device__ __forceinline__ mfl operator+(mfl a, mfl b) { return mfl(a.m + b.m, a.f + b.f); }
+__device__ __forceinline__ mfl operator-(mfl a, mfl b) { return mfl(a.m - b.m, a.f - b.f); }
+__device__ __forceinline__ mfl operator-(mfl a) { return mfl(-a.m, -a.f); }
+__device__ __forceinline__ mfl operator*(mfl a, mfl b) {
+  return mfl(a.m * b.m, fmaf(a.m, b.f, fmaf(a.f, b.m, a.f * b.f)));
+}
+__device__ __forceinline__ mfl& operator+=(mfl& a, mfl b) { a = a + b; return a; }
+
 // ------------------------------------------------------------ radix DFTs
 // DIR = -1: exp(-2 pi i jk/R) (forward); DIR = +1: exp(+2 pi i jk/R).
 template <int DIR, int R> struct Bfly;

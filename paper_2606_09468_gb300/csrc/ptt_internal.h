@@ -101,6 +101,14 @@ struct GroupDev {
   double2* DZ;       // 3D: Tr c after z synthesis [nb][N][nz][K]; state staging [9][N][nz][K]
   double2* DMZ;      // 3D: mid-plane quantities after z synthesis [nb][8][nz][K]
   double* MV;        // 3D: mid-plane values [nb][8][nz][nx]
+  // mixed groups, mean/fluctuation split of the products: the mean Fourier
+  // column (kx = 0, and kz = 0 in 3D) of the inverse y pass on the padded
+  // Gauss grid, in FP64 ([nb][9][M] in 2D, [nb][17][M] in 3D; the FP32
+  // arrays then carry the fluctuations only), and the mean column of the
+  // explicit terms on that grid ([nb][5][M], [nb][9][M]); complex like the
+  // other columns of the y passes (their imaginary parts are zero)
+  double2* Ym;
+  double2* Zm;
   double2* NR;       // [nb][5][K][N]  explicit nonlinear terms, spectral
   double2* Rb;       // [nb][4][K][N]  H_x, H_y of ptt_explicit_rhs
   double2* SS;       // 3D: [nb][columns][KZ][N]  per-mode scratch of the spectral stage
@@ -143,6 +151,9 @@ struct GroupDev {
   const float4* tw4Ed;
   FftPlan plP, plMx, plNx, plPu, plPe;   // lengths M, Mx, nx, 2(N-1), Me
   FftPlan plMz, plNz;                    // 3D: lengths Mz, nz
+  FftPlan plPn;      // mixed groups: length M with radices up to 5 (the
+                     // double-single passes of the mean column; plP may
+                     // hold radix-8 passes there)
 };
 
 constexpr int kPart = 48;  // values per diagnostics tile

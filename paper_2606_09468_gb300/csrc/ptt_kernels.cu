@@ -45,9 +45,33 @@ template <> __device__ __forceinline__ double2* zp_ptr<double2>(const GroupDev& 
 template <> __device__ __forceinline__ float2* zp_ptr<float2>(const GroupDev& g) { return g.Zpf; }
 template <> __device__ __forceinline__ dsc* zp_ptr<dsc>(const GroupDev& g) { return reinterpret_cast<dsc*>(g.Zp); }
 
+// The products of Eqs. 1-2 at one point of the padded grid, from the 14
+// physical fields q = (u, v, du/dy, du/dx, dv/dx, c_xx, c_xy, c_yy, dc_xx/dy,
+// dc_xy/dy, dc_yy/dy, dc_xx/dx, dc_xy/dx, dc_yy/dx) to (N_cxx, N_cxy, N_cyy,
+// N_u, N_v): L_ij = du_i/dx_j (L_yy = -du/dx by continuity), relaxation
+// factor 1 + eps Tr(c - I) with c_zz = 1.
+template <typename T>
+__device__ __forceinline__ void products2d(const T (&q)[14], T eps, T iwi, T (&o)[5]) {
+  const T u = q[0], v = q[1], uy = q[2], ux = q[3], vx = q[4], cxx = q[5];
+  const T cxy = q[6], cyy = q[7], cxx_y = q[8], cxy_y = q[9], cyy_y = q[10];
+  const T cxx_x = q[11], cxy_x = q[12], cyy_x = q[13];
+  const T rw = ((T)1 + eps * (cxx + cyy - (T)2)) * iwi;
+  o[0] = -(u * cxx_x + v * cxx_y) + (T)2 * (ux * cxx + uy * cxy) - (cxx - (T)1) * rw;
+  o[1] = -(u * cxy_x + v * cxy_y) + uy * cyy + vx * cxx - cxy * rw;
+  o[2] = -(u * cyy_x + v * cyy_y) + (T)2 * (vx * cxy - ux * cyy) - (cyy - (T)1) * rw;
+  // Eq. 2 advection
+  o[3] = -(u * ux + v * uy);
+  o[4] = -(u * vx - v * ux);
+}
+
 // C2 = double2: the FP64 path; C2 = float2: the mixed path (FP32 transforms
 // and products, FP64 state and solves); C2 = dsc: the double-single path
 // (FP64-accurate transforms and products on the FP32 pipe, PTT_FP64_DS).
+// Mixed groups split the products into mean and fluctuation parts (mfl):
+// the FP32 lines carry the fluctuations (their mean mode kk = 0 left out),
+// the row's means come in FP64 from g.Ym, the mean products are formed once
+// per row in FP64, and the mean column of the explicit terms goes to g.Zm
+// in FP64 (the FP32 output's mean mode is left zero).
 template <typename C2>
 __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   using T = typename RealOf<C2>::T;
@@ -62,6 +86,19 @@ __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   const C2* Y = yp_ptr<C2>(g) + (size_t)b * 9 * rows * K + (size_t)j * K;
   const T kfac = as_prec<T>(pr.kx1, pr.kx1f);
   const int tid = threadIdx.x, nt = blockDim.x;
+  constexpr bool kSplit = std::is_same<C2, float2>::value;
+  __shared__ float s_mq[14];    // the row's means as FP32 multipliers (split)
+  __shared__ double s_nb[5];    // the row's mean products (split)
+  if constexpr (kSplit) {
+    const double2* ym = g.Ym + (size_t)b * 9 * rows + j;
+    if (tid < 14) s_mq[tid] = c_xik[tid] ? 0.f : (float)ym[(size_t)c_xsrc[tid] * rows].x;
+    if (tid == 32) {   // another warp: the mean products, in FP64
+      double q[14], o[5];
+      for (int i = 0; i < 14; ++i) q[i] = c_xik[i] ? 0.0 : ym[(size_t)c_xsrc[i] * rows].x;
+      products2d<double>(q, pr.eps, pr.inv_wi, o);
+      for (int i = 0; i < 5; ++i) s_nb[i] = o[i];
+    }
+  }
   // the padded middle K <= k <= Mx - K of every line is zero
   {
     const int nmid = Mx - 2 * K + 1;
@@ -96,6 +133,7 @@ __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
         const int l = (int)fdiv((unsigned)it, dK), kk = it - l * K;
         C2 f = F[u], gg = G[u];
         if (kk == 0) { f.y = 0; gg.y = 0; }
+        if (kSplit && kk == 0) { f.x = 0; gg.x = 0; }   // the mean is in g.Ym
         const T km = kfac * kk;
         if (c_xik[2 * l]) f = cscl(mul_i(f), km);
         if (c_xik[2 * l + 1]) gg = cscl(mul_i(gg), km);
@@ -111,24 +149,32 @@ __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
   C2* oth = (res == A) ? B : A;
   const T eps = as_prec<T>(pr.eps, pr.epsf), iwi = as_prec<T>(pr.inv_wi, pr.inv_wif);
   for (int x = tid; x < Mx; x += nt) {
-    const C2 h0 = res[x], h1 = res[Mx + x], h2 = res[2 * Mx + x], h3 = res[3 * Mx + x];
-    const C2 h4 = res[4 * Mx + x], h5 = res[5 * Mx + x], h6 = res[6 * Mx + x];
-    const T u = h0.x, v = h0.y, uy = h1.x, ux = h1.y, vx = h2.x, cxx = h2.y;
-    const T cxy = h3.x, cyy = h3.y, cxx_y = h4.x, cxy_y = h4.y, cyy_y = h5.x;
-    const T cxx_x = h5.y, cxy_x = h6.x, cyy_x = h6.y;
-    // Eq. 1: L_ij = du_i/dx_j (L_yy = -ux by continuity); relaxation factor
-    // f = 1 + eps Tr(c - I) with c_zz = 1.
-    const T rw = ((T)1 + eps * (cxx + cyy - (T)2)) * iwi;
-    const T ncxx = -(u * cxx_x + v * cxx_y) + (T)2 * (ux * cxx + uy * cxy) - (cxx - (T)1) * rw;
-    const T ncxy = -(u * cxy_x + v * cxy_y) + uy * cyy + vx * cxx - cxy * rw;
-    const T ncyy = -(u * cyy_x + v * cyy_y) + (T)2 * (vx * cxy - ux * cyy) - (cyy - (T)1) * rw;
-    // Eq. 2 advection
-    const T nu_ = -(u * ux + v * uy);
-    const T nv_ = -(u * vx - v * ux);
+    T o[5];
+    if constexpr (kSplit) {
+      mfl q[14], om[5];
+#pragma unroll
+      for (int l = 0; l < 7; ++l) {
+        const C2 h = res[l * Mx + x];
+        q[2 * l] = mfl(s_mq[2 * l], h.x);
+        q[2 * l + 1] = mfl(s_mq[2 * l + 1], h.y);
+      }
+      products2d<mfl>(q, mfl(pr.epsf, 0.f), mfl(pr.inv_wif, 0.f), om);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) o[i] = om[i].f;
+    } else {
+      T q[14];
+#pragma unroll
+      for (int l = 0; l < 7; ++l) {
+        const C2 h = res[l * Mx + x];
+        q[2 * l] = h.x;
+        q[2 * l + 1] = h.y;
+      }
+      products2d<T>(q, eps, iwi, o);
+    }
     C2 o0, o1, o2;
-    o0.x = ncxx; o0.y = ncxy;
-    o1.x = ncyy; o1.y = nu_;
-    o2.x = nv_; o2.y = 0;
+    o0.x = o[0]; o0.y = o[1];
+    o1.x = o[2]; o1.y = o[3];
+    o2.x = o[4]; o2.y = 0;
     oth[x] = o0;
     oth[Mx + x] = o1;
     oth[2 * Mx + x] = o2;
@@ -141,11 +187,20 @@ __device__ __forceinline__ void xfused_block(const GroupDev& g, Blk bk) {
     const int l = (int)fdiv((unsigned)i, fast_div((unsigned)K)), k = i - l * K;
     const C2 hk = r2[l * Mx + k];
     const C2 hm = cconj(r2[l * Mx + (k == 0 ? 0 : Mx - k)]);
-    const C2 F = cscl(cadd(hk, hm), (T)0.5 * inv);
+    C2 F = cscl(cadd(hk, hm), (T)0.5 * inv);
     const C2 d = csub(hk, hm);
     C2 G;
     G.x = (T)0.5 * inv * d.y;
     G.y = (T)-0.5 * inv * d.x;
+    if constexpr (kSplit) {
+      if (k == 0) {   // mean column: the mean products plus the fluctuations' mean, FP64
+        double2* zm = g.Zm + (size_t)b * 5 * rows + j;
+        zm[(size_t)(2 * l) * rows] = make_double2(s_nb[2 * l] + (double)F.x, 0.0);
+        if (l < 2) zm[(size_t)(2 * l + 1) * rows] = make_double2(s_nb[2 * l + 1] + (double)G.x, 0.0);
+        F = zero2<C2>();
+        G = zero2<C2>();
+      }
+    }
     Z[(size_t)(2 * l) * rows * K + k] = F;
     if (l < 2) Z[(size_t)(2 * l + 1) * rows * K + k] = G;
   }
@@ -934,6 +989,26 @@ static YJob yjob_forward(const GroupDev& g) {   // the 5 explicit fields to coef
   for (int i = 0; i < 5; ++i) { F.src_field[i] = i; F.dst_field[i] = i; F.deriv[i] = 0; }
   return F;
 }
+// Mixed groups: the mean column (m = 0) of the inverse and forward y passes
+// in double-single, FP64 in and out (g.Ym, g.Zm; see xfused_block).  One
+// column per block; the narrow plan plPn (the double-single passes take
+// radices up to 5).
+static YJob yjob_mean_inverse(const GroupDev& g) {
+  YJob J = yjob_inverse(g);
+  J.K = 1; J.C = 1; J.pl = g.plPn;
+  J.dst = g.Ym; J.dst_f32 = 0;
+  J.dst_mstride = 9LL * g.M; J.dst_fstride = g.M;
+  J.vm = 1; J.vj = 1;
+  return J;
+}
+static YJob yjob_mean_forward(const GroupDev& g) {
+  YJob F = yjob_forward(g);
+  F.K = 1; F.C = 1; F.pl = g.plPn;
+  F.src = g.Zm; F.src_f32 = 0;
+  F.src_mstride = 5LL * g.M; F.src_fstride = g.M;
+  F.vm = 1; F.vj = 1;
+  return F;
+}
 static YJob yjob_energy(const GroupDev& g) {    // u, v on the Me Gauss points
   const size_t NK = (size_t)g.N * g.K;
   YJob J = make_yjob(g, true, g.Me, g.CcolE, g.plPe, g.tw4E);
@@ -976,14 +1051,18 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
         cudaError_t e = launch_cheb_mma(g, true, st, g.nsm);
         if (e) return e;
         n = 1;
-        break;
+      } else {
+        const YJob J = yjob_inverse(g);
+        const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
+        if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
+        else if (g.ds) k_ycols<dsc><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
+        else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
+        n = 1;
       }
-      const YJob J = yjob_inverse(g);
-      const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
-      if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
-      else if (g.ds) k_ycols<dsc><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
-      else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 9, g.nb), 256, sm, st>>>(J);
-      n = 1;
+      if (g.f32) {   // the mean column in double-single
+        k_ycols<dsc><<<dim3(1, 9, g.nb), 256, smem_ycols(1, g.M, 0), st>>>(yjob_mean_inverse(g));
+        ++n;
+      }
       break;
     }
     case 1:
@@ -997,14 +1076,18 @@ cudaError_t launch_stage(const GroupDev& g, int stage, cudaStream_t st, int* nl)
         cudaError_t e = launch_cheb_mma(g, false, st, g.nsm);
         if (e) return e;
         n = 1;
-        break;
+      } else {
+        const YJob F = yjob_forward(g);
+        const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
+        if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
+        else if (g.ds) k_ycols<dsc><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
+        else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
+        n = 1;
       }
-      const YJob F = yjob_forward(g);
-      const size_t sm = smem_ycols(g.Ccol, g.M, g.f32);
-      if (g.f32) k_ycols<float2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
-      else if (g.ds) k_ycols<dsc><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
-      else k_ycols<double2><<<dim3(cdiv(g.K, g.Ccol), 5, g.nb), 256, sm, st>>>(F);
-      n = 1;
+      if (g.f32) {   // the mean column in double-single, over the FP32 pass's zeros
+        k_ycols<dsc><<<dim3(1, 5, g.nb), 256, smem_ycols(1, g.M, 0), st>>>(yjob_mean_forward(g));
+        ++n;
+      }
       break;
     }
     case 3:
@@ -1090,11 +1173,13 @@ cudaError_t launch_diag_split(const GroupDev& g, const DiagStreams& d, int* nl) 
 struct Multi2DPlan {
   int ng = 0, f32 = 0, ds = 0;
   const GroupDev* dg = nullptr;
-  const YJob* dyj = nullptr;     // [4][ng]: inverse, forward, energy, Tr c
+  // [6][ng]: inverse, forward, energy, Tr c, mean-column inverse and forward
+  // (mixed groups)
+  const YJob* dyj = nullptr;
   const XJob* dxj = nullptr;     // [ng]: Tr c x synthesis
-  MultiMap inv, fwd, xf, spec[3], ye, yt, xr, mid, part, cnt, fin;
+  MultiMap inv, fwd, xf, spec[3], ye, yt, xr, mid, part, cnt, fin, ymi, ymf;
   size_t sm_inv = 0, sm_fwd = 0, sm_xf = 0, sm_spec[3] = {0, 0, 0}, sm_ye = 0, sm_yt = 0, sm_xr = 0,
-         sm_fin = 0;
+         sm_fin = 0, sm_ym = 0;
 };
 
 int multi2d_max_groups() { return kMaxGroupsMulti; }
@@ -1102,7 +1187,7 @@ int multi2d_max_groups() { return kMaxGroupsMulti; }
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t multi2d_bytes(int ng) {
-  return align256((size_t)ng * sizeof(GroupDev)) + align256((size_t)4 * ng * sizeof(YJob)) +
+  return align256((size_t)ng * sizeof(GroupDev)) + align256((size_t)6 * ng * sizeof(YJob)) +
          align256((size_t)ng * sizeof(XJob));
 }
 
@@ -1126,15 +1211,15 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
   p->f32 = groups[0]->f32;
   p->ds = groups[0]->ds;
   std::vector<GroupDev> hg(ng);
-  std::vector<YJob> hy(4 * (size_t)ng);
+  std::vector<YJob> hy(6 * (size_t)ng);
   std::vector<XJob> hx(ng);
   MultiMap* maps[] = {&p->inv, &p->fwd, &p->xf, &p->spec[0], &p->spec[1], &p->spec[2], &p->ye,
-                      &p->yt, &p->xr, &p->mid, &p->part, &p->cnt, &p->fin};
+                      &p->yt, &p->xr, &p->mid, &p->part, &p->cnt, &p->fin, &p->ymi, &p->ymf};
   for (MultiMap* m : maps) { m->ng = 0; m->start[0] = 0; }
   // Each launch lists the groups with the costliest blocks first, so that
   // the blocks dispatched last, which set the launch's tail, are short ones.
   struct Ent { double cost; int q; unsigned gx, gy, gz; };
-  std::vector<Ent> e_inv, e_fwd, e_xf, e_spec[3], e_ye, e_yt, e_xr, e_mid, e_part, e_fin;
+  std::vector<Ent> e_inv, e_fwd, e_xf, e_spec[3], e_ye, e_yt, e_xr, e_mid, e_part, e_fin, e_ymi, e_ymf;
   for (int q = 0; q < ng; ++q) {
     const GroupDev& g = *groups[q];
     if (g.nz != 1 || g.f32 != p->f32 || g.ds != p->ds || g.ymma) {
@@ -1147,6 +1232,13 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
     hy[ng + q] = yjob_forward(g);
     hy[2 * (size_t)ng + q] = yjob_energy(g);
     hy[3 * (size_t)ng + q] = yjob_trc(g);
+    if (g.f32) {
+      hy[4 * (size_t)ng + q] = yjob_mean_inverse(g);
+      hy[5 * (size_t)ng + q] = yjob_mean_forward(g);
+      e_ymi.push_back({(double)g.M, q, 1, 9, (unsigned)g.nb});
+      e_ymf.push_back({(double)g.M, q, 1, 5, (unsigned)g.nb});
+      p->sm_ym = std::max(p->sm_ym, smem_ycols(1, g.M, 0));
+    }
     hx[q] = xjob_trc(g);
     e_inv.push_back({(double)g.Ccol * g.M, q, cdiv(g.K, g.Ccol), 9, (unsigned)g.nb});
     e_fwd.push_back({(double)g.Ccol * g.M, q, cdiv(g.K, g.Ccol), 5, (unsigned)g.nb});
@@ -1185,11 +1277,13 @@ Multi2DPlan* multi2d_create(const std::vector<const GroupDev*>& groups, void* de
   std::vector<Ent> e_cnt = e_part;
   fill(p->cnt, e_cnt);
   fill(p->fin, e_fin);
+  fill(p->ymi, e_ymi);
+  fill(p->ymf, e_ymf);
   char* b = static_cast<char*>(dev);
   p->dg = reinterpret_cast<const GroupDev*>(b);
   p->dyj = reinterpret_cast<const YJob*>(b + align256((size_t)ng * sizeof(GroupDev)));
   p->dxj = reinterpret_cast<const XJob*>(b + align256((size_t)ng * sizeof(GroupDev)) +
-                                          align256((size_t)4 * ng * sizeof(YJob)));
+                                          align256((size_t)6 * ng * sizeof(YJob)));
   cudaError_t e = cudaMemcpyAsync((void*)p->dg, hg.data(), hg.size() * sizeof(GroupDev),
                                   cudaMemcpyHostToDevice, st);
   if (!e) e = cudaMemcpyAsync((void*)p->dyj, hy.data(), hy.size() * sizeof(YJob), cudaMemcpyHostToDevice, st);
@@ -1212,6 +1306,10 @@ cudaError_t launch_stage_multi(const Multi2DPlan* p, int stage, cudaStream_t st,
       else if (p->ds) k_ycols_multi<dsc><<<mm_blocks(p->inv), 256, p->sm_inv, st>>>(p->dyj, p->inv);
       else k_ycols_multi<double2><<<mm_blocks(p->inv), 256, p->sm_inv, st>>>(p->dyj, p->inv);
       n = 1;
+      if (p->ymi.ng) {   // mixed groups: the mean columns in double-single
+        k_ycols_multi<dsc><<<mm_blocks(p->ymi), 256, p->sm_ym, st>>>(p->dyj + 4 * ng, p->ymi);
+        ++n;
+      }
       break;
     case 1:
       if (p->f32) k_xfused_multi<float2><<<mm_blocks(p->xf), 512, p->sm_xf, st>>>(p->dg, p->xf);
@@ -1224,6 +1322,10 @@ cudaError_t launch_stage_multi(const Multi2DPlan* p, int stage, cudaStream_t st,
       else if (p->ds) k_ycols_multi<dsc><<<mm_blocks(p->fwd), 256, p->sm_fwd, st>>>(p->dyj + ng, p->fwd);
       else k_ycols_multi<double2><<<mm_blocks(p->fwd), 256, p->sm_fwd, st>>>(p->dyj + ng, p->fwd);
       n = 1;
+      if (p->ymf.ng) {
+        k_ycols_multi<dsc><<<mm_blocks(p->ymf), 256, p->sm_ym, st>>>(p->dyj + 5 * ng, p->ymf);
+        ++n;
+      }
       break;
     case 3:
       if (p->spec[0].ng) { k_spec_multi<2><<<mm_blocks(p->spec[0]), 256, p->sm_spec[0], st>>>(p->dg, p->spec[0], 0); ++n; }

@@ -47,6 +47,12 @@ struct ZJob {
   const int* status;
   const MemberPrm* prm;
   FftPlan pl;         // length Mz
+  // mixed groups' step passes (mean/fluctuation split, see k_xfused3):
+  // mean = 1, inverse: the kx = 0 line leaves its kz = 0 (mean) mode out;
+  // mean = 2, forward: the kx = 0 line's mean mode is added in FP64 to
+  // zm[member][dst field][row] and left zero in dst
+  int mean;
+  double2* zm;
 };
 
 // BIG: unpadded z length nz (radices 7, 11, 13 possible); the padded length
@@ -77,9 +83,10 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
     const int dz = J.dz[f];
     for (int i = tid; i < C * Mz; i += nt) A[i] = zero2<CT>();
     __syncthreads();
+    const bool skip0 = (J.mean == 1 && m0 == 0);
     for (int i = tid; i < C * nz; i += nt) {
       const int c = (int)fdiv((unsigned)i, fast_div((unsigned)nz)), mz = i - c * nz;
-      if (c < nc && mz != hz) {
+      if (c < nc && mz != hz && !(skip0 && c == 0 && mz == 0)) {
         const int s = (mz < hz) ? mz : mz - nz;
         CT v = ld2<CT>(src, (long long)(m0 + c) * nz + mz, J.src_f32);
         if (dz) v = cscl(mul_i(v), kfac * (T)s);
@@ -113,6 +120,12 @@ __global__ void __launch_bounds__(256) k_zcols(ZJob J) {
           const int s = (mz < hz) ? mz : mz - nz;
           v = cscl(res[c * Mz + (s >= 0 ? s : s + Mz)], inv);
         }
+        if constexpr (std::is_same<CT, float2>::value) {
+          if (J.mean == 2 && m0 + c == 0 && mz == 0) {
+            J.zm[((size_t)b * 9 + J.dst_field[f]) * J.rows + j].x += (double)v.x;
+            v = zero2<CT>();
+          }
+        }
         st2<CT>(dst, (long long)(m0 + c) * nz + mz, J.dst_f32, v);
       }
     }
@@ -136,6 +149,37 @@ template <> __device__ __forceinline__ double2* w3_ptr<double2>(const GroupDev& 
 template <> __device__ __forceinline__ float2* w3_ptr<float2>(const GroupDev& g) { return g.W3f; }
 template <> __device__ __forceinline__ dsc* w3_ptr<dsc>(const GroupDev& g) { return reinterpret_cast<dsc*>(g.W3); }
 
+// The products of Eqs. 1-2 at one point from the 35 physical fields q (Z3
+// order, then the x-derivatives of fields 0-8 at 26-34; q[35] unused) to
+// N_cxx, N_cxy, N_cxz, N_cyy, N_cyz, N_czz, N_u, N_v, N_w.
+template <typename T>
+__device__ __forceinline__ void products3d(const T (&q)[36], T eps, T iwi, T (&out)[9]) {
+  const T u = q[0], v = q[1], w = q[2];
+  const T C[3][3] = {{q[3], q[4], q[5]}, {q[4], q[6], q[7]}, {q[5], q[7], q[8]}};
+  const T ux = q[26], vx = q[27], wx = q[28];
+  const T uy = q[9], wy = q[10];
+  const T uz = q[17], vz = q[18], wz = q[19];
+  // L_ij = d u_i / d x_j, L_yy = -ux - wz (Eq. 3)
+  const T L[3][3] = {{ux, uy, uz}, {vx, -ux - wz, vz}, {wx, wy, wz}};
+  const T rw = ((T)1 + eps * (q[3] + q[6] + q[8] - (T)3)) * iwi;
+  // components in storage order xx, xy, xz, yy, yz, zz; gradients in q
+  const int ci[6] = {0, 0, 0, 1, 1, 2}, cj2[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int i = ci[c], jj = cj2[c];
+    const T adv = u * q[29 + c] + v * q[11 + c] + w * q[20 + c];
+    T st = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) st += L[i][k] * C[k][jj] + C[i][k] * L[jj][k];
+    const T dlt = (i == jj) ? (T)1 : (T)0;
+    out[c] = -adv + st - (C[i][jj] - dlt) * rw;
+  }
+  // Eq. 2 advection: -(u . grad) u_i = -sum_k u_k L_ik
+  const T uu[3] = {u, v, w};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[6 + i] = -(uu[0] * L[i][0] + uu[1] * L[i][1] + uu[2] * L[i][2]);
+}
+
 // IP: the lines stay in one buffer and every FFT pass works in place
 // (fft_lines_inplace; kIpThreads threads), for the FP64 lines too long for
 // two buffers in shared memory (Mx up to kIpMaxN).
@@ -154,6 +198,25 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
   const C2* Z = z3_ptr<C2>(g) + (size_t)b * 26 * plane + (size_t)row * K;
   const T kfac = as_prec<T>(pr.kx1, pr.kx1f);
   const int tid = threadIdx.x, nt = blockDim.x;
+  // mixed groups: mean/fluctuation split of the products (see xfused_block
+  // in the 2D kernels): the z pass left the mean mode out of the lines, the
+  // means of the 17 y-pass fields at this row's y come from g.Ym (the z- and
+  // x-derivatives have zero mean), the mean products go to g.Zm (written by
+  // the rows at z = 0; the forward z pass adds the fluctuations' mean)
+  constexpr bool kSplit = std::is_same<C2, float2>::value;
+  __shared__ float s_mq[17];
+  if constexpr (kSplit) {
+    const int jy = row / g.Mz;
+    const double2* ym = g.Ym + (size_t)b * 17 * g.M + jy;
+    if (tid < 17) s_mq[tid] = (float)ym[(size_t)tid * g.M].x;
+    if (tid == 32 && row - jy * g.Mz == 0) {
+      double q[36], o[9];
+      for (int i = 0; i < 36; ++i) q[i] = (i < 17) ? ym[(size_t)i * g.M].x : 0.0;
+      products3d<double>(q, pr.eps, pr.inv_wi, o);
+      double2* zm = g.Zm + (size_t)b * 9 * g.M + jy;
+      for (int i = 0; i < 9; ++i) zm[(size_t)i * g.M] = make_double2(o[i], 0.0);
+    }
+  }
   // the padded middle K <= k <= Mx - K of every line is zero
   {
     const int nmid = Mx - 2 * K + 1;
@@ -216,38 +279,28 @@ __global__ void __launch_bounds__(512) k_xfused3(GroupDev g) {
   }
   const T eps = as_prec<T>(pr.eps, pr.epsf), iwi = as_prec<T>(pr.inv_wi, pr.inv_wif);
   for (int x = tid; x < Mx; x += nt) {
-    T q[36];
-#pragma unroll
-    for (int l = 0; l < 18; ++l) {
-      const C2 h = res[l * Mx + x];
-      q[2 * l] = h.x;
-      q[2 * l + 1] = h.y;
-    }
-    const T u = q[0], v = q[1], w = q[2];
-    const T C[3][3] = {{q[3], q[4], q[5]}, {q[4], q[6], q[7]}, {q[5], q[7], q[8]}};
-    const T ux = q[26], vx = q[27], wx = q[28];
-    const T uy = q[9], wy = q[10];
-    const T uz = q[17], vz = q[18], wz = q[19];
-    // L_ij = d u_i / d x_j, L_yy = -ux - wz (Eq. 3)
-    const T L[3][3] = {{ux, uy, uz}, {vx, -ux - wz, vz}, {wx, wy, wz}};
-    const T rw = ((T)1 + eps * (q[3] + q[6] + q[8] - (T)3)) * iwi;
-    // components in storage order xx, xy, xz, yy, yz, zz; gradients in q
-    const int ci[6] = {0, 0, 0, 1, 1, 2}, cj2[6] = {0, 1, 2, 1, 2, 2};
     T out[9];
+    if constexpr (kSplit) {
+      mfl q[36], om[9];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const int i = ci[c], jj = cj2[c];
-      const T adv = u * q[29 + c] + v * q[11 + c] + w * q[20 + c];
-      T st = 0;
+      for (int l = 0; l < 18; ++l) {
+        const C2 h = res[l * Mx + x];
+        q[2 * l] = mfl(2 * l < 17 ? s_mq[2 * l] : 0.f, h.x);
+        q[2 * l + 1] = mfl(2 * l + 1 < 17 ? s_mq[2 * l + 1] : 0.f, h.y);
+      }
+      products3d<mfl>(q, mfl(pr.epsf, 0.f), mfl(pr.inv_wif, 0.f), om);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) st += L[i][k] * C[k][jj] + C[i][k] * L[jj][k];
-      const T dlt = (i == jj) ? (T)1 : (T)0;
-      out[c] = -adv + st - (C[i][jj] - dlt) * rw;
+      for (int i = 0; i < 9; ++i) out[i] = om[i].f;
+    } else {
+      T q[36];
+#pragma unroll
+      for (int l = 0; l < 18; ++l) {
+        const C2 h = res[l * Mx + x];
+        q[2 * l] = h.x;
+        q[2 * l + 1] = h.y;
+      }
+      products3d<T>(q, eps, iwi, out);
     }
-    // Eq. 2 advection: -(u . grad) u_i = -sum_k u_k L_ik
-    const T uu[3] = {u, v, w};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) out[6 + i] = -(uu[0] * L[i][0] + uu[1] * L[i][1] + uu[2] * L[i][2]);
 #pragma unroll
     for (int l = 0; l < 5; ++l) {
       C2 o;
@@ -907,10 +960,20 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
         k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 17, g.nb), 256, sm, st>>>(J);
       }
       ++n;
+      if (f32) {   // the mean column (kx = kz = 0) in double-single, FP64 out
+        YJob Jm = J;
+        Jm.K = 1; Jm.C = 1; Jm.pl = g.plPn;
+        Jm.dst = g.Ym; Jm.dst_f32 = 0;
+        Jm.dst_mstride = 17LL * M; Jm.dst_fstride = M;
+        Jm.vm = 1; Jm.vj = 1;
+        k_ycols<dsc><<<dim3(1, 17, g.nb), 256, smem_ycols(1, M, 0), st>>>(Jm);
+        ++n;
+      }
       ZJob Z = zjob(g, true, Mz, M, g.plMz);
       Z.C = g.zC;
       Z.src = J.dst; Z.src_f32 = fmt;
       Z.dst = f32 ? (void*)g.Z3f : (void*)g.Z3; Z.dst_f32 = fmt;
+      Z.mean = f32 ? 1 : 0;
       Z.src_mstride = 17 * yplane; Z.dst_mstride = 26 * zplane;
       Z.src_fstride = yplane; Z.dst_fstride = zplane;
       for (int i = 0; i < 26; ++i) {
@@ -940,6 +1003,8 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       Z.C = g.zC;
       Z.src = f32 ? (const void*)g.W3f : (const void*)g.W3; Z.src_f32 = fmt;
       Z.dst = f32 ? (void*)g.V3f : (void*)g.V3; Z.dst_f32 = fmt;
+      Z.mean = f32 ? 2 : 0;
+      Z.zm = g.Zm;
       Z.src_mstride = 9 * zplane; Z.dst_mstride = 9 * yplane;
       Z.src_fstride = zplane; Z.dst_fstride = yplane;
       for (int i = 0; i < 9; ++i) { Z.src_field[i] = i; Z.dst_field[i] = i; Z.dz[i] = 0; }
@@ -965,6 +1030,15 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
         k_ycols<double2><<<dim3(cdiv(KZ, g.Ccol), 9, g.nb), 256, sm, st>>>(F);
       }
       n = 2;
+      if (f32) {   // the mean column in double-single, over the FP32 pass's zeros
+        YJob Fm = F;
+        Fm.K = 1; Fm.C = 1; Fm.pl = g.plPn;
+        Fm.src = g.Zm; Fm.src_f32 = 0;
+        Fm.src_mstride = 9LL * M; Fm.src_fstride = M;
+        Fm.vm = 1; Fm.vj = 1;
+        k_ycols<dsc><<<dim3(1, 9, g.nb), 256, smem_ycols(1, M, 0), st>>>(Fm);
+        ++n;
+      }
       break;
     }
     case 3:

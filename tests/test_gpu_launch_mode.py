@@ -53,7 +53,8 @@ def test_launch_modes_are_bitwise_equal(precision):
         assert np.array_equal(h0[i], h1[i]), i
     # mode 1: stages 0-3 (inverse y, x, forward y, one spectral launch per
     # tau-scan class, counters) and 7 diagnostics launches
-    assert n1 <= 15 < n0, (n0, n1)
+    # mixed groups add the double-single mean-column passes (two launches)
+    assert n1 <= 17 < n0, (n0, n1)
 
 
 def test_full_ensemble_launch_count_and_equality():
@@ -74,7 +75,7 @@ def test_full_ensemble_launch_count_and_equality():
         res.append(([ctx.get_spectral(i).copy() for i in (0, 17, 40, 63)], ctx.launches_per_step()))
         ctx.close()
     assert all(np.array_equal(a, b) for a, b in zip(res[0][0], res[1][0]))
-    assert res[1][1] <= 15 and res[0][1] >= 40 * 10, (res[0][1], res[1][1])
+    assert res[1][1] <= 17 and res[0][1] >= 40 * 10, (res[0][1], res[1][1])
 
 
 def test_launch_mode_eligibility():

@@ -99,3 +99,51 @@ def test_mixed_diagnostics_against_oracle():
     assert abs(d["energy"] - o["energy"]) <= 1e-6 * o["energy"]
     for k in ("mean_trc", "min_trc", "max_trc"):
         assert abs(d[k] - o[k]) <= 1e-7 * abs(o[k]), k
+
+
+def test_mixed_error_scales_with_the_perturbation():
+    """The mean/fluctuation split of the mixed products: the FP32 rounding
+    scales with the fluctuations, not with the O(1e4) base state, so the
+    relative error of v (a pure fluctuation) after a few steps stays of the
+    same size when the perturbation is 100 times smaller.  (Rounding of the
+    whole fields in FP32 would leave an absolute error set by the base state,
+    a relative error 100 times larger.)"""
+    import paper_2606_09468_gb300 as P
+    nx, ny = I.SMALL
+    rel = {}
+    for amp in (1e-3, 1e-5):
+        ctx = _ctx(nx, ny, P.PTT_MIXED)
+        ctx.init_state(0, 0, amp)
+        ora = Channel2D(Params(nx=nx, ny=ny, dt=I.DT, **I.PAPER))
+        ora.init_state(0, amp)
+        ctx.step(5)
+        for _ in range(5):
+            ora.step()
+        assert ctx.synchronize() == 0
+        rel[amp] = _errs(I.abi_to_phys(ctx.get_state(0)), ora.get_physical())
+    print("mixed errors after 5 steps, amplitude 1e-3", rel[1e-3], "amplitude 1e-5", rel[1e-5])
+    assert rel[1e-5][1] <= 10 * max(rel[1e-3][1], 1e-9), (rel[1e-3][1], rel[1e-5][1])
+    assert np.all(rel[1e-5] <= 1e-6), rel[1e-5]
+
+
+def test_mixed_error_scales_with_the_perturbation_3d():
+    """As above in 3D, for the fields that vanish in the base state (v, w,
+    c_xz, c_yz)."""
+    import paper_2606_09468_gb300 as P
+    from oracle import ptt3d as O3
+    nx, ny, nz = 16, 17, 8
+    kw = dict(I.PAPER, lz=5.0, dt=I.DT)
+    rel = {}
+    for amp in (1e-3, 1e-5):
+        ctx = P.Context([P.make_params(nx=nx, ny=ny, nz=nz, precision=P.PTT_MIXED, **kw)])
+        ctx.init_state(0, 4, amp)
+        ora = O3.Channel3D(O3.Params3(nx=nx, ny=ny, nz=nz, **kw))
+        ora.init_state(4, amp)
+        ctx.step(3)
+        for _ in range(3):
+            ora.step()
+        assert ctx.synchronize() == 0
+        rel[amp] = _errs(I.abi_to_phys3(ctx.get_state(0)), ora.get_physical())
+    print("mixed 3D errors after 3 steps, amplitude 1e-3", rel[1e-3], "amplitude 1e-5", rel[1e-5])
+    for f in (1, 2, 5, 7):   # v, w, c_xz, c_yz
+        assert rel[1e-5][f] <= 10 * max(rel[1e-3][f], 1e-9), (f, rel[1e-3][f], rel[1e-5][f])
