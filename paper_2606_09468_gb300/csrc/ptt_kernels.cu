@@ -239,7 +239,9 @@ __global__ void __launch_bounds__(512) k_xfused_multi(const GroupDev* __restrict
 // CH: tau-scan rows per lane (register arrays of the solves; launch_spec
 // picks the smallest of 2, 4, 8 that holds ny).  Two blocks per SM run the
 // stage about 25 % faster than one block at the ~160 registers ptxas picks
-// unbounded.
+// unbounded; CH = 2 and 4 take three (80 registers, a few spilled words,
+// shared memory for three blocks up to ny = 257), CH = 8 two (its register
+// arrays would spill heavily at 80).
 template <int CH>
 __device__ __forceinline__ void spec_block(const GroupDev& g, int mode, Blk bk) {
   const int b = bk.y;
@@ -408,10 +410,13 @@ __device__ __forceinline__ void spec_block(const GroupDev& g, int mode, Blk bk) 
 }
 
 template <int CH>
-__global__ void __launch_bounds__(256, 2) k_spec(GroupDev g, int mode) { spec_block<CH>(g, mode, this_blk()); }
+__global__ void __launch_bounds__(256, (CH <= 4) ? 3 : 2) k_spec(GroupDev g, int mode) {
+  spec_block<CH>(g, mode, this_blk());
+}
 
 template <int CH>
-__global__ void __launch_bounds__(256, 2) k_spec_multi(const GroupDev* __restrict__ gs, MultiMap mm, int mode) {
+__global__ void __launch_bounds__(256, (CH <= 4) ? 3 : 2)
+    k_spec_multi(const GroupDev* __restrict__ gs, MultiMap mm, int mode) {
   Blk bk;
   const int q = multi_locate(mm, bk);
   spec_block<CH>(gs[q], mode, bk);
