@@ -68,10 +68,15 @@ extern "C" {
 
 #define PTT_FP64 0         /* every step of the path in FP64                     */
 #define PTT_MIXED 1        /* FP32 Fourier and Chebyshev transforms (FFTs; the
-                              Chebyshev ones as DCT-II/III) and products; FP64
-                              state, SBDF sums, tau solves and diagnostic sums
-                              (the energy's transform in FP32, the Tr c and
-                              mid-plane transforms in double-single)          */
+                              Chebyshev ones as DCT-II/III) and the products'
+                              fluctuation parts (means and mean products in
+                              FP64, the mean column through double-single y
+                              passes); in 2D the explicit-term history and
+                              its SBDF sum in FP32 (the mean mode's in FP64);
+                              FP64 state and its SBDF sum, tau
+                              solves and diagnostic sums (the energy's
+                              transform in FP32, the Tr c and mid-plane
+                              transforms in double-single)                   */
 #define PTT_MIXED_TC 2     /* as PTT_MIXED, with the Chebyshev transforms as dense
                               contractions on the tensor cores: BF16 slices of a
                               fixed-point split, FP32 accumulation (FP32 FFTs for

@@ -669,6 +669,23 @@ __constant__ double c_sb[4][4] = {{1.0, 0.0, 0.0, 0.0},
                                   {2.0, -1.0, 0.0, 0.0},
                                   {3.0, -3.0, 1.0, 0.0},
                                   {4.0, -6.0, 4.0, -1.0}};
+__constant__ float c_sbf[4][4] = {{1.f, 0.f, 0.f, 0.f},   // the same (exact in FP32)
+                                  {2.f, -1.f, 0.f, 0.f},
+                                  {3.f, -3.f, 1.f, 0.f},
+                                  {4.f, -6.f, 4.f, -1.f}};
+
+// 2D mixed groups keep the explicit-term history and its SBDF sum in FP32
+// for every mode but the mean (the explicit terms carry FP32 accuracy there):
+// each member's FP32 history sits in the first half of its own block of the
+// FP64 history array, the mean mode's FP64 history in the second half (so
+// checkpoints copy the same byte ranges).  FP64 <-> FP32 by integer
+// operations.
+__device__ __forceinline__ float2 f2_trunc(double2 v) {
+  return make_float2(ds_from_double(v.x).h, ds_from_double(v.y).h);
+}
+__device__ __forceinline__ double2 d2_exact(float2 v) {
+  return make_double2(ds_f32_to_f64(v.x), ds_f32_to_f64(v.y));
+}
 
 // ------------------------------------------- warp-cooperative recurrences
 // FP64 runs at a few lanes per clock per SM on this part, so a warp FP64

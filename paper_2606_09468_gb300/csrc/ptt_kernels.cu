@@ -325,9 +325,45 @@ __device__ __forceinline__ void spec_block(const GroupDev& g, int mode, Blk bk) 
     snq[n] = (m == 0) ? shx[n] : csub(cscl(mul_i(sR[n]), -km), cscl(shy[n], km2));
   __syncthreads();
   // history slot and SBDF sums
-  {
+  if (g.f32 && m != 0) {   // mixed groups: the explicit-term history and its sum in FP32
     double2* E = g.Eh + ((size_t)slot * nb + b) * 4 * NK + (size_t)m * N;
-    double2* Nn = g.Nh + ((size_t)slot * nb + b) * 4 * NK + (size_t)m * N;
+    float2* Nf = reinterpret_cast<float2*>(g.Nh + ((size_t)slot * nb + b) * 4 * NK) + (size_t)m * N;
+    const double idt = 1.0 / pr.dt;
+    for (int i = tid; i < N; i += nt) {
+      const double2 x[4] = {sc0[i], sc1[i], sc2[i], sq[i]};
+      const double2 nn[4] = {NR[i], NR[NK + i], NR[2 * NK + i], snq[i]};
+      double2 acc[4];
+      float2 an[4];
+      for (int s = 0; s < 4; ++s) {
+        const float2 nf = f2_trunc(nn[s]);
+        E[s * NK + i] = x[s];
+        Nf[s * NK + i] = nf;
+        acc[s] = cscl(x[s], -c_sa[o][1] * idt);
+        an[s] = cscl(nf, c_sbf[o][0]);
+      }
+      for (int jj = 1; jj <= o; ++jj) {
+        const size_t sl = (size_t)((slot - jj) & 3);
+        const double2* Eo = g.Eh + (sl * nb + b) * 4 * NK + (size_t)m * N + i;
+        const float2* No = reinterpret_cast<const float2*>(g.Nh + (sl * nb + b) * 4 * NK) + (size_t)m * N + i;
+        const double ca = -c_sa[o][jj + 1] * idt;
+        const float cb = c_sbf[o][jj];
+        for (int s = 0; s < 4; ++s) {
+          acc[s] = cfma(ca, Eo[s * NK], acc[s]);
+          an[s] = cfma(cb, No[s * NK], an[s]);
+        }
+      }
+      for (int s = 0; s < 4; ++s) sR[s * N + i] = cadd(acc[s], d2_exact(an[s]));
+    }
+  } else {
+    // FP64 history; a mixed group's mean mode keeps it in FP64 in the second
+    // half of the member's block (the FP32 view uses the first), stride N
+    const size_t hs = g.f32 ? (size_t)N : NK;
+    auto nd = [&](size_t sl) {
+      double2* base = g.Nh + (sl * nb + b) * 4 * NK;
+      return g.f32 ? base + 2 * NK : base + (size_t)m * N;
+    };
+    double2* E = g.Eh + ((size_t)slot * nb + b) * 4 * NK + (size_t)m * N;
+    double2* Nn = nd((size_t)slot);
     const double idt = 1.0 / pr.dt;
     for (int i = tid; i < N; i += nt) {
       const double2 x[4] = {sc0[i], sc1[i], sc2[i], sq[i]};
@@ -335,15 +371,15 @@ __device__ __forceinline__ void spec_block(const GroupDev& g, int mode, Blk bk) 
       double2 acc[4];
       for (int s = 0; s < 4; ++s) {
         E[s * NK + i] = x[s];
-        Nn[s * NK + i] = nn[s];
+        Nn[s * hs + i] = nn[s];
         acc[s] = cfma(c_sb[o][0], nn[s], cscl(x[s], -c_sa[o][1] * idt));
       }
       for (int jj = 1; jj <= o; ++jj) {
         const size_t sl = (size_t)((slot - jj) & 3);
         const double2* Eo = g.Eh + (sl * nb + b) * 4 * NK + (size_t)m * N + i;
-        const double2* No = g.Nh + (sl * nb + b) * 4 * NK + (size_t)m * N + i;
+        const double2* No = nd(sl) + i;
         const double ca = -c_sa[o][jj + 1] * idt, cb = c_sb[o][jj];
-        for (int s = 0; s < 4; ++s) acc[s] = cfma(cb, No[s * NK], cfma(ca, Eo[s * NK], acc[s]));
+        for (int s = 0; s < 4; ++s) acc[s] = cfma(cb, No[s * hs], cfma(ca, Eo[s * NK], acc[s]));
       }
       for (int s = 0; s < 4; ++s) sR[s * N + i] = acc[s];
     }

@@ -490,13 +490,22 @@ __global__ void __launch_bounds__(256) k_spec3(GroupDev g, int mode) {
     const double2* x = (s2 < 6) ? X + (size_t)(3 + s2) * NK : SC(S3_Q1 + (s2 - 6));
     const double2* nn = (s2 < 6) ? NR + (size_t)s2 * NK : SC(S3_F1 + (s2 - 6));
     double2* E = g.Eh + ((size_t)slot * nb + b) * 8 * NK + (size_t)s2 * NK + col;
-    double2* Nn = g.Nh + ((size_t)slot * nb + b) * 8 * NK + (size_t)s2 * NK + col;
     double2* R = SC(S3_R + s2);
     const double2* Eo[3];
-    const double2* No[3];
     for (int jj = 1; jj <= 3; ++jj) {
       const size_t sl = (size_t)((slot - jj) & 3);
       Eo[jj - 1] = g.Eh + (sl * nb + b) * 8 * NK + (size_t)s2 * NK + col;
+    }
+    // FP64 history in every form: in a mixed group the mean mode would need
+    // it in FP64 (its explicit terms carry the 2/Re forcing and the
+    // 10^4-sized stretching), and its lanes share warps with the other
+    // modes, so an FP32 history elsewhere would diverge the warps of the
+    // block holding the mean mode, which sets the launch's time (one wave
+    // at 128 x 97 x 64: measured 0.60 -> 0.66 ms)
+    double2* Nn = g.Nh + ((size_t)slot * nb + b) * 8 * NK + (size_t)s2 * NK + col;
+    const double2* No[3];
+    for (int jj = 1; jj <= 3; ++jj) {
+      const size_t sl = (size_t)((slot - jj) & 3);
       No[jj - 1] = g.Nh + (sl * nb + b) * 8 * NK + (size_t)s2 * NK + col;
     }
     lane_sbdf_any(o, N, p, 1.0 / pr.dt, x, nn, E, Nn, Eo, No, R);
@@ -926,6 +935,10 @@ cudaError_t set_kernel_attributes3(int optin_bytes) {
   return cudaSuccess;
 }
 
+static void launch_spec3(const GroupDev& g, int mode, cudaStream_t st) {
+  k_spec3<<<dim3(cdiv(g.KZ, kModesPerBlock), g.nb), 256, 0, st>>>(g, mode);
+}
+
 // Stage s of one 3D step for one group (same numbering as the 2D stages).
 cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl) {
   const int M = g.M, K = g.K, KZ = g.KZ, Mz = g.Mz;
@@ -1042,7 +1055,7 @@ cudaError_t launch_stage3(const GroupDev& g, int stage, cudaStream_t st, int* nl
       break;
     }
     case 3:
-      k_spec3<<<dim3(cdiv(KZ, kModesPerBlock), g.nb), 256, 0, st>>>(g, 0);
+      launch_spec3(g, 0, st);
       k_tick3<<<cdiv(g.nb, 128), 128, 0, st>>>(g);
       n = 2;
       break;
@@ -1173,7 +1186,7 @@ cudaError_t launch_explicit3(const GroupDev& g, cudaStream_t st) {
     cudaError_t e = launch_stage3(g, s, st, nullptr);
     if (e) return e;
   }
-  k_spec3<<<dim3(cdiv(g.KZ, kModesPerBlock), g.nb), 256, 0, st>>>(g, 1);
+  launch_spec3(g, 1, st);
   return cudaGetLastError();
 }
 
