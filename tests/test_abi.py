@@ -87,3 +87,18 @@ def test_noalloc_argument_checks_without_gpu(lib):
         with pytest.raises(P.PttError) as ei:
             P.ptt_explicit_rhs_noalloc(prm, din, dout, 0)
         assert ei.value.code == code, (prm.nx, prm.nz, prm.precision, din, dout)
+
+
+def test_header_constants_match_the_binding():
+    """Every #define PTT_* integer of include/ptt.h has the same value in the
+    Python binding (precision forms, status codes, histogram bins)."""
+    import paper_2606_09468_gb300 as P
+    src = open(os.path.join(ROOT, "include", "ptt.h")).read()
+    defs = dict(re.findall(r"#define\s+(PTT_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src))
+    assert {"PTT_FP64", "PTT_MIXED", "PTT_MIXED_TC", "PTT_FP64_DS", "PTT_OK", "PTT_BLOWUP"} <= set(defs)
+    checked = 0
+    for name, val in defs.items():
+        if hasattr(P, name):
+            assert getattr(P, name) == int(val), (name, getattr(P, name), val)
+            checked += 1
+    assert checked >= 8, checked
